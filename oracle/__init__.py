@@ -1,0 +1,228 @@
+"""Plain FP64 CPU oracle of the entropy-stable DGSEM (arXiv 2511.17551).
+
+TEST INFRASTRUCTURE ONLY.  The test-suite, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import this module; the GPU library and its
+Python binding never do.  It compiles the C sources in this directory with gcc
+(``build()``) and exposes them through ctypes with numpy marshalling.
+"""
+import ctypes as C
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB = os.path.join(_HERE, "liboracle.so")
+_SRCS = ["or_basis.c", "or_geometry.c", "or_physics.c", "or_rhs.c", "or_thermo_chem.c",
+         "or_mlp.c"]
+
+EULER, NAVIER_STOKES = 0, 1
+VF_RANOCHA, VF_DUCROS, VF_CENTRAL = 0, 1, 2
+SF_LLF, SF_HLLC, SF_EC = 0, 1, 2
+BC_INFLOW, BC_OUTFLOW, BC_SLIP_WALL = 1, 2, 3
+
+
+def build(force=False):
+    """Compile liboracle.so (gcc, -O2, OpenMP over elements)."""
+    srcs = [os.path.join(_HERE, s) for s in _SRCS if os.path.exists(os.path.join(_HERE, s))]
+    newest = max(os.path.getmtime(s) for s in srcs + [os.path.join(_HERE, "oracle.h")])
+    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= newest:
+        return _LIB
+    tmp = _LIB + ".tmp%d" % os.getpid()
+    cmd = ["gcc", "-O2", "-std=c11", "-D_DEFAULT_SOURCE", "-fPIC", "-shared", "-fopenmp",
+           "-o", tmp] + srcs + ["-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+_lib = None
+
+
+class Problem(C.Structure):
+    _fields_ = [
+        ("dim", C.c_int), ("N", C.c_int), ("K", C.c_int64),
+        ("n_species", C.c_int), ("equations", C.c_int),
+        ("volume_flux", C.c_int), ("surface_flux", C.c_int),
+        ("gamma", C.c_double), ("mu", C.c_double), ("Pr", C.c_double),
+        ("alpha_max", C.c_double),
+        ("nbr_elem", C.c_void_p), ("nbr_face", C.c_void_p),
+        ("n_bc", C.c_int), ("bc_kind", C.c_void_p), ("bc_prim", C.c_void_p),
+        ("species", C.c_void_p), ("Ja", C.c_void_p), ("J", C.c_void_p),
+        ("alpha_override", C.c_double),
+    ]
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        _lib = C.CDLL(_LIB)
+        d, i, vp = C.c_double, C.c_int, C.c_void_p
+        sig = {
+            "or_lgl": (i, [i, vp, vp]),
+            "or_dmat": (None, [i, vp, vp]),
+            "or_vandermonde_legendre": (None, [i, vp, vp]),
+            "or_geometry": (i, [i, i, C.c_int64, vp, vp, vp]),
+            "or_rhs": (i, [vp, vp, vp, vp, vp]),
+            "or_indicator": (i, [vp, vp, vp]),
+            "or_max_dt": (d, [vp, vp, d]),
+            "or_step_rk": (i, [vp, vp, i, d, d, vp]),
+            "or_diagnostics": (i, [vp, vp, vp]),
+            "or_prim_to_cons_field": (i, [vp, vp, vp]),
+            "or_ck45": (None, [vp, vp, vp]),
+            "or_ln_mean": (d, [d, d]),
+            "or_nv": (i, [i, i]),
+            "or_flux_pair": (i, [vp, vp, vp, vp, i, vp]),
+            "or_entropy_vars_u": (i, [vp, vp, vp]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(_lib, name)
+            f.restype = res
+            f.argtypes = args
+    return _lib
+
+
+def _p(a):
+    return a.ctypes.data if a is not None else None
+
+
+def lgl(N):
+    x = np.zeros(N + 1)
+    w = np.zeros(N + 1)
+    if lib().or_lgl(N, _p(x), _p(w)):
+        raise ValueError("bad N")
+    return x, w
+
+
+def dmat(N):
+    x, _ = lgl(N)
+    D = np.zeros((N + 1, N + 1))
+    lib().or_dmat(N, _p(x), _p(D))
+    return D
+
+
+def vandermonde(N):
+    x, _ = lgl(N)
+    V = np.zeros((N + 1, N + 1))
+    lib().or_vandermonde_legendre(N, _p(x), _p(V))
+    return V
+
+
+def geometry(dim, N, xyz):
+    xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+    K = xyz.shape[0]
+    np_ = (N + 1) ** dim
+    Ja = np.zeros((K, dim, dim, np_))
+    J = np.zeros((K, np_))
+    rc = lib().or_geometry(dim, N, K, _p(xyz), _p(Ja), _p(J))
+    if rc:
+        raise ValueError("or_geometry failed (%d)" % rc)
+    return Ja, J
+
+
+class Oracle:
+    """Holds one problem (mesh + physics) and its metric terms."""
+
+    def __init__(self, dim, N, xyz, nbr_elem, nbr_face, *, n_species=0, equations=EULER,
+                 volume_flux=VF_RANOCHA, surface_flux=SF_LLF, gamma=1.4, mu=0.0, Pr=0.72,
+                 alpha_max=0.0, bc_kind=None, bc_prim=None, species=None,
+                 alpha_override=-1.0):
+        self.dim, self.N = dim, N
+        self.np = (N + 1) ** dim
+        self.nv = lib().or_nv(dim, n_species)
+        self.Ja, self.J = geometry(dim, N, xyz)
+        self.K = self.J.shape[0]
+        self.nbr_elem = np.ascontiguousarray(nbr_elem, dtype=np.int64)
+        self.nbr_face = np.ascontiguousarray(nbr_face, dtype=np.int8)
+        self.bc_kind = np.ascontiguousarray(bc_kind if bc_kind is not None else [0],
+                                            dtype=np.int32)
+        self.bc_prim = np.ascontiguousarray(
+            bc_prim if bc_prim is not None else np.zeros((1, self.nv)), dtype=np.float64)
+        self.species = (np.ascontiguousarray(species, dtype=np.float64)
+                        if species is not None else None)
+        self.P = Problem(dim=dim, N=N, K=self.K, n_species=n_species, equations=equations,
+                         volume_flux=volume_flux, surface_flux=surface_flux, gamma=gamma,
+                         mu=mu, Pr=Pr, alpha_max=alpha_max,
+                         nbr_elem=_p(self.nbr_elem), nbr_face=_p(self.nbr_face),
+                         n_bc=len(self.bc_kind) if bc_kind is not None else 0,
+                         bc_kind=_p(self.bc_kind), bc_prim=_p(self.bc_prim),
+                         species=_p(self.species), Ja=_p(self.Ja), J=_p(self.J),
+                         alpha_override=alpha_override)
+
+    def _ref(self):
+        return C.byref(self.P)
+
+    def prim_to_cons(self, w):
+        w = np.ascontiguousarray(w, dtype=np.float64)
+        u = np.zeros_like(w)
+        if lib().or_prim_to_cons_field(self._ref(), _p(w), _p(u)):
+            raise ValueError("non-physical primitive state")
+        return u
+
+    def rhs(self, u, want_alpha=False, want_grad=False):
+        u = np.ascontiguousarray(u, dtype=np.float64)
+        r = np.zeros_like(u)
+        a = np.zeros(self.K) if want_alpha else None
+        g = (np.zeros((self.K, self.dim, self.dim + 1, self.np)) if want_grad else None)
+        rc = lib().or_rhs(self._ref(), _p(u), _p(r), _p(a), _p(g))
+        if rc:
+            raise ValueError("or_rhs failed (%d)" % rc)
+        out = [r]
+        if want_alpha:
+            out.append(a)
+        if want_grad:
+            out.append(g)
+        return out[0] if len(out) == 1 else tuple(out)
+
+    def indicator(self, u):
+        u = np.ascontiguousarray(u, dtype=np.float64)
+        a = np.zeros(self.K)
+        lib().or_indicator(self._ref(), _p(u), _p(a))
+        return a
+
+    def max_dt(self, u, cfl):
+        u = np.ascontiguousarray(u, dtype=np.float64)
+        return lib().or_max_dt(self._ref(), _p(u), cfl)
+
+    def step_rk(self, u, nsteps, cfl=0.5, dt_fixed=0.0, t=0.0):
+        u = np.array(u, dtype=np.float64, copy=True, order="C")
+        tt = C.c_double(t)
+        rc = lib().or_step_rk(self._ref(), _p(u), nsteps, cfl, dt_fixed, C.byref(tt))
+        if rc:
+            raise ValueError("or_step_rk failed (%d)" % rc)
+        return u, tt.value
+
+    def flux_pair(self, uL, uR, n, which):
+        """which = 0 volume flux, 1 surface flux, 2 physical flux of uL."""
+        uL = np.ascontiguousarray(uL, dtype=np.float64)
+        uR = np.ascontiguousarray(uR, dtype=np.float64)
+        n3 = np.zeros(3)
+        n3[:len(n)] = n
+        f = np.zeros(self.nv)
+        if lib().or_flux_pair(self._ref(), _p(uL), _p(uR), _p(n3), which, _p(f)):
+            raise ValueError("non-physical state")
+        return f
+
+    def entropy_vars(self, u):
+        u = np.ascontiguousarray(u, dtype=np.float64)
+        w = np.zeros(self.nv)
+        if lib().or_entropy_vars_u(self._ref(), _p(u), _p(w)):
+            raise ValueError("non-physical state")
+        return w
+
+    def diagnostics(self, u):
+        u = np.ascontiguousarray(u, dtype=np.float64)
+        out = np.zeros(8)
+        lib().or_diagnostics(self._ref(), _p(u), _p(out))
+        return out
+
+
+def ck45():
+    A, B, c = np.zeros(5), np.zeros(5), np.zeros(5)
+    lib().or_ck45(_p(A), _p(B), _p(c))
+    return A, B, c
+
+
+def ln_mean(x, y):
+    return lib().or_ln_mean(float(x), float(y))

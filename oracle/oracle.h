@@ -1,0 +1,112 @@
+/*
+ * Plain FP64 CPU oracle of the entropy-stable DGSEM right-hand side
+ * (H3PC, arXiv 2511.17551).  TEST INFRASTRUCTURE ONLY: the test-suite, the
+ * smoke check and the CPU-baseline leg of the benchmark call it; the GPU
+ * library never links, includes or calls anything in this directory.
+ *
+ * Every routine is the simplest loop nest that follows the paper's
+ * statement of the method (section "Methodology", Eqs. mapped_equation,
+ * strong_form, fluxes_discrete_strong, differencing, fluxdiffcons, DGvec,
+ * fluxes_discrete_with_fv, finitevolumeflux, auxil, auxstrongf) and, where
+ * the paper is silent or garbled, the readings written next to each routine.
+ *
+ * Layouts (all row-major, node index fastest):
+ *   node  = i + (N+1) j + (N+1)^2 k              (x fastest)
+ *   u     [K][nv][np]   conserved (rho_1..rho_ns, rho v_1..rho v_dim, rho E)
+ *   w     [K][nv][np]   primitive (rho_1..rho_ns, v_1..v_dim, p  or  T)
+ *   xyz   [K][dim][np]  node coordinates
+ *   Ja    [K][dim][dim][np]  Ja[k][i][n][node] = J d(xi_i)/d(x_n)
+ *   J     [K][np]
+ *   faces ordered -xi,+xi,-eta,+eta,-zeta,+zeta;  nbr_elem[k][f] >= 0 is the
+ *   neighbour element, < 0 encodes boundary id  -(bc+1).
+ */
+#ifndef DG_ORACLE_H
+#define DG_ORACLE_H
+#include <stdint.h>
+
+#define OR_MAX_N 15
+#define OR_MAX_SPECIES 8
+#define OR_MAX_NV (OR_MAX_SPECIES + 4)
+
+enum { OR_EULER = 0, OR_NAVIER_STOKES = 1 };
+enum { OR_VF_RANOCHA = 0, OR_VF_DUCROS = 1, OR_VF_CENTRAL = 2 };
+enum { OR_SF_LLF = 0, OR_SF_HLLC = 1, OR_SF_EC = 2 };
+enum { OR_BC_INFLOW = 1, OR_BC_OUTFLOW = 2, OR_BC_SLIP_WALL = 3 };
+
+typedef struct {
+  int dim, N;
+  int64_t K;
+  int n_species;       /* 0: single calorically perfect gas */
+  int equations;       /* OR_EULER | OR_NAVIER_STOKES */
+  int volume_flux;     /* OR_VF_* */
+  int surface_flux;    /* OR_SF_* */
+  double gamma;        /* ideal gas only */
+  double mu, Pr;       /* NS: constant dynamic viscosity, Prandtl number */
+  double alpha_max;    /* > 0 switches on DG / subcell-FV blending */
+  const int64_t* nbr_elem;  /* [K][2dim] */
+  const int8_t* nbr_face;   /* [K][2dim] */
+  int n_bc;
+  const int* bc_kind;       /* [n_bc] */
+  const double* bc_prim;    /* [n_bc][nv] primitive external states */
+  const double* species;    /* [ns][8] = W (kg/mol), a1..a7 */
+  const double* Ja;         /* [K][dim][dim][np] */
+  const double* J;          /* [K][np] */
+  double alpha_override;    /* >= 0: use this blending factor on every element */
+} or_problem;
+
+typedef struct {
+  double rho;                     /* total density */
+  double rhos[OR_MAX_SPECIES];    /* species densities (mixtures) */
+  double v[3];
+  double p;
+  double T;                       /* mixtures: temperature; ideal gas: p/rho */
+  double c;                       /* frozen sound speed */
+  double rhoE;
+} or_prim;
+
+/* ---- basis (or_basis.c) ---- */
+void or_legendre(int n, double x, double* P, double* dP);
+int or_lgl(int N, double* x, double* w);
+void or_dmat(int N, const double* x, double* D);
+void or_vandermonde_legendre(int N, const double* x, double* V);
+int or_invert(int n, const double* A, double* Ainv);
+
+/* ---- geometry (or_geometry.c) ---- */
+int or_geometry(int dim, int N, int64_t K, const double* xyz, double* Ja, double* J);
+
+/* ---- physics (or_physics.c) ---- */
+int or_nv(int dim, int n_species);
+double or_R_univ(void);
+double or_species_energy(const double* sp, double T);  /* e_s(T) per unit mass */
+double or_species_cv(const double* sp, double T);
+double or_mixture_energy(int ns, const double* species, const double* Y, double T);
+double or_mixture_cv(int ns, const double* species, const double* Y, double T);
+int or_temperature(int ns, const double* species, const double* Y, double e, double T0,
+                   double* T, int* iters);
+int or_cons_to_prim(const or_problem* P, const double* u, or_prim* q);
+int or_prim_to_cons(const or_problem* P, const double* w, double* u);
+void or_phys_flux(const or_problem* P, const or_prim* q, const double* u, const double* n,
+                  double* f);
+void or_volume_flux(const or_problem* P, const double* uL, const or_prim* qL,
+                    const double* uR, const or_prim* qR, const double* n, double* f);
+void or_surface_flux(const or_problem* P, const double* uL, const or_prim* qL,
+                     const double* uR, const or_prim* qR, const double* n, double* f);
+double or_ln_mean(double x, double y);
+void or_entropy_vars(const or_problem* P, const or_prim* q, double* wv);
+double or_entropy(const or_problem* P, const or_prim* q);
+int or_flux_pair(const or_problem* P, const double* uL, const double* uR, const double* n,
+                 int which, double* f);
+int or_entropy_vars_u(const or_problem* P, const double* u, double* wv);
+
+/* ---- right-hand side, time stepping, diagnostics (or_rhs.c) ---- */
+int or_prim_to_cons_field(const or_problem* P, const double* w, double* u);
+int or_rhs(const or_problem* P, const double* u, double* rhs, double* alpha_out,
+           double* gradW_out);
+int or_indicator(const or_problem* P, const double* u, double* alpha);
+double or_max_dt(const or_problem* P, const double* u, double cfl);
+int or_step_rk(const or_problem* P, double* u, int nsteps, double cfl, double dt_fixed,
+               double* t);
+int or_diagnostics(const or_problem* P, const double* u, double* out);
+void or_ck45(double* A, double* B, double* c);
+
+#endif

@@ -1,0 +1,47 @@
+"""Workload builders shared by the oracle pins and the GPU parity tests.
+
+Each builder takes the caller's own LGL node set (``xi``) so that the oracle
+side and the library side each place nodes with their own basis.
+"""
+import numpy as np
+
+import workloads as W
+
+GAMMA = 1.4
+
+
+def tgv(xi, n_el, warp=0.0, mach=0.1, shape=None):
+    shape = shape or (n_el,) * 3
+    xyz, nbr, face = W.box_mesh(shape, xi, (-np.pi,) * 3, (np.pi,) * 3, periodic=True,
+                                warp=warp)
+    return xyz, nbr, face, W.tgv_primitive(xyz, GAMMA, mach)
+
+
+def vortex(xi, n_el, t=0.0):
+    xyz, nbr, face = W.box_mesh((n_el, n_el), xi, (-5.0, -5.0), (5.0, 5.0), periodic=True)
+    return xyz, nbr, face, W.vortex_primitive(xyz, t=t, gamma=GAMMA)
+
+
+def perturbed_state(w, seed, amp=0.05):
+    """Random smooth-free perturbation of a primitive state (parity stress cases)."""
+    rng = np.random.default_rng(seed)
+    w = w.copy()
+    w *= 1.0 + amp * rng.uniform(-1, 1, size=w.shape)
+    return w
+
+
+def square_cylinder_small(xi, seed=3):
+    """A 24 x 12 cut of the square-cylinder workload with the same boundary kinds."""
+    lo = (-1.2, -0.6)
+    h = 0.1
+    nx, ny = 24, 12
+    xyz, nbr, face = W.box_mesh((nx, ny), xi, lo, (lo[0] + nx * h, lo[1] + ny * h),
+                                periodic=False, bc_ids=[0, 1, 0, 0])
+    k = np.arange(nx * ny)
+    ix, iy = k % nx, k // nx
+    solid = (ix >= 8) & (ix < 12) & (iy >= 4) & (iy < 8)
+    return W._compact_and_shuffle(xyz, nbr, face, ~solid, 2, seed)
+
+
+def mach3_freestream(gamma=GAMMA, mach=3.0):
+    return np.array([1.0, 1.0, 0.0, 1.0 / (gamma * mach * mach)])

@@ -1,0 +1,152 @@
+"""Pins of the oracle's two-point and interface fluxes (Eqs. conssymm, fluxdiff,
+riemann_problem1-3) and of the logarithmic mean."""
+import mpmath
+import numpy as np
+import pytest
+
+import workloads as W
+
+
+def _orc1(orc, dim=3, **kw):
+    N = 1
+    x, _ = orc.lgl(N)
+    shape = (1,) * dim
+    xyz, nbr, face = W.box_mesh(shape, x, (0,) * dim, (1,) * dim)
+    return orc.Oracle(dim, N, xyz, nbr, face, **kw)
+
+
+def _state(rng, dim, g=1.4):
+    rho = rng.uniform(0.5, 2.0)
+    v = rng.normal(size=dim)
+    p = rng.uniform(0.5, 3.0)
+    return np.concatenate([[rho], rho * v, [p / (g - 1) + 0.5 * rho * v @ v]])
+
+
+def _prim(u, g=1.4):
+    dim = len(u) - 2
+    rho = u[0]
+    v = u[1:1 + dim] / rho
+    p = (g - 1) * (u[-1] - 0.5 * rho * v @ v)
+    return rho, v, p
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("vf", [0, 1, 2])
+def test_volume_flux_consistency_and_symmetry(orc, dim, vf):
+    o = _orc1(orc, dim, volume_flux=vf)
+    rng = np.random.default_rng(vf + 10 * dim)
+    for _ in range(20):
+        uL, uR = _state(rng, dim), _state(rng, dim)
+        n = rng.normal(size=dim)
+        f = o.flux_pair(uL, uL, n, 2)
+        assert np.allclose(o.flux_pair(uL, uL, n, 0), f, rtol=1e-14, atol=1e-14)
+        assert np.allclose(o.flux_pair(uL, uR, n, 0), o.flux_pair(uR, uL, n, 0),
+                           rtol=1e-14, atol=1e-14)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_physical_flux_textbook(orc, dim):
+    o = _orc1(orc, dim)
+    rng = np.random.default_rng(3)
+    u = _state(rng, dim)
+    n = rng.normal(size=dim)
+    rho, v, p = _prim(u)
+    vn = v @ n
+    ref = np.concatenate([[rho * vn], rho * v * vn + p * n, [(u[-1] + p) * vn]])
+    assert np.allclose(o.flux_pair(u, u, n, 2), ref, rtol=1e-14)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_ranocha_tadmor_entropy_conservation(orc, dim):
+    """(w_R - w_L) . F#(u_L,u_R) = psi_R - psi_L with psi = rho v.n (Tadmor's condition for
+    the entropy S = -rho s/(gamma-1)); a dropped or mis-signed term breaks it."""
+    o = _orc1(orc, dim, volume_flux=0)
+    rng = np.random.default_rng(4)
+    for close in (False, True):
+        for _ in range(50):
+            uL = _state(rng, dim)
+            uR = uL * (1 + 1e-3 * rng.normal(size=uL.size)) if close else _state(rng, dim)
+            n = rng.normal(size=dim)
+            F = o.flux_pair(uL, uR, n, 0)
+            wL, wR = o.entropy_vars(uL), o.entropy_vars(uR)
+            psiL, psiR = uL[1:1 + dim] @ n, uR[1:1 + dim] @ n
+            lhs = (wR - wL) @ F
+            scale = np.abs(wR - wL) @ np.abs(F) + abs(psiR) + abs(psiL)
+            assert abs(lhs - (psiR - psiL)) < 1e-12 * scale
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_entropy_variables_are_gradient_of_entropy(orc, dim):
+    o = _orc1(orc, dim)
+    rng = np.random.default_rng(5)
+    u = _state(rng, dim)
+    g = 1.4
+
+    def S(uu):
+        rho, v, p = _prim(uu)
+        return -rho * (np.log(p) - g * np.log(rho)) / (g - 1)
+
+    w = o.entropy_vars(u)
+    h = 1e-6
+    for i in range(u.size):
+        e = np.zeros_like(u)
+        e[i] = h * max(1, abs(u[i]))
+        fd = (S(u + e) - S(u - e)) / (2 * e[i])
+        assert abs(fd - w[i]) < 1e-7 * max(1, abs(w[i]))
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("sf", [0, 1])
+def test_surface_flux_consistency_and_dissipation(orc, dim, sf):
+    o = _orc1(orc, dim, surface_flux=sf)
+    rng = np.random.default_rng(6 + sf)
+    for _ in range(50):
+        uL, uR = _state(rng, dim), _state(rng, dim)
+        n = rng.normal(size=dim)
+        assert np.allclose(o.flux_pair(uL, uL, n, 1), o.flux_pair(uL, uL, n, 2),
+                           rtol=1e-13, atol=1e-13)
+        if sf == 0:  # LLF produces entropy: (w_R - w_L).F* - (psi_R - psi_L) <= 0
+            F = o.flux_pair(uL, uR, n, 1)
+            wL, wR = o.entropy_vars(uL), o.entropy_vars(uR)
+            psiL, psiR = uL[1:1 + dim] @ n, uR[1:1 + dim] @ n
+            assert (wR - wL) @ F - (psiR - psiL) <= 1e-12 * (np.abs(wR - wL) @ np.abs(F))
+
+
+def test_hllc_resolves_stationary_contact(orc):
+    """A pure density jump at rest: HLLC returns the exact flux (0, p n, 0); LLF does not."""
+    g = 1.4
+    n = np.array([0.3, -1.2, 0.5])
+    p = 1.7
+    uL = np.array([1.0, 0, 0, 0, p / (g - 1)])
+    uR = np.array([0.125, 0, 0, 0, p / (g - 1)])
+    exact = np.concatenate([[0], p * n, [0]])
+    hllc = _orc1(orc, 3, surface_flux=1).flux_pair(uL, uR, n, 1)
+    llf = _orc1(orc, 3, surface_flux=0).flux_pair(uL, uR, n, 1)
+    assert np.allclose(hllc, exact, atol=1e-14)
+    assert np.abs(llf - exact).max() > 0.1
+
+
+def test_hllc_upwinds_supersonic_flow(orc):
+    o = _orc1(orc, 2, surface_flux=1)
+    g = 1.4
+    uL = np.array([1.0, 3.0, 0.0, 1.0 / (g - 1) + 4.5])  # u = 3 > c ~ 1.18
+    uR = np.array([0.5, 1.0, 0.2, 0.4 / (g - 1) + 1.04])
+    n = np.array([2.0, 0.0])
+    assert np.allclose(o.flux_pair(uL, uR, n, 1), o.flux_pair(uL, uL, n, 2), rtol=1e-14)
+    assert np.allclose(o.flux_pair(uR, uL, -n, 1), o.flux_pair(uL, uL, -n, 2), rtol=1e-14)
+
+
+def test_ln_mean_branches(orc):
+    mpmath.mp.dps = 40
+    rng = np.random.default_rng(7)
+    for _ in range(200):
+        x = rng.uniform(0.1, 10)
+        y = x * np.exp(rng.normal() * rng.choice([1e-6, 1e-3, 1e-2, 0.3, 2]))
+        exact = (mpmath.mpf(y) - mpmath.mpf(x)) / mpmath.log(mpmath.mpf(y) / mpmath.mpf(x))
+        assert abs(orc.ln_mean(x, y) - float(exact)) < 4e-15 * float(exact)
+    assert orc.ln_mean(2.5, 2.5) == 2.5
+    # both branches agree at the switch point |x-y|^2/(x+y)^2 = 1e-4
+    x = 1.0
+    y = (1 + 1e-2) / (1 - 1e-2)
+    lo, hi = orc.ln_mean(x, y * (1 - 1e-9)), orc.ln_mean(x, y * (1 + 1e-9))
+    assert abs(hi - lo) < 1e-8 * lo
