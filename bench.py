@@ -1,0 +1,293 @@
+"""Benchmark: DOF x RHS-evaluations per second of the entropy-stable DGSEM on GB300.
+
+Workload (default): Navier-Stokes Taylor-Green vortex, Re = 1600, Pr = 0.72, Ma = 0.1,
+32^3 curved hexahedra (x_i += 0.1 sin x sin y sin z), degree N = 3, seeded synthetic
+initial state.  One step = one Carpenter-Kennedy RK45 step (5 right-hand sides) at
+CFL 0.5 with the time step reduced on the device.  ``value`` is the mixed form
+(FP32 fluxes / sums, FP64 reductions); the FP64 form is timed beside it.
+
+Arms: ``--impl ours`` (default) runs libdg; ``--impl reference`` times the FP64 CPU
+oracle on the host cores on a bounded sample of the same workload.
+Multi-GPU: the method shards by elements, but every gpurun box has one GPU, so N > 1
+runs independent replicas (one per rank, weak scaling, no collective on the data path).
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+CONFIGS = {
+    "tgv_ns_32^3_N3": dict(n_el=32, N=3, warp=0.1, mu=1.0 / 1600.0),
+    "tgv_ns_16^3_N7": dict(n_el=16, N=7, warp=0.1, mu=1.0 / 1600.0),
+    "tgv_euler_4^3_N3": dict(n_el=4, N=3, warp=0.0, mu=0.0),
+}
+# algorithmic HBM words per node of one RK-stage launch (unique bytes, neighbour traces
+# excluded): main kernel reads u, Ja, 1/J, gradW, du and writes du, u_new;
+# gradient kernel reads u, Ja, 1/J and writes gradW.
+WORDS_MAIN_NS = 5 + 9 + 1 + 12 + 5 + 5 + 5
+WORDS_MAIN_EULER = 5 + 9 + 1 + 5 + 5 + 5
+WORDS_GRAD = 5 + 9 + 1 + 12
+
+
+def _env_rank():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampler during the timed region (200 ms)."""
+
+    def __init__(self, gpu_index):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), "--query-gpu=" + q,
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        self.p.wait()
+        self.f.flush()
+        rows = [r.split(",") for r in open(self.f.name).read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except (ValueError, IndexError):
+                continue
+            for nme, val in zip(names, r[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nme)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(mx)) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def build_workload(cfg, xi):
+    xyz, nbr, face = W.box_mesh((cfg["n_el"],) * 3, xi, (-np.pi,) * 3, (np.pi,) * 3,
+                                periodic=True, warp=cfg["warp"])
+    return xyz, nbr, face, W.tgv_primitive(xyz)
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+    import paper_2511_17551_gb300 as dg
+
+    torch.cuda.set_device(local_rank)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    cfg = CONFIGS[args.config]
+    N = cfg["N"]
+    xi, _ = dg.dg_lgl_nodes(N)
+    xyz, nbr, face, w0 = build_workload(cfg, xi)
+    K, npn = xyz.shape[0], (N + 1) ** 3
+    dof = K * npn * 5
+    eq = dg.DG_NAVIER_STOKES if cfg["mu"] > 0 else dg.DG_EULER
+    stream = torch.cuda.current_stream()
+
+    def make(precision):
+        s = dg.Solver(3, N, xyz, nbr, face, equations=eq, mu=cfg["mu"], Pr=0.72,
+                      precision=precision, stream=stream.cuda_stream)
+        s.set_primitive(w0)
+        return s
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def timed_steps(s, steps, profile=False):
+        s.step(args.warmup, cfg_cfl)
+        if profile:
+            dg.dg_profile(s.ctx, 1)
+            dg.dg_profile_read(s.ctx)
+        barrier()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        s.step(steps, cfg_cfl)
+        t1.record(stream)
+        barrier()
+        ms = t0.elapsed_time(t1)
+        prof = dg.dg_profile_read(s.ctx) if profile else None
+        if profile:
+            dg.dg_profile(s.ctx, 0)
+        return ms, prof
+
+    cfg_cfl = 0.5
+    # --- mixed form: the headline
+    s = make(dg.DG_MIXED)
+    clocks = Clocks(local_rank)
+    ms, prof = timed_steps(s, args.steps, profile=True)
+    clk = clocks.stop()
+    ms_t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms = float(ms_t.item())
+    value = world * dof * 5 * args.steps / (ms * 1e-3)
+    # --- end to end through the C ABI with host buffers (pinned), copies inside the region
+    u_host = torch.empty((K, 5, npn), dtype=torch.float64).pin_memory()
+    dg.dg_get_state(s.ctx, u_host)
+    e2e_steps = max(1, min(args.steps, 10))
+    barrier()
+    t_start = time.perf_counter()
+    for _ in range(e2e_steps):
+        dg.dg_set_state(s.ctx, u_host)
+        dg.dg_step_rk(s.ctx, 1, cfg_cfl)
+        dg.dg_get_state(s.ctx, u_host)
+    barrier()
+    e2e_s = time.perf_counter() - t_start
+    e2e_value = world * dof * 5 * e2e_steps / e2e_s
+    s.close()
+    # --- FP64 form on the same GPU
+    s64 = make(dg.DG_FP64)
+    k64 = max(1, min(args.steps, 5))
+    ms64, prof64 = timed_steps(s64, k64, profile=True)
+    s64.close()
+    value64 = world * dof * 5 * k64 / (ms64 * 1e-3)
+
+    # roofline of the dominant kernel (main RHS / RK-stage kernel of the mixed form)
+    peak, peak_kind = _peaks()
+    rhs_ms, rhs_n = prof["rhs"]
+    words = WORDS_MAIN_NS if eq == dg.DG_NAVIER_STOKES else WORDS_MAIN_EULER
+    bytes_launch = words * 4 * K * npn
+    achieved = bytes_launch / (rhs_ms / rhs_n * 1e-3) / 1e9
+    launches = sum(n for _, n in prof.values())
+    out = {
+        "metric": "DOF*RHS-evals/s (FP32+FP64-reductions form; FP64 form beside it)",
+        "value": value, "unit": "DOF*RHS/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": args.config, "elements": K, "N": N, "dof": dof,
+                   "rk": "CK45 5-stage, CFL 0.5, device dt", "parallelism": "replicas",
+                   "l2_flush": "working set %.0f MB > L2 (129 MB)" % (
+                       (words + WORDS_GRAD) * 4 * K * npn / 1e6)},
+        "fp64_form": {"value": value64, "ms_per_step": ms64 / k64, "steps": k64,
+                      "rhs_kernel_ms": prof64["rhs"][0] / max(1, prof64["rhs"][1])},
+        "e2e": {"value": e2e_value, "unit": "DOF*RHS/s", "h2d_bytes_per_step": dof * 8,
+                "d2h_bytes_per_step": dof * 8},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "kernel": "rhs_kernel<3,%d,1,NS> f32" % N,
+                     "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)"},
+        "kernels": {k: {"ms_per_launch": v[0] / v[1], "launches": v[1]}
+                    for k, v in prof.items() if v[1]},
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    if rank == 0:
+        if not args.no_cpu_baseline:
+            out["cpu_baseline"] = cpu_baseline(cfg, args.cpu_seconds)
+        print(json.dumps(out))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def cpu_baseline(cfg, budget_s):
+    """The oracle as it stands, FP64, all host cores (OpenMP over elements)."""
+    import oracle
+    N = cfg["N"]
+    xo, _ = oracle.lgl(N)
+    xyz, nbr, face, w0 = build_workload(cfg, xo)
+    o = oracle.Oracle(3, N, xyz, nbr, face, equations=1 if cfg["mu"] > 0 else 0, mu=cfg["mu"],
+                      Pr=0.72)
+    u = o.prim_to_cons(w0)
+    dof = u.size
+    n, t0 = 0, time.perf_counter()
+    while True:
+        o.rhs(u)
+        n += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count()))
+    return {"value": dof * n / dt, "unit": "DOF*RHS/s", "cores": cores, "kind": "oracle",
+            "sample": "%d full right-hand sides of the %d-element workload in %.1f s" % (
+                n, xyz.shape[0], dt)}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    import oracle
+    cfg = CONFIGS[args.config]
+    N = cfg["N"]
+    xo, _ = oracle.lgl(N)
+    # bounded sample: the same TGV at 8^3 elements (same N, mesh warp and physics)
+    n_el = min(cfg["n_el"], 8)
+    xyz, nbr, face = W.box_mesh((n_el,) * 3, xo, (-np.pi,) * 3, (np.pi,) * 3, periodic=True,
+                                warp=cfg["warp"])
+    o = oracle.Oracle(3, N, xyz, nbr, face, equations=1 if cfg["mu"] > 0 else 0, mu=cfg["mu"],
+                      Pr=0.72)
+    u = o.prim_to_cons(W.tgv_primitive(xyz))
+    dof = u.size
+    u, _ = o.step_rk(u, args.warmup)
+    t0 = time.perf_counter()
+    u, _ = o.step_rk(u, args.steps)
+    dt = time.perf_counter() - t0
+    value = dof * 5 * args.steps / dt
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count()))
+    sample = "%d^3-element cut of %s, %d CK45 steps" % (n_el, args.config, args.steps)
+    print(json.dumps({
+        "impl": "reference", "metric": "DOF*RHS-evals/s (FP32+FP64-reductions form; FP64 form beside it)",
+        "value": value, "unit": "DOF*RHS/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.config, "elements_sampled": n_el ** 3, "N": N},
+        "cpu_baseline": {"value": value, "unit": "DOF*RHS/s", "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "DOF*RHS/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="tgv_ns_32^3_N3", choices=sorted(CONFIGS))
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank, world, local_rank = _env_rank()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

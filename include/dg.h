@@ -1,0 +1,166 @@
+/*
+ * dg.h -- C ABI of libdg, a GB300 (sm_103a) implementation of the right-hand
+ * side and low-storage Runge-Kutta stepping of the entropy-stable DGSEM of
+ * Peyvan, Shukla & Karniadakis, "H3PC" (arXiv 2511.17551).
+ *
+ * The calls follow the paper's problem statement  dU/dt + div F = S  with
+ * boundary data U = Phi and initial data U(x,0) = Psi (Methodology, Eq. system)
+ * and its semi-discrete form (Eqs. strong_form, fluxes_discrete_strong).
+ *
+ * Conventions shared by every entry point
+ *  - Layouts are row-major with the node index fastest; node = i + (N+1) j
+ *    + (N+1)^2 k.  A state is [K][nv][np]: nv = n_sp + dim + 1 conserved
+ *    variables (rho_1..rho_nsp, rho v_1..rho v_dim, rho E; Eq. Uconserv),
+ *    n_sp = max(1, n_species), np = (N+1)^dim.  Primitive states use the same
+ *    shape with (rho_s, v, p) for one gas and (rho_s, v, T) for mixtures.
+ *  - Faces are ordered -xi,+xi,-eta,+eta,-zeta,+zeta.  nbr_elem[k][f] >= 0
+ *    names the neighbour element; a negative value -(b+1) names boundary b.
+ *    Face f of k must meet face f^1 of its neighbour with orientation 0
+ *    (conforming, aligned hexahedra/quadrilaterals).
+ *  - Host pointers passed to dg_init_mesh are read during the call and not
+ *    retained.  Device pointers passed to dg_rhs are borrowed for the call.
+ *    libdg owns every internal buffer (state, RK register, metric terms,
+ *    gradients, temperature cache, surrogate weights) and frees them in
+ *    dg_destroy.
+ *  - Arguments are validated before any work is queued; an invalid call
+ *    returns DG_EINVAL and changes nothing.  Work is queued on the context
+ *    stream.  Errors detected on the device (non-physical state, Newton
+ *    failure) are latched in a device status word and returned by the next
+ *    dg_sync / dg_step_rk / dg_get_state; kernels never trap.
+ *  - No call falls back to a CPU implementation: without a usable CUDA device
+ *    dg_init_mesh returns DG_ECUDA.
+ */
+#ifndef DG_H
+#define DG_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dg_ctx dg_ctx;
+
+typedef enum {
+  DG_OK = 0,
+  DG_EINVAL = 1,    /* bad argument or unsupported combination */
+  DG_ENOMEM = 2,    /* device allocation failed */
+  DG_ECUDA = 3,     /* CUDA runtime error, or no device */
+  DG_ENONPHYS = 4,  /* rho <= 0, p <= 0 or NaN met on the device */
+  DG_ENEWTON = 5,   /* temperature Newton iteration did not converge */
+  DG_ETIMEOUT = 6,  /* a bounded wait on the device ran out */
+  DG_ESTATE = 7     /* call out of order (e.g. no state set) */
+} dg_status;
+
+enum { DG_EULER = 0, DG_NAVIER_STOKES = 1 };
+/* two-point volume flux F# of Eq. fluxdiffcons */
+enum { DG_VF_RANOCHA = 0, DG_VF_DUCROS = 1, DG_VF_CENTRAL = 2 };
+/* interface flux F^Rie of Eqs. riemann_problem1-3; DG_SF_EC uses F# itself */
+enum { DG_SF_LLF = 0, DG_SF_HLLC = 1, DG_SF_EC = 2 };
+enum { DG_FP64 = 0, DG_MIXED = 1 };
+enum { DG_THERMO_NEWTON = 0, DG_THERMO_MLP = 1 };
+enum { DG_BC_INFLOW = 1, DG_BC_OUTFLOW = 2, DG_BC_SLIP_WALL = 3 };
+
+typedef struct {
+  int dim;                  /* 2 or 3 */
+  int N;                    /* polynomial degree on LGL nodes, 1..7 */
+  int64_t K;                /* number of elements, >= 1, < 2^31 */
+  const double* node_xyz;   /* host [K][dim][np]: geometry sampled at the LGL nodes
+                               returned by dg_lgl_nodes (degree-N map, Eq. mapp) */
+  const int64_t* nbr_elem;  /* host [K][2 dim] */
+  const int8_t* nbr_face;   /* host [K][2 dim], must equal f^1 */
+  const int8_t* nbr_orient; /* host [K][2 dim] or NULL; must be 0 */
+} dg_mesh_desc;
+
+typedef struct {
+  int equations;            /* DG_EULER | DG_NAVIER_STOKES (one gas, periodic only) */
+  int n_species;            /* 0: one calorically perfect gas; 1..8: mixture */
+  double gamma;             /* ratio of specific heats (one gas) */
+  double mu, Pr;            /* Navier-Stokes: dynamic viscosity, Prandtl number */
+  const double* species;    /* host [n_species][8] = W (kg/mol), a1..a7, or NULL */
+  int volume_flux;          /* DG_VF_* */
+  int surface_flux;         /* DG_SF_* */
+  double alpha_max;         /* > 0 turns on DG / subcell-FV blending, alpha in [0, alpha_max] */
+  int precision;            /* DG_FP64 | DG_MIXED (FP32 fluxes and sums, FP64 reductions) */
+  int thermo;               /* DG_THERMO_NEWTON | DG_THERMO_MLP (mixtures) */
+  int n_bc;                 /* number of boundary ids */
+  const int* bc_kind;       /* host [n_bc]: DG_BC_* */
+  const double* bc_prim;    /* host [n_bc][nv]: external primitive states */
+  void* stream;             /* cudaStream_t to queue work on, or NULL for a private stream */
+} dg_physics_desc;
+
+/* LGL nodes and weights used by libdg for degree N (host arrays of N+1).
+ * Reading of Eqs. lagrange_3d and lag: -1, +1 and the roots of P_N'. */
+dg_status dg_lgl_nodes(int N, double* nodes, double* weights);
+
+/* Build a context: copies geometry and topology to the device and computes
+ * the metric terms Ja^i = J grad(xi_i) (curl form) and J (Eqs. mapped_equation,
+ * jacobian) on the GPU.  *out receives the context or NULL on failure. */
+dg_status dg_init_mesh(const dg_mesh_desc* mesh, const dg_physics_desc* phys, dg_ctx** out);
+
+/* Set the state from FP64 conserved variables [K][nv][np] (host or device
+ * pointer, copied; converted to FP32 in DG_MIXED).  t is the solution time. */
+dg_status dg_set_state(dg_ctx* ctx, const double* u, int on_device, double t);
+
+/* Set the state from FP64 primitive variables (Eq. total_energy / eos applied
+ * on the device). */
+dg_status dg_set_state_primitive(dg_ctx* ctx, const double* w, int on_device, double t);
+
+/* Copy the current state to u (FP64 [K][nv][np], host or device) and its time
+ * to *t (may be NULL).  Synchronises the context stream. */
+dg_status dg_get_state(dg_ctx* ctx, double* u, int on_device, double* t);
+
+/* rhs = du/dt evaluated at u (Eq. strong_form with the split volume term of
+ * Eq. fluxdiffcons and, for Navier-Stokes, the BR1 terms of Eqs. auxil and
+ * auxstrongf).  u and rhs are device pointers of the context's precision
+ * (double*, or float* in DG_MIXED), [K][nv][np]; u and rhs must not overlap.
+ * Queued on the context stream; returns before the work finishes. */
+dg_status dg_rhs(dg_ctx* ctx, const void* u, void* rhs, double t);
+
+/* Advance the internal state by nsteps steps of the Carpenter-Kennedy
+ * five-stage fourth-order 2N-storage Runge-Kutta scheme.  dt_fixed > 0 uses
+ * that step; otherwise dt = cfl * 2 / ((N+1) max lambda) per step with
+ * lambda = sum_i (|v.Ja^i| + c |Ja^i|) / J (plus a viscous bound for
+ * Navier-Stokes), reduced on the device.  *t_inout is advanced by the elapsed
+ * time.  Synchronises at the end and returns any latched device error. */
+dg_status dg_step_rk(dg_ctx* ctx, int nsteps, double cfl, double dt_fixed, double* t_inout);
+
+/* FP64 domain integrals of the current state (Eqs. TGV_KE, TGV_SD):
+ * out[8] = { KE/|Omega|, enstrophy/|Omega|, int S, int rho, int rho E,
+ *            |Omega|, int (div v)^2 / |Omega|, 0 }. Synchronises. */
+dg_status dg_diagnostics(dg_ctx* ctx, double out[8]);
+
+/* Blending factors alpha [K] used by the last right-hand side (FP64, host). */
+dg_status dg_get_alpha(dg_ctx* ctx, double* alpha);
+
+/* BR1 gradients of (v, p/rho) from the last Navier-Stokes right-hand side,
+ * [K][dim][dim+1][np] FP64 host. */
+dg_status dg_get_gradients(dg_ctx* ctx, double* grad);
+
+/* Per-kernel device timing (tracing).  While enabled, every kernel launch of the
+ * context is bracketed by CUDA events recorded on the context stream.
+ * dg_profile_read waits for the stream and returns, per kernel kind, the summed
+ * device milliseconds and the number of launches since the last read
+ * (kinds: DG_PROF_RHS, DG_PROF_GRAD, DG_PROF_INDICATOR, DG_PROF_LAMBDA,
+ * DG_PROF_THERMO, DG_PROF_MLP, DG_PROF_CHEM, DG_PROF_OTHER); then it resets them.
+ * ms and launches are host arrays of n entries (n <= DG_PROF_KINDS). */
+enum { DG_PROF_RHS = 0, DG_PROF_GRAD = 1, DG_PROF_INDICATOR = 2, DG_PROF_LAMBDA = 3,
+       DG_PROF_THERMO = 4, DG_PROF_MLP = 5, DG_PROF_CHEM = 6, DG_PROF_OTHER = 7,
+       DG_PROF_KINDS = 8 };
+dg_status dg_profile(dg_ctx* ctx, int enable);
+dg_status dg_profile_read(dg_ctx* ctx, double* ms, int64_t* launches, int n);
+
+/* Wait (bounded) for the context stream, then return and clear the latched
+ * device status. */
+dg_status dg_sync(dg_ctx* ctx);
+
+/* Element index of the first latched device error, or -1. */
+int64_t dg_error_element(dg_ctx* ctx);
+
+const char* dg_status_string(dg_status s);
+
+void dg_destroy(dg_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,258 @@
+"""GB300-native entropy-stable DGSEM (arXiv 2511.17551) -- Python binding of libdg.
+
+A thin ctypes layer over the C ABI declared in ``include/dg.h``: the functions
+below carry the same names and only marshal arguments.  Every step of the
+right-hand side and of the Runge-Kutta stepping runs in the CUDA kernels of
+``libdg.so``; there is no CPU fallback.  Importing this module does not need a
+GPU; creating a context does, and fails with DgError(DG_ECUDA) without one.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+__all__ = [
+    "DgError", "lib", "dg_lgl_nodes", "dg_init_mesh", "dg_set_state", "dg_set_state_primitive",
+    "dg_get_state", "dg_rhs", "dg_step_rk", "dg_diagnostics", "dg_get_alpha", "dg_get_gradients",
+    "dg_sync", "dg_destroy", "dg_error_element", "dg_profile", "dg_profile_read", "Solver",
+    "EXPORTED",
+]
+
+DG_OK, DG_EINVAL, DG_ENOMEM, DG_ECUDA, DG_ENONPHYS, DG_ENEWTON, DG_ETIMEOUT, DG_ESTATE = range(8)
+DG_EULER, DG_NAVIER_STOKES = 0, 1
+DG_VF_RANOCHA, DG_VF_DUCROS, DG_VF_CENTRAL = 0, 1, 2
+DG_SF_LLF, DG_SF_HLLC, DG_SF_EC = 0, 1, 2
+DG_FP64, DG_MIXED = 0, 1
+DG_THERMO_NEWTON, DG_THERMO_MLP = 0, 1
+DG_BC_INFLOW, DG_BC_OUTFLOW, DG_BC_SLIP_WALL = 1, 2, 3
+
+# every symbol declared in include/dg.h
+EXPORTED = [
+    "dg_lgl_nodes", "dg_init_mesh", "dg_set_state", "dg_set_state_primitive", "dg_get_state",
+    "dg_rhs", "dg_step_rk", "dg_diagnostics", "dg_get_alpha", "dg_get_gradients", "dg_sync",
+    "dg_error_element", "dg_status_string", "dg_destroy", "dg_profile", "dg_profile_read",
+]
+PROF_KINDS = ["rhs", "gradients", "indicator", "lambda", "thermo", "mlp", "chem", "other"]
+
+
+class DgError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        msg = lib().dg_status_string(code).decode()
+        super().__init__("%s: %s (%d)" % (where, msg, code))
+
+
+class MeshDesc(C.Structure):
+    _fields_ = [("dim", C.c_int), ("N", C.c_int), ("K", C.c_int64),
+                ("node_xyz", C.c_void_p), ("nbr_elem", C.c_void_p),
+                ("nbr_face", C.c_void_p), ("nbr_orient", C.c_void_p)]
+
+
+class PhysicsDesc(C.Structure):
+    _fields_ = [("equations", C.c_int), ("n_species", C.c_int), ("gamma", C.c_double),
+                ("mu", C.c_double), ("Pr", C.c_double), ("species", C.c_void_p),
+                ("volume_flux", C.c_int), ("surface_flux", C.c_int),
+                ("alpha_max", C.c_double), ("precision", C.c_int), ("thermo", C.c_int),
+                ("n_bc", C.c_int), ("bc_kind", C.c_void_p), ("bc_prim", C.c_void_p),
+                ("stream", C.c_void_p)]
+
+
+_lib = None
+
+
+def lib():
+    """Load libdg.so (building it in-tree when missing or stale)."""
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        _lib = C.CDLL(path)
+        i, d, vp, i64 = C.c_int, C.c_double, C.c_void_p, C.c_int64
+        sig = {
+            "dg_lgl_nodes": (i, [i, vp, vp]),
+            "dg_init_mesh": (i, [vp, vp, vp]),
+            "dg_set_state": (i, [vp, vp, i, d]),
+            "dg_set_state_primitive": (i, [vp, vp, i, d]),
+            "dg_get_state": (i, [vp, vp, i, vp]),
+            "dg_rhs": (i, [vp, vp, vp, d]),
+            "dg_step_rk": (i, [vp, i, d, d, vp]),
+            "dg_diagnostics": (i, [vp, vp]),
+            "dg_get_alpha": (i, [vp, vp]),
+            "dg_get_gradients": (i, [vp, vp]),
+            "dg_sync": (i, [vp]),
+            "dg_error_element": (i64, [vp]),
+            "dg_status_string": (C.c_char_p, [i]),
+            "dg_destroy": (None, [vp]),
+            "dg_profile": (i, [vp, i]),
+            "dg_profile_read": (i, [vp, vp, vp, i]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(_lib, name)
+            f.restype = res
+            f.argtypes = args
+    return _lib
+
+
+def _check(code, where):
+    if code != DG_OK:
+        raise DgError(code, where)
+
+
+def _ptr(a):
+    """Address of a numpy array or of a torch tensor (device or host)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    return a.ctypes.data
+
+
+def _on_device(a):
+    return int(bool(getattr(a, "is_cuda", False)))
+
+
+# ----------------------------------------------------------------- C-ABI mirrors
+def dg_lgl_nodes(N):
+    x = np.zeros(N + 1)
+    w = np.zeros(N + 1)
+    _check(lib().dg_lgl_nodes(N, _ptr(x), _ptr(w)), "dg_lgl_nodes")
+    return x, w
+
+
+def dg_init_mesh(mesh, phys):
+    ctx = C.c_void_p()
+    _check(lib().dg_init_mesh(C.byref(mesh), C.byref(phys), C.byref(ctx)), "dg_init_mesh")
+    return ctx
+
+
+def dg_set_state(ctx, u, t=0.0):
+    _check(lib().dg_set_state(ctx, _ptr(u), _on_device(u), t), "dg_set_state")
+
+
+def dg_set_state_primitive(ctx, w, t=0.0):
+    _check(lib().dg_set_state_primitive(ctx, _ptr(w), _on_device(w), t), "dg_set_state_primitive")
+
+
+def dg_get_state(ctx, u):
+    t = C.c_double()
+    _check(lib().dg_get_state(ctx, _ptr(u), _on_device(u), C.byref(t)), "dg_get_state")
+    return t.value
+
+
+def dg_rhs(ctx, u, rhs, t=0.0):
+    _check(lib().dg_rhs(ctx, _ptr(u), _ptr(rhs), t), "dg_rhs")
+
+
+def dg_step_rk(ctx, nsteps, cfl=0.5, dt_fixed=0.0, t=0.0):
+    tt = C.c_double(t)
+    _check(lib().dg_step_rk(ctx, nsteps, cfl, dt_fixed, C.byref(tt)), "dg_step_rk")
+    return tt.value
+
+
+def dg_diagnostics(ctx):
+    out = np.zeros(8)
+    _check(lib().dg_diagnostics(ctx, _ptr(out)), "dg_diagnostics")
+    return out
+
+
+def dg_get_alpha(ctx, K):
+    a = np.zeros(K)
+    _check(lib().dg_get_alpha(ctx, _ptr(a)), "dg_get_alpha")
+    return a
+
+
+def dg_get_gradients(ctx, shape):
+    g = np.zeros(shape)
+    _check(lib().dg_get_gradients(ctx, _ptr(g)), "dg_get_gradients")
+    return g
+
+
+def dg_sync(ctx):
+    _check(lib().dg_sync(ctx), "dg_sync")
+
+
+def dg_error_element(ctx):
+    return lib().dg_error_element(ctx)
+
+
+def dg_profile(ctx, enable):
+    _check(lib().dg_profile(ctx, int(enable)), "dg_profile")
+
+
+def dg_profile_read(ctx):
+    """{kind: (milliseconds, launches)} since the last read."""
+    n = len(PROF_KINDS)
+    ms = np.zeros(n)
+    cnt = np.zeros(n, dtype=np.int64)
+    _check(lib().dg_profile_read(ctx, _ptr(ms), _ptr(cnt), n), "dg_profile_read")
+    return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(PROF_KINDS)}
+
+
+def dg_destroy(ctx):
+    if ctx:
+        lib().dg_destroy(ctx)
+
+
+# ----------------------------------------------------------------- convenience holder
+class Solver:
+    """Owns one libdg context and the host arrays its descriptors point at."""
+
+    def __init__(self, dim, N, xyz, nbr_elem, nbr_face, *, n_species=0, equations=DG_EULER,
+                 gamma=1.4, mu=0.0, Pr=0.72, species=None, volume_flux=DG_VF_RANOCHA,
+                 surface_flux=DG_SF_LLF, alpha_max=0.0, precision=DG_FP64,
+                 thermo=DG_THERMO_NEWTON, bc_kind=None, bc_prim=None, stream=None):
+        self.dim, self.N = dim, N
+        self.np = (N + 1) ** dim
+        self.nsp = max(1, n_species)
+        self.nv = self.nsp + dim + 1
+        self.precision = precision
+        self._xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+        self.K = self._xyz.shape[0]
+        self._nbr = np.ascontiguousarray(nbr_elem, dtype=np.int64)
+        self._face = np.ascontiguousarray(nbr_face, dtype=np.int8)
+        self._species = (np.ascontiguousarray(species, dtype=np.float64)
+                         if species is not None else None)
+        self._bck = np.ascontiguousarray(bc_kind if bc_kind is not None else [1], dtype=np.int32)
+        self._bcp = np.ascontiguousarray(bc_prim if bc_prim is not None else np.zeros((1, self.nv)),
+                                         dtype=np.float64)
+        mesh = MeshDesc(dim=dim, N=N, K=self.K, node_xyz=_ptr(self._xyz), nbr_elem=_ptr(self._nbr),
+                        nbr_face=_ptr(self._face), nbr_orient=None)
+        phys = PhysicsDesc(equations=equations, n_species=n_species, gamma=gamma, mu=mu, Pr=Pr,
+                           species=_ptr(self._species), volume_flux=volume_flux,
+                           surface_flux=surface_flux, alpha_max=alpha_max, precision=precision,
+                           thermo=thermo, n_bc=len(self._bck) if bc_kind is not None else 0,
+                           bc_kind=_ptr(self._bck), bc_prim=_ptr(self._bcp), stream=stream)
+        self.ctx = dg_init_mesh(mesh, phys)
+
+    @property
+    def shape(self):
+        return (self.K, self.nv, self.np)
+
+    def set_state(self, u, t=0.0):
+        dg_set_state(self.ctx, np.ascontiguousarray(u, dtype=np.float64) if isinstance(u, np.ndarray) else u, t)
+
+    def set_primitive(self, w, t=0.0):
+        dg_set_state_primitive(self.ctx, np.ascontiguousarray(w, dtype=np.float64) if isinstance(w, np.ndarray) else w, t)
+
+    def get_state(self):
+        u = np.zeros(self.shape)
+        t = dg_get_state(self.ctx, u)
+        return u, t
+
+    def step(self, nsteps, cfl=0.5, dt_fixed=0.0, t=0.0):
+        return dg_step_rk(self.ctx, nsteps, cfl, dt_fixed, t)
+
+    def diagnostics(self):
+        return dg_diagnostics(self.ctx)
+
+    def close(self):
+        if self.ctx:
+            dg_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,900 @@
+// C ABI of libdg (see include/dg.h): context management, set-up kernels (metric
+// terms, primitive -> conserved), state transfer, RK driver and FP64 domain
+// integrals.  The right-hand-side kernels live in dg_rhs_f64.cu / dg_rhs_f32.cu.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+#include <time.h>
+
+#include "../../include/dg.h"
+#include "dg_internal.h"
+#include "dg_thermo.h"
+
+struct dg_ctx {
+  int dev;
+  int dim, N, np, nv, nsp, nf;
+  int64_t K;
+  int equations, n_species, vf, sf, precision, thermo, n_bc;
+  double gamma, mu, Pr, alpha_max;
+  cudaStream_t stream;
+  bool own_stream;
+  size_t rs;  // bytes per real of the form
+  int* nbr;
+  double *Ja64, *J64, *invJ64;
+  float *Ja32, *invJ32;
+  void* u[2];
+  int cur;
+  void* du;
+  void* gradW;
+  void* alpha_raw;
+  double* alpha_used;
+  int* bc_kind;
+  void* bc_u;
+  double* scal;
+  unsigned long long* lam;
+  int lam_slot;
+  unsigned long long* status;
+  double* partial;
+  int diag_blocks;
+  double* stage64;  // FP64 staging buffer for host <-> device state transfers
+  bool have_state, have_grad, have_alpha;
+  DgThermo th;  // mixtures
+  // tracing: CUDA events around each launch while profiling is on
+  int prof;
+  cudaEvent_t* ev;
+  int* ev_kind;
+  int ev_cap, ev_used;
+  double prof_ms[DG_PROF_KINDS];
+  int64_t prof_n[DG_PROF_KINDS];
+};
+
+namespace {
+
+__constant__ double c_D64[(DG_MAXN + 1) * (DG_MAXN + 1)];
+__constant__ double c_w64[DG_MAXN + 1];
+int g_basis_uploaded_for = -1;  // device id
+
+#define CK(x)                                   \
+  do {                                          \
+    cudaError_t e_ = (x);                       \
+    if (e_ != cudaSuccess) return DG_ECUDA;     \
+  } while (0)
+
+cudaError_t upload_all_bases(int dev) {
+  if (g_basis_uploaded_for == dev) return cudaSuccess;
+  cudaError_t e = dg_f64_upload_basis();
+  if (e == cudaSuccess) e = dg_f32_upload_basis();
+  if (e == cudaSuccess) e = dg_thermo_upload_basis();
+  if (e == cudaSuccess) g_basis_uploaded_for = dev;
+  return e;
+}
+
+cudaError_t upload_local_basis(int N) {
+  DgHostBasis b;
+  if (dg_host_basis(N, &b)) return cudaErrorInvalidValue;
+  double D[(DG_MAXN + 1) * (DG_MAXN + 1)] = {0}, w[DG_MAXN + 1] = {0};
+  for (int i = 0; i < (N + 1) * (N + 1); ++i) D[i] = b.D[i];
+  for (int i = 0; i <= N; ++i) w[i] = b.w[i];
+  cudaError_t e = cudaMemcpyToSymbol(c_D64, D, sizeof(D));
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_w64, w, sizeof(w));
+  return e;
+}
+
+__device__ __forceinline__ int ipow_d(int b, int e) {
+  int r = 1;
+  for (int i = 0; i < e; ++i) r *= b;
+  return r;
+}
+
+// derivative along reference direction d of nodal field f (stride 1 over nodes)
+__device__ double dref(const double* f, int N, int d, int node) {
+  const int n1 = N + 1, s = ipow_d(n1, d), pos = (node / s) % n1, base = node - pos * s;
+  double acc = 0.0;
+  for (int l = 0; l < n1; ++l) acc += c_D64[pos * n1 + l] * f[base + l * s];
+  return acc;
+}
+
+// Metric terms, one CTA per element.  3D: conservative curl form
+// Ja^i_n = -[curl_xi (x_l grad_xi x_m)]_i, (n,m,l) cyclic; 2D: Ja^1 = (y_eta, -x_eta),
+// Ja^2 = (-y_xi, x_xi).  J = det(dx/dxi).
+__global__ void metrics_kernel(int dim, int N, int64_t K, const double* xyz, double* Ja,
+                               double* J, double* invJ, unsigned long long* status) {
+  extern __shared__ double sm[];
+  const int np = ipow_d(N + 1, dim);
+  double* X = sm;               // [dim][np]
+  double* V = X + dim * np;     // [3][np]
+  const int64_t k = blockIdx.x;
+  for (int i = threadIdx.x; i < dim * np; i += blockDim.x) X[i] = xyz[k * dim * np + i];
+  __syncthreads();
+  double* JA = Ja + k * dim * dim * np;
+  for (int node = threadIdx.x; node < np; node += blockDim.x) {
+    double a[3][3];
+    for (int n = 0; n < dim; ++n)
+      for (int j = 0; j < dim; ++j) a[n][j] = dref(X + n * np, N, j, node);
+    double det;
+    if (dim == 2) {
+      det = a[0][0] * a[1][1] - a[0][1] * a[1][0];
+      JA[0 * np + node] = a[1][1];
+      JA[1 * np + node] = -a[0][1];
+      JA[2 * np + node] = -a[1][0];
+      JA[3 * np + node] = a[0][0];
+    } else {
+      det = a[0][0] * (a[1][1] * a[2][2] - a[1][2] * a[2][1]) -
+            a[0][1] * (a[1][0] * a[2][2] - a[1][2] * a[2][0]) +
+            a[0][2] * (a[1][0] * a[2][1] - a[1][1] * a[2][0]);
+    }
+    J[k * np + node] = det;
+    invJ[k * np + node] = 1.0 / det;
+    if (!(det > 0.0)) atomicCAS(status, 0ull, (4ull << 56) | (unsigned long long)k);
+  }
+  if (dim == 3) {
+    for (int n = 0; n < 3; ++n) {
+      const int m = (n + 1) % 3, l = (n + 2) % 3;
+      __syncthreads();
+      for (int node = threadIdx.x; node < np; node += blockDim.x)
+        for (int j = 0; j < 3; ++j) V[j * np + node] = X[l * np + node] * dref(X + m * np, N, j, node);
+      __syncthreads();
+      for (int node = threadIdx.x; node < np; node += blockDim.x) {
+        double c0 = dref(V + 2 * np, N, 1, node) - dref(V + 1 * np, N, 2, node);
+        double c1 = dref(V + 0 * np, N, 2, node) - dref(V + 2 * np, N, 0, node);
+        double c2 = dref(V + 1 * np, N, 0, node) - dref(V + 0 * np, N, 1, node);
+        JA[(0 * 3 + n) * np + node] = -c0;
+        JA[(1 * 3 + n) * np + node] = -c1;
+        JA[(2 * 3 + n) * np + node] = -c2;
+      }
+    }
+  }
+}
+
+template <typename T>
+__global__ void cvt_kernel(const double* a, T* b, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = (T)a[i];
+}
+template <typename T>
+__global__ void cvt_back_kernel(const T* a, double* b, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = (double)a[i];
+}
+
+// one-gas primitive (rho, v, p) -> conserved, written in the form precision
+template <typename T>
+__global__ void prim2cons_kernel(const double* w, T* u, int64_t K, int dim, int np, double gamma) {
+  const int nv = dim + 2;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < K * np;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t k = i / np;
+    const int node = (int)(i % np);
+    const double* ww = w + k * nv * np + node;
+    T* uu = u + k * nv * np + node;
+    double rho = ww[0], ke = 0.0;
+    uu[0] = (T)rho;
+    for (int d = 0; d < dim; ++d) {
+      uu[(1 + d) * np] = (T)(rho * ww[(1 + d) * np]);
+      ke += ww[(1 + d) * np] * ww[(1 + d) * np];
+    }
+    uu[(1 + dim) * np] = (T)(ww[(1 + dim) * np] / (gamma - 1.0) + 0.5 * rho * ke);
+  }
+}
+
+// FP64 domain integrals, per block partial sums (deterministic: fixed order later)
+template <typename T>
+__global__ void diag_kernel(const T* u, const double* Ja, const double* J, int64_t K, int dim,
+                            int N, int nsp, double gamma, int single_gas, double* partial) {
+  const int np = ipow_d(N + 1, dim), nv = nsp + dim + 1;
+  double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < K * np;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t k = i / np;
+    const int node = (int)(i % np);
+    const T* uu = u + k * nv * np;
+    double wq = 1.0;
+    for (int d = 0; d < dim; ++d) wq *= c_w64[(node / ipow_d(N + 1, d)) % (N + 1)];
+    const double Jn = J[k * np + node];
+    double rho = 0.0;
+    for (int s = 0; s < nsp; ++s) rho += (double)uu[s * np + node];
+    double v[3] = {0, 0, 0}, v2 = 0.0;
+    for (int d = 0; d < dim; ++d) {
+      v[d] = (double)uu[(nsp + d) * np + node] / rho;
+      v2 += v[d] * v[d];
+    }
+    const double rhoE = (double)uu[(nsp + dim) * np + node];
+    double gv[3][3] = {{0}};
+    const int n1 = N + 1;
+    for (int a = 0; a < dim; ++a)
+      for (int d = 0; d < dim; ++d) {
+        const int s = ipow_d(n1, d), pos = (node / s) % n1, base = node - pos * s;
+        double dv = 0.0;
+        for (int l = 0; l < n1; ++l) {
+          const int m = base + l * s;
+          double rm = 0.0;
+          for (int q = 0; q < nsp; ++q) rm += (double)uu[q * np + m];
+          dv += c_D64[pos * n1 + l] * ((double)uu[(nsp + a) * np + m] / rm);
+        }
+        for (int x = 0; x < dim; ++x) gv[a][x] += Ja[((k * dim + d) * dim + x) * np + node] * dv / Jn;
+      }
+    double w2;
+    if (dim == 3) {
+      double wx = gv[2][1] - gv[1][2], wy = gv[0][2] - gv[2][0], wz = gv[1][0] - gv[0][1];
+      w2 = wx * wx + wy * wy + wz * wz;
+    } else {
+      double wz = gv[1][0] - gv[0][1];
+      w2 = wz * wz;
+    }
+    double div = 0.0;
+    for (int a = 0; a < dim; ++a) div += gv[a][a];
+    const double dV = wq * Jn;
+    acc[0] += dV;
+    acc[1] += dV * 0.5 * rho * v2;
+    acc[2] += dV * 0.5 * rho * w2;
+    if (single_gas) {
+      double p = (gamma - 1.0) * (rhoE - 0.5 * rho * v2);
+      acc[3] += dV * (-rho * (log(p) - gamma * log(rho)) / (gamma - 1.0));
+    }
+    acc[4] += dV * rho;
+    acc[5] += dV * rhoE;
+    acc[6] += dV * div * div;
+  }
+  __shared__ double red[7][256];
+  for (int q = 0; q < 7; ++q) red[q][threadIdx.x] = acc[q];
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w)
+      for (int q = 0; q < 7; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    for (int q = 0; q < 7; ++q) partial[blockIdx.x * 7 + q] = red[q][0];
+}
+
+__global__ void diag_final_kernel(const double* partial, int nb, double* out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double s[7] = {0, 0, 0, 0, 0, 0, 0};
+  for (int b = 0; b < nb; ++b)
+    for (int q = 0; q < 7; ++q) s[q] += partial[b * 7 + q];
+  out[0] = s[1] / s[0];
+  out[1] = s[2] / s[0];
+  out[2] = s[3];
+  out[3] = s[4];
+  out[4] = s[5];
+  out[5] = s[0];
+  out[6] = s[6] / s[0];
+  out[7] = 0.0;
+}
+
+void rk_ck45(double* A, double* B) {
+  // Carpenter & Kennedy (1994), five-stage fourth-order 2N-storage
+  A[0] = 0.0;
+  A[1] = -567301805773.0 / 1357537059087.0;
+  A[2] = -2404267990393.0 / 2016746695238.0;
+  A[3] = -3550918686646.0 / 2091501179385.0;
+  A[4] = -1275806237668.0 / 842570457699.0;
+  B[0] = 1432997174477.0 / 9575080441755.0;
+  B[1] = 5161836677717.0 / 13612068292357.0;
+  B[2] = 1720146321549.0 / 2090206949498.0;
+  B[3] = 3134564353537.0 / 4481467310338.0;
+  B[4] = 2277821191437.0 / 14882151754819.0;
+}
+
+unsigned grid_for(int64_t n, int bs) {
+  int64_t g = (n + bs - 1) / bs;
+  if (g > 152 * 32) g = 152 * 32;
+  return (unsigned)(g < 1 ? 1 : g);
+}
+
+DgArgs base_args(dg_ctx* c) {
+  DgArgs a;
+  memset(&a, 0, sizeof(a));
+  a.K = c->K;
+  a.dim = c->dim;
+  a.N = c->N;
+  a.nsp = c->nsp;
+  a.nv = c->nv;
+  a.np = c->np;
+  a.n_bc = c->n_bc;
+  a.vf = c->vf;
+  a.sf = c->sf;
+  a.ns = c->equations == DG_NAVIER_STOKES;
+  a.gamma = c->gamma;
+  a.mu = c->mu;
+  a.kappa_fac = a.ns ? c->mu * c->gamma / ((c->gamma - 1.0) * c->Pr) : 0.0;
+  a.visc_coef = a.ns ? c->gamma * c->mu / c->Pr : 0.0;
+  const bool f32 = c->precision == DG_MIXED;
+  a.Ja = f32 ? (const void*)c->Ja32 : (const void*)c->Ja64;
+  a.invJ = f32 ? (const void*)c->invJ32 : (const void*)c->invJ64;
+  a.gradW = c->gradW;
+  a.nbr = c->nbr;
+  a.bc_kind = c->bc_kind;
+  a.bc_u = c->bc_u;
+  a.scal = c->scal;
+  a.lam = c->lam;
+  a.status = c->status;
+  if (c->n_species > 0) {
+    a.pc = c->th.pc;
+    a.bc_pc = c->th.bc_pc;
+  }
+  return a;
+}
+
+void prof_flush(dg_ctx* c) {
+  if (c->ev_used == 0) return;
+  cudaEventSynchronize(c->ev[c->ev_used - 1]);
+  for (int i = 0; i < c->ev_used / 2; ++i) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, c->ev[2 * i], c->ev[2 * i + 1]) == cudaSuccess) {
+      c->prof_ms[c->ev_kind[i]] += ms;
+      c->prof_n[c->ev_kind[i]] += 1;
+    }
+  }
+  c->ev_used = 0;
+}
+
+template <typename F>
+cudaError_t timed(dg_ctx* c, int kind, F f) {
+  if (!c->prof) return f();
+  if (c->ev_used + 2 > c->ev_cap) prof_flush(c);
+  cudaEventRecord(c->ev[c->ev_used], c->stream);
+  cudaError_t r = f();
+  cudaEventRecord(c->ev[c->ev_used + 1], c->stream);
+  c->ev_kind[c->ev_used / 2] = kind;
+  c->ev_used += 2;
+  return r;
+}
+
+cudaError_t run_rhs(dg_ctx* c, DgArgs& a) {
+  return timed(c, DG_PROF_RHS, [&] {
+    return c->precision == DG_MIXED ? dg_f32_rhs(a, c->stream) : dg_f64_rhs(a, c->stream);
+  });
+}
+cudaError_t run_grad(dg_ctx* c, DgArgs& a) {
+  return timed(c, DG_PROF_GRAD, [&] {
+    return c->precision == DG_MIXED ? dg_f32_gradients(a, c->stream) : dg_f64_gradients(a, c->stream);
+  });
+}
+cudaError_t run_ind(dg_ctx* c, DgArgs& a) {
+  return timed(c, DG_PROF_INDICATOR, [&] {
+    return c->precision == DG_MIXED ? dg_f32_indicator(a, c->alpha_max, c->alpha_raw, c->stream)
+                                    : dg_f64_indicator(a, c->alpha_max, c->alpha_raw, c->stream);
+  });
+}
+cudaError_t run_lambda(dg_ctx* c, DgArgs& a, int slot) {
+  return timed(c, DG_PROF_LAMBDA, [&] {
+    return c->precision == DG_MIXED ? dg_f32_lambda(a, slot, c->stream) : dg_f64_lambda(a, slot, c->stream);
+  });
+}
+cudaError_t run_thermo(dg_ctx* c, const void* u) {
+  return timed(c, DG_PROF_THERMO, [&] {
+    return dg_thermo_update(&c->th, u, c->precision == DG_MIXED, c->stream);
+  });
+}
+
+// everything that precedes the main kernel of one right-hand side at state u
+cudaError_t pre_rhs(dg_ctx* c, DgArgs& a) {
+  cudaError_t e = cudaSuccess;
+  if (c->n_species > 0) {
+    e = run_thermo(c, a.u);
+    if (e != cudaSuccess) return e;
+  }
+  if (c->equations == DG_NAVIER_STOKES) {
+    e = run_grad(c, a);
+    if (e != cudaSuccess) return e;
+    c->have_grad = true;
+  }
+  if (c->alpha_max > 0.0) {
+    e = run_ind(c, a);
+    if (e != cudaSuccess) return e;
+    a.alpha_raw = c->alpha_raw;
+    a.alpha_used = c->alpha_used;
+    c->have_alpha = true;
+  }
+  return e;
+}
+
+dg_status wait_stream(dg_ctx* c) {
+  // bounded wait: poll for up to 600 s of wall time
+  struct timespec t0, t1;
+  clock_gettime(CLOCK_MONOTONIC, &t0);
+  for (;;) {
+    cudaError_t q = cudaStreamQuery(c->stream);
+    if (q == cudaSuccess) return DG_OK;
+    if (q != cudaErrorNotReady) return DG_ECUDA;
+    clock_gettime(CLOCK_MONOTONIC, &t1);
+    if ((t1.tv_sec - t0.tv_sec) > 600) return DG_ETIMEOUT;
+    struct timespec ts = {0, 20000};
+    nanosleep(&ts, NULL);
+  }
+}
+
+dg_status take_status(dg_ctx* c, int64_t* elem) {
+  unsigned long long st = 0;
+  if (cudaMemcpy(&st, c->status, sizeof(st), cudaMemcpyDeviceToHost) != cudaSuccess) return DG_ECUDA;
+  if (elem) *elem = st ? (int64_t)(st & 0x00ffffffffffffffull) : -1;
+  if (!st) return DG_OK;
+  unsigned long long code = st >> 56;
+  return code == DG_ST_NEWTON ? DG_ENEWTON : DG_ENONPHYS;
+}
+
+void free_ctx(dg_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->dev);
+  void* ptrs[] = {c->nbr, c->Ja64, c->J64, c->invJ64, c->Ja32, c->invJ32, c->u[0], c->u[1],
+                  c->du, c->gradW, c->alpha_raw, c->alpha_used, c->bc_kind, c->bc_u, c->scal,
+                  c->lam, c->status, c->partial, c->stage64};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  dg_thermo_free(&c->th);
+  if (c->ev) {
+    for (int i = 0; i < c->ev_cap; ++i) cudaEventDestroy(c->ev[i]);
+    free(c->ev);
+    free(c->ev_kind);
+  }
+  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  free(c);
+}
+
+bool supported_degree(int dim, int N, int ns) {
+  if (ns > 0) return dim == 3 && (N == 3 || N == 4);
+  return N == 2 || N == 3 || N == 4 || N == 7;
+}
+
+}  // namespace
+
+extern "C" {
+
+dg_status dg_lgl_nodes(int N, double* nodes, double* weights) {
+  if (N < 1 || N > DG_MAXN || !nodes) return DG_EINVAL;
+  DgHostBasis b;
+  if (dg_host_basis(N, &b)) return DG_EINVAL;
+  for (int i = 0; i <= N; ++i) {
+    nodes[i] = b.x[i];
+    if (weights) weights[i] = b.w[i];
+  }
+  return DG_OK;
+}
+
+const char* dg_status_string(dg_status s) {
+  switch (s) {
+    case DG_OK: return "ok";
+    case DG_EINVAL: return "invalid argument";
+    case DG_ENOMEM: return "device allocation failed";
+    case DG_ECUDA: return "CUDA error";
+    case DG_ENONPHYS: return "non-physical state";
+    case DG_ENEWTON: return "temperature Newton iteration failed";
+    case DG_ETIMEOUT: return "device wait timed out";
+    case DG_ESTATE: return "call out of order";
+  }
+  return "unknown";
+}
+
+dg_status dg_init_mesh(const dg_mesh_desc* m, const dg_physics_desc* p, dg_ctx** out) {
+  if (!out) return DG_EINVAL;
+  *out = NULL;
+  if (!m || !p || !m->node_xyz || !m->nbr_elem || !m->nbr_face) return DG_EINVAL;
+  if (m->dim < 2 || m->dim > 3 || m->K < 1 || m->K >= (1ll << 31)) return DG_EINVAL;
+  if (p->n_species < 0 || p->n_species > DG_MAX_SPECIES) return DG_EINVAL;
+  if (!supported_degree(m->dim, m->N, p->n_species)) return DG_EINVAL;
+  if (p->n_species > 0 && (p->n_species != 5 || !p->species)) return DG_EINVAL;
+  if (p->equations != DG_EULER && p->equations != DG_NAVIER_STOKES) return DG_EINVAL;
+  if (p->equations == DG_NAVIER_STOKES && (p->n_species > 0 || m->dim != 3 || !(p->mu > 0) ||
+                                           !(p->Pr > 0)))
+    return DG_EINVAL;
+  if (p->volume_flux < 0 || p->volume_flux > 2 || p->surface_flux < 0 || p->surface_flux > 2)
+    return DG_EINVAL;
+  if (p->n_species > 0 && p->volume_flux == DG_VF_RANOCHA) return DG_EINVAL;
+  if (p->n_species == 0 && !(p->gamma > 1.0)) return DG_EINVAL;
+  if (p->precision != DG_FP64 && p->precision != DG_MIXED) return DG_EINVAL;
+  if (p->thermo != DG_THERMO_NEWTON && p->thermo != DG_THERMO_MLP) return DG_EINVAL;
+  if (p->alpha_max < 0.0 || p->alpha_max > 1.0) return DG_EINVAL;
+  if (p->n_bc < 0 || (p->n_bc > 0 && (!p->bc_kind || !p->bc_prim))) return DG_EINVAL;
+  const int dim = m->dim, nf = 2 * dim, N = m->N;
+  const int64_t K = m->K;
+  for (int b = 0; b < p->n_bc; ++b)
+    if (p->bc_kind[b] < DG_BC_INFLOW || p->bc_kind[b] > DG_BC_SLIP_WALL) return DG_EINVAL;
+  int* nbr_h = (int*)malloc(sizeof(int) * K * nf);
+  if (!nbr_h) return DG_ENOMEM;
+  for (int64_t k = 0; k < K; ++k)
+    for (int f = 0; f < nf; ++f) {
+      const int64_t nb = m->nbr_elem[k * nf + f];
+      bool ok = true;
+      if (nb >= 0) {
+        ok = nb < K && m->nbr_face[k * nf + f] == (f ^ 1) &&
+             (!m->nbr_orient || m->nbr_orient[k * nf + f] == 0);
+      } else {
+        ok = -(nb + 1) < p->n_bc && p->equations != DG_NAVIER_STOKES;
+      }
+      if (!ok) {
+        free(nbr_h);
+        return DG_EINVAL;
+      }
+      nbr_h[k * nf + f] = (int)nb;
+    }
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {
+    free(nbr_h);
+    return DG_ECUDA;
+  }
+  dg_ctx* c = (dg_ctx*)calloc(1, sizeof(dg_ctx));
+  cudaGetDevice(&c->dev);
+  c->dim = dim;
+  c->N = N;
+  c->K = K;
+  c->nf = nf;
+  c->np = 1;
+  for (int d = 0; d < dim; ++d) c->np *= (N + 1);
+  c->n_species = p->n_species;
+  c->nsp = p->n_species > 0 ? p->n_species : 1;
+  c->nv = c->nsp + dim + 1;
+  c->equations = p->equations;
+  c->vf = p->volume_flux;
+  c->sf = p->surface_flux;
+  c->precision = p->precision;
+  c->thermo = p->thermo;
+  c->n_bc = p->n_bc;
+  c->gamma = p->gamma;
+  c->mu = p->mu;
+  c->Pr = p->Pr;
+  c->alpha_max = p->alpha_max;
+  c->rs = c->precision == DG_MIXED ? sizeof(float) : sizeof(double);
+  dg_status st = DG_OK;
+#define TRY(x)                    \
+  do {                            \
+    if ((x) != cudaSuccess) {     \
+      st = DG_ECUDA;              \
+      goto fail;                  \
+    }                             \
+  } while (0)
+#define TRYM(ptr, bytes)                                     \
+  do {                                                       \
+    if (cudaMalloc((void**)&(ptr), (bytes)) != cudaSuccess) { \
+      st = DG_ENOMEM;                                        \
+      goto fail;                                             \
+    }                                                        \
+  } while (0)
+  {
+    if (p->stream) {
+      c->stream = (cudaStream_t)p->stream;
+    } else {
+      TRY(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+      c->own_stream = true;
+    }
+    TRY(upload_all_bases(c->dev));
+    TRY(upload_local_basis(N));
+    const int64_t nst = K * c->nv * c->np;
+    TRYM(c->nbr, sizeof(int) * K * nf);
+    TRYM(c->Ja64, sizeof(double) * K * dim * dim * c->np);
+    TRYM(c->J64, sizeof(double) * K * c->np);
+    TRYM(c->invJ64, sizeof(double) * K * c->np);
+    if (c->precision == DG_MIXED) {
+      TRYM(c->Ja32, sizeof(float) * K * dim * dim * c->np);
+      TRYM(c->invJ32, sizeof(float) * K * c->np);
+    }
+    TRYM(c->u[0], c->rs * nst);
+    TRYM(c->u[1], c->rs * nst);
+    TRYM(c->du, c->rs * nst);
+    if (c->equations == DG_NAVIER_STOKES) TRYM(c->gradW, c->rs * K * dim * (dim + 1) * c->np);
+    if (c->alpha_max > 0.0) {
+      TRYM(c->alpha_raw, c->rs * K);
+      TRYM(c->alpha_used, sizeof(double) * K);
+    }
+    TRYM(c->bc_kind, sizeof(int) * (p->n_bc > 0 ? p->n_bc : 1));
+    TRYM(c->bc_u, c->rs * c->nv * (p->n_bc > 0 ? p->n_bc : 1));
+    TRYM(c->scal, sizeof(double) * 4);
+    TRYM(c->lam, sizeof(unsigned long long) * 4);
+    TRYM(c->status, sizeof(unsigned long long));
+    c->diag_blocks = 152 * 4;
+    TRYM(c->partial, sizeof(double) * 7 * c->diag_blocks);
+    TRYM(c->stage64, sizeof(double) * nst);
+    TRY(cudaMemset(c->status, 0, sizeof(unsigned long long)));
+    TRY(cudaMemset(c->scal, 0, sizeof(double) * 4));
+    TRY(cudaMemset(c->lam, 0, sizeof(unsigned long long) * 4));
+    TRY(cudaMemcpy(c->nbr, nbr_h, sizeof(int) * K * nf, cudaMemcpyHostToDevice));
+    if (p->n_bc > 0) TRY(cudaMemcpy(c->bc_kind, p->bc_kind, sizeof(int) * p->n_bc, cudaMemcpyHostToDevice));
+    // geometry -> metric terms
+    double* xyz = NULL;
+    TRYM(xyz, sizeof(double) * K * dim * c->np);
+    if (cudaMemcpy(xyz, m->node_xyz, sizeof(double) * K * dim * c->np, cudaMemcpyHostToDevice) !=
+        cudaSuccess) {
+      cudaFree(xyz);
+      st = DG_ECUDA;
+      goto fail;
+    }
+    const size_t msm = sizeof(double) * (dim + 3) * c->np;
+    if (msm > 48 * 1024)
+      cudaFuncSetAttribute(metrics_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)msm);
+    metrics_kernel<<<(unsigned)K, 128, msm, c->stream>>>(dim, N, K, xyz, c->Ja64, c->J64,
+                                                          c->invJ64, c->status);
+    cudaError_t ke = cudaGetLastError();
+    if (ke == cudaSuccess) ke = cudaStreamSynchronize(c->stream);
+    cudaFree(xyz);
+    TRY(ke);
+    int64_t bad = -1;
+    if (take_status(c, &bad) != DG_OK) {
+      st = DG_EINVAL;  // inverted element
+      goto fail;
+    }
+    if (c->precision == DG_MIXED) {
+      cvt_kernel<float><<<grid_for(K * dim * dim * c->np, 256), 256, 0, c->stream>>>(
+          c->Ja64, c->Ja32, K * dim * dim * c->np);
+      cvt_kernel<float><<<grid_for(K * c->np, 256), 256, 0, c->stream>>>(c->invJ64, c->invJ32,
+                                                                          K * c->np);
+      TRY(cudaGetLastError());
+    }
+    if (c->n_species > 0) {
+      if (dg_thermo_init(&c->th, K, c->np, dim, p->species, p->thermo, c->precision == DG_MIXED,
+                         c->status) != cudaSuccess) {
+        st = DG_ENOMEM;
+        goto fail;
+      }
+    }
+    // boundary states (primitive -> conserved on the device)
+    if (p->n_bc > 0) {
+      double* bw = NULL;
+      TRYM(bw, sizeof(double) * p->n_bc * c->nv);
+      cudaMemcpy(bw, p->bc_prim, sizeof(double) * p->n_bc * c->nv, cudaMemcpyHostToDevice);
+      cudaError_t e2;
+      if (c->n_species == 0) {
+        if (c->precision == DG_MIXED)
+          prim2cons_kernel<float><<<1, 32, 0, c->stream>>>(bw, (float*)c->bc_u, p->n_bc, dim, 1, c->gamma);
+        else
+          prim2cons_kernel<double><<<1, 32, 0, c->stream>>>(bw, (double*)c->bc_u, p->n_bc, dim, 1, c->gamma);
+        e2 = cudaGetLastError();
+      } else {
+        e2 = dg_thermo_boundary(&c->th, bw, p->n_bc, c->bc_u, c->stream);
+      }
+      if (e2 == cudaSuccess) e2 = cudaStreamSynchronize(c->stream);
+      cudaFree(bw);
+      TRY(e2);
+    }
+    TRY(cudaStreamSynchronize(c->stream));
+  }
+  free(nbr_h);
+  *out = c;
+  return DG_OK;
+fail:
+  free(nbr_h);
+  free_ctx(c);
+  return st;
+#undef TRY
+#undef TRYM
+}
+
+void dg_destroy(dg_ctx* c) { free_ctx(c); }
+
+dg_status dg_set_state(dg_ctx* c, const double* u, int on_device, double t) {
+  if (!c || !u) return DG_EINVAL;
+  const int64_t n = c->K * c->nv * c->np;
+  cudaSetDevice(c->dev);
+  const double* src = u;
+  if (!on_device) {
+    CK(cudaMemcpyAsync(c->stage64, u, sizeof(double) * n, cudaMemcpyHostToDevice, c->stream));
+    src = c->stage64;
+  }
+  if (c->precision == DG_MIXED) {
+    cvt_kernel<float><<<grid_for(n, 256), 256, 0, c->stream>>>(src, (float*)c->u[c->cur], n);
+  } else {
+    CK(cudaMemcpyAsync(c->u[c->cur], src, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream));
+  }
+  CK(cudaGetLastError());
+  if (c->n_species > 0) CK(dg_thermo_reset(&c->th, c->stream));
+  CK(cudaMemcpyAsync(c->scal, &t, sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  c->have_state = true;
+  return wait_stream(c);
+}
+
+dg_status dg_set_state_primitive(dg_ctx* c, const double* w, int on_device, double t) {
+  if (!c || !w) return DG_EINVAL;
+  const int64_t n = c->K * c->nv * c->np;
+  cudaSetDevice(c->dev);
+  const double* src = w;
+  if (!on_device) {
+    CK(cudaMemcpyAsync(c->stage64, w, sizeof(double) * n, cudaMemcpyHostToDevice, c->stream));
+    src = c->stage64;
+  }
+  if (c->n_species == 0) {
+    if (c->precision == DG_MIXED)
+      prim2cons_kernel<float><<<grid_for(c->K * c->np, 256), 256, 0, c->stream>>>(
+          src, (float*)c->u[c->cur], c->K, c->dim, c->np, c->gamma);
+    else
+      prim2cons_kernel<double><<<grid_for(c->K * c->np, 256), 256, 0, c->stream>>>(
+          src, (double*)c->u[c->cur], c->K, c->dim, c->np, c->gamma);
+    CK(cudaGetLastError());
+  } else {
+    CK(dg_thermo_prim2cons(&c->th, src, c->u[c->cur], c->stream));
+    CK(dg_thermo_reset(&c->th, c->stream));
+  }
+  CK(cudaMemcpyAsync(c->scal, &t, sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  c->have_state = true;
+  return wait_stream(c);
+}
+
+dg_status dg_get_state(dg_ctx* c, double* u, int on_device, double* t) {
+  if (!c || !u) return DG_EINVAL;
+  if (!c->have_state) return DG_ESTATE;
+  cudaSetDevice(c->dev);
+  const int64_t n = c->K * c->nv * c->np;
+  if (c->precision == DG_MIXED) {
+    double* dst = on_device ? u : c->stage64;
+    cvt_back_kernel<float><<<grid_for(n, 256), 256, 0, c->stream>>>((const float*)c->u[c->cur], dst, n);
+    CK(cudaGetLastError());
+    if (!on_device)
+      CK(cudaMemcpyAsync(u, c->stage64, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream));
+  } else {
+    CK(cudaMemcpyAsync(u, c->u[c->cur], sizeof(double) * n,
+                       on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+  }
+  double tt = 0.0;
+  CK(cudaMemcpyAsync(&tt, c->scal, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  dg_status w = wait_stream(c);
+  if (w != DG_OK) return w;
+  if (t) *t = tt;
+  return take_status(c, NULL);
+}
+
+dg_status dg_rhs(dg_ctx* c, const void* u, void* rhs, double t) {
+  (void)t;
+  if (!c || !u || !rhs || u == rhs) return DG_EINVAL;
+  cudaSetDevice(c->dev);
+  DgArgs a = base_args(c);
+  a.u = u;
+  a.out = rhs;
+  a.mode = 0;
+  CK(pre_rhs(c, a));
+  CK(run_rhs(c, a));
+  return DG_OK;
+}
+
+dg_status dg_step_rk(dg_ctx* c, int nsteps, double cfl, double dt_fixed, double* t_inout) {
+  if (!c || nsteps < 0 || (!(dt_fixed > 0.0) && !(cfl > 0.0))) return DG_EINVAL;
+  if (!c->have_state) return DG_ESTATE;
+  cudaSetDevice(c->dev);
+  double A[5], B[5];
+  rk_ck45(A, B);
+  CK(cudaMemsetAsync(c->scal, 0, sizeof(double), c->stream));  // elapsed time
+  DgArgs a = base_args(c);
+  if (!(dt_fixed > 0.0)) {
+    a.u = c->u[c->cur];
+    if (c->n_species > 0) CK(run_thermo(c, a.u));
+    CK(cudaMemsetAsync(c->lam + 2 * c->lam_slot, 0, 2 * sizeof(unsigned long long), c->stream));
+    CK(run_lambda(c, a, c->lam_slot));
+  }
+  for (int step = 0; step < nsteps; ++step) {
+    for (int s = 0; s < 5; ++s) {
+      DgArgs b = base_args(c);
+      b.u = c->u[c->cur];
+      b.out = c->u[c->cur ^ 1];
+      b.du = c->du;
+      b.mode = 1;
+      b.stage = s;
+      b.rkA = A[s];
+      b.rkB = B[s];
+      b.cfl = cfl;
+      b.dt_fixed = dt_fixed;
+      b.lam_cur = c->lam_slot;
+      b.want_lambda = (s == 4 && !(dt_fixed > 0.0) && c->n_species == 0) ? 1 : 0;
+      CK(pre_rhs(c, b));
+      CK(run_rhs(c, b));
+      c->cur ^= 1;
+    }
+    if (!(dt_fixed > 0.0)) {
+      if (c->n_species > 0) {
+        // mixtures: wave speeds need the new temperature field
+        DgArgs l = base_args(c);
+        l.u = c->u[c->cur];
+        CK(run_thermo(c, l.u));
+        CK(cudaMemsetAsync(c->lam + 2 * (c->lam_slot ^ 1), 0, 2 * sizeof(unsigned long long),
+                           c->stream));
+        CK(run_lambda(c, l, c->lam_slot ^ 1));
+      }
+      c->lam_slot ^= 1;
+    }
+  }
+  dg_status w = wait_stream(c);
+  if (w != DG_OK) return w;
+  double el = 0.0;
+  CK(cudaMemcpy(&el, c->scal, sizeof(double), cudaMemcpyDeviceToHost));
+  if (t_inout) *t_inout += el;
+  return take_status(c, NULL);
+}
+
+dg_status dg_diagnostics(dg_ctx* c, double out[8]) {
+  if (!c || !out) return DG_EINVAL;
+  if (!c->have_state) return DG_ESTATE;
+  cudaSetDevice(c->dev);
+  CK(upload_local_basis(c->N));
+  double* dout = c->partial;  // reuse the tail of the partial buffer for the result
+  const int nb = c->diag_blocks - 2;
+  if (c->precision == DG_MIXED)
+    diag_kernel<float><<<nb, 256, 0, c->stream>>>((const float*)c->u[c->cur], c->Ja64, c->J64,
+                                                  c->K, c->dim, c->N, c->nsp, c->gamma,
+                                                  c->n_species == 0, c->partial);
+  else
+    diag_kernel<double><<<nb, 256, 0, c->stream>>>((const double*)c->u[c->cur], c->Ja64, c->J64,
+                                                   c->K, c->dim, c->N, c->nsp, c->gamma,
+                                                   c->n_species == 0, c->partial);
+  CK(cudaGetLastError());
+  diag_final_kernel<<<1, 32, 0, c->stream>>>(c->partial, nb, dout + nb * 7);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(out, dout + nb * 7, sizeof(double) * 8, cudaMemcpyDeviceToHost, c->stream));
+  dg_status w = wait_stream(c);
+  if (w != DG_OK) return w;
+  return DG_OK;
+}
+
+dg_status dg_get_alpha(dg_ctx* c, double* alpha) {
+  if (!c || !alpha) return DG_EINVAL;
+  if (!c->have_alpha) return DG_ESTATE;
+  CK(cudaMemcpyAsync(alpha, c->alpha_used, sizeof(double) * c->K, cudaMemcpyDeviceToHost, c->stream));
+  return wait_stream(c);
+}
+
+dg_status dg_get_gradients(dg_ctx* c, double* g) {
+  if (!c || !g) return DG_EINVAL;
+  if (!c->have_grad) return DG_ESTATE;
+  const int64_t n = c->K * c->dim * (c->dim + 1) * c->np;
+  if (c->precision == DG_MIXED) {
+    double* tmp = NULL;
+    CK(cudaMalloc((void**)&tmp, sizeof(double) * n));
+    cvt_back_kernel<float><<<grid_for(n, 256), 256, 0, c->stream>>>((const float*)c->gradW, tmp, n);
+    CK(cudaMemcpyAsync(g, tmp, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream));
+    dg_status w = wait_stream(c);
+    cudaFree(tmp);
+    return w;
+  }
+  CK(cudaMemcpyAsync(g, c->gradW, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream));
+  return wait_stream(c);
+}
+
+dg_status dg_profile(dg_ctx* c, int enable) {
+  if (!c) return DG_EINVAL;
+  cudaSetDevice(c->dev);
+  if (enable && !c->ev) {
+    c->ev_cap = 8192;
+    c->ev = (cudaEvent_t*)calloc(c->ev_cap, sizeof(cudaEvent_t));
+    c->ev_kind = (int*)calloc(c->ev_cap / 2, sizeof(int));
+    if (!c->ev || !c->ev_kind) return DG_ENOMEM;
+    for (int i = 0; i < c->ev_cap; ++i) CK(cudaEventCreate(&c->ev[i]));
+  }
+  if (!enable && c->ev) prof_flush(c);
+  c->prof = enable ? 1 : 0;
+  return DG_OK;
+}
+
+dg_status dg_profile_read(dg_ctx* c, double* ms, int64_t* launches, int n) {
+  if (!c || n < 0 || n > DG_PROF_KINDS) return DG_EINVAL;
+  cudaSetDevice(c->dev);
+  dg_status w = wait_stream(c);
+  if (w != DG_OK) return w;
+  if (c->ev) prof_flush(c);
+  for (int i = 0; i < n; ++i) {
+    if (ms) ms[i] = c->prof_ms[i];
+    if (launches) launches[i] = c->prof_n[i];
+  }
+  for (int i = 0; i < DG_PROF_KINDS; ++i) {
+    c->prof_ms[i] = 0.0;
+    c->prof_n[i] = 0;
+  }
+  return DG_OK;
+}
+
+dg_status dg_sync(dg_ctx* c) {
+  if (!c) return DG_EINVAL;
+  cudaSetDevice(c->dev);
+  dg_status w = wait_stream(c);
+  if (w != DG_OK) return w;
+  dg_status s = take_status(c, NULL);
+  if (s != DG_OK) cudaMemset(c->status, 0, sizeof(unsigned long long));
+  return s;
+}
+
+int64_t dg_error_element(dg_ctx* c) {
+  if (!c) return -1;
+  int64_t e = -1;
+  take_status(c, &e);
+  return e;
+}
+
+}  // extern "C"

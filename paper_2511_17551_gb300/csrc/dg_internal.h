@@ -1,0 +1,67 @@
+// Internal interface between the C-ABI layer (dg_capi.cu) and the kernel
+// translation units.  Not part of the public ABI.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define DG_MAXN 7
+#define DG_MAX_SPECIES 8
+#define DG_MAX_NV (DG_MAX_SPECIES + 4)
+
+// device status word: (code << 56) | element
+#define DG_ST_NONPHYS 4ull
+#define DG_ST_NEWTON 5ull
+
+// Everything a right-hand-side / RK-stage launch needs, passed by value.
+struct DgArgs {
+  int64_t K;
+  int dim, N, nsp, nv, np;
+  int n_bc;
+  int vf, sf;             // DG_VF_*, DG_SF_*
+  int mode;               // 0: write rhs, 1: RK stage
+  int stage;              // RK stage 0..4
+  int want_lambda;        // mode 1: accumulate wave speeds of the new state
+  int lam_cur;            // slot holding the current step's wave-speed maxima
+  int ns;                 // Navier-Stokes terms on
+  double gamma, mu, kappa_fac;   // kappa_fac = mu gamma / ((gamma-1) Pr)
+  double visc_coef;              // gamma mu / Pr (viscous time-step bound)
+  double cfl, dt_fixed, rkA, rkB;
+  const void* u;          // [K][nv][np] input state
+  void* out;              // mode 0: rhs; mode 1: new state
+  void* du;               // mode 1: 2N-storage register
+  const void* Ja;         // [K][dim][dim][np]
+  const void* invJ;       // [K][np]
+  void* gradW;            // [K][dim][dim+1][np] (Navier-Stokes)
+  const void* alpha_raw;  // [K] unsmoothed blending factors, or null
+  double* alpha_used;     // [K] smoothed factors actually applied (FP64), or null
+  const int* nbr;         // [K][2 dim]
+  const int* bc_kind;     // [n_bc]
+  const void* bc_u;       // [n_bc][nv] conserved boundary states
+  const void* pc;         // mixtures: [K][2][np] pressure and sound speed
+  const void* bc_pc;      // mixtures: [n_bc][2]
+  double* scal;           // device scalars: [0] t, [1] dt of the running step
+  unsigned long long* lam;  // [2 slots][2] wave-speed maxima as ordered double bits
+  unsigned long long* status;
+};
+
+struct DgHostBasis {
+  int N;
+  double x[DG_MAXN + 1], w[DG_MAXN + 1];
+  double D[(DG_MAXN + 1) * (DG_MAXN + 1)];
+  double Vinv[(DG_MAXN + 1) * (DG_MAXN + 1)];  // nodal -> orthonormal Legendre modes
+};
+
+// host basis (dg_basis.cpp)
+int dg_host_basis(int N, DgHostBasis* b);
+
+// kernel translation units
+cudaError_t dg_f64_upload_basis();
+cudaError_t dg_f32_upload_basis();
+cudaError_t dg_f64_rhs(const DgArgs& a, cudaStream_t s);
+cudaError_t dg_f32_rhs(const DgArgs& a, cudaStream_t s);
+cudaError_t dg_f64_gradients(const DgArgs& a, cudaStream_t s);
+cudaError_t dg_f32_gradients(const DgArgs& a, cudaStream_t s);
+cudaError_t dg_f64_lambda(const DgArgs& a, int slot, cudaStream_t s);
+cudaError_t dg_f32_lambda(const DgArgs& a, int slot, cudaStream_t s);
+cudaError_t dg_f64_indicator(const DgArgs& a, double alpha_max, void* alpha_raw, cudaStream_t s);
+cudaError_t dg_f32_indicator(const DgArgs& a, double alpha_max, void* alpha_raw, cudaStream_t s);

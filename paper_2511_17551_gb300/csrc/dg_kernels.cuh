@@ -1,0 +1,293 @@
+// Right-hand-side kernels of the entropy-stable DGSEM (H3PC, arXiv 2511.17551),
+// templated on precision, dimension, degree and number of species.  Included by
+// one translation unit per precision (dg_rhs_f64.cu, dg_rhs_f32.cu).
+//
+// Design (one CTA = EPB elements, all of its data staged in shared memory):
+//   phase A  coalesced copy of the elements' conserved state, metric terms and
+//            1/J into shared memory; per-node primitives (rho, v, p, rho/p)
+//            computed once; for Navier-Stokes, the viscous fluxes f^v_x per node.
+//   phase B  one thread per grid line (direction d, line m): every symmetric pair
+//            (i < l) of the line is evaluated ONCE with the two-point flux and
+//            added to both end points with 2 D_il and 2 D_li held in registers
+//            (split form with zero diagonal, Eqs. fluxdiff / fluxdiffcons, so no
+//            self-flux is ever formed); the same thread owns the line's two face
+//            nodes and computes the interface fluxes there (Eqs. riemann_problem1-3)
+//            from the neighbour's trace, plus the subcell FV fluxes when the
+//            element is blended (Eq. fluxes_discrete_with_fv) and the BR1
+//            viscous divergence along the line (Eq. auxstrongf).  Accumulators
+//            live in registers; each line writes its N+1 node sums once.
+//   phase C  one thread per node: sum the DIM line contributions in a fixed
+//            order, scale by -1/J, and either store du/dt or apply the
+//            2N-storage Runge-Kutta update (and the wave-speed maximum of the
+//            new state for the next step's dt).
+// No atomics touch floating-point sums: results are deterministic.
+#pragma once
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include "dg_internal.h"
+#include "../../include/dg.h"
+
+namespace dgk {
+
+template <typename real>
+struct BasisTab {
+  real D[(DG_MAXN + 1) * (DG_MAXN + 1)];
+  real D2[(DG_MAXN + 1) * (DG_MAXN + 1)];  // 2 D with zero diagonal
+  real w[DG_MAXN + 1];
+  real iw[DG_MAXN + 1];
+  real Vinv[(DG_MAXN + 1) * (DG_MAXN + 1)];
+  real subw[DG_MAXN + 1];                   // w_m for subcell normal sums
+};
+
+template <typename real> struct RealOps;
+template <> struct RealOps<double> {
+  static __device__ __forceinline__ double rcp(double x) { return __drcp_rn(x); }
+  static __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
+  static __device__ __forceinline__ double log_(double x) { return log(x); }
+  static __device__ __forceinline__ double div(double a, double b) { return a / b; }
+  static constexpr double ln_eps = 1e-4;
+};
+template <> struct RealOps<float> {
+  static __device__ __forceinline__ float rcp(float x) { return __frcp_rn(x); }
+  static __device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
+  static __device__ __forceinline__ float log_(float x) { return logf(x); }
+  static __device__ __forceinline__ float div(float a, float b) { return __fdiv_rn(a, b); }
+  // the artanh series truncated after f^6 has relative error f^8/9: 1.1e-9 at 1e-2
+  static constexpr float ln_eps = 1e-2f;
+};
+
+// logarithmic mean L(x,y) = (y-x)/ln(y/x): artanh series for nearly equal
+// arguments, closed form otherwise
+template <typename real>
+__device__ __forceinline__ real ln_mean(real x, real y) {
+  real s = x + y, d = y - x;
+  real rs = RealOps<real>::rcp(s);
+  real f = d * rs, f2 = f * f;
+  if (f2 < RealOps<real>::ln_eps) {
+    real poly = real(2) + f2 * (real(2.0 / 3.0) + f2 * (real(2.0 / 5.0) + f2 * real(2.0 / 7.0)));
+    return s * RealOps<real>::rcp(poly);
+  }
+  return RealOps<real>::div(d, RealOps<real>::log_(RealOps<real>::div(y, x)));
+}
+
+// 1 / L(x,y)
+template <typename real>
+__device__ __forceinline__ real inv_ln_mean(real x, real y) {
+  real s = x + y, d = y - x;
+  real rs = RealOps<real>::rcp(s);
+  real f = d * rs, f2 = f * f;
+  if (f2 < RealOps<real>::ln_eps) {
+    real poly = real(2) + f2 * (real(2.0 / 3.0) + f2 * (real(2.0 / 5.0) + f2 * real(2.0 / 7.0)));
+    return poly * rs;
+  }
+  return RealOps<real>::div(RealOps<real>::log_(RealOps<real>::div(y, x)), d);
+}
+
+__device__ __forceinline__ void latch_status(unsigned long long* st, unsigned long long code,
+                                             int64_t elem) {
+  unsigned long long v = (code << 56) | (unsigned long long)(elem & 0x00ffffffffffffffll);
+  atomicCAS(st, 0ull, v);
+}
+
+__device__ __forceinline__ unsigned long long ordered_bits(double x) {
+  return (unsigned long long)__double_as_longlong(x);  // x >= 0: order preserved
+}
+
+template <int DIM, int N>
+struct Shape {
+  static constexpr int N1 = N + 1;
+  static constexpr int NP = DIM == 3 ? N1 * N1 * N1 : N1 * N1;
+  static constexpr int LPD = DIM == 3 ? N1 * N1 : N1;  // lines per direction
+  static constexpr int LINES = DIM * LPD;
+  static __device__ __forceinline__ int stride(int d) { return d == 0 ? 1 : (d == 1 ? N1 : N1 * N1); }
+  static __device__ __forceinline__ int line_base(int d, int m) {
+    if (DIM == 2) return d == 0 ? m * N1 : m;
+    if (d == 0) return m * N1;
+    if (d == 1) return (m % N1) + (m / N1) * N1 * N1;
+    return m;
+  }
+};
+
+// ---------------------------------------------------------------- pointwise physics
+// Node state in registers (one gas: NSP = 1).
+template <typename real, int DIM, int NSP>
+struct NodeState {
+  static constexpr int NV = NSP + DIM + 1;
+  real u[NV];
+  real rho, v[DIM], p, c;
+};
+
+template <typename real, int DIM, int NSP>
+__device__ __forceinline__ bool prim_from_cons(NodeState<real, DIM, NSP>& s, real gamma,
+                                               real p_ext, real c_ext) {
+  real rho = 0;
+#pragma unroll
+  for (int k = 0; k < NSP; ++k) rho += s.u[k];
+  s.rho = rho;
+  real ir = RealOps<real>::rcp(rho);
+  real ke = 0;
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) {
+    s.v[d] = s.u[NSP + d] * ir;
+    ke += s.u[NSP + d] * s.v[d];
+  }
+  if (NSP == 1) {
+    s.p = (gamma - real(1)) * (s.u[NSP + DIM] - real(0.5) * ke);
+    s.c = RealOps<real>::sqrt_(gamma * s.p * ir);
+  } else {
+    s.p = p_ext;
+    s.c = c_ext;
+  }
+  return rho > real(0) && s.p > real(0) && isfinite(s.p);
+}
+
+template <typename real, int DIM, int NSP>
+__device__ __forceinline__ void phys_flux(const NodeState<real, DIM, NSP>& s, const real* n,
+                                          real* f) {
+  real vn = 0;
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) vn += s.v[d] * n[d];
+#pragma unroll
+  for (int k = 0; k < NSP; ++k) f[k] = s.u[k] * vn;
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) f[NSP + d] = s.u[NSP + d] * vn + s.p * n[d];
+  f[NSP + DIM] = (s.u[NSP + DIM] + s.p) * vn;
+}
+
+// interface flux in the +n orientation between left state L and right state R
+template <typename real, int DIM, int NSP>
+__device__ __forceinline__ void surface_flux(int sf, const NodeState<real, DIM, NSP>& L,
+                                             const NodeState<real, DIM, NSP>& R, const real* n,
+                                             real inv_gm1, real* f);
+
+// two-point volume flux F#(L, R; n)
+template <typename real, int DIM, int NSP>
+__device__ __forceinline__ void volume_flux(int vf, real rL, const real* vL, real pL, real bL,
+                                            const real* uL, real rR, const real* vR, real pR,
+                                            real bR, const real* uR, const real* n,
+                                            real inv_gm1, real* f) {
+  constexpr int NV = NSP + DIM + 1;
+  real vnL = 0, vnR = 0;
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) {
+    vnL += vL[d] * n[d];
+    vnR += vR[d] * n[d];
+  }
+  if (NSP == 1 && vf == DG_VF_RANOCHA) {
+    real rho_m = ln_mean(rL, rR);
+    real ib = inv_ln_mean(bL, bR);  // 1 / L(rho/p)
+    real vv = 0;
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) vv += vL[d] * vR[d];
+    real frho = rho_m * real(0.5) * (vnL + vnR);
+    real pa = real(0.5) * (pL + pR);
+    f[0] = frho;
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) f[1 + d] = frho * real(0.5) * (vL[d] + vR[d]) + pa * n[d];
+    f[1 + DIM] = frho * (real(0.5) * vv + ib * inv_gm1) + real(0.5) * (pL * vnR + pR * vnL);
+  } else if (vf == DG_VF_DUCROS) {
+    real vn = real(0.5) * (vnL + vnR);
+    real pa = real(0.5) * (pL + pR);
+#pragma unroll
+    for (int k = 0; k < NSP; ++k) f[k] = real(0.5) * (uL[k] + uR[k]) * vn;
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) f[NSP + d] = real(0.5) * (uL[NSP + d] + uR[NSP + d]) * vn + pa * n[d];
+    f[NSP + DIM] = real(0.5) * (uL[NSP + DIM] + pL + uR[NSP + DIM] + pR) * vn;
+  } else {  // central
+#pragma unroll
+    for (int k = 0; k < NSP; ++k) f[k] = real(0.5) * (uL[k] * vnL + uR[k] * vnR);
+#pragma unroll
+    for (int d = 0; d < DIM; ++d)
+      f[NSP + d] = real(0.5) * (uL[NSP + d] * vnL + pL * n[d] + uR[NSP + d] * vnR + pR * n[d]);
+    f[NSP + DIM] = real(0.5) * ((uL[NSP + DIM] + pL) * vnL + (uR[NSP + DIM] + pR) * vnR);
+  }
+  (void)NV;
+}
+
+template <typename real, int DIM, int NSP>
+__device__ __forceinline__ void surface_flux(int sf, const NodeState<real, DIM, NSP>& L,
+                                             const NodeState<real, DIM, NSP>& R, const real* n,
+                                             real inv_gm1, real* f) {
+  constexpr int NV = NSP + DIM + 1;
+  if (sf == DG_SF_EC) {
+    real bL = L.rho * RealOps<real>::rcp(L.p), bR = R.rho * RealOps<real>::rcp(R.p);
+    volume_flux<real, DIM, NSP>(NSP == 1 ? DG_VF_RANOCHA : DG_VF_DUCROS, L.rho, L.v, L.p, bL, L.u,
+                                R.rho, R.v, R.p, bR, R.u, n, inv_gm1, f);
+    return;
+  }
+  real nn = 0, vnL = 0, vnR = 0;
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) {
+    nn += n[d] * n[d];
+    vnL += L.v[d] * n[d];
+    vnR += R.v[d] * n[d];
+  }
+  nn = RealOps<real>::sqrt_(nn);
+  real fL[NV], fR[NV];
+  phys_flux<real, DIM, NSP>(L, n, fL);
+  phys_flux<real, DIM, NSP>(R, n, fR);
+  if (sf == DG_SF_LLF) {
+    real lam = fmax(fabs(vnL) + L.c * nn, fabs(vnR) + R.c * nn);
+#pragma unroll
+    for (int k = 0; k < NV; ++k) f[k] = real(0.5) * (fL[k] + fR[k]) - real(0.5) * lam * (R.u[k] - L.u[k]);
+    return;
+  }
+  // HLLC along n/|n| with Davis speed estimates, scaled by |n|
+  real inn = RealOps<real>::rcp(nn);
+  real uLn = vnL * inn, uRn = vnR * inn;
+  real SL = fmin(uLn - L.c, uRn - R.c);
+  real SR = fmax(uLn + L.c, uRn + R.c);
+  if (SL >= real(0)) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) f[k] = fL[k];
+    return;
+  }
+  if (SR <= real(0)) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) f[k] = fR[k];
+    return;
+  }
+  real Ss = RealOps<real>::div(R.p - L.p + L.rho * uLn * (SL - uLn) - R.rho * uRn * (SR - uRn),
+                               L.rho * (SL - uLn) - R.rho * (SR - uRn));
+  const bool left = Ss >= real(0);
+  const NodeState<real, DIM, NSP>& K = left ? L : R;
+  const real* fK = left ? fL : fR;
+  real SK = left ? SL : SR, unK = left ? uLn : uRn;
+  real fac = RealOps<real>::div(SK - unK, SK - Ss);
+  real us[NV];
+#pragma unroll
+  for (int k = 0; k < NSP; ++k) us[k] = K.u[k] * fac;
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) us[NSP + d] = K.rho * fac * (K.v[d] + (Ss - unK) * n[d] * inn);
+  us[NSP + DIM] = K.rho * fac *
+                  (RealOps<real>::div(K.u[NSP + DIM], K.rho) +
+                   (Ss - unK) * (Ss + RealOps<real>::div(K.p, K.rho * (SK - unK))));
+#pragma unroll
+  for (int k = 0; k < NV; ++k) f[k] = fK[k] + nn * SK * (us[k] - K.u[k]);
+}
+
+// physical viscous flux f^v_x (x = physical direction) for one gas; c = 0..DIM-1
+// momentum, c = DIM energy (the density component is zero).  g[x][a] = d(W_a)/dx_x with
+// W = (v_1..v_DIM, theta = p / rho).
+template <typename real, int DIM>
+__device__ __forceinline__ void viscous_flux(const real (*g)[DIM + 1], const real* v, real mu,
+                                             real kap, real (*fv)[DIM + 1]) {
+  real div = 0;
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) div += g[a][a];
+#pragma unroll
+  for (int x = 0; x < DIM; ++x) {
+    real work = 0;
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+      real sig = mu * (g[x][a] + g[a][x]);
+      if (a == x) sig -= real(2.0 / 3.0) * mu * div;
+      fv[x][a] = sig;
+      work += v[a] * sig;
+    }
+    fv[x][DIM] = work + kap * g[x][DIM];
+  }
+}
+
+}  // namespace dgk

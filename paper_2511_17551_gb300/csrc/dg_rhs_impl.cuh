@@ -1,0 +1,847 @@
+// Kernels and launchers for one precision.  The including translation unit
+// defines DG_REAL (double or float) and DG_PREFIX (function-name prefix).
+#pragma once
+#include "dg_kernels.cuh"
+
+namespace {
+
+using real = DG_REAL;
+using namespace dgk;
+
+__constant__ BasisTab<real> c_tab[DG_MAXN + 1];
+
+// elements per CTA: about 128-256 line threads, bounded shared memory
+template <int DIM, int N>
+constexpr int epb() {
+  return Shape<DIM, N>::LINES >= 128 ? 1 : (256 / Shape<DIM, N>::LINES > 16 ? 16 : 256 / Shape<DIM, N>::LINES);
+}
+
+template <int DIM, int N, int NSP, bool NS>
+struct Layout {
+  using S = Shape<DIM, N>;
+  static constexpr int NV = NSP + DIM + 1;
+  static constexpr int NP = S::NP;
+  static constexpr int EPB = epb<DIM, N>();
+  static constexpr int NQ = DIM + 3;                // rho, v, p, beta(=rho/p)
+  static constexpr int NFV = NS ? DIM * (DIM + 1) : 0;
+  // shared memory offsets (in reals) per CTA
+  static constexpr int U = 0;
+  static constexpr int Q = U + EPB * NV * NP;
+  static constexpr int JA = Q + EPB * NQ * NP;
+  static constexpr int IJ = JA + EPB * DIM * DIM * NP;
+  static constexpr int ACC = IJ + EPB * NP;
+  static constexpr int FV = ACC + EPB * DIM * NV * NP;
+  static constexpr int PC = FV + EPB * NFV * NP;    // mixtures: p, c per node
+  static constexpr int TOTAL = PC + (NSP > 1 ? EPB * 2 * NP : 0);
+  static constexpr int THREADS = ((EPB * S::LINES + 31) / 32) * 32;
+};
+
+// boundary / neighbour state at a face node.  Returns 1 when the face flux is the
+// physical flux of the returned state (supersonic inflow / outflow).
+template <int DIM, int NSP>
+__device__ __forceinline__ int outer_state(const DgArgs& a, int nb, int nnode,
+                                           const NodeState<real, DIM, NSP>& own, const real* n,
+                                           NodeState<real, DIM, NSP>& x, bool& ok) {
+  constexpr int NV = NSP + DIM + 1;
+  const real* gu = (const real*)a.u;
+  const int np = a.np;
+  if (nb >= 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) x.u[k] = gu[((int64_t)nb * NV + k) * np + nnode];
+    real pe = 0, ce = 0;
+    if (NSP > 1) {
+      const real* pc = (const real*)a.pc;
+      pe = pc[((int64_t)nb * 2 + 0) * np + nnode];
+      ce = pc[((int64_t)nb * 2 + 1) * np + nnode];
+    }
+    ok = prim_from_cons<real, DIM, NSP>(x, real(a.gamma), pe, ce);
+    return 0;
+  }
+  int bc = -(nb + 1);
+  int kind = a.bc_kind[bc];
+  if (kind == DG_BC_INFLOW) {
+    const real* bu = (const real*)a.bc_u;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) x.u[k] = bu[bc * NV + k];
+    real pe = 0, ce = 0;
+    if (NSP > 1) {
+      pe = ((const real*)a.bc_pc)[bc * 2 + 0];
+      ce = ((const real*)a.bc_pc)[bc * 2 + 1];
+    }
+    ok = prim_from_cons<real, DIM, NSP>(x, real(a.gamma), pe, ce);
+    return 1;
+  }
+  x = own;
+  if (kind == DG_BC_OUTFLOW) return 1;
+  // slip wall: mirror the normal velocity
+  real nn = 0, vn = 0;
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) {
+    nn += n[d] * n[d];
+    vn += own.v[d] * n[d];
+  }
+  real s = real(2) * vn * RealOps<real>::rcp(nn);
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) {
+    x.v[d] = own.v[d] - s * n[d];
+    x.u[NSP + d] = own.rho * x.v[d];
+  }
+  return 0;
+}
+
+// ------------------------------------------------------------------ main RHS / RK kernel
+template <int DIM, int N, int NSP, bool NS>
+__global__ void __launch_bounds__(Layout<DIM, N, NSP, NS>::THREADS)
+rhs_kernel(const DgArgs a) {
+  using S = Shape<DIM, N>;
+  using L = Layout<DIM, N, NSP, NS>;
+  constexpr int NV = L::NV, NP = L::NP, N1 = S::N1, EPB = L::EPB, NQ = L::NQ;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  real* sm = reinterpret_cast<real*>(smem_raw);
+  real* su = sm + L::U;
+  real* sq = sm + L::Q;
+  real* sja = sm + L::JA;
+  real* sij = sm + L::IJ;
+  real* sacc = sm + L::ACC;
+  real* sfv = sm + L::FV;
+  real* spc = sm + L::PC;
+  __shared__ real s_alpha[EPB];
+  __shared__ real s_dt;
+  __shared__ unsigned long long s_lam[2];
+
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int64_t e0 = (int64_t)blockIdx.x * EPB;
+  const int ne = (int)((a.K - e0) < EPB ? (a.K - e0) : EPB);
+  const real gamma = real(a.gamma);
+  const real inv_gm1 = real(1) / (gamma - real(1));
+  const BasisTab<real>& B = c_tab[N];
+
+  // ---- phase A: stage state, metrics, 1/J
+  {
+    const real* gu = (const real*)a.u + e0 * NV * NP;
+    for (int i = tid; i < ne * NV * NP; i += nth) su[i] = gu[i];
+    const real* gj = (const real*)a.Ja + e0 * DIM * DIM * NP;
+    for (int i = tid; i < ne * DIM * DIM * NP; i += nth) sja[i] = gj[i];
+    const real* gi = (const real*)a.invJ + e0 * NP;
+    for (int i = tid; i < ne * NP; i += nth) sij[i] = gi[i];
+    if (NSP > 1) {
+      const real* gp = (const real*)a.pc + e0 * 2 * NP;
+      for (int i = tid; i < ne * 2 * NP; i += nth) spc[i] = gp[i];
+    }
+  }
+  if (tid < EPB) {
+    real al = 0;
+    if (a.alpha_raw && tid < ne) {
+      const real* ar = (const real*)a.alpha_raw;
+      int64_t e = e0 + tid;
+      al = ar[e];
+      for (int f = 0; f < 2 * DIM; ++f) {
+        int nb = a.nbr[e * 2 * DIM + f];
+        if (nb >= 0) al = fmax(al, real(0.5) * ar[nb]);
+      }
+      if (a.alpha_used) a.alpha_used[e] = (double)al;
+    }
+    s_alpha[tid] = al;
+  }
+  if (tid == 0) {
+    double dt = a.dt_fixed;
+    if (a.mode == 1 && !(dt > 0.0)) {
+      double la = __longlong_as_double((long long)a.lam[2 * a.lam_cur + 0]);
+      double lv = __longlong_as_double((long long)a.lam[2 * a.lam_cur + 1]);
+      dt = a.cfl * 2.0 / ((N + 1) * la);
+      if (a.ns && lv > 0.0) dt = fmin(dt, a.cfl * 4.0 / ((N + 1.0) * (N + 1.0) * lv));
+    }
+    s_dt = (real)dt;
+    if (a.mode == 1 && blockIdx.x == 0 && a.stage == 0) {
+      a.scal[1] = dt;
+      a.lam[2 * (a.lam_cur ^ 1) + 0] = 0ull;
+      a.lam[2 * (a.lam_cur ^ 1) + 1] = 0ull;
+    }
+    if (a.mode == 1 && blockIdx.x == 0 && a.stage == 4) a.scal[0] += dt;
+    s_lam[0] = s_lam[1] = 0ull;
+  }
+  __syncthreads();
+  for (int i = tid; i < ne * NP; i += nth) {
+    const int e = i / NP, node = i % NP;
+    const real* uu = su + e * NV * NP + node;
+    real rho = 0;
+#pragma unroll
+    for (int k = 0; k < NSP; ++k) rho += uu[k * NP];
+    real ir = RealOps<real>::rcp(rho), ke = 0;
+    real* q = sq + e * NQ * NP + node;
+    q[0] = rho;
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+      real v = uu[(NSP + d) * NP] * ir;
+      q[(1 + d) * NP] = v;
+      ke += uu[(NSP + d) * NP] * v;
+    }
+    real p;
+    if (NSP == 1) p = (gamma - real(1)) * (uu[(NSP + DIM) * NP] - real(0.5) * ke);
+    else p = spc[e * 2 * NP + node];
+    q[(1 + DIM) * NP] = p;
+    q[(2 + DIM) * NP] = rho * RealOps<real>::rcp(p);
+    if (!(rho > real(0) && p > real(0) && isfinite(p)))
+      latch_status(a.status, DG_ST_NONPHYS, e0 + e);
+    if (NS) {
+      // viscous fluxes from the BR1 gradients of (v, theta)
+      const real* g = (const real*)a.gradW + (e0 + e) * DIM * (DIM + 1) * NP + node;
+      real gg[DIM][DIM + 1], vv[DIM], fv[DIM][DIM + 1];
+#pragma unroll
+      for (int x = 0; x < DIM; ++x)
+#pragma unroll
+        for (int c = 0; c <= DIM; ++c) gg[x][c] = g[(x * (DIM + 1) + c) * NP];
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) vv[d] = q[(1 + d) * NP];
+      viscous_flux<real, DIM>(gg, vv, real(a.mu), real(a.kappa_fac), fv);
+      real* so = sfv + e * L::NFV * NP + node;
+#pragma unroll
+      for (int x = 0; x < DIM; ++x)
+#pragma unroll
+        for (int c = 0; c <= DIM; ++c) so[(x * (DIM + 1) + c) * NP] = fv[x][c];
+    }
+  }
+  __syncthreads();
+
+  // ---- phase B: one thread per line
+  for (int t = tid; t < ne * S::LINES; t += nth) {
+    const int e = t / S::LINES, r = t % S::LINES;
+    const int d = r / S::LPD, m = r % S::LPD;
+    const int s = S::stride(d), base = S::line_base(d, m);
+    const int64_t eg = e0 + e;
+    const real* q = sq + e * NQ * NP;
+    const real* ja = sja + (e * DIM + d) * DIM * NP;  // Ja^d components at [c][node]
+    const real* ue = su + e * NV * NP;
+    real acc[N1][NV];
+#pragma unroll
+    for (int i = 0; i < N1; ++i)
+#pragma unroll
+      for (int k = 0; k < NV; ++k) acc[i][k] = 0;
+    const real al = s_alpha[e];
+    const real wdg = real(1) - al;
+
+    // volume: every symmetric pair once (split form, diagonal-free)
+#pragma unroll
+    for (int i = 0; i < N1; ++i) {
+      const int ni = base + i * s;
+      real vi[DIM], ui[NV];
+#pragma unroll
+      for (int c = 0; c < DIM; ++c) vi[c] = q[(1 + c) * NP + ni];
+      if (NSP > 1 || a.vf != DG_VF_RANOCHA) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) ui[k] = ue[k * NP + ni];
+      }
+#pragma unroll
+      for (int l = i + 1; l < N1; ++l) {
+        const int nl = base + l * s;
+        real vl[DIM], ul[NV], nrm[DIM], F[NV];
+#pragma unroll
+        for (int c = 0; c < DIM; ++c) {
+          vl[c] = q[(1 + c) * NP + nl];
+          nrm[c] = real(0.5) * (ja[c * NP + ni] + ja[c * NP + nl]);
+        }
+        if (NSP > 1 || a.vf != DG_VF_RANOCHA) {
+#pragma unroll
+          for (int k = 0; k < NV; ++k) ul[k] = ue[k * NP + nl];
+        }
+        volume_flux<real, DIM, NSP>(a.vf, q[ni], vi, q[(1 + DIM) * NP + ni], q[(2 + DIM) * NP + ni], ui,
+                                    q[nl], vl, q[(1 + DIM) * NP + nl], q[(2 + DIM) * NP + nl], ul,
+                                    nrm, inv_gm1, F);
+        const real cil = wdg * B.D2[i * N1 + l], cli = wdg * B.D2[l * N1 + i];
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+          acc[i][k] += cil * F[k];
+          acc[l][k] += cli * F[k];
+        }
+      }
+    }
+
+    // the two face nodes of the line
+    NodeState<real, DIM, NSP> own[2];
+    real Fs[2][NV];
+    real nface[2][DIM];
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+      const int f = 2 * d + side;
+      const int node = base + (side ? N : 0) * s;
+      const int nnode = base + (side ? 0 : N) * s;
+      NodeState<real, DIM, NSP>& o = own[side];
+#pragma unroll
+      for (int k = 0; k < NV; ++k) o.u[k] = ue[k * NP + node];
+      o.rho = q[node];
+#pragma unroll
+      for (int c = 0; c < DIM; ++c) o.v[c] = q[(1 + c) * NP + node];
+      o.p = q[(1 + DIM) * NP + node];
+      o.c = NSP == 1 ? RealOps<real>::sqrt_(gamma * o.p * RealOps<real>::rcp(o.rho))
+                     : spc[(e * 2 + 1) * NP + node];
+#pragma unroll
+      for (int c = 0; c < DIM; ++c) nface[side][c] = ja[c * NP + node];
+      const int nb = a.nbr[eg * 2 * DIM + f];
+      NodeState<real, DIM, NSP> x;
+      bool ok = true;
+      int phys = outer_state<DIM, NSP>(a, nb, nnode, o, nface[side], x, ok);
+      if (!ok) latch_status(a.status, DG_ST_NONPHYS, nb >= 0 ? nb : eg);
+      if (phys) phys_flux<real, DIM, NSP>(x, nface[side], Fs[side]);
+      else if (side) surface_flux<real, DIM, NSP>(a.sf, o, x, nface[side], inv_gm1, Fs[side]);
+      else surface_flux<real, DIM, NSP>(a.sf, x, o, nface[side], inv_gm1, Fs[side]);
+    }
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      acc[0][k] -= B.iw[0] * Fs[0][k];
+      acc[N][k] += B.iw[N] * Fs[1][k];
+    }
+
+    // subcell finite-volume part of blended elements
+    if (al > real(0)) {
+      real nh[DIM];
+#pragma unroll
+      for (int c = 0; c < DIM; ++c) nh[c] = ja[c * NP + base];
+#pragma unroll
+      for (int j = 1; j < N1; ++j) {
+        // advance the subcell normal across subcell j-1: n += w_{j-1} (D Ja)_{j-1}
+#pragma unroll
+        for (int l = 0; l < N1; ++l) {
+          const real cw = B.w[j - 1] * B.D[(j - 1) * N1 + l];
+#pragma unroll
+          for (int c = 0; c < DIM; ++c) nh[c] += cw * ja[c * NP + base + l * s];
+        }
+        NodeState<real, DIM, NSP> Lq, Rq;
+        const int nl = base + (j - 1) * s, nr = base + j * s;
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+          Lq.u[k] = ue[k * NP + nl];
+          Rq.u[k] = ue[k * NP + nr];
+        }
+        Lq.rho = q[nl];
+        Rq.rho = q[nr];
+#pragma unroll
+        for (int c = 0; c < DIM; ++c) {
+          Lq.v[c] = q[(1 + c) * NP + nl];
+          Rq.v[c] = q[(1 + c) * NP + nr];
+        }
+        Lq.p = q[(1 + DIM) * NP + nl];
+        Rq.p = q[(1 + DIM) * NP + nr];
+        if (NSP == 1) {
+          Lq.c = RealOps<real>::sqrt_(gamma * Lq.p * RealOps<real>::rcp(Lq.rho));
+          Rq.c = RealOps<real>::sqrt_(gamma * Rq.p * RealOps<real>::rcp(Rq.rho));
+        } else {
+          Lq.c = spc[(e * 2 + 1) * NP + nl];
+          Rq.c = spc[(e * 2 + 1) * NP + nr];
+        }
+        real F[NV];
+        surface_flux<real, DIM, NSP>(a.sf == DG_SF_EC ? DG_SF_LLF : a.sf, Lq, Rq, nh, inv_gm1, F);
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+          acc[j - 1][k] += al * B.iw[j - 1] * F[k];
+          acc[j][k] -= al * B.iw[j] * F[k];
+        }
+      }
+    }
+
+    if (NS) {
+      // viscous divergence along the line: D Fv + M^{-1} B (Fv* - Fv); enters with + sign
+      real Fv[N1][DIM + 1];
+      const real* fvb = sfv + e * L::NFV * NP;
+#pragma unroll
+      for (int i = 0; i < N1; ++i) {
+        const int ni = base + i * s;
+#pragma unroll
+        for (int c = 0; c <= DIM; ++c) {
+          real acc_c = 0;
+#pragma unroll
+          for (int x = 0; x < DIM; ++x) acc_c += ja[x * NP + ni] * fvb[(x * (DIM + 1) + c) * NP + ni];
+          Fv[i][c] = acc_c;
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < N1; ++i)
+#pragma unroll
+        for (int c = 0; c <= DIM; ++c) {
+          real dsum = 0;
+#pragma unroll
+          for (int l = 0; l < N1; ++l) dsum += B.D[i * N1 + l] * Fv[l][c];
+          acc[i][NSP + c] -= dsum;
+        }
+#pragma unroll
+      for (int side = 0; side < 2; ++side) {
+        const int f = 2 * d + side;
+        const int node = base + (side ? N : 0) * s;
+        const int nnode = base + (side ? 0 : N) * s;
+        const int nb = a.nbr[eg * 2 * DIM + f];  // periodic / interior only
+        const real* gn = (const real*)a.gradW + (int64_t)nb * DIM * (DIM + 1) * NP + nnode;
+        const real* un = (const real*)a.u + (int64_t)nb * NV * NP + nnode;
+        real gg[DIM][DIM + 1], vn[DIM], fvn[DIM][DIM + 1];
+#pragma unroll
+        for (int x = 0; x < DIM; ++x)
+#pragma unroll
+          for (int c = 0; c <= DIM; ++c) gg[x][c] = gn[(x * (DIM + 1) + c) * NP];
+        real rn = 0;
+#pragma unroll
+        for (int k = 0; k < NSP; ++k) rn += un[k * NP];
+        real irn = RealOps<real>::rcp(rn);
+#pragma unroll
+        for (int c = 0; c < DIM; ++c) vn[c] = un[(NSP + c) * NP] * irn;
+        viscous_flux<real, DIM>(gg, vn, real(a.mu), real(a.kappa_fac), fvn);
+        const int i = side ? N : 0;
+#pragma unroll
+        for (int c = 0; c <= DIM; ++c) {
+          real Fs_c = 0;
+#pragma unroll
+          for (int x = 0; x < DIM; ++x)
+            Fs_c += real(0.5) * (fvb[(x * (DIM + 1) + c) * NP + node] + fvn[x][c]) * nface[side][x];
+          real jump = Fs_c - Fv[i][c];
+          if (side) acc[N][NSP + c] -= B.iw[N] * jump;
+          else acc[0][NSP + c] += B.iw[0] * jump;
+        }
+      }
+    }
+
+    real* sa = sacc + (e * DIM + d) * NV * NP;
+#pragma unroll
+    for (int i = 0; i < N1; ++i)
+#pragma unroll
+      for (int k = 0; k < NV; ++k) sa[k * NP + base + i * s] = acc[i][k];
+  }
+  __syncthreads();
+
+  // ---- phase C: one thread per node
+  real lam_a = 0, lam_v = 0;
+  for (int i = tid; i < ne * NP; i += nth) {
+    const int e = i / NP, node = i % NP;
+    const real ij = sij[e * NP + node];
+    const real* sa = sacc + e * DIM * NV * NP + node;
+    const int64_t gbase = (e0 + e) * NV * NP + node;
+    if (a.mode == 0) {
+      real* out = (real*)a.out;
+#pragma unroll
+      for (int k = 0; k < NV; ++k) {
+        real sum = 0;
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) sum += sa[(d * NV + k) * NP];
+        out[gbase + k * NP] = -ij * sum;
+      }
+    } else {
+      real* out = (real*)a.out;
+      real* du = (real*)a.du;
+      const real A = real(a.rkA), Bc = real(a.rkB), dt = s_dt;
+      real un[NV];
+#pragma unroll
+      for (int k = 0; k < NV; ++k) {
+        real sum = 0;
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) sum += sa[(d * NV + k) * NP];
+        const real r = -ij * sum;
+        real dn = (a.stage == 0 ? real(0) : A * du[gbase + k * NP]) + dt * r;
+        du[gbase + k * NP] = dn;
+        un[k] = su[(e * NV + k) * NP + node] + Bc * dn;
+        out[gbase + k * NP] = un[k];
+      }
+      if (a.want_lambda && NSP == 1) {
+        real rho = 0;
+#pragma unroll
+        for (int k = 0; k < NSP; ++k) rho += un[k];
+        real ir = RealOps<real>::rcp(rho), ke = 0, v[DIM];
+#pragma unroll
+        for (int dd = 0; dd < DIM; ++dd) {
+          v[dd] = un[NSP + dd] * ir;
+          ke += un[NSP + dd] * v[dd];
+        }
+        real p = (gamma - real(1)) * (un[NSP + DIM] - real(0.5) * ke);
+        real c = RealOps<real>::sqrt_(gamma * p * ir);
+        real la = 0, lv = 0;
+#pragma unroll
+        for (int dd = 0; dd < DIM; ++dd) {
+          real vn = 0, nn = 0;
+#pragma unroll
+          for (int cc = 0; cc < DIM; ++cc) {
+            real jv = sja[((e * DIM + dd) * DIM + cc) * NP + node];
+            vn += v[cc] * jv;
+            nn += jv * jv;
+          }
+          la += fabs(vn) + c * RealOps<real>::sqrt_(nn);
+          lv += nn;
+        }
+        la *= ij;
+        lv *= ij * ij * real(a.visc_coef) * ir;
+        if (!(p > real(0)) || !isfinite(la)) {
+          latch_status(a.status, DG_ST_NONPHYS, e0 + e);
+          la = real(0);
+        }
+        lam_a = fmax(lam_a, la);
+        lam_v = fmax(lam_v, lv);
+      }
+    }
+  }
+  if (a.mode == 1 && a.want_lambda) {
+    atomicMax(&s_lam[0], ordered_bits((double)lam_a));
+    if (a.ns) atomicMax(&s_lam[1], ordered_bits((double)lam_v));
+    __syncthreads();
+    if (tid == 0) {
+      atomicMax(&a.lam[2 * (a.lam_cur ^ 1) + 0], s_lam[0]);
+      if (a.ns) atomicMax(&a.lam[2 * (a.lam_cur ^ 1) + 1], s_lam[1]);
+    }
+  }
+}
+
+// ------------------------------------------------------------------ BR1 gradients
+template <int DIM, int N, int NSP>
+struct GLayout {
+  using S = Shape<DIM, N>;
+  static constexpr int NV = NSP + DIM + 1;
+  static constexpr int NP = S::NP;
+  static constexpr int EPB = epb<DIM, N>();
+  static constexpr int NW = DIM + 1;
+  static constexpr int W = 0;
+  static constexpr int JA = W + EPB * NW * NP;
+  static constexpr int IJ = JA + EPB * DIM * DIM * NP;
+  static constexpr int G = IJ + EPB * NP;
+  static constexpr int TOTAL = G + EPB * DIM * NW * NP;
+  static constexpr int THREADS = ((EPB * S::LINES + 31) / 32) * 32;
+};
+
+template <int DIM, int N, int NSP>
+__global__ void __launch_bounds__(GLayout<DIM, N, NSP>::THREADS)
+gradient_kernel(const DgArgs a) {
+  using S = Shape<DIM, N>;
+  using L = GLayout<DIM, N, NSP>;
+  constexpr int NV = L::NV, NP = L::NP, N1 = S::N1, EPB = L::EPB, NW = L::NW;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  real* sm = reinterpret_cast<real*>(smem_raw);
+  real* sw = sm + L::W;
+  real* sja = sm + L::JA;
+  real* sij = sm + L::IJ;
+  real* sg = sm + L::G;
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int64_t e0 = (int64_t)blockIdx.x * EPB;
+  const int ne = (int)((a.K - e0) < EPB ? (a.K - e0) : EPB);
+  const real gamma = real(a.gamma);
+  const BasisTab<real>& B = c_tab[N];
+  const real* gu = (const real*)a.u;
+  {
+    const real* gj = (const real*)a.Ja + e0 * DIM * DIM * NP;
+    for (int i = tid; i < ne * DIM * DIM * NP; i += nth) sja[i] = gj[i];
+    const real* gi = (const real*)a.invJ + e0 * NP;
+    for (int i = tid; i < ne * NP; i += nth) sij[i] = gi[i];
+  }
+  for (int i = tid; i < ne * NP; i += nth) {
+    const int e = i / NP, node = i % NP;
+    const real* uu = gu + (e0 + e) * NV * NP + node;
+    real rho = 0;
+#pragma unroll
+    for (int k = 0; k < NSP; ++k) rho += uu[k * NP];
+    real ir = RealOps<real>::rcp(rho), ke = 0;
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+      real v = uu[(NSP + d) * NP] * ir;
+      sw[(e * NW + d) * NP + node] = v;
+      ke += uu[(NSP + d) * NP] * v;
+    }
+    real p = (gamma - real(1)) * (uu[(NSP + DIM) * NP] - real(0.5) * ke);
+    sw[(e * NW + DIM) * NP + node] = p * ir;
+  }
+  __syncthreads();
+  for (int t = tid; t < ne * S::LINES; t += nth) {
+    const int e = t / S::LINES, r = t % S::LINES;
+    const int d = r / S::LPD, m = r % S::LPD;
+    const int s = S::stride(d), base = S::line_base(d, m);
+    const int64_t eg = e0 + e;
+    const real* w = sw + e * NW * NP;
+    real Wl[N1][NW];
+#pragma unroll
+    for (int i = 0; i < N1; ++i)
+#pragma unroll
+      for (int c = 0; c < NW; ++c) Wl[i][c] = w[c * NP + base + i * s];
+    real G[N1][NW];
+#pragma unroll
+    for (int i = 0; i < N1; ++i)
+#pragma unroll
+      for (int c = 0; c < NW; ++c) {
+        real acc = 0;
+#pragma unroll
+        for (int l = 0; l < N1; ++l) acc += B.D[i * N1 + l] * Wl[l][c];
+        G[i][c] = acc;
+      }
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+      const int f = 2 * d + side;
+      const int nnode = base + (side ? 0 : N) * s;
+      const int nb = a.nbr[eg * 2 * DIM + f];
+      const real* un = gu + (int64_t)nb * NV * NP + nnode;
+      real rn = 0;
+#pragma unroll
+      for (int k = 0; k < NSP; ++k) rn += un[k * NP];
+      real irn = RealOps<real>::rcp(rn), ke = 0, Wn[NW];
+#pragma unroll
+      for (int c = 0; c < DIM; ++c) {
+        Wn[c] = un[(NSP + c) * NP] * irn;
+        ke += un[(NSP + c) * NP] * Wn[c];
+      }
+      Wn[DIM] = (gamma - real(1)) * (un[(NSP + DIM) * NP] - real(0.5) * ke) * irn;
+      const int i = side ? N : 0;
+#pragma unroll
+      for (int c = 0; c < NW; ++c) {
+        real ws = real(0.5) * (Wl[i][c] + Wn[c]);
+        if (side) G[N][c] += B.iw[N] * (ws - Wl[N][c]);
+        else G[0][c] -= B.iw[0] * (ws - Wl[0][c]);
+      }
+    }
+    real* g = sg + (e * DIM + d) * NW * NP;
+#pragma unroll
+    for (int i = 0; i < N1; ++i)
+#pragma unroll
+      for (int c = 0; c < NW; ++c) g[c * NP + base + i * s] = G[i][c];
+  }
+  __syncthreads();
+  real* out = (real*)a.gradW;
+  for (int i = tid; i < ne * NP; i += nth) {
+    const int e = i / NP, node = i % NP;
+    const real ij = sij[e * NP + node];
+#pragma unroll
+    for (int x = 0; x < DIM; ++x)
+#pragma unroll
+      for (int c = 0; c < NW; ++c) {
+        real acc = 0;
+#pragma unroll
+        for (int d = 0; d < DIM; ++d)
+          acc += sja[((e * DIM + d) * DIM + x) * NP + node] * sg[((e * DIM + d) * NW + c) * NP + node];
+        out[((e0 + e) * DIM + x) * NW * NP + c * NP + node] = acc * ij;
+      }
+  }
+}
+
+// ------------------------------------------------------------------ wave speeds (dt)
+template <int DIM, int NSP>
+__global__ void lambda_kernel(const DgArgs a, int slot) {
+  __shared__ unsigned long long s_l[2];
+  constexpr int NV = NSP + DIM + 1;
+  const int np = a.np;
+  const int64_t n = a.K * np;
+  if (threadIdx.x == 0) s_l[0] = s_l[1] = 0ull;
+  __syncthreads();
+  real la_m = 0, lv_m = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = i / np;
+    const int node = (int)(i % np);
+    const real* uu = (const real*)a.u + e * NV * np + node;
+    real rho = 0;
+    for (int k = 0; k < NSP; ++k) rho += uu[k * np];
+    real ir = RealOps<real>::rcp(rho), ke = 0, v[DIM];
+    for (int d = 0; d < DIM; ++d) {
+      v[d] = uu[(NSP + d) * np] * ir;
+      ke += uu[(NSP + d) * np] * v[d];
+    }
+    real c;
+    if (NSP == 1) {
+      real p = (real(a.gamma) - real(1)) * (uu[(NSP + DIM) * np] - real(0.5) * ke);
+      c = RealOps<real>::sqrt_(real(a.gamma) * p * ir);
+    } else {
+      c = ((const real*)a.pc)[(e * 2 + 1) * np + node];
+    }
+    const real ij = ((const real*)a.invJ)[e * np + node];
+    real la = 0, lv = 0;
+    for (int d = 0; d < DIM; ++d) {
+      real vn = 0, nn = 0;
+      for (int x = 0; x < DIM; ++x) {
+        real jv = ((const real*)a.Ja)[((e * DIM + d) * DIM + x) * np + node];
+        vn += v[x] * jv;
+        nn += jv * jv;
+      }
+      la += fabs(vn) + c * RealOps<real>::sqrt_(nn);
+      lv += nn;
+    }
+    la *= ij;
+    lv *= ij * ij * real(a.visc_coef) * ir;
+    if (!isfinite(la)) la = real(0);
+    la_m = fmax(la_m, la);
+    lv_m = fmax(lv_m, lv);
+  }
+  atomicMax(&s_l[0], ordered_bits((double)la_m));
+  atomicMax(&s_l[1], ordered_bits((double)lv_m));
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    atomicMax(&a.lam[2 * slot + 0], s_l[0]);
+    if (a.ns) atomicMax(&a.lam[2 * slot + 1], s_l[1]);
+  }
+}
+
+// ------------------------------------------------------------------ shock indicator
+// Hennemann-Gassner modal energy of rho*p, one thread per element.
+template <int DIM, int N, int NSP>
+__global__ void indicator_kernel(const DgArgs a, real alpha_max, real* alpha_raw) {
+  using S = Shape<DIM, N>;
+  constexpr int NP = S::NP, N1 = S::N1, NV = NSP + DIM + 1;
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= a.K) return;
+  const BasisTab<real>& B = c_tab[N];
+  const real* uu = (const real*)a.u + e * NV * NP;
+  real f[NP];
+#pragma unroll
+  for (int node = 0; node < NP; ++node) {
+    real rho = 0;
+#pragma unroll
+    for (int k = 0; k < NSP; ++k) rho += uu[k * NP + node];
+    real p;
+    if (NSP == 1) {
+      real ke = 0;
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) ke += uu[(NSP + d) * NP + node] * uu[(NSP + d) * NP + node];
+      p = (real(a.gamma) - real(1)) * (uu[(NSP + DIM) * NP + node] - real(0.5) * ke * RealOps<real>::rcp(rho));
+    } else {
+      p = ((const real*)a.pc)[(e * 2) * NP + node];
+    }
+    f[node] = rho * p;
+  }
+  // modal coefficients: V^{-1} along each direction
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) {
+    const int s = d == 0 ? 1 : (d == 1 ? N1 : N1 * N1);
+    real g[NP];
+#pragma unroll
+    for (int node = 0; node < NP; ++node) {
+      const int pos = (node / s) % N1, base = node - pos * s;
+      real acc = 0;
+#pragma unroll
+      for (int l = 0; l < N1; ++l) acc += B.Vinv[pos * N1 + l] * f[base + l * s];
+      g[node] = acc;
+    }
+#pragma unroll
+    for (int node = 0; node < NP; ++node) f[node] = g[node];
+  }
+  real Et = 0, E1 = 0, E2 = 0;
+#pragma unroll
+  for (int node = 0; node < NP; ++node) {
+    int mx = node % N1;
+    if (DIM >= 2) mx = max(mx, (node / N1) % N1);
+    if (DIM == 3) mx = max(mx, node / (N1 * N1));
+    real e2 = f[node] * f[node];
+    Et += e2;
+    if (mx <= N - 1) E1 += e2;
+    if (mx <= N - 2) E2 += e2;
+  }
+  real fr1 = Et > real(0) ? (Et - E1) / Et : real(0);
+  real fr2 = E1 > real(0) ? (E1 - E2) / E1 : real(0);
+  real E = fmax(fr1, fr2);
+  const real thr = real(0.5 * pow(10.0, -1.8 * pow(N + 1.0, 0.25)));
+  const real sp = real(9.21024036697585);  // ln((1 - 1e-4) / 1e-4)
+  real al = real(1) / (real(1) + exp(-(sp / thr) * (E - thr)));
+  if (al < real(1e-3)) al = real(0);
+  if (al > alpha_max) al = alpha_max;
+  alpha_raw[e] = al;
+}
+
+template <typename KernelT>
+cudaError_t set_smem(KernelT k, size_t bytes) {
+  if (bytes <= 48 * 1024) return cudaSuccess;
+  return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+template <int DIM, int N, int NSP, bool NS>
+cudaError_t launch_rhs_t(const DgArgs& a, cudaStream_t st) {
+  using L = Layout<DIM, N, NSP, NS>;
+  const size_t smem = sizeof(real) * L::TOTAL;
+  auto k = rhs_kernel<DIM, N, NSP, NS>;
+  cudaError_t err = set_smem(k, smem);
+  if (err != cudaSuccess) return err;
+  const int64_t grid = (a.K + L::EPB - 1) / L::EPB;
+  k<<<(unsigned)grid, L::THREADS, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <int DIM, int N, int NSP>
+cudaError_t launch_grad_t(const DgArgs& a, cudaStream_t st) {
+  using L = GLayout<DIM, N, NSP>;
+  const size_t smem = sizeof(real) * L::TOTAL;
+  auto k = gradient_kernel<DIM, N, NSP>;
+  cudaError_t err = set_smem(k, smem);
+  if (err != cudaSuccess) return err;
+  const int64_t grid = (a.K + L::EPB - 1) / L::EPB;
+  k<<<(unsigned)grid, L::THREADS, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <int DIM, int N, int NSP>
+cudaError_t launch_ind_t(const DgArgs& a, double amax, void* out, cudaStream_t st) {
+  const int bs = 128;
+  const int64_t grid = (a.K + bs - 1) / bs;
+  indicator_kernel<DIM, N, NSP><<<(unsigned)grid, bs, 0, st>>>(a, (real)amax, (real*)out);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+#define DG_CAT2(a, b) a##b
+#define DG_CAT(a, b) DG_CAT2(a, b)
+
+// dispatch on (dim, N, nsp, ns)
+#define DG_DISPATCH_N(MACRO, DIM, NSP, ...)             \
+  switch (a.N) {                                        \
+    case 2: return MACRO(DIM, 2, NSP, __VA_ARGS__);     \
+    case 3: return MACRO(DIM, 3, NSP, __VA_ARGS__);     \
+    case 4: return MACRO(DIM, 4, NSP, __VA_ARGS__);     \
+    case 7: return MACRO(DIM, 7, NSP, __VA_ARGS__);     \
+    default: return cudaErrorInvalidValue;              \
+  }
+#define DG_DISPATCH_N_MIX(MACRO, DIM, NSP, ...)         \
+  switch (a.N) {                                        \
+    case 3: return MACRO(DIM, 3, NSP, __VA_ARGS__);     \
+    case 4: return MACRO(DIM, 4, NSP, __VA_ARGS__);     \
+    default: return cudaErrorInvalidValue;              \
+  }
+
+#define DG_RHS_CALL(DIM, N, NSP, NS) launch_rhs_t<DIM, N, NSP, NS>(a, st)
+#define DG_GRAD_CALL(DIM, N, NSP, X) launch_grad_t<DIM, N, NSP>(a, st)
+#define DG_IND_CALL(DIM, N, NSP, X) launch_ind_t<DIM, N, NSP>(a, amax, out, st)
+
+cudaError_t DG_CAT(DG_PREFIX, _rhs)(const DgArgs& a, cudaStream_t st) {
+  if (a.dim == 3 && a.nsp == 1 && a.ns) { DG_DISPATCH_N(DG_RHS_CALL, 3, 1, true) }
+  if (a.dim == 3 && a.nsp == 1) { DG_DISPATCH_N(DG_RHS_CALL, 3, 1, false) }
+  if (a.dim == 2 && a.nsp == 1) { DG_DISPATCH_N(DG_RHS_CALL, 2, 1, false) }
+  if (a.dim == 3 && a.nsp == 5) { DG_DISPATCH_N_MIX(DG_RHS_CALL, 3, 5, false) }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t DG_CAT(DG_PREFIX, _gradients)(const DgArgs& a, cudaStream_t st) {
+  if (a.dim == 3 && a.nsp == 1) { DG_DISPATCH_N(DG_GRAD_CALL, 3, 1, 0) }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t DG_CAT(DG_PREFIX, _indicator)(const DgArgs& a, double amax, void* out, cudaStream_t st) {
+  if (a.dim == 2 && a.nsp == 1) { DG_DISPATCH_N(DG_IND_CALL, 2, 1, 0) }
+  if (a.dim == 3 && a.nsp == 1) { DG_DISPATCH_N(DG_IND_CALL, 3, 1, 0) }
+  if (a.dim == 3 && a.nsp == 5) { DG_DISPATCH_N_MIX(DG_IND_CALL, 3, 5, 0) }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t DG_CAT(DG_PREFIX, _lambda)(const DgArgs& a, int slot, cudaStream_t st) {
+  const int bs = 256;
+  int64_t n = a.K * a.np;
+  int64_t grid = (n + bs - 1) / bs;
+  if (grid > 152 * 16) grid = 152 * 16;
+  if (a.dim == 3 && a.nsp == 1) lambda_kernel<3, 1><<<(unsigned)grid, bs, 0, st>>>(a, slot);
+  else if (a.dim == 2 && a.nsp == 1) lambda_kernel<2, 1><<<(unsigned)grid, bs, 0, st>>>(a, slot);
+  else if (a.dim == 3 && a.nsp == 5) lambda_kernel<3, 5><<<(unsigned)grid, bs, 0, st>>>(a, slot);
+  else return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
+cudaError_t DG_CAT(DG_PREFIX, _upload_basis)() {
+  BasisTab<real> tab[DG_MAXN + 1];
+  memset(tab, 0, sizeof(tab));
+  for (int N = 1; N <= DG_MAXN; ++N) {
+    DgHostBasis b;
+    if (dg_host_basis(N, &b)) return cudaErrorInvalidValue;
+    const int n1 = N + 1;
+    for (int i = 0; i < n1; ++i) {
+      tab[N].w[i] = (real)b.w[i];
+      tab[N].iw[i] = (real)(1.0 / b.w[i]);
+      tab[N].subw[i] = (real)b.w[i];
+      for (int j = 0; j < n1; ++j) {
+        tab[N].D[i * n1 + j] = (real)b.D[i * n1 + j];
+        tab[N].D2[i * n1 + j] = i == j ? (real)0 : (real)(2.0 * b.D[i * n1 + j]);
+        tab[N].Vinv[i * n1 + j] = (real)b.Vinv[i * n1 + j];
+      }
+    }
+  }
+  return cudaMemcpyToSymbol(c_tab, tab, sizeof(tab));
+}

@@ -1,0 +1,25 @@
+// Mixture thermodynamics on the device (temperature from internal energy,
+// pressure, frozen sound speed) for the multi-species Euler form.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+struct DgThermo {
+  int64_t K;
+  int np, dim, ns, mode, f32;
+  double* species;     // device [ns][8]
+  double* T;           // device [K][np] temperature cache (FP64)
+  void* pc;            // device [K][2][np] pressure, sound speed (form precision)
+  void* bc_pc;         // device [n_bc][2]
+  unsigned long long* status;
+  void* mlp;           // surrogate weights (device) or null
+};
+
+cudaError_t dg_thermo_upload_basis();
+cudaError_t dg_thermo_init(DgThermo* th, int64_t K, int np, int dim, const double* species_host,
+                           int mode, int f32, unsigned long long* status);
+void dg_thermo_free(DgThermo* th);
+cudaError_t dg_thermo_reset(DgThermo* th, cudaStream_t s);
+cudaError_t dg_thermo_update(DgThermo* th, const void* u, int f32, cudaStream_t s);
+cudaError_t dg_thermo_boundary(DgThermo* th, const double* bw, int n_bc, void* bc_u, cudaStream_t s);
+cudaError_t dg_thermo_prim2cons(DgThermo* th, const double* w, void* u, cudaStream_t s);

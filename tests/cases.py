@@ -45,3 +45,43 @@ def square_cylinder_small(xi, seed=3):
 
 def mach3_freestream(gamma=GAMMA, mach=3.0):
     return np.array([1.0, 1.0, 0.0, 1.0 / (gamma * mach * mach)])
+
+
+# ---------------------------------------------------------------- matched problem pairs
+def field_errors(a, ref, nsp, dim):
+    """Relative L2 error per conserved field (R19 reading): momentum components are
+    normalised by the norm of the whole momentum block."""
+    a = np.asarray(a, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    nv = a.shape[1]
+    out = []
+    mom = np.linalg.norm(ref[:, nsp:nsp + dim])
+    for v in range(nv):
+        den = mom if nsp <= v < nsp + dim else np.linalg.norm(ref[:, v])
+        out.append(np.linalg.norm(a[:, v] - ref[:, v]) / max(den, 1e-300))
+    return np.array(out)
+
+
+class Pair:
+    """The same workload built twice: once on the oracle's nodes, once on libdg's."""
+
+    def __init__(self, builder, dim, N, precision=0, **kw):
+        import oracle
+        import paper_2511_17551_gb300 as dg
+        self.dim, self.N = dim, N
+        xo, _ = oracle.lgl(N)
+        xg, _ = dg.dg_lgl_nodes(N)
+        self.mesh_o = builder(xo)
+        self.mesh_g = builder(xg)
+        okw = dict(kw)
+        gkw = dict(kw)
+        for k in ("equations", "volume_flux", "surface_flux"):
+            pass
+        self.orc = oracle.Oracle(dim, N, *self.mesh_o[:3], **okw)
+        gkw.pop("alpha_override", None)
+        self.gpu = dg.Solver(dim, N, *self.mesh_g[:3], precision=precision, **gkw)
+        self.K = self.orc.K
+        self.nv = self.orc.nv
+
+    def close(self):
+        self.gpu.close()

@@ -1,0 +1,252 @@
+"""GPU parity: libdg (through the C ABI) against the FP64 oracle on the same seeded inputs.
+
+Tolerances: FP64 form 1e-12 relative L2 per field (the target stated for the FP64
+GPU form); mixed form: see the per-test bounds, derived from FP32 rounding of the
+flux sums (about 1e-6 relative per right-hand side, growing with the cancellation
+in the field's RHS) and 1e-5 relative L2 on the stepped state.
+"""
+import numpy as np
+import pytest
+
+import cases
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-12
+
+
+@pytest.fixture(scope="module")
+def dg():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2511_17551_gb300 as dg
+    dg.lib()
+    return dg
+
+
+def _tgv_builder(n_el=None, shape=None, warp=0.1):
+    def b(x):
+        return cases.tgv(x, n_el, warp=warp, shape=shape)
+    return b
+
+
+def _rhs_pair(dg, pair, w_o, w_g):
+    import torch
+    u_o = pair.orc.prim_to_cons(w_o)
+    r_o = pair.orc.rhs(u_o)
+    pair.gpu.set_primitive(w_g)
+    dt = torch.float32 if pair.gpu.precision == dg.DG_MIXED else torch.float64
+    u_d = torch.empty(pair.gpu.shape, dtype=torch.float64, device="cuda")
+    dg.dg_get_state(pair.gpu.ctx, u_d)
+    u_d = u_d.to(dt)
+    r_d = torch.empty_like(u_d)
+    dg.dg_rhs(pair.gpu.ctx, u_d, r_d)
+    dg.dg_sync(pair.gpu.ctx)
+    return r_d.double().cpu().numpy(), r_o, u_o
+
+
+RHS_CASES = {
+    "tgv_euler_4^3_N3": dict(builder=_tgv_builder(4, warp=0.0), dim=3, N=3, kw={}),
+    "tgv_warped_ragged_N3_llf": dict(builder=_tgv_builder(shape=(3, 3, 5)), dim=3, N=3, kw={}),
+    "tgv_warped_ragged_N3_hllc": dict(builder=_tgv_builder(shape=(3, 3, 5)), dim=3, N=3,
+                                      kw=dict(surface_flux=1)),
+    "tgv_warped_ragged_N3_ec": dict(builder=_tgv_builder(shape=(3, 3, 5)), dim=3, N=3,
+                                    kw=dict(surface_flux=2)),
+    "tgv_warped_N2": dict(builder=_tgv_builder(shape=(3, 4, 3)), dim=3, N=2, kw={}),
+    "tgv_warped_N4_central": dict(builder=_tgv_builder(shape=(2, 3, 3)), dim=3, N=4,
+                                  kw=dict(volume_flux=2)),
+    "tgv_warped_N7": dict(builder=_tgv_builder(shape=(2, 2, 3)), dim=3, N=7, kw={}),
+    "tgv_ns_warped_N3": dict(builder=_tgv_builder(shape=(3, 3, 5)), dim=3, N=3,
+                             kw=dict(equations=1, mu=0.01, Pr=0.72)),
+    "tgv_ns_warped_N7": dict(builder=_tgv_builder(shape=(2, 2, 3)), dim=3, N=7,
+                             kw=dict(equations=1, mu=0.01, Pr=0.72)),
+    "vortex_2d_N3": dict(builder=lambda x: cases.vortex(x, 5), dim=2, N=3, kw={}),
+}
+
+
+def _perturbed(case, mesh, seed):
+    w = mesh[3]
+    return cases.perturbed_state(w, seed=seed, amp=0.05)
+
+
+@pytest.mark.parametrize("name", sorted(RHS_CASES))
+def test_rhs_fp64(dg, name):
+    c = RHS_CASES[name]
+    p = cases.Pair(c["builder"], c["dim"], c["N"], precision=dg.DG_FP64, **c["kw"])
+    try:
+        w_o = _perturbed(c, p.mesh_o, 7)
+        w_g = _perturbed(c, p.mesh_g, 7)
+        r_g, r_o, _ = _rhs_pair(dg, p, w_o, w_g)
+        err = cases.field_errors(r_g, r_o, 1, c["dim"])
+        assert err.max() < FP64_TOL, err
+    finally:
+        p.close()
+
+
+@pytest.mark.parametrize("name", sorted(RHS_CASES))
+def test_rhs_mixed(dg, name):
+    c = RHS_CASES[name]
+    p = cases.Pair(c["builder"], c["dim"], c["N"], precision=dg.DG_MIXED, **c["kw"])
+    try:
+        w_o = _perturbed(c, p.mesh_o, 7)
+        w_g = _perturbed(c, p.mesh_g, 7)
+        r_g, r_o, _ = _rhs_pair(dg, p, w_o, w_g)
+        err = cases.field_errors(r_g, r_o, 1, c["dim"])
+        # FP32 rounding of the state (6e-8) amplified by the flux-difference cancellation
+        assert err.max() < 2e-4, err
+    finally:
+        p.close()
+
+
+def _cyl_pair(dg, precision, N=3, alpha_max=0.5, sf=0):
+    fs = cases.mach3_freestream()
+    kw = dict(bc_kind=[1, 2, 3], bc_prim=np.stack([fs] * 3), alpha_max=alpha_max, surface_flux=sf)
+    return cases.Pair(lambda x: cases.square_cylinder_small(x), 2, N, precision=precision, **kw), fs
+
+
+def _blast(mesh, fs):
+    import workloads as W
+    xyz = mesh[0]
+    w = W.freestream_primitive(xyz.shape[0], xyz.shape[2], fs)
+    r2 = (xyz[:, 0] - 0.3) ** 2 + (xyz[:, 1] - 0.15) ** 2
+    w[:, 0] *= 1 + 2.0 * (r2 < 0.05)
+    w[:, 3] *= 1 + 4.0 * (r2 < 0.05)
+    return w
+
+
+@pytest.mark.parametrize("sf", [0, 1])
+def test_square_cylinder_blending_fp64(dg, sf):
+    p, fs = _cyl_pair(dg, dg.DG_FP64, sf=sf)
+    try:
+        r_g, r_o, u_o = _rhs_pair(dg, p, _blast(p.mesh_o, fs), _blast(p.mesh_g, fs))
+        _, a_o = p.orc.rhs(u_o, want_alpha=True)
+        a_g = dg.dg_get_alpha(p.gpu.ctx, p.K)
+        assert (a_o > 0).sum() > 3 and (a_o == 0).sum() > 3
+        assert np.allclose(a_g, a_o, rtol=1e-12, atol=1e-14)
+        err = cases.field_errors(r_g, r_o, 1, 2)
+        assert err.max() < FP64_TOL, err
+    finally:
+        p.close()
+
+
+def test_square_cylinder_blending_mixed(dg):
+    p, fs = _cyl_pair(dg, dg.DG_MIXED)
+    try:
+        r_g, r_o, u_o = _rhs_pair(dg, p, _blast(p.mesh_o, fs), _blast(p.mesh_g, fs))
+        _, a_o = p.orc.rhs(u_o, want_alpha=True)
+        a_g = dg.dg_get_alpha(p.gpu.ctx, p.K)
+        assert np.abs(a_g - a_o).max() < 1e-4
+        err = cases.field_errors(r_g, r_o, 1, 2)
+        assert err.max() < 2e-4, err
+    finally:
+        p.close()
+
+
+def test_ns_gradients_fp64(dg):
+    c = RHS_CASES["tgv_ns_warped_N3"]
+    p = cases.Pair(c["builder"], 3, 3, precision=dg.DG_FP64, **c["kw"])
+    try:
+        w_o = _perturbed(c, p.mesh_o, 3)
+        w_g = _perturbed(c, p.mesh_g, 3)
+        _rhs_pair(dg, p, w_o, w_g)
+        g_g = dg.dg_get_gradients(p.gpu.ctx, (p.K, 3, 4, 64))
+        _, g_o = p.orc.rhs(p.orc.prim_to_cons(w_o), want_grad=True)
+        err = np.linalg.norm(g_g - g_o) / np.linalg.norm(g_o)
+        assert err < FP64_TOL, err
+    finally:
+        p.close()
+
+
+@pytest.mark.parametrize("precision,tol", [(0, FP64_TOL), (1, 1e-5)])
+def test_rk_c1_ten_steps(dg, precision, tol):
+    """Config 1: 4^3 TGV Euler N=3, 10 CK45 steps at CFL 0.5 (device dt reduction)."""
+    p = cases.Pair(_tgv_builder(4, warp=0.0), 3, 3, precision=precision)
+    try:
+        u_o = p.orc.prim_to_cons(p.mesh_o[3])
+        p.gpu.set_primitive(p.mesh_g[3])
+        t_g = p.gpu.step(10, cfl=0.5)
+        u_g, _ = p.gpu.get_state()
+        u_r, t_o = p.orc.step_rk(u_o, 10, cfl=0.5)
+        assert abs(t_g - t_o) < (1e-14 if precision == 0 else 1e-6) * t_o
+        err = cases.field_errors(u_g, u_r, 1, 3)
+        assert err.max() < tol, err
+    finally:
+        p.close()
+
+
+@pytest.mark.parametrize("precision,tol", [(0, FP64_TOL), (1, 1e-5)])
+def test_rk_ns_warped(dg, precision, tol):
+    c = RHS_CASES["tgv_ns_warped_N3"]
+    p = cases.Pair(c["builder"], 3, 3, precision=precision, **c["kw"])
+    try:
+        u_o = p.orc.prim_to_cons(p.mesh_o[3])
+        p.gpu.set_primitive(p.mesh_g[3])
+        p.gpu.step(5, cfl=0.5)
+        u_g, _ = p.gpu.get_state()
+        u_r, _ = p.orc.step_rk(u_o, 5, cfl=0.5)
+        err = cases.field_errors(u_g, u_r, 1, 3)
+        assert err.max() < tol, err
+    finally:
+        p.close()
+
+
+def test_diagnostics(dg):
+    p = cases.Pair(_tgv_builder(shape=(3, 3, 5)), 3, 3, precision=0)
+    try:
+        u_o = p.orc.prim_to_cons(p.mesh_o[3])
+        p.gpu.set_primitive(p.mesh_g[3])
+        d_g = p.gpu.diagnostics()
+        d_o = p.orc.diagnostics(u_o)
+        assert np.allclose(d_g, d_o, rtol=1e-12, atol=1e-14), (d_g, d_o)
+    finally:
+        p.close()
+
+
+def test_checkpoint_restart_bitwise(dg):
+    p = cases.Pair(_tgv_builder(shape=(3, 3, 5)), 3, 3, precision=0, equations=1, mu=0.01)
+    try:
+        p.gpu.set_primitive(p.mesh_g[3])
+        p.gpu.step(6, cfl=0.5)
+        u_a, t_a = p.gpu.get_state()
+        p.gpu.set_primitive(p.mesh_g[3])
+        p.gpu.step(3, cfl=0.5)
+        u_mid, t_mid = p.gpu.get_state()
+        p.gpu.set_state(u_mid, t_mid)
+        p.gpu.step(3, cfl=0.5)
+        u_b, t_b = p.gpu.get_state()
+        assert np.array_equal(u_a, u_b)
+    finally:
+        p.close()
+
+
+def test_nonphysical_state_is_reported(dg):
+    p = cases.Pair(_tgv_builder(shape=(3, 3, 5)), 3, 3, precision=0)
+    try:
+        p.gpu.set_primitive(p.mesh_g[3])
+        u, _ = p.gpu.get_state()
+        u[17, 4, 5] = -1.0  # negative total energy -> negative pressure in element 17
+        p.gpu.set_state(u)
+        with pytest.raises(dg.DgError) as ei:
+            p.gpu.step(1, cfl=0.5)
+        assert ei.value.code == dg.DG_ENONPHYS
+        assert dg.dg_error_element(p.gpu.ctx) == 17
+    finally:
+        p.close()
+
+
+def test_invalid_arguments(dg):
+    import workloads as W
+    x, _ = dg.dg_lgl_nodes(3)
+    xyz, nbr, face = W.box_mesh((2, 2, 2), x, (0, 0, 0), (1, 1, 1))
+    with pytest.raises(dg.DgError) as ei:
+        dg.Solver(3, 5, xyz, nbr, face)  # degree not built
+    assert ei.value.code == dg.DG_EINVAL
+    bad = nbr.copy()
+    bad[0, 0] = 99
+    with pytest.raises(dg.DgError) as ei:
+        dg.Solver(3, 3, xyz, bad, face)
+    assert ei.value.code == dg.DG_EINVAL
+    with pytest.raises(dg.DgError) as ei:
+        dg.Solver(3, 3, xyz, nbr, face, n_species=5, species=np.zeros((5, 8)))  # Ranocha + mixture
+    assert ei.value.code == dg.DG_EINVAL
