@@ -31,6 +31,8 @@ CONFIGS = {
     "tgv_ns_32^3_N3": dict(n_el=32, N=3, warp=0.1, mu=1.0 / 1600.0),
     "tgv_ns_16^3_N7": dict(n_el=16, N=7, warp=0.1, mu=1.0 / 1600.0),
     "tgv_euler_4^3_N3": dict(n_el=4, N=3, warp=0.0, mu=0.0),
+    # profiling case for ncu section captures: same kernels, 245 MB working set (> L2)
+    "tgv_ns_24^3_N3": dict(n_el=24, N=3, warp=0.1, mu=1.0 / 1600.0),
 }
 # algorithmic HBM words per node of one RK-stage launch (unique bytes, neighbour traces
 # excluded): main kernel reads u, Ja, 1/J, gradW, du and writes du, u_new;
@@ -275,7 +277,7 @@ def run_reference(args, rank, world):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="tgv_ns_32^3_N3", choices=sorted(CONFIGS))
