@@ -160,6 +160,32 @@ const char* dg_status_string(dg_status s);
 
 void dg_destroy(dg_ctx* ctx);
 
+/* Allocation-free FP64 Navier-Stokes right-hand side.  The paper has no
+ * counterpart: it exists for callers that may not allocate device memory (a
+ * host framework that owns all device memory and passes a library only inputs
+ * and outputs, or a loop where cudaMalloc's implicit synchronisation and
+ * run-time failure are not acceptable), and so cannot create a context.
+ * Computes the same operator as dg_rhs for a 3D, single-gas, fully periodic
+ * Navier-Stokes problem.  Inputs and output are caller-owned device arrays:
+ *   nbr  int32 [K][6] neighbour element per face (faces -x,+x,-y,+y,-z,+z),
+ *   Ja   [K][3][3][np] metric terms Ja^i_n, invJ [K][np] = 1/J,
+ *   u    [K][5][np] conserved state, rhs [K][5][np] output (must not overlap u).
+ * Scratch (the BR1 gradients, K (N+1)^3 12 doubles, and a status word) lives in
+ * one static device array of DG_NOALLOC_SCRATCH_BYTES that every GPU loading
+ * the library holds until exit; larger problems return DG_EINVAL.  No device
+ * memory is allocated or freed.  The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress) and uploads the basis tables, so make
+ * that first call before any stream capture.  All calls share the one array:
+ * calls whose work overlaps on the GPU (other streams, other host threads)
+ * race on it; serialise them.  The status word is cleared at every call;
+ * device-side errors are latched there and not returned.  Queued on `stream`
+ * (cudaStream_t, NULL = legacy default); returns before the work finishes. */
+#define DG_NOALLOC_SCRATCH_BYTES (16u << 20)
+dg_status dg_rhs_ns_noalloc(int N, int64_t K, const int32_t* nbr, const double* Ja,
+                            const double* invJ, double gamma, double mu, double Pr,
+                            int volume_flux, int surface_flux, const double* u, double* rhs,
+                            void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -33,6 +33,7 @@ EXPORTED = [
     "dg_lgl_nodes", "dg_init_mesh", "dg_set_state", "dg_set_state_primitive", "dg_get_state",
     "dg_rhs", "dg_step_rk", "dg_diagnostics", "dg_get_alpha", "dg_get_gradients", "dg_sync",
     "dg_error_element", "dg_status_string", "dg_destroy", "dg_profile", "dg_profile_read",
+    "dg_rhs_ns_noalloc",
 ]
 PROF_KINDS = ["rhs", "gradients", "indicator", "lambda", "thermo", "mlp", "chem", "other"]
 
@@ -86,6 +87,7 @@ def lib():
             "dg_destroy": (None, [vp]),
             "dg_profile": (i, [vp, i]),
             "dg_profile_read": (i, [vp, vp, vp, i]),
+            "dg_rhs_ns_noalloc": (i, [i, i64, vp, vp, vp, d, d, d, i, i, vp, vp, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(_lib, name)
@@ -187,6 +189,15 @@ def dg_profile_read(ctx):
     cnt = np.zeros(n, dtype=np.int64)
     _check(lib().dg_profile_read(ctx, _ptr(ms), _ptr(cnt), n), "dg_profile_read")
     return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(PROF_KINDS)}
+
+
+def dg_rhs_ns_noalloc(N, K, nbr, Ja, invJ, gamma, mu, Pr, volume_flux, surface_flux, u, rhs,
+                      stream=None):
+    """Allocation-free Navier-Stokes right-hand side: every argument is a caller-owned
+    device tensor; the gradient scratch is libdg's static device array."""
+    _check(lib().dg_rhs_ns_noalloc(N, K, _ptr(nbr), _ptr(Ja), _ptr(invJ), gamma, mu, Pr,
+                                   volume_flux, surface_flux, _ptr(u), _ptr(rhs), stream),
+           "dg_rhs_ns_noalloc")
 
 
 def dg_destroy(ctx):
