@@ -75,6 +75,8 @@ def lib():
             "or_nv": (i, [i, i]),
             "or_flux_pair": (i, [vp, vp, vp, vp, i, vp]),
             "or_entropy_vars_u": (i, [vp, vp, vp]),
+            "or_mixture_eval": (i, [i, vp, i, vp, vp, vp, vp]),
+            "or_mixture_temperature": (i, [i, vp, i, vp, vp, vp, vp, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(_lib, name)
@@ -216,6 +218,30 @@ class Oracle:
         out = np.zeros(8)
         lib().or_diagnostics(self._ref(), _p(u), _p(out))
         return out
+
+
+def mixture_eval(species, Y, T):
+    """e(T) and cv(T) of mixtures with mass fractions Y [n][ns]."""
+    species = np.ascontiguousarray(species, dtype=np.float64)
+    Y = np.ascontiguousarray(Y, dtype=np.float64)
+    T = np.ascontiguousarray(T, dtype=np.float64)
+    e = np.zeros(len(T))
+    cv = np.zeros(len(T))
+    lib().or_mixture_eval(species.shape[0], _p(species), len(T), _p(Y), _p(T), _p(e), _p(cv))
+    return e, cv
+
+
+def mixture_temperature(species, Y, e, T0=None):
+    """Newton T(e) per state; returns (T, iterations, failed)."""
+    species = np.ascontiguousarray(species, dtype=np.float64)
+    Y = np.ascontiguousarray(Y, dtype=np.float64)
+    e = np.ascontiguousarray(e, dtype=np.float64)
+    T0 = None if T0 is None else np.ascontiguousarray(T0, dtype=np.float64)
+    T = np.zeros(len(e))
+    it = np.zeros(len(e), dtype=np.int32)
+    bad = lib().or_mixture_temperature(species.shape[0], _p(species), len(e), _p(Y), _p(e),
+                                       _p(T0), _p(T), _p(it))
+    return T, it, bool(bad)
 
 
 def ck45():

@@ -250,3 +250,22 @@ int or_entropy_vars_u(const or_problem* P, const double* u, double* wv) {
   or_entropy_vars(P, &q, wv);
   return 0;
 }
+
+/* vectorised helpers for the pin tests: e(T), cv(T), T(e) over n states */
+int or_mixture_eval(int ns, const double* species, int n, const double* Y, const double* T,
+                    double* e, double* cv) {
+  for (int i = 0; i < n; ++i) {
+    e[i] = or_mixture_energy(ns, species, Y + (size_t)i * ns, T[i]);
+    cv[i] = or_mixture_cv(ns, species, Y + (size_t)i * ns, T[i]);
+  }
+  return 0;
+}
+
+int or_mixture_temperature(int ns, const double* species, int n, const double* Y,
+                           const double* e, const double* T0, double* T, int* iters) {
+  int bad = 0;
+  for (int i = 0; i < n; ++i)
+    bad |= or_temperature(ns, species, Y + (size_t)i * ns, e[i], T0 ? T0[i] : 1000.0, T + i,
+                          iters ? iters + i : NULL);
+  return bad;
+}

@@ -97,6 +97,10 @@ double or_entropy(const or_problem* P, const or_prim* q);
 int or_flux_pair(const or_problem* P, const double* uL, const double* uR, const double* n,
                  int which, double* f);
 int or_entropy_vars_u(const or_problem* P, const double* u, double* wv);
+int or_mixture_eval(int ns, const double* species, int n, const double* Y, const double* T,
+                    double* e, double* cv);
+int or_mixture_temperature(int ns, const double* species, int n, const double* Y,
+                           const double* e, const double* T0, double* T, int* iters);
 
 /* ---- right-hand side, time stepping, diagnostics (or_rhs.c) ---- */
 int or_prim_to_cons_field(const or_problem* P, const double* w, double* u);

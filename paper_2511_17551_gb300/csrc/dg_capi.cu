@@ -366,6 +366,12 @@ cudaError_t run_lambda(dg_ctx* c, DgArgs& a, int slot) {
     return c->precision == DG_MIXED ? dg_f32_lambda(a, slot, c->stream) : dg_f64_lambda(a, slot, c->stream);
   });
 }
+cudaError_t run_step_dt(dg_ctx* c, DgArgs& a, int slot, int advance) {
+  return timed(c, DG_PROF_OTHER, [&] {
+    return c->precision == DG_MIXED ? dg_f32_step_dt(a, slot, advance, c->stream)
+                                    : dg_f64_step_dt(a, slot, advance, c->stream);
+  });
+}
 cudaError_t run_thermo(dg_ctx* c, const void* u) {
   return timed(c, DG_PROF_THERMO, [&] {
     return dg_thermo_update(&c->th, u, c->precision == DG_MIXED, c->stream);
@@ -753,14 +759,18 @@ dg_status dg_step_rk(dg_ctx* c, int nsteps, double cfl, double dt_fixed, double*
   cudaSetDevice(c->dev);
   double A[5], B[5];
   rk_ck45(A, B);
+  const bool cfl_mode = !(dt_fixed > 0.0);
   CK(cudaMemsetAsync(c->scal, 0, sizeof(double), c->stream));  // elapsed time
   DgArgs a = base_args(c);
-  if (!(dt_fixed > 0.0)) {
+  a.cfl = cfl;
+  a.dt_fixed = dt_fixed;
+  if (cfl_mode) {
     a.u = c->u[c->cur];
     if (c->n_species > 0) CK(run_thermo(c, a.u));
     CK(cudaMemsetAsync(c->lam + 2 * c->lam_slot, 0, 2 * sizeof(unsigned long long), c->stream));
     CK(run_lambda(c, a, c->lam_slot));
   }
+  CK(run_step_dt(c, a, c->lam_slot, 0));
   for (int step = 0; step < nsteps; ++step) {
     for (int s = 0; s < 5; ++s) {
       DgArgs b = base_args(c);
@@ -774,23 +784,23 @@ dg_status dg_step_rk(dg_ctx* c, int nsteps, double cfl, double dt_fixed, double*
       b.cfl = cfl;
       b.dt_fixed = dt_fixed;
       b.lam_cur = c->lam_slot;
-      b.want_lambda = (s == 4 && !(dt_fixed > 0.0) && c->n_species == 0) ? 1 : 0;
+      b.want_lambda = (s == 4 && cfl_mode && c->n_species == 0) ? 1 : 0;
       CK(pre_rhs(c, b));
       CK(run_rhs(c, b));
       c->cur ^= 1;
     }
-    if (!(dt_fixed > 0.0)) {
+    if (cfl_mode) {
       if (c->n_species > 0) {
         // mixtures: wave speeds need the new temperature field
         DgArgs l = base_args(c);
         l.u = c->u[c->cur];
         CK(run_thermo(c, l.u));
-        CK(cudaMemsetAsync(c->lam + 2 * (c->lam_slot ^ 1), 0, 2 * sizeof(unsigned long long),
-                           c->stream));
         CK(run_lambda(c, l, c->lam_slot ^ 1));
       }
       c->lam_slot ^= 1;
     }
+    // adds this step's dt to the elapsed time and sets the next step's dt
+    CK(run_step_dt(c, a, c->lam_slot, 1));
   }
   dg_status w = wait_stream(c);
   if (w != DG_OK) return w;

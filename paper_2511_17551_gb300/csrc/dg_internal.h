@@ -63,5 +63,7 @@ cudaError_t dg_f64_gradients(const DgArgs& a, cudaStream_t s);
 cudaError_t dg_f32_gradients(const DgArgs& a, cudaStream_t s);
 cudaError_t dg_f64_lambda(const DgArgs& a, int slot, cudaStream_t s);
 cudaError_t dg_f32_lambda(const DgArgs& a, int slot, cudaStream_t s);
+cudaError_t dg_f64_step_dt(const DgArgs& a, int slot, int advance_time, cudaStream_t s);
+cudaError_t dg_f32_step_dt(const DgArgs& a, int slot, int advance_time, cudaStream_t s);
 cudaError_t dg_f64_indicator(const DgArgs& a, double alpha_max, void* alpha_raw, cudaStream_t s);
 cudaError_t dg_f32_indicator(const DgArgs& a, double alpha_max, void* alpha_raw, cudaStream_t s);

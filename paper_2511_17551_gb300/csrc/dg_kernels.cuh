@@ -3,19 +3,19 @@
 // one translation unit per precision (dg_rhs_f64.cu, dg_rhs_f32.cu).
 //
 // Design (one CTA = EPB elements, all of its data staged in shared memory):
-//   phase A  coalesced copy of the elements' conserved state, metric terms and
-//            1/J into shared memory; per-node primitives (rho, v, p, rho/p)
-//            computed once; for Navier-Stokes, the viscous fluxes f^v_x per node.
-//   phase B  one thread per grid line (direction d, line m): every symmetric pair
+//   phase A  coalesced (16-byte) copy of the elements' conserved state, metric
+//            terms and 1/J into shared memory; per-node primitives (rho, v, p,
+//            rho/p) computed once; for Navier-Stokes, the viscous fluxes f^v_x.
+//   phase B1 one thread per grid line (direction d, line m): every symmetric pair
 //            (i < l) of the line is evaluated ONCE with the two-point flux and
-//            added to both end points with 2 D_il and 2 D_li held in registers
-//            (split form with zero diagonal, Eqs. fluxdiff / fluxdiffcons, so no
-//            self-flux is ever formed); the same thread owns the line's two face
-//            nodes and computes the interface fluxes there (Eqs. riemann_problem1-3)
-//            from the neighbour's trace, plus the subcell FV fluxes when the
-//            element is blended (Eq. fluxes_discrete_with_fv) and the BR1
-//            viscous divergence along the line (Eq. auxstrongf).  Accumulators
-//            live in registers; each line writes its N+1 node sums once.
+//            added to both end points with 2 D_il and 2 D_li in registers (split
+//            form with zero diagonal, Eqs. fluxdiff / fluxdiffcons, so no self-flux
+//            is ever formed), plus the subcell FV fluxes of blended elements
+//            (Eq. fluxes_discrete_with_fv) and the BR1 viscous volume term (Eq.
+//            auxstrongf); each line stores its N+1 node sums once.
+//   phase B2 one thread per face node: interface flux from the neighbour's trace
+//            (Eqs. riemann_problem1-3) or the boundary state, lifted onto the face
+//            node, plus the averaged viscous interface flux.
 //   phase C  one thread per node: sum the DIM line contributions in a fixed
 //            order, scale by -1/J, and either store du/dt or apply the
 //            2N-storage Runge-Kutta update (and the wave-speed maximum of the
@@ -37,7 +37,7 @@ struct BasisTab {
   real w[DG_MAXN + 1];
   real iw[DG_MAXN + 1];
   real Vinv[(DG_MAXN + 1) * (DG_MAXN + 1)];
-  real subw[DG_MAXN + 1];                   // w_m for subcell normal sums
+  real thr;                                 // indicator threshold 0.5 10^(-1.8 (N+1)^(1/4))
 };
 
 template <typename real> struct RealOps;
@@ -49,8 +49,10 @@ template <> struct RealOps<double> {
   static constexpr double ln_eps = 1e-4;
 };
 template <> struct RealOps<float> {
-  static __device__ __forceinline__ float rcp(float x) { return __frcp_rn(x); }
-  static __device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
+  // single MUFU reciprocal / reciprocal square root (<= 2 ulp): the mixed form's
+  // error budget (1e-5) is far above FP32 rounding
+  static __device__ __forceinline__ float rcp(float x) { return __fdividef(1.0f, x); }
+  static __device__ __forceinline__ float sqrt_(float x) { return x > 0.0f ? x * rsqrtf(x) : 0.0f; }
   static __device__ __forceinline__ float log_(float x) { return logf(x); }
   static __device__ __forceinline__ float div(float a, float b) { return __fdiv_rn(a, b); }
   // the artanh series truncated after f^6 has relative error f^8/9: 1.1e-9 at 1e-2

@@ -1,19 +1,40 @@
 // Kernels and launchers for one precision.  The including translation unit
-// defines DG_REAL (double or float) and DG_PREFIX (function-name prefix).
+// defines DG_REAL (double or float) and DG_PREFIX (namespace and function-name
+// prefix, e.g. dg_f32), so profiles name kernels dg_f32::rhs_kernel<...>.
 #pragma once
+#include <stdint.h>
 #include "dg_kernels.cuh"
 
-namespace {
+namespace DG_PREFIX {
 
 using real = DG_REAL;
 using namespace dgk;
 
 __constant__ BasisTab<real> c_tab[DG_MAXN + 1];
 
-// elements per CTA: about 128-256 line threads, bounded shared memory
+// Scalars of one launch in the form precision (no double arithmetic or double->float
+// conversion inside FP32 kernels).
+struct KConst {
+  real gamma, gm1, inv_gm1, mu, kap, visc, rkA, rkB;
+};
+
+inline KConst make_kconst(const DgArgs& a) {
+  KConst k;
+  k.gamma = (real)a.gamma;
+  k.gm1 = (real)(a.gamma - 1.0);
+  k.inv_gm1 = (real)(1.0 / (a.gamma - 1.0));
+  k.mu = (real)a.mu;
+  k.kap = (real)a.kappa_fac;
+  k.visc = (real)a.visc_coef;
+  k.rkA = (real)a.rkA;
+  k.rkB = (real)a.rkB;
+  return k;
+}
+
+// elements per CTA: the largest count whose line threads fit in 192 threads
 template <int DIM, int N>
 constexpr int epb() {
-  return Shape<DIM, N>::LINES >= 128 ? 1 : (256 / Shape<DIM, N>::LINES > 16 ? 16 : 256 / Shape<DIM, N>::LINES);
+  return Shape<DIM, N>::LINES >= 192 ? 1 : (192 / Shape<DIM, N>::LINES > 24 ? 24 : 192 / Shape<DIM, N>::LINES);
 }
 
 template <int DIM, int N, int NSP, bool NS>
@@ -24,6 +45,7 @@ struct Layout {
   static constexpr int EPB = epb<DIM, N>();
   static constexpr int NQ = DIM + 3;                // rho, v, p, beta(=rho/p)
   static constexpr int NFV = NS ? DIM * (DIM + 1) : 0;
+  static constexpr int FACE_NODES = 2 * DIM * S::LPD;  // per element
   // shared memory offsets (in reals) per CTA
   static constexpr int U = 0;
   static constexpr int Q = U + EPB * NV * NP;
@@ -34,12 +56,28 @@ struct Layout {
   static constexpr int PC = FV + EPB * NFV * NP;    // mixtures: p, c per node
   static constexpr int TOTAL = PC + (NSP > 1 ? EPB * 2 * NP : 0);
   static constexpr int THREADS = ((EPB * S::LINES + 31) / 32) * 32;
+  static constexpr size_t SMEM = sizeof(real) * TOTAL;
+  // CTAs per SM we ask the register allocator for (bounded by shared memory)
+  static constexpr int MINB_SMEM = (int)((227 * 1024) / (SMEM + 1024));
+  static constexpr int MINB = MINB_SMEM >= 4 ? 4 : (MINB_SMEM < 1 ? 1 : MINB_SMEM);
 };
+
+// cooperative copy global -> shared, 16-byte vectors when both sides allow it
+__device__ __forceinline__ void stage(real* dst, const real* src, int n, int tid, int nth) {
+  constexpr int V = 16 / sizeof(real);
+  if ((((uintptr_t)dst | (uintptr_t)src) & 15) == 0 && (n % V) == 0) {
+    const int4* s4 = reinterpret_cast<const int4*>(src);
+    int4* d4 = reinterpret_cast<int4*>(dst);
+    for (int i = tid; i < n / V; i += nth) d4[i] = s4[i];
+  } else {
+    for (int i = tid; i < n; i += nth) dst[i] = src[i];
+  }
+}
 
 // boundary / neighbour state at a face node.  Returns 1 when the face flux is the
 // physical flux of the returned state (supersonic inflow / outflow).
 template <int DIM, int NSP>
-__device__ __forceinline__ int outer_state(const DgArgs& a, int nb, int nnode,
+__device__ __forceinline__ int outer_state(const DgArgs& a, const KConst& kc, int nb, int nnode,
                                            const NodeState<real, DIM, NSP>& own, const real* n,
                                            NodeState<real, DIM, NSP>& x, bool& ok) {
   constexpr int NV = NSP + DIM + 1;
@@ -54,7 +92,7 @@ __device__ __forceinline__ int outer_state(const DgArgs& a, int nb, int nnode,
       pe = pc[((int64_t)nb * 2 + 0) * np + nnode];
       ce = pc[((int64_t)nb * 2 + 1) * np + nnode];
     }
-    ok = prim_from_cons<real, DIM, NSP>(x, real(a.gamma), pe, ce);
+    ok = prim_from_cons<real, DIM, NSP>(x, kc.gamma, pe, ce);
     return 0;
   }
   int bc = -(nb + 1);
@@ -68,7 +106,7 @@ __device__ __forceinline__ int outer_state(const DgArgs& a, int nb, int nnode,
       pe = ((const real*)a.bc_pc)[bc * 2 + 0];
       ce = ((const real*)a.bc_pc)[bc * 2 + 1];
     }
-    ok = prim_from_cons<real, DIM, NSP>(x, real(a.gamma), pe, ce);
+    ok = prim_from_cons<real, DIM, NSP>(x, kc.gamma, pe, ce);
     return 1;
   }
   x = own;
@@ -91,8 +129,8 @@ __device__ __forceinline__ int outer_state(const DgArgs& a, int nb, int nnode,
 
 // ------------------------------------------------------------------ main RHS / RK kernel
 template <int DIM, int N, int NSP, bool NS>
-__global__ void __launch_bounds__(Layout<DIM, N, NSP, NS>::THREADS)
-rhs_kernel(const DgArgs a) {
+__global__ void __launch_bounds__(Layout<DIM, N, NSP, NS>::THREADS, Layout<DIM, N, NSP, NS>::MINB)
+rhs_kernel(const DgArgs a, const KConst kc) {
   using S = Shape<DIM, N>;
   using L = Layout<DIM, N, NSP, NS>;
   constexpr int NV = L::NV, NP = L::NP, N1 = S::N1, EPB = L::EPB, NQ = L::NQ;
@@ -112,23 +150,13 @@ rhs_kernel(const DgArgs a) {
   const int tid = threadIdx.x, nth = blockDim.x;
   const int64_t e0 = (int64_t)blockIdx.x * EPB;
   const int ne = (int)((a.K - e0) < EPB ? (a.K - e0) : EPB);
-  const real gamma = real(a.gamma);
-  const real inv_gm1 = real(1) / (gamma - real(1));
   const BasisTab<real>& B = c_tab[N];
 
-  // ---- phase A: stage state, metrics, 1/J
-  {
-    const real* gu = (const real*)a.u + e0 * NV * NP;
-    for (int i = tid; i < ne * NV * NP; i += nth) su[i] = gu[i];
-    const real* gj = (const real*)a.Ja + e0 * DIM * DIM * NP;
-    for (int i = tid; i < ne * DIM * DIM * NP; i += nth) sja[i] = gj[i];
-    const real* gi = (const real*)a.invJ + e0 * NP;
-    for (int i = tid; i < ne * NP; i += nth) sij[i] = gi[i];
-    if (NSP > 1) {
-      const real* gp = (const real*)a.pc + e0 * 2 * NP;
-      for (int i = tid; i < ne * 2 * NP; i += nth) spc[i] = gp[i];
-    }
-  }
+  // ---- phase A: stage state, metric terms, 1/J
+  stage(su, (const real*)a.u + e0 * NV * NP, ne * NV * NP, tid, nth);
+  stage(sja, (const real*)a.Ja + e0 * DIM * DIM * NP, ne * DIM * DIM * NP, tid, nth);
+  stage(sij, (const real*)a.invJ + e0 * NP, ne * NP, tid, nth);
+  if (NSP > 1) stage(spc, (const real*)a.pc + e0 * 2 * NP, ne * 2 * NP, tid, nth);
   if (tid < EPB) {
     real al = 0;
     if (a.alpha_raw && tid < ne) {
@@ -144,20 +172,8 @@ rhs_kernel(const DgArgs a) {
     s_alpha[tid] = al;
   }
   if (tid == 0) {
-    double dt = a.dt_fixed;
-    if (a.mode == 1 && !(dt > 0.0)) {
-      double la = __longlong_as_double((long long)a.lam[2 * a.lam_cur + 0]);
-      double lv = __longlong_as_double((long long)a.lam[2 * a.lam_cur + 1]);
-      dt = a.cfl * 2.0 / ((N + 1) * la);
-      if (a.ns && lv > 0.0) dt = fmin(dt, a.cfl * 4.0 / ((N + 1.0) * (N + 1.0) * lv));
-    }
-    s_dt = (real)dt;
-    if (a.mode == 1 && blockIdx.x == 0 && a.stage == 0) {
-      a.scal[1] = dt;
-      a.lam[2 * (a.lam_cur ^ 1) + 0] = 0ull;
-      a.lam[2 * (a.lam_cur ^ 1) + 1] = 0ull;
-    }
-    if (a.mode == 1 && blockIdx.x == 0 && a.stage == 4) a.scal[0] += dt;
+    // the step's dt was reduced in FP64 by step_dt_kernel; the stage reads it
+    if (a.mode == 1) s_dt = (real)a.scal[1];
     s_lam[0] = s_lam[1] = 0ull;
   }
   __syncthreads();
@@ -177,7 +193,7 @@ rhs_kernel(const DgArgs a) {
       ke += uu[(NSP + d) * NP] * v;
     }
     real p;
-    if (NSP == 1) p = (gamma - real(1)) * (uu[(NSP + DIM) * NP] - real(0.5) * ke);
+    if (NSP == 1) p = kc.gm1 * (uu[(NSP + DIM) * NP] - real(0.5) * ke);
     else p = spc[e * 2 * NP + node];
     q[(1 + DIM) * NP] = p;
     q[(2 + DIM) * NP] = rho * RealOps<real>::rcp(p);
@@ -193,7 +209,7 @@ rhs_kernel(const DgArgs a) {
         for (int c = 0; c <= DIM; ++c) gg[x][c] = g[(x * (DIM + 1) + c) * NP];
 #pragma unroll
       for (int d = 0; d < DIM; ++d) vv[d] = q[(1 + d) * NP];
-      viscous_flux<real, DIM>(gg, vv, real(a.mu), real(a.kappa_fac), fv);
+      viscous_flux<real, DIM>(gg, vv, kc.mu, kc.kap, fv);
       real* so = sfv + e * L::NFV * NP + node;
 #pragma unroll
       for (int x = 0; x < DIM; ++x)
@@ -203,12 +219,11 @@ rhs_kernel(const DgArgs a) {
   }
   __syncthreads();
 
-  // ---- phase B: one thread per line
+  // ---- phase B1: one thread per line: volume terms
   for (int t = tid; t < ne * S::LINES; t += nth) {
     const int e = t / S::LINES, r = t % S::LINES;
     const int d = r / S::LPD, m = r % S::LPD;
     const int s = S::stride(d), base = S::line_base(d, m);
-    const int64_t eg = e0 + e;
     const real* q = sq + e * NQ * NP;
     const real* ja = sja + (e * DIM + d) * DIM * NP;  // Ja^d components at [c][node]
     const real* ue = su + e * NV * NP;
@@ -220,7 +235,7 @@ rhs_kernel(const DgArgs a) {
     const real al = s_alpha[e];
     const real wdg = real(1) - al;
 
-    // volume: every symmetric pair once (split form, diagonal-free)
+    // flux differencing: every symmetric pair once (split form, zero diagonal)
 #pragma unroll
     for (int i = 0; i < N1; ++i) {
       const int ni = base + i * s;
@@ -246,7 +261,7 @@ rhs_kernel(const DgArgs a) {
         }
         volume_flux<real, DIM, NSP>(a.vf, q[ni], vi, q[(1 + DIM) * NP + ni], q[(2 + DIM) * NP + ni], ui,
                                     q[nl], vl, q[(1 + DIM) * NP + nl], q[(2 + DIM) * NP + nl], ul,
-                                    nrm, inv_gm1, F);
+                                    nrm, kc.inv_gm1, F);
         const real cil = wdg * B.D2[i * N1 + l], cli = wdg * B.D2[l * N1 + i];
 #pragma unroll
         for (int k = 0; k < NV; ++k) {
@@ -254,41 +269,6 @@ rhs_kernel(const DgArgs a) {
           acc[l][k] += cli * F[k];
         }
       }
-    }
-
-    // the two face nodes of the line
-    NodeState<real, DIM, NSP> own[2];
-    real Fs[2][NV];
-    real nface[2][DIM];
-#pragma unroll
-    for (int side = 0; side < 2; ++side) {
-      const int f = 2 * d + side;
-      const int node = base + (side ? N : 0) * s;
-      const int nnode = base + (side ? 0 : N) * s;
-      NodeState<real, DIM, NSP>& o = own[side];
-#pragma unroll
-      for (int k = 0; k < NV; ++k) o.u[k] = ue[k * NP + node];
-      o.rho = q[node];
-#pragma unroll
-      for (int c = 0; c < DIM; ++c) o.v[c] = q[(1 + c) * NP + node];
-      o.p = q[(1 + DIM) * NP + node];
-      o.c = NSP == 1 ? RealOps<real>::sqrt_(gamma * o.p * RealOps<real>::rcp(o.rho))
-                     : spc[(e * 2 + 1) * NP + node];
-#pragma unroll
-      for (int c = 0; c < DIM; ++c) nface[side][c] = ja[c * NP + node];
-      const int nb = a.nbr[eg * 2 * DIM + f];
-      NodeState<real, DIM, NSP> x;
-      bool ok = true;
-      int phys = outer_state<DIM, NSP>(a, nb, nnode, o, nface[side], x, ok);
-      if (!ok) latch_status(a.status, DG_ST_NONPHYS, nb >= 0 ? nb : eg);
-      if (phys) phys_flux<real, DIM, NSP>(x, nface[side], Fs[side]);
-      else if (side) surface_flux<real, DIM, NSP>(a.sf, o, x, nface[side], inv_gm1, Fs[side]);
-      else surface_flux<real, DIM, NSP>(a.sf, x, o, nface[side], inv_gm1, Fs[side]);
-    }
-#pragma unroll
-    for (int k = 0; k < NV; ++k) {
-      acc[0][k] -= B.iw[0] * Fs[0][k];
-      acc[N][k] += B.iw[N] * Fs[1][k];
     }
 
     // subcell finite-volume part of blended elements
@@ -322,14 +302,14 @@ rhs_kernel(const DgArgs a) {
         Lq.p = q[(1 + DIM) * NP + nl];
         Rq.p = q[(1 + DIM) * NP + nr];
         if (NSP == 1) {
-          Lq.c = RealOps<real>::sqrt_(gamma * Lq.p * RealOps<real>::rcp(Lq.rho));
-          Rq.c = RealOps<real>::sqrt_(gamma * Rq.p * RealOps<real>::rcp(Rq.rho));
+          Lq.c = RealOps<real>::sqrt_(kc.gamma * Lq.p * RealOps<real>::rcp(Lq.rho));
+          Rq.c = RealOps<real>::sqrt_(kc.gamma * Rq.p * RealOps<real>::rcp(Rq.rho));
         } else {
           Lq.c = spc[(e * 2 + 1) * NP + nl];
           Rq.c = spc[(e * 2 + 1) * NP + nr];
         }
         real F[NV];
-        surface_flux<real, DIM, NSP>(a.sf == DG_SF_EC ? DG_SF_LLF : a.sf, Lq, Rq, nh, inv_gm1, F);
+        surface_flux<real, DIM, NSP>(a.sf == DG_SF_EC ? DG_SF_LLF : a.sf, Lq, Rq, nh, kc.inv_gm1, F);
 #pragma unroll
         for (int k = 0; k < NV; ++k) {
           acc[j - 1][k] += al * B.iw[j - 1] * F[k];
@@ -339,9 +319,9 @@ rhs_kernel(const DgArgs a) {
     }
 
     if (NS) {
-      // viscous divergence along the line: D Fv + M^{-1} B (Fv* - Fv); enters with + sign
-      real Fv[N1][DIM + 1];
+      // viscous volume term along the line: D Fv (enters the RHS with + sign)
       const real* fvb = sfv + e * L::NFV * NP;
+      real Fv[N1][DIM + 1];
 #pragma unroll
       for (int i = 0; i < N1; ++i) {
         const int ni = base + i * s;
@@ -362,38 +342,6 @@ rhs_kernel(const DgArgs a) {
           for (int l = 0; l < N1; ++l) dsum += B.D[i * N1 + l] * Fv[l][c];
           acc[i][NSP + c] -= dsum;
         }
-#pragma unroll
-      for (int side = 0; side < 2; ++side) {
-        const int f = 2 * d + side;
-        const int node = base + (side ? N : 0) * s;
-        const int nnode = base + (side ? 0 : N) * s;
-        const int nb = a.nbr[eg * 2 * DIM + f];  // periodic / interior only
-        const real* gn = (const real*)a.gradW + (int64_t)nb * DIM * (DIM + 1) * NP + nnode;
-        const real* un = (const real*)a.u + (int64_t)nb * NV * NP + nnode;
-        real gg[DIM][DIM + 1], vn[DIM], fvn[DIM][DIM + 1];
-#pragma unroll
-        for (int x = 0; x < DIM; ++x)
-#pragma unroll
-          for (int c = 0; c <= DIM; ++c) gg[x][c] = gn[(x * (DIM + 1) + c) * NP];
-        real rn = 0;
-#pragma unroll
-        for (int k = 0; k < NSP; ++k) rn += un[k * NP];
-        real irn = RealOps<real>::rcp(rn);
-#pragma unroll
-        for (int c = 0; c < DIM; ++c) vn[c] = un[(NSP + c) * NP] * irn;
-        viscous_flux<real, DIM>(gg, vn, real(a.mu), real(a.kappa_fac), fvn);
-        const int i = side ? N : 0;
-#pragma unroll
-        for (int c = 0; c <= DIM; ++c) {
-          real Fs_c = 0;
-#pragma unroll
-          for (int x = 0; x < DIM; ++x)
-            Fs_c += real(0.5) * (fvb[(x * (DIM + 1) + c) * NP + node] + fvn[x][c]) * nface[side][x];
-          real jump = Fs_c - Fv[i][c];
-          if (side) acc[N][NSP + c] -= B.iw[N] * jump;
-          else acc[0][NSP + c] += B.iw[0] * jump;
-        }
-      }
     }
 
     real* sa = sacc + (e * DIM + d) * NV * NP;
@@ -401,6 +349,68 @@ rhs_kernel(const DgArgs a) {
     for (int i = 0; i < N1; ++i)
 #pragma unroll
       for (int k = 0; k < NV; ++k) sa[k * NP + base + i * s] = acc[i][k];
+  }
+  __syncthreads();
+
+  // ---- phase B2: one thread per face node: interface fluxes and lifting
+  for (int t = tid; t < ne * L::FACE_NODES; t += nth) {
+    const int e = t / L::FACE_NODES, r = t % L::FACE_NODES;
+    const int f = r / S::LPD, m = r % S::LPD;
+    const int d = f >> 1, side = f & 1;
+    const int s = S::stride(d), base = S::line_base(d, m);
+    const int node = base + (side ? N : 0) * s;
+    const int nnode = base + (side ? 0 : N) * s;
+    const int64_t eg = e0 + e;
+    const real* q = sq + e * NQ * NP;
+    const real* ja = sja + (e * DIM + d) * DIM * NP;
+    const real* ue = su + e * NV * NP;
+    real* sa = sacc + (e * DIM + d) * NV * NP + node;
+    const real iw = side ? B.iw[N] : -B.iw[0];
+    NodeState<real, DIM, NSP> o;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) o.u[k] = ue[k * NP + node];
+    o.rho = q[node];
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) o.v[c] = q[(1 + c) * NP + node];
+    o.p = q[(1 + DIM) * NP + node];
+    o.c = NSP == 1 ? RealOps<real>::sqrt_(kc.gamma * o.p * RealOps<real>::rcp(o.rho))
+                   : spc[(e * 2 + 1) * NP + node];
+    real nface[DIM];
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) nface[c] = ja[c * NP + node];
+    const int nb = a.nbr[eg * 2 * DIM + f];
+    NodeState<real, DIM, NSP> x;
+    bool ok = true;
+    real Fs[NV];
+    int phys = outer_state<DIM, NSP>(a, kc, nb, nnode, o, nface, x, ok);
+    if (!ok) latch_status(a.status, DG_ST_NONPHYS, nb >= 0 ? nb : eg);
+    if (phys) phys_flux<real, DIM, NSP>(x, nface, Fs);
+    else if (side) surface_flux<real, DIM, NSP>(a.sf, o, x, nface, kc.inv_gm1, Fs);
+    else surface_flux<real, DIM, NSP>(a.sf, x, o, nface, kc.inv_gm1, Fs);
+#pragma unroll
+    for (int k = 0; k < NV; ++k) sa[k * NP] += iw * Fs[k];
+    if (NS) {
+      // viscous interface flux: mean of both sides' f^v . n, lifted as (Fv* - Fv)
+      const real* fvb = sfv + e * L::NFV * NP + node;
+      const real* gn = (const real*)a.gradW + (int64_t)nb * DIM * (DIM + 1) * NP + nnode;
+      real gg[DIM][DIM + 1], fvn[DIM][DIM + 1];
+#pragma unroll
+      for (int xx = 0; xx < DIM; ++xx)
+#pragma unroll
+        for (int c = 0; c <= DIM; ++c) gg[xx][c] = gn[(xx * (DIM + 1) + c) * NP];
+      viscous_flux<real, DIM>(gg, x.v, kc.mu, kc.kap, fvn);
+#pragma unroll
+      for (int c = 0; c <= DIM; ++c) {
+        real own_n = 0, mean_n = 0;
+#pragma unroll
+        for (int xx = 0; xx < DIM; ++xx) {
+          const real fo = fvb[(xx * (DIM + 1) + c) * NP];
+          own_n += fo * nface[xx];
+          mean_n += real(0.5) * (fo + fvn[xx][c]) * nface[xx];
+        }
+        sa[(NSP + c) * NP] -= iw * (mean_n - own_n);
+      }
+    }
   }
   __syncthreads();
 
@@ -423,7 +433,7 @@ rhs_kernel(const DgArgs a) {
     } else {
       real* out = (real*)a.out;
       real* du = (real*)a.du;
-      const real A = real(a.rkA), Bc = real(a.rkB), dt = s_dt;
+      const real dt = s_dt;
       real un[NV];
 #pragma unroll
       for (int k = 0; k < NV; ++k) {
@@ -431,9 +441,9 @@ rhs_kernel(const DgArgs a) {
 #pragma unroll
         for (int d = 0; d < DIM; ++d) sum += sa[(d * NV + k) * NP];
         const real r = -ij * sum;
-        real dn = (a.stage == 0 ? real(0) : A * du[gbase + k * NP]) + dt * r;
+        real dn = (a.stage == 0 ? real(0) : kc.rkA * du[gbase + k * NP]) + dt * r;
         du[gbase + k * NP] = dn;
-        un[k] = su[(e * NV + k) * NP + node] + Bc * dn;
+        un[k] = su[(e * NV + k) * NP + node] + kc.rkB * dn;
         out[gbase + k * NP] = un[k];
       }
       if (a.want_lambda && NSP == 1) {
@@ -446,8 +456,8 @@ rhs_kernel(const DgArgs a) {
           v[dd] = un[NSP + dd] * ir;
           ke += un[NSP + dd] * v[dd];
         }
-        real p = (gamma - real(1)) * (un[NSP + DIM] - real(0.5) * ke);
-        real c = RealOps<real>::sqrt_(gamma * p * ir);
+        real p = kc.gm1 * (un[NSP + DIM] - real(0.5) * ke);
+        real c = RealOps<real>::sqrt_(kc.gamma * p * ir);
         real la = 0, lv = 0;
 #pragma unroll
         for (int dd = 0; dd < DIM; ++dd) {
@@ -462,7 +472,7 @@ rhs_kernel(const DgArgs a) {
           lv += nn;
         }
         la *= ij;
-        lv *= ij * ij * real(a.visc_coef) * ir;
+        lv *= ij * ij * kc.visc * ir;
         if (!(p > real(0)) || !isfinite(la)) {
           latch_status(a.status, DG_ST_NONPHYS, e0 + e);
           la = real(0);
@@ -483,6 +493,25 @@ rhs_kernel(const DgArgs a) {
   }
 }
 
+// ------------------------------------------------------------------ time step (FP64)
+// One thread: dt = cfl 2/((N+1) max lambda) (and the viscous bound) from the wave-speed
+// maxima in slot `slot`, or dt_fixed; adds the previous step's dt to the elapsed time
+// and clears the other slot for the coming step's reduction.
+__global__ void step_dt_kernel(const DgArgs a, int slot, int advance_time) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  if (advance_time) a.scal[0] += a.scal[1];
+  double dt = a.dt_fixed;
+  if (!(dt > 0.0)) {
+    const double la = __longlong_as_double((long long)a.lam[2 * slot + 0]);
+    const double lv = __longlong_as_double((long long)a.lam[2 * slot + 1]);
+    dt = a.cfl * 2.0 / ((a.N + 1) * la);
+    if (a.ns && lv > 0.0) dt = fmin(dt, a.cfl * 4.0 / ((a.N + 1.0) * (a.N + 1.0) * lv));
+  }
+  a.scal[1] = dt;
+  a.lam[2 * (slot ^ 1) + 0] = 0ull;
+  a.lam[2 * (slot ^ 1) + 1] = 0ull;
+}
+
 // ------------------------------------------------------------------ BR1 gradients
 template <int DIM, int N, int NSP>
 struct GLayout {
@@ -501,10 +530,10 @@ struct GLayout {
 
 template <int DIM, int N, int NSP>
 __global__ void __launch_bounds__(GLayout<DIM, N, NSP>::THREADS)
-gradient_kernel(const DgArgs a) {
+gradient_kernel(const DgArgs a, const KConst kc) {
   using S = Shape<DIM, N>;
   using L = GLayout<DIM, N, NSP>;
-  constexpr int NV = L::NV, NP = L::NP, N1 = S::N1, EPB = L::EPB, NW = L::NW;
+  constexpr int NV = L::NV, NP = L::NP, N1 = S::N1, NW = L::NW;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   real* sm = reinterpret_cast<real*>(smem_raw);
   real* sw = sm + L::W;
@@ -512,17 +541,12 @@ gradient_kernel(const DgArgs a) {
   real* sij = sm + L::IJ;
   real* sg = sm + L::G;
   const int tid = threadIdx.x, nth = blockDim.x;
-  const int64_t e0 = (int64_t)blockIdx.x * EPB;
-  const int ne = (int)((a.K - e0) < EPB ? (a.K - e0) : EPB);
-  const real gamma = real(a.gamma);
+  const int64_t e0 = (int64_t)blockIdx.x * L::EPB;
+  const int ne = (int)((a.K - e0) < L::EPB ? (a.K - e0) : L::EPB);
   const BasisTab<real>& B = c_tab[N];
   const real* gu = (const real*)a.u;
-  {
-    const real* gj = (const real*)a.Ja + e0 * DIM * DIM * NP;
-    for (int i = tid; i < ne * DIM * DIM * NP; i += nth) sja[i] = gj[i];
-    const real* gi = (const real*)a.invJ + e0 * NP;
-    for (int i = tid; i < ne * NP; i += nth) sij[i] = gi[i];
-  }
+  stage(sja, (const real*)a.Ja + e0 * DIM * DIM * NP, ne * DIM * DIM * NP, tid, nth);
+  stage(sij, (const real*)a.invJ + e0 * NP, ne * NP, tid, nth);
   for (int i = tid; i < ne * NP; i += nth) {
     const int e = i / NP, node = i % NP;
     const real* uu = gu + (e0 + e) * NV * NP + node;
@@ -536,7 +560,7 @@ gradient_kernel(const DgArgs a) {
       sw[(e * NW + d) * NP + node] = v;
       ke += uu[(NSP + d) * NP] * v;
     }
-    real p = (gamma - real(1)) * (uu[(NSP + DIM) * NP] - real(0.5) * ke);
+    real p = kc.gm1 * (uu[(NSP + DIM) * NP] - real(0.5) * ke);
     sw[(e * NW + DIM) * NP + node] = p * ir;
   }
   __syncthreads();
@@ -576,7 +600,7 @@ gradient_kernel(const DgArgs a) {
         Wn[c] = un[(NSP + c) * NP] * irn;
         ke += un[(NSP + c) * NP] * Wn[c];
       }
-      Wn[DIM] = (gamma - real(1)) * (un[(NSP + DIM) * NP] - real(0.5) * ke) * irn;
+      Wn[DIM] = kc.gm1 * (un[(NSP + DIM) * NP] - real(0.5) * ke) * irn;
       const int i = side ? N : 0;
 #pragma unroll
       for (int c = 0; c < NW; ++c) {
@@ -611,7 +635,7 @@ gradient_kernel(const DgArgs a) {
 
 // ------------------------------------------------------------------ wave speeds (dt)
 template <int DIM, int NSP>
-__global__ void lambda_kernel(const DgArgs a, int slot) {
+__global__ void lambda_kernel(const DgArgs a, const KConst kc, int slot) {
   __shared__ unsigned long long s_l[2];
   constexpr int NV = NSP + DIM + 1;
   const int np = a.np;
@@ -633,8 +657,8 @@ __global__ void lambda_kernel(const DgArgs a, int slot) {
     }
     real c;
     if (NSP == 1) {
-      real p = (real(a.gamma) - real(1)) * (uu[(NSP + DIM) * np] - real(0.5) * ke);
-      c = RealOps<real>::sqrt_(real(a.gamma) * p * ir);
+      real p = kc.gm1 * (uu[(NSP + DIM) * np] - real(0.5) * ke);
+      c = RealOps<real>::sqrt_(kc.gamma * p * ir);
     } else {
       c = ((const real*)a.pc)[(e * 2 + 1) * np + node];
     }
@@ -651,7 +675,7 @@ __global__ void lambda_kernel(const DgArgs a, int slot) {
       lv += nn;
     }
     la *= ij;
-    lv *= ij * ij * real(a.visc_coef) * ir;
+    lv *= ij * ij * kc.visc * ir;
     if (!isfinite(la)) la = real(0);
     la_m = fmax(la_m, la);
     lv_m = fmax(lv_m, lv);
@@ -668,7 +692,7 @@ __global__ void lambda_kernel(const DgArgs a, int slot) {
 // ------------------------------------------------------------------ shock indicator
 // Hennemann-Gassner modal energy of rho*p, one thread per element.
 template <int DIM, int N, int NSP>
-__global__ void indicator_kernel(const DgArgs a, real alpha_max, real* alpha_raw) {
+__global__ void indicator_kernel(const DgArgs a, const KConst kc, real alpha_max, real* alpha_raw) {
   using S = Shape<DIM, N>;
   constexpr int NP = S::NP, N1 = S::N1, NV = NSP + DIM + 1;
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -686,7 +710,7 @@ __global__ void indicator_kernel(const DgArgs a, real alpha_max, real* alpha_raw
       real ke = 0;
 #pragma unroll
       for (int d = 0; d < DIM; ++d) ke += uu[(NSP + d) * NP + node] * uu[(NSP + d) * NP + node];
-      p = (real(a.gamma) - real(1)) * (uu[(NSP + DIM) * NP + node] - real(0.5) * ke * RealOps<real>::rcp(rho));
+      p = kc.gm1 * (uu[(NSP + DIM) * NP + node] - real(0.5) * ke * RealOps<real>::rcp(rho));
     } else {
       p = ((const real*)a.pc)[(e * 2) * NP + node];
     }
@@ -722,7 +746,7 @@ __global__ void indicator_kernel(const DgArgs a, real alpha_max, real* alpha_raw
   real fr1 = Et > real(0) ? (Et - E1) / Et : real(0);
   real fr2 = E1 > real(0) ? (E1 - E2) / E1 : real(0);
   real E = fmax(fr1, fr2);
-  const real thr = real(0.5 * pow(10.0, -1.8 * pow(N + 1.0, 0.25)));
+  const real thr = B.thr;
   const real sp = real(9.21024036697585);  // ln((1 - 1e-4) / 1e-4)
   real al = real(1) / (real(1) + exp(-(sp / thr) * (E - thr)));
   if (al < real(1e-3)) al = real(0);
@@ -730,21 +754,21 @@ __global__ void indicator_kernel(const DgArgs a, real alpha_max, real* alpha_raw
   alpha_raw[e] = al;
 }
 
+// opt in to more than the default 48 KB (dynamic + static) of shared memory
 template <typename KernelT>
 cudaError_t set_smem(KernelT k, size_t bytes) {
-  if (bytes <= 48 * 1024) return cudaSuccess;
+  if (bytes + 1024 <= 48 * 1024) return cudaSuccess;
   return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
 template <int DIM, int N, int NSP, bool NS>
 cudaError_t launch_rhs_t(const DgArgs& a, cudaStream_t st) {
   using L = Layout<DIM, N, NSP, NS>;
-  const size_t smem = sizeof(real) * L::TOTAL;
   auto k = rhs_kernel<DIM, N, NSP, NS>;
-  cudaError_t err = set_smem(k, smem);
+  cudaError_t err = set_smem(k, L::SMEM);
   if (err != cudaSuccess) return err;
   const int64_t grid = (a.K + L::EPB - 1) / L::EPB;
-  k<<<(unsigned)grid, L::THREADS, smem, st>>>(a);
+  k<<<(unsigned)grid, L::THREADS, L::SMEM, st>>>(a, make_kconst(a));
   return cudaGetLastError();
 }
 
@@ -756,7 +780,7 @@ cudaError_t launch_grad_t(const DgArgs& a, cudaStream_t st) {
   cudaError_t err = set_smem(k, smem);
   if (err != cudaSuccess) return err;
   const int64_t grid = (a.K + L::EPB - 1) / L::EPB;
-  k<<<(unsigned)grid, L::THREADS, smem, st>>>(a);
+  k<<<(unsigned)grid, L::THREADS, smem, st>>>(a, make_kconst(a));
   return cudaGetLastError();
 }
 
@@ -764,11 +788,11 @@ template <int DIM, int N, int NSP>
 cudaError_t launch_ind_t(const DgArgs& a, double amax, void* out, cudaStream_t st) {
   const int bs = 128;
   const int64_t grid = (a.K + bs - 1) / bs;
-  indicator_kernel<DIM, N, NSP><<<(unsigned)grid, bs, 0, st>>>(a, (real)amax, (real*)out);
+  indicator_kernel<DIM, N, NSP><<<(unsigned)grid, bs, 0, st>>>(a, make_kconst(a), (real)amax, (real*)out);
   return cudaGetLastError();
 }
 
-}  // namespace
+}  // namespace DG_PREFIX
 
 #define DG_CAT2(a, b) a##b
 #define DG_CAT(a, b) DG_CAT2(a, b)
@@ -789,9 +813,9 @@ cudaError_t launch_ind_t(const DgArgs& a, double amax, void* out, cudaStream_t s
     default: return cudaErrorInvalidValue;              \
   }
 
-#define DG_RHS_CALL(DIM, N, NSP, NS) launch_rhs_t<DIM, N, NSP, NS>(a, st)
-#define DG_GRAD_CALL(DIM, N, NSP, X) launch_grad_t<DIM, N, NSP>(a, st)
-#define DG_IND_CALL(DIM, N, NSP, X) launch_ind_t<DIM, N, NSP>(a, amax, out, st)
+#define DG_RHS_CALL(DIM, N, NSP, NS) DG_PREFIX::launch_rhs_t<DIM, N, NSP, NS>(a, st)
+#define DG_GRAD_CALL(DIM, N, NSP, X) DG_PREFIX::launch_grad_t<DIM, N, NSP>(a, st)
+#define DG_IND_CALL(DIM, N, NSP, X) DG_PREFIX::launch_ind_t<DIM, N, NSP>(a, amax, out, st)
 
 cudaError_t DG_CAT(DG_PREFIX, _rhs)(const DgArgs& a, cudaStream_t st) {
   if (a.dim == 3 && a.nsp == 1 && a.ns) { DG_DISPATCH_N(DG_RHS_CALL, 3, 1, true) }
@@ -818,15 +842,22 @@ cudaError_t DG_CAT(DG_PREFIX, _lambda)(const DgArgs& a, int slot, cudaStream_t s
   int64_t n = a.K * a.np;
   int64_t grid = (n + bs - 1) / bs;
   if (grid > 152 * 16) grid = 152 * 16;
-  if (a.dim == 3 && a.nsp == 1) lambda_kernel<3, 1><<<(unsigned)grid, bs, 0, st>>>(a, slot);
-  else if (a.dim == 2 && a.nsp == 1) lambda_kernel<2, 1><<<(unsigned)grid, bs, 0, st>>>(a, slot);
-  else if (a.dim == 3 && a.nsp == 5) lambda_kernel<3, 5><<<(unsigned)grid, bs, 0, st>>>(a, slot);
+  const DG_PREFIX::KConst kc = DG_PREFIX::make_kconst(a);
+  if (a.dim == 3 && a.nsp == 1) DG_PREFIX::lambda_kernel<3, 1><<<(unsigned)grid, bs, 0, st>>>(a, kc, slot);
+  else if (a.dim == 2 && a.nsp == 1) DG_PREFIX::lambda_kernel<2, 1><<<(unsigned)grid, bs, 0, st>>>(a, kc, slot);
+  else if (a.dim == 3 && a.nsp == 5) DG_PREFIX::lambda_kernel<3, 5><<<(unsigned)grid, bs, 0, st>>>(a, kc, slot);
   else return cudaErrorInvalidValue;
   return cudaGetLastError();
 }
 
+cudaError_t DG_CAT(DG_PREFIX, _step_dt)(const DgArgs& a, int slot, int advance_time, cudaStream_t st) {
+  DG_PREFIX::step_dt_kernel<<<1, 32, 0, st>>>(a, slot, advance_time);
+  return cudaGetLastError();
+}
+
 cudaError_t DG_CAT(DG_PREFIX, _upload_basis)() {
-  BasisTab<real> tab[DG_MAXN + 1];
+  using DG_PREFIX::real;
+  dgk::BasisTab<real> tab[DG_MAXN + 1];
   memset(tab, 0, sizeof(tab));
   for (int N = 1; N <= DG_MAXN; ++N) {
     DgHostBasis b;
@@ -835,13 +866,13 @@ cudaError_t DG_CAT(DG_PREFIX, _upload_basis)() {
     for (int i = 0; i < n1; ++i) {
       tab[N].w[i] = (real)b.w[i];
       tab[N].iw[i] = (real)(1.0 / b.w[i]);
-      tab[N].subw[i] = (real)b.w[i];
       for (int j = 0; j < n1; ++j) {
         tab[N].D[i * n1 + j] = (real)b.D[i * n1 + j];
         tab[N].D2[i * n1 + j] = i == j ? (real)0 : (real)(2.0 * b.D[i * n1 + j]);
         tab[N].Vinv[i * n1 + j] = (real)b.Vinv[i * n1 + j];
       }
     }
+    tab[N].thr = (real)(0.5 * pow(10.0, -1.8 * pow(N + 1.0, 0.25)));
   }
-  return cudaMemcpyToSymbol(c_tab, tab, sizeof(tab));
+  return cudaMemcpyToSymbol(DG_PREFIX::c_tab, tab, sizeof(tab));
 }
