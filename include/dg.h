@@ -129,6 +129,12 @@ dg_status dg_step_rk(dg_ctx* ctx, int nsteps, double cfl, double dt_fixed, doubl
  *            |Omega|, int (div v)^2 / |Omega|, 0 }. Synchronises. */
 dg_status dg_diagnostics(dg_ctx* ctx, double out[8]);
 
+/* Temperature of the current state of a mixture context (Eqs. total_energy,
+ * internal_energies, eos; T recovered from e per node), FP64 [K][np] host.
+ * Runs the temperature solve of the context's thermo mode on the current state.
+ * DG_EINVAL for a single-gas context. Synchronises. */
+dg_status dg_get_temperature(dg_ctx* ctx, double* T);
+
 /* Blending factors alpha [K] used by the last right-hand side (FP64, host). */
 dg_status dg_get_alpha(dg_ctx* ctx, double* alpha);
 

@@ -76,6 +76,7 @@ def lib():
             "or_flux_pair": (i, [vp, vp, vp, vp, i, vp]),
             "or_entropy_vars_u": (i, [vp, vp, vp]),
             "or_mixture_eval": (i, [i, vp, i, vp, vp, vp, vp]),
+            "or_temperature_field": (i, [vp, vp, vp]),
             "or_mixture_temperature": (i, [i, vp, i, vp, vp, vp, vp, vp]),
         }
         for name, (res, args) in sig.items():
@@ -212,6 +213,13 @@ class Oracle:
         if lib().or_entropy_vars_u(self._ref(), _p(u), _p(w)):
             raise ValueError("non-physical state")
         return w
+
+    def temperature(self, u):
+        u = np.ascontiguousarray(u, dtype=np.float64)
+        T = np.zeros((self.K, self.np))
+        if lib().or_temperature_field(self._ref(), _p(u), _p(T)):
+            raise ValueError("temperature solve failed")
+        return T
 
     def diagnostics(self, u):
         u = np.ascontiguousarray(u, dtype=np.float64)

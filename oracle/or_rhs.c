@@ -629,3 +629,19 @@ int or_diagnostics(const or_problem* P, const double* u, double* out) {
   out[5] = vol; out[6] = dil / vol; out[7] = 0.0;
   return err;
 }
+
+/* temperature of every node (mixtures: Newton from 1000 K; one gas: p / rho) */
+int or_temperature_field(const or_problem* P, const double* u, double* T) {
+  basis b;
+  make_basis(P, &b);
+  int err = 0;
+  for (int64_t k = 0; k < P->K; ++k)
+    for (int node = 0; node < b.np; ++node) {
+      double uu[OR_MAX_NV];
+      or_prim q;
+      node_u(&b, u, k, node, uu);
+      err |= or_cons_to_prim(P, uu, &q);
+      T[(size_t)k * b.np + node] = q.T;
+    }
+  return err;
+}

@@ -112,5 +112,6 @@ int or_step_rk(const or_problem* P, double* u, int nsteps, double cfl, double dt
                double* t);
 int or_diagnostics(const or_problem* P, const double* u, double* out);
 void or_ck45(double* A, double* B, double* c);
+int or_temperature_field(const or_problem* P, const double* u, double* T);
 
 #endif

@@ -33,7 +33,7 @@ EXPORTED = [
     "dg_lgl_nodes", "dg_init_mesh", "dg_set_state", "dg_set_state_primitive", "dg_get_state",
     "dg_rhs", "dg_step_rk", "dg_diagnostics", "dg_get_alpha", "dg_get_gradients", "dg_sync",
     "dg_error_element", "dg_status_string", "dg_destroy", "dg_profile", "dg_profile_read",
-    "dg_rhs_ns_noalloc",
+    "dg_rhs_ns_noalloc", "dg_get_temperature",
 ]
 PROF_KINDS = ["rhs", "gradients", "indicator", "lambda", "thermo", "mlp", "chem", "other"]
 
@@ -88,6 +88,7 @@ def lib():
             "dg_profile": (i, [vp, i]),
             "dg_profile_read": (i, [vp, vp, vp, i]),
             "dg_rhs_ns_noalloc": (i, [i, i64, vp, vp, vp, d, d, d, i, i, vp, vp, vp]),
+            "dg_get_temperature": (i, [vp, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(_lib, name)
@@ -156,6 +157,12 @@ def dg_diagnostics(ctx):
     out = np.zeros(8)
     _check(lib().dg_diagnostics(ctx, _ptr(out)), "dg_diagnostics")
     return out
+
+
+def dg_get_temperature(ctx, shape):
+    T = np.zeros(shape)
+    _check(lib().dg_get_temperature(ctx, _ptr(T)), "dg_get_temperature")
+    return T
 
 
 def dg_get_alpha(ctx, K):

@@ -483,7 +483,7 @@ dg_status dg_init_mesh(const dg_mesh_desc* m, const dg_physics_desc* p, dg_ctx**
   if (m->dim < 2 || m->dim > 3 || m->K < 1 || m->K >= (1ll << 31)) return DG_EINVAL;
   if (p->n_species < 0 || p->n_species > DG_MAX_SPECIES) return DG_EINVAL;
   if (!supported_degree(m->dim, m->N, p->n_species)) return DG_EINVAL;
-  if (p->n_species > 0 && (p->n_species != 5 || !p->species)) return DG_EINVAL;
+  if (p->n_species > 0 && (p->n_species != 5 || !p->species || p->n_bc > 64)) return DG_EINVAL;
   if (p->equations != DG_EULER && p->equations != DG_NAVIER_STOKES) return DG_EINVAL;
   if (p->equations == DG_NAVIER_STOKES && (p->n_species > 0 || m->dim != 3 || !(p->mu > 0) ||
                                            !(p->Pr > 0)))
@@ -832,6 +832,17 @@ dg_status dg_diagnostics(dg_ctx* c, double out[8]) {
   dg_status w = wait_stream(c);
   if (w != DG_OK) return w;
   return DG_OK;
+}
+
+dg_status dg_get_temperature(dg_ctx* c, double* T) {
+  if (!c || !T || c->n_species == 0) return DG_EINVAL;
+  if (!c->have_state) return DG_ESTATE;
+  cudaSetDevice(c->dev);
+  CK(run_thermo(c, c->u[c->cur]));
+  CK(cudaMemcpyAsync(T, c->th.T, sizeof(double) * c->K * c->np, cudaMemcpyDeviceToHost, c->stream));
+  dg_status w = wait_stream(c);
+  if (w != DG_OK) return w;
+  return take_status(c, NULL);
 }
 
 dg_status dg_get_alpha(dg_ctx* c, double* alpha) {

@@ -85,3 +85,31 @@ class Pair:
 
     def close(self):
         self.gpu.close()
+
+
+# ---------------------------------------------------------------- mixture workloads
+MIX_RHO, MIX_T = 0.1, 300.0
+MIX_U = 2000.0  # nominal Mach 5 for the seeded mixture at 300 K
+
+
+def mixture_ogrid(xi, nr=3, nth=4, nz=2, u_inf=MIX_U, seed=7, hot=None):
+    """Half O-grid around a cylinder (R = 0.5 m), inflow on the outer arc, outflow at the
+    ends, slip wall on the body, periodic span; seeded Dirichlet mass-fraction field."""
+    import workloads as W
+    xyz, nbr, face = W.ogrid_mesh(xi, nr, nth, nz)
+    w = W.mixture_primitive(xyz, rho=MIX_RHO, vel=(u_inf, 0.0, 0.0), T=MIX_T, seed=seed, hot=hot)
+    return xyz, nbr, face, w
+
+
+def mixture_bc(w):
+    fs = w[0, :, 0].copy()
+    return [1, 2, 3], np.stack([fs, fs, fs])
+
+
+def mixture_perturbed(w, seed):
+    rng = np.random.default_rng(seed)
+    w = w.copy()
+    w[:, :5] *= 1 + 0.05 * rng.uniform(-1, 1, size=w[:, :5].shape)
+    w[:, 5:8] += 100.0 * rng.normal(size=w[:, 5:8].shape)
+    w[:, 8] *= 1 + 0.3 * rng.uniform(-1, 1, size=w[:, 8].shape)
+    return w
