@@ -77,6 +77,12 @@ def lib():
             "or_entropy_vars_u": (i, [vp, vp, vp]),
             "or_mixture_eval": (i, [i, vp, i, vp, vp, vp, vp]),
             "or_temperature_field": (i, [vp, vp, vp]),
+            "or_mlp_nparams": (i, []),
+            "or_gelu": (d, [d]),
+            "or_gelu_d": (d, [d]),
+            "or_mlp_forward": (None, [vp, i, vp, vp]),
+            "or_mlp_loss_grad": (d, [vp, i, vp, vp, vp]),
+            "or_adam_step": (None, [vp, vp, vp, vp, i, i, d, d, d, d]),
             "or_mixture_temperature": (i, [i, vp, i, vp, vp, vp, vp, vp]),
         }
         for name, (res, args) in sig.items():
@@ -250,6 +256,41 @@ def mixture_temperature(species, Y, e, T0=None):
     bad = lib().or_mixture_temperature(species.shape[0], _p(species), len(e), _p(Y), _p(e),
                                        _p(T0), _p(T), _p(it))
     return T, it, bool(bad)
+
+
+def mlp_nparams():
+    return lib().or_mlp_nparams()
+
+
+def mlp_forward(params, X):
+    params = np.ascontiguousarray(params, dtype=np.float64)
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    y = np.zeros(X.shape[0])
+    lib().or_mlp_forward(_p(params), X.shape[0], _p(X), _p(y))
+    return y
+
+
+def mlp_loss_grad(params, X, t):
+    params = np.ascontiguousarray(params, dtype=np.float64)
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    t = np.ascontiguousarray(t, dtype=np.float64)
+    g = np.zeros_like(params)
+    loss = lib().or_mlp_loss_grad(_p(params), X.shape[0], _p(X), _p(t), _p(g))
+    return loss, g
+
+
+def adam_step(params, m, v, g, step, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
+    """In-place Adam update of float64 arrays."""
+    lib().or_adam_step(_p(params), _p(m), _p(v), _p(np.ascontiguousarray(g)), len(params), step,
+                       lr, b1, b2, eps)
+
+
+def gelu(x):
+    return lib().or_gelu(float(x))
+
+
+def gelu_d(x):
+    return lib().or_gelu_d(float(x))
 
 
 def ck45():

@@ -114,4 +114,13 @@ int or_diagnostics(const or_problem* P, const double* u, double* out);
 void or_ck45(double* A, double* B, double* c);
 int or_temperature_field(const or_problem* P, const double* u, double* T);
 
+/* ---- learned temperature surrogate (or_mlp.c) ---- */
+int or_mlp_nparams(void);
+double or_gelu(double x);
+double or_gelu_d(double x);
+void or_mlp_forward(const double* p, int n, const double* X, double* y);
+double or_mlp_loss_grad(const double* p, int n, const double* X, const double* t, double* g);
+void or_adam_step(double* p, double* m, double* v, const double* g, int np_, int step, double lr,
+                  double b1, double b2, double eps);
+
 #endif

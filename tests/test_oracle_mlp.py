@@ -1,0 +1,93 @@
+"""Pins of the oracle's learned-temperature perceptron (forward, back-propagation, Adam)."""
+import math
+
+import numpy as np
+
+
+def _params(orc, seed=0, scale=0.5):
+    rng = np.random.default_rng(seed)
+    return scale * rng.normal(size=orc.mlp_nparams())
+
+
+def test_layout_size(orc):
+    assert orc.mlp_nparams() == 64 * 7 + 64 + 64 * 64 + 64 + 64 + 1
+
+
+def test_gelu_identities(orc):
+    # gelu(x) - gelu(-x) = x for the tanh form; gelu(0) = 0; tanh form within 1e-3 of x Phi(x)
+    for x in np.linspace(-6, 6, 49):
+        assert abs(orc.gelu(x) - orc.gelu(-x) - x) < 1e-14 * max(1, abs(x))
+        exact = 0.5 * x * (1 + math.erf(x / math.sqrt(2)))
+        assert abs(orc.gelu(x) - exact) < 1e-3
+        h = 1e-6
+        fd = (orc.gelu(x + h) - orc.gelu(x - h)) / (2 * h)
+        assert abs(orc.gelu_d(x) - fd) < 1e-8
+    assert orc.gelu(0.0) == 0.0
+
+
+def test_forward_single_path_by_hand(orc):
+    """Only one path through the network carries weight: y = b3 + w3 gelu(W2 gelu(W1 x))."""
+    p = np.zeros(orc.mlp_nparams())
+    off_b1 = 64 * 7
+    off_w2 = off_b1 + 64
+    off_b2 = off_w2 + 64 * 64
+    off_w3 = off_b2 + 64
+    p[0 * 7 + 3] = 0.7          # W1[0][3]
+    p[off_b1 + 0] = -0.2
+    p[off_w2 + 5 * 64 + 0] = 1.3  # W2[5][0]
+    p[off_b2 + 5] = 0.1
+    p[off_w3 + 5] = -2.0
+    p[-1] = 0.25
+    x = np.array([[0.1, 0.2, 0.3, 0.4, 0.5, 0.6, 0.7]])
+    h1 = orc.gelu(0.7 * 0.4 - 0.2)
+    h2 = orc.gelu(1.3 * h1 + 0.1)
+    # every other hidden unit sees gelu(0) = 0 except through the biases (zero here)
+    assert abs(orc.mlp_forward(p, x)[0] - (0.25 - 2.0 * h2)) < 1e-15
+
+
+def test_gradient_matches_finite_differences(orc):
+    rng = np.random.default_rng(1)
+    p = _params(orc, 1, 0.3)
+    X = rng.normal(size=(5, 7))
+    t = rng.normal(size=5)
+    loss, g = orc.mlp_loss_grad(p, X, t)
+    idx = rng.choice(len(p), size=60, replace=False)
+    idx = np.concatenate([idx, [len(p) - 1, 64 * 7, 64 * 7 + 64 + 3]])
+    for i in idx:
+        h = 1e-5 * max(1.0, abs(p[i]))
+        pp, pm = p.copy(), p.copy()
+        pp[i] += h
+        pm[i] -= h
+        fd = (orc.mlp_loss_grad(pp, X, t)[0] - orc.mlp_loss_grad(pm, X, t)[0]) / (2 * h)
+        # central differences: truncation ~h^2, rounding ~eps*loss/h (~1e-10 absolute)
+        assert abs(fd - g[i]) < 1e-6 * abs(g[i]) + 2e-9, (i, fd, g[i])
+    y = orc.mlp_forward(p, X)
+    assert abs(loss - np.mean((y - t) ** 2)) < 1e-14 * max(1, loss)
+
+
+def test_adam_first_step_closed_form(orc):
+    """At step 1 the bias-corrected moments are g and g^2: dp = -lr g / (|g| + eps)."""
+    g = np.array([3.0, -1e-3, 0.0, 1e-9, -7.5])
+    p = np.zeros(5)
+    m = np.zeros(5)
+    v = np.zeros(5)
+    orc.adam_step(p, m, v, g, 1, lr=1e-3)
+    assert np.allclose(p, -1e-3 * g / (np.abs(g) + 1e-8), rtol=1e-14, atol=0)
+    # two steps with a constant gradient: still -lr g/(|g|+eps) per step
+    orc.adam_step(p, m, v, g, 2, lr=1e-3)
+    assert np.allclose(p, -2e-3 * g / (np.abs(g) + 1e-8), rtol=1e-12, atol=1e-20)
+
+
+def test_training_reduces_loss_on_a_smooth_map(orc):
+    """Full-batch Adam on a smooth 7-input target must reduce the loss tenfold."""
+    rng = np.random.default_rng(2)
+    X = rng.uniform(-1, 1, size=(256, 7))
+    t = np.sin(X[:, 0]) + 0.5 * X[:, 1] * X[:, 2] - 0.3 * X[:, 6]
+    p = _params(orc, 3, 0.2)
+    m = np.zeros_like(p)
+    v = np.zeros_like(p)
+    l0 = orc.mlp_loss_grad(p, X, t)[0]
+    for s in range(1, 301):
+        _, g = orc.mlp_loss_grad(p, X, t)
+        orc.adam_step(p, m, v, g, s, lr=3e-3)
+    assert orc.mlp_loss_grad(p, X, t)[0] < 0.1 * l0
