@@ -135,6 +135,47 @@ dg_status dg_diagnostics(dg_ctx* ctx, double out[8]);
  * DG_EINVAL for a single-gas context. Synchronises. */
 dg_status dg_get_temperature(dg_ctx* ctx, double* T);
 
+/* ---- learned temperature surrogate (no counterpart in the paper: the learned form of
+ * the per-node temperature solve of Eqs. total_energy / internal_energies / eos).
+ * Network 7 -> 64 -> 64 -> 1, GELU (tanh form); inputs standardised
+ * (Y_1..Y_5, ln rho, e), output standardised T.  Parameter vector (FP32, P =
+ * dg_mlp_nparams()): W1[64][7], b1[64], W2[64][64], b2[64], w3[64], b3.
+ * Normalisation stats (FP64, 16): mean[7], std[7], mean_T, std_T. */
+
+/* Load (params, stats: host arrays) into a mixture context and switch its temperature
+ * solve to BF16 tensor-core inference + one FP64 Newton polish + residual check
+ * (accept when the next Newton correction is <= 1e-7 T) with the plain Newton
+ * iteration as fallback.  params == NULL switches back to the plain Newton solve.
+ * which must be 0 (temperature surrogate). */
+dg_status dg_set_surrogate(dg_ctx* ctx, int which, const float* params, const double* stats);
+
+/* Nodes accepted after the polish and nodes sent to the fallback since the last call
+ * (host int64[2]); resets the counters. */
+dg_status dg_surrogate_stats(dg_ctx* ctx, int64_t* accepted_fallback);
+
+/* Training data from the plain solver: runs the temperature solve on the current state,
+ * then writes n samples drawn with splitmix64(seed + j) over all nodes:
+ * X [n][7] raw features (Y_1..Y_5, ln rho, e) and T [n] (device float arrays). */
+dg_status dg_thermo_sample(dg_ctx* ctx, int64_t n, uint64_t seed, float* X, float* T);
+
+int dg_mlp_nparams(void);
+/* Workspace bytes that dg_mlp_grad / dg_mlp_train_step need for a batch. */
+size_t dg_mlp_workspace_bytes(int batch);
+/* Gradient of loss = mean((y - t)^2) over a batch (FP32 back-propagation, fixed-order
+ * reduction): params [P], X [batch][7] standardised inputs, t [batch] standardised
+ * targets, grad [P] out, loss (device double*, may be NULL); all device pointers. */
+dg_status dg_mlp_grad(const float* params, const float* X, const float* t, int batch, float* grad,
+                      double* loss, float* workspace, size_t ws_bytes, void* stream);
+/* One Adam step (beta = 0.9, 0.999, eps = 1e-8, bias-corrected, step >= 1) on the same
+ * loss; params, m, v updated in place (device). */
+dg_status dg_mlp_train_step(float* params, float* m, float* v, const float* X, const float* t,
+                            int batch, int step, float lr, double* loss, float* workspace,
+                            size_t ws_bytes, void* stream);
+/* y[n] = network(X[n][7]) for standardised X (device); tensor_cores = 1 uses the BF16
+ * MMA path of the inference kernel, 0 the FP32 path.  stats may be NULL. */
+dg_status dg_mlp_forward(const float* params, const double* stats, const float* X, float* y,
+                         int64_t n, int tensor_cores, void* stream);
+
 /* Blending factors alpha [K] used by the last right-hand side (FP64, host). */
 dg_status dg_get_alpha(dg_ctx* ctx, double* alpha);
 

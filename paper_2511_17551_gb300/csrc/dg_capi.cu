@@ -845,6 +845,46 @@ dg_status dg_get_temperature(dg_ctx* c, double* T) {
   return take_status(c, NULL);
 }
 
+dg_status dg_set_surrogate(dg_ctx* c, int which, const float* params, const double* stats) {
+  if (!c || which != 0 || c->n_species == 0 || (params && !stats)) return DG_EINVAL;
+  cudaSetDevice(c->dev);
+  if (params)
+    for (int q = 0; q < 7; ++q)
+      if (!(stats[7 + q] > 0.0)) return DG_EINVAL;
+  CK(cudaStreamSynchronize(c->stream));
+  CK(dg_mlp_set(&c->th, params, stats));
+  c->th.mode = params ? DG_THERMO_MLP : DG_THERMO_NEWTON;
+  return DG_OK;
+}
+
+dg_status dg_surrogate_stats(dg_ctx* c, int64_t* out) {
+  if (!c || !out || c->n_species == 0) return DG_EINVAL;
+  if (!c->th.mlp_stats) {
+    out[0] = out[1] = 0;
+    return DG_OK;
+  }
+  cudaSetDevice(c->dev);
+  dg_status w = wait_stream(c);
+  if (w != DG_OK) return w;
+  unsigned long long h[2];
+  CK(cudaMemcpy(h, c->th.mlp_stats, sizeof(h), cudaMemcpyDeviceToHost));
+  CK(cudaMemset(c->th.mlp_stats, 0, sizeof(h)));
+  out[0] = (int64_t)h[0];
+  out[1] = (int64_t)h[1];
+  return DG_OK;
+}
+
+dg_status dg_thermo_sample(dg_ctx* c, int64_t n, uint64_t seed, float* X, float* T) {
+  if (!c || n < 1 || !X || !T || c->n_species == 0) return DG_EINVAL;
+  if (!c->have_state) return DG_ESTATE;
+  cudaSetDevice(c->dev);
+  CK(run_thermo(c, c->u[c->cur]));
+  CK(dg_mlp_sample(&c->th, c->u[c->cur], c->precision == DG_MIXED, n, seed, X, T, c->stream));
+  dg_status w = wait_stream(c);
+  if (w != DG_OK) return w;
+  return take_status(c, NULL);
+}
+
 dg_status dg_get_alpha(dg_ctx* c, double* alpha) {
   if (!c || !alpha) return DG_EINVAL;
   if (!c->have_alpha) return DG_ESTATE;

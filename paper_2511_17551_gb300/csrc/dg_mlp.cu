@@ -1,0 +1,619 @@
+// Learned temperature surrogate: training kernels (FP32) and BF16 tensor-core
+// inference fused with the per-node FP64 Newton polish and the Newton fallback.
+//
+// Network: x in R^7 -> 64 -> 64 -> 1 with the tanh form of GELU after the two hidden
+// layers; x = standardised (Y_1..Y_5, ln rho, e), output = standardised T.
+// Parameter vector (FP32 master copy): W1[64][7], b1[64], W2[64][64], b2[64], w3[64], b3.
+//
+// Inference (dg_thermo_update in surrogate mode): one warp evaluates 16 nodes with
+// mma.sync m16n8k16 (BF16 operands, FP32 accumulation): layer 1 is 8 MMAs against
+// W1 zero-padded to K = 16, layer 2 is 32 MMAs; the FP32 accumulator fragments of a
+// layer are exactly the A fragments of the next (two n-tiles of 8 = one k-block of 16),
+// so activations never leave registers.  Layer 3 is a 64-term dot product reduced
+// across the 4 lanes sharing a row.  Then, per node in FP64: one Newton step from the
+// prediction, accept when the next correction would be <= 1e-7 T, otherwise run the
+// plain Newton iteration (fallback, counted).
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include "../../include/dg.h"
+#include "dg_internal.h"
+#include "dg_thermo.h"
+
+#define NI 7
+#define NH 64
+#define OFF_W1 0
+#define OFF_B1 (OFF_W1 + NH * NI)
+#define OFF_W2 (OFF_B1 + NH)
+#define OFF_B2 (OFF_W2 + NH * NH)
+#define OFF_W3 (OFF_B2 + NH)
+#define OFF_B3 (OFF_W3 + NH)
+#define NPARAM (OFF_B3 + 1)
+#define DG_RU 8.314462618
+#define NSPEC 5
+
+struct __align__(16) DgMlpDev {
+  __nv_bfloat16 W1[NH * 16];  // [j][k], k >= 7 zero
+  __nv_bfloat16 W2[NH * NH];  // [j][i]
+  float b1[NH], b2[NH], w3[NH], b3;
+  float mean[NI], inv_std[NI];
+  float muT, sigT;
+};
+
+namespace {
+
+__device__ __forceinline__ float gelu_f(float x) {
+  const float k = 0.7978845608028654f;  // sqrt(2/pi)
+  return 0.5f * x * (1.0f + tanhf(k * (x + 0.044715f * x * x * x)));
+}
+__device__ __forceinline__ float gelu_d_f(float x) {
+  const float k = 0.7978845608028654f;
+  float t = tanhf(k * (x + 0.044715f * x * x * x));
+  return 0.5f * (1.0f + t) + 0.5f * x * (1.0f - t * t) * k * (1.0f + 3.0f * 0.044715f * x * x);
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+  __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<uint32_t*>(&v);
+}
+
+__device__ __forceinline__ void mma_bf16(float* d, const uint32_t* a, uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+      "{%8,%9}, {%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// 16 rows of standardised features in smem feat[16][16] (float) -> outputs y[16] (rows)
+// for the calling warp.  Every lane of the warp must call it.
+__device__ __forceinline__ void mlp16(const DgMlpDev& m, const float (*feat)[17], float* yrow) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  uint32_t A[4];
+  A[0] = pack_bf16(feat[g][2 * t], feat[g][2 * t + 1]);
+  A[1] = pack_bf16(feat[g + 8][2 * t], feat[g + 8][2 * t + 1]);
+  A[2] = pack_bf16(feat[g][2 * t + 8], feat[g][2 * t + 9]);
+  A[3] = pack_bf16(feat[g + 8][2 * t + 8], feat[g + 8][2 * t + 9]);
+  float h[8][4];
+#pragma unroll
+  for (int nt = 0; nt < 8; ++nt) {
+    const int col = 8 * nt + 2 * t;
+    h[nt][0] = h[nt][2] = m.b1[col];
+    h[nt][1] = h[nt][3] = m.b1[col + 1];
+    const uint32_t* w = reinterpret_cast<const uint32_t*>(m.W1 + (8 * nt + g) * 16);
+    mma_bf16(h[nt], A, w[t], w[t + 4]);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) h[nt][q] = gelu_f(h[nt][q]);
+  }
+  uint32_t A2[4][4];
+#pragma unroll
+  for (int kb = 0; kb < 4; ++kb) {
+    A2[kb][0] = pack_bf16(h[2 * kb][0], h[2 * kb][1]);
+    A2[kb][1] = pack_bf16(h[2 * kb][2], h[2 * kb][3]);
+    A2[kb][2] = pack_bf16(h[2 * kb + 1][0], h[2 * kb + 1][1]);
+    A2[kb][3] = pack_bf16(h[2 * kb + 1][2], h[2 * kb + 1][3]);
+  }
+  float yg = 0.f, yg8 = 0.f;
+#pragma unroll
+  for (int nt = 0; nt < 8; ++nt) {
+    const int col = 8 * nt + 2 * t;
+    float o[4] = {m.b2[col], m.b2[col + 1], m.b2[col], m.b2[col + 1]};
+#pragma unroll
+    for (int kb = 0; kb < 4; ++kb) {
+      const uint32_t* w = reinterpret_cast<const uint32_t*>(m.W2 + (8 * nt + g) * NH + 16 * kb);
+      mma_bf16(o, A2[kb], w[t], w[t + 4]);
+    }
+    yg += m.w3[col] * gelu_f(o[0]) + m.w3[col + 1] * gelu_f(o[1]);
+    yg8 += m.w3[col] * gelu_f(o[2]) + m.w3[col + 1] * gelu_f(o[3]);
+  }
+  yg += __shfl_xor_sync(0xffffffffu, yg, 1);
+  yg += __shfl_xor_sync(0xffffffffu, yg, 2);
+  yg8 += __shfl_xor_sync(0xffffffffu, yg8, 1);
+  yg8 += __shfl_xor_sync(0xffffffffu, yg8, 2);
+  if (t == 0) {
+    yrow[g] = yg + m.b3;
+    yrow[g + 8] = yg8 + m.b3;
+  }
+}
+
+struct PolyD {
+  double b[6], Rmix;
+  __device__ __forceinline__ double e(double T) const {
+    return b[0] + T * (b[1] + T * (b[2] + T * (b[3] + T * (b[4] + T * b[5]))));
+  }
+  __device__ __forceinline__ double cv(double T) const {
+    return b[1] + T * (2.0 * b[2] + T * (3.0 * b[3] + T * (4.0 * b[4] + T * (5.0 * b[5]))));
+  }
+};
+
+__device__ __forceinline__ void poly_d(const double* sp, const double* Y, PolyD& P) {
+  for (int k = 0; k < 6; ++k) P.b[k] = 0.0;
+  P.Rmix = 0.0;
+#pragma unroll
+  for (int s = 0; s < NSPEC; ++s) {
+    const double* a = sp + 8 * s + 1;
+    const double w = Y[s] * DG_RU / sp[8 * s];
+    P.b[0] += w * a[5];
+    P.b[1] += w * (a[0] - 1.0);
+    P.b[2] += w * a[1] * 0.5;
+    P.b[3] += w * a[2] / 3.0;
+    P.b[4] += w * a[3] * 0.25;
+    P.b[5] += w * a[4] * 0.2;
+    P.Rmix += w;
+  }
+}
+
+__device__ __forceinline__ double clampT(double T) { return T < 200.0 ? 200.0 : (T > 1e4 ? 1e4 : T); }
+
+#define MLP_WARPS 4
+
+template <typename T>
+__global__ void __launch_bounds__(32 * MLP_WARPS)
+thermo_mlp_kernel(const T* u, int64_t K, int np, int dim, const double* sp, double* Tc, T* pc,
+                  unsigned long long* status, const DgMlpDev* mlp, unsigned long long* stats) {
+  __shared__ DgMlpDev m;
+  __shared__ float feat[MLP_WARPS][16][17];
+  __shared__ float yv[MLP_WARPS][16];
+  {
+    const int4* src = reinterpret_cast<const int4*>(mlp);
+    int4* dst = reinterpret_cast<int4*>(&m);
+    for (int i = threadIdx.x; i < (int)(sizeof(DgMlpDev) / 16); i += blockDim.x) dst[i] = src[i];
+  }
+  __syncthreads();
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nv = NSPEC + dim + 1;
+  const int64_t total = K * np;
+  unsigned long long n_ok = 0, n_fb = 0;
+  for (int64_t base = ((int64_t)blockIdx.x * MLP_WARPS + w) * 16; base < total;
+       base += (int64_t)gridDim.x * MLP_WARPS * 16) {
+    const int64_t i = base + (lane & 15);
+    const bool mine = lane < 16 && i < total;
+    double Y[NSPEC], rho = 1.0, e = 0.0;
+    int64_t k = 0;
+    int node = 0;
+    if (lane < 16) {
+      if (mine) {
+        k = i / np;
+        node = (int)(i % np);
+        const T* uu = u + k * nv * np + node;
+        rho = 0.0;
+#pragma unroll
+        for (int s = 0; s < NSPEC; ++s) {
+          Y[s] = (double)uu[s * np];
+          rho += Y[s];
+        }
+        double ke = 0.0;
+        for (int d = 0; d < dim; ++d) {
+          const double mm = (double)uu[(NSPEC + d) * np];
+          ke += mm * mm;
+        }
+        e = (double)uu[(NSPEC + dim) * np] / rho - 0.5 * ke / (rho * rho);
+#pragma unroll
+        for (int s = 0; s < NSPEC; ++s) Y[s] /= rho;
+      } else {
+#pragma unroll
+        for (int s = 0; s < NSPEC; ++s) Y[s] = 0.2;
+      }
+      float f[NI];
+#pragma unroll
+      for (int s = 0; s < NSPEC; ++s) f[s] = (float)Y[s];
+      f[5] = logf((float)rho);
+      f[6] = (float)e;
+#pragma unroll
+      for (int q = 0; q < NI; ++q) feat[w][lane][q] = (f[q] - m.mean[q]) * m.inv_std[q];
+#pragma unroll
+      for (int q = NI; q < 16; ++q) feat[w][lane][q] = 0.f;
+    }
+    __syncwarp();
+    mlp16(m, feat[w], yv[w]);
+    __syncwarp();
+    if (mine) {
+      PolyD P;
+      poly_d(sp, Y, P);
+      double T0 = clampT((double)(m.muT + m.sigT * yv[w][lane]));
+      double T1 = clampT(T0 - (P.e(T0) - e) / P.cv(T0));
+      const double r1 = P.e(T1) - e;
+      if (fabs(r1) <= 1e-7 * P.cv(T1) * T1) {
+        ++n_ok;
+      } else {
+        // fallback: the plain Newton iteration from the polished value
+        ++n_fb;
+        bool conv = false;
+        for (int it = 0; it < 50; ++it) {
+          const double Tn = clampT(T1 - (P.e(T1) - e) / P.cv(T1));
+          const double step = fabs(Tn - T1);
+          T1 = Tn;
+          if (step <= 1e-12 * T1) {
+            conv = true;
+            break;
+          }
+        }
+        if (!conv) atomicCAS(status, 0ull, (DG_ST_NEWTON << 56) | (unsigned long long)k);
+      }
+      Tc[k * np + node] = T1;
+      const double p = rho * P.Rmix * T1, cv = P.cv(T1);
+      pc[(k * 2 + 0) * np + node] = (T)p;
+      pc[(k * 2 + 1) * np + node] = (T)sqrt((cv + P.Rmix) / cv * p / rho);
+    }
+    __syncwarp();
+  }
+  if (stats) {
+    for (int o = 16; o > 0; o >>= 1) {
+      n_ok += __shfl_xor_sync(0xffffffffu, n_ok, o);
+      n_fb += __shfl_xor_sync(0xffffffffu, n_fb, o);
+    }
+    if (lane == 0) {
+      atomicAdd(&stats[0], n_ok);
+      atomicAdd(&stats[1], n_fb);
+    }
+  }
+}
+
+// plain tensor-core forward for standardised inputs X[n][7] -> y[n] (checks / data)
+__global__ void __launch_bounds__(32 * MLP_WARPS)
+mlp_forward_tc_kernel(const DgMlpDev* mlp, const float* X, float* y, int64_t n) {
+  __shared__ DgMlpDev m;
+  __shared__ float feat[MLP_WARPS][16][17];
+  __shared__ float yv[MLP_WARPS][16];
+  {
+    const int4* src = reinterpret_cast<const int4*>(mlp);
+    int4* dst = reinterpret_cast<int4*>(&m);
+    for (int i = threadIdx.x; i < (int)(sizeof(DgMlpDev) / 16); i += blockDim.x) dst[i] = src[i];
+  }
+  __syncthreads();
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int64_t base = ((int64_t)blockIdx.x * MLP_WARPS + w) * 16; base < n;
+       base += (int64_t)gridDim.x * MLP_WARPS * 16) {
+    if (lane < 16) {
+      const int64_t i = base + lane;
+#pragma unroll
+      for (int q = 0; q < 16; ++q) feat[w][lane][q] = (i < n && q < NI) ? X[i * NI + q] : 0.f;
+    }
+    __syncwarp();
+    mlp16(m, feat[w], yv[w]);
+    __syncwarp();
+    if (lane < 16 && base + lane < n) y[base + lane] = yv[w][lane];
+    __syncwarp();
+  }
+}
+
+// FP32 SIMT forward of one sample per thread (reference path of the device code)
+__global__ void mlp_forward_f32_kernel(const float* P, const float* X, float* y, int64_t n) {
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n;
+       s += (int64_t)gridDim.x * blockDim.x) {
+    float h1[NH];
+    for (int j = 0; j < NH; ++j) {
+      float a = P[OFF_B1 + j];
+      for (int k = 0; k < NI; ++k) a += P[OFF_W1 + j * NI + k] * X[s * NI + k];
+      h1[j] = gelu_f(a);
+    }
+    float out = P[OFF_B3];
+    for (int j = 0; j < NH; ++j) {
+      float a = P[OFF_B2 + j];
+      for (int i = 0; i < NH; ++i) a += P[OFF_W2 + j * NH + i] * h1[i];
+      out += P[OFF_W3 + j] * gelu_f(a);
+    }
+    y[s] = out;
+  }
+}
+
+// ------------------------------------------------------------------ training (FP32)
+#define TS 32  // samples per tile
+struct TrainSmem {
+  float W1[NH * NI], b1[NH], W2[NH * NH], W2T[NH * NH], b2[NH], w3[NH], b3;
+  float X[TS][NI], a1[TS][NH], h1[TS][NH], a2[TS][NH], h2[TS][NH];
+  float dy[TS], r2[TS];
+  float g[NPARAM];  // gW2 stored transposed [i][j]
+  float loss;
+};
+
+// per-CTA partial gradients of loss = (1/B) sum (y - t)^2 over the CTA's tiles
+__global__ void __launch_bounds__(NH) mlp_grad_kernel(const float* P, const float* X, const float* t,
+                                                      int B, float* partial) {
+  extern __shared__ __align__(16) unsigned char raw[];
+  TrainSmem& S = *reinterpret_cast<TrainSmem*>(raw);
+  const int j = threadIdx.x;
+  for (int q = j; q < NH * NI; q += NH) S.W1[q] = P[OFF_W1 + q];
+  for (int q = j; q < NH * NH; q += NH) {
+    S.W2[q] = P[OFF_W2 + q];
+    S.W2T[(q % NH) * NH + q / NH] = P[OFF_W2 + q];
+  }
+  S.b1[j] = P[OFF_B1 + j];
+  S.b2[j] = P[OFF_B2 + j];
+  S.w3[j] = P[OFF_W3 + j];
+  if (j == 0) {
+    S.b3 = P[OFF_B3];
+    S.loss = 0.f;
+  }
+  for (int q = j; q < NPARAM; q += NH) S.g[q] = 0.f;
+  __syncthreads();
+  const float invB = 1.0f / B;
+  for (int s0 = blockIdx.x * TS; s0 < B; s0 += gridDim.x * TS) {
+    const int ns = min(TS, B - s0);
+    for (int q = j; q < TS * NI; q += NH) S.X[q / NI][q % NI] = q / NI < ns ? X[(int64_t)s0 * NI + q] : 0.f;
+    __syncthreads();
+    for (int s = 0; s < ns; ++s) {
+      float a = S.b1[j];
+#pragma unroll
+      for (int k = 0; k < NI; ++k) a += S.W1[j * NI + k] * S.X[s][k];
+      S.a1[s][j] = a;
+      S.h1[s][j] = gelu_f(a);
+    }
+    __syncthreads();
+    for (int s = 0; s < ns; ++s) {
+      float a = S.b2[j];
+      for (int i = 0; i < NH; ++i) a += S.W2T[i * NH + j] * S.h1[s][i];
+      S.a2[s][j] = a;
+      S.h2[s][j] = gelu_f(a);
+    }
+    __syncthreads();
+    if (j < ns) {
+      float y = S.b3;
+      for (int q = 0; q < NH; ++q) y += S.w3[q] * S.h2[j][q];
+      const float r = y - t[s0 + j];
+      S.dy[j] = 2.0f * r * invB;
+      S.r2[j] = r * r * invB;
+    }
+    __syncthreads();
+    if (j == 0)
+      for (int s = 0; s < ns; ++s) S.loss += S.r2[s];  // fixed order: deterministic
+    float gw3 = 0.f, gb2 = 0.f;
+    for (int s = 0; s < ns; ++s) {
+      gw3 += S.dy[s] * S.h2[s][j];
+      const float d2 = S.dy[s] * S.w3[j] * gelu_d_f(S.a2[s][j]);
+      S.a2[s][j] = d2;  // a2 now holds delta2
+      gb2 += d2;
+    }
+    S.g[OFF_W3 + j] += gw3;
+    S.g[OFF_B2 + j] += gb2;
+    if (j == 0) {
+      float gb3 = 0.f;
+      for (int s = 0; s < ns; ++s) gb3 += S.dy[s];
+      S.g[OFF_B3] += gb3;
+    }
+    __syncthreads();
+    // thread j: row j of dW2 (stored transposed) and delta1 of hidden unit j
+    for (int i = 0; i < NH; ++i) {
+      float acc = 0.f;
+      for (int s = 0; s < ns; ++s) acc += S.a2[s][j] * S.h1[s][i];
+      S.g[OFF_W2 + i * NH + j] += acc;
+    }
+    float gb1 = 0.f, gw1[NI] = {0, 0, 0, 0, 0, 0, 0};
+    for (int s = 0; s < ns; ++s) {
+      float acc = 0.f;
+      for (int q = 0; q < NH; ++q) acc += S.W2[q * NH + j] * S.a2[s][q];
+      const float d1 = acc * gelu_d_f(S.a1[s][j]);
+      gb1 += d1;
+#pragma unroll
+      for (int k = 0; k < NI; ++k) gw1[k] += d1 * S.X[s][k];
+    }
+    S.g[OFF_B1 + j] += gb1;
+#pragma unroll
+    for (int k = 0; k < NI; ++k) S.g[OFF_W1 + j * NI + k] += gw1[k];
+    __syncthreads();
+  }
+  float* out = partial + (int64_t)blockIdx.x * (NPARAM + 1);
+  for (int q = j; q < NPARAM; q += NH) {
+    float v = S.g[q];
+    if (q >= OFF_W2 && q < OFF_W2 + NH * NH) {  // back to row-major [j][i]
+      const int i = (q - OFF_W2) / NH, jj = (q - OFF_W2) % NH;
+      v = S.g[q];
+      out[OFF_W2 + jj * NH + i] = v;
+    } else {
+      out[q] = v;
+    }
+  }
+  if (j == 0) out[NPARAM] = S.loss;
+}
+
+// fixed-order sum of the partial gradients, then (optionally) one Adam step
+__global__ void mlp_reduce_adam_kernel(const float* partial, int nb, float* grad, float* P, float* mo,
+                                       float* vo, int step, float lr, float b1, float b2, float eps,
+                                       double* loss) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q > NPARAM) return;
+  float s = 0.f;
+  for (int b = 0; b < nb; ++b) s += partial[(int64_t)b * (NPARAM + 1) + q];
+  if (q == NPARAM) {
+    if (loss) *loss = (double)s;
+    return;
+  }
+  if (grad) grad[q] = s;
+  if (P) {
+    const float c1 = 1.0f - powf(b1, (float)step), c2 = 1.0f - powf(b2, (float)step);
+    const float m = b1 * mo[q] + (1.0f - b1) * s;
+    const float v = b2 * vo[q] + (1.0f - b2) * s * s;
+    mo[q] = m;
+    vo[q] = v;
+    P[q] -= lr * (m / c1) / (sqrtf(v / c2) + eps);
+  }
+}
+
+// counter-based sampling of node states (splitmix64 of seed + index)
+__device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
+  x += 0x9E3779B97F4A7C15ull;
+  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+  x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+  return x ^ (x >> 31);
+}
+
+template <typename T>
+__global__ void sample_kernel(const T* u, const double* Tc, int64_t K, int np, int dim, int64_t n,
+                              uint64_t seed, float* X, float* Tout) {
+  const int nv = NSPEC + dim + 1;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = (int64_t)(splitmix64(seed + (uint64_t)j) % (uint64_t)(K * np));
+    const int64_t k = i / np;
+    const int node = (int)(i % np);
+    const T* uu = u + k * nv * np + node;
+    double rho = 0.0, ke = 0.0;
+    for (int s = 0; s < NSPEC; ++s) rho += (double)uu[s * np];
+    for (int d = 0; d < dim; ++d) {
+      const double mm = (double)uu[(NSPEC + d) * np];
+      ke += mm * mm;
+    }
+    for (int s = 0; s < NSPEC; ++s) X[j * NI + s] = (float)((double)uu[s * np] / rho);
+    X[j * NI + 5] = (float)log(rho);
+    X[j * NI + 6] = (float)((double)uu[(NSPEC + dim) * np] / rho - 0.5 * ke / (rho * rho));
+    Tout[j] = (float)Tc[i];
+  }
+}
+
+unsigned grid_of(int64_t n, int bs) {
+  int64_t g = (n + bs - 1) / bs;
+  if (g > 152 * 32) g = 152 * 32;
+  return (unsigned)(g < 1 ? 1 : g);
+}
+
+void pack_host(const float* params, const double* stats, DgMlpDev* h) {
+  memset(h, 0, sizeof(*h));
+  for (int j = 0; j < NH; ++j) {
+    for (int k = 0; k < NI; ++k) h->W1[j * 16 + k] = __float2bfloat16(params[OFF_W1 + j * NI + k]);
+    for (int i = 0; i < NH; ++i) h->W2[j * NH + i] = __float2bfloat16(params[OFF_W2 + j * NH + i]);
+    h->b1[j] = params[OFF_B1 + j];
+    h->b2[j] = params[OFF_B2 + j];
+    h->w3[j] = params[OFF_W3 + j];
+  }
+  h->b3 = params[OFF_B3];
+  for (int q = 0; q < NI; ++q) {
+    h->mean[q] = (float)stats[q];
+    h->inv_std[q] = (float)(1.0 / stats[NI + q]);
+  }
+  h->muT = (float)stats[2 * NI];
+  h->sigT = (float)stats[2 * NI + 1];
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- thermo hooks
+cudaError_t dg_mlp_set(DgThermo* th, const float* params_host, const double* stats_host) {
+  if (!params_host) {
+    if (th->mlp) cudaFree(th->mlp);
+    th->mlp = NULL;
+    return cudaSuccess;
+  }
+  DgMlpDev h;
+  pack_host(params_host, stats_host, &h);
+  cudaError_t e = cudaSuccess;
+  if (!th->mlp) e = cudaMalloc(&th->mlp, sizeof(DgMlpDev));
+  if (e == cudaSuccess && !th->mlp_stats) e = cudaMalloc((void**)&th->mlp_stats, 2 * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMemset(th->mlp_stats, 0, 2 * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMemcpy(th->mlp, &h, sizeof(h), cudaMemcpyHostToDevice);
+  return e;
+}
+
+cudaError_t dg_mlp_thermo_update(DgThermo* th, const void* u, int f32, cudaStream_t s) {
+  const int64_t n = th->K * th->np;
+  const unsigned grid = grid_of((n + 15) / 16, MLP_WARPS);
+  if (f32)
+    thermo_mlp_kernel<float><<<grid, 32 * MLP_WARPS, 0, s>>>((const float*)u, th->K, th->np, th->dim,
+        th->species, th->T, (float*)th->pc, th->status, (const DgMlpDev*)th->mlp, th->mlp_stats);
+  else
+    thermo_mlp_kernel<double><<<grid, 32 * MLP_WARPS, 0, s>>>((const double*)u, th->K, th->np, th->dim,
+        th->species, th->T, (double*)th->pc, th->status, (const DgMlpDev*)th->mlp, th->mlp_stats);
+  return cudaGetLastError();
+}
+
+cudaError_t dg_mlp_sample(DgThermo* th, const void* u, int f32, int64_t n, uint64_t seed, float* X,
+                          float* T, cudaStream_t s) {
+  if (f32)
+    sample_kernel<float><<<grid_of(n, 256), 256, 0, s>>>((const float*)u, th->T, th->K, th->np, th->dim,
+                                                         n, seed, X, T);
+  else
+    sample_kernel<double><<<grid_of(n, 256), 256, 0, s>>>((const double*)u, th->T, th->K, th->np, th->dim,
+                                                          n, seed, X, T);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- C ABI (training)
+extern "C" {
+
+int dg_mlp_nparams(void) { return NPARAM; }
+
+size_t dg_mlp_workspace_bytes(int batch) {
+  int nb = (batch + TS - 1) / TS;
+  if (nb > 152) nb = 152;
+  return sizeof(float) * (size_t)nb * (NPARAM + 1);
+}
+
+static dg_status grad_common(const float* P, const float* X, const float* t, int B, float* ws,
+                             size_t ws_bytes, cudaStream_t st, int* nb_out) {
+  if (!P || !X || !t || !ws || B < 1) return DG_EINVAL;
+  if (ws_bytes < dg_mlp_workspace_bytes(B)) return DG_EINVAL;
+  int nb = (B + TS - 1) / TS;
+  if (nb > 152) nb = 152;
+  const size_t smem = sizeof(TrainSmem);
+  if (cudaFuncSetAttribute(mlp_grad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+      cudaSuccess)
+    return DG_ECUDA;
+  mlp_grad_kernel<<<nb, NH, smem, st>>>(P, X, t, B, ws);
+  if (cudaGetLastError() != cudaSuccess) return DG_ECUDA;
+  *nb_out = nb;
+  return DG_OK;
+}
+
+dg_status dg_mlp_grad(const float* params, const float* X, const float* t, int batch, float* grad,
+                      double* loss, float* workspace, size_t ws_bytes, void* stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  int nb = 0;
+  dg_status r = grad_common(params, X, t, batch, workspace, ws_bytes, st, &nb);
+  if (r != DG_OK) return r;
+  if (!grad) return DG_EINVAL;
+  mlp_reduce_adam_kernel<<<(NPARAM + 1 + 255) / 256, 256, 0, st>>>(workspace, nb, grad, NULL, NULL, NULL, 0,
+                                                                   0.f, 0.f, 0.f, 0.f, loss);
+  return cudaGetLastError() == cudaSuccess ? DG_OK : DG_ECUDA;
+}
+
+dg_status dg_mlp_train_step(float* params, float* m, float* v, const float* X, const float* t, int batch,
+                            int step, float lr, double* loss, float* workspace, size_t ws_bytes,
+                            void* stream) {
+  if (!m || !v || step < 1 || !(lr > 0.f)) return DG_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  int nb = 0;
+  dg_status r = grad_common(params, X, t, batch, workspace, ws_bytes, st, &nb);
+  if (r != DG_OK) return r;
+  mlp_reduce_adam_kernel<<<(NPARAM + 1 + 255) / 256, 256, 0, st>>>(workspace, nb, NULL, params, m, v, step,
+                                                                   lr, 0.9f, 0.999f, 1e-8f, loss);
+  return cudaGetLastError() == cudaSuccess ? DG_OK : DG_ECUDA;
+}
+
+dg_status dg_mlp_forward(const float* params, const double* stats, const float* X, float* y, int64_t n,
+                         int tensor_cores, void* stream) {
+  if (!params || !X || !y || n < 1) return DG_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (!tensor_cores) {
+    mlp_forward_f32_kernel<<<grid_of(n, 128), 128, 0, st>>>(params, X, y, n);
+    return cudaGetLastError() == cudaSuccess ? DG_OK : DG_ECUDA;
+  }
+  // tensor-core path: pack the host copy of the device parameters
+  float* hp = (float*)malloc(sizeof(float) * NPARAM);
+  if (!hp) return DG_ENOMEM;
+  if (cudaMemcpy(hp, params, sizeof(float) * NPARAM, cudaMemcpyDeviceToHost) != cudaSuccess) {
+    free(hp);
+    return DG_ECUDA;
+  }
+  double unit[2 * NI + 2];
+  for (int q = 0; q < NI; ++q) {
+    unit[q] = 0.0;
+    unit[NI + q] = 1.0;
+  }
+  unit[2 * NI] = stats ? stats[2 * NI] : 0.0;
+  unit[2 * NI + 1] = stats ? stats[2 * NI + 1] : 1.0;
+  DgMlpDev h;
+  pack_host(hp, unit, &h);
+  free(hp);
+  DgMlpDev* d = NULL;
+  if (cudaMalloc((void**)&d, sizeof(h)) != cudaSuccess) return DG_ENOMEM;
+  cudaMemcpy(d, &h, sizeof(h), cudaMemcpyHostToDevice);
+  mlp_forward_tc_kernel<<<grid_of((n + 15) / 16, MLP_WARPS), 32 * MLP_WARPS, 0, st>>>(d, X, y, n);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(d);
+  return e == cudaSuccess ? DG_OK : DG_ECUDA;
+}
+
+}  // extern "C"

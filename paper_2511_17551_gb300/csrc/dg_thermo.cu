@@ -203,6 +203,8 @@ cudaError_t dg_thermo_init(DgThermo* th, int64_t K, int np, int dim, const doubl
 }
 
 void dg_thermo_free(DgThermo* th) {
+  if (th->mlp) cudaFree(th->mlp);
+  if (th->mlp_stats) cudaFree(th->mlp_stats);
   if (th->species) cudaFree(th->species);
   if (th->T) cudaFree(th->T);
   if (th->pc) cudaFree(th->pc);
@@ -217,6 +219,7 @@ cudaError_t dg_thermo_reset(DgThermo* th, cudaStream_t s) {
 }
 
 cudaError_t dg_thermo_update(DgThermo* th, const void* u, int f32, cudaStream_t s) {
+  if (th->mode == 1 && th->mlp) return dg_mlp_thermo_update(th, u, f32, s);
   if (f32)
     thermo_update_kernel<float><<<grid_of(th->K * th->np), 256, 0, s>>>(
         (const float*)u, th->K, th->np, th->dim, th->species, th->T, (float*)th->pc, th->status, 1);

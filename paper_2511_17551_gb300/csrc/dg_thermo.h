@@ -13,6 +13,7 @@ struct DgThermo {
   void* bc_pc;         // device [n_bc][2]
   unsigned long long* status;
   void* mlp;           // surrogate weights (device) or null
+  unsigned long long* mlp_stats;  // [accepted, fallback] node counts of the surrogate
 };
 
 cudaError_t dg_thermo_upload_basis();
@@ -23,3 +24,8 @@ cudaError_t dg_thermo_reset(DgThermo* th, cudaStream_t s);
 cudaError_t dg_thermo_update(DgThermo* th, const void* u, int f32, cudaStream_t s);
 cudaError_t dg_thermo_boundary(DgThermo* th, const double* bw, int n_bc, void* bc_u, cudaStream_t s);
 cudaError_t dg_thermo_prim2cons(DgThermo* th, const double* w, void* u, cudaStream_t s);
+// surrogate (dg_mlp.cu)
+cudaError_t dg_mlp_set(DgThermo* th, const float* params_host, const double* stats_host);
+cudaError_t dg_mlp_thermo_update(DgThermo* th, const void* u, int f32, cudaStream_t s);
+cudaError_t dg_mlp_sample(DgThermo* th, const void* u, int f32, int64_t n, uint64_t seed, float* X,
+                          float* T, cudaStream_t s);
