@@ -208,12 +208,102 @@ def run_ours(args, rank, world, local_rank):
         "gpu_launches": launches,
         "clocks": clk,
     }
+    if not args.no_mixture:
+        out["mixture"] = run_mixture(args, stream.cuda_stream, world)
     if rank == 0:
         if not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline(cfg, args.cpu_seconds)
         print(json.dumps(out))
     if world > 1:
         dist.destroy_process_group()
+
+
+def run_mixture(args, stream_ptr, world):
+    """Five-species frozen mixture on the 24^3-element cylinder O-grid, N = 4 (Mach 5 nominal):
+    the per-node temperature solve by (a) the plain Newton iteration and (b) the learned
+    surrogate (trained here on states drawn from the plain solver's own run) in the mixed
+    form, and (c) the FP64 plain form.  Also the surrogate's gain over a cold and a warm
+    plain Newton solve (thermo kernel time alone)."""
+    import torch
+    import paper_2511_17551_gb300 as dg
+    from paper_2511_17551_gb300 import surrogate as S
+    N, nr = 4, args.mix_elements
+    xi, _ = dg.dg_lgl_nodes(N)
+    xyz, nbr, face = W.ogrid_mesh(xi, nr, nr, nr)
+    w0 = W.mixture_primitive(xyz, rho=0.1, vel=(2000.0, 0.0, 0.0), T=300.0, seed=7)
+    fs = w0[0, :, 0].copy()
+    K, npn = xyz.shape[0], (N + 1) ** 3
+    dof = K * npn * 9
+    steps = max(2, args.mix_steps)
+    sp = W.species_table()
+
+    def make(precision):
+        s = dg.Solver(3, N, xyz, nbr, face, n_species=5, species=sp, volume_flux=dg.DG_VF_DUCROS,
+                      surface_flux=dg.DG_SF_LLF, bc_kind=[1, 2, 3], bc_prim=np.stack([fs] * 3),
+                      precision=precision, stream=stream_ptr)
+        s.set_primitive(w0)
+        return s
+
+    def timed(s, n):
+        s.step(2, 0.3)
+        dg.dg_profile(s.ctx, 1)
+        dg.dg_profile_read(s.ctx)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s.step(n, 0.3)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        prof = dg.dg_profile_read(s.ctx)
+        dg.dg_profile(s.ctx, 0)
+        dev_ms = sum(v[0] for v in prof.values())
+        return wall, prof, dev_ms
+
+    out = {"workload": "mixture_5sp_ogrid_%d^3_N4" % nr, "elements": K, "dof": dof, "steps": steps}
+    s = make(dg.DG_MIXED)
+    wall, prof, dev_ms = timed(s, steps)
+    out["mixed_newton"] = {"value": world * dof * 5 * steps / wall, "ms_per_step": wall * 1e3 / steps,
+                           "thermo_ms_per_launch": prof["thermo"][0] / max(1, prof["thermo"][1]),
+                           "rhs_ms_per_launch": prof["rhs"][0] / max(1, prof["rhs"][1])}
+    # training data from the plain solver's own run, then the surrogate
+    t0 = time.perf_counter()
+    X, T = S.collect(s.ctx, args.train_samples, 10, 2, cfl=0.3)
+    params, stats, hist = S.train(X, T, epochs=args.train_epochs, batch=4096, lr=2e-3)
+    out["training"] = {"samples": int(X.shape[0]), "epochs": args.train_epochs,
+                       "val_mse_first_last": [hist[0][2], hist[-1][2]],
+                       "seconds": time.perf_counter() - t0}
+    # gain on the thermo kernel alone: cold Newton, warm Newton, surrogate
+    u_host = np.zeros((K, 9, npn))
+    dg.dg_get_state(s.ctx, u_host)
+    dg.dg_profile(s.ctx, 1)
+    dg.dg_set_state(s.ctx, u_host)
+    dg.dg_profile_read(s.ctx)
+    Tshape = (K, npn)
+    T_cold = dg.dg_get_temperature(s.ctx, Tshape)
+    cold = dg.dg_profile_read(s.ctx)["thermo"][0]
+    dg.dg_get_temperature(s.ctx, Tshape)
+    warm = dg.dg_profile_read(s.ctx)["thermo"][0]
+    dg.dg_set_surrogate(s.ctx, params, stats)
+    T_mlp = dg.dg_get_temperature(s.ctx, Tshape)
+    mlp = dg.dg_profile_read(s.ctx)["thermo"][0]
+    acc, fb = dg.dg_surrogate_stats(s.ctx)
+    dg.dg_profile(s.ctx, 0)
+    out["thermo_gain"] = {"cold_newton_ms": cold, "converged_cache_newton_ms": warm,
+                          "surrogate_ms": mlp, "accepted": acc, "fallback": fb,
+                          "max_rel_T_diff_vs_newton": float(np.abs(T_mlp / T_cold - 1).max())}
+    wall, prof, dev_ms = timed(s, steps)
+    acc, fb = dg.dg_surrogate_stats(s.ctx)
+    out["mixed_surrogate"] = {"value": world * dof * 5 * steps / wall, "ms_per_step": wall * 1e3 / steps,
+                              "thermo_ms_per_launch": prof["thermo"][0] / max(1, prof["thermo"][1]),
+                              "accept_frac": acc / max(1, acc + fb)}
+    s.close()
+    s64 = make(dg.DG_FP64)
+    n64 = max(2, steps // 5)
+    wall, prof, _ = timed(s64, n64)
+    out["fp64_newton"] = {"value": world * dof * 5 * n64 / wall, "ms_per_step": wall * 1e3 / n64,
+                          "thermo_ms_per_launch": prof["thermo"][0] / max(1, prof["thermo"][1]),
+                          "rhs_ms_per_launch": prof["rhs"][0] / max(1, prof["rhs"][1])}
+    s64.close()
+    return out
 
 
 def cpu_baseline(cfg, budget_s):
@@ -283,6 +373,11 @@ def main():
     ap.add_argument("--config", default="tgv_ns_32^3_N3", choices=sorted(CONFIGS))
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-mixture", action="store_true")
+    ap.add_argument("--mix-elements", type=int, default=24, help="O-grid elements per direction")
+    ap.add_argument("--mix-steps", type=int, default=40)
+    ap.add_argument("--train-samples", type=int, default=1000000)
+    ap.add_argument("--train-epochs", type=int, default=20)
     args = ap.parse_args()
     rank, world, local_rank = _env_rank()
     if args.impl == "reference":

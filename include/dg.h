@@ -32,6 +32,7 @@
  */
 #ifndef DG_H
 #define DG_H
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -98,11 +99,12 @@ dg_status dg_lgl_nodes(int N, double* nodes, double* weights);
 dg_status dg_init_mesh(const dg_mesh_desc* mesh, const dg_physics_desc* phys, dg_ctx** out);
 
 /* Set the state from FP64 conserved variables [K][nv][np] (host or device
- * pointer, copied; converted to FP32 in DG_MIXED).  t is the solution time. */
+ * pointer, copied; converted to FP32 in DG_MIXED).  t is the solution time.
+ * Mixtures: the per-node temperature cache restarts cold (Newton from 1000 K). */
 dg_status dg_set_state(dg_ctx* ctx, const double* u, int on_device, double t);
 
 /* Set the state from FP64 primitive variables (Eq. total_energy / eos applied
- * on the device). */
+ * on the device).  Mixtures: the given temperatures seed the temperature cache. */
 dg_status dg_set_state_primitive(dg_ctx* ctx, const double* w, int on_device, double t);
 
 /* Copy the current state to u (FP64 [K][nv][np], host or device) and its time
@@ -144,7 +146,7 @@ dg_status dg_get_temperature(dg_ctx* ctx, double* T);
 
 /* Load (params, stats: host arrays) into a mixture context and switch its temperature
  * solve to BF16 tensor-core inference + one FP64 Newton polish + residual check
- * (accept when the next Newton correction is <= 1e-7 T) with the plain Newton
+ * (accept when the next Newton correction is <= 1e-6 T) with the plain Newton
  * iteration as fallback.  params == NULL switches back to the plain Newton solve.
  * which must be 0 (temperature surrogate). */
 dg_status dg_set_surrogate(dg_ctx* ctx, int which, const float* params, const double* stats);

@@ -709,8 +709,8 @@ dg_status dg_set_state_primitive(dg_ctx* c, const double* w, int on_device, doub
           src, (double*)c->u[c->cur], c->K, c->dim, c->np, c->gamma);
     CK(cudaGetLastError());
   } else {
+    // also seeds the temperature cache with the given temperatures
     CK(dg_thermo_prim2cons(&c->th, src, c->u[c->cur], c->stream));
-    CK(dg_thermo_reset(&c->th, c->stream));
   }
   CK(cudaMemcpyAsync(c->scal, &t, sizeof(double), cudaMemcpyHostToDevice, c->stream));
   c->have_state = true;

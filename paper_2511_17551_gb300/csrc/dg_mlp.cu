@@ -11,7 +11,7 @@
 // layer are exactly the A fragments of the next (two n-tiles of 8 = one k-block of 16),
 // so activations never leave registers.  Layer 3 is a 64-term dot product reduced
 // across the 4 lanes sharing a row.  Then, per node in FP64: one Newton step from the
-// prediction, accept when the next correction would be <= 1e-7 T, otherwise run the
+// prediction, accept when the next correction would be <= 1e-6 T, otherwise run the
 // plain Newton iteration (fallback, counted).
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -216,7 +216,7 @@ thermo_mlp_kernel(const T* u, int64_t K, int np, int dim, const double* sp, doub
       double T0 = clampT((double)(m.muT + m.sigT * yv[w][lane]));
       double T1 = clampT(T0 - (P.e(T0) - e) / P.cv(T0));
       const double r1 = P.e(T1) - e;
-      if (fabs(r1) <= 1e-7 * P.cv(T1) * T1) {
+      if (fabs(r1) <= 1e-6 * P.cv(T1) * T1) {
         ++n_ok;
       } else {
         // fallback: the plain Newton iteration from the polished value
