@@ -230,8 +230,10 @@ def run_mixture(args, stream_ptr, world):
     N, nr = 4, args.mix_elements
     xi, _ = dg.dg_lgl_nodes(N)
     xyz, nbr, face = W.ogrid_mesh(xi, nr, nr, nr)
-    w0 = W.mixture_primitive(xyz, rho=0.1, vel=(2000.0, 0.0, 0.0), T=300.0, seed=7)
-    fs = w0[0, :, 0].copy()
+    # potential flow past the cylinder as the start (tangent at the wall), free stream at
+    # the far field; subcell-FV blending (alpha <= 0.5) captures the bow shock that forms
+    w0 = W.mixture_primitive(xyz, rho=0.1, vel=(2000.0, 0.0, 0.0), T=300.0, seed=7, cylinder=0.5)
+    fs = W.mixture_primitive(xyz[:1], rho=0.1, vel=(2000.0, 0.0, 0.0), T=300.0, seed=7)[0, :, 0]
     K, npn = xyz.shape[0], (N + 1) ** 3
     dof = K * npn * 9
     steps = max(2, args.mix_steps)
@@ -240,7 +242,7 @@ def run_mixture(args, stream_ptr, world):
     def make(precision):
         s = dg.Solver(3, N, xyz, nbr, face, n_species=5, species=sp, volume_flux=dg.DG_VF_DUCROS,
                       surface_flux=dg.DG_SF_LLF, bc_kind=[1, 2, 3], bc_prim=np.stack([fs] * 3),
-                      precision=precision, stream=stream_ptr)
+                      alpha_max=0.5, precision=precision, stream=stream_ptr)
         s.set_primitive(w0)
         return s
 

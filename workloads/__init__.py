@@ -204,11 +204,13 @@ def species_table(seed=5, ns=5):
     return tab
 
 
-def mixture_primitive(xyz, rho, vel, T, seed=7, ns=5, hot=None):
+def mixture_primitive(xyz, rho, vel, T, seed=7, ns=5, hot=None, cylinder=None):
     """(rho_s, v, T) with Y from a smooth seeded Dirichlet field.
 
     Y_s ~ b_s (1 + 0.5 sin(k_s . x + phi_s)), normalised, b ~ Dirichlet(1..1).
     ``hot`` = (radius, T_hot): nodes closer than radius to the z axis get T_hot.
+    ``cylinder`` = R: the velocity is the incompressible potential flow past a cylinder of
+    radius R on the z axis (free stream vel[0] along x), tangent to the body at r = R.
     """
     rng = np.random.default_rng(seed)
     b = rng.dirichlet(np.ones(ns))
@@ -223,6 +225,16 @@ def mixture_primitive(xyz, rho, vel, T, seed=7, ns=5, hot=None):
         w[:, s] = rho * Y[s]
     for d in range(dim):
         w[:, ns + d] = vel[d]
+    if cylinder is not None:
+        R = cylinder
+        x, y = xyz[:, 0], xyz[:, 1]
+        r2 = np.maximum(x * x + y * y, 1e-300)
+        U = vel[0]
+        # u - i v = U (1 - R^2 / z^2) with z = x + i y
+        zr2 = (x * x - y * y) / (r2 * r2)
+        zi2 = -2 * x * y / (r2 * r2)
+        w[:, ns + 0] = U * (1.0 - R * R * zr2)
+        w[:, ns + 1] = U * R * R * zi2
     w[:, ns + dim] = T
     if hot is not None:
         rad, Th = hot
