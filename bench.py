@@ -260,12 +260,16 @@ def run_mixture(args, stream_ptr, world):
         dev_ms = sum(v[0] for v in prof.values())
         return wall, prof, dev_ms
 
+    def per_kind(prof, n):
+        return {k: round(v[0] / n, 4) for k, v in prof.items() if v[1]}
+
     out = {"workload": "mixture_5sp_ogrid_%d^3_N4" % nr, "elements": K, "dof": dof, "steps": steps}
     s = make(dg.DG_MIXED)
     wall, prof, dev_ms = timed(s, steps)
     out["mixed_newton"] = {"value": world * dof * 5 * steps / wall, "ms_per_step": wall * 1e3 / steps,
                            "thermo_ms_per_launch": prof["thermo"][0] / max(1, prof["thermo"][1]),
-                           "rhs_ms_per_launch": prof["rhs"][0] / max(1, prof["rhs"][1])}
+                           "rhs_ms_per_launch": prof["rhs"][0] / max(1, prof["rhs"][1]),
+                           "device_ms_per_step_by_kernel": per_kind(prof, steps)}
     # training data from the plain solver's own run, then the surrogate
     t0 = time.perf_counter()
     X, T = S.collect(s.ctx, args.train_samples, 10, 2, cfl=0.3)

@@ -129,20 +129,17 @@ struct PolyD {
   }
 };
 
-__device__ __forceinline__ void poly_d(const double* sp, const double* Y, PolyD& P) {
+// mixture polynomial from the per-species coefficient rows of the context
+// ([R a6, R (a1-1), R a2/2, R a3/3, R a4/4, R a5/5, R, 0] per species)
+__device__ __forceinline__ void poly_d(const double* cf, const double* Y, PolyD& P) {
+#pragma unroll
   for (int k = 0; k < 6; ++k) P.b[k] = 0.0;
   P.Rmix = 0.0;
 #pragma unroll
   for (int s = 0; s < NSPEC; ++s) {
-    const double* a = sp + 8 * s + 1;
-    const double w = Y[s] * DG_RU / sp[8 * s];
-    P.b[0] += w * a[5];
-    P.b[1] += w * (a[0] - 1.0);
-    P.b[2] += w * a[1] * 0.5;
-    P.b[3] += w * a[2] / 3.0;
-    P.b[4] += w * a[3] * 0.25;
-    P.b[5] += w * a[4] * 0.2;
-    P.Rmix += w;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) P.b[k] += Y[s] * cf[8 * s + k];
+    P.Rmix += Y[s] * cf[8 * s + 6];
   }
 }
 
@@ -155,8 +152,8 @@ __global__ void __launch_bounds__(32 * MLP_WARPS)
 thermo_mlp_kernel(const T* u, int64_t K, int np, int dim, const double* sp, double* Tc, T* pc,
                   unsigned long long* status, const DgMlpDev* mlp, unsigned long long* stats) {
   __shared__ DgMlpDev m;
-  __shared__ float feat[MLP_WARPS][16][17];
-  __shared__ float yv[MLP_WARPS][16];
+  __shared__ float feat[MLP_WARPS][32][17];
+  __shared__ float yv[MLP_WARPS][32];
   {
     const int4* src = reinterpret_cast<const int4*>(mlp);
     int4* dst = reinterpret_cast<int4*>(&m);
@@ -167,36 +164,38 @@ thermo_mlp_kernel(const T* u, int64_t K, int np, int dim, const double* sp, doub
   const int nv = NSPEC + dim + 1;
   const int64_t total = K * np;
   unsigned long long n_ok = 0, n_fb = 0;
-  for (int64_t base = ((int64_t)blockIdx.x * MLP_WARPS + w) * 16; base < total;
-       base += (int64_t)gridDim.x * MLP_WARPS * 16) {
-    const int64_t i = base + (lane & 15);
-    const bool mine = lane < 16 && i < total;
+  // 32 nodes per warp and pass: two 16-row MMA tiles, then one node per lane in FP64
+  for (int64_t base = ((int64_t)blockIdx.x * MLP_WARPS + w) * 32; base < total;
+       base += (int64_t)gridDim.x * MLP_WARPS * 32) {
+    const int64_t i = base + lane;
+    const bool mine = i < total;
     double Y[NSPEC], rho = 1.0, e = 0.0;
     int64_t k = 0;
     int node = 0;
-    if (lane < 16) {
-      if (mine) {
-        k = i / np;
-        node = (int)(i % np);
-        const T* uu = u + k * nv * np + node;
-        rho = 0.0;
+    if (mine) {
+      k = i / np;
+      node = (int)(i % np);
+      const T* uu = u + k * nv * np + node;
+      rho = 0.0;
 #pragma unroll
-        for (int s = 0; s < NSPEC; ++s) {
-          Y[s] = (double)uu[s * np];
-          rho += Y[s];
-        }
-        double ke = 0.0;
-        for (int d = 0; d < dim; ++d) {
-          const double mm = (double)uu[(NSPEC + d) * np];
-          ke += mm * mm;
-        }
-        e = (double)uu[(NSPEC + dim) * np] / rho - 0.5 * ke / (rho * rho);
-#pragma unroll
-        for (int s = 0; s < NSPEC; ++s) Y[s] /= rho;
-      } else {
-#pragma unroll
-        for (int s = 0; s < NSPEC; ++s) Y[s] = 0.2;
+      for (int s = 0; s < NSPEC; ++s) {
+        Y[s] = (double)uu[s * np];
+        rho += Y[s];
       }
+      double ke = 0.0;
+      for (int d = 0; d < dim; ++d) {
+        const double mm = (double)uu[(NSPEC + d) * np];
+        ke += mm * mm;
+      }
+      const double ir = 1.0 / rho;
+      e = (double)uu[(NSPEC + dim) * np] * ir - 0.5 * ke * ir * ir;
+#pragma unroll
+      for (int s = 0; s < NSPEC; ++s) Y[s] *= ir;
+    } else {
+#pragma unroll
+      for (int s = 0; s < NSPEC; ++s) Y[s] = 0.2;
+    }
+    {
       float f[NI];
 #pragma unroll
       for (int s = 0; s < NSPEC; ++s) f[s] = (float)Y[s];
@@ -209,6 +208,7 @@ thermo_mlp_kernel(const T* u, int64_t K, int np, int dim, const double* sp, doub
     }
     __syncwarp();
     mlp16(m, feat[w], yv[w]);
+    mlp16(m, feat[w] + 16, yv[w] + 16);
     __syncwarp();
     if (mine) {
       PolyD P;
@@ -508,7 +508,7 @@ cudaError_t dg_mlp_set(DgThermo* th, const float* params_host, const double* sta
 
 cudaError_t dg_mlp_thermo_update(DgThermo* th, const void* u, int f32, cudaStream_t s) {
   const int64_t n = th->K * th->np;
-  const unsigned grid = grid_of((n + 15) / 16, MLP_WARPS);
+  const unsigned grid = grid_of((n + 31) / 32, MLP_WARPS);
   if (f32)
     thermo_mlp_kernel<float><<<grid, 32 * MLP_WARPS, 0, s>>>((const float*)u, th->K, th->np, th->dim,
         th->species, th->T, (float*)th->pc, th->status, (const DgMlpDev*)th->mlp, th->mlp_stats);

@@ -5,13 +5,15 @@
 // Eq. Internal_energy): cp_s/R_s = a1 + a2 T + a3 T^2 + a4 T^3 + a5 T^4 and
 //   e_s(T) = R_s (a1 T + a2 T^2/2 + a3 T^3/3 + a4 T^4/4 + a5 T^5/5 + a6 - T),
 // e = sum Y_s e_s (Eq. internal_energies), p = sum rho_s R_s T (Eq. eos).
-// Per node the species sums are folded into one polynomial
-//   e(T) = b0 + b1 T + b2 T^2 + b3 T^3 + b4 T^4 + b5 T^5,  cv = de/dT,
-// evaluated by Horner's rule.  Newton T <- T - (e(T) - e)/cv(T), warm-started from
-// the previous temperature of the node, stop when |dT| <= 1e-12 T (at most 50
-// steps, T kept in [200, 1e4] K); failure latches DG_ENEWTON.  The mixed form
-// iterates in FP32 to |dT| <= 1e-6 T and finishes with FP64 Newton steps on the
-// FP64 residual (the FP64 final residual of the mixed form).
+// At set-up every species becomes one row of a coefficient table
+//   [R_s a6, R_s (a1-1), R_s a2/2, R_s a3/3, R_s a4/4, R_s a5/5, R_s, 0],
+// so a node folds its mixture into e(T) = b0 + b1 T + ... + b5 T^5 with 30 multiply-adds
+// (no divisions) and evaluates e and cv = de/dT by Horner's rule.  Newton
+// T <- T - (e(T) - e)/cv(T) is warm-started from the node's previous temperature and
+// stops at |dT| <= 1e-12 T (at most 50 steps, T kept in [200, 1e4] K); failure latches
+// DG_ENEWTON.  Mixed form: FP32 Newton on e(T) - b0 = e - b0 (the constant b0 is
+// removed so FP32 resolves the residual) to |dT| <= 1e-6 T, then FP64 Newton steps on
+// the FP64 residual (normally one).
 #include <cuda_runtime.h>
 #include <math.h>
 #include <string.h>
@@ -35,98 +37,99 @@ struct Poly {
   __device__ __forceinline__ R e(R T) const {
     return b[0] + T * (b[1] + T * (b[2] + T * (b[3] + T * (b[4] + T * b[5]))));
   }
+  __device__ __forceinline__ R e_noconst(R T) const {
+    return T * (b[1] + T * (b[2] + T * (b[3] + T * (b[4] + T * b[5]))));
+  }
   __device__ __forceinline__ R cv(R T) const {
     return b[1] + T * (R(2) * b[2] + T * (R(3) * b[3] + T * (R(4) * b[4] + T * (R(5) * b[5]))));
   }
 };
 
 template <typename R>
-__device__ __forceinline__ void build_poly(const double* sp, const R* Y, Poly<R>& P) {
+__device__ __forceinline__ void build_poly(const R* cf, const R* Y, Poly<R>& P) {
+#pragma unroll
   for (int k = 0; k < 6; ++k) P.b[k] = R(0);
   P.Rmix = R(0);
 #pragma unroll
   for (int s = 0; s < NSPEC; ++s) {
-    const double* a = sp + 8 * s + 1;
-    const R Rs = R(DG_RU / sp[8 * s]);
-    const R w = Y[s] * Rs;
-    P.b[0] += w * R(a[5]);
-    P.b[1] += w * (R(a[0]) - R(1));
-    P.b[2] += w * R(a[1] * 0.5);
-    P.b[3] += w * R(a[2] / 3.0);
-    P.b[4] += w * R(a[3] * 0.25);
-    P.b[5] += w * R(a[4] * 0.2);
-    P.Rmix += w;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) P.b[k] += Y[s] * cf[8 * s + k];
+    P.Rmix += Y[s] * cf[8 * s + 6];
   }
 }
 
-// Newton on e(T) = e in precision R from T0; returns iterations used, or -1
-template <typename R>
-__device__ __forceinline__ int newton(const Poly<R>& P, R e, R& T, R tol, int maxit) {
-  for (int it = 1; it <= maxit; ++it) {
-    R dT = (P.e(T) - e) / P.cv(T);
-    R Tn = T - dT;
-    Tn = Tn < R(200) ? R(200) : (Tn > R(1e4) ? R(1e4) : Tn);
-    R step = fabs(Tn - T);
+__device__ __forceinline__ double clampT(double T) { return T < 200.0 ? 200.0 : (T > 1e4 ? 1e4 : T); }
+__device__ __forceinline__ float clampTf(float T) { return T < 200.f ? 200.f : (T > 1e4f ? 1e4f : T); }
+
+// FP64 Newton from T; returns true on convergence
+__device__ __forceinline__ bool newton64(const Poly<double>& P, double e, double& T) {
+  for (int it = 0; it < 50; ++it) {
+    const double Tn = clampT(T - (P.e(T) - e) / P.cv(T));
+    const double step = fabs(Tn - T);
     T = Tn;
-    if (step <= tol * T) return it;
+    if (step <= 1e-12 * T) return true;
   }
-  return -1;
+  return false;
 }
 
 template <typename T>
-__global__ void thermo_update_kernel(const T* u, int64_t K, int np, int dim, const double* sp,
-                                     double* Tc, T* pc, unsigned long long* status, int mixed) {
+__global__ void thermo_update_kernel(const T* u, int64_t K, int np, int dim, const double* cf,
+                                     const float* cf32, double* Tc, T* pc,
+                                     unsigned long long* status, int mixed) {
   const int nv = NSPEC + dim + 1;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < K * np;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t k = i / np;
     const int node = (int)(i % np);
     const T* uu = u + k * nv * np + node;
-    double rs[NSPEC], rho = 0.0, ke = 0.0;
+    double Y[NSPEC], rho = 0.0, ke = 0.0;
 #pragma unroll
     for (int s = 0; s < NSPEC; ++s) {
-      rs[s] = (double)uu[s * np];
-      rho += rs[s];
+      Y[s] = (double)uu[s * np];
+      rho += Y[s];
     }
     for (int d = 0; d < dim; ++d) {
       const double m = (double)uu[(NSPEC + d) * np];
       ke += m * m;
     }
-    const double e = (double)uu[(NSPEC + dim) * np] / rho - 0.5 * ke / (rho * rho);
+    const double ir = 1.0 / rho;
+    const double e = (double)uu[(NSPEC + dim) * np] * ir - 0.5 * ke * ir * ir;
+#pragma unroll
+    for (int s = 0; s < NSPEC; ++s) Y[s] *= ir;
     double Tk = Tc[k * np + node];
     if (!(Tk >= 200.0 && Tk <= 1e4)) Tk = 1000.0;
-    bool ok = rho > 0.0;
     Poly<double> P;
-    double Y[NSPEC];
-#pragma unroll
-    for (int s = 0; s < NSPEC; ++s) Y[s] = rs[s] / rho;
+    build_poly<double>(cf, Y, P);
     if (mixed) {
-      // FP32 iterations, then FP64 Newton steps on the FP64 residual
       Poly<float> Pf;
       float Yf[NSPEC];
 #pragma unroll
       for (int s = 0; s < NSPEC; ++s) Yf[s] = (float)Y[s];
-      build_poly<float>(sp, Yf, Pf);
+      build_poly<float>(cf32, Yf, Pf);
+      const float er = (float)(e - P.b[0]);
       float Tf = (float)Tk;
-      newton<float>(Pf, (float)e, Tf, 1e-6f, 30);
+      for (int it = 0; it < 12; ++it) {
+        const float Tn = clampTf(Tf - (Pf.e_noconst(Tf) - er) / Pf.cv(Tf));
+        const float step = fabsf(Tn - Tf);
+        Tf = Tn;
+        if (step <= 1e-6f * Tf) break;
+      }
       Tk = (double)Tf;
     }
-    build_poly<double>(sp, Y, P);
-    ok = ok && newton<double>(P, e, Tk, 1e-12, 50) > 0;
+    const bool ok = rho > 0.0 && newton64(P, e, Tk);
     if (!ok) latch(status, DG_ST_NEWTON, k);
     Tc[k * np + node] = Tk;
     const double p = rho * P.Rmix * Tk;
     const double cv = P.cv(Tk);
-    const double c = sqrt((cv + P.Rmix) / cv * p / rho);
     pc[(k * 2 + 0) * np + node] = (T)p;
-    pc[(k * 2 + 1) * np + node] = (T)c;
+    pc[(k * 2 + 1) * np + node] = (T)sqrt((cv + P.Rmix) / cv * p * ir);
   }
 }
 
 // (rho_s, v, T) -> conserved and (p, c); also seeds the temperature cache
 template <typename T>
 __global__ void thermo_prim2cons_kernel(const double* w, T* u, int64_t K, int np, int dim,
-                                        const double* sp, double* Tc, T* pc) {
+                                        const double* cf, double* Tc, T* pc) {
   const int nv = NSPEC + dim + 1;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < K * np;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -151,7 +154,7 @@ __global__ void thermo_prim2cons_kernel(const double* w, T* u, int64_t K, int np
     }
     const double Tk = ww[(NSPEC + dim) * np];
     Poly<double> P;
-    build_poly<double>(sp, Y, P);
+    build_poly<double>(cf, Y, P);
     uu[(NSPEC + dim) * np] = (T)(rho * (P.e(Tk) + 0.5 * ke));
     if (Tc) Tc[k * np + node] = Tk;
     if (pc) {
@@ -188,9 +191,25 @@ cudaError_t dg_thermo_init(DgThermo* th, int64_t K, int np, int dim, const doubl
   th->mode = mode;
   th->f32 = f32;
   th->status = status;
+  // per-species coefficient rows (see the header comment)
+  double cf[8 * NSPEC];
+  float cf32[8 * NSPEC];
+  for (int s = 0; s < NSPEC; ++s) {
+    const double* sp = species_host + 8 * s;
+    const double Rs = DG_RU / sp[0];
+    const double* a = sp + 1;
+    const double row[8] = {Rs * a[5], Rs * (a[0] - 1.0), Rs * a[1] / 2.0, Rs * a[2] / 3.0,
+                           Rs * a[3] / 4.0, Rs * a[4] / 5.0, Rs, 0.0};
+    for (int k = 0; k < 8; ++k) {
+      cf[8 * s + k] = row[k];
+      cf32[8 * s + k] = (float)row[k];
+    }
+  }
   const size_t rs = f32 ? sizeof(float) : sizeof(double);
-  cudaError_t e = cudaMalloc((void**)&th->species, sizeof(double) * 8 * NSPEC);
-  if (e == cudaSuccess) e = cudaMemcpy(th->species, species_host, sizeof(double) * 8 * NSPEC, cudaMemcpyHostToDevice);
+  cudaError_t e = cudaMalloc((void**)&th->species, sizeof(cf));
+  if (e == cudaSuccess) e = cudaMemcpy(th->species, cf, sizeof(cf), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&th->coef32, sizeof(cf32));
+  if (e == cudaSuccess) e = cudaMemcpy(th->coef32, cf32, sizeof(cf32), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMalloc((void**)&th->T, sizeof(double) * K * np);
   if (e == cudaSuccess) e = cudaMalloc(&th->pc, rs * 2 * K * np);
   if (e == cudaSuccess) e = cudaMalloc(&th->bc_pc, rs * 2 * 64);
@@ -206,6 +225,7 @@ void dg_thermo_free(DgThermo* th) {
   if (th->mlp) cudaFree(th->mlp);
   if (th->mlp_stats) cudaFree(th->mlp_stats);
   if (th->species) cudaFree(th->species);
+  if (th->coef32) cudaFree(th->coef32);
   if (th->T) cudaFree(th->T);
   if (th->pc) cudaFree(th->pc);
   if (th->bc_pc) cudaFree(th->bc_pc);
@@ -222,10 +242,12 @@ cudaError_t dg_thermo_update(DgThermo* th, const void* u, int f32, cudaStream_t 
   if (th->mode == 1 && th->mlp) return dg_mlp_thermo_update(th, u, f32, s);
   if (f32)
     thermo_update_kernel<float><<<grid_of(th->K * th->np), 256, 0, s>>>(
-        (const float*)u, th->K, th->np, th->dim, th->species, th->T, (float*)th->pc, th->status, 1);
+        (const float*)u, th->K, th->np, th->dim, th->species, th->coef32, th->T, (float*)th->pc,
+        th->status, 1);
   else
     thermo_update_kernel<double><<<grid_of(th->K * th->np), 256, 0, s>>>(
-        (const double*)u, th->K, th->np, th->dim, th->species, th->T, (double*)th->pc, th->status, 0);
+        (const double*)u, th->K, th->np, th->dim, th->species, th->coef32, th->T,
+        (double*)th->pc, th->status, 0);
   return cudaGetLastError();
 }
 

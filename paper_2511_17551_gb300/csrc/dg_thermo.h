@@ -7,7 +7,8 @@
 struct DgThermo {
   int64_t K;
   int np, dim, ns, mode, f32;
-  double* species;     // device [ns][8]
+  double* species;     // device [ns][8] e(T) polynomial coefficient rows per species
+  float* coef32;       // device [ns][8] FP32 copy
   double* T;           // device [K][np] temperature cache (FP64)
   void* pc;            // device [K][2][np] pressure, sound speed (form precision)
   void* bc_pc;         // device [n_bc][2]
