@@ -49,6 +49,14 @@ __device__ __forceinline__ float gelu_f(float x) {
   const float k = 0.7978845608028654f;  // sqrt(2/pi)
   return 0.5f * x * (1.0f + tanhf(k * (x + 0.044715f * x * x * x)));
 }
+// inference GELU: the hardware tanh approximation (tanh.approx.f32, relative error about
+// 2^-11), below the BF16 rounding of the layer inputs
+__device__ __forceinline__ float gelu_fast(float x) {
+  const float k = 0.7978845608028654f;
+  float z = k * (x + 0.044715f * x * x * x), t;
+  asm("tanh.approx.f32 %0, %1;" : "=f"(t) : "f"(z));
+  return 0.5f * x * (1.0f + t);
+}
 __device__ __forceinline__ float gelu_d_f(float x) {
   const float k = 0.7978845608028654f;
   float t = tanhf(k * (x + 0.044715f * x * x * x));
@@ -86,7 +94,7 @@ __device__ __forceinline__ void mlp16(const DgMlpDev& m, const float (*feat)[17]
     const uint32_t* w = reinterpret_cast<const uint32_t*>(m.W1 + (8 * nt + g) * 16);
     mma_bf16(h[nt], A, w[t], w[t + 4]);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) h[nt][q] = gelu_f(h[nt][q]);
+    for (int q = 0; q < 4; ++q) h[nt][q] = gelu_fast(h[nt][q]);
   }
   uint32_t A2[4][4];
 #pragma unroll
@@ -106,8 +114,8 @@ __device__ __forceinline__ void mlp16(const DgMlpDev& m, const float (*feat)[17]
       const uint32_t* w = reinterpret_cast<const uint32_t*>(m.W2 + (8 * nt + g) * NH + 16 * kb);
       mma_bf16(o, A2[kb], w[t], w[t + 4]);
     }
-    yg += m.w3[col] * gelu_f(o[0]) + m.w3[col + 1] * gelu_f(o[1]);
-    yg8 += m.w3[col] * gelu_f(o[2]) + m.w3[col + 1] * gelu_f(o[3]);
+    yg += m.w3[col] * gelu_fast(o[0]) + m.w3[col + 1] * gelu_fast(o[1]);
+    yg8 += m.w3[col] * gelu_fast(o[2]) + m.w3[col + 1] * gelu_fast(o[3]);
   }
   yg += __shfl_xor_sync(0xffffffffu, yg, 1);
   yg += __shfl_xor_sync(0xffffffffu, yg, 2);
@@ -214,9 +222,12 @@ thermo_mlp_kernel(const T* u, int64_t K, int np, int dim, const double* sp, doub
       PolyD P;
       poly_d(sp, Y, P);
       double T0 = clampT((double)(m.muT + m.sigT * yv[w][lane]));
-      double T1 = clampT(T0 - (P.e(T0) - e) / P.cv(T0));
+      // FP64 residuals; cv only scales the correction, FP32 is enough for it
+      const float cv0 = (float)P.b[1] + (float)T0 * (2.f * (float)P.b[2] + (float)T0 *
+                        (3.f * (float)P.b[3] + (float)T0 * (4.f * (float)P.b[4] + (float)T0 * 5.f * (float)P.b[5])));
+      double T1 = clampT(T0 - (P.e(T0) - e) / (double)cv0);
       const double r1 = P.e(T1) - e;
-      if (fabs(r1) <= 1e-6 * P.cv(T1) * T1) {
+      if (fabs(r1) <= 1e-6 * (double)cv0 * T1) {
         ++n_ok;
       } else {
         // fallback: the plain Newton iteration from the polished value

@@ -108,13 +108,29 @@ __global__ void thermo_update_kernel(const T* u, int64_t K, int np, int dim, con
       build_poly<float>(cf32, Yf, Pf);
       const float er = (float)(e - P.b[0]);
       float Tf = (float)Tk;
+      bool conv = false;
       for (int it = 0; it < 12; ++it) {
         const float Tn = clampTf(Tf - (Pf.e_noconst(Tf) - er) / Pf.cv(Tf));
         const float step = fabsf(Tn - Tf);
         Tf = Tn;
-        if (step <= 1e-6f * Tf) break;
+        if (step <= 1e-6f * Tf) {
+          conv = true;
+          break;
+        }
       }
-      Tk = (double)Tf;
+      // the FP64 final residual: one Newton correction on e64(T) - e (cv in FP32 is
+      // accurate enough for a correction of relative size <= 1e-6); further FP64
+      // iterations only when the FP32 stage did not converge
+      double T64 = (double)Tf;
+      T64 = clampT(T64 - (P.e(T64) - e) / (double)Pf.cv(Tf));
+      bool ok = rho > 0.0 && (conv || newton64(P, e, T64));
+      if (!ok) latch(status, DG_ST_NEWTON, k);
+      Tc[k * np + node] = T64;
+      const float Tq = (float)T64, rhof = (float)rho;
+      const float pf = rhof * Pf.Rmix * Tq, cvf = Pf.cv(Tq);
+      pc[(k * 2 + 0) * np + node] = (T)pf;
+      pc[(k * 2 + 1) * np + node] = (T)sqrtf((cvf + Pf.Rmix) / cvf * pf / rhof);
+      continue;
     }
     const bool ok = rho > 0.0 && newton64(P, e, Tk);
     if (!ok) latch(status, DG_ST_NEWTON, k);
