@@ -50,6 +50,7 @@ class Problem(C.Structure):
         ("n_bc", C.c_int), ("bc_kind", C.c_void_p), ("bc_prim", C.c_void_p),
         ("species", C.c_void_p), ("Ja", C.c_void_p), ("J", C.c_void_p),
         ("alpha_override", C.c_double),
+        ("n_reactions", C.c_int), ("reactions", C.c_void_p), ("chem_dt", C.c_double),
     ]
 
 
@@ -78,6 +79,7 @@ def lib():
             "or_mixture_eval": (i, [i, vp, i, vp, vp, vp, vp]),
             "or_temperature_field": (i, [vp, vp, vp]),
             "or_mlp_nparams": (i, []),
+            "or_chem_eval": (i, [vp, i, vp, i, vp, vp, d, vp, vp, vp]),
             "or_gelu": (d, [d]),
             "or_gelu_d": (d, [d]),
             "or_mlp_forward": (None, [vp, i, vp, vp]),
@@ -136,7 +138,7 @@ class Oracle:
     def __init__(self, dim, N, xyz, nbr_elem, nbr_face, *, n_species=0, equations=EULER,
                  volume_flux=VF_RANOCHA, surface_flux=SF_LLF, gamma=1.4, mu=0.0, Pr=0.72,
                  alpha_max=0.0, bc_kind=None, bc_prim=None, species=None,
-                 alpha_override=-1.0):
+                 alpha_override=-1.0, reactions=None, chem_dt=0.0):
         self.dim, self.N = dim, N
         self.np = (N + 1) ** dim
         self.nv = lib().or_nv(dim, n_species)
@@ -150,6 +152,8 @@ class Oracle:
             bc_prim if bc_prim is not None else np.zeros((1, self.nv)), dtype=np.float64)
         self.species = (np.ascontiguousarray(species, dtype=np.float64)
                         if species is not None else None)
+        self.reactions = (np.ascontiguousarray(reactions, dtype=np.float64)
+                          if reactions is not None else None)
         self.P = Problem(dim=dim, N=N, K=self.K, n_species=n_species, equations=equations,
                          volume_flux=volume_flux, surface_flux=surface_flux, gamma=gamma,
                          mu=mu, Pr=Pr, alpha_max=alpha_max,
@@ -157,7 +161,9 @@ class Oracle:
                          n_bc=len(self.bc_kind) if bc_kind is not None else 0,
                          bc_kind=_p(self.bc_kind), bc_prim=_p(self.bc_prim),
                          species=_p(self.species), Ja=_p(self.Ja), J=_p(self.J),
-                         alpha_override=alpha_override)
+                         alpha_override=alpha_override,
+                         n_reactions=0 if reactions is None else len(self.reactions),
+                         reactions=_p(self.reactions), chem_dt=chem_dt)
 
     def _ref(self):
         return C.byref(self.P)
@@ -256,6 +262,19 @@ def mixture_temperature(species, Y, e, T0=None):
     bad = lib().or_mixture_temperature(species.shape[0], _p(species), len(e), _p(Y), _p(e),
                                        _p(T0), _p(T), _p(it))
     return T, it, bool(bad)
+
+
+def chem_eval(species, reactions, rhos, T, dt=0.0):
+    """omega, diagonal Jacobian and point-implicit source for states rhos [n][5], T [n]."""
+    species = np.ascontiguousarray(species, dtype=np.float64)
+    reactions = np.ascontiguousarray(reactions, dtype=np.float64)
+    rhos = np.ascontiguousarray(rhos, dtype=np.float64)
+    T = np.ascontiguousarray(T, dtype=np.float64)
+    n = len(T)
+    om, jd, S = np.zeros((n, 5)), np.zeros((n, 5)), np.zeros((n, 5))
+    lib().or_chem_eval(_p(species), len(reactions), _p(reactions), n, _p(rhos), _p(T), dt, _p(om),
+                       _p(jd), _p(S))
+    return om, jd, S
 
 
 def mlp_nparams():

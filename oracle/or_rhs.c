@@ -410,6 +410,15 @@ int or_rhs(const or_problem* P, const double* u, double* rhs, double* alpha_out,
       for (int v = 0; v < nv; ++v)
         rhs[((size_t)k * nv + v) * np + node] = -acc[v * np + node] / Jn;
     }
+    /* finite-rate species sources (Eq. source_term) */
+    if (P->n_reactions > 0 && P->n_species == 5) {
+      for (int node = 0; node < np; ++node) {
+        double S[5];
+        or_chem_source(P->species, P->n_reactions, P->reactions, qe[node].rhos, qe[node].T,
+                       P->chem_dt, S);
+        for (int s = 0; s < 5; ++s) rhs[((size_t)k * nv + s) * np + node] += S[s];
+      }
+    }
     free(acc); free(ue); free(qe);
   }
   if (P->equations == OR_NAVIER_STOKES) {
@@ -556,7 +565,9 @@ int or_step_rk(const or_problem* P, double* u, int nsteps, double cfl, double dt
   for (int st = 0; st < nsteps && !err; ++st) {
     double dt = dt_fixed > 0.0 ? dt_fixed : or_max_dt(P, u, cfl);
     for (int s = 0; s < 5 && !err; ++s) {
-      err |= or_rhs(P, u, r, NULL, NULL);
+      or_problem Q = *P;
+      Q.chem_dt = dt; /* point-implicit scaling of the chemistry source uses the step */
+      err |= or_rhs(&Q, u, r, NULL, NULL);
       for (size_t i = 0; i < n; ++i) {
         du[i] = (s == 0 ? 0.0 : A[s] * du[i]) + dt * r[i];
         u[i] += B[s] * du[i];

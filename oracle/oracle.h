@@ -52,6 +52,9 @@ typedef struct {
   const double* Ja;         /* [K][dim][dim][np] */
   const double* J;          /* [K][np] */
   double alpha_override;    /* >= 0: use this blending factor on every element */
+  int n_reactions;          /* finite-rate chemistry (5 species), 0 = frozen */
+  const double* reactions;  /* [n_reactions][19] */
+  double chem_dt;           /* point-implicit time scale of the source; 0 = explicit */
 } or_problem;
 
 typedef struct {
@@ -113,6 +116,14 @@ int or_step_rk(const or_problem* P, double* u, int nsteps, double cfl, double dt
 int or_diagnostics(const or_problem* P, const double* u, double* out);
 void or_ck45(double* A, double* B, double* c);
 int or_temperature_field(const or_problem* P, const double* u, double* T);
+
+/* ---- finite-rate chemistry (or_thermo_chem.c) ---- */
+int or_chem_omega(const double* species, int nr, const double* reac, const double* rhos, double T,
+                  double* omega, double* jdiag);
+int or_chem_source(const double* species, int nr, const double* reac, const double* rhos, double T,
+                   double dt, double* S);
+int or_chem_eval(const double* species, int nr, const double* reac, int n, const double* rhos,
+                 const double* T, double dt, double* omega, double* jdiag, double* S);
 
 /* ---- learned temperature surrogate (or_mlp.c) ---- */
 int or_mlp_nparams(void);

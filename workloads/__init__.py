@@ -184,8 +184,9 @@ def species_table(seed=5, ns=5):
 
     Atom masses a, b ~ U[14,16] g/mol; cp/R = c0 + c1 tau + .. + c4 tau^4 with
     tau = T/1000 K, c0 ~ U[2.5,3.5], c_k ~ U[0,1]*(0.2, 0.02, 1e-3, 3e-5)
-    (all >= 0: cp > 0 and increasing on 200..1e4 K); a6 ~ U[-2e4,2e4] K,
-    a7 ~ U[0,20].
+    (all >= 0: cp > 0 and increasing on 200..1e4 K); a7 ~ U[0,20].  Formation
+    constants a6 (K): atoms U[2e4, 5e4], molecules U[-1e4, 1e4], so that the
+    molecules are bound (dissociation is endothermic, dH/R in 3e4..1.1e5 K).
     """
     rng = np.random.default_rng(seed)
     a, b = rng.uniform(14.0, 16.0, size=2)
@@ -199,7 +200,9 @@ def species_table(seed=5, ns=5):
     tab[:, 3] = ck[:, 1] / 1e6
     tab[:, 4] = ck[:, 2] / 1e9
     tab[:, 5] = ck[:, 3] / 1e12
-    tab[:, 6] = rng.uniform(-2e4, 2e4, size=ns)
+    a6 = rng.uniform(-1e4, 1e4, size=5)
+    a6[:2] = rng.uniform(2e4, 5e4, size=2)  # atoms A, B
+    tab[:, 6] = a6[:ns]
     tab[:, 7] = rng.uniform(0.0, 20.0, size=ns)
     return tab
 
@@ -243,13 +246,17 @@ def mixture_primitive(xyz, rho, vel, T, seed=7, ns=5, hot=None, cylinder=None):
     return w
 
 
-def reaction_table(seed=11, nr=17, n_third=4):
+def reaction_table(seed=11, nr=17, n_third=4, species=None):
     """Seeded element-balanced mechanism over species {A,B,A2,B2,AB}.
 
     Rows: [nu_f(5), nu_b(5), third_body_flag, eff(5), A, beta, theta].
-    A log-uniform in [1e9,1e22], beta U[-1.5,0.5], theta U[0,1.2e5] K,
-    third-body efficiencies U[0.2,22].
+    A log-uniform in [1e9,1e22], beta U[-1.5,0.5], third-body efficiencies U[0.2,22].
+    Activation temperature theta = max(0, dH_r/R) + U[0, 1e4] K (capped at 1.2e5 K),
+    dH_r/R = sum_s dnu_s a6_s from the species' formation constants, so the backward
+    activation theta - dH/R is never negative (no recombination rate that grows
+    without bound as T falls).
     """
+    sp = species if species is not None else species_table()
     A_, B_, A2, B2, AB = range(5)
     pool = []
     for X2, prods in ((A2, (A_, A_)), (B2, (B_, B_)), (AB, (A_, B_))):
@@ -274,7 +281,8 @@ def reaction_table(seed=11, nr=17, n_third=4):
         rows[r, 11:16] = rng.uniform(0.2, 22.0, size=5) if tb else 0.0
         rows[r, 16] = 10.0 ** rng.uniform(9.0, 22.0)
         rows[r, 17] = rng.uniform(-1.5, 0.5)
-        rows[r, 18] = rng.uniform(0.0, 1.2e5)
+        dH = float((rows[r, 5:10] - rows[r, 0:5]) @ sp[:, 6])
+        rows[r, 18] = min(1.2e5, max(0.0, dH) + rng.uniform(0.0, 1e4))
     return rows
 
 
