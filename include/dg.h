@@ -87,6 +87,10 @@ typedef struct {
   const int* bc_kind;       /* host [n_bc]: DG_BC_* */
   const double* bc_prim;    /* host [n_bc][nv]: external primitive states */
   void* stream;             /* cudaStream_t to queue work on, or NULL for a private stream */
+  const double* reactions;  /* host [n_reactions][19] finite-rate mechanism (mixtures):
+                               nu'(5), nu''(5), third-body flag, efficiencies(5), A, beta,
+                               theta = E/R_u (appendix, Eqs. chemreact..calc_prod), or NULL */
+  int n_reactions;          /* 0: frozen mixture; 1..64 */
 } dg_physics_desc;
 
 /* LGL nodes and weights used by libdg for degree N (host arrays of N+1).

@@ -59,7 +59,7 @@ class PhysicsDesc(C.Structure):
                 ("volume_flux", C.c_int), ("surface_flux", C.c_int),
                 ("alpha_max", C.c_double), ("precision", C.c_int), ("thermo", C.c_int),
                 ("n_bc", C.c_int), ("bc_kind", C.c_void_p), ("bc_prim", C.c_void_p),
-                ("stream", C.c_void_p)]
+                ("stream", C.c_void_p), ("reactions", C.c_void_p), ("n_reactions", C.c_int)]
 
 
 _lib = None
@@ -275,7 +275,8 @@ class Solver:
     def __init__(self, dim, N, xyz, nbr_elem, nbr_face, *, n_species=0, equations=DG_EULER,
                  gamma=1.4, mu=0.0, Pr=0.72, species=None, volume_flux=DG_VF_RANOCHA,
                  surface_flux=DG_SF_LLF, alpha_max=0.0, precision=DG_FP64,
-                 thermo=DG_THERMO_NEWTON, bc_kind=None, bc_prim=None, stream=None):
+                 thermo=DG_THERMO_NEWTON, bc_kind=None, bc_prim=None, stream=None,
+                 reactions=None):
         self.dim, self.N = dim, N
         self.np = (N + 1) ** dim
         self.nsp = max(1, n_species)
@@ -290,13 +291,17 @@ class Solver:
         self._bck = np.ascontiguousarray(bc_kind if bc_kind is not None else [1], dtype=np.int32)
         self._bcp = np.ascontiguousarray(bc_prim if bc_prim is not None else np.zeros((1, self.nv)),
                                          dtype=np.float64)
+        self._reac = (np.ascontiguousarray(reactions, dtype=np.float64)
+                      if reactions is not None else None)
         mesh = MeshDesc(dim=dim, N=N, K=self.K, node_xyz=_ptr(self._xyz), nbr_elem=_ptr(self._nbr),
                         nbr_face=_ptr(self._face), nbr_orient=None)
         phys = PhysicsDesc(equations=equations, n_species=n_species, gamma=gamma, mu=mu, Pr=Pr,
                            species=_ptr(self._species), volume_flux=volume_flux,
                            surface_flux=surface_flux, alpha_max=alpha_max, precision=precision,
                            thermo=thermo, n_bc=len(self._bck) if bc_kind is not None else 0,
-                           bc_kind=_ptr(self._bck), bc_prim=_ptr(self._bcp), stream=stream)
+                           bc_kind=_ptr(self._bck), bc_prim=_ptr(self._bcp), stream=stream,
+                           reactions=_ptr(self._reac),
+                           n_reactions=0 if reactions is None else len(self._reac))
         self.ctx = dg_init_mesh(mesh, phys)
 
     @property

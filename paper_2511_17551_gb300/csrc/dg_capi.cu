@@ -384,6 +384,15 @@ cudaError_t pre_rhs(dg_ctx* c, DgArgs& a) {
   if (c->n_species > 0) {
     e = run_thermo(c, a.u);
     if (e != cudaSuccess) return e;
+    if (c->th.nr > 0) {
+      // species sources; point-implicit with the running step in RK stages
+      e = timed(c, DG_PROF_CHEM, [&] {
+        return dg_chem_source(&c->th, a.u, c->precision == DG_MIXED, a.mode == 1 ? c->scal + 1 : NULL,
+                              c->stream);
+      });
+      if (e != cudaSuccess) return e;
+      a.src = c->th.src;
+    }
   }
   if (c->equations == DG_NAVIER_STOKES) {
     e = run_grad(c, a);
@@ -484,6 +493,8 @@ dg_status dg_init_mesh(const dg_mesh_desc* m, const dg_physics_desc* p, dg_ctx**
   if (p->n_species < 0 || p->n_species > DG_MAX_SPECIES) return DG_EINVAL;
   if (!supported_degree(m->dim, m->N, p->n_species)) return DG_EINVAL;
   if (p->n_species > 0 && (p->n_species != 5 || !p->species || p->n_bc > 64)) return DG_EINVAL;
+  if (p->n_reactions < 0 || p->n_reactions > 64 || (p->n_reactions > 0 && (!p->reactions || p->n_species != 5)))
+    return DG_EINVAL;
   if (p->equations != DG_EULER && p->equations != DG_NAVIER_STOKES) return DG_EINVAL;
   if (p->equations == DG_NAVIER_STOKES && (p->n_species > 0 || m->dim != 3 || !(p->mu > 0) ||
                                            !(p->Pr > 0)))
@@ -632,6 +643,11 @@ dg_status dg_init_mesh(const dg_mesh_desc* m, const dg_physics_desc* p, dg_ctx**
     if (c->n_species > 0) {
       if (dg_thermo_init(&c->th, K, c->np, dim, p->species, p->thermo, c->precision == DG_MIXED,
                          c->status) != cudaSuccess) {
+        st = DG_ENOMEM;
+        goto fail;
+      }
+      if (p->n_reactions > 0 &&
+          dg_chem_init(&c->th, p->species, p->reactions, p->n_reactions) != cudaSuccess) {
         st = DG_ENOMEM;
         goto fail;
       }

@@ -39,6 +39,7 @@ struct DgArgs {
   const void* bc_u;       // [n_bc][nv] conserved boundary states
   const void* pc;         // mixtures: [K][2][np] pressure and sound speed
   const void* bc_pc;      // mixtures: [n_bc][2]
+  const void* src;        // mixtures with chemistry: [K][nsp][np] species source, or null
   double* scal;           // device scalars: [0] t, [1] dt of the running step
   unsigned long long* lam;  // [2 slots][2] wave-speed maxima as ordered double bits
   unsigned long long* status;

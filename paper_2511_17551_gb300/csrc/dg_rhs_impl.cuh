@@ -428,7 +428,9 @@ rhs_kernel(const DgArgs a, const KConst kc) {
         real sum = 0;
 #pragma unroll
         for (int d = 0; d < DIM; ++d) sum += sa[(d * NV + k) * NP];
-        out[gbase + k * NP] = -ij * sum;
+        real r = -ij * sum;
+        if (NSP > 1 && k < NSP && a.src) r += ((const real*)a.src)[((e0 + e) * NSP + k) * NP + node];
+        out[gbase + k * NP] = r;
       }
     } else {
       real* out = (real*)a.out;
@@ -440,7 +442,8 @@ rhs_kernel(const DgArgs a, const KConst kc) {
         real sum = 0;
 #pragma unroll
         for (int d = 0; d < DIM; ++d) sum += sa[(d * NV + k) * NP];
-        const real r = -ij * sum;
+        real r = -ij * sum;
+        if (NSP > 1 && k < NSP && a.src) r += ((const real*)a.src)[((e0 + e) * NSP + k) * NP + node];
         real dn = (a.stage == 0 ? real(0) : kc.rkA * du[gbase + k * NP]) + dt * r;
         du[gbase + k * NP] = dn;
         un[k] = su[(e * NV + k) * NP + node] + kc.rkB * dn;

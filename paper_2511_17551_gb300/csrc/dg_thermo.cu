@@ -242,6 +242,9 @@ void dg_thermo_free(DgThermo* th) {
   if (th->mlp_stats) cudaFree(th->mlp_stats);
   if (th->species) cudaFree(th->species);
   if (th->coef32) cudaFree(th->coef32);
+  if (th->species_raw) cudaFree(th->species_raw);
+  if (th->reac) cudaFree(th->reac);
+  if (th->src) cudaFree(th->src);
   if (th->T) cudaFree(th->T);
   if (th->pc) cudaFree(th->pc);
   if (th->bc_pc) cudaFree(th->bc_pc);

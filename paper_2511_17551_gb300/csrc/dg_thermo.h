@@ -13,6 +13,10 @@ struct DgThermo {
   void* pc;            // device [K][2][np] pressure, sound speed (form precision)
   void* bc_pc;         // device [n_bc][2]
   unsigned long long* status;
+  double* species_raw; // device [ns][8] W, a1..a7 (chemistry)
+  double* reac;        // device [nr][20] reaction rows (ln A in slot 16)
+  int nr;              // number of reactions, 0 = frozen
+  void* src;           // device [K][ns][np] chemistry source (form precision)
   void* mlp;           // surrogate weights (device) or null
   unsigned long long* mlp_stats;  // [accepted, fallback] node counts of the surrogate
 };
@@ -25,6 +29,9 @@ cudaError_t dg_thermo_reset(DgThermo* th, cudaStream_t s);
 cudaError_t dg_thermo_update(DgThermo* th, const void* u, int f32, cudaStream_t s);
 cudaError_t dg_thermo_boundary(DgThermo* th, const double* bw, int n_bc, void* bc_u, cudaStream_t s);
 cudaError_t dg_thermo_prim2cons(DgThermo* th, const double* w, void* u, cudaStream_t s);
+// chemistry (dg_chem.cu)
+cudaError_t dg_chem_init(DgThermo* th, const double* species_host, const double* reac_host, int nr);
+cudaError_t dg_chem_source(DgThermo* th, const void* u, int f32, const double* dt_dev, cudaStream_t s);
 // surrogate (dg_mlp.cu)
 cudaError_t dg_mlp_set(DgThermo* th, const float* params_host, const double* stats_host);
 cudaError_t dg_mlp_thermo_update(DgThermo* th, const void* u, int f32, cudaStream_t s);
