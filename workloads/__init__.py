@@ -240,9 +240,10 @@ def mixture_primitive(xyz, rho, vel, T, seed=7, ns=5, hot=None, cylinder=None):
         w[:, ns + 1] = U * R * R * zi2
     w[:, ns + dim] = T
     if hot is not None:
+        # smooth hot layer around the z axis: T + (T_hot - T) exp(-(r / rad)^4)
         rad, Th = hot
         r = np.sqrt(xyz[:, 0] ** 2 + xyz[:, 1] ** 2)
-        w[:, ns + dim] = np.where(r < rad, Th, T)
+        w[:, ns + dim] = T + (Th - T) * np.exp(-(r / rad) ** 4)
     return w
 
 
@@ -250,11 +251,13 @@ def reaction_table(seed=11, nr=17, n_third=4, species=None):
     """Seeded element-balanced mechanism over species {A,B,A2,B2,AB}.
 
     Rows: [nu_f(5), nu_b(5), third_body_flag, eff(5), A, beta, theta].
-    A log-uniform in [1e9,1e22], beta U[-1.5,0.5], third-body efficiencies U[0.2,22].
-    Activation temperature theta = max(0, dH_r/R) + U[0, 1e4] K (capped at 1.2e5 K),
+    beta U[-1.5,0.5]; A = 10^U[9,12] / 5000^beta, so that the rate constant at 5000 K is
+    1e9..1e12 cm^3/(mol s) (chemical time scales near the flow step; A within [1e9, 1e22]);
+    third-body efficiencies U[0.2,22].  Activation temperature theta = max(0, dH_r/R) +
+    U[0, 1e4] K for dissociations and + U[1e4, 3e4] K for exchanges (capped at 1.2e5 K),
     dH_r/R = sum_s dnu_s a6_s from the species' formation constants, so the backward
-    activation theta - dH/R is never negative (no recombination rate that grows
-    without bound as T falls).
+    activation theta - dH/R is never negative (no recombination rate that grows without
+    bound as T falls).
     """
     sp = species if species is not None else species_table()
     A_, B_, A2, B2, AB = range(5)
@@ -279,10 +282,13 @@ def reaction_table(seed=11, nr=17, n_third=4, species=None):
             rows[r, 5 + s] += 1
         rows[r, 10] = tb
         rows[r, 11:16] = rng.uniform(0.2, 22.0, size=5) if tb else 0.0
-        rows[r, 16] = 10.0 ** rng.uniform(9.0, 22.0)
-        rows[r, 17] = rng.uniform(-1.5, 0.5)
-        dH = float((rows[r, 5:10] - rows[r, 0:5]) @ sp[:, 6])
-        rows[r, 18] = min(1.2e5, max(0.0, dH) + rng.uniform(0.0, 1e4))
+        beta = rng.uniform(-1.5, 0.5)
+        rows[r, 16] = min(1e22, max(1e9, 10.0 ** rng.uniform(9.0, 12.0) / 5000.0 ** beta))
+        rows[r, 17] = beta
+        dnu = rows[r, 5:10] - rows[r, 0:5]
+        dH = float(dnu @ sp[:, 6])
+        margin = rng.uniform(0.0, 1e4) if dnu.sum() > 0 else rng.uniform(1e4, 3e4)
+        rows[r, 18] = min(1.2e5, max(0.0, dH) + margin)
     return rows
 
 
