@@ -208,8 +208,13 @@ def run_ours(args, rank, world, local_rank):
         "gpu_launches": launches,
         "clocks": clk,
     }
+    out["arith_peaks_tflops"] = {"fp64_fma": dg.dg_peak_flops(dg.DG_FP64, 4000),
+                                 "fp32_fma": dg.dg_peak_flops(dg.DG_MIXED, 20000),
+                                 "source": "measured here, FMA chains, 152x8 CTAs"}
     if not args.no_mixture:
         out["mixture"] = run_mixture(args, stream.cuda_stream, world)
+    if not args.no_reacting:
+        out["reacting"] = run_reacting(args, stream.cuda_stream, world)
     if rank == 0:
         if not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline(cfg, args.cpu_seconds)
@@ -312,6 +317,53 @@ def run_mixture(args, stream_ptr, world):
     return out
 
 
+def run_reacting(args, stream_ptr, world):
+    """Five-species reacting mixture (17 reactions, FP64 finite-rate source with point-implicit
+    scaling) on a 48 x 48 x 16-element cylinder O-grid, N = 4, with a 3000 K layer round the
+    body: per-kernel device time per step in the mixed and the FP64 form, and the chemistry
+    kernel against the measured FP64 arithmetic peak."""
+    import torch
+    import paper_2511_17551_gb300 as dg
+    N = 4
+    nr, nth, nz = args.react_elements, args.react_elements, max(2, args.react_elements // 3)
+    xi, _ = dg.dg_lgl_nodes(N)
+    xyz, nbr, face = W.ogrid_mesh(xi, nr, nth, nz)
+    sp, R = W.species_table(), W.reaction_table()
+    u_inf = (2400.0, 0.0, 0.0)
+    w0 = W.mixture_primitive(xyz, rho=0.1, vel=u_inf, T=300.0, seed=7, cylinder=0.5,
+                             hot=(1.2, 3000.0))
+    fs = W.mixture_primitive(xyz[:1], rho=0.1, vel=u_inf, T=300.0, seed=7)[0, :, 0]
+    K, npn = xyz.shape[0], (N + 1) ** 3
+    dof = K * npn * 10
+    out = {"workload": "reacting_5sp_17r_ogrid_%dx%dx%d_N4" % (nr, nth, nz), "elements": K,
+           "dof": dof, "cfl": 0.05}
+    for name, prec, n in (("mixed", dg.DG_MIXED, args.react_steps),
+                          ("fp64", dg.DG_FP64, max(1, args.react_steps // 2))):
+        s = dg.Solver(3, N, xyz, nbr, face, n_species=5, species=sp, volume_flux=dg.DG_VF_DUCROS,
+                      surface_flux=dg.DG_SF_LLF, bc_kind=[1, 2, 3], bc_prim=np.stack([fs] * 3),
+                      alpha_max=0.5, precision=prec, reactions=R, stream=stream_ptr)
+        s.set_primitive(w0)
+        s.step(2, 0.05)
+        dg.dg_profile(s.ctx, 1)
+        dg.dg_profile_read(s.ctx)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s.step(n, 0.05)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        prof = dg.dg_profile_read(s.ctx)
+        dg.dg_profile(s.ctx, 0)
+        s.close()
+        chem_ms = prof["chem"][0] / max(1, prof["chem"][1])
+        out[name] = {"value": world * dof * 5 * n / wall, "unit": "DOF*RHS/s",
+                     "ms_per_step": wall * 1e3 / n, "steps": n,
+                     "chem_ms_per_launch": chem_ms,
+                     "chem_ns_per_node": chem_ms * 1e6 / (K * npn),
+                     "device_ms_per_step_by_kernel": {k: round(v[0] / n, 4)
+                                                      for k, v in prof.items() if v[1]}}
+    return out
+
+
 def cpu_baseline(cfg, budget_s):
     """The oracle as it stands, FP64, all host cores (OpenMP over elements)."""
     import oracle
@@ -384,6 +436,9 @@ def main():
     ap.add_argument("--mix-steps", type=int, default=40)
     ap.add_argument("--train-samples", type=int, default=1000000)
     ap.add_argument("--train-epochs", type=int, default=20)
+    ap.add_argument("--no-reacting", action="store_true")
+    ap.add_argument("--react-elements", type=int, default=48, help="O-grid radial/angular elements")
+    ap.add_argument("--react-steps", type=int, default=4)
     args = ap.parse_args()
     rank, world, local_rank = _env_rank()
     if args.impl == "reference":

@@ -202,6 +202,12 @@ enum { DG_PROF_RHS = 0, DG_PROF_GRAD = 1, DG_PROF_INDICATOR = 2, DG_PROF_LAMBDA 
 dg_status dg_profile(dg_ctx* ctx, int enable);
 dg_status dg_profile_read(dg_ctx* ctx, double* ms, int64_t* launches, int n);
 
+/* Measured arithmetic peak of the current device (no counterpart in the paper; the
+ * roofline denominator of arithmetic-bound kernels): chains of fused multiply-adds in
+ * FP64 (precision = DG_FP64) or FP32 (DG_MIXED), iters FMAs per chain, CUDA-event
+ * timed; *tflops = 2 flops per FMA / time.  Synchronises the device. */
+dg_status dg_peak_flops(int precision, int iters, double* tflops);
+
 /* Wait (bounded) for the context stream, then return and clear the latched
  * device status. */
 dg_status dg_sync(dg_ctx* ctx);

@@ -35,7 +35,7 @@ EXPORTED = [
     "dg_error_element", "dg_status_string", "dg_destroy", "dg_profile", "dg_profile_read",
     "dg_rhs_ns_noalloc", "dg_get_temperature", "dg_set_surrogate", "dg_surrogate_stats",
     "dg_thermo_sample", "dg_mlp_nparams", "dg_mlp_workspace_bytes", "dg_mlp_grad",
-    "dg_mlp_train_step", "dg_mlp_forward",
+    "dg_mlp_train_step", "dg_mlp_forward", "dg_peak_flops",
 ]
 PROF_KINDS = ["rhs", "gradients", "indicator", "lambda", "thermo", "mlp", "chem", "other"]
 
@@ -100,6 +100,7 @@ def lib():
             "dg_mlp_train_step": (i, [vp, vp, vp, vp, vp, i, i, C.c_float, vp, vp, C.c_size_t,
                                       vp]),
             "dg_mlp_forward": (i, [vp, vp, vp, vp, i64, i, vp]),
+            "dg_peak_flops": (i, [i, i, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(_lib, name)
@@ -219,6 +220,13 @@ def dg_mlp_forward(params, X, y, tensor_cores=1, stats=None, stream=None):
     s = None if stats is None else np.ascontiguousarray(stats, dtype=np.float64)
     _check(lib().dg_mlp_forward(_ptr(params), _ptr(s), _ptr(X), _ptr(y), y.shape[0],
                                 int(tensor_cores), stream), "dg_mlp_forward")
+
+
+def dg_peak_flops(precision, iters=20000):
+    """Measured FMA peak of the device in TFLOP/s (DG_FP64 or DG_MIXED = FP32)."""
+    t = C.c_double()
+    _check(lib().dg_peak_flops(precision, iters, C.byref(t)), "dg_peak_flops")
+    return t.value
 
 
 def dg_get_alpha(ctx, K):

@@ -22,9 +22,11 @@
 
 namespace {
 
-// integer powers 0, 1, 2 of the stoichiometric coefficients
+// c^nu for the small non-negative integer stoichiometric coefficients (0..3 here)
 __device__ __forceinline__ double ipow012(double c, double nu) {
-  return nu == 0.0 ? 1.0 : (nu == 1.0 ? c : c * c);
+  double r = 1.0;
+  for (int q = 0; q < (int)nu; ++q) r *= c;
+  return r;
 }
 
 template <typename T>
