@@ -56,6 +56,12 @@ struct DgHostBasis {
 int dg_host_basis(int N, DgHostBasis* b);
 
 // kernel translation units
+// generic-flux halves of the right-hand-side kernels (called by dg_f64_rhs / dg_f32_rhs
+// for non-production flux pairs; their basis tables are uploaded with the production ones)
+cudaError_t dg_f64g_upload_basis();
+cudaError_t dg_f32g_upload_basis();
+cudaError_t dg_f64g_rhs(const DgArgs& a, cudaStream_t s);
+cudaError_t dg_f32g_rhs(const DgArgs& a, cudaStream_t s);
 cudaError_t dg_f64_upload_basis();
 cudaError_t dg_f32_upload_basis();
 cudaError_t dg_f64_rhs(const DgArgs& a, cudaStream_t s);

@@ -1,0 +1,6 @@
+// Mixed form, right-hand-side kernels with the runtime choice of volume and surface flux.
+#define DG_REAL float
+#define DG_PREFIX dg_f32g
+#define DG_GENERIC_ONLY 1
+#include <string.h>
+#include "dg_rhs_impl.cuh"

@@ -1,9 +1,23 @@
 // Kernels and launchers for one precision.  The including translation unit
 // defines DG_REAL (double or float) and DG_PREFIX (namespace and function-name
 // prefix, e.g. dg_f32), so profiles name kernels dg_f32::rhs_kernel<...>.
+//
+// The right-hand-side kernel comes in two flavours: FL = 1 fixes the production flux
+// pair at compile time (Ranocha volume flux for one gas, Ducros for mixtures; LLF at
+// interfaces and subcells), FL = 0 switches on the runtime choice (every other pair).
+// A translation unit that defines DG_GENERIC_ONLY emits only the FL = 0 kernels (and
+// its own basis table); the other one emits everything else and forwards non-production
+// pairs to DG_GENERIC_RHS.  The split keeps register pressure of the production kernel
+// free of the unused branches and lets the two halves compile in parallel.
 #pragma once
 #include <stdint.h>
 #include "dg_kernels.cuh"
+
+#ifdef DG_GENERIC_ONLY
+#define DG_FL 0
+#else
+#define DG_FL 1
+#endif
 
 namespace DG_PREFIX {
 
@@ -54,45 +68,56 @@ struct Layout {
   static constexpr int ACC = IJ + EPB * NP;
   static constexpr int FV = ACC + EPB * DIM * NV * NP;
   static constexpr int PC = FV + EPB * NFV * NP;    // mixtures: p, c per node
-  static constexpr int TOTAL = PC + (NSP > 1 ? EPB * 2 * NP : 0);
+  static constexpr int DU = PC + (NSP > 1 ? EPB * 2 * NP : 0);  // prefetched RK register du
+  static constexpr int ctas_of(size_t bytes) {
+    return (int)((227 * 1024) / (bytes + 1024)) >= 4 ? 4 : (int)((227 * 1024) / (bytes + 1024));
+  }
+  // du is staged with the rest when that does not cost a resident CTA
+  static constexpr bool PREFETCH_DU =
+      ctas_of(sizeof(real) * (DU + EPB * NV * NP)) == ctas_of(sizeof(real) * DU);
+  static constexpr int TOTAL = DU + (PREFETCH_DU ? EPB * NV * NP : 0);
   static constexpr int THREADS = ((EPB * S::LINES + 31) / 32) * 32;
   static constexpr size_t SMEM = sizeof(real) * TOTAL;
   // CTAs per SM we ask the register allocator for (bounded by shared memory)
-  static constexpr int MINB_SMEM = (int)((227 * 1024) / (SMEM + 1024));
-  static constexpr int MINB = MINB_SMEM >= 4 ? 4 : (MINB_SMEM < 1 ? 1 : MINB_SMEM);
+  static constexpr int MINB = ctas_of(SMEM) < 1 ? 1 : ctas_of(SMEM);
+  // face nodes each thread takes in the interface phase
+  static constexpr int FIT = (EPB * FACE_NODES + THREADS - 1) / THREADS;
 };
 
-// cooperative copy global -> shared, 16-byte vectors when both sides allow it
-__device__ __forceinline__ void stage(real* dst, const real* src, int n, int tid, int nth) {
+// asynchronous global -> shared copies (cp.async): every copy of a phase is in flight at
+// once and one wait retires them, instead of one memory round trip per loop iteration
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(src) : "memory");
+}
+template <int BYTES>
+__device__ __forceinline__ void cp_async_small(void* dst, const void* src) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(s), "l"(src), "n"(BYTES) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+__device__ __forceinline__ void stage_async(real* dst, const real* src, int n, int tid, int nth) {
   constexpr int V = 16 / sizeof(real);
   if ((((uintptr_t)dst | (uintptr_t)src) & 15) == 0 && (n % V) == 0) {
-    const int4* s4 = reinterpret_cast<const int4*>(src);
-    int4* d4 = reinterpret_cast<int4*>(dst);
-    for (int i = tid; i < n / V; i += nth) d4[i] = s4[i];
+    for (int i = tid; i < n / V; i += nth) cp_async16(dst + i * V, src + i * V);
   } else {
-    for (int i = tid; i < n; i += nth) dst[i] = src[i];
+    for (int i = tid; i < n; i += nth) cp_async_small<sizeof(real)>(dst + i, src + i);
   }
 }
 
 // boundary / neighbour state at a face node.  Returns 1 when the face flux is the
-// physical flux of the returned state (supersonic inflow / outflow).
+// physical flux of the returned state (supersonic inflow / outflow).  For an interior
+// face the neighbour's conserved state (and p, c for mixtures) arrives preloaded in nu/npc.
 template <int DIM, int NSP>
-__device__ __forceinline__ int outer_state(const DgArgs& a, const KConst& kc, int nb, int nnode,
-                                           const NodeState<real, DIM, NSP>& own, const real* n,
-                                           NodeState<real, DIM, NSP>& x, bool& ok) {
+__device__ __forceinline__ int outer_state(const DgArgs& a, const KConst& kc, int nb, const real* nu,
+                                           const real* npc, const NodeState<real, DIM, NSP>& own,
+                                           const real* n, NodeState<real, DIM, NSP>& x, bool& ok) {
   constexpr int NV = NSP + DIM + 1;
-  const real* gu = (const real*)a.u;
-  const int np = a.np;
   if (nb >= 0) {
 #pragma unroll
-    for (int k = 0; k < NV; ++k) x.u[k] = gu[((int64_t)nb * NV + k) * np + nnode];
-    real pe = 0, ce = 0;
-    if (NSP > 1) {
-      const real* pc = (const real*)a.pc;
-      pe = pc[((int64_t)nb * 2 + 0) * np + nnode];
-      ce = pc[((int64_t)nb * 2 + 1) * np + nnode];
-    }
-    ok = prim_from_cons<real, DIM, NSP>(x, kc.gamma, pe, ce);
+    for (int k = 0; k < NV; ++k) x.u[k] = nu[k];
+    ok = prim_from_cons<real, DIM, NSP>(x, kc.gamma, NSP > 1 ? npc[0] : real(0), NSP > 1 ? npc[1] : real(0));
     return 0;
   }
   int bc = -(nb + 1);
@@ -128,7 +153,7 @@ __device__ __forceinline__ int outer_state(const DgArgs& a, const KConst& kc, in
 }
 
 // ------------------------------------------------------------------ main RHS / RK kernel
-template <int DIM, int N, int NSP, bool NS>
+template <int DIM, int N, int NSP, bool NS, int FL>
 __global__ void __launch_bounds__(Layout<DIM, N, NSP, NS>::THREADS, Layout<DIM, N, NSP, NS>::MINB)
 rhs_kernel(const DgArgs a, const KConst kc) {
   using S = Shape<DIM, N>;
@@ -143,6 +168,7 @@ rhs_kernel(const DgArgs a, const KConst kc) {
   real* sacc = sm + L::ACC;
   real* sfv = sm + L::FV;
   real* spc = sm + L::PC;
+  real* sdu = sm + L::DU;
   __shared__ real s_alpha[EPB];
   __shared__ real s_dt;
   __shared__ unsigned long long s_lam[2];
@@ -151,12 +177,17 @@ rhs_kernel(const DgArgs a, const KConst kc) {
   const int64_t e0 = (int64_t)blockIdx.x * EPB;
   const int ne = (int)((a.K - e0) < EPB ? (a.K - e0) : EPB);
   const BasisTab<real>& B = c_tab[N];
+  const bool read_du = a.mode == 1 && a.stage != 0;
+  const int vf = FL ? (NSP == 1 ? DG_VF_RANOCHA : DG_VF_DUCROS) : a.vf;
+  const int sf = FL ? DG_SF_LLF : a.sf;
 
-  // ---- phase A: stage state, metric terms, 1/J
-  stage(su, (const real*)a.u + e0 * NV * NP, ne * NV * NP, tid, nth);
-  stage(sja, (const real*)a.Ja + e0 * DIM * DIM * NP, ne * DIM * DIM * NP, tid, nth);
-  stage(sij, (const real*)a.invJ + e0 * NP, ne * NP, tid, nth);
-  if (NSP > 1) stage(spc, (const real*)a.pc + e0 * 2 * NP, ne * 2 * NP, tid, nth);
+  // ---- phase A: stage state, metric terms, 1/J, BR1 gradients (and du) asynchronously
+  stage_async(su, (const real*)a.u + e0 * NV * NP, ne * NV * NP, tid, nth);
+  stage_async(sja, (const real*)a.Ja + e0 * DIM * DIM * NP, ne * DIM * DIM * NP, tid, nth);
+  stage_async(sij, (const real*)a.invJ + e0 * NP, ne * NP, tid, nth);
+  if (NSP > 1) stage_async(spc, (const real*)a.pc + e0 * 2 * NP, ne * 2 * NP, tid, nth);
+  if (NS) stage_async(sfv, (const real*)a.gradW + e0 * L::NFV * NP, ne * L::NFV * NP, tid, nth);
+  if (L::PREFETCH_DU && read_du) stage_async(sdu, (const real*)a.du + e0 * NV * NP, ne * NV * NP, tid, nth);
   if (tid < EPB) {
     real al = 0;
     if (a.alpha_raw && tid < ne) {
@@ -176,6 +207,7 @@ rhs_kernel(const DgArgs a, const KConst kc) {
     if (a.mode == 1) s_dt = (real)a.scal[1];
     s_lam[0] = s_lam[1] = 0ull;
   }
+  cp_async_wait_all();
   __syncthreads();
   for (int i = tid; i < ne * NP; i += nth) {
     const int e = i / NP, node = i % NP;
@@ -200,21 +232,28 @@ rhs_kernel(const DgArgs a, const KConst kc) {
     if (!(rho > real(0) && p > real(0) && isfinite(p)))
       latch_status(a.status, DG_ST_NONPHYS, e0 + e);
     if (NS) {
-      // viscous fluxes from the BR1 gradients of (v, theta)
-      const real* g = (const real*)a.gradW + (e0 + e) * DIM * (DIM + 1) * NP + node;
+      // viscous fluxes from the staged BR1 gradients of (v, theta), in place
+      real* so = sfv + e * L::NFV * NP + node;
       real gg[DIM][DIM + 1], vv[DIM], fv[DIM][DIM + 1];
 #pragma unroll
       for (int x = 0; x < DIM; ++x)
 #pragma unroll
-        for (int c = 0; c <= DIM; ++c) gg[x][c] = g[(x * (DIM + 1) + c) * NP];
+        for (int c = 0; c <= DIM; ++c) gg[x][c] = so[(x * (DIM + 1) + c) * NP];
 #pragma unroll
       for (int d = 0; d < DIM; ++d) vv[d] = q[(1 + d) * NP];
       viscous_flux<real, DIM>(gg, vv, kc.mu, kc.kap, fv);
-      real* so = sfv + e * L::NFV * NP + node;
+      // stored contravariant: slot (d, c) holds sum_x Ja^d_x f^v_{x,c}, the flux along
+      // reference direction d (and, at a face of direction d, the own f^v . n)
+      const real* jn = sja + e * DIM * DIM * NP + node;
 #pragma unroll
-      for (int x = 0; x < DIM; ++x)
+      for (int d = 0; d < DIM; ++d)
 #pragma unroll
-        for (int c = 0; c <= DIM; ++c) so[(x * (DIM + 1) + c) * NP] = fv[x][c];
+        for (int c = 0; c <= DIM; ++c) {
+          real acc_c = 0;
+#pragma unroll
+          for (int x = 0; x < DIM; ++x) acc_c += jn[(d * DIM + x) * NP] * fv[x][c];
+          so[(d * (DIM + 1) + c) * NP] = acc_c;
+        }
     }
   }
   __syncthreads();
@@ -242,7 +281,7 @@ rhs_kernel(const DgArgs a, const KConst kc) {
       real vi[DIM], ui[NV];
 #pragma unroll
       for (int c = 0; c < DIM; ++c) vi[c] = q[(1 + c) * NP + ni];
-      if (NSP > 1 || a.vf != DG_VF_RANOCHA) {
+      if (NSP > 1 || vf != DG_VF_RANOCHA) {
 #pragma unroll
         for (int k = 0; k < NV; ++k) ui[k] = ue[k * NP + ni];
       }
@@ -255,11 +294,11 @@ rhs_kernel(const DgArgs a, const KConst kc) {
           vl[c] = q[(1 + c) * NP + nl];
           nrm[c] = real(0.5) * (ja[c * NP + ni] + ja[c * NP + nl]);
         }
-        if (NSP > 1 || a.vf != DG_VF_RANOCHA) {
+        if (NSP > 1 || vf != DG_VF_RANOCHA) {
 #pragma unroll
           for (int k = 0; k < NV; ++k) ul[k] = ue[k * NP + nl];
         }
-        volume_flux<real, DIM, NSP>(a.vf, q[ni], vi, q[(1 + DIM) * NP + ni], q[(2 + DIM) * NP + ni], ui,
+        volume_flux<real, DIM, NSP>(vf, q[ni], vi, q[(1 + DIM) * NP + ni], q[(2 + DIM) * NP + ni], ui,
                                     q[nl], vl, q[(1 + DIM) * NP + nl], q[(2 + DIM) * NP + nl], ul,
                                     nrm, kc.inv_gm1, F);
         const real cil = wdg * B.D2[i * N1 + l], cli = wdg * B.D2[l * N1 + i];
@@ -309,7 +348,7 @@ rhs_kernel(const DgArgs a, const KConst kc) {
           Rq.c = spc[(e * 2 + 1) * NP + nr];
         }
         real F[NV];
-        surface_flux<real, DIM, NSP>(a.sf == DG_SF_EC ? DG_SF_LLF : a.sf, Lq, Rq, nh, kc.inv_gm1, F);
+        surface_flux<real, DIM, NSP>(sf == DG_SF_EC ? DG_SF_LLF : sf, Lq, Rq, nh, kc.inv_gm1, F);
 #pragma unroll
         for (int k = 0; k < NV; ++k) {
           acc[j - 1][k] += al * B.iw[j - 1] * F[k];
@@ -319,27 +358,16 @@ rhs_kernel(const DgArgs a, const KConst kc) {
     }
 
     if (NS) {
-      // viscous volume term along the line: D Fv (enters the RHS with + sign)
-      const real* fvb = sfv + e * L::NFV * NP;
-      real Fv[N1][DIM + 1];
-#pragma unroll
-      for (int i = 0; i < N1; ++i) {
-        const int ni = base + i * s;
-#pragma unroll
-        for (int c = 0; c <= DIM; ++c) {
-          real acc_c = 0;
-#pragma unroll
-          for (int x = 0; x < DIM; ++x) acc_c += ja[x * NP + ni] * fvb[(x * (DIM + 1) + c) * NP + ni];
-          Fv[i][c] = acc_c;
-        }
-      }
+      // viscous volume term along the line: D Fv (enters the RHS with + sign), with the
+      // contravariant flux of this direction read from shared memory
+      const real* fvd = sfv + (e * L::NFV + d * (DIM + 1)) * NP + base;
 #pragma unroll
       for (int i = 0; i < N1; ++i)
 #pragma unroll
         for (int c = 0; c <= DIM; ++c) {
           real dsum = 0;
 #pragma unroll
-          for (int l = 0; l < N1; ++l) dsum += B.D[i * N1 + l] * Fv[l][c];
+          for (int l = 0; l < N1; ++l) dsum += B.D[i * N1 + l] * fvd[c * NP + l * s];
           acc[i][NSP + c] -= dsum;
         }
     }
@@ -352,14 +380,45 @@ rhs_kernel(const DgArgs a, const KConst kc) {
   }
   __syncthreads();
 
-  // ---- phase B2: one thread per face node: interface fluxes and lifting
-  for (int t = tid; t < ne * L::FACE_NODES; t += nth) {
-    const int e = t / L::FACE_NODES, r = t % L::FACE_NODES;
+  // ---- phase B2: one thread per face node: interface fluxes and lifting.  The
+  // neighbour traces of all of a thread's face nodes are loaded before any is used.
+  constexpr int FN = L::FACE_NODES, FIT = L::FIT, NG = NS ? L::NFV : 1;
+  real nbu[FIT][NV], nbpc[FIT][2], nbg[FIT][NG];
+#pragma unroll
+  for (int it = 0; it < FIT; ++it) {
+    const int t = tid + it * L::THREADS;
+    if (t < ne * FN) {
+      const int e = t / FN, r = t % FN;
+      const int f = r / S::LPD, m = r % S::LPD;
+      const int d = f >> 1, side = f & 1;
+      const int nnode = S::line_base(d, m) + (side ? 0 : N) * S::stride(d);
+      const int nb = a.nbr[(e0 + e) * 2 * DIM + f];
+      if (nb >= 0) {
+        const real* gu = (const real*)a.u + (int64_t)nb * NV * NP + nnode;
+#pragma unroll
+        for (int k = 0; k < NV; ++k) nbu[it][k] = gu[k * NP];
+        if (NSP > 1) {
+          const real* pc = (const real*)a.pc + (int64_t)nb * 2 * NP + nnode;
+          nbpc[it][0] = pc[0];
+          nbpc[it][1] = pc[NP];
+        }
+        if (NS) {
+          const real* gn = (const real*)a.gradW + (int64_t)nb * L::NFV * NP + nnode;
+#pragma unroll
+          for (int c = 0; c < NG; ++c) nbg[it][c] = gn[c * NP];
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int it = 0; it < FIT; ++it) {
+    const int t = tid + it * L::THREADS;
+    if (t >= ne * FN) break;
+    const int e = t / FN, r = t % FN;
     const int f = r / S::LPD, m = r % S::LPD;
     const int d = f >> 1, side = f & 1;
     const int s = S::stride(d), base = S::line_base(d, m);
     const int node = base + (side ? N : 0) * s;
-    const int nnode = base + (side ? 0 : N) * s;
     const int64_t eg = e0 + e;
     const real* q = sq + e * NQ * NP;
     const real* ja = sja + (e * DIM + d) * DIM * NP;
@@ -382,33 +441,28 @@ rhs_kernel(const DgArgs a, const KConst kc) {
     NodeState<real, DIM, NSP> x;
     bool ok = true;
     real Fs[NV];
-    int phys = outer_state<DIM, NSP>(a, kc, nb, nnode, o, nface, x, ok);
+    int phys = outer_state<DIM, NSP>(a, kc, nb, nbu[it], nbpc[it], o, nface, x, ok);
     if (!ok) latch_status(a.status, DG_ST_NONPHYS, nb >= 0 ? nb : eg);
     if (phys) phys_flux<real, DIM, NSP>(x, nface, Fs);
-    else if (side) surface_flux<real, DIM, NSP>(a.sf, o, x, nface, kc.inv_gm1, Fs);
-    else surface_flux<real, DIM, NSP>(a.sf, x, o, nface, kc.inv_gm1, Fs);
+    else if (side) surface_flux<real, DIM, NSP>(sf, o, x, nface, kc.inv_gm1, Fs);
+    else surface_flux<real, DIM, NSP>(sf, x, o, nface, kc.inv_gm1, Fs);
 #pragma unroll
     for (int k = 0; k < NV; ++k) sa[k * NP] += iw * Fs[k];
     if (NS) {
       // viscous interface flux: mean of both sides' f^v . n, lifted as (Fv* - Fv)
-      const real* fvb = sfv + e * L::NFV * NP + node;
-      const real* gn = (const real*)a.gradW + (int64_t)nb * DIM * (DIM + 1) * NP + nnode;
+      const real* fvd = sfv + (e * L::NFV + d * (DIM + 1)) * NP + node;
       real gg[DIM][DIM + 1], fvn[DIM][DIM + 1];
 #pragma unroll
       for (int xx = 0; xx < DIM; ++xx)
 #pragma unroll
-        for (int c = 0; c <= DIM; ++c) gg[xx][c] = gn[(xx * (DIM + 1) + c) * NP];
+        for (int c = 0; c <= DIM; ++c) gg[xx][c] = nbg[it][(xx * (DIM + 1) + c) % NG];
       viscous_flux<real, DIM>(gg, x.v, kc.mu, kc.kap, fvn);
 #pragma unroll
       for (int c = 0; c <= DIM; ++c) {
-        real own_n = 0, mean_n = 0;
+        real nbr_n = 0;
 #pragma unroll
-        for (int xx = 0; xx < DIM; ++xx) {
-          const real fo = fvb[(xx * (DIM + 1) + c) * NP];
-          own_n += fo * nface[xx];
-          mean_n += real(0.5) * (fo + fvn[xx][c]) * nface[xx];
-        }
-        sa[(NSP + c) * NP] -= iw * (mean_n - own_n);
+        for (int xx = 0; xx < DIM; ++xx) nbr_n += fvn[xx][c] * nface[xx];
+        sa[(NSP + c) * NP] -= iw * (real(0.5) * (nbr_n - fvd[c * NP]));
       }
     }
   }
@@ -444,7 +498,9 @@ rhs_kernel(const DgArgs a, const KConst kc) {
         for (int d = 0; d < DIM; ++d) sum += sa[(d * NV + k) * NP];
         real r = -ij * sum;
         if (NSP > 1 && k < NSP && a.src) r += ((const real*)a.src)[((e0 + e) * NSP + k) * NP + node];
-        real dn = (a.stage == 0 ? real(0) : kc.rkA * du[gbase + k * NP]) + dt * r;
+        const real dold = !read_du ? real(0)
+                          : (L::PREFETCH_DU ? sdu[(e * NV + k) * NP + node] : du[gbase + k * NP]);
+        real dn = kc.rkA * dold + dt * r;
         du[gbase + k * NP] = dn;
         un[k] = su[(e * NV + k) * NP + node] + kc.rkB * dn;
         out[gbase + k * NP] = un[k];
@@ -548,11 +604,16 @@ gradient_kernel(const DgArgs a, const KConst kc) {
   const int ne = (int)((a.K - e0) < L::EPB ? (a.K - e0) : L::EPB);
   const BasisTab<real>& B = c_tab[N];
   const real* gu = (const real*)a.u;
-  stage(sja, (const real*)a.Ja + e0 * DIM * DIM * NP, ne * DIM * DIM * NP, tid, nth);
-  stage(sij, (const real*)a.invJ + e0 * NP, ne * NP, tid, nth);
+  // the conserved state is staged in the gradient region, which is free until the line phase
+  static_assert(L::TOTAL - L::G >= L::EPB * NV * NP, "gradient region too small for the state");
+  stage_async(sja, (const real*)a.Ja + e0 * DIM * DIM * NP, ne * DIM * DIM * NP, tid, nth);
+  stage_async(sij, (const real*)a.invJ + e0 * NP, ne * NP, tid, nth);
+  stage_async(sg, gu + e0 * NV * NP, ne * NV * NP, tid, nth);
+  cp_async_wait_all();
+  __syncthreads();
   for (int i = tid; i < ne * NP; i += nth) {
     const int e = i / NP, node = i % NP;
-    const real* uu = gu + (e0 + e) * NV * NP + node;
+    const real* uu = sg + e * NV * NP + node;
     real rho = 0;
 #pragma unroll
     for (int k = 0; k < NSP; ++k) rho += uu[k * NP];
@@ -767,7 +828,7 @@ cudaError_t set_smem(KernelT k, size_t bytes) {
 template <int DIM, int N, int NSP, bool NS>
 cudaError_t launch_rhs_t(const DgArgs& a, cudaStream_t st) {
   using L = Layout<DIM, N, NSP, NS>;
-  auto k = rhs_kernel<DIM, N, NSP, NS>;
+  auto k = rhs_kernel<DIM, N, NSP, NS, DG_FL>;
   cudaError_t err = set_smem(k, L::SMEM);
   if (err != cudaSuccess) return err;
   const int64_t grid = (a.K + L::EPB - 1) / L::EPB;
@@ -775,6 +836,7 @@ cudaError_t launch_rhs_t(const DgArgs& a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+#ifndef DG_GENERIC_ONLY
 template <int DIM, int N, int NSP>
 cudaError_t launch_grad_t(const DgArgs& a, cudaStream_t st) {
   using L = GLayout<DIM, N, NSP>;
@@ -794,6 +856,7 @@ cudaError_t launch_ind_t(const DgArgs& a, double amax, void* out, cudaStream_t s
   indicator_kernel<DIM, N, NSP><<<(unsigned)grid, bs, 0, st>>>(a, make_kconst(a), (real)amax, (real*)out);
   return cudaGetLastError();
 }
+#endif  // DG_GENERIC_ONLY
 
 }  // namespace DG_PREFIX
 
@@ -821,6 +884,10 @@ cudaError_t launch_ind_t(const DgArgs& a, double amax, void* out, cudaStream_t s
 #define DG_IND_CALL(DIM, N, NSP, X) DG_PREFIX::launch_ind_t<DIM, N, NSP>(a, amax, out, st)
 
 cudaError_t DG_CAT(DG_PREFIX, _rhs)(const DgArgs& a, cudaStream_t st) {
+#ifndef DG_GENERIC_ONLY
+  const bool production = a.sf == DG_SF_LLF && a.vf == (a.nsp == 1 ? DG_VF_RANOCHA : DG_VF_DUCROS);
+  if (!production) return DG_GENERIC_RHS(a, st);
+#endif
   if (a.dim == 3 && a.nsp == 1 && a.ns) { DG_DISPATCH_N(DG_RHS_CALL, 3, 1, true) }
   if (a.dim == 3 && a.nsp == 1) { DG_DISPATCH_N(DG_RHS_CALL, 3, 1, false) }
   if (a.dim == 2 && a.nsp == 1) { DG_DISPATCH_N(DG_RHS_CALL, 2, 1, false) }
@@ -828,6 +895,7 @@ cudaError_t DG_CAT(DG_PREFIX, _rhs)(const DgArgs& a, cudaStream_t st) {
   return cudaErrorInvalidValue;
 }
 
+#ifndef DG_GENERIC_ONLY
 cudaError_t DG_CAT(DG_PREFIX, _gradients)(const DgArgs& a, cudaStream_t st) {
   if (a.dim == 3 && a.nsp == 1) { DG_DISPATCH_N(DG_GRAD_CALL, 3, 1, 0) }
   return cudaErrorInvalidValue;
@@ -858,6 +926,8 @@ cudaError_t DG_CAT(DG_PREFIX, _step_dt)(const DgArgs& a, int slot, int advance_t
   return cudaGetLastError();
 }
 
+#endif  // DG_GENERIC_ONLY
+
 cudaError_t DG_CAT(DG_PREFIX, _upload_basis)() {
   using DG_PREFIX::real;
   dgk::BasisTab<real> tab[DG_MAXN + 1];
@@ -877,5 +947,9 @@ cudaError_t DG_CAT(DG_PREFIX, _upload_basis)() {
     }
     tab[N].thr = (real)(0.5 * pow(10.0, -1.8 * pow(N + 1.0, 0.25)));
   }
-  return cudaMemcpyToSymbol(DG_PREFIX::c_tab, tab, sizeof(tab));
+  cudaError_t err = cudaMemcpyToSymbol(DG_PREFIX::c_tab, tab, sizeof(tab));
+#ifndef DG_GENERIC_ONLY
+  if (err == cudaSuccess) err = DG_GENERIC_UPLOAD();
+#endif
+  return err;
 }
