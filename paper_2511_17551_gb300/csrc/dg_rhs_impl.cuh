@@ -69,8 +69,11 @@ struct Layout {
   static constexpr int FV = ACC + EPB * DIM * NV * NP;
   static constexpr int PC = FV + EPB * NFV * NP;    // mixtures: p, c per node
   static constexpr int DU = PC + (NSP > 1 ? EPB * 2 * NP : 0);  // prefetched RK register du
+  // resident-CTA target (measured: 4 for one gas; 3 for mixtures, whose 9-variable line
+  // accumulators spill below ~110 registers a thread), lowered where shared memory binds
+  static constexpr int CAP = NSP > 1 ? 3 : 4;
   static constexpr int ctas_of(size_t bytes) {
-    return (int)((227 * 1024) / (bytes + 1024)) >= 4 ? 4 : (int)((227 * 1024) / (bytes + 1024));
+    return (int)((227 * 1024) / (bytes + 1024)) >= CAP ? CAP : (int)((227 * 1024) / (bytes + 1024));
   }
   // du is staged with the rest when that does not cost a resident CTA
   static constexpr bool PREFETCH_DU =
