@@ -51,6 +51,20 @@ constexpr int epb() {
   return Shape<DIM, N>::LINES >= 192 ? 1 : (192 / Shape<DIM, N>::LINES > 24 ? 24 : 192 / Shape<DIM, N>::LINES);
 }
 
+// Shared-memory position of node n inside a per-variable block.  For power-of-two line
+// lengths in 3D the i and j digits are XOR-ed with k: any two of (i, j, k) then fix the
+// position mod N1^2, so the lines of every direction (and the nodes of every face) fall
+// on distinct banks.  An involution; identity otherwise.
+template <int DIM, int N>
+struct Swizzle {
+  static constexpr int N1 = N + 1;
+  static constexpr bool ON = DIM == 3 && (N1 & (N1 - 1)) == 0;
+  static __device__ __forceinline__ int at(int n) {
+    if (!ON) return n;
+    return n ^ ((n / (N1 * N1)) * (N1 + 1));
+  }
+};
+
 template <int DIM, int N, int NSP, bool NS>
 struct Layout {
   using S = Shape<DIM, N>;
@@ -60,15 +74,25 @@ struct Layout {
   static constexpr int NQ = DIM + 3;                // rho, v, p, beta(=rho/p)
   static constexpr int NFV = NS ? DIM * (DIM + 1) : 0;
   static constexpr int FACE_NODES = 2 * DIM * S::LPD;  // per element
-  // shared memory offsets (in reals) per CTA
+  // Bank-conflict-free shared layout for power-of-two line lengths: nodes are swizzled
+  // (swz), warps of the line and face phases take one direction (face) of two elements,
+  // and in FP32 consecutive elements sit 16 words (mod 32) apart, so the two elements of
+  // a warp fill complementary halves of the 32 banks.
+  static constexpr bool SWZ = Swizzle<DIM, N>::ON;
+  static constexpr bool UNI = SWZ && (EPB * S::LPD) % 32 == 0;
+  static constexpr int padded(int w) { return (SWZ && sizeof(real) == 4) ? w + (48 - w % 32) % 32 : w; }
+  // per-element strides (reals) and region offsets of one CTA
+  static constexpr int SU = padded(NV * NP), SQ = padded(NQ * NP), SJA = padded(DIM * DIM * NP);
+  static constexpr int SIJ = NP, SACC = padded(DIM * NV * NP), SFV = NS ? padded(NFV * NP) : 0;
+  static constexpr int SPC = NSP > 1 ? padded(2 * NP) : 0, SDU = NV * NP;
   static constexpr int U = 0;
-  static constexpr int Q = U + EPB * NV * NP;
-  static constexpr int JA = Q + EPB * NQ * NP;
-  static constexpr int IJ = JA + EPB * DIM * DIM * NP;
-  static constexpr int ACC = IJ + EPB * NP;
-  static constexpr int FV = ACC + EPB * DIM * NV * NP;
-  static constexpr int PC = FV + EPB * NFV * NP;    // mixtures: p, c per node
-  static constexpr int DU = PC + (NSP > 1 ? EPB * 2 * NP : 0);  // prefetched RK register du
+  static constexpr int Q = U + EPB * SU;
+  static constexpr int JA = Q + EPB * SQ;
+  static constexpr int IJ = JA + EPB * SJA;
+  static constexpr int ACC = IJ + EPB * SIJ;
+  static constexpr int FV = ACC + EPB * SACC;
+  static constexpr int PC = FV + EPB * SFV;          // mixtures: p, c per node
+  static constexpr int DU = PC + EPB * SPC;           // prefetched RK register du
   // resident-CTA target (measured: 4 for one gas; 3 for mixtures, whose 9-variable line
   // accumulators spill below ~110 registers a thread), lowered where shared memory binds
   static constexpr int CAP = NSP > 1 ? 3 : 4;
@@ -77,8 +101,8 @@ struct Layout {
   }
   // du is staged with the rest when that does not cost a resident CTA
   static constexpr bool PREFETCH_DU =
-      ctas_of(sizeof(real) * (DU + EPB * NV * NP)) == ctas_of(sizeof(real) * DU);
-  static constexpr int TOTAL = DU + (PREFETCH_DU ? EPB * NV * NP : 0);
+      ctas_of(sizeof(real) * (DU + EPB * SDU)) == ctas_of(sizeof(real) * DU);
+  static constexpr int TOTAL = DU + (PREFETCH_DU ? EPB * SDU : 0);
   static constexpr int THREADS = ((EPB * S::LINES + 31) / 32) * 32;
   static constexpr size_t SMEM = sizeof(real) * TOTAL;
   // CTAs per SM we ask the register allocator for (bounded by shared memory)
@@ -106,6 +130,29 @@ __device__ __forceinline__ void stage_async(real* dst, const real* src, int n, i
     for (int i = tid; i < n / V; i += nth) cp_async16(dst + i * V, src + i * V);
   } else {
     for (int i = tid; i < n; i += nth) cp_async_small<sizeof(real)>(dst + i, src + i);
+  }
+}
+
+// stage ne elements of XV variable blocks into a region of element stride XS (a padded
+// layout), 16-byte copies where both sides allow, element-wise otherwise
+template <int XV, int XS, int NP>
+__device__ __forceinline__ void stage_strided(real* dst, const real* src, int ne, int tid, int nth) {
+  constexpr int V = 16 / sizeof(real);
+  if (XS == XV * NP) {
+    stage_async(dst, src, ne * XV * NP, tid, nth);
+    return;
+  }
+  if ((XV * NP) % V == 0 && XS % V == 0 && (((uintptr_t)dst | (uintptr_t)src) & 15) == 0) {
+    constexpr int PER = XV * NP / V;
+    for (int i = tid; i < ne * PER; i += nth) {
+      const int e = i / PER, r = i % PER;
+      cp_async16(dst + e * XS + r * V, src + e * XV * NP + r * V);
+    }
+  } else {
+    for (int i = tid; i < ne * XV * NP; i += nth) {
+      const int e = i / (XV * NP), r = i % (XV * NP);
+      cp_async_small<sizeof(real)>(dst + e * XS + r, src + i);
+    }
   }
 }
 
@@ -183,14 +230,18 @@ rhs_kernel(const DgArgs a, const KConst kc) {
   const bool read_du = a.mode == 1 && a.stage != 0;
   const int vf = FL ? (NSP == 1 ? DG_VF_RANOCHA : DG_VF_DUCROS) : a.vf;
   const int sf = FL ? DG_SF_LLF : a.sf;
+  auto SW = [](int n) { return Swizzle<DIM, N>::at(n); };
 
-  // ---- phase A: stage state, metric terms, 1/J, BR1 gradients (and du) asynchronously
-  stage_async(su, (const real*)a.u + e0 * NV * NP, ne * NV * NP, tid, nth);
-  stage_async(sja, (const real*)a.Ja + e0 * DIM * DIM * NP, ne * DIM * DIM * NP, tid, nth);
-  stage_async(sij, (const real*)a.invJ + e0 * NP, ne * NP, tid, nth);
-  if (NSP > 1) stage_async(spc, (const real*)a.pc + e0 * 2 * NP, ne * 2 * NP, tid, nth);
-  if (NS) stage_async(sfv, (const real*)a.gradW + e0 * L::NFV * NP, ne * L::NFV * NP, tid, nth);
-  if (L::PREFETCH_DU && read_du) stage_async(sdu, (const real*)a.du + e0 * NV * NP, ne * NV * NP, tid, nth);
+  // ---- phase A: stage state, metric terms, 1/J, BR1 gradients (and du) asynchronously,
+  // unswizzled (16-byte copies)
+  stage_strided<NV, L::SU, NP>(su, (const real*)a.u + e0 * NV * NP, ne, tid, nth);
+  stage_strided<DIM * DIM, L::SJA, NP>(sja, (const real*)a.Ja + e0 * DIM * DIM * NP, ne, tid, nth);
+  stage_strided<1, L::SIJ, NP>(sij, (const real*)a.invJ + e0 * NP, ne, tid, nth);
+  if (NSP > 1) stage_strided<2, (NSP > 1 ? L::SPC : 2 * NP), NP>(spc, (const real*)a.pc + e0 * 2 * NP, ne, tid, nth);
+  if (NS)
+    stage_strided<(NS ? L::NFV : 1), (NS ? L::SFV : NP), NP>(sfv, (const real*)a.gradW + e0 * L::NFV * NP, ne,
+                                                             tid, nth);
+  if (L::PREFETCH_DU && read_du) stage_strided<NV, L::SDU, NP>(sdu, (const real*)a.du + e0 * NV * NP, ne, tid, nth);
   if (tid < EPB) {
     real al = 0;
     if (a.alpha_raw && tid < ne) {
@@ -212,63 +263,107 @@ rhs_kernel(const DgArgs a, const KConst kc) {
   }
   cp_async_wait_all();
   __syncthreads();
-  for (int i = tid; i < ne * NP; i += nth) {
-    const int e = i / NP, node = i % NP;
-    const real* uu = su + e * NV * NP + node;
-    real rho = 0;
+  // One thread per node: primitives (written swizzled), viscous fluxes, and the swizzled
+  // rewrite of the metric terms, gradients -> contravariant viscous fluxes and p, c.  The
+  // rewrite stays inside k-slabs of N1^2 nodes and nth is a multiple of N1^2, so one
+  // barrier between the reads and the writes of a pass keeps it race-free.
+  static_assert(!L::SWZ || (L::THREADS % (S::N1 * S::N1)) == 0, "swizzle slabs must not straddle passes");
+  for (int i0 = 0; i0 < ne * NP; i0 += nth) {
+    const int i = i0 + tid;
+    const bool act = i < ne * NP;
+    const int e = act ? i / NP : 0, n = i % NP, pn = SW(n);
+    real jv[L::SWZ ? DIM * DIM : 1], fl[NS ? L::NFV : 1], pcv[2];
+    if (act) {
+      const real* uu = su + e * L::SU + n;
+      real rho = 0;
 #pragma unroll
-    for (int k = 0; k < NSP; ++k) rho += uu[k * NP];
-    real ir = RealOps<real>::rcp(rho), ke = 0;
-    real* q = sq + e * NQ * NP + node;
-    q[0] = rho;
+      for (int k = 0; k < NSP; ++k) rho += uu[k * NP];
+      real ir = RealOps<real>::rcp(rho), ke = 0;
+      real* q = sq + e * L::SQ + pn;
+      q[0] = rho;
+      real vv[DIM];
 #pragma unroll
-    for (int d = 0; d < DIM; ++d) {
-      real v = uu[(NSP + d) * NP] * ir;
-      q[(1 + d) * NP] = v;
-      ke += uu[(NSP + d) * NP] * v;
+      for (int d = 0; d < DIM; ++d) {
+        vv[d] = uu[(NSP + d) * NP] * ir;
+        q[(1 + d) * NP] = vv[d];
+        ke += uu[(NSP + d) * NP] * vv[d];
+      }
+      real p;
+      if (NSP == 1) {
+        p = kc.gm1 * (uu[(NSP + DIM) * NP] - real(0.5) * ke);
+      } else {
+        pcv[0] = spc[e * L::SPC + n];
+        pcv[1] = spc[e * L::SPC + NP + n];
+        p = pcv[0];
+      }
+      q[(1 + DIM) * NP] = p;
+      q[(2 + DIM) * NP] = rho * RealOps<real>::rcp(p);
+      if (!(rho > real(0) && p > real(0) && isfinite(p)))
+        latch_status(a.status, DG_ST_NONPHYS, e0 + e);
+      const real* jn = sja + e * L::SJA + n;
+      if (L::SWZ) {
+#pragma unroll
+        for (int c = 0; c < DIM * DIM; ++c) jv[c] = jn[c * NP];
+      }
+      if (NS) {
+        // viscous fluxes from the staged BR1 gradients of (v, theta), stored contravariant:
+        // slot (d, c) holds sum_x Ja^d_x f^v_{x,c}, the flux along reference direction d
+        // (and, at a face of direction d, the own f^v . n)
+        const real* gi = sfv + e * L::SFV + n;
+        real gg[DIM][DIM + 1], fv[DIM][DIM + 1];
+#pragma unroll
+        for (int x = 0; x < DIM; ++x)
+#pragma unroll
+          for (int c = 0; c <= DIM; ++c) gg[x][c] = gi[(x * (DIM + 1) + c) * NP];
+        viscous_flux<real, DIM>(gg, vv, kc.mu, kc.kap, fv);
+#pragma unroll
+        for (int d = 0; d < DIM; ++d)
+#pragma unroll
+          for (int c = 0; c <= DIM; ++c) {
+            real acc_c = 0;
+#pragma unroll
+            for (int x = 0; x < DIM; ++x) acc_c += jn[(d * DIM + x) * NP] * fv[x][c];
+            fl[d * (DIM + 1) + c] = acc_c;
+          }
+      }
     }
-    real p;
-    if (NSP == 1) p = kc.gm1 * (uu[(NSP + DIM) * NP] - real(0.5) * ke);
-    else p = spc[e * 2 * NP + node];
-    q[(1 + DIM) * NP] = p;
-    q[(2 + DIM) * NP] = rho * RealOps<real>::rcp(p);
-    if (!(rho > real(0) && p > real(0) && isfinite(p)))
-      latch_status(a.status, DG_ST_NONPHYS, e0 + e);
-    if (NS) {
-      // viscous fluxes from the staged BR1 gradients of (v, theta), in place
-      real* so = sfv + e * L::NFV * NP + node;
-      real gg[DIM][DIM + 1], vv[DIM], fv[DIM][DIM + 1];
+    if (L::SWZ) __syncthreads();
+    if (act) {
+      if (L::SWZ) {
+        real* jo = sja + e * L::SJA + pn;
 #pragma unroll
-      for (int x = 0; x < DIM; ++x)
-#pragma unroll
-        for (int c = 0; c <= DIM; ++c) gg[x][c] = so[(x * (DIM + 1) + c) * NP];
-#pragma unroll
-      for (int d = 0; d < DIM; ++d) vv[d] = q[(1 + d) * NP];
-      viscous_flux<real, DIM>(gg, vv, kc.mu, kc.kap, fv);
-      // stored contravariant: slot (d, c) holds sum_x Ja^d_x f^v_{x,c}, the flux along
-      // reference direction d (and, at a face of direction d, the own f^v . n)
-      const real* jn = sja + e * DIM * DIM * NP + node;
-#pragma unroll
-      for (int d = 0; d < DIM; ++d)
-#pragma unroll
-        for (int c = 0; c <= DIM; ++c) {
-          real acc_c = 0;
-#pragma unroll
-          for (int x = 0; x < DIM; ++x) acc_c += jn[(d * DIM + x) * NP] * fv[x][c];
-          so[(d * (DIM + 1) + c) * NP] = acc_c;
+        for (int c = 0; c < DIM * DIM; ++c) jo[c * NP] = jv[c];
+        if (NSP > 1) {
+          spc[e * L::SPC + pn] = pcv[0];
+          spc[e * L::SPC + NP + pn] = pcv[1];
         }
+      }
+      if (NS) {
+        real* so = sfv + e * L::SFV + pn;
+#pragma unroll
+        for (int c = 0; c < (NS ? L::NFV : 1); ++c) so[c * NP] = fl[c];
+      }
     }
   }
   __syncthreads();
 
   // ---- phase B1: one thread per line: volume terms
-  for (int t = tid; t < ne * S::LINES; t += nth) {
-    const int e = t / S::LINES, r = t % S::LINES;
-    const int d = r / S::LPD, m = r % S::LPD;
+  for (int t = tid; t < EPB * S::LINES; t += nth) {
+    int e, d, m;
+    if (L::UNI) {  // warp-uniform direction
+      d = t / (EPB * S::LPD);
+      e = (t / S::LPD) % EPB;
+      m = t % S::LPD;
+    } else {
+      e = t / S::LINES;
+      d = (t % S::LINES) / S::LPD;
+      m = t % S::LPD;
+    }
+    if (e >= ne) continue;
     const int s = S::stride(d), base = S::line_base(d, m);
-    const real* q = sq + e * NQ * NP;
-    const real* ja = sja + (e * DIM + d) * DIM * NP;  // Ja^d components at [c][node]
-    const real* ue = su + e * NV * NP;
+    const real* q = sq + e * L::SQ;
+    const real* ja = sja + e * L::SJA + d * DIM * NP;  // Ja^d components at [c][node]
+    const real* ue = su + e * L::SU;
     real acc[N1][NV];
 #pragma unroll
     for (int i = 0; i < N1; ++i)
@@ -280,17 +375,17 @@ rhs_kernel(const DgArgs a, const KConst kc) {
     // flux differencing: every symmetric pair once (split form, zero diagonal)
 #pragma unroll
     for (int i = 0; i < N1; ++i) {
-      const int ni = base + i * s;
+      const int ri = base + i * s, ni = SW(ri);
       real vi[DIM], ui[NV];
 #pragma unroll
       for (int c = 0; c < DIM; ++c) vi[c] = q[(1 + c) * NP + ni];
       if (NSP > 1 || vf != DG_VF_RANOCHA) {
 #pragma unroll
-        for (int k = 0; k < NV; ++k) ui[k] = ue[k * NP + ni];
+        for (int k = 0; k < NV; ++k) ui[k] = ue[k * NP + ri];
       }
 #pragma unroll
       for (int l = i + 1; l < N1; ++l) {
-        const int nl = base + l * s;
+        const int rl = base + l * s, nl = SW(rl);
         real vl[DIM], ul[NV], nrm[DIM], F[NV];
 #pragma unroll
         for (int c = 0; c < DIM; ++c) {
@@ -299,7 +394,7 @@ rhs_kernel(const DgArgs a, const KConst kc) {
         }
         if (NSP > 1 || vf != DG_VF_RANOCHA) {
 #pragma unroll
-          for (int k = 0; k < NV; ++k) ul[k] = ue[k * NP + nl];
+          for (int k = 0; k < NV; ++k) ul[k] = ue[k * NP + rl];
         }
         volume_flux<real, DIM, NSP>(vf, q[ni], vi, q[(1 + DIM) * NP + ni], q[(2 + DIM) * NP + ni], ui,
                                     q[nl], vl, q[(1 + DIM) * NP + nl], q[(2 + DIM) * NP + nl], ul,
@@ -317,7 +412,7 @@ rhs_kernel(const DgArgs a, const KConst kc) {
     if (al > real(0)) {
       real nh[DIM];
 #pragma unroll
-      for (int c = 0; c < DIM; ++c) nh[c] = ja[c * NP + base];
+      for (int c = 0; c < DIM; ++c) nh[c] = ja[c * NP + SW(base)];
 #pragma unroll
       for (int j = 1; j < N1; ++j) {
         // advance the subcell normal across subcell j-1: n += w_{j-1} (D Ja)_{j-1}
@@ -325,14 +420,14 @@ rhs_kernel(const DgArgs a, const KConst kc) {
         for (int l = 0; l < N1; ++l) {
           const real cw = B.w[j - 1] * B.D[(j - 1) * N1 + l];
 #pragma unroll
-          for (int c = 0; c < DIM; ++c) nh[c] += cw * ja[c * NP + base + l * s];
+          for (int c = 0; c < DIM; ++c) nh[c] += cw * ja[c * NP + SW(base + l * s)];
         }
         NodeState<real, DIM, NSP> Lq, Rq;
-        const int nl = base + (j - 1) * s, nr = base + j * s;
+        const int rl = base + (j - 1) * s, rr = base + j * s, nl = SW(rl), nr = SW(rr);
 #pragma unroll
         for (int k = 0; k < NV; ++k) {
-          Lq.u[k] = ue[k * NP + nl];
-          Rq.u[k] = ue[k * NP + nr];
+          Lq.u[k] = ue[k * NP + rl];
+          Rq.u[k] = ue[k * NP + rr];
         }
         Lq.rho = q[nl];
         Rq.rho = q[nr];
@@ -347,8 +442,8 @@ rhs_kernel(const DgArgs a, const KConst kc) {
           Lq.c = RealOps<real>::sqrt_(kc.gamma * Lq.p * RealOps<real>::rcp(Lq.rho));
           Rq.c = RealOps<real>::sqrt_(kc.gamma * Rq.p * RealOps<real>::rcp(Rq.rho));
         } else {
-          Lq.c = spc[(e * 2 + 1) * NP + nl];
-          Rq.c = spc[(e * 2 + 1) * NP + nr];
+          Lq.c = spc[e * L::SPC + NP + nl];
+          Rq.c = spc[e * L::SPC + NP + nr];
         }
         real F[NV];
         surface_flux<real, DIM, NSP>(sf == DG_SF_EC ? DG_SF_LLF : sf, Lq, Rq, nh, kc.inv_gm1, F);
@@ -363,36 +458,47 @@ rhs_kernel(const DgArgs a, const KConst kc) {
     if (NS) {
       // viscous volume term along the line: D Fv (enters the RHS with + sign), with the
       // contravariant flux of this direction read from shared memory
-      const real* fvd = sfv + (e * L::NFV + d * (DIM + 1)) * NP + base;
+      const real* fvd = sfv + e * L::SFV + d * (DIM + 1) * NP;
 #pragma unroll
       for (int i = 0; i < N1; ++i)
 #pragma unroll
         for (int c = 0; c <= DIM; ++c) {
           real dsum = 0;
 #pragma unroll
-          for (int l = 0; l < N1; ++l) dsum += B.D[i * N1 + l] * fvd[c * NP + l * s];
+          for (int l = 0; l < N1; ++l) dsum += B.D[i * N1 + l] * fvd[c * NP + SW(base + l * s)];
           acc[i][NSP + c] -= dsum;
         }
     }
 
-    real* sa = sacc + (e * DIM + d) * NV * NP;
+    real* sa = sacc + e * L::SACC + d * NV * NP;
 #pragma unroll
     for (int i = 0; i < N1; ++i)
 #pragma unroll
-      for (int k = 0; k < NV; ++k) sa[k * NP + base + i * s] = acc[i][k];
+      for (int k = 0; k < NV; ++k) sa[k * NP + SW(base + i * s)] = acc[i][k];
   }
   __syncthreads();
 
   // ---- phase B2: one thread per face node: interface fluxes and lifting.  The
   // neighbour traces of all of a thread's face nodes are loaded before any is used.
   constexpr int FN = L::FACE_NODES, FIT = L::FIT, NG = NS ? L::NFV : 1;
+  // face-node threads: face-uniform warps where the layout is swizzled
+  auto face_of = [](int t, int& e, int& f, int& m) {
+    if (L::UNI) {
+      f = t / (EPB * S::LPD);
+      e = f < 2 * DIM ? (t / S::LPD) % EPB : EPB;
+      m = t % S::LPD;
+    } else {
+      e = t / FN;
+      f = (t % FN) / S::LPD;
+      m = t % S::LPD;
+    }
+  };
   real nbu[FIT][NV], nbpc[FIT][2], nbg[FIT][NG];
 #pragma unroll
   for (int it = 0; it < FIT; ++it) {
-    const int t = tid + it * L::THREADS;
-    if (t < ne * FN) {
-      const int e = t / FN, r = t % FN;
-      const int f = r / S::LPD, m = r % S::LPD;
+    int e, f, m;
+    face_of(tid + it * L::THREADS, e, f, m);
+    if (e < ne) {
       const int d = f >> 1, side = f & 1;
       const int nnode = S::line_base(d, m) + (side ? 0 : N) * S::stride(d);
       const int nb = a.nbr[(e0 + e) * 2 * DIM + f];
@@ -415,28 +521,27 @@ rhs_kernel(const DgArgs a, const KConst kc) {
   }
 #pragma unroll
   for (int it = 0; it < FIT; ++it) {
-    const int t = tid + it * L::THREADS;
-    if (t >= ne * FN) break;
-    const int e = t / FN, r = t % FN;
-    const int f = r / S::LPD, m = r % S::LPD;
+    int e, f, m;
+    face_of(tid + it * L::THREADS, e, f, m);
+    if (e >= ne) continue;
     const int d = f >> 1, side = f & 1;
     const int s = S::stride(d), base = S::line_base(d, m);
-    const int node = base + (side ? N : 0) * s;
+    const int rnode = base + (side ? N : 0) * s, node = SW(rnode);
     const int64_t eg = e0 + e;
-    const real* q = sq + e * NQ * NP;
-    const real* ja = sja + (e * DIM + d) * DIM * NP;
-    const real* ue = su + e * NV * NP;
-    real* sa = sacc + (e * DIM + d) * NV * NP + node;
+    const real* q = sq + e * L::SQ;
+    const real* ja = sja + e * L::SJA + d * DIM * NP;
+    const real* ue = su + e * L::SU;
+    real* sa = sacc + e * L::SACC + d * NV * NP + node;
     const real iw = side ? B.iw[N] : -B.iw[0];
     NodeState<real, DIM, NSP> o;
 #pragma unroll
-    for (int k = 0; k < NV; ++k) o.u[k] = ue[k * NP + node];
+    for (int k = 0; k < NV; ++k) o.u[k] = ue[k * NP + rnode];
     o.rho = q[node];
 #pragma unroll
     for (int c = 0; c < DIM; ++c) o.v[c] = q[(1 + c) * NP + node];
     o.p = q[(1 + DIM) * NP + node];
     o.c = NSP == 1 ? RealOps<real>::sqrt_(kc.gamma * o.p * RealOps<real>::rcp(o.rho))
-                   : spc[(e * 2 + 1) * NP + node];
+                   : spc[e * L::SPC + NP + node];
     real nface[DIM];
 #pragma unroll
     for (int c = 0; c < DIM; ++c) nface[c] = ja[c * NP + node];
@@ -453,7 +558,7 @@ rhs_kernel(const DgArgs a, const KConst kc) {
     for (int k = 0; k < NV; ++k) sa[k * NP] += iw * Fs[k];
     if (NS) {
       // viscous interface flux: mean of both sides' f^v . n, lifted as (Fv* - Fv)
-      const real* fvd = sfv + (e * L::NFV + d * (DIM + 1)) * NP + node;
+      const real* fvd = sfv + e * L::SFV + d * (DIM + 1) * NP + node;
       real gg[DIM][DIM + 1], fvn[DIM][DIM + 1];
 #pragma unroll
       for (int xx = 0; xx < DIM; ++xx)
@@ -474,9 +579,9 @@ rhs_kernel(const DgArgs a, const KConst kc) {
   // ---- phase C: one thread per node
   real lam_a = 0, lam_v = 0;
   for (int i = tid; i < ne * NP; i += nth) {
-    const int e = i / NP, node = i % NP;
-    const real ij = sij[e * NP + node];
-    const real* sa = sacc + e * DIM * NV * NP + node;
+    const int e = i / NP, node = i % NP, pn = SW(node);
+    const real ij = sij[e * L::SIJ + node];
+    const real* sa = sacc + e * L::SACC + pn;
     const int64_t gbase = (e0 + e) * NV * NP + node;
     if (a.mode == 0) {
       real* out = (real*)a.out;
@@ -502,10 +607,10 @@ rhs_kernel(const DgArgs a, const KConst kc) {
         real r = -ij * sum;
         if (NSP > 1 && k < NSP && a.src) r += ((const real*)a.src)[((e0 + e) * NSP + k) * NP + node];
         const real dold = !read_du ? real(0)
-                          : (L::PREFETCH_DU ? sdu[(e * NV + k) * NP + node] : du[gbase + k * NP]);
+                          : (L::PREFETCH_DU ? sdu[e * L::SDU + k * NP + node] : du[gbase + k * NP]);
         real dn = kc.rkA * dold + dt * r;
         du[gbase + k * NP] = dn;
-        un[k] = su[(e * NV + k) * NP + node] + kc.rkB * dn;
+        un[k] = su[e * L::SU + k * NP + node] + kc.rkB * dn;
         out[gbase + k * NP] = un[k];
       }
       if (a.want_lambda && NSP == 1) {
@@ -526,7 +631,7 @@ rhs_kernel(const DgArgs a, const KConst kc) {
           real vn = 0, nn = 0;
 #pragma unroll
           for (int cc = 0; cc < DIM; ++cc) {
-            real jv = sja[((e * DIM + dd) * DIM + cc) * NP + node];
+            real jv = sja[e * L::SJA + (dd * DIM + cc) * NP + pn];
             vn += v[cc] * jv;
             nn += jv * jv;
           }
