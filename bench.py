@@ -40,6 +40,9 @@ CONFIGS = {
 WORDS_MAIN_NS = 5 + 9 + 1 + 12 + 5 + 5 + 5
 WORDS_MAIN_EULER = 5 + 9 + 1 + 5 + 5 + 5
 WORDS_GRAD = 5 + 9 + 1 + 12
+# dram__bytes_read.sum + dram__bytes_write.sum of the current mixed-form NS N=3 rhs_kernel
+# per node, from one ncu capture of the 24^3 case (traffic scales with the node count)
+RHS_DRAM_B_PER_NODE = 129.0
 
 
 def _env_rank():
@@ -200,7 +203,9 @@ def run_ours(args, rank, world, local_rank):
         "e2e": {"value": e2e_value, "unit": "DOF*RHS/s", "h2d_bytes_per_step": dof * 8,
                 "d2h_bytes_per_step": dof * 8},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak,
+                     "traffic": (RHS_DRAM_B_PER_NODE * K * npn
+                                 if eq == dg.DG_NAVIER_STOKES and N == 3 else None),
                      "kernel": "rhs_kernel<3,%d,1,NS> f32" % N,
                      "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)"},
         "kernels": {k: {"ms_per_launch": v[0] / v[1], "launches": v[1]}

@@ -79,6 +79,9 @@ def lib():
             "or_mixture_eval": (i, [i, vp, i, vp, vp, vp, vp]),
             "or_temperature_field": (i, [vp, vp, vp]),
             "or_mlp_nparams": (i, []),
+            "or_mlp_nparams_n": (i, [i]),
+            "or_mlp_forward_n": (i, [vp, i, i, vp, vp]),
+            "or_mlp_loss_grad_n": (d, [vp, i, i, vp, vp, vp]),
             "or_chem_eval": (i, [vp, i, vp, i, vp, vp, d, vp, vp, vp]),
             "or_gelu": (d, [d]),
             "or_gelu_d": (d, [d]),
@@ -277,24 +280,28 @@ def chem_eval(species, reactions, rhos, T, dt=0.0):
     return om, jd, S
 
 
-def mlp_nparams():
-    return lib().or_mlp_nparams()
+def mlp_nparams(n_out=1):
+    return lib().or_mlp_nparams_n(n_out)
 
 
-def mlp_forward(params, X):
+def mlp_forward(params, X, n_out=1):
+    """Outputs [n] for one output, [n][n_out] otherwise."""
     params = np.ascontiguousarray(params, dtype=np.float64)
     X = np.ascontiguousarray(X, dtype=np.float64)
-    y = np.zeros(X.shape[0])
-    lib().or_mlp_forward(_p(params), X.shape[0], _p(X), _p(y))
-    return y
+    y = np.zeros((X.shape[0], n_out))
+    if lib().or_mlp_forward_n(_p(params), n_out, X.shape[0], _p(X), _p(y)):
+        raise ValueError("n_out out of range")
+    return y[:, 0] if n_out == 1 else y
 
 
-def mlp_loss_grad(params, X, t):
+def mlp_loss_grad(params, X, t, n_out=1):
     params = np.ascontiguousarray(params, dtype=np.float64)
     X = np.ascontiguousarray(X, dtype=np.float64)
     t = np.ascontiguousarray(t, dtype=np.float64)
     g = np.zeros_like(params)
-    loss = lib().or_mlp_loss_grad(_p(params), X.shape[0], _p(X), _p(t), _p(g))
+    loss = lib().or_mlp_loss_grad_n(_p(params), n_out, X.shape[0], _p(X), _p(t), _p(g))
+    if loss < 0:
+        raise ValueError("n_out out of range")
     return loss, g
 
 

@@ -1,12 +1,15 @@
 /*
- * Oracle (test infrastructure only): the learned temperature surrogate.
+ * Oracle (test infrastructure only): the learned surrogates (temperature: one output;
+ * chemistry source: ten outputs).
  *
- * The paper has no surrogate; this is the plain FP64 reference for the learned form
- * of the per-node temperature solve: a 7 -> 64 -> 64 -> 1 perceptron with the tanh
- * form of GELU, gelu(x) = x/2 (1 + tanh(sqrt(2/pi) (x + 0.044715 x^3)))
- * (Hendrycks & Gimpel), mean-squared-error loss, back-propagation written out layer
- * by layer, and the Adam update (Kingma & Ba) with bias correction.
- * Parameter vector layout: W1[64][7], b1[64], W2[64][64], b2[64], w3[64], b3.
+ * The paper has no surrogate; this is the plain FP64 reference for the learned forms of
+ * the per-node temperature solve and of the finite-rate source: a 7 -> 64 -> 64 -> n_out
+ * perceptron with the tanh form of GELU after both hidden layers,
+ * gelu(x) = x/2 (1 + tanh(sqrt(2/pi) (x + 0.044715 x^3))) (Hendrycks & Gimpel),
+ * mean-squared-error loss averaged over samples and outputs, back-propagation written
+ * out layer by layer, and the Adam update (Kingma & Ba) with bias correction.
+ * Parameter vector layout: W1[64][7], b1[64], W2[64][64], b2[64], W3[n_out][64],
+ * b3[n_out] (n_out = 1: w3[64], b3).
  */
 #include <math.h>
 #include <stdlib.h>
@@ -15,15 +18,16 @@
 
 #define NI 7
 #define NH 64
+#define NO_MAX 16
 #define OFF_W1 0
 #define OFF_B1 (OFF_W1 + NH * NI)
 #define OFF_W2 (OFF_B1 + NH)
 #define OFF_B2 (OFF_W2 + NH * NH)
 #define OFF_W3 (OFF_B2 + NH)
-#define OFF_B3 (OFF_W3 + NH)
-#define NPARAM (OFF_B3 + 1)
+#define OFF_B3(no) (OFF_W3 + (no) * NH)
 
-int or_mlp_nparams(void) { return NPARAM; }
+int or_mlp_nparams_n(int n_out) { return OFF_B3(n_out) + n_out; }
+int or_mlp_nparams(void) { return or_mlp_nparams_n(1); }
 
 double or_gelu(double x) {
   const double k = sqrt(2.0 / M_PI);
@@ -38,9 +42,9 @@ double or_gelu_d(double x) {
   return 0.5 * (1.0 + t) + 0.5 * x * (1.0 - t * t) * dz;
 }
 
-/* one sample: pre-activations a1, a2 and activations h1, h2; returns the output */
-static double forward1(const double* p, const double* x, double* a1, double* h1, double* a2,
-                       double* h2) {
+/* one sample: pre-activations a1, a2, activations h1, h2 and the n_out outputs y */
+static void forward1(const double* p, int no, const double* x, double* a1, double* h1, double* a2,
+                     double* h2, double* y) {
   for (int j = 0; j < NH; ++j) {
     double s = p[OFF_B1 + j];
     for (int i = 0; i < NI; ++i) s += p[OFF_W1 + j * NI + i] * x[i];
@@ -53,31 +57,44 @@ static double forward1(const double* p, const double* x, double* a1, double* h1,
     a2[j] = s;
     h2[j] = or_gelu(s);
   }
-  double y = p[OFF_B3];
-  for (int i = 0; i < NH; ++i) y += p[OFF_W3 + i] * h2[i];
-  return y;
+  for (int o = 0; o < no; ++o) {
+    double s = p[OFF_B3(no) + o];
+    for (int i = 0; i < NH; ++i) s += p[OFF_W3 + o * NH + i] * h2[i];
+    y[o] = s;
+  }
 }
 
-void or_mlp_forward(const double* p, int n, const double* X, double* y) {
+int or_mlp_forward_n(const double* p, int no, int n, const double* X, double* Y) {
+  if (no < 1 || no > NO_MAX) return 1;
   double a1[NH], h1[NH], a2[NH], h2[NH];
-  for (int s = 0; s < n; ++s) y[s] = forward1(p, X + (size_t)s * NI, a1, h1, a2, h2);
+  for (int s = 0; s < n; ++s) forward1(p, no, X + (size_t)s * NI, a1, h1, a2, h2, Y + (size_t)s * no);
+  return 0;
 }
 
-/* loss = (1/n) sum (y - t)^2 and its gradient with respect to every parameter */
-double or_mlp_loss_grad(const double* p, int n, const double* X, const double* t, double* g) {
-  double a1[NH], h1[NH], a2[NH], h2[NH], d2[NH], d1[NH];
-  memset(g, 0, sizeof(double) * NPARAM);
+void or_mlp_forward(const double* p, int n, const double* X, double* y) { or_mlp_forward_n(p, 1, n, X, y); }
+
+/* loss = (1/(n n_out)) sum_s sum_o (y_so - t_so)^2 and its gradient with respect to every
+ * parameter; returns the loss (negative on invalid n_out) */
+double or_mlp_loss_grad_n(const double* p, int no, int n, const double* X, const double* t, double* g) {
+  if (no < 1 || no > NO_MAX) return -1.0;
+  double a1[NH], h1[NH], a2[NH], h2[NH], d2[NH], d1[NH], y[NO_MAX], dy[NO_MAX];
+  memset(g, 0, sizeof(double) * or_mlp_nparams_n(no));
   double loss = 0.0;
+  const double scale = 1.0 / ((double)n * no);
   for (int s = 0; s < n; ++s) {
     const double* x = X + (size_t)s * NI;
-    double y = forward1(p, x, a1, h1, a2, h2);
-    double r = y - t[s];
-    loss += r * r;
-    double dy = 2.0 * r / n;
-    g[OFF_B3] += dy;
+    forward1(p, no, x, a1, h1, a2, h2, y);
+    for (int o = 0; o < no; ++o) {
+      double r = y[o] - t[(size_t)s * no + o];
+      loss += r * r;
+      dy[o] = 2.0 * r * scale;
+      g[OFF_B3(no) + o] += dy[o];
+      for (int i = 0; i < NH; ++i) g[OFF_W3 + o * NH + i] += dy[o] * h2[i];
+    }
     for (int i = 0; i < NH; ++i) {
-      g[OFF_W3 + i] += dy * h2[i];
-      d2[i] = dy * p[OFF_W3 + i] * or_gelu_d(a2[i]);
+      double back = 0.0;
+      for (int o = 0; o < no; ++o) back += dy[o] * p[OFF_W3 + o * NH + i];
+      d2[i] = back * or_gelu_d(a2[i]);
     }
     for (int j = 0; j < NH; ++j) {
       g[OFF_B2 + j] += d2[j];
@@ -93,7 +110,11 @@ double or_mlp_loss_grad(const double* p, int n, const double* X, const double* t
       for (int i = 0; i < NI; ++i) g[OFF_W1 + j * NI + i] += d1[j] * x[i];
     }
   }
-  return loss / n;
+  return loss * scale;
+}
+
+double or_mlp_loss_grad(const double* p, int n, const double* X, const double* t, double* g) {
+  return or_mlp_loss_grad_n(p, 1, n, X, t, g);
 }
 
 /* Adam with bias correction; step counts from 1 */

@@ -125,8 +125,12 @@ int or_chem_source(const double* species, int nr, const double* reac, const doub
 int or_chem_eval(const double* species, int nr, const double* reac, int n, const double* rhos,
                  const double* T, double dt, double* omega, double* jdiag, double* S);
 
-/* ---- learned temperature surrogate (or_mlp.c) ---- */
+/* ---- learned surrogates: temperature (1 output), chemistry source (10) (or_mlp.c) ---- */
 int or_mlp_nparams(void);
+int or_mlp_nparams_n(int n_out);
+int or_mlp_forward_n(const double* p, int n_out, int n, const double* X, double* Y);
+double or_mlp_loss_grad_n(const double* p, int n_out, int n, const double* X, const double* t,
+                          double* g);
 double or_gelu(double x);
 double or_gelu_d(double x);
 void or_mlp_forward(const double* p, int n, const double* X, double* y);

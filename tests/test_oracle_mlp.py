@@ -91,3 +91,66 @@ def test_training_reduces_loss_on_a_smooth_map(orc):
         _, g = orc.mlp_loss_grad(p, X, t)
         orc.adam_step(p, m, v, g, s, lr=3e-3)
     assert orc.mlp_loss_grad(p, X, t)[0] < 0.1 * l0
+
+
+# ---- several outputs (the chemistry-source surrogate has ten)
+
+def _slice(p, no, o):
+    """Parameters of the one-output network made of output row o of an no-output one."""
+    head = 64 * 7 + 64 + 64 * 64 + 64
+    w3 = p[head:head + no * 64].reshape(no, 64)
+    b3 = p[head + no * 64:]
+    return np.concatenate([p[:head], w3[o], [b3[o]]])
+
+
+def test_multi_output_layout(orc):
+    for no in (1, 2, 10, 16):
+        assert orc.mlp_nparams(no) == 64 * 7 + 64 + 64 * 64 + 64 + no * 64 + no
+    assert orc.mlp_nparams(1) == orc.mlp_nparams()
+
+
+def test_multi_output_rows_are_independent_heads(orc):
+    """Output o of an n_out network equals the one-output network of row o (forward), and
+    loss / gradients are the averages over outputs of the single-output ones: the shared
+    hidden layers receive the mean of the heads' back-propagated signals."""
+    rng = np.random.default_rng(5)
+    no = 10
+    p = 0.3 * rng.normal(size=orc.mlp_nparams(no))
+    X = rng.normal(size=(6, 7))
+    T = rng.normal(size=(6, no))
+    Y = orc.mlp_forward(p, X, no)
+    assert Y.shape == (6, no)
+    loss, g = orc.mlp_loss_grad(p, X, T, no)
+    head = 64 * 7 + 64 + 64 * 64 + 64
+    g_shared = np.zeros(head)
+    l_sum = 0.0
+    for o in range(no):
+        q = _slice(p, no, o)
+        assert np.allclose(orc.mlp_forward(q, X), Y[:, o], rtol=0, atol=1e-14)
+        lo, go = orc.mlp_loss_grad(q, X, T[:, o])
+        l_sum += lo
+        g_shared += go[:head]
+        # the head's own weights: gradient of the mean loss = gradient of its loss / no
+        assert np.allclose(g[head + o * 64:head + (o + 1) * 64], go[head:head + 64] / no, rtol=1e-12, atol=1e-16)
+        assert abs(g[head + no * 64 + o] - go[-1] / no) < 1e-14
+    assert abs(loss - l_sum / no) < 1e-13 * max(1.0, loss)
+    assert np.allclose(g[:head], g_shared / no, rtol=1e-11, atol=1e-15)
+
+
+def test_multi_output_gradient_matches_finite_differences(orc):
+    rng = np.random.default_rng(7)
+    no = 10
+    p = 0.3 * rng.normal(size=orc.mlp_nparams(no))
+    X = rng.normal(size=(4, 7))
+    T = rng.normal(size=(4, no))
+    loss, g = orc.mlp_loss_grad(p, X, T, no)
+    idx = np.concatenate([rng.choice(len(p), size=40, replace=False), [len(p) - 1, len(p) - no - 1]])
+    for i in idx:
+        h = 1e-5 * max(1.0, abs(p[i]))
+        pp, pm = p.copy(), p.copy()
+        pp[i] += h
+        pm[i] -= h
+        fd = (orc.mlp_loss_grad(pp, X, T, no)[0] - orc.mlp_loss_grad(pm, X, T, no)[0]) / (2 * h)
+        assert abs(fd - g[i]) < 1e-6 * abs(g[i]) + 2e-9, (i, fd, g[i])
+    Y = orc.mlp_forward(p, X, no)
+    assert abs(loss - np.mean((Y - T) ** 2)) < 1e-14 * max(1, loss)
