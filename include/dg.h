@@ -141,46 +141,86 @@ dg_status dg_diagnostics(dg_ctx* ctx, double out[8]);
  * DG_EINVAL for a single-gas context. Synchronises. */
 dg_status dg_get_temperature(dg_ctx* ctx, double* T);
 
-/* ---- learned temperature surrogate (no counterpart in the paper: the learned form of
- * the per-node temperature solve of Eqs. total_energy / internal_energies / eos).
- * Network 7 -> 64 -> 64 -> 1, GELU (tanh form); inputs standardised
- * (Y_1..Y_5, ln rho, e), output standardised T.  Parameter vector (FP32, P =
- * dg_mlp_nparams()): W1[64][7], b1[64], W2[64][64], b2[64], w3[64], b3.
- * Normalisation stats (FP64, 16): mean[7], std[7], mean_T, std_T. */
+/* ---- learned surrogates (no counterpart in the paper).  Both are a perceptron
+ * 7 -> 64 -> 64 -> n_out with the tanh form of GELU after the hidden layers, evaluated
+ * with BF16 tensor-core MMAs (FP32 accumulation) and always checked against the plain
+ * FP64 computation they replace, which remains the fallback.  Parameter vector (FP32,
+ * P = dg_mlp_nparams(n_out)): W1[64][7], b1[64], W2[64][64], b2[64], W3[n_out][64],
+ * b3[n_out].
+ *
+ * DG_SURROGATE_TEMPERATURE (n_out = 1): the per-node temperature solve of Eqs.
+ *   total_energy / internal_energies / eos.  Inputs standardised (Y_1..Y_5, ln rho, e),
+ *   output standardised T; stats (FP64, 16): mean[7], std[7], mean_T, std_T.  Every
+ *   prediction gets one FP64 Newton step and is accepted when the next correction would
+ *   be <= 1e-6 T, otherwise the plain Newton iteration runs (per node).
+ * DG_SURROGATE_SOURCE (n_out = 10): the finite-rate source of Eqs. nrp / forward_rate /
+ *   backward / calc_prod with its point-implicit terms.  Inputs standardised
+ *   (Y_1..Y_5, ln rho, T); outputs the standardised z_s = asinh(omega_s / omega_ref) and
+ *   z_{5+s} = asinh(jpi_s / jpi_ref), jpi_s = max(0, -d omega_s / d rho_s), so that
+ *   S_s = omega_s / (1 + dt jpi_s) for any RK step dt.  Stats (FP64, DG_SRC_NSTATS)
+ *   indexed by the DG_SRC_* offsets below.  Acceptance per tile of 32 consecutive nodes:
+ *   every node's raw features inside the training box, every node's raw rates
+ *   mass-balanced (|sum omega| <= tol_mass sum |omega|), and, at one node per tile drawn
+ *   anew each evaluation, |S_learned - S_plain| <= tol_check sum_s |S_plain| + floor for
+ *   every species; rejected tiles are recomputed with the plain FP64 source.  Accepted
+ *   rates are projected onto exact mass balance, omega_s -= |omega_s| sum omega / sum|omega|. */
+enum { DG_SURROGATE_TEMPERATURE = 0, DG_SURROGATE_SOURCE = 1 };
+enum {
+  DG_SRC_X_MEAN = 0,      /* [7] feature means (Y_1..Y_5, ln rho, T) */
+  DG_SRC_X_STD = 7,       /* [7] feature standard deviations */
+  DG_SRC_Y_MEAN = 14,     /* [10] target means (asinh images) */
+  DG_SRC_Y_STD = 24,      /* [10] target standard deviations */
+  DG_SRC_OMEGA_REF = 34,  /* omega_ref, kg/(m^3 s) */
+  DG_SRC_JPI_REF = 35,    /* jpi_ref, 1/s */
+  DG_SRC_BOX_LO = 36,     /* [7] trust box: smallest raw feature values of the training set */
+  DG_SRC_BOX_HI = 43,     /* [7] largest */
+  DG_SRC_TOL_CHECK = 50,  /* sampled-node check, relative tolerance */
+  DG_SRC_TOL_MASS = 51,   /* raw mass-balance tolerance */
+  DG_SRC_FLOOR = 52,      /* sampled-node check, absolute floor, kg/(m^3 s) */
+  DG_SRC_NSTATS = 53
+};
 
-/* Load (params, stats: host arrays) into a mixture context and switch its temperature
- * solve to BF16 tensor-core inference + one FP64 Newton polish + residual check
- * (accept when the next Newton correction is <= 1e-6 T) with the plain Newton
- * iteration as fallback.  params == NULL switches back to the plain Newton solve.
- * which must be 0 (temperature surrogate). */
+/* Load (params, stats: host arrays) into a mixture context and switch the temperature
+ * solve (which = DG_SURROGATE_TEMPERATURE) or the chemistry source (which =
+ * DG_SURROGATE_SOURCE, reacting contexts only) to the learned form described above.
+ * params == NULL switches back to the plain computation.  DG_EINVAL for a single-gas
+ * context, a frozen mixture with DG_SURROGATE_SOURCE, or non-positive deviations. */
 dg_status dg_set_surrogate(dg_ctx* ctx, int which, const float* params, const double* stats);
 
-/* Nodes accepted after the polish and nodes sent to the fallback since the last call
- * (host int64[2]); resets the counters. */
-dg_status dg_surrogate_stats(dg_ctx* ctx, int64_t* accepted_fallback);
+/* Nodes accepted and nodes recomputed plainly by the surrogate `which` since the last
+ * call (host int64[2]); resets the counters. */
+dg_status dg_surrogate_stats(dg_ctx* ctx, int which, int64_t* accepted_fallback);
 
 /* Training data from the plain solver: runs the temperature solve on the current state,
  * then writes n samples drawn with splitmix64(seed + j) over all nodes:
  * X [n][7] raw features (Y_1..Y_5, ln rho, e) and T [n] (device float arrays). */
 dg_status dg_thermo_sample(dg_ctx* ctx, int64_t n, uint64_t seed, float* X, float* T);
 
-int dg_mlp_nparams(void);
-/* Workspace bytes that dg_mlp_grad / dg_mlp_train_step need for a batch. */
-size_t dg_mlp_workspace_bytes(int batch);
-/* Gradient of loss = mean((y - t)^2) over a batch (FP32 back-propagation, fixed-order
- * reduction): params [P], X [batch][7] standardised inputs, t [batch] standardised
- * targets, grad [P] out, loss (device double*, may be NULL); all device pointers. */
-dg_status dg_mlp_grad(const float* params, const float* X, const float* t, int batch, float* grad,
-                      double* loss, float* workspace, size_t ws_bytes, void* stream);
+/* Training data for the source surrogate (reacting contexts): runs the temperature solve
+ * on the current state, then for n nodes drawn with splitmix64(seed + j): X [n][7] raw
+ * features (Y_1..Y_5, ln rho, T) (device float) and targets [n][10] = (omega_1..5,
+ * jpi_1..5) of the plain FP64 source (device double). */
+dg_status dg_chem_sample(dg_ctx* ctx, int64_t n, uint64_t seed, float* X, double* targets);
+
+/* ---- training and checking kernels (device pointers, queued on `stream`) */
+/* Parameter count for n_out outputs (1..16), -1 otherwise. */
+int dg_mlp_nparams(int n_out);
+/* Workspace bytes that dg_mlp_grad / dg_mlp_train_step need for a batch (0 if invalid). */
+size_t dg_mlp_workspace_bytes(int batch, int n_out);
+/* Gradient of loss = mean over samples and outputs of (y - t)^2 (FP32 back-propagation,
+ * fixed-order reduction): params [P], X [batch][7] standardised inputs, t [batch][n_out]
+ * standardised targets, grad [P] out, loss (device double*, may be NULL). */
+dg_status dg_mlp_grad(const float* params, int n_out, const float* X, const float* t, int batch,
+                      float* grad, double* loss, float* workspace, size_t ws_bytes, void* stream);
 /* One Adam step (beta = 0.9, 0.999, eps = 1e-8, bias-corrected, step >= 1) on the same
- * loss; params, m, v updated in place (device). */
-dg_status dg_mlp_train_step(float* params, float* m, float* v, const float* X, const float* t,
-                            int batch, int step, float lr, double* loss, float* workspace,
-                            size_t ws_bytes, void* stream);
-/* y[n] = network(X[n][7]) for standardised X (device); tensor_cores = 1 uses the BF16
- * MMA path of the inference kernel, 0 the FP32 path.  stats may be NULL. */
-dg_status dg_mlp_forward(const float* params, const double* stats, const float* X, float* y,
-                         int64_t n, int tensor_cores, void* stream);
+ * loss; params, m, v updated in place. */
+dg_status dg_mlp_train_step(float* params, int n_out, float* m, float* v, const float* X,
+                            const float* t, int batch, int step, float lr, double* loss,
+                            float* workspace, size_t ws_bytes, void* stream);
+/* y[n][n_out] = network(X[n][7]) for standardised X; tensor_cores = 1 uses the BF16 MMA
+ * path of the inference kernels (n_out 1 or 10; synchronises), 0 the FP32 path. */
+dg_status dg_mlp_forward(const float* params, int n_out, const float* X, float* y, int64_t n,
+                         int tensor_cores, void* stream);
 
 /* Blending factors alpha [K] used by the last right-hand side (FP64, host). */
 dg_status dg_get_alpha(dg_ctx* ctx, double* alpha);

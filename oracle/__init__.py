@@ -305,6 +305,36 @@ def mlp_loss_grad(params, X, t, n_out=1):
     return loss, g
 
 
+def chem_surrogate_source(params, stats, rhos, T, dt=0.0):
+    """FP64 evaluation of the learned chemistry source at nodes (rhos [n][5] species
+    densities, T [n]) with the ten-output perceptron and the statistics vector of the
+    C interface (offsets: feature mean 0, std 7; target mean 14, std 24; omega_ref 34,
+    jpi_ref 35; box lo 36, hi 43; tolerances 50 (check), 51 (mass), floor 52).
+
+    Steps: raw features x = (Y_1..Y_5, ln rho, T); network on (x - mean)/std; decode
+    omega_s = omega_ref sinh(mu_s + sd_s y_s), jpi_s = max(0, jpi_ref sinh(mu_{5+s} +
+    sd_{5+s} y_{5+s})); node accepted when x lies in the box and |sum omega| <=
+    tol_mass sum|omega|; projection omega_s -= |omega_s| sum(omega)/sum|omega|;
+    S_s = omega_s / (1 + dt jpi_s).  Returns (S [n][5], accepted [n] bool, omega raw
+    [n][5], jpi [n][5])."""
+    st = np.asarray(stats, dtype=np.float64)
+    rhos = np.asarray(rhos, dtype=np.float64)
+    T = np.asarray(T, dtype=np.float64)
+    rho = rhos.sum(axis=1)
+    x = np.column_stack([rhos / rho[:, None], np.log(rho), T])
+    y = mlp_forward(params, (x - st[0:7]) / st[7:14], 10)
+    z = st[14:24] + st[24:34] * y
+    om = st[34] * np.sinh(z[:, :5])
+    jpi = np.maximum(0.0, st[35] * np.sinh(z[:, 5:]))
+    msum = om.sum(axis=1)
+    asum = np.abs(om).sum(axis=1)
+    inside = np.all((x >= st[36:43]) & (x <= st[43:50]), axis=1)
+    accepted = inside & (np.abs(msum) <= st[51] * asum)
+    frac = np.divide(msum, asum, out=np.zeros_like(msum), where=asum > 0)
+    S = (om - np.abs(om) * frac[:, None]) / (1.0 + dt * jpi)
+    return S, accepted, om, jpi
+
+
 def adam_step(params, m, v, g, step, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
     """In-place Adam update of float64 arrays."""
     lib().or_adam_step(_p(params), _p(m), _p(v), _p(np.ascontiguousarray(g)), len(params), step,

@@ -35,7 +35,7 @@ EXPORTED = [
     "dg_error_element", "dg_status_string", "dg_destroy", "dg_profile", "dg_profile_read",
     "dg_rhs_ns_noalloc", "dg_get_temperature", "dg_set_surrogate", "dg_surrogate_stats",
     "dg_thermo_sample", "dg_mlp_nparams", "dg_mlp_workspace_bytes", "dg_mlp_grad",
-    "dg_mlp_train_step", "dg_mlp_forward", "dg_peak_flops",
+    "dg_mlp_train_step", "dg_mlp_forward", "dg_peak_flops", "dg_chem_sample",
 ]
 PROF_KINDS = ["rhs", "gradients", "indicator", "lambda", "thermo", "mlp", "chem", "other"]
 
@@ -92,14 +92,15 @@ def lib():
             "dg_rhs_ns_noalloc": (i, [i, i64, vp, vp, vp, d, d, d, i, i, vp, vp, vp]),
             "dg_get_temperature": (i, [vp, vp]),
             "dg_set_surrogate": (i, [vp, i, vp, vp]),
-            "dg_surrogate_stats": (i, [vp, vp]),
+            "dg_surrogate_stats": (i, [vp, i, vp]),
+            "dg_chem_sample": (i, [vp, i64, C.c_uint64, vp, vp]),
             "dg_thermo_sample": (i, [vp, i64, C.c_uint64, vp, vp]),
-            "dg_mlp_nparams": (i, []),
-            "dg_mlp_workspace_bytes": (C.c_size_t, [i]),
-            "dg_mlp_grad": (i, [vp, vp, vp, i, vp, vp, vp, C.c_size_t, vp]),
-            "dg_mlp_train_step": (i, [vp, vp, vp, vp, vp, i, i, C.c_float, vp, vp, C.c_size_t,
+            "dg_mlp_nparams": (i, [i]),
+            "dg_mlp_workspace_bytes": (C.c_size_t, [i, i]),
+            "dg_mlp_grad": (i, [vp, i, vp, vp, i, vp, vp, vp, C.c_size_t, vp]),
+            "dg_mlp_train_step": (i, [vp, i, vp, vp, vp, vp, i, i, C.c_float, vp, vp, C.c_size_t,
                                       vp]),
-            "dg_mlp_forward": (i, [vp, vp, vp, vp, i64, i, vp]),
+            "dg_mlp_forward": (i, [vp, i, vp, vp, i64, i, vp]),
             "dg_peak_flops": (i, [i, i, vp]),
         }
         for name, (res, args) in sig.items():
@@ -177,16 +178,22 @@ def dg_get_temperature(ctx, shape):
     return T
 
 
-def dg_set_surrogate(ctx, params=None, stats=None, which=0):
-    """params: host float32 [P] (or None to switch the surrogate off); stats: float64 [16]."""
+DG_SURROGATE_TEMPERATURE = 0
+DG_SURROGATE_SOURCE = 1
+DG_SRC_NSTATS = 53
+
+
+def dg_set_surrogate(ctx, params=None, stats=None, which=DG_SURROGATE_TEMPERATURE):
+    """params: host float32 [P] (or None to switch the surrogate off); stats: float64
+    [16] (temperature) or [DG_SRC_NSTATS] (source)."""
     p = None if params is None else np.ascontiguousarray(params, dtype=np.float32)
     s = None if stats is None else np.ascontiguousarray(stats, dtype=np.float64)
     _check(lib().dg_set_surrogate(ctx, which, _ptr(p), _ptr(s)), "dg_set_surrogate")
 
 
-def dg_surrogate_stats(ctx):
+def dg_surrogate_stats(ctx, which=DG_SURROGATE_TEMPERATURE):
     out = np.zeros(2, dtype=np.int64)
-    _check(lib().dg_surrogate_stats(ctx, _ptr(out)), "dg_surrogate_stats")
+    _check(lib().dg_surrogate_stats(ctx, which, _ptr(out)), "dg_surrogate_stats")
     return int(out[0]), int(out[1])
 
 
@@ -195,30 +202,41 @@ def dg_thermo_sample(ctx, X, T, seed=0):
     _check(lib().dg_thermo_sample(ctx, T.shape[0], seed, _ptr(X), _ptr(T)), "dg_thermo_sample")
 
 
-def dg_mlp_nparams():
-    return lib().dg_mlp_nparams()
+def dg_chem_sample(ctx, X, targets, seed=0):
+    """X: device float32 [n][7] (Y_1..Y_5, ln rho, T); targets: device float64 [n][10]
+    (omega_1..5, jpi_1..5) of the plain source."""
+    _check(lib().dg_chem_sample(ctx, targets.shape[0], seed, _ptr(X), _ptr(targets)), "dg_chem_sample")
 
 
-def dg_mlp_workspace_bytes(batch):
-    return lib().dg_mlp_workspace_bytes(batch)
+def _n_out(t):
+    return 1 if t.dim() == 1 else t.shape[1]
+
+
+def dg_mlp_nparams(n_out=1):
+    return lib().dg_mlp_nparams(n_out)
+
+
+def dg_mlp_workspace_bytes(batch, n_out=1):
+    return lib().dg_mlp_workspace_bytes(batch, n_out)
 
 
 def dg_mlp_grad(params, X, t, grad, loss, workspace, stream=None):
-    _check(lib().dg_mlp_grad(_ptr(params), _ptr(X), _ptr(t), t.shape[0], _ptr(grad), _ptr(loss),
+    """t: [batch] (one output) or [batch][n_out] standardised targets (device float32)."""
+    _check(lib().dg_mlp_grad(_ptr(params), _n_out(t), _ptr(X), _ptr(t), t.shape[0], _ptr(grad), _ptr(loss),
                              _ptr(workspace), workspace.numel() * workspace.element_size(), stream),
            "dg_mlp_grad")
 
 
 def dg_mlp_train_step(params, m, v, X, t, step, lr, loss, workspace, stream=None):
-    _check(lib().dg_mlp_train_step(_ptr(params), _ptr(m), _ptr(v), _ptr(X), _ptr(t), t.shape[0],
+    _check(lib().dg_mlp_train_step(_ptr(params), _n_out(t), _ptr(m), _ptr(v), _ptr(X), _ptr(t), t.shape[0],
                                    step, lr, _ptr(loss), _ptr(workspace),
                                    workspace.numel() * workspace.element_size(), stream),
            "dg_mlp_train_step")
 
 
-def dg_mlp_forward(params, X, y, tensor_cores=1, stats=None, stream=None):
-    s = None if stats is None else np.ascontiguousarray(stats, dtype=np.float64)
-    _check(lib().dg_mlp_forward(_ptr(params), _ptr(s), _ptr(X), _ptr(y), y.shape[0],
+def dg_mlp_forward(params, X, y, tensor_cores=1, stream=None):
+    """y: [n] (one output) or [n][n_out] device float32."""
+    _check(lib().dg_mlp_forward(_ptr(params), _n_out(y), _ptr(X), _ptr(y), y.shape[0],
                                 int(tensor_cores), stream), "dg_mlp_forward")
 
 

@@ -862,20 +862,37 @@ dg_status dg_get_temperature(dg_ctx* c, double* T) {
 }
 
 dg_status dg_set_surrogate(dg_ctx* c, int which, const float* params, const double* stats) {
-  if (!c || which != 0 || c->n_species == 0 || (params && !stats)) return DG_EINVAL;
+  if (!c || c->n_species == 0 || (params && !stats)) return DG_EINVAL;
+  if (which != DG_SURROGATE_TEMPERATURE && which != DG_SURROGATE_SOURCE) return DG_EINVAL;
+  if (which == DG_SURROGATE_SOURCE && c->th.nr == 0) return DG_EINVAL;
   cudaSetDevice(c->dev);
-  if (params)
+  if (params) {
+    const int std_off = which == DG_SURROGATE_TEMPERATURE ? 7 : DG_SRC_X_STD;
     for (int q = 0; q < 7; ++q)
-      if (!(stats[7 + q] > 0.0)) return DG_EINVAL;
+      if (!(stats[std_off + q] > 0.0)) return DG_EINVAL;
+    if (which == DG_SURROGATE_SOURCE) {
+      for (int q = 0; q < 10; ++q)
+        if (!(stats[DG_SRC_Y_STD + q] > 0.0)) return DG_EINVAL;
+      if (!(stats[DG_SRC_OMEGA_REF] > 0.0) || !(stats[DG_SRC_JPI_REF] > 0.0) ||
+          !(stats[DG_SRC_TOL_CHECK] >= 0.0) || !(stats[DG_SRC_TOL_MASS] >= 0.0) || !(stats[DG_SRC_FLOOR] >= 0.0))
+        return DG_EINVAL;
+    }
+  }
   CK(cudaStreamSynchronize(c->stream));
+  if (which == DG_SURROGATE_SOURCE) {
+    CK(dg_chem_mlp_set(&c->th, params, stats));
+    return DG_OK;
+  }
   CK(dg_mlp_set(&c->th, params, stats));
   c->th.mode = params ? DG_THERMO_MLP : DG_THERMO_NEWTON;
   return DG_OK;
 }
 
-dg_status dg_surrogate_stats(dg_ctx* c, int64_t* out) {
+dg_status dg_surrogate_stats(dg_ctx* c, int which, int64_t* out) {
   if (!c || !out || c->n_species == 0) return DG_EINVAL;
-  if (!c->th.mlp_stats) {
+  if (which != DG_SURROGATE_TEMPERATURE && which != DG_SURROGATE_SOURCE) return DG_EINVAL;
+  unsigned long long* dev = which == DG_SURROGATE_SOURCE ? c->th.chem_stats : c->th.mlp_stats;
+  if (!dev) {
     out[0] = out[1] = 0;
     return DG_OK;
   }
@@ -883,11 +900,22 @@ dg_status dg_surrogate_stats(dg_ctx* c, int64_t* out) {
   dg_status w = wait_stream(c);
   if (w != DG_OK) return w;
   unsigned long long h[2];
-  CK(cudaMemcpy(h, c->th.mlp_stats, sizeof(h), cudaMemcpyDeviceToHost));
-  CK(cudaMemset(c->th.mlp_stats, 0, sizeof(h)));
+  CK(cudaMemcpy(h, dev, sizeof(h), cudaMemcpyDeviceToHost));
+  CK(cudaMemset(dev, 0, sizeof(h)));
   out[0] = (int64_t)h[0];
   out[1] = (int64_t)h[1];
   return DG_OK;
+}
+
+dg_status dg_chem_sample(dg_ctx* c, int64_t n, uint64_t seed, float* X, double* targets) {
+  if (!c || n < 1 || !X || !targets || c->n_species == 0 || c->th.nr == 0) return DG_EINVAL;
+  if (!c->have_state) return DG_ESTATE;
+  cudaSetDevice(c->dev);
+  CK(run_thermo(c, c->u[c->cur]));
+  CK(dg_chem_sample_dev(&c->th, c->u[c->cur], c->precision == DG_MIXED, n, seed, X, targets, c->stream));
+  dg_status w = wait_stream(c);
+  if (w != DG_OK) return w;
+  return take_status(c, NULL);
 }
 
 dg_status dg_thermo_sample(dg_ctx* c, int64_t n, uint64_t seed, float* X, float* T) {

@@ -11,9 +11,12 @@
 // Jacobian at fixed T, dt = the running RK step (0 outside RK stepping).
 #include <cuda_runtime.h>
 #include <math.h>
+#include <stdlib.h>
 #include <string.h>
 
+#include "../../include/dg.h"
 #include "dg_internal.h"
+#include "dg_mlp.cuh"
 #include "dg_thermo.h"
 
 #define NSPEC 5
@@ -29,6 +32,77 @@ __device__ __forceinline__ double ipow012(double c, double nu) {
   return r;
 }
 
+// Plain FP64 source at one node: omega_s (kg/m^3/s) and the point-implicit terms
+// jpi_s = max(0, -d omega_s / d rho_s) of the analytic diagonal Jacobian at fixed T.
+// uu points at the node's first species density, stride np between variables.
+template <typename T>
+__device__ __forceinline__ void chem_node(const T* uu, int np, double Tk, const double* sp_raw,
+                                          const double* reac, int nr, double* om, double* jpi) {
+  const double lnT = log(Tk), iT = 1.0 / Tk;
+  double c[NSPEC], g[NSPEC], jd[NSPEC];
+#pragma unroll
+  for (int s = 0; s < NSPEC; ++s) {
+    const double* a = sp_raw + 8 * s + 1;
+    c[s] = 1e-6 * (double)uu[s * np] / sp_raw[8 * s];
+    const double h = a[0] + Tk * (a[1] / 2.0 + Tk * (a[2] / 3.0 + Tk * (a[3] / 4.0 + Tk * a[4] / 5.0))) + a[5] * iT;
+    const double sr = a[0] * lnT + Tk * (a[1] + Tk * (a[2] / 2.0 + Tk * (a[3] / 3.0 + Tk * a[4] / 4.0))) + a[6];
+    g[s] = h - sr;
+    om[s] = 0.0;
+    jd[s] = 0.0;
+  }
+  const double lnP = log(1e-6 * DG_P0 / (DG_RU * Tk));
+  for (int r = 0; r < nr; ++r) {
+    const double* row = reac + 20 * r;  // [nu'(5), nu''(5), tb, eff(5), lnA, beta, theta, 0]
+    double dg = 0.0, dn = 0.0;
+#pragma unroll
+    for (int s = 0; s < NSPEC; ++s) {
+      const double d = row[5 + s] - row[s];
+      dg += d * g[s];
+      dn += d;
+    }
+    const double lnkf = row[16] + row[17] * lnT - row[18] * iT;
+    const double kf = exp(lnkf);
+    const double kb = exp(lnkf + dg - dn * lnP);
+    double pf = kf, pb = kb;
+#pragma unroll
+    for (int s = 0; s < NSPEC; ++s) {
+      pf *= ipow012(c[s], row[s]);
+      pb *= ipow012(c[s], row[5 + s]);
+    }
+    double M = 1.0;
+    const bool tb = row[10] != 0.0;
+    if (tb) {
+      M = 0.0;
+#pragma unroll
+      for (int s = 0; s < NSPEC; ++s) M += row[11 + s] * c[s];
+    }
+    const double Rr = (pf - pb) * M;
+#pragma unroll
+    for (int s = 0; s < NSPEC; ++s) {
+      const double d = row[5 + s] - row[s];
+      om[s] += 1e6 * sp_raw[8 * s] * d * Rr;
+      // d R_r / d c_s (explicit products when c_s = 0)
+      double dpf = 0.0, dpb = 0.0;
+      if (c[s] > 0.0) {
+        dpf = row[s] > 0.0 ? pf * row[s] / c[s] : 0.0;
+        dpb = row[5 + s] > 0.0 ? pb * row[5 + s] / c[s] : 0.0;
+      } else {
+        if (row[s] == 1.0) {
+          dpf = kf;
+          for (int q = 0; q < NSPEC; ++q) if (q != s) dpf *= ipow012(c[q], row[q]);
+        }
+        if (row[5 + s] == 1.0) {
+          dpb = kb;
+          for (int q = 0; q < NSPEC; ++q) if (q != s) dpb *= ipow012(c[q], row[5 + q]);
+        }
+      }
+      jd[s] += d * ((dpf - dpb) * M + (tb ? (pf - pb) * row[11 + s] : 0.0));
+    }
+  }
+#pragma unroll
+  for (int s = 0; s < NSPEC; ++s) jpi[s] = -jd[s] > 0.0 ? -jd[s] : 0.0;
+}
+
 template <typename T>
 __global__ void chem_kernel(const T* u, const double* Tc, int64_t K, int np, int dim,
                             const double* sp_raw, const double* reac, int nr, const double* dtp,
@@ -39,75 +113,199 @@ __global__ void chem_kernel(const T* u, const double* Tc, int64_t K, int np, int
        i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t k = i / np;
     const int node = (int)(i % np);
-    const T* uu = u + k * nv * np + node;
-    const double Tk = Tc[k * np + node];
-    const double lnT = log(Tk), iT = 1.0 / Tk;
-    double c[NSPEC], g[NSPEC], om[NSPEC], jd[NSPEC];
-#pragma unroll
-    for (int s = 0; s < NSPEC; ++s) {
-      const double* a = sp_raw + 8 * s + 1;
-      c[s] = 1e-6 * (double)uu[s * np] / sp_raw[8 * s];
-      const double h = a[0] + Tk * (a[1] / 2.0 + Tk * (a[2] / 3.0 + Tk * (a[3] / 4.0 + Tk * a[4] / 5.0))) + a[5] * iT;
-      const double sr = a[0] * lnT + Tk * (a[1] + Tk * (a[2] / 2.0 + Tk * (a[3] / 3.0 + Tk * a[4] / 4.0))) + a[6];
-      g[s] = h - sr;
-      om[s] = 0.0;
-      jd[s] = 0.0;
-    }
-    const double lnP = log(1e-6 * DG_P0 / (DG_RU * Tk));
-    for (int r = 0; r < nr; ++r) {
-      const double* row = reac + 20 * r;  // [nu'(5), nu''(5), tb, eff(5), lnA, beta, theta, 0]
-      double dg = 0.0, dn = 0.0;
-#pragma unroll
-      for (int s = 0; s < NSPEC; ++s) {
-        const double d = row[5 + s] - row[s];
-        dg += d * g[s];
-        dn += d;
-      }
-      const double lnkf = row[16] + row[17] * lnT - row[18] * iT;
-      const double kf = exp(lnkf);
-      const double kb = exp(lnkf + dg - dn * lnP);
-      double pf = kf, pb = kb;
-#pragma unroll
-      for (int s = 0; s < NSPEC; ++s) {
-        pf *= ipow012(c[s], row[s]);
-        pb *= ipow012(c[s], row[5 + s]);
-      }
-      double M = 1.0;
-      const bool tb = row[10] != 0.0;
-      if (tb) {
-        M = 0.0;
-#pragma unroll
-        for (int s = 0; s < NSPEC; ++s) M += row[11 + s] * c[s];
-      }
-      const double Rr = (pf - pb) * M;
-#pragma unroll
-      for (int s = 0; s < NSPEC; ++s) {
-        const double d = row[5 + s] - row[s];
-        om[s] += 1e6 * sp_raw[8 * s] * d * Rr;
-        // d R_r / d c_s (explicit products when c_s = 0)
-        double dpf = 0.0, dpb = 0.0;
-        if (c[s] > 0.0) {
-          dpf = row[s] > 0.0 ? pf * row[s] / c[s] : 0.0;
-          dpb = row[5 + s] > 0.0 ? pb * row[5 + s] / c[s] : 0.0;
-        } else {
-          if (row[s] == 1.0) {
-            dpf = kf;
-            for (int q = 0; q < NSPEC; ++q) if (q != s) dpf *= ipow012(c[q], row[q]);
-          }
-          if (row[5 + s] == 1.0) {
-            dpb = kb;
-            for (int q = 0; q < NSPEC; ++q) if (q != s) dpb *= ipow012(c[q], row[5 + q]);
-          }
-        }
-        jd[s] += d * ((dpf - dpb) * M + (tb ? (pf - pb) * row[11 + s] : 0.0));
-      }
-    }
+    double om[NSPEC], jpi[NSPEC];
+    chem_node<T>(u + k * nv * np + node, np, Tc[i], sp_raw, reac, nr, om, jpi);
     T* so = src + k * NSPEC * np + node;
 #pragma unroll
-    for (int s = 0; s < NSPEC; ++s) {
-      const double dj = -jd[s] > 0.0 ? -jd[s] : 0.0;
-      so[s * np] = (T)(om[s] / (1.0 + dt * dj));
+    for (int s = 0; s < NSPEC; ++s) so[s * np] = (T)(om[s] / (1.0 + dt * jpi[s]));
+  }
+}
+
+// ------------------------------------------------------------------ learned source
+// Surrogate of (omega, jpi): 7 -> 64 -> 64 -> 10 perceptron on standardised features
+// (Y_1..Y_5, ln rho, T); outputs are the standardised asinh images
+// z_s = asinh(omega_s / omega_ref), z_{5+s} = asinh(jpi_s / jpi_ref).
+// Acceptance, per tile of 32 nodes (one warp): every node inside the training box, every
+// node's raw rates mass-balanced within tol_mass, and one sampled node per tile (moved
+// each call) within tol_check of the plain FP64 source; otherwise the tile's source is
+// recomputed plainly.  Accepted rates are projected onto exact mass balance:
+// omega_s -= |omega_s| sum(omega) / sum|omega|.
+struct __align__(16) DgChemMlp {
+  DgMlpW<10> w;
+  float mean[7], inv_std[7], muY[10], sdY[10], lo[7], hi[7];
+  float w_ref, j_ref, tol_mass, pad;
+  double tol_check, floor;
+};
+
+#define CM_WARPS 4
+
+__device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
+  x += 0x9E3779B97F4A7C15ull;
+  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+  x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+  return x ^ (x >> 31);
+}
+
+// raw features of one node: Y_1..Y_5, ln rho, T
+template <typename T>
+__device__ __forceinline__ void chem_features(const T* uu, int np, double Tk, float* x) {
+  double r[NSPEC], rho = 0.0;
+#pragma unroll
+  for (int s = 0; s < NSPEC; ++s) {
+    r[s] = (double)uu[s * np];
+    rho += r[s];
+  }
+  const double ir = 1.0 / rho;
+#pragma unroll
+  for (int s = 0; s < NSPEC; ++s) x[s] = (float)(r[s] * ir);
+  x[5] = (float)log(rho);
+  x[6] = (float)Tk;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(32 * CM_WARPS)
+chem_mlp_kernel(const T* u, const double* Tc, int64_t K, int np, int dim, const DgChemMlp* mlp,
+                const double* dtp, T* src, unsigned char* flags) {
+  __shared__ DgChemMlp m;
+  __shared__ float feat[CM_WARPS][32][17];
+  __shared__ float yv[CM_WARPS][2][10][16];
+  dgmlp::copy_to_smem(m, mlp);
+  __syncthreads();
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nv = NSPEC + dim + 1;
+  const int64_t total = K * np;
+  const float dt = dtp ? (float)*dtp : 0.f;
+  for (int64_t base = ((int64_t)blockIdx.x * CM_WARPS + w) * 32; base < total;
+       base += (int64_t)gridDim.x * CM_WARPS * 32) {
+    const int64_t i = base + lane;
+    const bool mine = i < total;
+    const int64_t k = mine ? i / np : 0;
+    const int node = mine ? (int)(i % np) : 0;
+    float x[7];
+    bool ok = true;
+    if (mine) {
+      chem_features<T>(u + k * nv * np + node, np, Tc[i], x);
+#pragma unroll
+      for (int q = 0; q < 7; ++q) ok = ok && x[q] >= m.lo[q] && x[q] <= m.hi[q];
+    } else {
+#pragma unroll
+      for (int q = 0; q < 7; ++q) x[q] = m.mean[q];
     }
+#pragma unroll
+    for (int q = 0; q < 7; ++q) feat[w][lane][q] = (x[q] - m.mean[q]) * m.inv_std[q];
+#pragma unroll
+    for (int q = 7; q < 17; ++q) feat[w][lane][q] = 0.f;
+    __syncwarp();
+    dgmlp::mlp16<10>(m.w, feat[w], yv[w][0]);
+    dgmlp::mlp16<10>(m.w, feat[w] + 16, yv[w][1]);
+    __syncwarp();
+    if (mine) {
+      float om[NSPEC], jp[NSPEC], msum = 0.f, asum = 0.f;
+#pragma unroll
+      for (int s = 0; s < NSPEC; ++s) {
+        om[s] = m.w_ref * sinhf(m.muY[s] + m.sdY[s] * yv[w][lane >> 4][s][lane & 15]);
+        jp[s] = fmaxf(0.f, m.j_ref * sinhf(m.muY[5 + s] + m.sdY[5 + s] * yv[w][lane >> 4][5 + s][lane & 15]));
+        msum += om[s];
+        asum += fabsf(om[s]);
+      }
+      ok = ok && isfinite(asum) && fabsf(msum) <= m.tol_mass * asum;
+      const float f = asum > 0.f ? msum / asum : 0.f;
+      T* so = src + k * NSPEC * np + node;
+#pragma unroll
+      for (int s = 0; s < NSPEC; ++s) so[s * np] = (T)((om[s] - fabsf(om[s]) * f) / (1.f + dt * jp[s]));
+    }
+    const bool tile_ok = __all_sync(0xffffffffu, ok);
+    if (lane == 0) flags[base >> 5] = tile_ok ? 0 : 1;
+    __syncwarp();
+  }
+}
+
+// one thread per tile still accepted: compare the learned source at the tile's sampled
+// node with the plain FP64 source there
+template <typename T>
+__global__ void chem_check_kernel(const T* u, const double* Tc, int64_t K, int np, int dim,
+                                  const double* sp_raw, const double* reac, int nr, const DgChemMlp* mlp,
+                                  const double* dtp, const T* src, unsigned char* flags, uint64_t call) {
+  const int nv = NSPEC + dim + 1;
+  const int64_t total = K * np, ntiles = (total + 31) / 32;
+  const double dt = dtp ? *dtp : 0.0;
+  const double tol = mlp->tol_check, floor_ = mlp->floor;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < ntiles;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    if (flags[t]) continue;
+    const int64_t in_tile = total - t * 32 < 32 ? total - t * 32 : 32;
+    const int64_t i = t * 32 + (int64_t)(splitmix64(call * 0x100000001B3ull + (uint64_t)t) % (uint64_t)in_tile);
+    const int64_t k = i / np;
+    const int node = (int)(i % np);
+    double om[NSPEC], jpi[NSPEC], Sp[NSPEC], scale = 0.0;
+    chem_node<T>(u + k * nv * np + node, np, Tc[i], sp_raw, reac, nr, om, jpi);
+#pragma unroll
+    for (int s = 0; s < NSPEC; ++s) {
+      Sp[s] = om[s] / (1.0 + dt * jpi[s]);
+      scale += fabs(Sp[s]);
+    }
+    bool ok = true;
+#pragma unroll
+    for (int s = 0; s < NSPEC; ++s) {
+      const double Sm = (double)src[(k * NSPEC + s) * np + node];
+      ok = ok && fabs(Sm - Sp[s]) <= tol * scale + floor_;
+    }
+    if (!ok) flags[t] = 2;
+  }
+}
+
+// one warp per tile: recompute rejected tiles with the plain source; count nodes
+template <typename T>
+__global__ void __launch_bounds__(128)
+chem_fallback_kernel(const T* u, const double* Tc, int64_t K, int np, int dim, const double* sp_raw,
+                     const double* reac, int nr, const double* dtp, T* src, const unsigned char* flags,
+                     unsigned long long* stats) {
+  const int nv = NSPEC + dim + 1;
+  const int lane = threadIdx.x & 31;
+  const int64_t total = K * np, ntiles = (total + 31) / 32;
+  const double dt = dtp ? *dtp : 0.0;
+  unsigned long long n_ok = 0, n_fb = 0;
+  for (int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; t < ntiles;
+       t += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    const int64_t i = t * 32 + lane;
+    if (i >= total) continue;
+    if (!flags[t]) {
+      ++n_ok;
+      continue;
+    }
+    ++n_fb;
+    const int64_t k = i / np;
+    const int node = (int)(i % np);
+    double om[NSPEC], jpi[NSPEC];
+    chem_node<T>(u + k * nv * np + node, np, Tc[i], sp_raw, reac, nr, om, jpi);
+    T* so = src + k * NSPEC * np + node;
+#pragma unroll
+    for (int s = 0; s < NSPEC; ++s) so[s * np] = (T)(om[s] / (1.0 + dt * jpi[s]));
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    n_ok += __shfl_xor_sync(0xffffffffu, n_ok, o);
+    n_fb += __shfl_xor_sync(0xffffffffu, n_fb, o);
+  }
+  if (lane == 0 && (n_ok | n_fb)) {
+    atomicAdd(&stats[0], n_ok);
+    atomicAdd(&stats[1], n_fb);
+  }
+}
+
+// training data: raw features and the plain (omega, jpi) at counter-sampled nodes
+template <typename T>
+__global__ void chem_sample_kernel(const T* u, const double* Tc, int64_t K, int np, int dim,
+                                   const double* sp_raw, const double* reac, int nr, int64_t n, uint64_t seed,
+                                   float* X, double* Y) {
+  const int nv = NSPEC + dim + 1;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = (int64_t)(splitmix64(seed + (uint64_t)j) % (uint64_t)(K * np));
+    const int64_t k = i / np;
+    const int node = (int)(i % np);
+    const T* uu = u + k * nv * np + node;
+    chem_features<T>(uu, np, Tc[i], X + j * 7);
+    chem_node<T>(uu, np, Tc[i], sp_raw, reac, nr, Y + j * 10, Y + j * 10 + 5);
   }
 }
 
@@ -142,7 +340,29 @@ cudaError_t dg_chem_init(DgThermo* th, const double* species_host, const double*
   return e;
 }
 
+template <typename T>
+static cudaError_t chem_learned(DgThermo* th, const T* u, const double* dt_dev, cudaStream_t s) {
+  const int64_t total = th->K * th->np, ntiles = (total + 31) / 32;
+  const DgChemMlp* m = (const DgChemMlp*)th->chem_mlp;
+  int64_t g1 = (ntiles + CM_WARPS - 1) / CM_WARPS;
+  if (g1 > 152 * 16) g1 = 152 * 16;
+  chem_mlp_kernel<T><<<(unsigned)g1, 32 * CM_WARPS, 0, s>>>(u, th->T, th->K, th->np, th->dim, m, dt_dev,
+                                                             (T*)th->src, th->chem_flags);
+  chem_check_kernel<T><<<grid_of(ntiles), 128, 0, s>>>(u, th->T, th->K, th->np, th->dim, th->species_raw,
+                                                       th->reac, th->nr, m, dt_dev, (const T*)th->src,
+                                                       th->chem_flags, th->chem_calls++);
+  int64_t g3 = (ntiles + 3) / 4;
+  if (g3 > 152 * 64) g3 = 152 * 64;
+  chem_fallback_kernel<T><<<(unsigned)g3, 128, 0, s>>>(u, th->T, th->K, th->np, th->dim, th->species_raw,
+                                                        th->reac, th->nr, dt_dev, (T*)th->src, th->chem_flags,
+                                                        th->chem_stats);
+  return cudaGetLastError();
+}
+
 cudaError_t dg_chem_source(DgThermo* th, const void* u, int f32, const double* dt_dev, cudaStream_t s) {
+  if (th->chem_mlp)
+    return f32 ? chem_learned<float>(th, (const float*)u, dt_dev, s)
+               : chem_learned<double>(th, (const double*)u, dt_dev, s);
   if (f32)
     chem_kernel<float><<<grid_of(th->K * th->np), 128, 0, s>>>(
         (const float*)u, th->T, th->K, th->np, th->dim, th->species_raw, th->reac, th->nr, dt_dev,
@@ -151,5 +371,51 @@ cudaError_t dg_chem_source(DgThermo* th, const void* u, int f32, const double* d
     chem_kernel<double><<<grid_of(th->K * th->np), 128, 0, s>>>(
         (const double*)u, th->T, th->K, th->np, th->dim, th->species_raw, th->reac, th->nr, dt_dev,
         (double*)th->src);
+  return cudaGetLastError();
+}
+
+cudaError_t dg_chem_mlp_set(DgThermo* th, const float* params_host, const double* st) {
+  if (!params_host) {
+    if (th->chem_mlp) cudaFree(th->chem_mlp);
+    th->chem_mlp = NULL;
+    return cudaSuccess;
+  }
+  DgChemMlp* h = (DgChemMlp*)calloc(1, sizeof(DgChemMlp));
+  if (!h) return cudaErrorMemoryAllocation;
+  dg_mlp_pack<10>(params_host, &h->w);
+  for (int q = 0; q < 7; ++q) {
+    h->mean[q] = (float)st[DG_SRC_X_MEAN + q];
+    h->inv_std[q] = (float)(1.0 / st[DG_SRC_X_STD + q]);
+    h->lo[q] = (float)st[DG_SRC_BOX_LO + q];
+    h->hi[q] = (float)st[DG_SRC_BOX_HI + q];
+  }
+  for (int q = 0; q < 10; ++q) {
+    h->muY[q] = (float)st[DG_SRC_Y_MEAN + q];
+    h->sdY[q] = (float)st[DG_SRC_Y_STD + q];
+  }
+  h->w_ref = (float)st[DG_SRC_OMEGA_REF];
+  h->j_ref = (float)st[DG_SRC_JPI_REF];
+  h->tol_mass = (float)st[DG_SRC_TOL_MASS];
+  h->tol_check = st[DG_SRC_TOL_CHECK];
+  h->floor = st[DG_SRC_FLOOR];
+  const int64_t ntiles = (th->K * th->np + 31) / 32;
+  cudaError_t e = cudaSuccess;
+  if (!th->chem_mlp) e = cudaMalloc(&th->chem_mlp, sizeof(DgChemMlp));
+  if (e == cudaSuccess && !th->chem_stats) e = cudaMalloc((void**)&th->chem_stats, 2 * sizeof(unsigned long long));
+  if (e == cudaSuccess && !th->chem_flags) e = cudaMalloc((void**)&th->chem_flags, (size_t)ntiles);
+  if (e == cudaSuccess) e = cudaMemset(th->chem_stats, 0, 2 * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMemcpy(th->chem_mlp, h, sizeof(DgChemMlp), cudaMemcpyHostToDevice);
+  free(h);
+  return e;
+}
+
+cudaError_t dg_chem_sample_dev(DgThermo* th, const void* u, int f32, int64_t n, uint64_t seed, float* X,
+                           double* targets, cudaStream_t s) {
+  if (f32)
+    chem_sample_kernel<float><<<grid_of(n), 128, 0, s>>>((const float*)u, th->T, th->K, th->np, th->dim,
+                                                         th->species_raw, th->reac, th->nr, n, seed, X, targets);
+  else
+    chem_sample_kernel<double><<<grid_of(n), 128, 0, s>>>((const double*)u, th->T, th->K, th->np, th->dim,
+                                                          th->species_raw, th->reac, th->nr, n, seed, X, targets);
   return cudaGetLastError();
 }

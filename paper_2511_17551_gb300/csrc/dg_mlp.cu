@@ -1,131 +1,39 @@
-// Learned temperature surrogate: training kernels (FP32) and BF16 tensor-core
-// inference fused with the per-node FP64 Newton polish and the Newton fallback.
+// Learned surrogates: training kernels (FP32, any number of outputs up to 16) and the
+// temperature surrogate's BF16 tensor-core inference fused with the per-node FP64
+// Newton polish and the Newton fallback.
 //
-// Network: x in R^7 -> 64 -> 64 -> 1 with the tanh form of GELU after the two hidden
-// layers; x = standardised (Y_1..Y_5, ln rho, e), output = standardised T.
-// Parameter vector (FP32 master copy): W1[64][7], b1[64], W2[64][64], b2[64], w3[64], b3.
-//
-// Inference (dg_thermo_update in surrogate mode): one warp evaluates 16 nodes with
-// mma.sync m16n8k16 (BF16 operands, FP32 accumulation): layer 1 is 8 MMAs against
-// W1 zero-padded to K = 16, layer 2 is 32 MMAs; the FP32 accumulator fragments of a
-// layer are exactly the A fragments of the next (two n-tiles of 8 = one k-block of 16),
-// so activations never leave registers.  Layer 3 is a 64-term dot product reduced
-// across the 4 lanes sharing a row.  Then, per node in FP64: one Newton step from the
-// prediction, accept when the next correction would be <= 1e-6 T, otherwise run the
-// plain Newton iteration (fallback, counted).
+// Temperature surrogate: x in R^7 -> 64 -> 64 -> 1, x = standardised (Y_1..Y_5, ln rho,
+// e), output = standardised T.  Inference (dg_thermo_update in surrogate mode): one warp
+// evaluates 32 nodes as two 16-row tensor-core tiles (dg_mlp.cuh), then per node in
+// FP64: one Newton step from the prediction, accept when the next correction would be
+// <= 1e-6 T, otherwise run the plain Newton iteration (fallback, counted).
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include "../../include/dg.h"
 #include "dg_internal.h"
+#include "dg_mlp.cuh"
 #include "dg_thermo.h"
 
-#define NI 7
-#define NH 64
-#define OFF_W1 0
-#define OFF_B1 (OFF_W1 + NH * NI)
-#define OFF_W2 (OFF_B1 + NH)
-#define OFF_B2 (OFF_W2 + NH * NH)
-#define OFF_W3 (OFF_B2 + NH)
-#define OFF_B3 (OFF_W3 + NH)
-#define NPARAM (OFF_B3 + 1)
+#define NI DG_MLP_NI
+#define NH DG_MLP_NH
+#define NO_MAX DG_MLP_NO_MAX
 #define DG_RU 8.314462618
 #define NSPEC 5
 
+// temperature surrogate: weights and input / output standardisation
 struct __align__(16) DgMlpDev {
-  __nv_bfloat16 W1[NH * 16];  // [j][k], k >= 7 zero
-  __nv_bfloat16 W2[NH * NH];  // [j][i]
-  float b1[NH], b2[NH], w3[NH], b3;
+  DgMlpW<1> w;
   float mean[NI], inv_std[NI];
   float muT, sigT;
 };
 
 namespace {
-
-__device__ __forceinline__ float gelu_f(float x) {
-  const float k = 0.7978845608028654f;  // sqrt(2/pi)
-  return 0.5f * x * (1.0f + tanhf(k * (x + 0.044715f * x * x * x)));
-}
-// inference GELU: the hardware tanh approximation (tanh.approx.f32, relative error about
-// 2^-11), below the BF16 rounding of the layer inputs
-__device__ __forceinline__ float gelu_fast(float x) {
-  const float k = 0.7978845608028654f;
-  float z = k * (x + 0.044715f * x * x * x), t;
-  asm("tanh.approx.f32 %0, %1;" : "=f"(t) : "f"(z));
-  return 0.5f * x * (1.0f + t);
-}
-__device__ __forceinline__ float gelu_d_f(float x) {
-  const float k = 0.7978845608028654f;
-  float t = tanhf(k * (x + 0.044715f * x * x * x));
-  return 0.5f * (1.0f + t) + 0.5f * x * (1.0f - t * t) * k * (1.0f + 3.0f * 0.044715f * x * x);
-}
-
-__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
-  __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
-  return *reinterpret_cast<uint32_t*>(&v);
-}
-
-__device__ __forceinline__ void mma_bf16(float* d, const uint32_t* a, uint32_t b0, uint32_t b1) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
-      "{%8,%9}, {%0,%1,%2,%3};\n"
-      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-
-// 16 rows of standardised features in smem feat[16][16] (float) -> outputs y[16] (rows)
-// for the calling warp.  Every lane of the warp must call it.
-__device__ __forceinline__ void mlp16(const DgMlpDev& m, const float (*feat)[17], float* yrow) {
-  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-  uint32_t A[4];
-  A[0] = pack_bf16(feat[g][2 * t], feat[g][2 * t + 1]);
-  A[1] = pack_bf16(feat[g + 8][2 * t], feat[g + 8][2 * t + 1]);
-  A[2] = pack_bf16(feat[g][2 * t + 8], feat[g][2 * t + 9]);
-  A[3] = pack_bf16(feat[g + 8][2 * t + 8], feat[g + 8][2 * t + 9]);
-  float h[8][4];
-#pragma unroll
-  for (int nt = 0; nt < 8; ++nt) {
-    const int col = 8 * nt + 2 * t;
-    h[nt][0] = h[nt][2] = m.b1[col];
-    h[nt][1] = h[nt][3] = m.b1[col + 1];
-    const uint32_t* w = reinterpret_cast<const uint32_t*>(m.W1 + (8 * nt + g) * 16);
-    mma_bf16(h[nt], A, w[t], w[t + 4]);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) h[nt][q] = gelu_fast(h[nt][q]);
-  }
-  uint32_t A2[4][4];
-#pragma unroll
-  for (int kb = 0; kb < 4; ++kb) {
-    A2[kb][0] = pack_bf16(h[2 * kb][0], h[2 * kb][1]);
-    A2[kb][1] = pack_bf16(h[2 * kb][2], h[2 * kb][3]);
-    A2[kb][2] = pack_bf16(h[2 * kb + 1][0], h[2 * kb + 1][1]);
-    A2[kb][3] = pack_bf16(h[2 * kb + 1][2], h[2 * kb + 1][3]);
-  }
-  float yg = 0.f, yg8 = 0.f;
-#pragma unroll
-  for (int nt = 0; nt < 8; ++nt) {
-    const int col = 8 * nt + 2 * t;
-    float o[4] = {m.b2[col], m.b2[col + 1], m.b2[col], m.b2[col + 1]};
-#pragma unroll
-    for (int kb = 0; kb < 4; ++kb) {
-      const uint32_t* w = reinterpret_cast<const uint32_t*>(m.W2 + (8 * nt + g) * NH + 16 * kb);
-      mma_bf16(o, A2[kb], w[t], w[t + 4]);
-    }
-    yg += m.w3[col] * gelu_fast(o[0]) + m.w3[col + 1] * gelu_fast(o[1]);
-    yg8 += m.w3[col] * gelu_fast(o[2]) + m.w3[col + 1] * gelu_fast(o[3]);
-  }
-  yg += __shfl_xor_sync(0xffffffffu, yg, 1);
-  yg += __shfl_xor_sync(0xffffffffu, yg, 2);
-  yg8 += __shfl_xor_sync(0xffffffffu, yg8, 1);
-  yg8 += __shfl_xor_sync(0xffffffffu, yg8, 2);
-  if (t == 0) {
-    yrow[g] = yg + m.b3;
-    yrow[g + 8] = yg8 + m.b3;
-  }
-}
+using namespace dgmlp;
 
 struct PolyD {
   double b[6], Rmix;
@@ -161,12 +69,8 @@ thermo_mlp_kernel(const T* u, int64_t K, int np, int dim, const double* sp, doub
                   unsigned long long* status, const DgMlpDev* mlp, unsigned long long* stats) {
   __shared__ DgMlpDev m;
   __shared__ float feat[MLP_WARPS][32][17];
-  __shared__ float yv[MLP_WARPS][32];
-  {
-    const int4* src = reinterpret_cast<const int4*>(mlp);
-    int4* dst = reinterpret_cast<int4*>(&m);
-    for (int i = threadIdx.x; i < (int)(sizeof(DgMlpDev) / 16); i += blockDim.x) dst[i] = src[i];
-  }
+  __shared__ float yv[MLP_WARPS][2][1][16];
+  copy_to_smem(m, mlp);
   __syncthreads();
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nv = NSPEC + dim + 1;
@@ -212,16 +116,16 @@ thermo_mlp_kernel(const T* u, int64_t K, int np, int dim, const double* sp, doub
 #pragma unroll
       for (int q = 0; q < NI; ++q) feat[w][lane][q] = (f[q] - m.mean[q]) * m.inv_std[q];
 #pragma unroll
-      for (int q = NI; q < 16; ++q) feat[w][lane][q] = 0.f;
+      for (int q = NI; q < 17; ++q) feat[w][lane][q] = 0.f;
     }
     __syncwarp();
-    mlp16(m, feat[w], yv[w]);
-    mlp16(m, feat[w] + 16, yv[w] + 16);
+    mlp16<1>(m.w, feat[w], yv[w][0]);
+    mlp16<1>(m.w, feat[w] + 16, yv[w][1]);
     __syncwarp();
     if (mine) {
       PolyD P;
       poly_d(sp, Y, P);
-      double T0 = clampT((double)(m.muT + m.sigT * yv[w][lane]));
+      double T0 = clampT((double)(m.muT + m.sigT * yv[w][lane >> 4][0][lane & 15]));
       // FP64 residuals; cv only scales the correction, FP32 is enough for it
       const float cv0 = (float)P.b[1] + (float)T0 * (2.f * (float)P.b[2] + (float)T0 *
                         (3.f * (float)P.b[3] + (float)T0 * (4.f * (float)P.b[4] + (float)T0 * 5.f * (float)P.b[5])));
@@ -263,17 +167,14 @@ thermo_mlp_kernel(const T* u, int64_t K, int np, int dim, const double* sp, doub
   }
 }
 
-// plain tensor-core forward for standardised inputs X[n][7] -> y[n] (checks / data)
+// plain tensor-core forward for standardised inputs X[n][7] -> y[n][NO] (checks)
+template <int NO>
 __global__ void __launch_bounds__(32 * MLP_WARPS)
-mlp_forward_tc_kernel(const DgMlpDev* mlp, const float* X, float* y, int64_t n) {
-  __shared__ DgMlpDev m;
+mlp_forward_tc_kernel(const DgMlpW<NO>* mlp, const float* X, float* y, int64_t n) {
+  __shared__ DgMlpW<NO> m;
   __shared__ float feat[MLP_WARPS][16][17];
-  __shared__ float yv[MLP_WARPS][16];
-  {
-    const int4* src = reinterpret_cast<const int4*>(mlp);
-    int4* dst = reinterpret_cast<int4*>(&m);
-    for (int i = threadIdx.x; i < (int)(sizeof(DgMlpDev) / 16); i += blockDim.x) dst[i] = src[i];
-  }
+  __shared__ float yv[MLP_WARPS][NO][16];
+  copy_to_smem(m, mlp);
   __syncthreads();
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int64_t base = ((int64_t)blockIdx.x * MLP_WARPS + w) * 16; base < n;
@@ -281,52 +182,62 @@ mlp_forward_tc_kernel(const DgMlpDev* mlp, const float* X, float* y, int64_t n) 
     if (lane < 16) {
       const int64_t i = base + lane;
 #pragma unroll
-      for (int q = 0; q < 16; ++q) feat[w][lane][q] = (i < n && q < NI) ? X[i * NI + q] : 0.f;
+      for (int q = 0; q < 17; ++q) feat[w][lane][q] = (i < n && q < NI) ? X[i * NI + q] : 0.f;
     }
     __syncwarp();
-    mlp16(m, feat[w], yv[w]);
+    mlp16<NO>(m, feat[w], yv[w]);
     __syncwarp();
-    if (lane < 16 && base + lane < n) y[base + lane] = yv[w][lane];
+    if (lane < 16 && base + lane < n)
+      for (int o = 0; o < NO; ++o) y[(base + lane) * NO + o] = yv[w][o][lane];
     __syncwarp();
   }
 }
 
 // FP32 SIMT forward of one sample per thread (reference path of the device code)
-__global__ void mlp_forward_f32_kernel(const float* P, const float* X, float* y, int64_t n) {
+__global__ void mlp_forward_f32_kernel(const float* P, int no, const float* X, float* y, int64_t n) {
   for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n;
        s += (int64_t)gridDim.x * blockDim.x) {
-    float h1[NH];
+    float h1[NH], h2[NH];
     for (int j = 0; j < NH; ++j) {
-      float a = P[OFF_B1 + j];
-      for (int k = 0; k < NI; ++k) a += P[OFF_W1 + j * NI + k] * X[s * NI + k];
+      float a = P[NH * NI + j];
+      for (int k = 0; k < NI; ++k) a += P[j * NI + k] * X[s * NI + k];
       h1[j] = gelu_f(a);
     }
-    float out = P[OFF_B3];
     for (int j = 0; j < NH; ++j) {
-      float a = P[OFF_B2 + j];
-      for (int i = 0; i < NH; ++i) a += P[OFF_W2 + j * NH + i] * h1[i];
-      out += P[OFF_W3 + j] * gelu_f(a);
+      float a = P[NH * NI + NH + NH * NH + j];
+      for (int i = 0; i < NH; ++i) a += P[NH * NI + NH + j * NH + i] * h1[i];
+      h2[j] = gelu_f(a);
     }
-    y[s] = out;
+    for (int o = 0; o < no; ++o) {
+      float out = P[dg_mlp_off_b3(no) + o];
+      for (int j = 0; j < NH; ++j) out += P[dg_mlp_off_w3() + o * NH + j] * h2[j];
+      y[s * no + o] = out;
+    }
   }
 }
 
 // ------------------------------------------------------------------ training (FP32)
 #define TS 32  // samples per tile
+#define OFF_W1 0
+#define OFF_B1 (NH * NI)
+#define OFF_W2 (OFF_B1 + NH)
+#define OFF_B2 (OFF_W2 + NH * NH)
 struct TrainSmem {
-  float W1[NH * NI], b1[NH], W2[NH * NH], W2T[NH * NH], b2[NH], w3[NH], b3;
+  float W1[NH * NI], b1[NH], W2[NH * NH], W2T[NH * NH], b2[NH], W3[NO_MAX * NH], b3[NO_MAX];
   float X[TS][NI], a1[TS][NH], h1[TS][NH], a2[TS][NH], h2[TS][NH];
-  float dy[TS], r2[TS];
-  float g[NPARAM];  // gW2 stored transposed [i][j]
+  float dy[TS][NO_MAX], r2[TS][NO_MAX];
+  float g[dg_mlp_np(NO_MAX)];  // gW2 stored transposed [i][j]
   float loss;
 };
 
-// per-CTA partial gradients of loss = (1/B) sum (y - t)^2 over the CTA's tiles
-__global__ void __launch_bounds__(NH) mlp_grad_kernel(const float* P, const float* X, const float* t,
+// per-CTA partial gradients of loss = (1/(B no)) sum_s sum_o (y_so - t_so)^2 over the
+// CTA's tiles
+__global__ void __launch_bounds__(NH) mlp_grad_kernel(const float* P, int no, const float* X, const float* t,
                                                       int B, float* partial) {
   extern __shared__ __align__(16) unsigned char raw[];
   TrainSmem& S = *reinterpret_cast<TrainSmem*>(raw);
   const int j = threadIdx.x;
+  const int OW3 = dg_mlp_off_w3(), OB3 = dg_mlp_off_b3(no), NPAR = dg_mlp_np(no);
   for (int q = j; q < NH * NI; q += NH) S.W1[q] = P[OFF_W1 + q];
   for (int q = j; q < NH * NH; q += NH) {
     S.W2[q] = P[OFF_W2 + q];
@@ -334,14 +245,12 @@ __global__ void __launch_bounds__(NH) mlp_grad_kernel(const float* P, const floa
   }
   S.b1[j] = P[OFF_B1 + j];
   S.b2[j] = P[OFF_B2 + j];
-  S.w3[j] = P[OFF_W3 + j];
-  if (j == 0) {
-    S.b3 = P[OFF_B3];
-    S.loss = 0.f;
-  }
-  for (int q = j; q < NPARAM; q += NH) S.g[q] = 0.f;
+  for (int o = 0; o < no; ++o) S.W3[o * NH + j] = P[OW3 + o * NH + j];
+  if (j < no) S.b3[j] = P[OB3 + j];
+  if (j == 0) S.loss = 0.f;
+  for (int q = j; q < NPAR; q += NH) S.g[q] = 0.f;
   __syncthreads();
-  const float invB = 1.0f / B;
+  const float inv = 1.0f / ((float)B * (float)no);
   for (int s0 = blockIdx.x * TS; s0 < B; s0 += gridDim.x * TS) {
     const int ns = min(TS, B - s0);
     for (int q = j; q < TS * NI; q += NH) S.X[q / NI][q % NI] = q / NI < ns ? X[(int64_t)s0 * NI + q] : 0.f;
@@ -361,29 +270,36 @@ __global__ void __launch_bounds__(NH) mlp_grad_kernel(const float* P, const floa
       S.h2[s][j] = gelu_f(a);
     }
     __syncthreads();
-    if (j < ns) {
-      float y = S.b3;
-      for (int q = 0; q < NH; ++q) y += S.w3[q] * S.h2[j][q];
-      const float r = y - t[s0 + j];
-      S.dy[j] = 2.0f * r * invB;
-      S.r2[j] = r * r * invB;
+    for (int q = j; q < ns * no; q += NH) {
+      const int s = q / no, o = q % no;
+      float y = S.b3[o];
+      for (int i = 0; i < NH; ++i) y += S.W3[o * NH + i] * S.h2[s][i];
+      const float r = y - t[(int64_t)(s0 + s) * no + o];
+      S.dy[s][o] = 2.0f * r * inv;
+      S.r2[s][o] = r * r * inv;
     }
     __syncthreads();
-    if (j == 0)
-      for (int s = 0; s < ns; ++s) S.loss += S.r2[s];  // fixed order: deterministic
-    float gw3 = 0.f, gb2 = 0.f;
+    if (j == 0)  // fixed order: deterministic
+      for (int s = 0; s < ns; ++s)
+        for (int o = 0; o < no; ++o) S.loss += S.r2[s][o];
+    float gb2 = 0.f;
+    for (int o = 0; o < no; ++o) {
+      float gw3 = 0.f;
+      for (int s = 0; s < ns; ++s) gw3 += S.dy[s][o] * S.h2[s][j];
+      S.g[OW3 + o * NH + j] += gw3;
+    }
     for (int s = 0; s < ns; ++s) {
-      gw3 += S.dy[s] * S.h2[s][j];
-      const float d2 = S.dy[s] * S.w3[j] * gelu_d_f(S.a2[s][j]);
+      float back = 0.f;
+      for (int o = 0; o < no; ++o) back += S.dy[s][o] * S.W3[o * NH + j];
+      const float d2 = back * gelu_d_f(S.a2[s][j]);
       S.a2[s][j] = d2;  // a2 now holds delta2
       gb2 += d2;
     }
-    S.g[OFF_W3 + j] += gw3;
     S.g[OFF_B2 + j] += gb2;
-    if (j == 0) {
+    if (j < no) {
       float gb3 = 0.f;
-      for (int s = 0; s < ns; ++s) gb3 += S.dy[s];
-      S.g[OFF_B3] += gb3;
+      for (int s = 0; s < ns; ++s) gb3 += S.dy[s][j];
+      S.g[OB3 + j] += gb3;
     }
     __syncthreads();
     // thread j: row j of dW2 (stored transposed) and delta1 of hidden unit j
@@ -406,29 +322,27 @@ __global__ void __launch_bounds__(NH) mlp_grad_kernel(const float* P, const floa
     for (int k = 0; k < NI; ++k) S.g[OFF_W1 + j * NI + k] += gw1[k];
     __syncthreads();
   }
-  float* out = partial + (int64_t)blockIdx.x * (NPARAM + 1);
-  for (int q = j; q < NPARAM; q += NH) {
-    float v = S.g[q];
+  float* out = partial + (int64_t)blockIdx.x * (NPAR + 1);
+  for (int q = j; q < NPAR; q += NH) {
     if (q >= OFF_W2 && q < OFF_W2 + NH * NH) {  // back to row-major [j][i]
       const int i = (q - OFF_W2) / NH, jj = (q - OFF_W2) % NH;
-      v = S.g[q];
-      out[OFF_W2 + jj * NH + i] = v;
+      out[OFF_W2 + jj * NH + i] = S.g[q];
     } else {
-      out[q] = v;
+      out[q] = S.g[q];
     }
   }
-  if (j == 0) out[NPARAM] = S.loss;
+  if (j == 0) out[NPAR] = S.loss;
 }
 
 // fixed-order sum of the partial gradients, then (optionally) one Adam step
-__global__ void mlp_reduce_adam_kernel(const float* partial, int nb, float* grad, float* P, float* mo,
+__global__ void mlp_reduce_adam_kernel(const float* partial, int nb, int npar, float* grad, float* P, float* mo,
                                        float* vo, int step, float lr, float b1, float b2, float eps,
                                        double* loss) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
-  if (q > NPARAM) return;
+  if (q > npar) return;
   float s = 0.f;
-  for (int b = 0; b < nb; ++b) s += partial[(int64_t)b * (NPARAM + 1) + q];
-  if (q == NPARAM) {
+  for (int b = 0; b < nb; ++b) s += partial[(int64_t)b * (npar + 1) + q];
+  if (q == npar) {
     if (loss) *loss = (double)s;
     return;
   }
@@ -482,14 +396,7 @@ unsigned grid_of(int64_t n, int bs) {
 
 void pack_host(const float* params, const double* stats, DgMlpDev* h) {
   memset(h, 0, sizeof(*h));
-  for (int j = 0; j < NH; ++j) {
-    for (int k = 0; k < NI; ++k) h->W1[j * 16 + k] = __float2bfloat16(params[OFF_W1 + j * NI + k]);
-    for (int i = 0; i < NH; ++i) h->W2[j * NH + i] = __float2bfloat16(params[OFF_W2 + j * NH + i]);
-    h->b1[j] = params[OFF_B1 + j];
-    h->b2[j] = params[OFF_B2 + j];
-    h->w3[j] = params[OFF_W3 + j];
-  }
-  h->b3 = params[OFF_B3];
+  dg_mlp_pack<1>(params, &h->w);
   for (int q = 0; q < NI; ++q) {
     h->mean[q] = (float)stats[q];
     h->inv_std[q] = (float)(1.0 / stats[NI + q]);
@@ -540,91 +447,97 @@ cudaError_t dg_mlp_sample(DgThermo* th, const void* u, int f32, int64_t n, uint6
   return cudaGetLastError();
 }
 
+template <int NO>
+static dg_status forward_tc(const float* hp, const float* X, float* y, int64_t n, cudaStream_t st) {
+  DgMlpW<NO> h;
+  memset(&h, 0, sizeof(h));
+  dg_mlp_pack<NO>(hp, &h);
+  DgMlpW<NO>* d = NULL;
+  if (cudaMalloc((void**)&d, sizeof(h)) != cudaSuccess) return DG_ENOMEM;
+  cudaError_t e = cudaMemcpy(d, &h, sizeof(h), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    mlp_forward_tc_kernel<NO><<<grid_of((n + 15) / 16, MLP_WARPS), 32 * MLP_WARPS, 0, st>>>(d, X, y, n);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(d);
+  return e == cudaSuccess ? DG_OK : DG_ECUDA;
+}
+
 // ---------------------------------------------------------------- C ABI (training)
 extern "C" {
 
-int dg_mlp_nparams(void) { return NPARAM; }
+int dg_mlp_nparams(int n_out) { return n_out >= 1 && n_out <= NO_MAX ? dg_mlp_np(n_out) : -1; }
 
-size_t dg_mlp_workspace_bytes(int batch) {
+size_t dg_mlp_workspace_bytes(int batch, int n_out) {
+  if (batch < 1 || n_out < 1 || n_out > NO_MAX) return 0;
   int nb = (batch + TS - 1) / TS;
   if (nb > 152) nb = 152;
-  return sizeof(float) * (size_t)nb * (NPARAM + 1);
+  return sizeof(float) * (size_t)nb * (dg_mlp_np(n_out) + 1);
 }
 
-static dg_status grad_common(const float* P, const float* X, const float* t, int B, float* ws,
+static dg_status grad_common(const float* P, int no, const float* X, const float* t, int B, float* ws,
                              size_t ws_bytes, cudaStream_t st, int* nb_out) {
-  if (!P || !X || !t || !ws || B < 1) return DG_EINVAL;
-  if (ws_bytes < dg_mlp_workspace_bytes(B)) return DG_EINVAL;
+  if (!P || !X || !t || !ws || B < 1 || no < 1 || no > NO_MAX) return DG_EINVAL;
+  if (ws_bytes < dg_mlp_workspace_bytes(B, no)) return DG_EINVAL;
   int nb = (B + TS - 1) / TS;
   if (nb > 152) nb = 152;
   const size_t smem = sizeof(TrainSmem);
   if (cudaFuncSetAttribute(mlp_grad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
       cudaSuccess)
     return DG_ECUDA;
-  mlp_grad_kernel<<<nb, NH, smem, st>>>(P, X, t, B, ws);
+  mlp_grad_kernel<<<nb, NH, smem, st>>>(P, no, X, t, B, ws);
   if (cudaGetLastError() != cudaSuccess) return DG_ECUDA;
   *nb_out = nb;
   return DG_OK;
 }
 
-dg_status dg_mlp_grad(const float* params, const float* X, const float* t, int batch, float* grad,
+dg_status dg_mlp_grad(const float* params, int n_out, const float* X, const float* t, int batch, float* grad,
                       double* loss, float* workspace, size_t ws_bytes, void* stream) {
   cudaStream_t st = (cudaStream_t)stream;
   int nb = 0;
-  dg_status r = grad_common(params, X, t, batch, workspace, ws_bytes, st, &nb);
+  dg_status r = grad_common(params, n_out, X, t, batch, workspace, ws_bytes, st, &nb);
   if (r != DG_OK) return r;
   if (!grad) return DG_EINVAL;
-  mlp_reduce_adam_kernel<<<(NPARAM + 1 + 255) / 256, 256, 0, st>>>(workspace, nb, grad, NULL, NULL, NULL, 0,
-                                                                   0.f, 0.f, 0.f, 0.f, loss);
+  const int npar = dg_mlp_np(n_out);
+  mlp_reduce_adam_kernel<<<(npar + 1 + 255) / 256, 256, 0, st>>>(workspace, nb, npar, grad, NULL, NULL, NULL, 0,
+                                                                 0.f, 0.f, 0.f, 0.f, loss);
   return cudaGetLastError() == cudaSuccess ? DG_OK : DG_ECUDA;
 }
 
-dg_status dg_mlp_train_step(float* params, float* m, float* v, const float* X, const float* t, int batch,
-                            int step, float lr, double* loss, float* workspace, size_t ws_bytes,
+dg_status dg_mlp_train_step(float* params, int n_out, float* m, float* v, const float* X, const float* t,
+                            int batch, int step, float lr, double* loss, float* workspace, size_t ws_bytes,
                             void* stream) {
   if (!m || !v || step < 1 || !(lr > 0.f)) return DG_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
   int nb = 0;
-  dg_status r = grad_common(params, X, t, batch, workspace, ws_bytes, st, &nb);
+  dg_status r = grad_common(params, n_out, X, t, batch, workspace, ws_bytes, st, &nb);
   if (r != DG_OK) return r;
-  mlp_reduce_adam_kernel<<<(NPARAM + 1 + 255) / 256, 256, 0, st>>>(workspace, nb, NULL, params, m, v, step,
-                                                                   lr, 0.9f, 0.999f, 1e-8f, loss);
+  const int npar = dg_mlp_np(n_out);
+  mlp_reduce_adam_kernel<<<(npar + 1 + 255) / 256, 256, 0, st>>>(workspace, nb, npar, NULL, params, m, v, step,
+                                                                 lr, 0.9f, 0.999f, 1e-8f, loss);
   return cudaGetLastError() == cudaSuccess ? DG_OK : DG_ECUDA;
 }
 
-dg_status dg_mlp_forward(const float* params, const double* stats, const float* X, float* y, int64_t n,
-                         int tensor_cores, void* stream) {
-  if (!params || !X || !y || n < 1) return DG_EINVAL;
+dg_status dg_mlp_forward(const float* params, int n_out, const float* X, float* y, int64_t n, int tensor_cores,
+                         void* stream) {
+  if (!params || !X || !y || n < 1 || n_out < 1 || n_out > NO_MAX) return DG_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
   if (!tensor_cores) {
-    mlp_forward_f32_kernel<<<grid_of(n, 128), 128, 0, st>>>(params, X, y, n);
+    mlp_forward_f32_kernel<<<grid_of(n, 128), 128, 0, st>>>(params, n_out, X, y, n);
     return cudaGetLastError() == cudaSuccess ? DG_OK : DG_ECUDA;
   }
-  // tensor-core path: pack the host copy of the device parameters
-  float* hp = (float*)malloc(sizeof(float) * NPARAM);
+  if (n_out != 1 && n_out != 10) return DG_EINVAL;  // the surrogates' output counts
+  const int npar = dg_mlp_np(n_out);
+  float* hp = (float*)malloc(sizeof(float) * npar);
   if (!hp) return DG_ENOMEM;
-  if (cudaMemcpy(hp, params, sizeof(float) * NPARAM, cudaMemcpyDeviceToHost) != cudaSuccess) {
+  if (cudaMemcpy(hp, params, sizeof(float) * npar, cudaMemcpyDeviceToHost) != cudaSuccess) {
     free(hp);
     return DG_ECUDA;
   }
-  double unit[2 * NI + 2];
-  for (int q = 0; q < NI; ++q) {
-    unit[q] = 0.0;
-    unit[NI + q] = 1.0;
-  }
-  unit[2 * NI] = stats ? stats[2 * NI] : 0.0;
-  unit[2 * NI + 1] = stats ? stats[2 * NI + 1] : 1.0;
-  DgMlpDev h;
-  pack_host(hp, unit, &h);
+  dg_status r = n_out == 1 ? forward_tc<1>(hp, X, y, n, st) : forward_tc<10>(hp, X, y, n, st);
   free(hp);
-  DgMlpDev* d = NULL;
-  if (cudaMalloc((void**)&d, sizeof(h)) != cudaSuccess) return DG_ENOMEM;
-  cudaMemcpy(d, &h, sizeof(h), cudaMemcpyHostToDevice);
-  mlp_forward_tc_kernel<<<grid_of((n + 15) / 16, MLP_WARPS), 32 * MLP_WARPS, 0, st>>>(d, X, y, n);
-  cudaError_t e = cudaGetLastError();
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  cudaFree(d);
-  return e == cudaSuccess ? DG_OK : DG_ECUDA;
+  return r;
 }
 
 }  // extern "C"

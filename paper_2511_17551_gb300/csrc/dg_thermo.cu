@@ -240,6 +240,9 @@ cudaError_t dg_thermo_init(DgThermo* th, int64_t K, int np, int dim, const doubl
 void dg_thermo_free(DgThermo* th) {
   if (th->mlp) cudaFree(th->mlp);
   if (th->mlp_stats) cudaFree(th->mlp_stats);
+  if (th->chem_mlp) cudaFree(th->chem_mlp);
+  if (th->chem_stats) cudaFree(th->chem_stats);
+  if (th->chem_flags) cudaFree(th->chem_flags);
   if (th->species) cudaFree(th->species);
   if (th->coef32) cudaFree(th->coef32);
   if (th->species_raw) cudaFree(th->species_raw);

@@ -17,8 +17,12 @@ struct DgThermo {
   double* reac;        // device [nr][20] reaction rows (ln A in slot 16)
   int nr;              // number of reactions, 0 = frozen
   void* src;           // device [K][ns][np] chemistry source (form precision)
-  void* mlp;           // surrogate weights (device) or null
+  void* mlp;           // temperature surrogate weights (device) or null
   unsigned long long* mlp_stats;  // [accepted, fallback] node counts of the surrogate
+  void* chem_mlp;                 // chemistry-source surrogate (device) or null
+  unsigned long long* chem_stats; // [accepted, fallback] node counts of the source surrogate
+  unsigned char* chem_flags;      // per 32-node tile: 0 accepted, otherwise recomputed plainly
+  unsigned long long chem_calls;  // source evaluations so far (moves each tile's sampled node)
 };
 
 cudaError_t dg_thermo_upload_basis();
@@ -32,6 +36,10 @@ cudaError_t dg_thermo_prim2cons(DgThermo* th, const double* w, void* u, cudaStre
 // chemistry (dg_chem.cu)
 cudaError_t dg_chem_init(DgThermo* th, const double* species_host, const double* reac_host, int nr);
 cudaError_t dg_chem_source(DgThermo* th, const void* u, int f32, const double* dt_dev, cudaStream_t s);
+// learned source (dg_chem.cu): set / clear (params null) and plain-source training samples
+cudaError_t dg_chem_mlp_set(DgThermo* th, const float* params_host, const double* stats_host);
+cudaError_t dg_chem_sample_dev(DgThermo* th, const void* u, int f32, int64_t n, uint64_t seed, float* X,
+                           double* targets, cudaStream_t s);
 // surrogate (dg_mlp.cu)
 cudaError_t dg_mlp_set(DgThermo* th, const float* params_host, const double* stats_host);
 cudaError_t dg_mlp_thermo_update(DgThermo* th, const void* u, int f32, cudaStream_t s);

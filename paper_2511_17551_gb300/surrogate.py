@@ -1,25 +1,25 @@
-"""Training driver for the learned temperature surrogate.
+"""Training drivers for the learned surrogates (temperature solve; chemistry source).
 
 Data come from the plain solver itself: a mixture context is stepped with the plain
-Newton temperature solve and ``dg_thermo_sample`` draws node states (raw features
-Y_1..Y_5, ln rho, e and the converged T) after every ``steps_between`` RK steps.  The
-driver standardises the data, initialises the network (Xavier-uniform from a seed) and
-runs Adam epochs with ``dg_mlp_train_step``; forward, back-propagation, the gradient
-reduction and the update all run in libdg's kernels.  PyTorch only holds the device
-buffers and draws the epoch permutations.
+computations and ``dg_thermo_sample`` / ``dg_chem_sample`` draw node states after every
+``steps_between`` RK steps (raw features and the plain FP64 results).  The drivers
+standardise the data, initialise the network (Xavier-uniform from a seed) and run Adam
+epochs with ``dg_mlp_train_step``; forward, back-propagation, the gradient reduction and
+the update all run in libdg's kernels.  PyTorch only holds the device buffers and draws
+the epoch permutations.
 """
 import math
 
 import numpy as np
 
-from . import (dg_mlp_nparams, dg_mlp_train_step, dg_mlp_workspace_bytes, dg_step_rk,
-               dg_thermo_sample)
+from . import (DG_SRC_NSTATS, dg_chem_sample, dg_mlp_nparams, dg_mlp_train_step,
+               dg_mlp_workspace_bytes, dg_step_rk, dg_thermo_sample)
 
 NI, NH = 7, 64
 
 
 def collect(ctx, n_total, n_snapshots, steps_between, cfl=0.3, seed=1):
-    """Sample n_total states from n_snapshots states of a plain-solver run."""
+    """Temperature surrogate data: n_total states from n_snapshots states of a plain run."""
     import torch
     per = int(math.ceil(n_total / n_snapshots))
     X = torch.empty((per * n_snapshots, NI), dtype=torch.float32, device="cuda")
@@ -32,11 +32,25 @@ def collect(ctx, n_total, n_snapshots, steps_between, cfl=0.3, seed=1):
     return X[:n_total], T[:n_total]
 
 
-def xavier_params(seed=0):
+def collect_source(ctx, n_total, n_snapshots, steps_between, cfl=0.05, dt_fixed=0.0, seed=1):
+    """Source surrogate data: raw features [n][7] (float32) and the plain (omega, jpi)
+    [n][10] (float64) from n_snapshots states of a plain reacting run."""
+    import torch
+    per = int(math.ceil(n_total / n_snapshots))
+    X = torch.empty((per * n_snapshots, NI), dtype=torch.float32, device="cuda")
+    Y = torch.empty((per * n_snapshots, 10), dtype=torch.float64, device="cuda")
+    for s in range(n_snapshots):
+        if s:
+            dg_step_rk(ctx, steps_between, cfl, dt_fixed)
+        dg_chem_sample(ctx, X[s * per:(s + 1) * per], Y[s * per:(s + 1) * per], seed=seed * 1000003 + s)
+    return X[:n_total], Y[:n_total]
+
+
+def xavier_params(seed=0, n_out=1):
     rng = np.random.default_rng(seed)
-    p = np.zeros(dg_mlp_nparams(), dtype=np.float32)
+    p = np.zeros(dg_mlp_nparams(n_out), dtype=np.float32)
     o = 0
-    for fan_in, fan_out in ((NI, NH), (NH, NH), (NH, 1)):
+    for fan_in, fan_out in ((NI, NH), (NH, NH), (NH, n_out)):
         lim = math.sqrt(6.0 / (fan_in + fan_out))
         p[o:o + fan_in * fan_out] = rng.uniform(-lim, lim, fan_in * fan_out)
         o += fan_in * fan_out + fan_out  # weights then zero biases
@@ -44,7 +58,7 @@ def xavier_params(seed=0):
 
 
 def standardise(X, T):
-    """Dataset statistics: mean/std of each feature and of T (float64 [16])."""
+    """Temperature surrogate statistics: mean/std of each feature and of T (float64 [16])."""
     mx = X.double().mean(0)
     sx = X.double().std(0).clamp_min(1e-12)
     mt = T.double().mean()
@@ -55,23 +69,22 @@ def standardise(X, T):
     return Xn, Tn, stats
 
 
-def train(X, T, epochs=20, batch=4096, lr=1e-3, seed=0, val_frac=0.1, log=None):
-    """Adam on mean-squared error of the standardised temperature.
-
-    Returns (params float32 [P] host, stats float64 [16], history of (epoch, train, val)).
-    """
+def fit(Xn, Yn, epochs=20, batch=4096, lr=1e-3, seed=0, val_frac=0.1, log=None):
+    """Adam on the mean-squared error of standardised targets Yn ([n] or [n][n_out]).
+    Returns (params float32 [P] device, history of (epoch, train, val))."""
     import torch
-    Xn, Tn, stats = standardise(X, T)
+    n_out = 1 if Yn.dim() == 1 else Yn.shape[1]
     n = Xn.shape[0]
     g = torch.Generator(device="cpu").manual_seed(seed)
     perm = torch.randperm(n, generator=g).cuda()
     nval = max(1, int(val_frac * n))
-    Xv, Tv = Xn[perm[:nval]], Tn[perm[:nval]]
-    Xt, Tt = Xn[perm[nval:]], Tn[perm[nval:]]
-    params = torch.from_numpy(xavier_params(seed)).cuda()
+    Xv, Yv = Xn[perm[:nval]], Yn[perm[:nval]]
+    Xt, Yt = Xn[perm[nval:]], Yn[perm[nval:]]
+    batch = min(batch, Xt.shape[0])
+    params = torch.from_numpy(xavier_params(seed, n_out)).cuda()
     m = torch.zeros_like(params)
     v = torch.zeros_like(params)
-    ws = torch.empty(dg_mlp_workspace_bytes(batch) // 4 + 1, dtype=torch.float32, device="cuda")
+    ws = torch.empty(dg_mlp_workspace_bytes(batch, n_out) // 4 + 1, dtype=torch.float32, device="cuda")
     loss = torch.zeros(1, dtype=torch.float64, device="cuda")
     hist = []
     step = 0
@@ -80,21 +93,68 @@ def train(X, T, epochs=20, batch=4096, lr=1e-3, seed=0, val_frac=0.1, log=None):
         tot, nb = 0.0, 0
         for b0 in range(0, Xt.shape[0] - batch + 1, batch):
             idx = order[b0:b0 + batch]
-            xb, tb = Xt[idx].contiguous(), Tt[idx].contiguous()
+            xb, tb = Xt[idx].contiguous(), Yt[idx].contiguous()
             step += 1
             dg_mlp_train_step(params, m, v, xb, tb, step, lr, loss, ws)
             tot += loss.item() if (nb % 50 == 0) else 0.0
             nb += 1
-        vloss = validation_loss(params, Xv, Tv)
+        vloss = validation_loss(params, Xv, Yv)
         hist.append((ep, tot, vloss))
         if log:
             log("epoch %d  val mse %.3e" % (ep, vloss))
+    return params, hist
+
+
+def train(X, T, epochs=20, batch=4096, lr=1e-3, seed=0, val_frac=0.1, log=None):
+    """Temperature surrogate.  Returns (params float32 [P] host, stats float64 [16],
+    history of (epoch, train, val))."""
+    Xn, Tn, stats = standardise(X, T)
+    params, hist = fit(Xn, Tn, epochs, batch, lr, seed, val_frac, log)
     return params.cpu().numpy(), stats, hist
 
 
-def validation_loss(params, Xv, Tv):
+def source_stats(X, Y, ref_quantile=0.99, ref_fraction=1e-3, tol_check=0.05, tol_mass=0.05,
+                 floor_fraction=0.1):
+    """Statistics of the source surrogate (float64 [DG_SRC_NSTATS]) and the standardised
+    training arrays.  omega_ref (jpi_ref) = ref_fraction x the ref_quantile of |omega|
+    (of jpi) over the samples, so the asinh map is logarithmic over the rates that matter
+    and linear near zero; the trust box is the per-feature range of the samples; the
+    sampled-node check accepts |S_learned - S_plain| <= tol_check sum|S_plain| +
+    floor_fraction omega_ref."""
+    import torch
+    Xd, Yd = X.double(), Y.double()
+    w_ref = float(torch.quantile(Yd[:, :5].abs().flatten(), ref_quantile).item()) * ref_fraction
+    j_ref = float(torch.quantile(Yd[:, 5:].abs().flatten(), ref_quantile).item()) * ref_fraction
+    w_ref = max(w_ref, 1e-30)
+    j_ref = max(j_ref, 1e-30)
+    Z = torch.cat([torch.asinh(Yd[:, :5] / w_ref), torch.asinh(Yd[:, 5:] / j_ref)], dim=1)
+    mx, sx = Xd.mean(0), Xd.std(0).clamp_min(1e-12)
+    mz, sz = Z.mean(0), Z.std(0).clamp_min(1e-6)
+    st = np.zeros(DG_SRC_NSTATS)
+    st[0:7] = mx.cpu().numpy()
+    st[7:14] = sx.cpu().numpy()
+    st[14:24] = mz.cpu().numpy()
+    st[24:34] = sz.cpu().numpy()
+    st[34], st[35] = w_ref, j_ref
+    st[36:43] = Xd.min(0).values.cpu().numpy()
+    st[43:50] = Xd.max(0).values.cpu().numpy()
+    st[50], st[51], st[52] = tol_check, tol_mass, floor_fraction * w_ref
+    Xn = ((Xd - mx) / sx).float().contiguous()
+    Zn = ((Z - mz) / sz).float().contiguous()
+    return Xn, Zn, st
+
+
+def train_source(X, Y, epochs=30, batch=4096, lr=2e-3, seed=0, val_frac=0.1, log=None, **stat_kw):
+    """Source surrogate (ten outputs).  Returns (params float32 [P] host, stats float64
+    [DG_SRC_NSTATS], history)."""
+    Xn, Zn, st = source_stats(X, Y, **stat_kw)
+    params, hist = fit(Xn, Zn, epochs, batch, lr, seed, val_frac, log)
+    return params.cpu().numpy(), st, hist
+
+
+def validation_loss(params, Xv, Yv):
     import torch
     from . import dg_mlp_forward
-    y = torch.empty_like(Tv)
+    y = torch.empty_like(Yv)
     dg_mlp_forward(params, Xv, y, tensor_cores=0)
-    return float(((y - Tv) ** 2).mean().item())
+    return float(((y - Yv) ** 2).mean().item())

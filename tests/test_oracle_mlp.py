@@ -154,3 +154,84 @@ def test_multi_output_gradient_matches_finite_differences(orc):
         assert abs(fd - g[i]) < 1e-6 * abs(g[i]) + 2e-9, (i, fd, g[i])
     Y = orc.mlp_forward(p, X, no)
     assert abs(loss - np.mean((Y - T) ** 2)) < 1e-14 * max(1, loss)
+
+
+# ---- the oracle's learned-source evaluation (decode, acceptance flags, projection)
+
+def _const_net(orc, c):
+    """Ten-output network whose outputs are the constants c (W3 = 0, b3 = c)."""
+    p = np.zeros(orc.mlp_nparams(10))
+    p[-10:] = c
+    return p
+
+
+def _stats(mu, sd, w_ref=2.0, j_ref=3.0, lo=-1e30, hi=1e30, tol_mass=0.05):
+    st = np.zeros(53)
+    st[0:7] = [0.2, 0.2, 0.2, 0.2, 0.2, math.log(0.05), 2500.0]
+    st[7:14] = [0.1, 0.1, 0.1, 0.1, 0.1, 1.0, 1500.0]
+    st[14:24] = mu
+    st[24:34] = sd
+    st[34], st[35] = w_ref, j_ref
+    st[36:43], st[43:50] = lo, hi
+    st[50], st[51], st[52] = 0.05, tol_mass, 0.0
+    return st
+
+
+def test_source_surrogate_decode_closed_form(orc):
+    """Constant network outputs y: omega_s = w_ref sinh(mu + sd y), jpi = max(0, j_ref
+    sinh(...)), the projection sum-free, S = omega / (1 + dt jpi)."""
+    c = np.array([0.3, -0.2, 0.1, 0.5, -0.4, 0.2, -1.0, 0.7, 0.0, 1.3])
+    mu = np.linspace(-0.5, 0.5, 10)
+    sd = np.linspace(0.5, 2.0, 10)
+    st = _stats(mu, sd, tol_mass=10.0)
+    rhos = np.array([[0.01, 0.02, 0.03, 0.005, 0.0015], [1.0, 0.1, 0.2, 0.3, 0.4]])
+    T = np.array([3000.0, 800.0])
+    dt = 1e-6
+    S, ok, om, jpi = orc.chem_surrogate_source(_const_net(orc, c), st, rhos, T, dt)
+    z = mu + sd * c
+    om_ref = 2.0 * np.sinh(z[:5])
+    jpi_ref = np.maximum(0.0, 3.0 * np.sinh(z[5:]))
+    for r in range(2):
+        assert np.allclose(om[r], om_ref, rtol=1e-14, atol=0)
+        assert np.allclose(jpi[r], jpi_ref, rtol=1e-14, atol=0)
+        proj = om_ref - np.abs(om_ref) * om_ref.sum() / np.abs(om_ref).sum()
+        assert np.allclose(S[r], proj / (1.0 + dt * jpi_ref), rtol=1e-13, atol=1e-15)
+        assert abs(S[r].sum() * 0 + (proj).sum()) < 1e-14 * np.abs(om_ref).sum()
+    assert ok.all()
+
+
+def test_source_surrogate_projection_is_mass_conserving(orc):
+    rng = np.random.default_rng(11)
+    p = 0.4 * rng.normal(size=orc.mlp_nparams(10))
+    st = _stats(np.zeros(10), np.ones(10), w_ref=1e3, j_ref=1e2, tol_mass=1e9)
+    rhos = rng.uniform(1e-3, 0.1, size=(64, 5))
+    T = rng.uniform(300, 5000, size=64)
+    S, ok, om, jpi = orc.chem_surrogate_source(p, st, rhos, T, dt=0.0)
+    assert np.all(np.abs(S.sum(axis=1)) <= 1e-13 * np.abs(om).sum(axis=1))
+    # a species whose raw rate is zero stays zero (the correction is proportional to |omega|)
+    p2 = p.copy()
+    head = 64 * 7 + 64 + 64 * 64 + 64
+    p2[head + 2 * 64:head + 3 * 64] = 0.0   # head of output 2 (omega_3)
+    p2[head + 10 * 64 + 2] = 0.0            # its bias
+    S2, _, om2, _ = orc.chem_surrogate_source(p2, st, rhos, T)
+    assert np.all(om2[:, 2] == 0.0) and np.all(S2[:, 2] == 0.0)
+
+
+def test_source_surrogate_acceptance_flags(orc):
+    c = np.array([0.3, -0.2, 0.1, 0.5, -0.4, 0, 0, 0, 0, 0])
+    rhos = np.array([[0.01, 0.02, 0.03, 0.005, 0.0015]])
+    T = np.array([3000.0])
+    om = 2.0 * np.sinh(c[:5])
+    imbalance = abs(om.sum()) / np.abs(om).sum()
+    p = _const_net(orc, c)
+    # mass balance just above / below the raw imbalance
+    _, ok, _, _ = orc.chem_surrogate_source(p, _stats(np.zeros(10), np.ones(10), tol_mass=imbalance * 1.001), rhos, T)
+    assert ok.all()
+    _, ok, _, _ = orc.chem_surrogate_source(p, _stats(np.zeros(10), np.ones(10), tol_mass=imbalance * 0.999), rhos, T)
+    assert not ok.any()
+    # box: T outside [lo, hi] rejects
+    lo = np.full(7, -1e30)
+    hi = np.full(7, 1e30)
+    hi[6] = 2999.0
+    _, ok, _, _ = orc.chem_surrogate_source(p, _stats(np.zeros(10), np.ones(10), lo=lo, hi=hi, tol_mass=1.0), rhos, T)
+    assert not ok.any()
