@@ -325,10 +325,11 @@ def run_mixture(args, stream_ptr, world):
 def run_reacting(args, stream_ptr, world):
     """Five-species reacting mixture (17 reactions, FP64 finite-rate source with point-implicit
     scaling) on a 48 x 48 x 16-element cylinder O-grid, N = 4, with a 3000 K layer round the
-    body: per-kernel device time per step in the mixed and the FP64 form, and the chemistry
-    kernel against the measured FP64 arithmetic peak."""
+    body: per-kernel device time per step in the mixed and the FP64 form, and the mixed form
+    with the learned source (trained here on states of the plain run)."""
     import torch
     import paper_2511_17551_gb300 as dg
+    from paper_2511_17551_gb300 import surrogate as S
     N = 4
     nr, nth, nz = args.react_elements, args.react_elements, max(2, args.react_elements // 3)
     xi, _ = dg.dg_lgl_nodes(N)
@@ -340,32 +341,55 @@ def run_reacting(args, stream_ptr, world):
     fs = W.mixture_primitive(xyz[:1], rho=0.1, vel=u_inf, T=300.0, seed=7)[0, :, 0]
     K, npn = xyz.shape[0], (N + 1) ** 3
     dof = K * npn * 10
+    cfl = 0.05
     out = {"workload": "reacting_5sp_17r_ogrid_%dx%dx%d_N4" % (nr, nth, nz), "elements": K,
-           "dof": dof, "cfl": 0.05}
-    for name, prec, n in (("mixed", dg.DG_MIXED, args.react_steps),
-                          ("fp64", dg.DG_FP64, max(1, args.react_steps // 2))):
+           "dof": dof, "cfl": cfl}
+
+    def make(prec):
         s = dg.Solver(3, N, xyz, nbr, face, n_species=5, species=sp, volume_flux=dg.DG_VF_DUCROS,
                       surface_flux=dg.DG_SF_LLF, bc_kind=[1, 2, 3], bc_prim=np.stack([fs] * 3),
                       alpha_max=0.5, precision=prec, reactions=R, stream=stream_ptr)
         s.set_primitive(w0)
-        s.step(2, 0.05)
+        return s
+
+    def timed(s, n):
+        s.step(2, cfl)
         dg.dg_profile(s.ctx, 1)
         dg.dg_profile_read(s.ctx)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        s.step(n, 0.05)
+        s.step(n, cfl)
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
         prof = dg.dg_profile_read(s.ctx)
         dg.dg_profile(s.ctx, 0)
-        s.close()
         chem_ms = prof["chem"][0] / max(1, prof["chem"][1])
-        out[name] = {"value": world * dof * 5 * n / wall, "unit": "DOF*RHS/s",
-                     "ms_per_step": wall * 1e3 / n, "steps": n,
-                     "chem_ms_per_launch": chem_ms,
-                     "chem_ns_per_node": chem_ms * 1e6 / (K * npn),
-                     "device_ms_per_step_by_kernel": {k: round(v[0] / n, 4)
-                                                      for k, v in prof.items() if v[1]}}
+        return {"value": world * dof * 5 * n / wall, "unit": "DOF*RHS/s",
+                "ms_per_step": wall * 1e3 / n, "steps": n, "chem_ms_per_launch": chem_ms,
+                "chem_ns_per_node": chem_ms * 1e6 / (K * npn),
+                "device_ms_per_step_by_kernel": {k: round(v[0] / n, 4) for k, v in prof.items() if v[1]}}
+
+    s = make(dg.DG_MIXED)
+    out["mixed"] = timed(s, args.react_steps)
+    # learned source: data from the plain run's own states, training, the same steps again
+    t0 = time.perf_counter()
+    s.set_primitive(w0)
+    X, Y = S.collect_source(s.ctx, args.train_samples, 8, 1, cfl=cfl)
+    params, stats, hist = S.train_source(X, Y, epochs=args.train_epochs, batch=4096, lr=2e-3)
+    train_s = time.perf_counter() - t0
+    s.set_primitive(w0)
+    dg.dg_set_surrogate(s.ctx, params, stats, which=dg.DG_SURROGATE_SOURCE)
+    dg.dg_surrogate_stats(s.ctx, dg.DG_SURROGATE_SOURCE)
+    learned = timed(s, args.react_steps)
+    acc, fb = dg.dg_surrogate_stats(s.ctx, dg.DG_SURROGATE_SOURCE)
+    learned["accepted_node_fraction"] = acc / max(1, acc + fb)
+    learned["training"] = {"samples": int(X.shape[0]), "epochs": args.train_epochs,
+                           "val_mse_first_last": [hist[0][2], hist[-1][2]], "seconds": train_s}
+    out["mixed_learned_source"] = learned
+    s.close()
+    s64 = make(dg.DG_FP64)
+    out["fp64"] = timed(s64, max(1, args.react_steps // 2))
+    s64.close()
     return out
 
 

@@ -160,7 +160,7 @@ dg_status dg_get_temperature(dg_ctx* ctx, double* T);
  *   S_s = omega_s / (1 + dt jpi_s) for any RK step dt.  Stats (FP64, DG_SRC_NSTATS)
  *   indexed by the DG_SRC_* offsets below.  Acceptance per tile of 32 consecutive nodes:
  *   every node's raw features inside the training box, every node's raw rates
- *   mass-balanced (|sum omega| <= tol_mass sum |omega|), and, at one node per tile drawn
+ *   mass-balanced (|sum omega| <= tol_mass sum |omega| + floor), and, at one node per tile drawn
  *   anew each evaluation, |S_learned - S_plain| <= tol_check sum_s |S_plain| + floor for
  *   every species; rejected tiles are recomputed with the plain FP64 source.  Accepted
  *   rates are projected onto exact mass balance, omega_s -= |omega_s| sum omega / sum|omega|. */
@@ -176,7 +176,7 @@ enum {
   DG_SRC_BOX_HI = 43,     /* [7] largest */
   DG_SRC_TOL_CHECK = 50,  /* sampled-node check, relative tolerance */
   DG_SRC_TOL_MASS = 51,   /* raw mass-balance tolerance */
-  DG_SRC_FLOOR = 52,      /* sampled-node check, absolute floor, kg/(m^3 s) */
+  DG_SRC_FLOOR = 52,      /* absolute floor of both rate checks, kg/(m^3 s) */
   DG_SRC_NSTATS = 53
 };
 

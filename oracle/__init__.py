@@ -314,7 +314,7 @@ def chem_surrogate_source(params, stats, rhos, T, dt=0.0):
     Steps: raw features x = (Y_1..Y_5, ln rho, T); network on (x - mean)/std; decode
     omega_s = omega_ref sinh(mu_s + sd_s y_s), jpi_s = max(0, jpi_ref sinh(mu_{5+s} +
     sd_{5+s} y_{5+s})); node accepted when x lies in the box and |sum omega| <=
-    tol_mass sum|omega|; projection omega_s -= |omega_s| sum(omega)/sum|omega|;
+    tol_mass sum|omega| + floor; projection omega_s -= |omega_s| sum(omega)/sum|omega|;
     S_s = omega_s / (1 + dt jpi_s).  Returns (S [n][5], accepted [n] bool, omega raw
     [n][5], jpi [n][5])."""
     st = np.asarray(stats, dtype=np.float64)
@@ -329,7 +329,7 @@ def chem_surrogate_source(params, stats, rhos, T, dt=0.0):
     msum = om.sum(axis=1)
     asum = np.abs(om).sum(axis=1)
     inside = np.all((x >= st[36:43]) & (x <= st[43:50]), axis=1)
-    accepted = inside & (np.abs(msum) <= st[51] * asum)
+    accepted = inside & (np.abs(msum) <= st[51] * asum + st[52])
     frac = np.divide(msum, asum, out=np.zeros_like(msum), where=asum > 0)
     S = (om - np.abs(om) * frac[:, None]) / (1.0 + dt * jpi)
     return S, accepted, om, jpi

@@ -126,14 +126,15 @@ __global__ void chem_kernel(const T* u, const double* Tc, int64_t K, int np, int
 // (Y_1..Y_5, ln rho, T); outputs are the standardised asinh images
 // z_s = asinh(omega_s / omega_ref), z_{5+s} = asinh(jpi_s / jpi_ref).
 // Acceptance, per tile of 32 nodes (one warp): every node inside the training box, every
-// node's raw rates mass-balanced within tol_mass, and one sampled node per tile (moved
+// node's raw rates mass-balanced (|sum omega| <= tol_mass sum|omega| + floor), and one
+// sampled node per tile (moved
 // each call) within tol_check of the plain FP64 source; otherwise the tile's source is
 // recomputed plainly.  Accepted rates are projected onto exact mass balance:
 // omega_s -= |omega_s| sum(omega) / sum|omega|.
 struct __align__(16) DgChemMlp {
   DgMlpW<10> w;
   float mean[7], inv_std[7], muY[10], sdY[10], lo[7], hi[7];
-  float w_ref, j_ref, tol_mass, pad;
+  float w_ref, j_ref, tol_mass, floor32;
   double tol_check, floor;
 };
 
@@ -208,7 +209,7 @@ chem_mlp_kernel(const T* u, const double* Tc, int64_t K, int np, int dim, const 
         msum += om[s];
         asum += fabsf(om[s]);
       }
-      ok = ok && isfinite(asum) && fabsf(msum) <= m.tol_mass * asum;
+      ok = ok && isfinite(asum) && fabsf(msum) <= m.tol_mass * asum + m.floor32;
       const float f = asum > 0.f ? msum / asum : 0.f;
       T* so = src + k * NSPEC * np + node;
 #pragma unroll
@@ -398,6 +399,7 @@ cudaError_t dg_chem_mlp_set(DgThermo* th, const float* params_host, const double
   h->tol_mass = (float)st[DG_SRC_TOL_MASS];
   h->tol_check = st[DG_SRC_TOL_CHECK];
   h->floor = st[DG_SRC_FLOOR];
+  h->floor32 = (float)st[DG_SRC_FLOOR];
   const int64_t ntiles = (th->K * th->np + 31) / 32;
   cudaError_t e = cudaSuccess;
   if (!th->chem_mlp) e = cudaMalloc(&th->chem_mlp, sizeof(DgChemMlp));

@@ -114,13 +114,14 @@ def train(X, T, epochs=20, batch=4096, lr=1e-3, seed=0, val_frac=0.1, log=None):
 
 
 def source_stats(X, Y, ref_quantile=0.99, ref_fraction=1e-3, tol_check=0.05, tol_mass=0.05,
-                 floor_fraction=0.1):
+                 floor_fraction=0.1, box_margin=0.01):
     """Statistics of the source surrogate (float64 [DG_SRC_NSTATS]) and the standardised
     training arrays.  omega_ref (jpi_ref) = ref_fraction x the ref_quantile of |omega|
     (of jpi) over the samples, so the asinh map is logarithmic over the rates that matter
-    and linear near zero; the trust box is the per-feature range of the samples; the
-    sampled-node check accepts |S_learned - S_plain| <= tol_check sum|S_plain| +
-    floor_fraction omega_ref."""
+    and linear near zero; the trust box is the per-feature range of the samples widened
+    by box_margin of its width on each side; both rate checks carry the absolute floor
+    floor_fraction omega_ref (the sampled-node check accepts |S_learned - S_plain| <=
+    tol_check sum|S_plain| + floor)."""
     import torch
     Xd, Yd = X.double(), Y.double()
     w_ref = float(torch.quantile(Yd[:, :5].abs().flatten(), ref_quantile).item()) * ref_fraction
@@ -136,8 +137,9 @@ def source_stats(X, Y, ref_quantile=0.99, ref_fraction=1e-3, tol_check=0.05, tol
     st[14:24] = mz.cpu().numpy()
     st[24:34] = sz.cpu().numpy()
     st[34], st[35] = w_ref, j_ref
-    st[36:43] = Xd.min(0).values.cpu().numpy()
-    st[43:50] = Xd.max(0).values.cpu().numpy()
+    lo, hi = Xd.min(0).values, Xd.max(0).values
+    st[36:43] = (lo - box_margin * (hi - lo)).cpu().numpy()
+    st[43:50] = (hi + box_margin * (hi - lo)).cpu().numpy()
     st[50], st[51], st[52] = tol_check, tol_mass, floor_fraction * w_ref
     Xn = ((Xd - mx) / sx).float().contiguous()
     Zn = ((Z - mz) / sz).float().contiguous()

@@ -56,10 +56,14 @@ def _reacting(dg, precision=0, N=3):
                   surface_flux=0, bc_kind=kinds, bc_prim=bcp, precision=precision,
                   reactions=W.reaction_table())
     s.set_primitive(w)
+    s.w0 = w
     return s
 
 
 def _rhs(dg, torch, s):
+    """Right-hand side of the initial state.  Setting the state again re-seeds the
+    temperature cache, so repeated evaluations start the Newton solve identically."""
+    s.set_primitive(s.w0)
     u = torch.empty(s.shape, dtype=torch.float64, device="cuda")
     dg.dg_get_state(s.ctx, u)
     r = torch.empty_like(u)
@@ -157,7 +161,7 @@ def trained_source(env):
                           bc_kind=kinds, bc_prim=bcp, reactions=W.reaction_table())
         dt = 0.1 * o.max_dt(o.prim_to_cons(w_o), 0.5)
         X, Y = S.collect_source(s.ctx, 48000, 24, 1, dt_fixed=dt)
-        params, stats, hist = S.train_source(X, Y, epochs=40, batch=2048, lr=3e-3)
+        params, stats, hist = S.train_source(X, Y, epochs=150, batch=2048, lr=3e-3)
         return params, stats, hist, dt
     finally:
         s.close()
@@ -187,15 +191,26 @@ def test_trained_source_surrogate(env, trained_source):
         frac_within = np.mean(np.all(np.abs(dS) <= 2.0 * bound[:, None], axis=1))
         assert frac_within > 0.95, (frac_within, acc, fb)
         # RK steps with the learned source stay close to the plain FP64 run
-        s.set_primitive(cases.mixture_ogrid(dg.dg_lgl_nodes(3)[0], hot=(1.2, 2500.0))[3])
+        s.set_primitive(s.w0)
         dg.dg_set_surrogate(s.ctx, params, stats, which=dg.DG_SURROGATE_SOURCE)
         s.step(3, dt_fixed=dt)
         u_l, _ = s.get_state()
         dg.dg_set_surrogate(s.ctx, None, which=dg.DG_SURROGATE_SOURCE)
-        s.set_primitive(cases.mixture_ogrid(dg.dg_lgl_nodes(3)[0], hot=(1.2, 2500.0))[3])
+        s.set_primitive(s.w0)
         s.step(3, dt_fixed=dt)
         u_p, _ = s.get_state()
+        # the species increments of the learned run against those of the plain run: the
+        # accepted sources carry up to tol_check of the local rates (plus the floor), so
+        # the increments differ by a fraction of that order
+        u0 = np.zeros_like(u_p)
+        s.set_primitive(s.w0)
+        u0, _ = s.get_state()
+        inc = np.linalg.norm((u_p - u0)[:, :5, :].transpose(1, 0, 2).reshape(5, -1), axis=1)
+        dif = np.linalg.norm((u_l - u_p)[:, :5, :].transpose(1, 0, 2).reshape(5, -1), axis=1)
+        ratio = dif / inc
+        assert ratio.max() < 0.25, (ratio, acc, fb)
+        # momentum and energy are not touched by the source beyond the coupling
         err = cases.field_errors(u_l, u_p, 5, 3)
-        assert err.max() < 1e-2, err
+        assert err[5:].max() < 1e-3, err
     finally:
         s.close()
