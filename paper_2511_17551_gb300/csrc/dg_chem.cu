@@ -32,37 +32,43 @@ __device__ __forceinline__ double ipow012(double c, double nu) {
   return r;
 }
 
+// Device tables (built by dg_chem_init from the species and reaction arrays):
+// species rows [16]: 1e-6/W, 1e6 W, h/(RT) coefficients (a1, a2/2, a3/3, a4/4, a5/5, a6),
+//   s/R coefficients (a1 [times ln T], a2, a3/2, a4/3, a5/4, a7), ln(1e-6 p0 / R_u), 0;
+// reaction rows [32]: nu'(5), nu''(5), third_body, eff(5), ln A, beta, theta,
+//   dn = sum dnu, dnu(5), 0...
+#define SP_W 16
+#define RX_W 32
+
 // Plain FP64 source at one node: omega_s (kg/m^3/s) and the point-implicit terms
 // jpi_s = max(0, -d omega_s / d rho_s) of the analytic diagonal Jacobian at fixed T.
 // uu points at the node's first species density, stride np between variables.
 template <typename T>
-__device__ __forceinline__ void chem_node(const T* uu, int np, double Tk, const double* sp_raw,
+__device__ __forceinline__ void chem_node(const T* uu, int np, double Tk, const double* sp,
                                           const double* reac, int nr, double* om, double* jpi) {
   const double lnT = log(Tk), iT = 1.0 / Tk;
-  double c[NSPEC], g[NSPEC], jd[NSPEC];
+  // ln(1e-6 p0 / (R_u T)) = ln(1e-6 p0 / R_u) - ln T (the constant sits in species row 0)
+  const double lnP = sp[14] - lnT;
+  double c[NSPEC], ic[NSPEC], g[NSPEC], jd[NSPEC];
 #pragma unroll
   for (int s = 0; s < NSPEC; ++s) {
-    const double* a = sp_raw + 8 * s + 1;
-    c[s] = 1e-6 * (double)uu[s * np] / sp_raw[8 * s];
-    const double h = a[0] + Tk * (a[1] / 2.0 + Tk * (a[2] / 3.0 + Tk * (a[3] / 4.0 + Tk * a[4] / 5.0))) + a[5] * iT;
-    const double sr = a[0] * lnT + Tk * (a[1] + Tk * (a[2] / 2.0 + Tk * (a[3] / 3.0 + Tk * a[4] / 4.0))) + a[6];
+    const double* q = sp + SP_W * s;
+    c[s] = q[0] * (double)uu[s * np];
+    ic[s] = c[s] > 0.0 ? 1.0 / c[s] : 0.0;
+    const double h = q[2] + Tk * (q[3] + Tk * (q[4] + Tk * (q[5] + Tk * q[6]))) + q[7] * iT;
+    const double sr = q[8] * lnT + Tk * (q[9] + Tk * (q[10] + Tk * (q[11] + Tk * q[12]))) + q[13];
     g[s] = h - sr;
     om[s] = 0.0;
     jd[s] = 0.0;
   }
-  const double lnP = log(1e-6 * DG_P0 / (DG_RU * Tk));
   for (int r = 0; r < nr; ++r) {
-    const double* row = reac + 20 * r;  // [nu'(5), nu''(5), tb, eff(5), lnA, beta, theta, 0]
-    double dg = 0.0, dn = 0.0;
+    const double* row = reac + RX_W * r;
+    double dg = 0.0;
 #pragma unroll
-    for (int s = 0; s < NSPEC; ++s) {
-      const double d = row[5 + s] - row[s];
-      dg += d * g[s];
-      dn += d;
-    }
+    for (int s = 0; s < NSPEC; ++s) dg += row[20 + s] * g[s];
     const double lnkf = row[16] + row[17] * lnT - row[18] * iT;
     const double kf = exp(lnkf);
-    const double kb = exp(lnkf + dg - dn * lnP);
+    const double kb = exp(lnkf + dg - row[19] * lnP);
     double pf = kf, pb = kb;
 #pragma unroll
     for (int s = 0; s < NSPEC; ++s) {
@@ -79,13 +85,14 @@ __device__ __forceinline__ void chem_node(const T* uu, int np, double Tk, const 
     const double Rr = (pf - pb) * M;
 #pragma unroll
     for (int s = 0; s < NSPEC; ++s) {
-      const double d = row[5 + s] - row[s];
-      om[s] += 1e6 * sp_raw[8 * s] * d * Rr;
+      const double d = row[20 + s];
+      if (d == 0.0) continue;  // the same for every node: no divergence
+      om[s] += d * Rr;
       // d R_r / d c_s (explicit products when c_s = 0)
       double dpf = 0.0, dpb = 0.0;
       if (c[s] > 0.0) {
-        dpf = row[s] > 0.0 ? pf * row[s] / c[s] : 0.0;
-        dpb = row[5 + s] > 0.0 ? pb * row[5 + s] / c[s] : 0.0;
+        dpf = pf * row[s] * ic[s];
+        dpb = pb * row[5 + s] * ic[s];
       } else {
         if (row[s] == 1.0) {
           dpf = kf;
@@ -99,8 +106,12 @@ __device__ __forceinline__ void chem_node(const T* uu, int np, double Tk, const 
       jd[s] += d * ((dpf - dpb) * M + (tb ? (pf - pb) * row[11 + s] : 0.0));
     }
   }
+  // omega in kg/(m^3 s); d omega_s / d rho_s = 1e6 W_s (1e-6 / W_s) d(...)/dc_s = jd_s
 #pragma unroll
-  for (int s = 0; s < NSPEC; ++s) jpi[s] = -jd[s] > 0.0 ? -jd[s] : 0.0;
+  for (int s = 0; s < NSPEC; ++s) {
+    om[s] *= sp[SP_W * s + 1];
+    jpi[s] = -jd[s] > 0.0 ? -jd[s] : 0.0;
+  }
 }
 
 template <typename T>
@@ -320,21 +331,47 @@ unsigned grid_of(int64_t n) {
 
 cudaError_t dg_chem_init(DgThermo* th, const double* species_host, const double* reac_host, int nr) {
   if (nr < 1 || nr > 64) return cudaErrorInvalidValue;
-  double* rows = (double*)malloc(sizeof(double) * 20 * nr);
+  double* rows = (double*)calloc((size_t)RX_W * nr + SP_W * NSPEC, sizeof(double));
   if (!rows) return cudaErrorMemoryAllocation;
   for (int r = 0; r < nr; ++r) {
-    for (int q = 0; q < 16; ++q) rows[20 * r + q] = reac_host[19 * r + q];
-    rows[20 * r + 16] = log(reac_host[19 * r + 16]);
-    rows[20 * r + 17] = reac_host[19 * r + 17];
-    rows[20 * r + 18] = reac_host[19 * r + 18];
-    rows[20 * r + 19] = 0.0;
+    const double* in = reac_host + 19 * r;  // [nu'(5), nu''(5), tb, eff(5), A, beta, theta]
+    double* o = rows + RX_W * r;
+    for (int q = 0; q < 16; ++q) o[q] = in[q];
+    o[16] = log(in[16]);
+    o[17] = in[17];
+    o[18] = in[18];
+    double dn = 0.0;
+    for (int s = 0; s < NSPEC; ++s) {
+      o[20 + s] = in[5 + s] - in[s];
+      dn += o[20 + s];
+    }
+    o[19] = dn;
+  }
+  double* sp = rows + (size_t)RX_W * nr;
+  for (int s = 0; s < NSPEC; ++s) {
+    const double* in = species_host + 8 * s;  // [W, a1..a7]
+    double* o = sp + SP_W * s;
+    o[0] = 1e-6 / in[0];
+    o[1] = 1e6 * in[0];
+    o[2] = in[1];
+    o[3] = in[2] / 2.0;
+    o[4] = in[3] / 3.0;
+    o[5] = in[4] / 4.0;
+    o[6] = in[5] / 5.0;
+    o[7] = in[6];
+    o[8] = in[1];
+    o[9] = in[2];
+    o[10] = in[3] / 2.0;
+    o[11] = in[4] / 3.0;
+    o[12] = in[5] / 4.0;
+    o[13] = in[7];
+    o[14] = log(1e-6 * DG_P0 / DG_RU);
   }
   const size_t rs = th->f32 ? sizeof(float) : sizeof(double);
-  cudaError_t e = cudaMalloc((void**)&th->reac, sizeof(double) * 20 * nr);
-  if (e == cudaSuccess) e = cudaMemcpy(th->reac, rows, sizeof(double) * 20 * nr, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMalloc((void**)&th->species_raw, sizeof(double) * 8 * NSPEC);
-  if (e == cudaSuccess)
-    e = cudaMemcpy(th->species_raw, species_host, sizeof(double) * 8 * NSPEC, cudaMemcpyHostToDevice);
+  cudaError_t e = cudaMalloc((void**)&th->reac, sizeof(double) * RX_W * nr);
+  if (e == cudaSuccess) e = cudaMemcpy(th->reac, rows, sizeof(double) * RX_W * nr, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&th->species_raw, sizeof(double) * SP_W * NSPEC);
+  if (e == cudaSuccess) e = cudaMemcpy(th->species_raw, sp, sizeof(double) * SP_W * NSPEC, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMalloc(&th->src, rs * NSPEC * th->K * th->np);
   free(rows);
   th->nr = nr;

@@ -687,16 +687,25 @@ struct GLayout {
   static constexpr int NP = S::NP;
   static constexpr int EPB = epb<DIM, N>();
   static constexpr int NW = DIM + 1;
+  // swizzled W and G blocks, direction-uniform line warps and (FP32) element strides of
+  // 16 words mod 32, as in the right-hand-side kernel
+  static constexpr bool SWZ = Swizzle<DIM, N>::ON;
+  static constexpr bool UNI = SWZ && (EPB * S::LPD) % 32 == 0;
+  static constexpr int padded(int w) { return (SWZ && sizeof(real) == 4) ? w + (48 - w % 32) % 32 : w; }
+  static constexpr int SW = padded(NW * NP), SG = padded(DIM * NW * NP);
   static constexpr int W = 0;
-  static constexpr int JA = W + EPB * NW * NP;
+  static constexpr int JA = W + EPB * SW;
   static constexpr int IJ = JA + EPB * DIM * DIM * NP;
   static constexpr int G = IJ + EPB * NP;
-  static constexpr int TOTAL = G + EPB * DIM * NW * NP;
+  static constexpr int TOTAL = G + EPB * SG;
   static constexpr int THREADS = ((EPB * S::LINES + 31) / 32) * 32;
+  // resident CTAs the register allocator is asked for: what shared memory allows, <= 8
+  static constexpr int BY_SMEM = (int)((227 * 1024) / (sizeof(real) * TOTAL + 1024));
+  static constexpr int MINB = BY_SMEM >= 8 ? 8 : (BY_SMEM < 1 ? 1 : BY_SMEM);
 };
 
 template <int DIM, int N, int NSP>
-__global__ void __launch_bounds__(GLayout<DIM, N, NSP>::THREADS)
+__global__ void __launch_bounds__(GLayout<DIM, N, NSP>::THREADS, GLayout<DIM, N, NSP>::MINB)
 gradient_kernel(const DgArgs a, const KConst kc) {
   using S = Shape<DIM, N>;
   using L = GLayout<DIM, N, NSP>;
@@ -719,34 +728,46 @@ gradient_kernel(const DgArgs a, const KConst kc) {
   stage_async(sg, gu + e0 * NV * NP, ne * NV * NP, tid, nth);
   cp_async_wait_all();
   __syncthreads();
+  auto SWZ = [](int n) { return Swizzle<DIM, N>::at(n); };
   for (int i = tid; i < ne * NP; i += nth) {
-    const int e = i / NP, node = i % NP;
+    const int e = i / NP, node = i % NP, pn = SWZ(node);
     const real* uu = sg + e * NV * NP + node;
     real rho = 0;
 #pragma unroll
     for (int k = 0; k < NSP; ++k) rho += uu[k * NP];
     real ir = RealOps<real>::rcp(rho), ke = 0;
+    real vv[DIM];
 #pragma unroll
     for (int d = 0; d < DIM; ++d) {
-      real v = uu[(NSP + d) * NP] * ir;
-      sw[(e * NW + d) * NP + node] = v;
-      ke += uu[(NSP + d) * NP] * v;
+      vv[d] = uu[(NSP + d) * NP] * ir;
+      ke += uu[(NSP + d) * NP] * vv[d];
     }
     real p = kc.gm1 * (uu[(NSP + DIM) * NP] - real(0.5) * ke);
-    sw[(e * NW + DIM) * NP + node] = p * ir;
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) sw[e * L::SW + d * NP + pn] = vv[d];
+    sw[e * L::SW + DIM * NP + pn] = p * ir;
   }
   __syncthreads();
-  for (int t = tid; t < ne * S::LINES; t += nth) {
-    const int e = t / S::LINES, r = t % S::LINES;
-    const int d = r / S::LPD, m = r % S::LPD;
+  for (int t = tid; t < L::EPB * S::LINES; t += nth) {
+    int e, d, m;
+    if (L::UNI) {  // warp-uniform direction
+      d = t / (L::EPB * S::LPD);
+      e = (t / S::LPD) % L::EPB;
+      m = t % S::LPD;
+    } else {
+      e = t / S::LINES;
+      d = (t % S::LINES) / S::LPD;
+      m = t % S::LPD;
+    }
+    if (e >= ne) continue;
     const int s = S::stride(d), base = S::line_base(d, m);
     const int64_t eg = e0 + e;
-    const real* w = sw + e * NW * NP;
+    const real* w = sw + e * L::SW;
     real Wl[N1][NW];
 #pragma unroll
     for (int i = 0; i < N1; ++i)
 #pragma unroll
-      for (int c = 0; c < NW; ++c) Wl[i][c] = w[c * NP + base + i * s];
+      for (int c = 0; c < NW; ++c) Wl[i][c] = w[c * NP + SWZ(base + i * s)];
     real G[N1][NW];
 #pragma unroll
     for (int i = 0; i < N1; ++i)
@@ -781,11 +802,11 @@ gradient_kernel(const DgArgs a, const KConst kc) {
         else G[0][c] -= B.iw[0] * (ws - Wl[0][c]);
       }
     }
-    real* g = sg + (e * DIM + d) * NW * NP;
+    real* g = sg + e * L::SG + d * NW * NP;
 #pragma unroll
     for (int i = 0; i < N1; ++i)
 #pragma unroll
-      for (int c = 0; c < NW; ++c) g[c * NP + base + i * s] = G[i][c];
+      for (int c = 0; c < NW; ++c) g[c * NP + SWZ(base + i * s)] = G[i][c];
   }
   __syncthreads();
   real* out = (real*)a.gradW;
@@ -799,7 +820,7 @@ gradient_kernel(const DgArgs a, const KConst kc) {
         real acc = 0;
 #pragma unroll
         for (int d = 0; d < DIM; ++d)
-          acc += sja[((e * DIM + d) * DIM + x) * NP + node] * sg[((e * DIM + d) * NW + c) * NP + node];
+          acc += sja[((e * DIM + d) * DIM + x) * NP + node] * sg[e * L::SG + (d * NW + c) * NP + SWZ(node)];
         out[((e0 + e) * DIM + x) * NW * NP + c * NP + node] = acc * ij;
       }
   }

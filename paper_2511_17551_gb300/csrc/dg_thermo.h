@@ -13,7 +13,7 @@ struct DgThermo {
   void* pc;            // device [K][2][np] pressure, sound speed (form precision)
   void* bc_pc;         // device [n_bc][2]
   unsigned long long* status;
-  double* species_raw; // device [ns][8] W, a1..a7 (chemistry)
+  double* species_raw; // device [ns][16] chemistry coefficient rows (dg_chem.cu)
   double* reac;        // device [nr][20] reaction rows (ln A in slot 16)
   int nr;              // number of reactions, 0 = frozen
   void* src;           // device [K][ns][np] chemistry source (form precision)
