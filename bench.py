@@ -45,6 +45,18 @@ WORDS_GRAD = 5 + 9 + 1 + 12
 RHS_DRAM_B_PER_NODE = 129.0
 
 
+def job_rate(ms_local, units_local, world, device="cpu"):
+    """Whole-job throughput of N replicas: the units all ranks processed over the slowest
+    rank's time (max over ranks of the timed region).  Returns (units/s, max ms)."""
+    import torch
+    t = torch.tensor([ms_local], dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms = float(t.item())
+    return world * units_local / (ms * 1e-3), ms
+
+
 def _env_rank():
     return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
             int(os.environ.get("LOCAL_RANK", "0")))
@@ -156,11 +168,7 @@ def run_ours(args, rank, world, local_rank):
     clocks = Clocks(local_rank)
     ms, prof = timed_steps(s, args.steps, profile=True)
     clk = clocks.stop()
-    ms_t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-    if world > 1:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-    ms = float(ms_t.item())
-    value = world * dof * 5 * args.steps / (ms * 1e-3)
+    value, ms = job_rate(ms, dof * 5 * args.steps, world, device="cuda")
     # --- end to end through the C ABI with host buffers (pinned), copies inside the region
     u_host = torch.empty((K, 5, npn), dtype=torch.float64).pin_memory()
     dg.dg_get_state(s.ctx, u_host)
@@ -222,7 +230,22 @@ def run_ours(args, rank, world, local_rank):
         out["reacting"] = run_reacting(args, stream.cuda_stream, world)
     if rank == 0:
         if not args.no_cpu_baseline:
-            out["cpu_baseline"] = cpu_baseline(cfg, args.cpu_seconds)
+            out["cpu_baseline"], r_oracle = cpu_baseline(cfg, args.cpu_seconds)
+            # the right-hand side of the workload's initial state from both GPU forms
+            # against the one the baseline leg computed
+            par = {"norm": "relative L2 per conserved field (rho, rho v x3, rho E); momentum "
+                           "over the momentum-block norm", "state": "initial state of the workload"}
+            for name, prec in (("rhs_fp64", dg.DG_FP64), ("rhs_mixed", dg.DG_MIXED)):
+                sp = make(prec)
+                ud = torch.empty(sp.shape, dtype=torch.float64, device="cuda")
+                dg.dg_get_state(sp.ctx, ud)
+                ud = ud.to(torch.float32 if prec == dg.DG_MIXED else torch.float64)
+                rd = torch.empty_like(ud)
+                dg.dg_rhs(sp.ctx, ud, rd)
+                dg.dg_sync(sp.ctx)
+                par[name] = field_errors(rd.double().cpu().numpy(), r_oracle)
+                sp.close()
+            out["parity_vs_oracle"] = par
         print(json.dumps(out))
     if world > 1:
         dist.destroy_process_group()
@@ -405,7 +428,7 @@ def cpu_baseline(cfg, budget_s):
     dof = u.size
     n, t0 = 0, time.perf_counter()
     while True:
-        o.rhs(u)
+        r = o.rhs(u)
         n += 1
         if time.perf_counter() - t0 > budget_s:
             break
@@ -413,7 +436,15 @@ def cpu_baseline(cfg, budget_s):
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count()))
     return {"value": dof * n / dt, "unit": "DOF*RHS/s", "cores": cores, "kind": "oracle",
             "sample": "%d full right-hand sides of the %d-element workload in %.1f s" % (
-                n, xyz.shape[0], dt)}
+                n, xyz.shape[0], dt)}, r
+
+
+def field_errors(a, ref, dim=3):
+    """Relative L2 error per conserved field (momentum components over the norm of the
+    whole momentum block)."""
+    mom = np.linalg.norm(ref[:, 1:1 + dim])
+    return [float(np.linalg.norm(a[:, v] - ref[:, v]) /
+                  (mom if 1 <= v <= dim else np.linalg.norm(ref[:, v]))) for v in range(a.shape[1])]
 
 
 def run_reference(args, rank, world):
