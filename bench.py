@@ -35,10 +35,10 @@ CONFIGS = {
     "tgv_ns_24^3_N3": dict(n_el=24, N=3, warp=0.1, mu=1.0 / 1600.0),
 }
 # algorithmic HBM words per node of one RK-stage launch (unique bytes, neighbour traces
-# excluded): main kernel reads u, Ja, 1/J, gradW, du and writes du, u_new;
-# gradient kernel reads u, Ja, 1/J and writes gradW.
-WORDS_MAIN_NS = 5 + 9 + 1 + 12 + 5 + 5 + 5
-WORDS_MAIN_EULER = 5 + 9 + 1 + 5 + 5 + 5
+# excluded): main kernel reads u, Ja, 1/J, gradW, du and the compensation part u_lo of the
+# FP32 state, writes du, u_new, u_lo; gradient kernel reads u, Ja, 1/J and writes gradW.
+WORDS_MAIN_NS = 5 + 9 + 1 + 12 + 5 + 5 + 5 + 10
+WORDS_MAIN_EULER = 5 + 9 + 1 + 5 + 5 + 5 + 10
 WORDS_GRAD = 5 + 9 + 1 + 12
 # dram__bytes_read.sum + dram__bytes_write.sum of the current mixed-form NS N=3 rhs_kernel
 # per node, from one ncu capture of the 24^3 case (traffic scales with the node count)

@@ -25,6 +25,7 @@ struct dg_ctx {
   double *Ja64, *J64, *invJ64;
   float *Ja32, *invJ32;
   void* u[2];
+  float* ulo;  // mixed form: low part of the compensated state (in place)
   int cur;
   void* du;
   void* gradW;
@@ -161,9 +162,25 @@ __global__ void cvt_back_kernel(const T* a, double* b, int64_t n) {
     b[i] = (double)a[i];
 }
 
+// compensated FP32 state of the mixed form: u = hi + lo, hi = fl32(u), lo = fl32(u - hi)
+__global__ void split_kernel(const double* a, float* hi, float* lo, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const float h = (float)a[i];
+    hi[i] = h;
+    lo[i] = (float)(a[i] - (double)h);
+  }
+}
+__global__ void merge_kernel(const float* hi, const float* lo, double* b, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = (double)hi[i] + (double)lo[i];
+}
+
 // one-gas primitive (rho, v, p) -> conserved, written in the form precision
+// (lo: the FP32 form's compensation part, or null)
 template <typename T>
-__global__ void prim2cons_kernel(const double* w, T* u, int64_t K, int dim, int np, double gamma) {
+__global__ void prim2cons_kernel(const double* w, T* u, float* lo, int64_t K, int dim, int np, double gamma) {
   const int nv = dim + 2;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < K * np;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -171,13 +188,17 @@ __global__ void prim2cons_kernel(const double* w, T* u, int64_t K, int dim, int 
     const int node = (int)(i % np);
     const double* ww = w + k * nv * np + node;
     T* uu = u + k * nv * np + node;
-    double rho = ww[0], ke = 0.0;
-    uu[0] = (T)rho;
+    double rho = ww[0], ke = 0.0, c[8];
+    c[0] = rho;
     for (int d = 0; d < dim; ++d) {
-      uu[(1 + d) * np] = (T)(rho * ww[(1 + d) * np]);
+      c[1 + d] = rho * ww[(1 + d) * np];
       ke += ww[(1 + d) * np] * ww[(1 + d) * np];
     }
-    uu[(1 + dim) * np] = (T)(ww[(1 + dim) * np] / (gamma - 1.0) + 0.5 * rho * ke);
+    c[1 + dim] = ww[(1 + dim) * np] / (gamma - 1.0) + 0.5 * rho * ke;
+    for (int v = 0; v < nv; ++v) {
+      uu[v * np] = (T)c[v];
+      if (lo) lo[k * nv * np + v * np + node] = (float)(c[v] - (double)(T)c[v]);
+    }
   }
 }
 
@@ -437,7 +458,7 @@ void free_ctx(dg_ctx* c) {
   if (!c) return;
   cudaSetDevice(c->dev);
   void* ptrs[] = {c->nbr, c->Ja64, c->J64, c->invJ64, c->Ja32, c->invJ32, c->u[0], c->u[1],
-                  c->du, c->gradW, c->alpha_raw, c->alpha_used, c->bc_kind, c->bc_u, c->scal,
+                  c->du, c->ulo, c->gradW, c->alpha_raw, c->alpha_used, c->bc_kind, c->bc_u, c->scal,
                   c->lam, c->status, c->partial, c->stage64};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -592,6 +613,7 @@ dg_status dg_init_mesh(const dg_mesh_desc* m, const dg_physics_desc* p, dg_ctx**
     TRYM(c->u[0], c->rs * nst);
     TRYM(c->u[1], c->rs * nst);
     TRYM(c->du, c->rs * nst);
+    if (c->precision == DG_MIXED) TRYM(c->ulo, sizeof(float) * nst);
     if (c->equations == DG_NAVIER_STOKES) TRYM(c->gradW, c->rs * K * dim * (dim + 1) * c->np);
     if (c->alpha_max > 0.0) {
       TRYM(c->alpha_raw, c->rs * K);
@@ -696,7 +718,7 @@ dg_status dg_set_state(dg_ctx* c, const double* u, int on_device, double t) {
     src = c->stage64;
   }
   if (c->precision == DG_MIXED) {
-    cvt_kernel<float><<<grid_for(n, 256), 256, 0, c->stream>>>(src, (float*)c->u[c->cur], n);
+    split_kernel<<<grid_for(n, 256), 256, 0, c->stream>>>(src, (float*)c->u[c->cur], c->ulo, n);
   } else {
     CK(cudaMemcpyAsync(c->u[c->cur], src, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream));
   }
@@ -719,14 +741,16 @@ dg_status dg_set_state_primitive(dg_ctx* c, const double* w, int on_device, doub
   if (c->n_species == 0) {
     if (c->precision == DG_MIXED)
       prim2cons_kernel<float><<<grid_for(c->K * c->np, 256), 256, 0, c->stream>>>(
-          src, (float*)c->u[c->cur], c->K, c->dim, c->np, c->gamma);
+          src, (float*)c->u[c->cur], c->ulo, c->K, c->dim, c->np, c->gamma);
     else
       prim2cons_kernel<double><<<grid_for(c->K * c->np, 256), 256, 0, c->stream>>>(
-          src, (double*)c->u[c->cur], c->K, c->dim, c->np, c->gamma);
+          src, (double*)c->u[c->cur], NULL, c->K, c->dim, c->np, c->gamma);
     CK(cudaGetLastError());
   } else {
-    // also seeds the temperature cache with the given temperatures
+    // also seeds the temperature cache with the given temperatures; the compensation part
+    // of a mixture state starts at zero (the FP32-rounded initial state)
     CK(dg_thermo_prim2cons(&c->th, src, c->u[c->cur], c->stream));
+    if (c->ulo) CK(cudaMemsetAsync(c->ulo, 0, sizeof(float) * n, c->stream));
   }
   CK(cudaMemcpyAsync(c->scal, &t, sizeof(double), cudaMemcpyHostToDevice, c->stream));
   c->have_state = true;
@@ -740,7 +764,7 @@ dg_status dg_get_state(dg_ctx* c, double* u, int on_device, double* t) {
   const int64_t n = c->K * c->nv * c->np;
   if (c->precision == DG_MIXED) {
     double* dst = on_device ? u : c->stage64;
-    cvt_back_kernel<float><<<grid_for(n, 256), 256, 0, c->stream>>>((const float*)c->u[c->cur], dst, n);
+    merge_kernel<<<grid_for(n, 256), 256, 0, c->stream>>>((const float*)c->u[c->cur], c->ulo, dst, n);
     CK(cudaGetLastError());
     if (!on_device)
       CK(cudaMemcpyAsync(u, c->stage64, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream));
@@ -793,6 +817,7 @@ dg_status dg_step_rk(dg_ctx* c, int nsteps, double cfl, double dt_fixed, double*
       b.u = c->u[c->cur];
       b.out = c->u[c->cur ^ 1];
       b.du = c->du;
+      b.ulo = c->ulo;
       b.mode = 1;
       b.stage = s;
       b.rkA = A[s];

@@ -610,7 +610,19 @@ rhs_kernel(const DgArgs a, const KConst kc) {
                           : (L::PREFETCH_DU ? sdu[e * L::SDU + k * NP + node] : du[gbase + k * NP]);
         real dn = kc.rkA * dold + dt * r;
         du[gbase + k * NP] = dn;
-        un[k] = su[e * L::SU + k * NP + node] + kc.rkB * dn;
+        const real hi = su[e * L::SU + k * NP + node];
+        if (sizeof(real) == 4 && a.ulo) {
+          // compensated FP32 state: (hi, lo) += B dn by an exact TwoSum (Knuth), so the
+          // rounding of every stage update is carried instead of lost
+          real* lo = (real*)a.ulo + gbase + k * NP;
+          const real inc = *lo + kc.rkB * dn;
+          const real s2 = hi + inc;
+          const real bb = s2 - hi;
+          *lo = (hi - (s2 - bb)) + (inc - bb);
+          un[k] = s2;
+        } else {
+          un[k] = hi + kc.rkB * dn;
+        }
         out[gbase + k * NP] = un[k];
       }
       if (a.want_lambda && NSP == 1) {
