@@ -682,9 +682,9 @@ dg_status dg_init_mesh(const dg_mesh_desc* m, const dg_physics_desc* p, dg_ctx**
       cudaError_t e2;
       if (c->n_species == 0) {
         if (c->precision == DG_MIXED)
-          prim2cons_kernel<float><<<1, 32, 0, c->stream>>>(bw, (float*)c->bc_u, p->n_bc, dim, 1, c->gamma);
+          prim2cons_kernel<float><<<1, 32, 0, c->stream>>>(bw, (float*)c->bc_u, NULL, p->n_bc, dim, 1, c->gamma);
         else
-          prim2cons_kernel<double><<<1, 32, 0, c->stream>>>(bw, (double*)c->bc_u, p->n_bc, dim, 1, c->gamma);
+          prim2cons_kernel<double><<<1, 32, 0, c->stream>>>(bw, (double*)c->bc_u, NULL, p->n_bc, dim, 1, c->gamma);
         e2 = cudaGetLastError();
       } else {
         e2 = dg_thermo_boundary(&c->th, bw, p->n_bc, c->bc_u, c->stream);
