@@ -134,8 +134,9 @@ def run_ours(args, rank, world, local_rank):
     stream = torch.cuda.current_stream()
 
     def make(precision):
+        # p_ref = the mean pressure p0 = 1/(gamma Ma^2) of the Mach-0.1 state
         s = dg.Solver(3, N, xyz, nbr, face, equations=eq, mu=cfg["mu"], Pr=0.72,
-                      precision=precision, stream=stream.cuda_stream)
+                      precision=precision, stream=stream.cuda_stream, p_ref=1.0 / (1.4 * 0.01))
         s.set_primitive(w0)
         return s
 

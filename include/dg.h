@@ -91,6 +91,13 @@ typedef struct {
                                nu'(5), nu''(5), third-body flag, efficiencies(5), A, beta,
                                theta = E/R_u (appendix, Eqs. chemreact..calc_prod), or NULL */
   int n_reactions;          /* 0: frozen mixture; 1..64 */
+  double p_ref;             /* one gas: pressure offset p_ref; the momentum components of
+                               every numerical flux use p - p_ref (a constant pressure adds
+                               nothing to the discrete right-hand side, so the result is the
+                               same in exact arithmetic) and the pressure of the mixed form is
+                               recovered from the compensated energy relative to
+                               p_ref / (gamma - 1): low-Mach fluctuations keep their FP32
+                               digits.  0 for none; must be 0 for mixtures. */
 } dg_physics_desc;
 
 /* LGL nodes and weights used by libdg for degree N (host arrays of N+1).

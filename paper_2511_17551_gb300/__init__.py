@@ -59,7 +59,8 @@ class PhysicsDesc(C.Structure):
                 ("volume_flux", C.c_int), ("surface_flux", C.c_int),
                 ("alpha_max", C.c_double), ("precision", C.c_int), ("thermo", C.c_int),
                 ("n_bc", C.c_int), ("bc_kind", C.c_void_p), ("bc_prim", C.c_void_p),
-                ("stream", C.c_void_p), ("reactions", C.c_void_p), ("n_reactions", C.c_int)]
+                ("stream", C.c_void_p), ("reactions", C.c_void_p), ("n_reactions", C.c_int),
+                ("p_ref", C.c_double)]
 
 
 _lib = None
@@ -302,7 +303,7 @@ class Solver:
                  gamma=1.4, mu=0.0, Pr=0.72, species=None, volume_flux=DG_VF_RANOCHA,
                  surface_flux=DG_SF_LLF, alpha_max=0.0, precision=DG_FP64,
                  thermo=DG_THERMO_NEWTON, bc_kind=None, bc_prim=None, stream=None,
-                 reactions=None):
+                 reactions=None, p_ref=0.0):
         self.dim, self.N = dim, N
         self.np = (N + 1) ** dim
         self.nsp = max(1, n_species)
@@ -327,7 +328,7 @@ class Solver:
                            thermo=thermo, n_bc=len(self._bck) if bc_kind is not None else 0,
                            bc_kind=_ptr(self._bck), bc_prim=_ptr(self._bcp), stream=stream,
                            reactions=_ptr(self._reac),
-                           n_reactions=0 if reactions is None else len(self._reac))
+                           n_reactions=0 if reactions is None else len(self._reac), p_ref=p_ref)
         self.ctx = dg_init_mesh(mesh, phys)
 
     @property

@@ -17,7 +17,7 @@ struct dg_ctx {
   int dim, N, np, nv, nsp, nf;
   int64_t K;
   int equations, n_species, vf, sf, precision, thermo, n_bc;
-  double gamma, mu, Pr, alpha_max;
+  double gamma, mu, Pr, alpha_max, p_ref;
   cudaStream_t stream;
   bool own_stream;
   size_t rs;  // bytes per real of the form
@@ -321,6 +321,7 @@ DgArgs base_args(dg_ctx* c) {
   a.sf = c->sf;
   a.ns = c->equations == DG_NAVIER_STOKES;
   a.gamma = c->gamma;
+  a.pref = c->p_ref;
   a.mu = c->mu;
   a.kappa_fac = a.ns ? c->mu * c->gamma / ((c->gamma - 1.0) * c->Pr) : 0.0;
   a.visc_coef = a.ns ? c->gamma * c->mu / c->Pr : 0.0;
@@ -524,6 +525,7 @@ dg_status dg_init_mesh(const dg_mesh_desc* m, const dg_physics_desc* p, dg_ctx**
     return DG_EINVAL;
   if (p->n_species > 0 && p->volume_flux == DG_VF_RANOCHA) return DG_EINVAL;
   if (p->n_species == 0 && !(p->gamma > 1.0)) return DG_EINVAL;
+  if (!(p->p_ref >= 0.0) || (p->n_species > 0 && p->p_ref != 0.0)) return DG_EINVAL;
   if (p->precision != DG_FP64 && p->precision != DG_MIXED) return DG_EINVAL;
   if (p->thermo != DG_THERMO_NEWTON && p->thermo != DG_THERMO_MLP) return DG_EINVAL;
   if (p->alpha_max < 0.0 || p->alpha_max > 1.0) return DG_EINVAL;
@@ -573,6 +575,7 @@ dg_status dg_init_mesh(const dg_mesh_desc* m, const dg_physics_desc* p, dg_ctx**
   c->thermo = p->thermo;
   c->n_bc = p->n_bc;
   c->gamma = p->gamma;
+  c->p_ref = p->p_ref;
   c->mu = p->mu;
   c->Pr = p->Pr;
   c->alpha_max = p->alpha_max;

@@ -24,6 +24,7 @@ struct DgArgs {
   int lam_cur;            // slot holding the current step's wave-speed maxima
   int ns;                 // Navier-Stokes terms on
   double gamma, mu, kappa_fac;   // kappa_fac = mu gamma / ((gamma-1) Pr)
+  double pref;                   // pressure offset of the momentum fluxes (one gas)
   double visc_coef;              // gamma mu / Pr (viscous time-step bound)
   double cfl, dt_fixed, rkA, rkB;
   const void* u;          // [K][nv][np] input state

@@ -112,17 +112,24 @@ struct Shape {
 };
 
 // ---------------------------------------------------------------- pointwise physics
-// Node state in registers (one gas: NSP = 1).
+// Node state in registers (one gas: NSP = 1).  p is the pressure, pp = p - p_ref the
+// shifted pressure that the momentum components of every flux use: a constant pressure
+// contributes nothing to the discrete right-hand side (free-stream preservation), so the
+// shift is exact in arithmetic and keeps low-Mach pressure fluctuations in FP32.
 template <typename real, int DIM, int NSP>
 struct NodeState {
   static constexpr int NV = NSP + DIM + 1;
   real u[NV];
-  real rho, v[DIM], p, c;
+  real rho, v[DIM], p, c, pp;
 };
 
+// pref, eref = pref / (gamma - 1): pressure offset; elo: low part of the compensated
+// energy (0 when the state is not compensated).  pp = (gamma - 1)((E - eref) + elo - ke/2),
+// E - eref exact near the reference (Sterbenz).
 template <typename real, int DIM, int NSP>
 __device__ __forceinline__ bool prim_from_cons(NodeState<real, DIM, NSP>& s, real gamma,
-                                               real p_ext, real c_ext) {
+                                               real p_ext, real c_ext, real pref = real(0),
+                                               real eref = real(0), real elo = real(0)) {
   real rho = 0;
 #pragma unroll
   for (int k = 0; k < NSP; ++k) rho += s.u[k];
@@ -135,10 +142,12 @@ __device__ __forceinline__ bool prim_from_cons(NodeState<real, DIM, NSP>& s, rea
     ke += s.u[NSP + d] * s.v[d];
   }
   if (NSP == 1) {
-    s.p = (gamma - real(1)) * (s.u[NSP + DIM] - real(0.5) * ke);
+    s.pp = (gamma - real(1)) * (((s.u[NSP + DIM] - eref) + elo) - real(0.5) * ke);
+    s.p = s.pp + pref;
     s.c = RealOps<real>::sqrt_(gamma * s.p * ir);
   } else {
     s.p = p_ext;
+    s.pp = p_ext - pref;
     s.c = c_ext;
   }
   return rho > real(0) && s.p > real(0) && isfinite(s.p);
@@ -153,7 +162,7 @@ __device__ __forceinline__ void phys_flux(const NodeState<real, DIM, NSP>& s, co
 #pragma unroll
   for (int k = 0; k < NSP; ++k) f[k] = s.u[k] * vn;
 #pragma unroll
-  for (int d = 0; d < DIM; ++d) f[NSP + d] = s.u[NSP + d] * vn + s.p * n[d];
+  for (int d = 0; d < DIM; ++d) f[NSP + d] = s.u[NSP + d] * vn + s.pp * n[d];
   f[NSP + DIM] = (s.u[NSP + DIM] + s.p) * vn;
 }
 
@@ -161,14 +170,15 @@ __device__ __forceinline__ void phys_flux(const NodeState<real, DIM, NSP>& s, co
 template <typename real, int DIM, int NSP>
 __device__ __forceinline__ void surface_flux(int sf, const NodeState<real, DIM, NSP>& L,
                                              const NodeState<real, DIM, NSP>& R, const real* n,
-                                             real inv_gm1, real* f);
+                                             real inv_gm1, real pref, real* f);
 
-// two-point volume flux F#(L, R; n)
+// two-point volume flux F#(L, R; n); pL, pR are shifted pressures p - pref (momentum
+// components), bL, bR = rho / p of the full pressures
 template <typename real, int DIM, int NSP>
 __device__ __forceinline__ void volume_flux(int vf, real rL, const real* vL, real pL, real bL,
                                             const real* uL, real rR, const real* vR, real pR,
                                             real bR, const real* uR, const real* n,
-                                            real inv_gm1, real* f) {
+                                            real inv_gm1, real pref, real* f) {
   constexpr int NV = NSP + DIM + 1;
   real vnL = 0, vnR = 0;
 #pragma unroll
@@ -187,7 +197,7 @@ __device__ __forceinline__ void volume_flux(int vf, real rL, const real* vL, rea
     f[0] = frho;
 #pragma unroll
     for (int d = 0; d < DIM; ++d) f[1 + d] = frho * real(0.5) * (vL[d] + vR[d]) + pa * n[d];
-    f[1 + DIM] = frho * (real(0.5) * vv + ib * inv_gm1) + real(0.5) * (pL * vnR + pR * vnL);
+    f[1 + DIM] = frho * (real(0.5) * vv + ib * inv_gm1) + real(0.5) * ((pL + pref) * vnR + (pR + pref) * vnL);
   } else if (vf == DG_VF_DUCROS) {
     real vn = real(0.5) * (vnL + vnR);
     real pa = real(0.5) * (pL + pR);
@@ -195,14 +205,14 @@ __device__ __forceinline__ void volume_flux(int vf, real rL, const real* vL, rea
     for (int k = 0; k < NSP; ++k) f[k] = real(0.5) * (uL[k] + uR[k]) * vn;
 #pragma unroll
     for (int d = 0; d < DIM; ++d) f[NSP + d] = real(0.5) * (uL[NSP + d] + uR[NSP + d]) * vn + pa * n[d];
-    f[NSP + DIM] = real(0.5) * (uL[NSP + DIM] + pL + uR[NSP + DIM] + pR) * vn;
+    f[NSP + DIM] = real(0.5) * (uL[NSP + DIM] + (pL + pref) + uR[NSP + DIM] + (pR + pref)) * vn;
   } else {  // central
 #pragma unroll
     for (int k = 0; k < NSP; ++k) f[k] = real(0.5) * (uL[k] * vnL + uR[k] * vnR);
 #pragma unroll
     for (int d = 0; d < DIM; ++d)
       f[NSP + d] = real(0.5) * (uL[NSP + d] * vnL + pL * n[d] + uR[NSP + d] * vnR + pR * n[d]);
-    f[NSP + DIM] = real(0.5) * ((uL[NSP + DIM] + pL) * vnL + (uR[NSP + DIM] + pR) * vnR);
+    f[NSP + DIM] = real(0.5) * ((uL[NSP + DIM] + (pL + pref)) * vnL + (uR[NSP + DIM] + (pR + pref)) * vnR);
   }
   (void)NV;
 }
@@ -210,12 +220,12 @@ __device__ __forceinline__ void volume_flux(int vf, real rL, const real* vL, rea
 template <typename real, int DIM, int NSP>
 __device__ __forceinline__ void surface_flux(int sf, const NodeState<real, DIM, NSP>& L,
                                              const NodeState<real, DIM, NSP>& R, const real* n,
-                                             real inv_gm1, real* f) {
+                                             real inv_gm1, real pref, real* f) {
   constexpr int NV = NSP + DIM + 1;
   if (sf == DG_SF_EC) {
     real bL = L.rho * RealOps<real>::rcp(L.p), bR = R.rho * RealOps<real>::rcp(R.p);
-    volume_flux<real, DIM, NSP>(NSP == 1 ? DG_VF_RANOCHA : DG_VF_DUCROS, L.rho, L.v, L.p, bL, L.u,
-                                R.rho, R.v, R.p, bR, R.u, n, inv_gm1, f);
+    volume_flux<real, DIM, NSP>(NSP == 1 ? DG_VF_RANOCHA : DG_VF_DUCROS, L.rho, L.v, L.pp, bL, L.u,
+                                R.rho, R.v, R.pp, bR, R.u, n, inv_gm1, pref, f);
     return;
   }
   real nn = 0, vnL = 0, vnR = 0;

@@ -30,6 +30,7 @@ __constant__ BasisTab<real> c_tab[DG_MAXN + 1];
 // conversion inside FP32 kernels).
 struct KConst {
   real gamma, gm1, inv_gm1, mu, kap, visc, rkA, rkB;
+  real pref, eref;  // pressure offset of the momentum fluxes and pref / (gamma - 1)
 };
 
 inline KConst make_kconst(const DgArgs& a) {
@@ -42,6 +43,8 @@ inline KConst make_kconst(const DgArgs& a) {
   k.visc = (real)a.visc_coef;
   k.rkA = (real)a.rkA;
   k.rkB = (real)a.rkB;
+  k.pref = (real)a.pref;
+  k.eref = (real)(a.pref / (a.gamma - 1.0));
   return k;
 }
 
@@ -156,18 +159,38 @@ __device__ __forceinline__ void stage_strided(real* dst, const real* src, int ne
   }
 }
 
+// stage one NP-block per element (source stride sstride reals between elements) into
+// dst[e][NP], 16-byte copies when aligned
+template <int NP>
+__device__ __forceinline__ void stage_rows(real* dst, const real* src, int sstride, int ne, int tid, int nth) {
+  constexpr int V = 16 / sizeof(real);
+  if (NP % V == 0 && (sstride % V) == 0 && (((uintptr_t)dst | (uintptr_t)src) & 15) == 0) {
+    constexpr int PER = NP / V;
+    for (int i = tid; i < ne * PER; i += nth) {
+      const int e = i / PER, r = i % PER;
+      cp_async16(dst + e * NP + r * V, src + (int64_t)e * sstride + r * V);
+    }
+  } else {
+    for (int i = tid; i < ne * NP; i += nth) {
+      const int e = i / NP, r = i % NP;
+      cp_async_small<sizeof(real)>(dst + e * NP + r, src + (int64_t)e * sstride + r);
+    }
+  }
+}
+
 // boundary / neighbour state at a face node.  Returns 1 when the face flux is the
 // physical flux of the returned state (supersonic inflow / outflow).  For an interior
 // face the neighbour's conserved state (and p, c for mixtures) arrives preloaded in nu/npc.
 template <int DIM, int NSP>
 __device__ __forceinline__ int outer_state(const DgArgs& a, const KConst& kc, int nb, const real* nu,
-                                           const real* npc, const NodeState<real, DIM, NSP>& own,
+                                           const real* npc, real nelo, const NodeState<real, DIM, NSP>& own,
                                            const real* n, NodeState<real, DIM, NSP>& x, bool& ok) {
   constexpr int NV = NSP + DIM + 1;
   if (nb >= 0) {
 #pragma unroll
     for (int k = 0; k < NV; ++k) x.u[k] = nu[k];
-    ok = prim_from_cons<real, DIM, NSP>(x, kc.gamma, NSP > 1 ? npc[0] : real(0), NSP > 1 ? npc[1] : real(0));
+    ok = prim_from_cons<real, DIM, NSP>(x, kc.gamma, NSP > 1 ? npc[0] : real(0), NSP > 1 ? npc[1] : real(0),
+                                        kc.pref, kc.eref, nelo);
     return 0;
   }
   int bc = -(nb + 1);
@@ -181,7 +204,7 @@ __device__ __forceinline__ int outer_state(const DgArgs& a, const KConst& kc, in
       pe = ((const real*)a.bc_pc)[bc * 2 + 0];
       ce = ((const real*)a.bc_pc)[bc * 2 + 1];
     }
-    ok = prim_from_cons<real, DIM, NSP>(x, kc.gamma, pe, ce);
+    ok = prim_from_cons<real, DIM, NSP>(x, kc.gamma, pe, ce, kc.pref, kc.eref);
     return 1;
   }
   x = own;
@@ -242,6 +265,10 @@ rhs_kernel(const DgArgs a, const KConst kc) {
     stage_strided<(NS ? L::NFV : 1), (NS ? L::SFV : NP), NP>(sfv, (const real*)a.gradW + e0 * L::NFV * NP, ne,
                                                              tid, nth);
   if (L::PREFETCH_DU && read_du) stage_strided<NV, L::SDU, NP>(sdu, (const real*)a.du + e0 * NV * NP, ne, tid, nth);
+  // low part of the compensated energy (FP32 state), in the accumulator region that the
+  // line phase fills later: [e][node], unswizzled
+  const bool have_elo = sizeof(real) == 4 && NSP == 1 && a.ulo != nullptr;
+  if (have_elo) stage_rows<NP>(sacc, (const real*)a.ulo + e0 * NV * NP + (NSP + DIM) * NP, NV * NP, ne, tid, nth);
   if (tid < EPB) {
     real al = 0;
     if (a.alpha_raw && tid < ne) {
@@ -288,15 +315,18 @@ rhs_kernel(const DgArgs a, const KConst kc) {
         q[(1 + d) * NP] = vv[d];
         ke += uu[(NSP + d) * NP] * vv[d];
       }
-      real p;
+      real p, pp;
       if (NSP == 1) {
-        p = kc.gm1 * (uu[(NSP + DIM) * NP] - real(0.5) * ke);
+        const real elo = have_elo ? sacc[e * NP + n] : real(0);
+        pp = kc.gm1 * (((uu[(NSP + DIM) * NP] - kc.eref) + elo) - real(0.5) * ke);
+        p = pp + kc.pref;
       } else {
         pcv[0] = spc[e * L::SPC + n];
         pcv[1] = spc[e * L::SPC + NP + n];
         p = pcv[0];
+        pp = p - kc.pref;
       }
-      q[(1 + DIM) * NP] = p;
+      q[(1 + DIM) * NP] = pp;  // shifted pressure
       q[(2 + DIM) * NP] = rho * RealOps<real>::rcp(p);
       if (!(rho > real(0) && p > real(0) && isfinite(p)))
         latch_status(a.status, DG_ST_NONPHYS, e0 + e);
@@ -398,7 +428,7 @@ rhs_kernel(const DgArgs a, const KConst kc) {
         }
         volume_flux<real, DIM, NSP>(vf, q[ni], vi, q[(1 + DIM) * NP + ni], q[(2 + DIM) * NP + ni], ui,
                                     q[nl], vl, q[(1 + DIM) * NP + nl], q[(2 + DIM) * NP + nl], ul,
-                                    nrm, kc.inv_gm1, F);
+                                    nrm, kc.inv_gm1, kc.pref, F);
         const real cil = wdg * B.D2[i * N1 + l], cli = wdg * B.D2[l * N1 + i];
 #pragma unroll
         for (int k = 0; k < NV; ++k) {
@@ -436,8 +466,10 @@ rhs_kernel(const DgArgs a, const KConst kc) {
           Lq.v[c] = q[(1 + c) * NP + nl];
           Rq.v[c] = q[(1 + c) * NP + nr];
         }
-        Lq.p = q[(1 + DIM) * NP + nl];
-        Rq.p = q[(1 + DIM) * NP + nr];
+        Lq.pp = q[(1 + DIM) * NP + nl];
+        Rq.pp = q[(1 + DIM) * NP + nr];
+        Lq.p = Lq.pp + kc.pref;
+        Rq.p = Rq.pp + kc.pref;
         if (NSP == 1) {
           Lq.c = RealOps<real>::sqrt_(kc.gamma * Lq.p * RealOps<real>::rcp(Lq.rho));
           Rq.c = RealOps<real>::sqrt_(kc.gamma * Rq.p * RealOps<real>::rcp(Rq.rho));
@@ -446,7 +478,7 @@ rhs_kernel(const DgArgs a, const KConst kc) {
           Rq.c = spc[e * L::SPC + NP + nr];
         }
         real F[NV];
-        surface_flux<real, DIM, NSP>(sf == DG_SF_EC ? DG_SF_LLF : sf, Lq, Rq, nh, kc.inv_gm1, F);
+        surface_flux<real, DIM, NSP>(sf == DG_SF_EC ? DG_SF_LLF : sf, Lq, Rq, nh, kc.inv_gm1, kc.pref, F);
 #pragma unroll
         for (int k = 0; k < NV; ++k) {
           acc[j - 1][k] += al * B.iw[j - 1] * F[k];
@@ -493,7 +525,7 @@ rhs_kernel(const DgArgs a, const KConst kc) {
       m = t % S::LPD;
     }
   };
-  real nbu[FIT][NV], nbpc[FIT][2], nbg[FIT][NG];
+  real nbu[FIT][NV], nbpc[FIT][2], nbg[FIT][NG], nbe[FIT];
 #pragma unroll
   for (int it = 0; it < FIT; ++it) {
     int e, f, m;
@@ -502,10 +534,12 @@ rhs_kernel(const DgArgs a, const KConst kc) {
       const int d = f >> 1, side = f & 1;
       const int nnode = S::line_base(d, m) + (side ? 0 : N) * S::stride(d);
       const int nb = a.nbr[(e0 + e) * 2 * DIM + f];
+      nbe[it] = real(0);
       if (nb >= 0) {
         const real* gu = (const real*)a.u + (int64_t)nb * NV * NP + nnode;
 #pragma unroll
         for (int k = 0; k < NV; ++k) nbu[it][k] = gu[k * NP];
+        if (have_elo) nbe[it] = ((const real*)a.ulo)[(int64_t)nb * NV * NP + (NSP + DIM) * NP + nnode];
         if (NSP > 1) {
           const real* pc = (const real*)a.pc + (int64_t)nb * 2 * NP + nnode;
           nbpc[it][0] = pc[0];
@@ -539,7 +573,8 @@ rhs_kernel(const DgArgs a, const KConst kc) {
     o.rho = q[node];
 #pragma unroll
     for (int c = 0; c < DIM; ++c) o.v[c] = q[(1 + c) * NP + node];
-    o.p = q[(1 + DIM) * NP + node];
+    o.pp = q[(1 + DIM) * NP + node];
+    o.p = o.pp + kc.pref;
     o.c = NSP == 1 ? RealOps<real>::sqrt_(kc.gamma * o.p * RealOps<real>::rcp(o.rho))
                    : spc[e * L::SPC + NP + node];
     real nface[DIM];
@@ -549,11 +584,11 @@ rhs_kernel(const DgArgs a, const KConst kc) {
     NodeState<real, DIM, NSP> x;
     bool ok = true;
     real Fs[NV];
-    int phys = outer_state<DIM, NSP>(a, kc, nb, nbu[it], nbpc[it], o, nface, x, ok);
+    int phys = outer_state<DIM, NSP>(a, kc, nb, nbu[it], nbpc[it], nbe[it], o, nface, x, ok);
     if (!ok) latch_status(a.status, DG_ST_NONPHYS, nb >= 0 ? nb : eg);
     if (phys) phys_flux<real, DIM, NSP>(x, nface, Fs);
-    else if (side) surface_flux<real, DIM, NSP>(sf, o, x, nface, kc.inv_gm1, Fs);
-    else surface_flux<real, DIM, NSP>(sf, x, o, nface, kc.inv_gm1, Fs);
+    else if (side) surface_flux<real, DIM, NSP>(sf, o, x, nface, kc.inv_gm1, kc.pref, Fs);
+    else surface_flux<real, DIM, NSP>(sf, x, o, nface, kc.inv_gm1, kc.pref, Fs);
 #pragma unroll
     for (int k = 0; k < NV; ++k) sa[k * NP] += iw * Fs[k];
     if (NS) {

@@ -17,6 +17,11 @@ def tgv(xi, n_el, warp=0.0, mach=0.1, shape=None):
     return xyz, nbr, face, W.tgv_primitive(xyz, GAMMA, mach)
 
 
+def tgv_p0(mach=0.1):
+    """Mean pressure of the Taylor-Green state, p0 = 1 / (gamma Ma^2)."""
+    return 1.0 / (GAMMA * mach * mach)
+
+
 def vortex(xi, n_el, t=0.0):
     xyz, nbr, face = W.box_mesh((n_el, n_el), xi, (-5.0, -5.0), (5.0, 5.0), periodic=True)
     return xyz, nbr, face, W.vortex_primitive(xyz, t=t, gamma=GAMMA)
@@ -75,6 +80,7 @@ class Pair:
         self.mesh_g = builder(xg)
         okw = dict(kw)
         gkw = dict(kw)
+        okw.pop("p_ref", None)  # an offset the oracle does not need (exact in arithmetic)
         for k in ("equations", "volume_flux", "surface_flux"):
             pass
         self.orc = oracle.Oracle(dim, N, *self.mesh_o[:3], **okw)

@@ -28,7 +28,7 @@ def _gpu_history(dg, N, n_el, precision, steps, every, dt, final_state=False):
     x, _ = dg.dg_lgl_nodes(N)
     xyz, nbr, face, w = cases.tgv(x, n_el, warp=0.1)
     s = dg.Solver(3, N, xyz, nbr, face, equations=dg.DG_NAVIER_STOKES, mu=MU, Pr=0.72,
-                  precision=precision)
+                  precision=precision, p_ref=cases.tgv_p0())
     try:
         s.set_primitive(w)
         h = [s.diagnostics()[:2]]

@@ -49,6 +49,11 @@ def _rhs_pair(dg, pair, w_o, w_g):
 RHS_CASES = {
     "tgv_euler_4^3_N3": dict(builder=_tgv_builder(4, warp=0.0), dim=3, N=3, kw={}),
     "tgv_warped_ragged_N3_llf": dict(builder=_tgv_builder(shape=(3, 3, 5)), dim=3, N=3, kw={}),
+    # pressure offset of the momentum fluxes (exact in arithmetic): same bars
+    "tgv_warped_ragged_N3_pref": dict(builder=_tgv_builder(shape=(3, 3, 5)), dim=3, N=3,
+                                      kw=dict(p_ref=cases.tgv_p0())),
+    "tgv_warped_ragged_N3_hllc_pref": dict(builder=_tgv_builder(shape=(3, 3, 5)), dim=3, N=3,
+                                           kw=dict(surface_flux=1, p_ref=cases.tgv_p0())),
     "tgv_warped_ragged_N3_hllc": dict(builder=_tgv_builder(shape=(3, 3, 5)), dim=3, N=3,
                                       kw=dict(surface_flux=1)),
     "tgv_warped_ragged_N3_ec": dict(builder=_tgv_builder(shape=(3, 3, 5)), dim=3, N=3,
@@ -59,6 +64,8 @@ RHS_CASES = {
     "tgv_warped_N7": dict(builder=_tgv_builder(shape=(2, 2, 3)), dim=3, N=7, kw={}),
     "tgv_ns_warped_N3": dict(builder=_tgv_builder(shape=(3, 3, 5)), dim=3, N=3,
                              kw=dict(equations=1, mu=0.01, Pr=0.72)),
+    "tgv_ns_warped_N3_pref": dict(builder=_tgv_builder(shape=(3, 3, 5)), dim=3, N=3,
+                                  kw=dict(equations=1, mu=0.01, Pr=0.72, p_ref=cases.tgv_p0())),
     "tgv_ns_warped_N7": dict(builder=_tgv_builder(shape=(2, 2, 3)), dim=3, N=7,
                              kw=dict(equations=1, mu=0.01, Pr=0.72)),
     "vortex_2d_N3": dict(builder=lambda x: cases.vortex(x, 5), dim=2, N=3, kw={}),
