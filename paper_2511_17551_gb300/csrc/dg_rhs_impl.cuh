@@ -611,9 +611,27 @@ rhs_kernel(const DgArgs a, const KConst kc) {
   }
   __syncthreads();
 
-  // ---- phase C: one thread per node
+  // ---- phase C: one thread per node.  The compensation parts of all of a thread's
+  // nodes are loaded first (one memory round trip).
   real lam_a = 0, lam_v = 0;
-  for (int i = tid; i < ne * NP; i += nth) {
+  constexpr int CIT = (EPB * NP + L::THREADS - 1) / L::THREADS;
+  const bool comp = sizeof(real) == 4 && a.mode == 1 && a.ulo != nullptr;
+  real lo_r[CIT][NV];
+  if (comp) {
+#pragma unroll
+    for (int it = 0; it < CIT; ++it) {
+      const int i = tid + it * L::THREADS;
+      if (i < ne * NP) {
+        const real* lp = (const real*)a.ulo + (e0 + i / NP) * NV * NP + i % NP;
+#pragma unroll
+        for (int k = 0; k < NV; ++k) lo_r[it][k] = lp[k * NP];
+      }
+    }
+  }
+#pragma unroll
+  for (int it = 0; it < CIT; ++it) {
+    const int i = tid + it * L::THREADS;
+    if (i >= ne * NP) break;
     const int e = i / NP, node = i % NP, pn = SW(node);
     const real ij = sij[e * L::SIJ + node];
     const real* sa = sacc + e * L::SACC + pn;
@@ -646,14 +664,13 @@ rhs_kernel(const DgArgs a, const KConst kc) {
         real dn = kc.rkA * dold + dt * r;
         du[gbase + k * NP] = dn;
         const real hi = su[e * L::SU + k * NP + node];
-        if (sizeof(real) == 4 && a.ulo) {
+        if (comp) {
           // compensated FP32 state: (hi, lo) += B dn by an exact TwoSum (Knuth), so the
           // rounding of every stage update is carried instead of lost
-          real* lo = (real*)a.ulo + gbase + k * NP;
-          const real inc = *lo + kc.rkB * dn;
+          const real inc = lo_r[it][k] + kc.rkB * dn;
           const real s2 = hi + inc;
           const real bb = s2 - hi;
-          *lo = (hi - (s2 - bb)) + (inc - bb);
+          ((real*)a.ulo)[gbase + k * NP] = (hi - (s2 - bb)) + (inc - bb);
           un[k] = s2;
         } else {
           un[k] = hi + kc.rkB * dn;
