@@ -335,7 +335,9 @@ def run_mixture(args, stream_ptr, world):
     dg.dg_profile(s.ctx, 0)
     out["thermo_gain"] = {"cold_newton_ms": cold, "converged_cache_newton_ms": warm,
                           "surrogate_ms": mlp, "accepted": acc, "fallback": fb,
-                          "max_rel_T_diff_vs_newton": float(np.abs(T_mlp / T_cold - 1).max())}
+                          "max_rel_T_diff_vs_newton": float(np.abs(T_mlp / T_cold - 1).max()),
+                          "median_rel_T_diff_vs_newton": float(np.median(np.abs(T_mlp / T_cold - 1))),
+                          "nodes_differing_from_newton": int((T_mlp != T_cold).sum())}
     wall, prof, dev_ms = timed(s, steps)
     acc, fb = dg.dg_surrogate_stats(s.ctx)
     out["mixed_surrogate"] = {"value": world * dof * 5 * steps / wall, "ms_per_step": wall * 1e3 / steps,
