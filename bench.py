@@ -43,6 +43,9 @@ WORDS_GRAD = 5 + 9 + 1 + 12
 # dram__bytes_read.sum + dram__bytes_write.sum of the current mixed-form NS N=3 rhs_kernel
 # per node, from one ncu capture of the 24^3 case (traffic scales with the node count)
 RHS_DRAM_B_PER_NODE = 161.3
+# FP64 flops per node of the FP64-form NS N=3 rhs_kernel (2 DFMA + DMUL + DADD thread
+# instructions, one ncu capture of the 16^3 case): its roofline is the FP64 pipe
+RHS_FP64_FLOPS_PER_NODE = 1246.3
 
 
 def job_rate(ms_local, units_local, world, device="cpu"):
@@ -193,6 +196,10 @@ def run_ours(args, rank, world, local_rank):
 
     # roofline of the dominant kernel (main RHS / RK-stage kernel of the mixed form)
     peak, peak_kind = _peaks()
+    fp64_peak = dg.dg_peak_flops(dg.DG_FP64, 4000)
+    fp32_peak = dg.dg_peak_flops(dg.DG_MIXED, 20000)
+    rhs64_ms = prof64["rhs"][0] / max(1, prof64["rhs"][1])
+    fp64_achieved = RHS_FP64_FLOPS_PER_NODE * K * npn / (rhs64_ms * 1e-3) / 1e12
     rhs_ms, rhs_n = prof["rhs"]
     words = WORDS_MAIN_NS if eq == dg.DG_NAVIER_STOKES else WORDS_MAIN_EULER
     bytes_launch = words * 4 * K * npn
@@ -208,7 +215,11 @@ def run_ours(args, rank, world, local_rank):
                    "l2_flush": "working set %.0f MB > L2 (129 MB)" % (
                        (words + WORDS_GRAD) * 4 * K * npn / 1e6)},
         "fp64_form": {"value": value64, "ms_per_step": ms64 / k64, "steps": k64,
-                      "rhs_kernel_ms": prof64["rhs"][0] / max(1, prof64["rhs"][1])},
+                      "rhs_kernel_ms": rhs64_ms,
+                      "roofline": {"bound": "alu", "achieved": fp64_achieved, "peak": fp64_peak,
+                                   "unit": "TFLOP/s", "frac": fp64_achieved / fp64_peak,
+                                   "flops_per_node": RHS_FP64_FLOPS_PER_NODE,
+                                   "peak_source": "FP64 FMA chains measured here (dg_peak_flops)"}},
         "e2e": {"value": e2e_value, "unit": "DOF*RHS/s", "h2d_bytes_per_step": dof * 8,
                 "d2h_bytes_per_step": dof * 8},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -222,8 +233,7 @@ def run_ours(args, rank, world, local_rank):
         "gpu_launches": launches,
         "clocks": clk,
     }
-    out["arith_peaks_tflops"] = {"fp64_fma": dg.dg_peak_flops(dg.DG_FP64, 4000),
-                                 "fp32_fma": dg.dg_peak_flops(dg.DG_MIXED, 20000),
+    out["arith_peaks_tflops"] = {"fp64_fma": fp64_peak, "fp32_fma": fp32_peak,
                                  "source": "measured here, FMA chains, 152x8 CTAs"}
     if not args.no_mixture:
         out["mixture"] = run_mixture(args, stream.cuda_stream, world)
@@ -497,6 +507,40 @@ def run_reference(args, rank, world):
     }))
 
 
+def run_profile_case(name):
+    """Small cases for ncu section captures (2 RK steps, then exit): 'fp64rhs' (NS TGV 16^3,
+    N = 3, FP64 form), 'mixture' (5-species O-grid 16^3, N = 4, mixed), 'reacting'
+    (reacting O-grid 24 x 24 x 8, N = 4, mixed)."""
+    import torch
+    import paper_2511_17551_gb300 as dg
+    if name == "fp64rhs":
+        N = 3
+        xi, _ = dg.dg_lgl_nodes(N)
+        xyz, nbr, face = W.box_mesh((16,) * 3, xi, (-np.pi,) * 3, (np.pi,) * 3, periodic=True, warp=0.1)
+        s = dg.Solver(3, N, xyz, nbr, face, equations=dg.DG_NAVIER_STOKES, mu=1.0 / 1600.0, Pr=0.72,
+                      precision=dg.DG_FP64, p_ref=1.0 / (1.4 * 0.01))
+        s.set_primitive(W.tgv_primitive(xyz))
+        s.step(2, 0.5)
+    else:
+        N = 4
+        xi, _ = dg.dg_lgl_nodes(N)
+        react = name == "reacting"
+        xyz, nbr, face = W.ogrid_mesh(xi, *((24, 24, 8) if react else (16, 16, 16)))
+        vel = (2400.0 if react else 2000.0, 0.0, 0.0)
+        hot = (1.2, 3000.0) if react else None
+        w0 = W.mixture_primitive(xyz, rho=0.1, vel=vel, T=300.0, seed=7, cylinder=0.5, hot=hot)
+        fs = W.mixture_primitive(xyz[:1], rho=0.1, vel=vel, T=300.0, seed=7)[0, :, 0]
+        s = dg.Solver(3, N, xyz, nbr, face, n_species=5, species=W.species_table(),
+                      volume_flux=dg.DG_VF_DUCROS, surface_flux=dg.DG_SF_LLF, bc_kind=[1, 2, 3],
+                      bc_prim=np.stack([fs] * 3), alpha_max=0.5, precision=dg.DG_MIXED,
+                      reactions=W.reaction_table() if react else None)
+        s.set_primitive(w0)
+        s.step(2, 0.05 if react else 0.3)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_case": name, "nodes": s.K * s.np}))
+    s.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -514,8 +558,13 @@ def main():
     ap.add_argument("--no-reacting", action="store_true")
     ap.add_argument("--react-elements", type=int, default=48, help="O-grid radial/angular elements")
     ap.add_argument("--react-steps", type=int, default=4)
+    ap.add_argument("--profile-case", choices=["fp64rhs", "mixture", "reacting"],
+                    help="run one small case for an ncu capture and exit")
     args = ap.parse_args()
     rank, world, local_rank = _env_rank()
+    if args.profile_case:
+        run_profile_case(args.profile_case)
+        return
     if args.impl == "reference":
         run_reference(args, rank, world)
     else:
