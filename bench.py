@@ -216,7 +216,8 @@ def run_ours(args, rank, world, local_rank):
                        (words + WORDS_GRAD) * 4 * K * npn / 1e6)},
         "fp64_form": {"value": value64, "ms_per_step": ms64 / k64, "steps": k64,
                       "rhs_kernel_ms": rhs64_ms,
-                      "roofline": {"bound": "alu", "achieved": fp64_achieved, "peak": fp64_peak,
+                      "roofline": None if not (eq == dg.DG_NAVIER_STOKES and N == 3) else
+                                  {"bound": "alu", "achieved": fp64_achieved, "peak": fp64_peak,
                                    "unit": "TFLOP/s", "frac": fp64_achieved / fp64_peak,
                                    "flops_per_node": RHS_FP64_FLOPS_PER_NODE,
                                    "peak_source": "FP64 FMA chains measured here (dg_peak_flops)"}},
@@ -239,6 +240,8 @@ def run_ours(args, rank, world, local_rank):
         out["mixture"] = run_mixture(args, stream.cuda_stream, world)
     if not args.no_reacting:
         out["reacting"] = run_reacting(args, stream.cuda_stream, world)
+    if not args.no_other_shapes:
+        out.update(run_other_shapes(args, stream.cuda_stream, world))
     if rank == 0:
         if not args.no_cpu_baseline:
             out["cpu_baseline"], r_oracle, u_oracle, n_or, dt_or = cpu_baseline(cfg, args.cpu_seconds)
@@ -435,6 +438,67 @@ def run_reacting(args, stream_ptr, world):
     return out
 
 
+def run_other_shapes(args, stream_ptr, world):
+    """The other full-size shapes: NS Taylor-Green 16^3 at N = 7 (same DOF as the headline)
+    and the 2D Mach-3 square cylinder (512 x 256 quads less the body, N = 3, shock capturing
+    with alpha <= 0.5), both forms; DOF*RHS-evals/s and per-kernel device time per step."""
+    import torch
+    import paper_2511_17551_gb300 as dg
+    out = {}
+
+    def timed(s, n, cfl):
+        s.step(2, cfl)
+        dg.dg_profile(s.ctx, 1)
+        dg.dg_profile_read(s.ctx)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s.step(n, cfl)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        prof = dg.dg_profile_read(s.ctx)
+        dg.dg_profile(s.ctx, 0)
+        return wall, {k: round(v[0] / n, 4) for k, v in prof.items() if v[1]}
+
+    # NS TGV 16^3, N = 7
+    cfg = CONFIGS["tgv_ns_16^3_N7"]
+    xi, _ = dg.dg_lgl_nodes(cfg["N"])
+    xyz, nbr, face, w0 = build_workload(cfg, xi)
+    dof = xyz.shape[0] * (cfg["N"] + 1) ** 3 * 5
+    blk = {"workload": "tgv_ns_16^3_N7", "dof": dof}
+    for name, prec, n in (("mixed", dg.DG_MIXED, 50), ("fp64", dg.DG_FP64, 3)):
+        s = dg.Solver(3, cfg["N"], xyz, nbr, face, equations=dg.DG_NAVIER_STOKES, mu=cfg["mu"],
+                      Pr=0.72, precision=prec, stream=stream_ptr, p_ref=1.0 / (1.4 * 0.01))
+        s.set_primitive(w0)
+        wall, per = timed(s, n, 0.5)
+        s.close()
+        blk[name] = {"value": world * dof * 5 * n / wall, "ms_per_step": wall * 1e3 / n, "steps": n,
+                     "device_ms_per_step_by_kernel": per}
+    out["tgv_ns_16^3_N7"] = blk
+    # 2D Mach-3 square cylinder
+    xi, _ = dg.dg_lgl_nodes(3)
+    xyz, nbr, face = W.square_cylinder_mesh(xi)
+    gamma, mach = 1.4, 3.0
+    fs = np.array([1.0, 1.0, 0.0, 1.0 / (gamma * mach * mach)])
+    w0 = W.freestream_primitive(xyz.shape[0], 16, fs)
+    dof = xyz.shape[0] * 16 * 4
+    blk = {"workload": "square_cylinder_mach3_512x256_N3", "elements": xyz.shape[0], "dof": dof,
+           "alpha_max": 0.5, "cfl": 0.3}
+    for name, prec, n in (("mixed", dg.DG_MIXED, 40), ("fp64", dg.DG_FP64, 10)):
+        s = dg.Solver(2, 3, xyz, nbr, face, bc_kind=[1, 2, 3], bc_prim=np.stack([fs] * 3),
+                      alpha_max=0.5, precision=prec, stream=stream_ptr)
+        s.set_primitive(w0)
+        try:
+            wall, per = timed(s, n, 0.3)
+            blk[name] = {"value": world * dof * 5 * n / wall, "ms_per_step": wall * 1e3 / n, "steps": n,
+                         "blended_elements": int((dg.dg_get_alpha(s.ctx, s.K) > 0).sum()),
+                         "device_ms_per_step_by_kernel": per}
+        except dg.DgError as e:
+            blk[name] = {"error": str(e)}
+        s.close()
+    out["square_cylinder"] = blk
+    return out
+
+
 def cpu_baseline(cfg, budget_s):
     """The oracle as it stands, FP64, all host cores (OpenMP over elements): CK45 steps of
     the workload at a fixed step (the oracle's CFL-0.5 step of the initial state) for about
@@ -556,6 +620,8 @@ def main():
     ap.add_argument("--train-samples", type=int, default=1000000)
     ap.add_argument("--train-epochs", type=int, default=20)
     ap.add_argument("--no-reacting", action="store_true")
+    ap.add_argument("--no-other-shapes", action="store_true",
+                    help="skip the 16^3 N=7 Taylor-Green and the square-cylinder blocks")
     ap.add_argument("--react-elements", type=int, default=48, help="O-grid radial/angular elements")
     ap.add_argument("--react-steps", type=int, default=4)
     ap.add_argument("--profile-case", choices=["fp64rhs", "mixture", "reacting"],
