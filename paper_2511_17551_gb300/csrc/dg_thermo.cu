@@ -94,19 +94,24 @@ __global__ void thermo_update_kernel(const T* u, int64_t K, int np, int dim, con
     }
     const double ir = 1.0 / rho;
     const double e = (double)uu[(NSPEC + dim) * np] * ir - 0.5 * ke * ir * ir;
-#pragma unroll
-    for (int s = 0; s < NSPEC; ++s) Y[s] *= ir;
     double Tk = Tc[k * np + node];
     if (!(Tk >= 200.0 && Tk <= 1e4)) Tk = 1000.0;
     Poly<double> P;
-    build_poly<double>(cf, Y, P);
     if (mixed) {
+      // FP32 mixture polynomial for the Newton iteration; in FP64 only the large constant
+      // b0 (formation energies), from density-weighted sums
       Poly<float> Pf;
       float Yf[NSPEC];
+      double b0 = 0.0;
+      const float irf = (float)ir;
 #pragma unroll
-      for (int s = 0; s < NSPEC; ++s) Yf[s] = (float)Y[s];
+      for (int s = 0; s < NSPEC; ++s) {
+        Yf[s] = (float)Y[s] * irf;
+        b0 += Y[s] * cf[8 * s];
+      }
+      b0 *= ir;
       build_poly<float>(cf32, Yf, Pf);
-      const float er = (float)(e - P.b[0]);
+      const float er = (float)(e - b0);
       float Tf = (float)Tk;
       bool conv = false;
       for (int it = 0; it < 12; ++it) {
@@ -118,12 +123,21 @@ __global__ void thermo_update_kernel(const T* u, int64_t K, int np, int dim, con
           break;
         }
       }
-      // the FP64 final residual: one Newton correction on e64(T) - e (cv in FP32 is
-      // accurate enough for a correction of relative size <= 1e-6); further FP64
-      // iterations only when the FP32 stage did not converge
+      // the FP64 final residual: one Newton correction on e64(T) - e, evaluated in FP64
+      // with the FP64 constant b0 and the FP32-rounded temperature coefficients (their
+      // rounding moves e by ~1e-7 relative, i.e. T by ~1e-4 K); cv in FP32 only scales the
+      // correction.  The full FP64 iteration runs only where the FP32 stage did not converge.
       double T64 = (double)Tf;
-      T64 = clampT(T64 - (P.e(T64) - e) / (double)Pf.cv(Tf));
-      bool ok = rho > 0.0 && (conv || newton64(P, e, T64));
+      const double r = (b0 + T64 * ((double)Pf.b[1] + T64 * ((double)Pf.b[2] + T64 * ((double)Pf.b[3] +
+                        T64 * ((double)Pf.b[4] + T64 * (double)Pf.b[5]))))) - e;
+      T64 = clampT(T64 - r * (double)(1.0f / Pf.cv(Tf)));
+      bool ok = rho > 0.0;
+      if (ok && !conv) {
+#pragma unroll
+        for (int s = 0; s < NSPEC; ++s) Y[s] *= ir;
+        build_poly<double>(cf, Y, P);
+        ok = newton64(P, e, T64);
+      }
       if (!ok) latch(status, DG_ST_NEWTON, k);
       Tc[k * np + node] = T64;
       const float Tq = (float)T64, rhof = (float)rho;
@@ -132,6 +146,9 @@ __global__ void thermo_update_kernel(const T* u, int64_t K, int np, int dim, con
       pc[(k * 2 + 1) * np + node] = (T)sqrtf((cvf + Pf.Rmix) / cvf * pf / rhof);
       continue;
     }
+#pragma unroll
+    for (int s = 0; s < NSPEC; ++s) Y[s] *= ir;
+    build_poly<double>(cf, Y, P);
     const bool ok = rho > 0.0 && newton64(P, e, Tk);
     if (!ok) latch(status, DG_ST_NEWTON, k);
     Tc[k * np + node] = Tk;
