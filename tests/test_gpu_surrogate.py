@@ -128,8 +128,9 @@ def test_surrogate_temperature_accuracy_and_fallback(env, trained):
         T_o = o.temperature(o.prim_to_cons(cases.mixture_perturbed(w_o, 5)))
         assert np.abs(T_s / T_o - 1).max() < 1e-4
         assert acc + fb == s.K * s.np and acc > 0.25 * (acc + fb)
-        # wrong weights: every node falls back, and the result equals the plain Newton solve
-        # of the same (FP32-stored) state
+        # wrong weights: every node falls back; the fallback's full FP64 Newton solve and the
+        # mixed form's plain solve (FP32 Newton, FP64 residual with FP32-rounded temperature
+        # coefficients: about 2e-7 relative) agree within the latter's accuracy
         dg.dg_set_surrogate(s.ctx, None)
         T_plain = dg.dg_get_temperature(s.ctx, (s.K, s.np))
         bad = params.copy()
@@ -138,7 +139,7 @@ def test_surrogate_temperature_accuracy_and_fallback(env, trained):
         T_b = dg.dg_get_temperature(s.ctx, (s.K, s.np))
         acc, fb = dg.dg_surrogate_stats(s.ctx)
         assert acc == 0 and fb == s.K * s.np
-        assert np.abs(T_b / T_plain - 1).max() < 1e-12
+        assert np.abs(T_b / T_plain - 1).max() < 1e-6
     finally:
         s.close()
 
