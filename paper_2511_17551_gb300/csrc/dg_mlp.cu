@@ -65,8 +65,8 @@ __device__ __forceinline__ double clampT(double T) { return T < 200.0 ? 200.0 : 
 
 template <typename T>
 __global__ void __launch_bounds__(32 * MLP_WARPS)
-thermo_mlp_kernel(const T* u, int64_t K, int np, int dim, const double* sp, double* Tc, T* pc,
-                  unsigned long long* status, const DgMlpDev* mlp, unsigned long long* stats) {
+thermo_mlp_kernel(const T* u, int64_t K, int np, int dim, const double* sp, const float* sp32, double* Tc,
+                  T* pc, unsigned long long* status, const DgMlpDev* mlp, unsigned long long* stats) {
   __shared__ DgMlpDev m;
   __shared__ float feat[MLP_WARPS][32][17];
   __shared__ float yv[MLP_WARPS][2][1][16];
@@ -122,7 +122,58 @@ thermo_mlp_kernel(const T* u, int64_t K, int np, int dim, const double* sp, doub
     mlp16<1>(m.w, feat[w], yv[w][0]);
     mlp16<1>(m.w, feat[w] + 16, yv[w][1]);
     __syncwarp();
-    if (mine) {
+    if (mine && sizeof(T) == 4) {
+      // mixed form: the same equation as its plain solve -- FP64 formation-energy constant
+      // b0, FP32-rounded temperature coefficients, FP64 residual -- so accepted nodes and
+      // the plain path agree to the acceptance tolerance
+      const double T0 = clampT((double)(m.muT + m.sigT * yv[w][lane >> 4][0][lane & 15]));
+      float c32[6], R32 = 0.f;
+      double b0 = 0.0;
+#pragma unroll
+      for (int q = 0; q < 6; ++q) c32[q] = 0.f;
+#pragma unroll
+      for (int s = 0; s < NSPEC; ++s) {
+        b0 += Y[s] * sp[8 * s];
+        const float yf = (float)Y[s];
+#pragma unroll
+        for (int q = 1; q < 6; ++q) c32[q] += yf * sp32[8 * s + q];
+        R32 += yf * sp32[8 * s + 6];
+      }
+      auto e64 = [&](double t) {
+        return b0 + t * ((double)c32[1] + t * ((double)c32[2] + t * ((double)c32[3] +
+                         t * ((double)c32[4] + t * (double)c32[5]))));
+      };
+      auto cv32 = [&](float t) {
+        return c32[1] + t * (2.f * c32[2] + t * (3.f * c32[3] + t * (4.f * c32[4] + t * 5.f * c32[5])));
+      };
+      const float cv0 = cv32((float)T0);
+      double T1 = clampT(T0 - (e64(T0) - e) * (double)(1.0f / cv0));
+      const double r1 = e64(T1) - e;
+      if (fabs(r1) <= 1e-6 * (double)cv0 * T1) {
+        ++n_ok;
+      } else {
+        // fallback: the plain FP64 Newton iteration from the polished value
+        ++n_fb;
+        PolyD P;
+        poly_d(sp, Y, P);
+        bool conv = false;
+        for (int it = 0; it < 50; ++it) {
+          const double Tn = clampT(T1 - (P.e(T1) - e) / P.cv(T1));
+          const double step = fabs(Tn - T1);
+          T1 = Tn;
+          if (step <= 1e-12 * T1) {
+            conv = true;
+            break;
+          }
+        }
+        if (!conv) atomicCAS(status, 0ull, (DG_ST_NEWTON << 56) | (unsigned long long)k);
+      }
+      Tc[k * np + node] = T1;
+      const float Tq = (float)T1, rhof = (float)rho;
+      const float pf = rhof * R32 * Tq, cvf = cv32(Tq);
+      pc[(k * 2 + 0) * np + node] = (T)pf;
+      pc[(k * 2 + 1) * np + node] = (T)sqrtf((cvf + R32) / cvf * pf / rhof);
+    } else if (mine) {
       PolyD P;
       poly_d(sp, Y, P);
       double T0 = clampT((double)(m.muT + m.sigT * yv[w][lane >> 4][0][lane & 15]));
@@ -429,10 +480,10 @@ cudaError_t dg_mlp_thermo_update(DgThermo* th, const void* u, int f32, cudaStrea
   const unsigned grid = grid_of((n + 31) / 32, MLP_WARPS);
   if (f32)
     thermo_mlp_kernel<float><<<grid, 32 * MLP_WARPS, 0, s>>>((const float*)u, th->K, th->np, th->dim,
-        th->species, th->T, (float*)th->pc, th->status, (const DgMlpDev*)th->mlp, th->mlp_stats);
+        th->species, th->coef32, th->T, (float*)th->pc, th->status, (const DgMlpDev*)th->mlp, th->mlp_stats);
   else
     thermo_mlp_kernel<double><<<grid, 32 * MLP_WARPS, 0, s>>>((const double*)u, th->K, th->np, th->dim,
-        th->species, th->T, (double*)th->pc, th->status, (const DgMlpDev*)th->mlp, th->mlp_stats);
+        th->species, th->coef32, th->T, (double*)th->pc, th->status, (const DgMlpDev*)th->mlp, th->mlp_stats);
   return cudaGetLastError();
 }
 
