@@ -67,6 +67,12 @@ __device__ __forceinline__ real ln_mean(real x, real y) {
   real rs = RealOps<real>::rcp(s);
   real f = d * rs, f2 = f * f;
   if (f2 < RealOps<real>::ln_eps) {
+    if (sizeof(real) == 8) {
+      // L = (s/2) / (1 + x), x = f2 (1/3 + f2 (1/5 + f2/7)) <= 3.4e-5: the geometric series
+      // to x^3 is exact to FP64 rounding (x^4 < 2e-18) and needs no second reciprocal
+      const real x = f2 * (real(1.0 / 3.0) + f2 * (real(1.0 / 5.0) + f2 * real(1.0 / 7.0)));
+      return real(0.5) * s * (real(1) - x * (real(1) - x * (real(1) - x)));
+    }
     real poly = real(2) + f2 * (real(2.0 / 3.0) + f2 * (real(2.0 / 5.0) + f2 * real(2.0 / 7.0)));
     return s * RealOps<real>::rcp(poly);
   }
