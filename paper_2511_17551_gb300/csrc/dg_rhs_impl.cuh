@@ -48,10 +48,10 @@ inline KConst make_kconst(const DgArgs& a) {
   return k;
 }
 
-// elements per CTA: the largest count whose line threads fit in 192 threads
-template <int DIM, int N>
+// elements per CTA: the largest count whose line threads fit in TPB threads
+template <int DIM, int N, int TPB = 192>
 constexpr int epb() {
-  return Shape<DIM, N>::LINES >= 192 ? 1 : (192 / Shape<DIM, N>::LINES > 24 ? 24 : 192 / Shape<DIM, N>::LINES);
+  return Shape<DIM, N>::LINES >= TPB ? 1 : (TPB / Shape<DIM, N>::LINES > 24 ? 24 : TPB / Shape<DIM, N>::LINES);
 }
 
 // Shared-memory position of node n inside a per-variable block.  For power-of-two line
@@ -73,7 +73,8 @@ struct Layout {
   using S = Shape<DIM, N>;
   static constexpr int NV = NSP + DIM + 1;
   static constexpr int NP = S::NP;
-  static constexpr int EPB = epb<DIM, N>();
+  // CTA shape (measured): one gas 96-thread CTAs, up to 8 per SM; mixtures 192 threads
+  static constexpr int EPB = epb<DIM, N, (NSP > 1 ? 192 : 96)>();
   static constexpr int NQ = DIM + 3;                // rho, v, p, beta(=rho/p)
   static constexpr int NFV = NS ? DIM * (DIM + 1) : 0;
   static constexpr int FACE_NODES = 2 * DIM * S::LPD;  // per element
@@ -96,9 +97,10 @@ struct Layout {
   static constexpr int FV = ACC + EPB * SACC;
   static constexpr int PC = FV + EPB * SFV;          // mixtures: p, c per node
   static constexpr int DU = PC + EPB * SPC;           // prefetched RK register du
-  // resident-CTA target (measured: 4 for one gas; 3 for mixtures, whose 9-variable line
-  // accumulators spill below ~110 registers a thread), lowered where shared memory binds
-  static constexpr int CAP = NSP > 1 ? 3 : 4;
+  // resident-CTA target (measured: 8 of the 96-thread CTAs for one gas; 3 for mixtures,
+  // whose 9-variable line accumulators spill below ~110 registers a thread), lowered where
+  // shared memory binds
+  static constexpr int CAP = NSP > 1 ? 3 : 8;
   static constexpr int ctas_of(size_t bytes) {
     return (int)((227 * 1024) / (bytes + 1024)) >= CAP ? CAP : (int)((227 * 1024) / (bytes + 1024));
   }
