@@ -51,6 +51,7 @@ class Problem(C.Structure):
         ("species", C.c_void_p), ("Ja", C.c_void_p), ("J", C.c_void_p),
         ("alpha_override", C.c_double),
         ("n_reactions", C.c_int), ("reactions", C.c_void_p), ("chem_dt", C.c_double),
+        ("positivity_eps", C.c_double),
     ]
 
 
@@ -89,6 +90,7 @@ def lib():
             "or_mlp_loss_grad": (d, [vp, i, vp, vp, vp]),
             "or_adam_step": (None, [vp, vp, vp, vp, i, i, d, d, d, d]),
             "or_mixture_temperature": (i, [i, vp, i, vp, vp, vp, vp, vp]),
+            "or_positivity": (i, [vp, vp, d, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(_lib, name)
@@ -141,7 +143,7 @@ class Oracle:
     def __init__(self, dim, N, xyz, nbr_elem, nbr_face, *, n_species=0, equations=EULER,
                  volume_flux=VF_RANOCHA, surface_flux=SF_LLF, gamma=1.4, mu=0.0, Pr=0.72,
                  alpha_max=0.0, bc_kind=None, bc_prim=None, species=None,
-                 alpha_override=-1.0, reactions=None, chem_dt=0.0):
+                 alpha_override=-1.0, reactions=None, chem_dt=0.0, positivity_eps=0.0):
         self.dim, self.N = dim, N
         self.np = (N + 1) ** dim
         self.nv = lib().or_nv(dim, n_species)
@@ -166,7 +168,8 @@ class Oracle:
                          species=_p(self.species), Ja=_p(self.Ja), J=_p(self.J),
                          alpha_override=alpha_override,
                          n_reactions=0 if reactions is None else len(self.reactions),
-                         reactions=_p(self.reactions), chem_dt=chem_dt)
+                         reactions=_p(self.reactions), chem_dt=chem_dt,
+                         positivity_eps=positivity_eps)
 
     def _ref(self):
         return C.byref(self.P)
@@ -235,6 +238,15 @@ class Oracle:
         if lib().or_temperature_field(self._ref(), _p(u), _p(T)):
             raise ValueError("temperature solve failed")
         return T
+
+    def positivity(self, u, eps):
+        """Zhang-Shu limited copy of u and the number of elements changed."""
+        u = np.array(u, dtype=np.float64, copy=True, order="C")
+        n = C.c_int(0)
+        rc = lib().or_positivity(self._ref(), _p(u), eps, C.byref(n))
+        if rc:
+            raise ValueError("an element mean is not admissible")
+        return u, n.value
 
     def diagnostics(self, u):
         u = np.ascontiguousarray(u, dtype=np.float64)

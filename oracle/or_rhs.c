@@ -572,10 +572,100 @@ int or_step_rk(const or_problem* P, double* u, int nsteps, double cfl, double dt
         du[i] = (s == 0 ? 0.0 : A[s] * du[i]) + dt * r[i];
         u[i] += B[s] * du[i];
       }
+      if (P->positivity_eps > 0.0) err |= or_positivity(P, u, P->positivity_eps, NULL);
     }
     *t += dt;
   }
   free(du); free(r);
+  return err;
+}
+
+/* Zhang-Shu positivity limiter (the positivity-preserving limiter the paper applies to
+ * its shock problems), one calorically perfect gas.  Per element, with the quadrature
+ * weights W_i = w_i J_i and the element mean ubar = sum W_i u_i / sum W_i:
+ *   1. density: if min rho_i < eps, rho_i <- rhobar + th1 (rho_i - rhobar) with
+ *      th1 = (rhobar - eps) / (rhobar - min rho_i);
+ *   2. pressure: for every node with p(u_i) < eps, t_i in (0, 1) solves
+ *      p(ubar + t (u_i - ubar)) = eps, i.e. the quadratic
+ *      (E(t) - eps/(gamma-1)) rho(t) - |m(t)|^2 / 2 = 0; th2 = min t_i and every variable
+ *      u_i <- ubar + th2 (u_i - ubar).
+ * Both steps keep the element mean.  Returns 1 when an element mean itself is not
+ * admissible (rhobar <= eps or p(ubar) <= eps).  n_limited (may be NULL) counts the
+ * elements changed. */
+int or_positivity(const or_problem* P, double* u, double eps, int* n_limited) {
+  basis b;
+  make_basis(P, &b);
+  const int dim = b.dim, np = b.np, nv = b.nv;
+  if (P->n_species > 0) return 1;
+  const double g1 = P->gamma - 1.0;
+  int err = 0, nlim = 0;
+  double* W = (double*)malloc(sizeof(double) * np);
+  for (int64_t k = 0; k < P->K; ++k) {
+    double* ue = u + (size_t)k * nv * np;
+    double Wsum = 0.0, ubar[OR_MAX_NV] = {0};
+    for (int node = 0; node < np; ++node) {
+      double wq = 1.0;
+      for (int d = 0; d < dim; ++d) wq *= b.w[line_pos(&b, d, node)];
+      W[node] = wq * P->J[(size_t)k * np + node];
+      Wsum += W[node];
+      for (int v = 0; v < nv; ++v) ubar[v] += W[node] * ue[v * np + node];
+    }
+    for (int v = 0; v < nv; ++v) ubar[v] /= Wsum;
+    double mb2 = 0.0;
+    for (int d = 0; d < dim; ++d) mb2 += ubar[1 + d] * ubar[1 + d];
+    const double pbar = g1 * (ubar[1 + dim] - 0.5 * mb2 / ubar[0]);
+    if (!(ubar[0] > eps) || !(pbar > eps)) {
+      err = 1;
+      continue;
+    }
+    int changed = 0;
+    /* 1. density */
+    double rmin = ue[0];
+    for (int node = 1; node < np; ++node) rmin = fmin(rmin, ue[node]);
+    if (rmin < eps) {
+      const double th1 = (ubar[0] - eps) / (ubar[0] - rmin);
+      for (int node = 0; node < np; ++node) ue[node] = ubar[0] + th1 * (ue[node] - ubar[0]);
+      changed = 1;
+    }
+    /* 2. pressure */
+    const double ep = eps / g1;
+    double th2 = 1.0;
+    for (int node = 0; node < np; ++node) {
+      double m2 = 0.0;
+      for (int d = 0; d < dim; ++d) m2 += ue[(1 + d) * np + node] * ue[(1 + d) * np + node];
+      const double p = g1 * (ue[(1 + dim) * np + node] - 0.5 * m2 / ue[node]);
+      if (p >= eps) continue;
+      const double dr = ue[node] - ubar[0], dE = ue[(1 + dim) * np + node] - ubar[1 + dim];
+      double mdm = 0.0, dm2 = 0.0;
+      for (int d = 0; d < dim; ++d) {
+        const double dm = ue[(1 + d) * np + node] - ubar[1 + d];
+        mdm += ubar[1 + d] * dm;
+        dm2 += dm * dm;
+      }
+      const double a = dE * dr - 0.5 * dm2;
+      const double bq = dE * ubar[0] + (ubar[1 + dim] - ep) * dr - mdm;
+      const double c = (ubar[1 + dim] - ep) * ubar[0] - 0.5 * mb2;  /* > 0 */
+      double t;
+      if (fabs(a) < 1e-14 * (fabs(bq) + fabs(c))) {
+        t = -c / bq;
+      } else {
+        const double disc = fmax(0.0, bq * bq - 4.0 * a * c);
+        const double q = -0.5 * (bq + copysign(sqrt(disc), bq));
+        const double t1 = q / a, t2 = c / q;
+        t = (t1 >= 0.0 && t1 <= 1.0) ? t1 : t2;
+      }
+      t = fmin(1.0, fmax(0.0, t));
+      th2 = fmin(th2, t);
+    }
+    if (th2 < 1.0) {
+      for (int v = 0; v < nv; ++v)
+        for (int node = 0; node < np; ++node) ue[v * np + node] = ubar[v] + th2 * (ue[v * np + node] - ubar[v]);
+      changed = 1;
+    }
+    nlim += changed;
+  }
+  free(W);
+  if (n_limited) *n_limited = nlim;
   return err;
 }
 

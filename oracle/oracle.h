@@ -55,6 +55,7 @@ typedef struct {
   int n_reactions;          /* finite-rate chemistry (5 species), 0 = frozen */
   const double* reactions;  /* [n_reactions][19] */
   double chem_dt;           /* point-implicit time scale of the source; 0 = explicit */
+  double positivity_eps;    /* > 0: Zhang-Shu positivity limiter after every RK stage (one gas) */
 } or_problem;
 
 typedef struct {
@@ -114,6 +115,7 @@ double or_max_dt(const or_problem* P, const double* u, double cfl);
 int or_step_rk(const or_problem* P, double* u, int nsteps, double cfl, double dt_fixed,
                double* t);
 int or_diagnostics(const or_problem* P, const double* u, double* out);
+int or_positivity(const or_problem* P, double* u, double eps, int* n_limited);
 void or_ck45(double* A, double* B, double* c);
 int or_temperature_field(const or_problem* P, const double* u, double* T);
 
