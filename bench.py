@@ -482,15 +482,16 @@ def run_other_shapes(args, stream_ptr, world):
     w0 = W.freestream_primitive(xyz.shape[0], 16, fs)
     dof = xyz.shape[0] * 16 * 4
     blk = {"workload": "square_cylinder_mach3_512x256_N3", "elements": xyz.shape[0], "dof": dof,
-           "alpha_max": 0.5, "cfl": 0.3}
+           "alpha_max": 0.5, "cfl": 0.3, "positivity_eps": 1e-10}
     for name, prec, n in (("mixed", dg.DG_MIXED, 40), ("fp64", dg.DG_FP64, 10)):
         s = dg.Solver(2, 3, xyz, nbr, face, bc_kind=[1, 2, 3], bc_prim=np.stack([fs] * 3),
-                      alpha_max=0.5, precision=prec, stream=stream_ptr)
+                      alpha_max=0.5, precision=prec, stream=stream_ptr, positivity_eps=1e-10)
         s.set_primitive(w0)
         try:
             wall, per = timed(s, n, 0.3)
             blk[name] = {"value": world * dof * 5 * n / wall, "ms_per_step": wall * 1e3 / n, "steps": n,
                          "blended_elements": int((dg.dg_get_alpha(s.ctx, s.K) > 0).sum()),
+                         "limited_element_stages": dg.dg_limiter_stats(s.ctx),
                          "device_ms_per_step_by_kernel": per}
         except dg.DgError as e:
             blk[name] = {"error": str(e)}

@@ -98,6 +98,13 @@ typedef struct {
                                recovered from the compensated energy relative to
                                p_ref / (gamma - 1): low-Mach fluctuations keep their FP32
                                digits.  0 for none; must be 0 for mixtures. */
+  double positivity_eps;    /* one gas: > 0 applies the Zhang-Shu positivity limiter (the
+                               limiter the paper uses for its shock problems) to the state
+                               after every RK stage of dg_step_rk: per element, density then
+                               pressure >= positivity_eps at every node by scaling toward the
+                               element mean (which it keeps).  The next step's CFL time step
+                               uses the wave speeds of the last stage before limiting.  0 for
+                               none; must be 0 for mixtures. */
 } dg_physics_desc;
 
 /* LGL nodes and weights used by libdg for degree N (host arrays of N+1).
@@ -241,13 +248,22 @@ dg_status dg_get_gradients(dg_ctx* ctx, double* grad);
  * dg_profile_read waits for the stream and returns, per kernel kind, the summed
  * device milliseconds and the number of launches since the last read
  * (kinds: DG_PROF_RHS, DG_PROF_GRAD, DG_PROF_INDICATOR, DG_PROF_LAMBDA,
- * DG_PROF_THERMO, DG_PROF_MLP, DG_PROF_CHEM, DG_PROF_OTHER); then it resets them.
- * ms and launches are host arrays of n entries (n <= DG_PROF_KINDS). */
+ * DG_PROF_THERMO, DG_PROF_MLP, DG_PROF_CHEM, DG_PROF_OTHER, DG_PROF_LIMITER); then it
+ * resets them.  ms and launches are host arrays of n entries (n <= DG_PROF_KINDS). */
 enum { DG_PROF_RHS = 0, DG_PROF_GRAD = 1, DG_PROF_INDICATOR = 2, DG_PROF_LAMBDA = 3,
        DG_PROF_THERMO = 4, DG_PROF_MLP = 5, DG_PROF_CHEM = 6, DG_PROF_OTHER = 7,
-       DG_PROF_KINDS = 8 };
+       DG_PROF_LIMITER = 8, DG_PROF_KINDS = 9 };
 dg_status dg_profile(dg_ctx* ctx, int enable);
 dg_status dg_profile_read(dg_ctx* ctx, double* ms, int64_t* launches, int n);
+
+/* Apply the positivity limiter (eps = positivity_eps of the context, which must be > 0)
+ * once to the current state, e.g. to a raw initial condition.  Synchronises; returns
+ * DG_ENONPHYS when an element mean is not admissible. */
+dg_status dg_limit_state(dg_ctx* ctx);
+
+/* Elements changed by the positivity limiter since the last call (host int64); resets
+ * the count.  0 when the limiter is off. */
+dg_status dg_limiter_stats(dg_ctx* ctx, int64_t* elements);
 
 /* Measured arithmetic peak of the current device (no counterpart in the paper; the
  * roofline denominator of arithmetic-bound kernels): chains of fused multiply-adds in

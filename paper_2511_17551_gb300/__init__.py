@@ -35,9 +35,9 @@ EXPORTED = [
     "dg_error_element", "dg_status_string", "dg_destroy", "dg_profile", "dg_profile_read",
     "dg_rhs_ns_noalloc", "dg_get_temperature", "dg_set_surrogate", "dg_surrogate_stats",
     "dg_thermo_sample", "dg_mlp_nparams", "dg_mlp_workspace_bytes", "dg_mlp_grad",
-    "dg_mlp_train_step", "dg_mlp_forward", "dg_peak_flops", "dg_chem_sample",
+    "dg_mlp_train_step", "dg_mlp_forward", "dg_peak_flops", "dg_chem_sample", "dg_limiter_stats", "dg_limit_state",
 ]
-PROF_KINDS = ["rhs", "gradients", "indicator", "lambda", "thermo", "mlp", "chem", "other"]
+PROF_KINDS = ["rhs", "gradients", "indicator", "lambda", "thermo", "mlp", "chem", "other", "limiter"]
 
 
 class DgError(RuntimeError):
@@ -60,7 +60,7 @@ class PhysicsDesc(C.Structure):
                 ("alpha_max", C.c_double), ("precision", C.c_int), ("thermo", C.c_int),
                 ("n_bc", C.c_int), ("bc_kind", C.c_void_p), ("bc_prim", C.c_void_p),
                 ("stream", C.c_void_p), ("reactions", C.c_void_p), ("n_reactions", C.c_int),
-                ("p_ref", C.c_double)]
+                ("p_ref", C.c_double), ("positivity_eps", C.c_double)]
 
 
 _lib = None
@@ -95,6 +95,8 @@ def lib():
             "dg_set_surrogate": (i, [vp, i, vp, vp]),
             "dg_surrogate_stats": (i, [vp, i, vp]),
             "dg_chem_sample": (i, [vp, i64, C.c_uint64, vp, vp]),
+            "dg_limiter_stats": (i, [vp, vp]),
+            "dg_limit_state": (i, [vp]),
             "dg_thermo_sample": (i, [vp, i64, C.c_uint64, vp, vp]),
             "dg_mlp_nparams": (i, [i]),
             "dg_mlp_workspace_bytes": (C.c_size_t, [i, i]),
@@ -241,6 +243,17 @@ def dg_mlp_forward(params, X, y, tensor_cores=1, stream=None):
                                 int(tensor_cores), stream), "dg_mlp_forward")
 
 
+def dg_limit_state(ctx):
+    _check(lib().dg_limit_state(ctx), "dg_limit_state")
+
+
+def dg_limiter_stats(ctx):
+    """Elements changed by the positivity limiter since the last call."""
+    out = np.zeros(1, dtype=np.int64)
+    _check(lib().dg_limiter_stats(ctx, _ptr(out)), "dg_limiter_stats")
+    return int(out[0])
+
+
 def dg_peak_flops(precision, iters=20000):
     """Measured FMA peak of the device in TFLOP/s (DG_FP64 or DG_MIXED = FP32)."""
     t = C.c_double()
@@ -303,7 +316,7 @@ class Solver:
                  gamma=1.4, mu=0.0, Pr=0.72, species=None, volume_flux=DG_VF_RANOCHA,
                  surface_flux=DG_SF_LLF, alpha_max=0.0, precision=DG_FP64,
                  thermo=DG_THERMO_NEWTON, bc_kind=None, bc_prim=None, stream=None,
-                 reactions=None, p_ref=0.0):
+                 reactions=None, p_ref=0.0, positivity_eps=0.0):
         self.dim, self.N = dim, N
         self.np = (N + 1) ** dim
         self.nsp = max(1, n_species)
@@ -328,7 +341,8 @@ class Solver:
                            thermo=thermo, n_bc=len(self._bck) if bc_kind is not None else 0,
                            bc_kind=_ptr(self._bck), bc_prim=_ptr(self._bcp), stream=stream,
                            reactions=_ptr(self._reac),
-                           n_reactions=0 if reactions is None else len(self._reac), p_ref=p_ref)
+                           n_reactions=0 if reactions is None else len(self._reac), p_ref=p_ref,
+                           positivity_eps=positivity_eps)
         self.ctx = dg_init_mesh(mesh, phys)
 
     @property

@@ -17,7 +17,8 @@ struct dg_ctx {
   int dim, N, np, nv, nsp, nf;
   int64_t K;
   int equations, n_species, vf, sf, precision, thermo, n_bc;
-  double gamma, mu, Pr, alpha_max, p_ref;
+  double gamma, mu, Pr, alpha_max, p_ref, pos_eps;
+  unsigned long long* pos_count;  // elements changed by the positivity limiter
   cudaStream_t stream;
   bool own_stream;
   size_t rs;  // bytes per real of the form
@@ -400,6 +401,13 @@ cudaError_t run_thermo(dg_ctx* c, const void* u) {
   });
 }
 
+cudaError_t run_positivity(dg_ctx* c, const DgArgs& b) {
+  return timed(c, DG_PROF_LIMITER, [&] {
+    return c->precision == DG_MIXED ? dg_f32_positivity(b, b.out, c->ulo, c->pos_eps, c->pos_count, c->stream)
+                                    : dg_f64_positivity(b, b.out, nullptr, c->pos_eps, c->pos_count, c->stream);
+  });
+}
+
 // everything that precedes the main kernel of one right-hand side at state u
 cudaError_t pre_rhs(dg_ctx* c, DgArgs& a) {
   cudaError_t e = cudaSuccess;
@@ -459,7 +467,7 @@ void free_ctx(dg_ctx* c) {
   if (!c) return;
   cudaSetDevice(c->dev);
   void* ptrs[] = {c->nbr, c->Ja64, c->J64, c->invJ64, c->Ja32, c->invJ32, c->u[0], c->u[1],
-                  c->du, c->ulo, c->gradW, c->alpha_raw, c->alpha_used, c->bc_kind, c->bc_u, c->scal,
+                  c->du, c->ulo, c->pos_count, c->gradW, c->alpha_raw, c->alpha_used, c->bc_kind, c->bc_u, c->scal,
                   c->lam, c->status, c->partial, c->stage64};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -526,6 +534,7 @@ dg_status dg_init_mesh(const dg_mesh_desc* m, const dg_physics_desc* p, dg_ctx**
   if (p->n_species > 0 && p->volume_flux == DG_VF_RANOCHA) return DG_EINVAL;
   if (p->n_species == 0 && !(p->gamma > 1.0)) return DG_EINVAL;
   if (!(p->p_ref >= 0.0) || (p->n_species > 0 && p->p_ref != 0.0)) return DG_EINVAL;
+  if (!(p->positivity_eps >= 0.0) || (p->n_species > 0 && p->positivity_eps != 0.0)) return DG_EINVAL;
   if (p->precision != DG_FP64 && p->precision != DG_MIXED) return DG_EINVAL;
   if (p->thermo != DG_THERMO_NEWTON && p->thermo != DG_THERMO_MLP) return DG_EINVAL;
   if (p->alpha_max < 0.0 || p->alpha_max > 1.0) return DG_EINVAL;
@@ -576,6 +585,7 @@ dg_status dg_init_mesh(const dg_mesh_desc* m, const dg_physics_desc* p, dg_ctx**
   c->n_bc = p->n_bc;
   c->gamma = p->gamma;
   c->p_ref = p->p_ref;
+  c->pos_eps = p->positivity_eps;
   c->mu = p->mu;
   c->Pr = p->Pr;
   c->alpha_max = p->alpha_max;
@@ -617,6 +627,10 @@ dg_status dg_init_mesh(const dg_mesh_desc* m, const dg_physics_desc* p, dg_ctx**
     TRYM(c->u[1], c->rs * nst);
     TRYM(c->du, c->rs * nst);
     if (c->precision == DG_MIXED) TRYM(c->ulo, sizeof(float) * nst);
+    if (c->pos_eps > 0.0) {
+      TRYM(c->pos_count, sizeof(unsigned long long));
+      TRY(cudaMemset(c->pos_count, 0, sizeof(unsigned long long)));
+    }
     if (c->equations == DG_NAVIER_STOKES) TRYM(c->gradW, c->rs * K * dim * (dim + 1) * c->np);
     if (c->alpha_max > 0.0) {
       TRYM(c->alpha_raw, c->rs * K);
@@ -831,6 +845,7 @@ dg_status dg_step_rk(dg_ctx* c, int nsteps, double cfl, double dt_fixed, double*
       b.want_lambda = (s == 4 && cfl_mode && c->n_species == 0) ? 1 : 0;
       CK(pre_rhs(c, b));
       CK(run_rhs(c, b));
+      if (c->pos_eps > 0.0) CK(run_positivity(c, b));
       c->cur ^= 1;
     }
     if (cfl_mode) {
@@ -1031,3 +1046,29 @@ int64_t dg_error_element(dg_ctx* c) {
 }
 
 }  // extern "C"
+
+extern "C" dg_status dg_limiter_stats(dg_ctx* c, int64_t* out) {
+  if (!c || !out) return DG_EINVAL;
+  out[0] = 0;
+  if (!c->pos_count) return DG_OK;
+  cudaSetDevice(c->dev);
+  dg_status w = wait_stream(c);
+  if (w != DG_OK) return w;
+  unsigned long long h = 0;
+  CK(cudaMemcpy(&h, c->pos_count, sizeof(h), cudaMemcpyDeviceToHost));
+  CK(cudaMemset(c->pos_count, 0, sizeof(h)));
+  out[0] = (int64_t)h;
+  return DG_OK;
+}
+
+extern "C" dg_status dg_limit_state(dg_ctx* c) {
+  if (!c || !(c->pos_eps > 0.0)) return DG_EINVAL;
+  if (!c->have_state) return DG_ESTATE;
+  cudaSetDevice(c->dev);
+  DgArgs b = base_args(c);
+  b.out = c->u[c->cur];
+  CK(run_positivity(c, b));
+  dg_status w = wait_stream(c);
+  if (w != DG_OK) return w;
+  return take_status(c, NULL);
+}

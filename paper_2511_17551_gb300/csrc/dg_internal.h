@@ -64,6 +64,11 @@ cudaError_t dg_f64g_upload_basis();
 cudaError_t dg_f32g_upload_basis();
 cudaError_t dg_f64g_rhs(const DgArgs& a, cudaStream_t s);
 cudaError_t dg_f32g_rhs(const DgArgs& a, cudaStream_t s);
+// Zhang-Shu positivity limiter on a state of the context's precision (one gas)
+cudaError_t dg_f64_positivity(const DgArgs& a, void* u, void* ulo, double eps, unsigned long long* nlim,
+                              cudaStream_t s);
+cudaError_t dg_f32_positivity(const DgArgs& a, void* u, void* ulo, double eps, unsigned long long* nlim,
+                              cudaStream_t s);
 cudaError_t dg_f64_upload_basis();
 cudaError_t dg_f32_upload_basis();
 cudaError_t dg_f64_rhs(const DgArgs& a, cudaStream_t s);

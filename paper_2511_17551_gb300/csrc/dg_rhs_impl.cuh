@@ -745,6 +745,124 @@ __global__ void step_dt_kernel(const DgArgs a, int slot, int advance_time) {
   a.lam[2 * (slot ^ 1) + 1] = 0ull;
 }
 
+// ------------------------------------------------------------------ positivity limiter
+// Zhang-Shu limiter for one gas, one warp per element, applied to a stage's output state
+// (u: form precision; ulo: the low part of the compensated FP32 state, or null).  With
+// W_n = w_n / invJ_n and the element mean ubar (FP64 accumulation of hi + lo):
+// density step rho <- rhobar + th1 (rho - rhobar), th1 = (rhobar - eps)/(rhobar - min rho);
+// pressure step u <- ubar + th2 (u - ubar), th2 = min over nodes of the root t in (0, 1)
+// of (E(t) - eps/(gamma-1)) rho(t) - |m(t)|^2/2 = 0.  Elements whose nodes are admissible
+// are only read.  An inadmissible mean latches a non-physical status.
+template <int DIM, int N>
+__global__ void __launch_bounds__(128) positivity_kernel(const DgArgs a, real* u, real* ulo, double eps,
+                                                         unsigned long long* nlim) {
+  using S = Shape<DIM, N>;
+  constexpr int NP = S::NP, N1 = S::N1, NV = DIM + 2;
+  const int lane = threadIdx.x & 31;
+  const int64_t k = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  if (k >= a.K) return;
+  const BasisTab<real>& B = c_tab[N];
+  const double g1 = a.gamma - 1.0;
+  real* ue = u + k * NV * NP;
+  real* le = ulo ? ulo + k * NV * NP : nullptr;
+  const real* ij = (const real*)a.invJ + k * NP;
+  auto val = [&](int v, int n) { return (double)ue[v * NP + n] + (le ? (double)le[v * NP + n] : 0.0); };
+  auto weight = [&](int n) {
+    double wq = (double)B.w[n % N1] * (double)B.w[(n / N1) % N1];
+    if (DIM == 3) wq *= (double)B.w[n / (N1 * N1)];
+    return wq / (double)ij[n];
+  };
+  auto pres = [&](const double* s) {
+    double m2 = 0.0;
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) m2 += s[1 + d] * s[1 + d];
+    return g1 * (s[1 + DIM] - 0.5 * m2 / s[0]);
+  };
+  // pass 1: mean, minima
+  double acc[NV + 1], rmin = 1e300, pmin = 1e300;
+#pragma unroll
+  for (int v = 0; v <= NV; ++v) acc[v] = 0.0;
+  for (int n = lane; n < NP; n += 32) {
+    const double W = weight(n);
+    double s[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      s[v] = val(v, n);
+      acc[v] += W * s[v];
+    }
+    acc[NV] += W;
+    rmin = fmin(rmin, s[0]);
+    pmin = fmin(pmin, pres(s));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+    for (int v = 0; v <= NV; ++v) acc[v] += __shfl_xor_sync(0xffffffffu, acc[v], o);
+    rmin = fmin(rmin, __shfl_xor_sync(0xffffffffu, rmin, o));
+    pmin = fmin(pmin, __shfl_xor_sync(0xffffffffu, pmin, o));
+  }
+  if (rmin >= eps && pmin >= eps) return;
+  double ub[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) ub[v] = acc[v] / acc[NV];
+  if (!(ub[0] > eps) || !(pres(ub) > eps)) {
+    if (lane == 0) latch_status(a.status, DG_ST_NONPHYS, k);
+    return;
+  }
+  auto put = [&](int v, int n, double x) {
+    const real h = (real)x;
+    ue[v * NP + n] = h;
+    if (le) le[v * NP + n] = (real)(x - (double)h);
+  };
+  // pass 2: density
+  if (rmin < eps) {
+    const double th1 = (ub[0] - eps) / (ub[0] - rmin);
+    for (int n = lane; n < NP; n += 32) put(0, n, ub[0] + th1 * (val(0, n) - ub[0]));
+    __syncwarp();
+  }
+  // pass 3: pressure
+  const double ep = eps / g1;
+  double mb2 = 0.0;
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) mb2 += ub[1 + d] * ub[1 + d];
+  const double c = (ub[1 + DIM] - ep) * ub[0] - 0.5 * mb2;
+  double th2 = 1.0;
+  for (int n = lane; n < NP; n += 32) {
+    double s[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) s[v] = val(v, n);
+    if (pres(s) >= eps) continue;
+    const double dr = s[0] - ub[0], dE = s[1 + DIM] - ub[1 + DIM];
+    double mdm = 0.0, dm2 = 0.0;
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+      const double dm = s[1 + d] - ub[1 + d];
+      mdm += ub[1 + d] * dm;
+      dm2 += dm * dm;
+    }
+    const double qa = dE * dr - 0.5 * dm2;
+    const double qb = dE * ub[0] + (ub[1 + DIM] - ep) * dr - mdm;
+    double t;
+    if (fabs(qa) < 1e-14 * (fabs(qb) + fabs(c))) {
+      t = -c / qb;
+    } else {
+      const double disc = fmax(0.0, qb * qb - 4.0 * qa * c);
+      const double q = -0.5 * (qb + copysign(sqrt(disc), qb));
+      const double t1 = q / qa, t2 = c / q;
+      t = (t1 >= 0.0 && t1 <= 1.0) ? t1 : t2;
+    }
+    th2 = fmin(th2, fmin(1.0, fmax(0.0, t)));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) th2 = fmin(th2, __shfl_xor_sync(0xffffffffu, th2, o));
+  if (th2 < 1.0) {
+    for (int n = lane; n < NP; n += 32)
+#pragma unroll
+      for (int v = 0; v < NV; ++v) put(v, n, ub[v] + th2 * (val(v, n) - ub[v]));
+  }
+  if (lane == 0 && nlim) atomicAdd(nlim, 1ull);
+}
+
 // ------------------------------------------------------------------ BR1 gradients
 template <int DIM, int N, int NSP>
 struct GLayout {
@@ -1044,6 +1162,14 @@ cudaError_t launch_grad_t(const DgArgs& a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+template <int DIM, int N>
+cudaError_t launch_pos_t(const DgArgs& a, void* u, void* ulo, double eps, unsigned long long* nlim,
+                         cudaStream_t st) {
+  const int64_t grid = (a.K * 32 + 127) / 128;
+  positivity_kernel<DIM, N><<<(unsigned)grid, 128, 0, st>>>(a, (real*)u, (real*)ulo, eps, nlim);
+  return cudaGetLastError();
+}
+
 template <int DIM, int N, int NSP>
 cudaError_t launch_ind_t(const DgArgs& a, double amax, void* out, cudaStream_t st) {
   const int bs = 128;
@@ -1077,6 +1203,7 @@ cudaError_t launch_ind_t(const DgArgs& a, double amax, void* out, cudaStream_t s
 #define DG_RHS_CALL(DIM, N, NSP, NS) DG_PREFIX::launch_rhs_t<DIM, N, NSP, NS>(a, st)
 #define DG_GRAD_CALL(DIM, N, NSP, X) DG_PREFIX::launch_grad_t<DIM, N, NSP>(a, st)
 #define DG_IND_CALL(DIM, N, NSP, X) DG_PREFIX::launch_ind_t<DIM, N, NSP>(a, amax, out, st)
+#define DG_POS_CALL(DIM, N, NSP, X) DG_PREFIX::launch_pos_t<DIM, N>(a, u, ulo, eps, nlim, st)
 
 cudaError_t DG_CAT(DG_PREFIX, _rhs)(const DgArgs& a, cudaStream_t st) {
 #ifndef DG_GENERIC_ONLY
@@ -1100,6 +1227,13 @@ cudaError_t DG_CAT(DG_PREFIX, _indicator)(const DgArgs& a, double amax, void* ou
   if (a.dim == 2 && a.nsp == 1) { DG_DISPATCH_N(DG_IND_CALL, 2, 1, 0) }
   if (a.dim == 3 && a.nsp == 1) { DG_DISPATCH_N(DG_IND_CALL, 3, 1, 0) }
   if (a.dim == 3 && a.nsp == 5) { DG_DISPATCH_N_MIX(DG_IND_CALL, 3, 5, 0) }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t DG_CAT(DG_PREFIX, _positivity)(const DgArgs& a, void* u, void* ulo, double eps,
+                                          unsigned long long* nlim, cudaStream_t st) {
+  if (a.dim == 3 && a.nsp == 1) { DG_DISPATCH_N(DG_POS_CALL, 3, 1, 0) }
+  if (a.dim == 2 && a.nsp == 1) { DG_DISPATCH_N(DG_POS_CALL, 2, 1, 0) }
   return cudaErrorInvalidValue;
 }
 
