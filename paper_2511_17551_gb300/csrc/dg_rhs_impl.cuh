@@ -778,6 +778,22 @@ __global__ void __launch_bounds__(128) positivity_kernel(const DgArgs a, real* u
     for (int d = 0; d < DIM; ++d) m2 += s[1 + d] * s[1 + d];
     return g1 * (s[1 + DIM] - 0.5 * m2 / s[0]);
   };
+  // pass 0, in the form's precision: can any node of the element be outside the bounds?
+  // (margins cover the rounding of the check itself and the low part of the state)
+  {
+    const real tol = sizeof(real) == 4 ? real(1e-6) : real(1e-14);
+    const real epsr = (real)eps;
+    bool viol = false;
+    for (int n = lane; n < NP; n += 32) {
+      const real r = ue[n], E = ue[(1 + DIM) * NP + n];
+      real m2 = 0;
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) m2 += ue[(1 + d) * NP + n] * ue[(1 + d) * NP + n];
+      const real pr = (real)g1 * (E - real(0.5) * m2 * RealOps<real>::rcp(r));
+      viol = viol || !(r >= epsr * (real(1) + tol) && pr >= epsr + tol * fabs(E));
+    }
+    if (!__any_sync(0xffffffffu, viol)) return;
+  }
   // pass 1: mean, minima
   double acc[NV + 1], rmin = 1e300, pmin = 1e300;
 #pragma unroll
