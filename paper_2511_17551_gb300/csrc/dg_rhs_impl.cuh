@@ -789,8 +789,9 @@ __global__ void __launch_bounds__(128) positivity_kernel(const DgArgs a, real* u
       real m2 = 0;
 #pragma unroll
       for (int d = 0; d < DIM; ++d) m2 += ue[(1 + d) * NP + n] * ue[(1 + d) * NP + n];
-      const real pr = (real)g1 * (E - real(0.5) * m2 * RealOps<real>::rcp(r));
-      viol = viol || !(r >= epsr * (real(1) + tol) && pr >= epsr + tol * fabs(E));
+      // with r > 0: p >= eps + margin  <=>  r (E - (eps + margin)/(gamma-1)) >= |m|^2 / 2
+      const real pbound = (epsr + tol * fabs(E)) * (real)(1.0 / g1);
+      viol = viol || !(r >= epsr * (real(1) + tol) && r * (E - pbound) >= real(0.5) * m2);
     }
     if (!__any_sync(0xffffffffu, viol)) return;
   }
