@@ -174,15 +174,23 @@ class Oracle:
     def _ref(self):
         return C.byref(self.P)
 
+    def _field(self, u, copy=False):
+        """u as a C-contiguous float64 [K][nv][np] array (shape checked: the C side trusts it)."""
+        u = np.array(u, dtype=np.float64, copy=True, order="C") if copy else \
+            np.ascontiguousarray(u, dtype=np.float64)
+        if u.shape != (self.K, self.nv, self.np):
+            raise ValueError("state shape %s, expected %s" % (u.shape, (self.K, self.nv, self.np)))
+        return u
+
     def prim_to_cons(self, w):
-        w = np.ascontiguousarray(w, dtype=np.float64)
+        w = self._field(w)
         u = np.zeros_like(w)
         if lib().or_prim_to_cons_field(self._ref(), _p(w), _p(u)):
             raise ValueError("non-physical primitive state")
         return u
 
     def rhs(self, u, want_alpha=False, want_grad=False):
-        u = np.ascontiguousarray(u, dtype=np.float64)
+        u = self._field(u)
         r = np.zeros_like(u)
         a = np.zeros(self.K) if want_alpha else None
         g = (np.zeros((self.K, self.dim, self.dim + 1, self.np)) if want_grad else None)
@@ -197,17 +205,17 @@ class Oracle:
         return out[0] if len(out) == 1 else tuple(out)
 
     def indicator(self, u):
-        u = np.ascontiguousarray(u, dtype=np.float64)
+        u = self._field(u)
         a = np.zeros(self.K)
         lib().or_indicator(self._ref(), _p(u), _p(a))
         return a
 
     def max_dt(self, u, cfl):
-        u = np.ascontiguousarray(u, dtype=np.float64)
+        u = self._field(u)
         return lib().or_max_dt(self._ref(), _p(u), cfl)
 
     def step_rk(self, u, nsteps, cfl=0.5, dt_fixed=0.0, t=0.0):
-        u = np.array(u, dtype=np.float64, copy=True, order="C")
+        u = self._field(u, copy=True)
         tt = C.c_double(t)
         rc = lib().or_step_rk(self._ref(), _p(u), nsteps, cfl, dt_fixed, C.byref(tt))
         if rc:
@@ -233,7 +241,7 @@ class Oracle:
         return w
 
     def temperature(self, u):
-        u = np.ascontiguousarray(u, dtype=np.float64)
+        u = self._field(u)
         T = np.zeros((self.K, self.np))
         if lib().or_temperature_field(self._ref(), _p(u), _p(T)):
             raise ValueError("temperature solve failed")
@@ -241,7 +249,7 @@ class Oracle:
 
     def positivity(self, u, eps):
         """Zhang-Shu limited copy of u and the number of elements changed."""
-        u = np.array(u, dtype=np.float64, copy=True, order="C")
+        u = self._field(u, copy=True)
         n = C.c_int(0)
         rc = lib().or_positivity(self._ref(), _p(u), eps, C.byref(n))
         if rc:
@@ -249,7 +257,7 @@ class Oracle:
         return u, n.value
 
     def diagnostics(self, u):
-        u = np.ascontiguousarray(u, dtype=np.float64)
+        u = self._field(u)
         out = np.zeros(8)
         lib().or_diagnostics(self._ref(), _p(u), _p(out))
         return out

@@ -162,6 +162,21 @@ void or_volume_flux(const or_problem* P, const double* uL, const or_prim* qL,
     f[nsp + dim] = 0.5 * (qL->rhoE + qL->p + qR->rhoE + qR->p) * vn;
     return;
   }
+  if (P->volume_flux == OR_VF_KG || P->volume_flux == OR_VF_PIROZZOLI) {
+    /* Kennedy-Gruber and Pirozzoli split forms (single gas), as two-point fluxes: products
+     * of arithmetic means, {{rho}} {{v.n}} for mass; momentum f_rho {{v}} + {{p}} n; energy
+     * f_rho {{E/rho}} + {{p}} {{v.n}} (Kennedy-Gruber) or f_rho {{(E + p)/rho}} (Pirozzoli) */
+    double frho = 0.5 * (qL->rho + qR->rho) * 0.5 * (vnL + vnR);
+    f[0] = frho;
+    for (int d = 0; d < dim; ++d)
+      f[1 + d] = frho * 0.5 * (qL->v[d] + qR->v[d]) + 0.5 * (qL->p + qR->p) * n[d];
+    if (P->volume_flux == OR_VF_KG)
+      f[1 + dim] = frho * 0.5 * (qL->rhoE / qL->rho + qR->rhoE / qR->rho) +
+                   0.5 * (qL->p + qR->p) * 0.5 * (vnL + vnR);
+    else
+      f[1 + dim] = frho * 0.5 * ((qL->rhoE + qL->p) / qL->rho + (qR->rhoE + qR->p) / qR->rho);
+    return;
+  }
   /* Ranocha EC flux (single ideal gas) */
   double g = P->gamma;
   double rho_m = or_ln_mean(qL->rho, qR->rho);
@@ -202,6 +217,12 @@ void or_surface_flux(const or_problem* P, const double* uL, const or_prim* qL,
   double SR = fmax(uL_n + qL->c, uR_n + qR->c);
   if (SL >= 0.0) { for (int v = 0; v < nv; ++v) f[v] = fL[v]; return; }
   if (SR <= 0.0) { for (int v = 0; v < nv; ++v) f[v] = fR[v]; return; }
+  if (P->surface_flux == OR_SF_HLL) {
+    /* HLL (Harten, Lax, van Leer) with the same Davis speeds: one intermediate state */
+    for (int v = 0; v < nv; ++v)
+      f[v] = (SR * fL[v] - SL * fR[v] + nn * SL * SR * (uR[v] - uL[v])) / (SR - SL);
+    return;
+  }
   double Ss = (qR->p - qL->p + qL->rho * uL_n * (SL - uL_n) - qR->rho * uR_n * (SR - uR_n)) /
               (qL->rho * (SL - uL_n) - qR->rho * (SR - uR_n));
   const double* uK = Ss >= 0.0 ? uL : uR;

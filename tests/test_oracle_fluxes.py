@@ -31,7 +31,7 @@ def _prim(u, g=1.4):
 
 
 @pytest.mark.parametrize("dim", [2, 3])
-@pytest.mark.parametrize("vf", [0, 1, 2])
+@pytest.mark.parametrize("vf", [0, 1, 2, 3, 4])
 def test_volume_flux_consistency_and_symmetry(orc, dim, vf):
     o = _orc1(orc, dim, volume_flux=vf)
     rng = np.random.default_rng(vf + 10 * dim)
@@ -96,7 +96,7 @@ def test_entropy_variables_are_gradient_of_entropy(orc, dim):
 
 
 @pytest.mark.parametrize("dim", [2, 3])
-@pytest.mark.parametrize("sf", [0, 1])
+@pytest.mark.parametrize("sf", [0, 1, 3])
 def test_surface_flux_consistency_and_dissipation(orc, dim, sf):
     o = _orc1(orc, dim, surface_flux=sf)
     rng = np.random.default_rng(6 + sf)
@@ -150,3 +150,44 @@ def test_ln_mean_branches(orc):
     y = (1 + 1e-2) / (1 - 1e-2)
     lo, hi = orc.ln_mean(x, y * (1 - 1e-9)), orc.ln_mean(x, y * (1 + 1e-9))
     assert abs(hi - lo) < 1e-8 * lo
+
+
+@pytest.mark.parametrize("vf", [0, 3, 4])
+def test_kinetic_energy_preserving_momentum(orc, vf):
+    """Ranocha, Kennedy-Gruber and Pirozzoli fluxes share the kinetic-energy-preserving
+    momentum flux f_rho {{v}} + {{p}} n; KG and Pirozzoli carry f_rho = {{rho}} {{v.n}}."""
+    o = _orc1(orc, 3, volume_flux=vf)
+    rng = np.random.default_rng(30 + vf)
+    for _ in range(20):
+        uL, uR = _state(rng, 3), _state(rng, 3)
+        n = rng.normal(size=3)
+        f = o.flux_pair(uL, uR, n, 0)
+        (rL, vL, pL), (rR, vR, pR) = _prim(uL), _prim(uR)
+        assert np.allclose(f[1:4], f[0] * 0.5 * (vL + vR) + 0.5 * (pL + pR) * n, rtol=1e-13, atol=1e-13)
+        if vf:
+            assert abs(f[0] - 0.5 * (rL + rR) * 0.5 * (vL + vR) @ n) < 1e-13 * (1 + abs(f[0]))
+            h = (lambda u, r, p: (u[-1] + p) / r)
+            e = (lambda u, r: u[-1] / r)
+            fe = (f[0] * 0.5 * (e(uL, rL) + e(uR, rR)) + 0.5 * (pL + pR) * 0.5 * (vL + vR) @ n if vf == 3
+                  else f[0] * 0.5 * (h(uL, rL, pL) + h(uR, rR, pR)))
+            assert abs(f[4] - fe) < 1e-13 * (1 + abs(fe))
+
+
+def test_hll_stationary_contact_and_upwinding(orc):
+    """HLL with the Davis speeds: for a density jump at rest the speeds are -+c_max|n| and
+    HLL reduces to LLF, mass flux -c_max |n| (rho_R - rho_L) / 2; supersonic flow upwinds."""
+    g = 1.4
+    n = np.array([0.3, -1.2, 0.5])
+    p = 1.7
+    uL = np.array([1.0, 0, 0, 0, p / (g - 1)])
+    uR = np.array([0.125, 0, 0, 0, p / (g - 1)])
+    hll = _orc1(orc, 3, surface_flux=3).flux_pair(uL, uR, n, 1)
+    llf = _orc1(orc, 3, surface_flux=0).flux_pair(uL, uR, n, 1)
+    cmax = np.sqrt(g * p / 0.125)
+    assert np.allclose(hll, llf, rtol=1e-13, atol=1e-13)
+    assert abs(hll[0] + 0.5 * cmax * np.linalg.norm(n) * (0.125 - 1.0)) < 1e-13
+    o = _orc1(orc, 2, surface_flux=3)
+    uL = np.array([1.0, 3.0, 0.0, 1.0 / (g - 1) + 4.5])
+    uR = np.array([0.5, 1.0, 0.2, 0.4 / (g - 1) + 1.04])
+    n2 = np.array([2.0, 0.0])
+    assert np.allclose(o.flux_pair(uL, uR, n2, 1), o.flux_pair(uL, uL, n2, 2), rtol=1e-14)

@@ -382,3 +382,20 @@ def test_time_step_closed_form(orc):
     c = np.sqrt(g * p / rho)
     lam = np.sum(np.abs(vel) + c) / 0.25  # h/2 = 0.25 per direction
     assert abs(o.max_dt(u, 0.5) - 0.5 * 2 / (4 * lam)) < 1e-14
+
+
+@pytest.mark.parametrize("vf,sf", [(3, 0), (4, 3), (3, 3)])
+def test_free_stream_and_conservation_other_split_forms(orc, vf, sf):
+    """Kennedy-Gruber / Pirozzoli volume fluxes with LLF / HLL faces: free stream preserved
+    on the warped mesh, total mass / momentum / energy conserved on the periodic box."""
+    o, u = _tgv_oracle(orc, 3, 3, volume_flux=vf, surface_flux=sf)
+    const = np.array([1.1, 0.3, -0.2, 0.5, 80.0])
+    r = o.rhs(np.broadcast_to(const[None, :, None], u.shape).copy())
+    scale = np.abs(const).max() * np.abs(o.Ja).max() / o.J.min() * 9
+    assert np.abs(r).max() < 1e-13 * scale
+    u = o.prim_to_cons(cases.perturbed_state(cases.tgv(orc.lgl(3)[0], 3, warp=0.1)[3], 4))
+    r = o.rhs(u)
+    x, w = orc.lgl(3)
+    W = np.einsum("i,j,k->kji", w, w, w).reshape(-1)[None, :] * o.J
+    tot = np.einsum("kn,kvn->v", W, r)
+    assert np.abs(tot).max() < 1e-12 * np.abs(np.einsum("kn,kvn->v", W, np.abs(r))).max()
