@@ -54,9 +54,15 @@ typedef enum {
 
 enum { DG_EULER = 0, DG_NAVIER_STOKES = 1 };
 /* two-point volume flux F# of Eq. fluxdiffcons */
-enum { DG_VF_RANOCHA = 0, DG_VF_DUCROS = 1, DG_VF_CENTRAL = 2 };
+enum { DG_VF_RANOCHA = 0, DG_VF_DUCROS = 1, DG_VF_CENTRAL = 2,
+       /* split forms the paper lists beside Ducros (one gas): Kennedy-Gruber
+          ({{rho}}{{v.n}}, f_rho {{v}} + {{p}} n, f_rho {{E/rho}} + {{p}}{{v.n}}) and Pirozzoli
+          (energy f_rho {{(E + p)/rho}}) */
+       DG_VF_KG = 3, DG_VF_PIROZZOLI = 4 };
 /* interface flux F^Rie of Eqs. riemann_problem1-3; DG_SF_EC uses F# itself */
-enum { DG_SF_LLF = 0, DG_SF_HLLC = 1, DG_SF_EC = 2 };
+enum { DG_SF_LLF = 0, DG_SF_HLLC = 1, DG_SF_EC = 2,
+       /* HLL with the Davis wave speeds (the third solver the paper names) */
+       DG_SF_HLL = 3 };
 enum { DG_FP64 = 0, DG_MIXED = 1 };
 enum { DG_THERMO_NEWTON = 0, DG_THERMO_MLP = 1 };
 enum { DG_BC_INFLOW = 1, DG_BC_OUTFLOW = 2, DG_BC_SLIP_WALL = 3 };

@@ -204,6 +204,18 @@ __device__ __forceinline__ void volume_flux(int vf, real rL, const real* vL, rea
 #pragma unroll
     for (int d = 0; d < DIM; ++d) f[1 + d] = frho * real(0.5) * (vL[d] + vR[d]) + pa * n[d];
     f[1 + DIM] = frho * (real(0.5) * vv + ib * inv_gm1) + real(0.5) * ((pL + pref) * vnR + (pR + pref) * vnL);
+  } else if (NSP == 1 && (vf == DG_VF_KG || vf == DG_VF_PIROZZOLI)) {
+    // Kennedy-Gruber / Pirozzoli split forms as products of arithmetic means
+    const real frho = real(0.25) * (rL + rR) * (vnL + vnR);
+    const real irL = RealOps<real>::rcp(rL), irR = RealOps<real>::rcp(rR);
+    f[0] = frho;
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) f[1 + d] = frho * real(0.5) * (vL[d] + vR[d]) + real(0.5) * (pL + pR) * n[d];
+    if (vf == DG_VF_KG)
+      f[1 + DIM] = frho * real(0.5) * (uL[1 + DIM] * irL + uR[1 + DIM] * irR) +
+                   real(0.25) * ((pL + pref) + (pR + pref)) * (vnL + vnR);
+    else
+      f[1 + DIM] = frho * real(0.5) * ((uL[1 + DIM] + (pL + pref)) * irL + (uR[1 + DIM] + (pR + pref)) * irR);
   } else if (vf == DG_VF_DUCROS) {
     real vn = real(0.5) * (vnL + vnR);
     real pa = real(0.5) * (pL + pR);
@@ -264,6 +276,13 @@ __device__ __forceinline__ void surface_flux(int sf, const NodeState<real, DIM, 
   if (SR <= real(0)) {
 #pragma unroll
     for (int k = 0; k < NV; ++k) f[k] = fR[k];
+    return;
+  }
+  if (sf == DG_SF_HLL) {
+    // HLL with the same Davis speeds (one intermediate state), scaled by |n|
+    const real iden = RealOps<real>::rcp(SR - SL);
+#pragma unroll
+    for (int k = 0; k < NV; ++k) f[k] = (SR * fL[k] - SL * fR[k] + nn * SL * SR * (R.u[k] - L.u[k])) * iden;
     return;
   }
   real Ss = RealOps<real>::div(R.p - L.p + L.rho * uLn * (SL - uLn) - R.rho * uRn * (SR - uRn),

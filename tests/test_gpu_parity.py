@@ -49,6 +49,15 @@ def _rhs_pair(dg, pair, w_o, w_g):
 RHS_CASES = {
     "tgv_euler_4^3_N3": dict(builder=_tgv_builder(4, warp=0.0), dim=3, N=3, kw={}),
     "tgv_warped_ragged_N3_llf": dict(builder=_tgv_builder(shape=(3, 3, 5)), dim=3, N=3, kw={}),
+    # the other split forms the paper lists, with LLF and HLL faces
+    "tgv_warped_ragged_N3_kg_hll": dict(builder=_tgv_builder(shape=(3, 3, 5)), dim=3, N=3,
+                                        kw=dict(volume_flux=3, surface_flux=3)),
+    "tgv_warped_N4_pirozzoli": dict(builder=_tgv_builder(shape=(2, 3, 3)), dim=3, N=4,
+                                    kw=dict(volume_flux=4)),
+    "tgv_ns_warped_N3_pirozzoli_hll_pref": dict(builder=_tgv_builder(shape=(3, 3, 5)), dim=3, N=3,
+                                                kw=dict(equations=1, mu=0.01, Pr=0.72, volume_flux=4,
+                                                        surface_flux=3, p_ref=cases.tgv_p0())),
+    "vortex_2d_N3_kg": dict(builder=lambda x: cases.vortex(x, 5), dim=2, N=3, kw=dict(volume_flux=3)),
     # pressure offset of the momentum fluxes (exact in arithmetic): same bars
     "tgv_warped_ragged_N3_pref": dict(builder=_tgv_builder(shape=(3, 3, 5)), dim=3, N=3,
                                       kw=dict(p_ref=cases.tgv_p0())),
