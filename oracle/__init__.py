@@ -17,8 +17,8 @@ _SRCS = ["or_basis.c", "or_geometry.c", "or_physics.c", "or_rhs.c", "or_thermo_c
          "or_mlp.c"]
 
 EULER, NAVIER_STOKES = 0, 1
-VF_RANOCHA, VF_DUCROS, VF_CENTRAL = 0, 1, 2
-SF_LLF, SF_HLLC, SF_EC = 0, 1, 2
+VF_RANOCHA, VF_DUCROS, VF_CENTRAL, VF_KG, VF_PIROZZOLI, VF_MORINISHI = 0, 1, 2, 3, 4, 5
+SF_LLF, SF_HLLC, SF_EC, SF_HLL = 0, 1, 2, 3
 BC_INFLOW, BC_OUTFLOW, BC_SLIP_WALL = 1, 2, 3
 
 

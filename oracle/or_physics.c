@@ -177,6 +177,22 @@ void or_volume_flux(const or_problem* P, const double* uL, const or_prim* qL,
       f[1 + dim] = frho * 0.5 * ((qL->rhoE + qL->p) / qL->rho + (qR->rhoE + qR->p) / qR->rho);
     return;
   }
+  if (P->volume_flux == OR_VF_MORINISHI) {
+    /* Morinishi's form (single gas): mass {{rho v}}.n in divergence form, momentum
+     * f_rho {{v}} + {{p}} n (skew-symmetric), enthalpy g/(g-1) {{p v}}.n in divergence
+     * form and kinetic energy f_rho v_L.v_R / 2 */
+    double frho = 0.0, pv = 0.0, vv = 0.0;
+    for (int d = 0; d < dim; ++d) {
+      frho += 0.5 * (uL[1 + d] + uR[1 + d]) * n[d];
+      vv += qL->v[d] * qR->v[d];
+    }
+    pv = 0.5 * (qL->p * vnL + qR->p * vnR);
+    f[0] = frho;
+    for (int d = 0; d < dim; ++d)
+      f[1 + d] = frho * 0.5 * (qL->v[d] + qR->v[d]) + 0.5 * (qL->p + qR->p) * n[d];
+    f[1 + dim] = P->gamma / (P->gamma - 1.0) * pv + frho * 0.5 * vv;
+    return;
+  }
   /* Ranocha EC flux (single ideal gas) */
   double g = P->gamma;
   double rho_m = or_ln_mean(qL->rho, qR->rho);

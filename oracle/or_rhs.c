@@ -301,7 +301,8 @@ int or_rhs(const or_problem* P, const double* u, double* rhs, double* alpha_out,
   if (P->dim < 2 || P->dim > 3 || P->N < 1 || P->N > OR_MAX_N) return 1;
   if (check_mesh(P)) return 1;
   make_basis(P, &b);
-  if (P->n_species > 0 && P->volume_flux == OR_VF_RANOCHA) return 1;
+  /* the Ranocha, Kennedy-Gruber, Pirozzoli and Morinishi forms are single-gas fluxes */
+  if (P->n_species > 0 && P->volume_flux != OR_VF_DUCROS && P->volume_flux != OR_VF_CENTRAL) return 1;
   if (P->n_species > 0 && P->equations == OR_NAVIER_STOKES) return 1;
   int dim = b.dim, N = b.N, np = b.np, nv = b.nv;
   double* alpha = NULL;

@@ -29,7 +29,8 @@
 #define OR_MAX_NV (OR_MAX_SPECIES + 4)
 
 enum { OR_EULER = 0, OR_NAVIER_STOKES = 1 };
-enum { OR_VF_RANOCHA = 0, OR_VF_DUCROS = 1, OR_VF_CENTRAL = 2, OR_VF_KG = 3, OR_VF_PIROZZOLI = 4 };
+enum { OR_VF_RANOCHA = 0, OR_VF_DUCROS = 1, OR_VF_CENTRAL = 2, OR_VF_KG = 3, OR_VF_PIROZZOLI = 4,
+       OR_VF_MORINISHI = 5 };
 enum { OR_SF_LLF = 0, OR_SF_HLLC = 1, OR_SF_EC = 2, OR_SF_HLL = 3 };
 enum { OR_BC_INFLOW = 1, OR_BC_OUTFLOW = 2, OR_BC_SLIP_WALL = 3 };
 

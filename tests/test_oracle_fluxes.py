@@ -31,7 +31,7 @@ def _prim(u, g=1.4):
 
 
 @pytest.mark.parametrize("dim", [2, 3])
-@pytest.mark.parametrize("vf", [0, 1, 2, 3, 4])
+@pytest.mark.parametrize("vf", [0, 1, 2, 3, 4, 5])
 def test_volume_flux_consistency_and_symmetry(orc, dim, vf):
     o = _orc1(orc, dim, volume_flux=vf)
     rng = np.random.default_rng(vf + 10 * dim)
@@ -191,3 +191,65 @@ def test_hll_stationary_contact_and_upwinding(orc):
     uR = np.array([0.5, 1.0, 0.2, 0.4 / (g - 1) + 1.04])
     n2 = np.array([2.0, 0.0])
     assert np.allclose(o.flux_pair(uL, uR, n2, 1), o.flux_pair(uL, uL, n2, 2), rtol=1e-14)
+
+
+def _split_form_derivative(vf, U, n, D, g=1.4):
+    """The split-form derivative each named two-point flux stands for (Gassner, Winters and
+    Kopriva's product-rule splittings): with constant metrics n, flux differencing
+    2 sum_l D_il F#(U_i, U_l) equals, for every D with zero row sums,
+      {{a}}{{b}}      ->  (D(ab) + a Db + b Da) / 2
+      {{a}}{{b}}{{c}} ->  (D(abc) + a D(bc) + b D(ac) + c D(ab) + ab Dc + ac Db + bc Da) / 4
+      {{a}}           ->  Da,   {{a}}  v_L.v_R / 2 with a = rho v.n  ->  (a v.Dv + v.D(a v)) / 2.
+    Written here from the splittings, not from the two-point formulas."""
+    dim = U.shape[1] - 2
+    rho, m, E = U[:, 0], U[:, 1:1 + dim], U[:, -1]
+    v = m / rho[:, None]
+    p = (g - 1) * (E - 0.5 * rho * (v * v).sum(1))
+    vn = v @ n
+    s2 = lambda a, b: 0.5 * (D @ (a * b) + a * (D @ b) + b * (D @ a))
+    s3 = lambda a, b, c: 0.25 * (D @ (a * b * c) + a * (D @ (b * c)) + b * (D @ (a * c)) + c * (D @ (a * b))
+                                 + a * b * (D @ c) + a * c * (D @ b) + b * c * (D @ a))
+    out = np.zeros_like(U)
+    if vf == 1:      # Ducros: every conserved quantity times v.n, pressure in divergence form
+        out[:, 0] = s2(rho, vn)
+        for d in range(dim):
+            out[:, 1 + d] = s2(m[:, d], vn) + (D @ p) * n[d]
+        out[:, -1] = s2(E + p, vn)
+    elif vf == 2:    # standard DG: the divergence of the flux
+        out[:, 0] = D @ (rho * vn)
+        for d in range(dim):
+            out[:, 1 + d] = D @ (m[:, d] * vn + p * n[d])
+        out[:, -1] = D @ ((E + p) * vn)
+    elif vf in (3, 4):  # Kennedy-Gruber / Pirozzoli: cubic splits of rho (v.n) phi
+        out[:, 0] = s2(rho, vn)
+        for d in range(dim):
+            out[:, 1 + d] = s3(rho, vn, v[:, d]) + (D @ p) * n[d]
+        out[:, -1] = s3(rho, vn, E / rho) + s2(p, vn) if vf == 3 else s3(rho, vn, (E + p) / rho)
+    elif vf == 5:    # Morinishi: mass and enthalpy in divergence form, skew momentum and KE
+        mn = m @ n
+        out[:, 0] = D @ mn
+        for d in range(dim):
+            out[:, 1 + d] = s2(mn, v[:, d]) + (D @ p) * n[d]
+        ke = 0.5 * ((mn[:, None] * v) * (D @ v)).sum(1) + 0.5 * (v * (D @ (mn[:, None] * v))).sum(1)
+        out[:, -1] = g / (g - 1) * (D @ (p * vn)) + ke
+    return out
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("vf", [1, 2, 3, 4, 5])
+def test_two_point_flux_is_its_split_form(orc, dim, vf):
+    """Flux differencing with each two-point flux reproduces its split-form derivative
+    (Eq. fluxdiffcons with the forms listed beside it) on a line of random states."""
+    o = _orc1(orc, dim, volume_flux=vf)
+    rng = np.random.default_rng(70 + vf + 10 * dim)
+    n_pts = 6
+    U = np.array([_state(rng, dim) for _ in range(n_pts)])
+    D = rng.normal(size=(n_pts, n_pts))
+    D -= D.mean(1, keepdims=True)   # zero row sums: the only property the identity uses
+    n = rng.normal(size=dim)
+    fd = np.zeros_like(U)
+    for i in range(n_pts):
+        for l in range(n_pts):
+            fd[i] += 2 * D[i, l] * o.flux_pair(U[i], U[l], n, 0)
+    ref = _split_form_derivative(vf, U, n, D)
+    assert np.allclose(fd, ref, rtol=1e-12, atol=1e-12 * np.abs(ref).max())

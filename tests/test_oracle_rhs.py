@@ -384,7 +384,7 @@ def test_time_step_closed_form(orc):
     assert abs(o.max_dt(u, 0.5) - 0.5 * 2 / (4 * lam)) < 1e-14
 
 
-@pytest.mark.parametrize("vf,sf", [(3, 0), (4, 3), (3, 3)])
+@pytest.mark.parametrize("vf,sf", [(3, 0), (4, 3), (3, 3), (5, 0), (5, 1)])
 def test_free_stream_and_conservation_other_split_forms(orc, vf, sf):
     """Kennedy-Gruber / Pirozzoli volume fluxes with LLF / HLL faces: free stream preserved
     on the warped mesh, total mass / momentum / energy conserved on the periodic box."""
