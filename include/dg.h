@@ -54,11 +54,13 @@ typedef enum {
 
 enum { DG_EULER = 0, DG_NAVIER_STOKES = 1 };
 /* two-point volume flux F# of Eq. fluxdiffcons */
+/* DG_VF_CENTRAL = {{f(u).n}}, the standard DG form; DG_VF_DUCROS = {{u}}{{v.n}} + {{p}} */
 enum { DG_VF_RANOCHA = 0, DG_VF_DUCROS = 1, DG_VF_CENTRAL = 2,
        /* split forms the paper lists beside Ducros (one gas): Kennedy-Gruber
-          ({{rho}}{{v.n}}, f_rho {{v}} + {{p}} n, f_rho {{E/rho}} + {{p}}{{v.n}}) and Pirozzoli
-          (energy f_rho {{(E + p)/rho}}) */
-       DG_VF_KG = 3, DG_VF_PIROZZOLI = 4 };
+          ({{rho}}{{v.n}}, f_rho {{v}} + {{p}} n, f_rho {{E/rho}} + {{p}}{{v.n}}), Pirozzoli
+          (energy f_rho {{(E + p)/rho}}) and Morinishi (f_rho = {{rho v}}.n, f_rho {{v}} + {{p}} n,
+          g/(g-1) {{p v}}.n + f_rho v_L.v_R / 2) */
+       DG_VF_KG = 3, DG_VF_PIROZZOLI = 4, DG_VF_MORINISHI = 5 };
 /* interface flux F^Rie of Eqs. riemann_problem1-3; DG_SF_EC uses F# itself */
 enum { DG_SF_LLF = 0, DG_SF_HLLC = 1, DG_SF_EC = 2,
        /* HLL with the Davis wave speeds (the third solver the paper names) */

@@ -22,7 +22,7 @@ __all__ = [
 
 DG_OK, DG_EINVAL, DG_ENOMEM, DG_ECUDA, DG_ENONPHYS, DG_ENEWTON, DG_ETIMEOUT, DG_ESTATE = range(8)
 DG_EULER, DG_NAVIER_STOKES = 0, 1
-DG_VF_RANOCHA, DG_VF_DUCROS, DG_VF_CENTRAL, DG_VF_KG, DG_VF_PIROZZOLI = 0, 1, 2, 3, 4
+DG_VF_RANOCHA, DG_VF_DUCROS, DG_VF_CENTRAL, DG_VF_KG, DG_VF_PIROZZOLI, DG_VF_MORINISHI = 0, 1, 2, 3, 4, 5
 DG_SF_LLF, DG_SF_HLLC, DG_SF_EC, DG_SF_HLL = 0, 1, 2, 3
 DG_FP64, DG_MIXED = 0, 1
 DG_THERMO_NEWTON, DG_THERMO_MLP = 0, 1

@@ -529,10 +529,10 @@ dg_status dg_init_mesh(const dg_mesh_desc* m, const dg_physics_desc* p, dg_ctx**
   if (p->equations == DG_NAVIER_STOKES && (p->n_species > 0 || m->dim != 3 || !(p->mu > 0) ||
                                            !(p->Pr > 0)))
     return DG_EINVAL;
-  if (p->volume_flux < 0 || p->volume_flux > DG_VF_PIROZZOLI || p->surface_flux < 0 || p->surface_flux > DG_SF_HLL)
+  if (p->volume_flux < 0 || p->volume_flux > DG_VF_MORINISHI || p->surface_flux < 0 || p->surface_flux > DG_SF_HLL)
     return DG_EINVAL;
   if (p->n_species > 0 && (p->volume_flux == DG_VF_RANOCHA || p->volume_flux == DG_VF_KG ||
-                           p->volume_flux == DG_VF_PIROZZOLI))
+                           p->volume_flux == DG_VF_PIROZZOLI || p->volume_flux == DG_VF_MORINISHI))
     return DG_EINVAL;
   if (p->n_species == 0 && !(p->gamma > 1.0)) return DG_EINVAL;
   if (!(p->p_ref >= 0.0) || (p->n_species > 0 && p->p_ref != 0.0)) return DG_EINVAL;

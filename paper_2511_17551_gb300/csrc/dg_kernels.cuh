@@ -216,6 +216,20 @@ __device__ __forceinline__ void volume_flux(int vf, real rL, const real* vL, rea
                    real(0.25) * ((pL + pref) + (pR + pref)) * (vnL + vnR);
     else
       f[1 + DIM] = frho * real(0.5) * ((uL[1 + DIM] + (pL + pref)) * irL + (uR[1 + DIM] + (pR + pref)) * irR);
+  } else if (NSP == 1 && vf == DG_VF_MORINISHI) {
+    // Morinishi: mass and enthalpy in divergence form, skew-symmetric momentum, kinetic
+    // energy f_rho v_L.v_R / 2
+    real frho = 0, vv = 0;
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+      frho += (uL[1 + d] + uR[1 + d]) * n[d];
+      vv += vL[d] * vR[d];
+    }
+    frho *= real(0.5);
+    f[0] = frho;
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) f[1 + d] = frho * real(0.5) * (vL[d] + vR[d]) + real(0.5) * (pL + pR) * n[d];
+    f[1 + DIM] = (real(1) + inv_gm1) * real(0.5) * ((pL + pref) * vnL + (pR + pref) * vnR) + frho * real(0.5) * vv;
   } else if (vf == DG_VF_DUCROS) {
     real vn = real(0.5) * (vnL + vnR);
     real pa = real(0.5) * (pL + pR);

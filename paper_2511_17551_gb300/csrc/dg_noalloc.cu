@@ -36,7 +36,7 @@ extern "C" dg_status dg_rhs_ns_noalloc(int N, int64_t K, const int32_t* nbr, con
       u == rhs)
     return DG_EINVAL;
   if (!(gamma > 1.0) || !(mu > 0.0) || !(Pr > 0.0)) return DG_EINVAL;
-  if (volume_flux < 0 || volume_flux > DG_VF_PIROZZOLI || surface_flux < 0 || surface_flux > DG_SF_HLL) return DG_EINVAL;
+  if (volume_flux < 0 || volume_flux > DG_VF_MORINISHI || surface_flux < 0 || surface_flux > DG_SF_HLL) return DG_EINVAL;
   const int np = (N + 1) * (N + 1) * (N + 1);
   const double need = 256.0 + (double)K * np * 12.0 * sizeof(double);
   if (need > (double)DG_NOALLOC_SCRATCH_BYTES) return DG_EINVAL;  // beyond the static scratch

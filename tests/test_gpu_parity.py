@@ -58,6 +58,9 @@ RHS_CASES = {
                                                 kw=dict(equations=1, mu=0.01, Pr=0.72, volume_flux=4,
                                                         surface_flux=3, p_ref=cases.tgv_p0())),
     "vortex_2d_N3_kg": dict(builder=lambda x: cases.vortex(x, 5), dim=2, N=3, kw=dict(volume_flux=3)),
+    "tgv_warped_ragged_N3_morinishi_hllc_pref": dict(builder=_tgv_builder(shape=(3, 3, 5)), dim=3, N=3,
+                                                     kw=dict(volume_flux=5, surface_flux=1,
+                                                             p_ref=cases.tgv_p0())),
     # pressure offset of the momentum fluxes (exact in arithmetic): same bars
     "tgv_warped_ragged_N3_pref": dict(builder=_tgv_builder(shape=(3, 3, 5)), dim=3, N=3,
                                       kw=dict(p_ref=cases.tgv_p0())),
@@ -266,3 +269,11 @@ def test_invalid_arguments(dg):
     with pytest.raises(dg.DgError) as ei:
         dg.Solver(3, 3, xyz, nbr, face, n_species=5, species=np.zeros((5, 8)))  # Ranocha + mixture
     assert ei.value.code == dg.DG_EINVAL
+    for kw in (dict(volume_flux=6), dict(surface_flux=4), dict(volume_flux=-1)):
+        with pytest.raises(dg.DgError) as ei:
+            dg.Solver(3, 3, xyz, nbr, face, **kw)
+        assert ei.value.code == dg.DG_EINVAL
+    for vf in (3, 4, 5):  # single-gas split forms with a mixture
+        with pytest.raises(dg.DgError) as ei:
+            dg.Solver(3, 3, xyz, nbr, face, n_species=5, species=np.zeros((5, 8)), volume_flux=vf)
+        assert ei.value.code == dg.DG_EINVAL
