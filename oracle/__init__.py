@@ -52,6 +52,7 @@ class Problem(C.Structure):
         ("alpha_override", C.c_double),
         ("n_reactions", C.c_int), ("reactions", C.c_void_p), ("chem_dt", C.c_double),
         ("positivity_eps", C.c_double),
+        ("sutherland_s", C.c_double), ("sutherland_rt", C.c_double), ("indicator_var", C.c_int),
     ]
 
 
@@ -143,7 +144,8 @@ class Oracle:
     def __init__(self, dim, N, xyz, nbr_elem, nbr_face, *, n_species=0, equations=EULER,
                  volume_flux=VF_RANOCHA, surface_flux=SF_LLF, gamma=1.4, mu=0.0, Pr=0.72,
                  alpha_max=0.0, bc_kind=None, bc_prim=None, species=None,
-                 alpha_override=-1.0, reactions=None, chem_dt=0.0, positivity_eps=0.0):
+                 alpha_override=-1.0, reactions=None, chem_dt=0.0, positivity_eps=0.0,
+                 sutherland_s=0.0, sutherland_rt=1.0, indicator_variable=0):
         self.dim, self.N = dim, N
         self.np = (N + 1) ** dim
         self.nv = lib().or_nv(dim, n_species)
@@ -169,7 +171,8 @@ class Oracle:
                          alpha_override=alpha_override,
                          n_reactions=0 if reactions is None else len(self.reactions),
                          reactions=_p(self.reactions), chem_dt=chem_dt,
-                         positivity_eps=positivity_eps)
+                         positivity_eps=positivity_eps, sutherland_s=sutherland_s,
+                         sutherland_rt=sutherland_rt, indicator_var=indicator_variable)
 
     def _ref(self):
         return C.byref(self.P)

@@ -23,7 +23,8 @@
  * direction (the sign that makes sum_i w_i Q_i = W*_r - W*_l), physical
  * gradient (1/J) sum_i Ja^i Q^i; viscous flux f^v_x = (0, sigma_.x,
  * sigma_.x . v + kappa dT/dx) with sigma per Eq. stress (lambda = 0) and
- * kappa dT/dx = mu gamma / ((gamma-1) Pr) dtheta/dx; interface viscous flux
+ * kappa dT/dx = mu gamma / ((gamma-1) Pr) dtheta/dx (mu and kappa scaled per node by
+ * Sutherland's law, Eq. sutherland, when it is on); interface viscous flux
  * = average of both sides' f^v, dotted with the face normal; it enters as
  * + (1/J)[D Fv + M^{-1} B (Fv* - Fv)].
  */
@@ -72,8 +73,19 @@ static int nbr_node(const basis* b, int f, int node) {
   return node + (target - pos) * s;
 }
 
+/* mu(T) / mu by Sutherland's law (Eq. sutherland) at a node; 1 when it is off */
+static double mu_ratio(const or_problem* P, const or_prim* q) {
+  double s = P->sutherland_s;
+  if (!(s > 0.0)) return 1.0;
+  double th = q->p / (q->rho * P->sutherland_rt);
+  return (1.0 + s) * pow(th, 1.5) / (th + s);
+}
+
 static int check_mesh(const or_problem* P) {
   int nf = 2 * P->dim;
+  if (P->sutherland_s < 0.0 || (P->sutherland_s > 0.0 && !(P->sutherland_rt > 0.0))) return 1;
+  if (P->sutherland_s > 0.0 && P->n_species > 0) return 1;
+  if (P->indicator_var != 0 && P->indicator_var != 1) return 1;
   for (int64_t k = 0; k < P->K; ++k)
     for (int f = 0; f < nf; ++f) {
       int64_t nb = P->nbr_elem[k * nf + f];
@@ -154,7 +166,7 @@ static int element_alpha_raw(const or_problem* P, const basis* b, const double* 
     or_prim q;
     node_u(b, u, k, node, uu);
     if (or_cons_to_prim(P, uu, &q)) err = 1;
-    f[node] = q.rho * q.p;
+    f[node] = P->indicator_var ? q.p : q.rho * q.p;
   }
   /* modal coefficients: apply V^{-1} along every direction */
   memcpy(m, f, sizeof(double) * np);
@@ -271,7 +283,8 @@ static int br1_gradients(const or_problem* P, const basis* b, const double* u, d
 
 /* physical viscous flux f^v_x (x = physical direction) at a node */
 static void visc_flux(const or_problem* P, const basis* b, const double* G, int64_t k, int node,
-                      const double* v, double (*fv)[OR_MAX_NV]) {
+                      const or_prim* q, double (*fv)[OR_MAX_NV]) {
+  const double* v = q->v;
   int dim = b->dim, nW = dim + 1, np = b->np;
   double gv[3][3], gth[3];
   for (int x = 0; x < dim; ++x) {
@@ -280,7 +293,7 @@ static void visc_flux(const or_problem* P, const basis* b, const double* G, int6
   }
   double div = 0.0;
   for (int a = 0; a < dim; ++a) div += gv[a][a];
-  double mu = P->mu, g = P->gamma;
+  double mu = P->mu * mu_ratio(P, q), g = P->gamma;
   double kap = mu * g / ((g - 1.0) * P->Pr);
   for (int x = 0; x < dim; ++x) {
     fv[x][0] = 0.0;
@@ -436,7 +449,7 @@ int or_rhs(const or_problem* P, const double* u, double* rhs, double* alpha_out,
         or_prim q;
         node_u(&b, u, k, node, uu);
         if (or_cons_to_prim(P, uu, &q)) err |= 1;
-        visc_flux(P, &b, G, k, node, q.v, fv);
+        visc_flux(P, &b, G, k, node, &q, fv);
         for (int d = 0; d < dim; ++d) {
           double n[3];
           node_metric(P, &b, k, d, node, n);
@@ -462,10 +475,10 @@ int or_rhs(const or_problem* P, const double* u, double* rhs, double* alpha_out,
             or_prim q;
             node_u(&b, u, k, node, uu);
             or_cons_to_prim(P, uu, &q);
-            visc_flux(P, &b, G, k, node, q.v, fo);
+            visc_flux(P, &b, G, k, node, &q, fo);
             node_u(&b, u, nb, mn, uu);
             or_cons_to_prim(P, uu, &q);
-            visc_flux(P, &b, G, nb, mn, q.v, fx);
+            visc_flux(P, &b, G, nb, mn, &q, fx);
             node_metric(P, &b, k, d, node, n);
             for (int v = 0; v < nv; ++v) {
               double Fs = 0.0;
@@ -502,7 +515,7 @@ int or_prim_to_cons_field(const or_problem* P, const double* w, double* u) {
 }
 
 /* ---------- time step: dt = cfl * 2 / ((N+1) max lambda), lambda = sum_i (|v.Ja^i| + c|Ja^i|)/J;
- * Navier-Stokes adds dt_v = cfl * 4 / ((N+1)^2 max gamma mu/(Pr rho) sum_i |Ja^i|^2 / J^2) */
+ * Navier-Stokes adds dt_v = cfl * 4 / ((N+1)^2 max gamma mu(T)/(Pr rho) sum_i |Ja^i|^2 / J^2) */
 double or_max_dt(const or_problem* P, const double* u, double cfl) {
   basis b;
   make_basis(P, &b);
@@ -522,7 +535,7 @@ double or_max_dt(const or_problem* P, const double* u, double cfl) {
         lv += nn;
       }
       l /= Jn;
-      lv = P->gamma * P->mu / (P->Pr * q.rho) * lv / (Jn * Jn);
+      lv = P->gamma * P->mu * mu_ratio(P, &q) / (P->Pr * q.rho) * lv / (Jn * Jn);
       if (l > lam) lam = l;
       if (lv > lamv) lamv = lv;
     }
@@ -672,12 +685,14 @@ int or_positivity(const or_problem* P, double* u, double eps, int* n_limited) {
 
 /* domain integrals with the LGL quadrature:
  * out = [KE/|Omega|, enstrophy/|Omega|, int S, int rho, int rho E, |Omega|,
- *        int (div v)^2 / |Omega|, 0]; vorticity from element-local derivatives. */
+ *        int (mu(T)/mu) (div v)^2 / |Omega|, int (mu(T)/mu) |omega|^2 / |Omega|] (the
+ *        integrals of Eqs. TGV_DD and TGV_SD; mu(T)/mu = 1 without Sutherland's law);
+ *        vorticity from element-local derivatives. */
 int or_diagnostics(const or_problem* P, const double* u, double* out) {
   basis b;
   make_basis(P, &b);
   int dim = b.dim, N = b.N, np = b.np;
-  double vol = 0.0, ke = 0.0, ens = 0.0, ent = 0.0, mass = 0.0, en = 0.0, dil = 0.0;
+  double vol = 0.0, ke = 0.0, ens = 0.0, ent = 0.0, mass = 0.0, en = 0.0, dil = 0.0, sol = 0.0;
   int err = 0;
   for (int64_t k = 0; k < P->K; ++k) {
     for (int node = 0; node < np; ++node) {
@@ -724,11 +739,13 @@ int or_diagnostics(const or_problem* P, const double* u, double* out) {
       ent += P->n_species == 0 ? dV * or_entropy(P, &q) : 0.0;
       mass += dV * q.rho;
       en += dV * q.rhoE;
-      dil += dV * div * div;
+      double mr = P->n_species == 0 ? mu_ratio(P, &q) : 1.0;
+      dil += dV * mr * div * div;
+      sol += dV * mr * w2;
     }
   }
   out[0] = ke / vol; out[1] = ens / vol; out[2] = ent; out[3] = mass; out[4] = en;
-  out[5] = vol; out[6] = dil / vol; out[7] = 0.0;
+  out[5] = vol; out[6] = dil / vol; out[7] = sol / vol;
   return err;
 }
 

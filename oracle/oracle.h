@@ -57,6 +57,10 @@ typedef struct {
   const double* reactions;  /* [n_reactions][19] */
   double chem_dt;           /* point-implicit time scale of the source; 0 = explicit */
   double positivity_eps;    /* > 0: Zhang-Shu positivity limiter after every RK stage (one gas) */
+  /* NS, one gas: s > 0 switches on Sutherland's law (Eq. sutherland),
+   * mu(T) = mu (1 + s) th^1.5 / (th + s), th = (p / rho) / rt; mu is the viscosity at th = 1 */
+  double sutherland_s, sutherland_rt;
+  int indicator_var;        /* shock-indicator quantity: 0 = rho p, 1 = p */
 } or_problem;
 
 typedef struct {

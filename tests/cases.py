@@ -17,6 +17,13 @@ def tgv(xi, n_el, warp=0.0, mach=0.1, shape=None):
     return xyz, nbr, face, W.tgv_primitive(xyz, GAMMA, mach)
 
 
+def supersonic_tgv(xi, n_el, warp=0.0, shape=None, mach=1.25):
+    shape = shape or (n_el,) * 3
+    xyz, nbr, face = W.box_mesh(shape, xi, (-np.pi,) * 3, (np.pi,) * 3, periodic=True,
+                                warp=warp)
+    return xyz, nbr, face, W.supersonic_tgv_primitive(xyz, GAMMA, mach)
+
+
 def tgv_p0(mach=0.1):
     """Mean pressure of the Taylor-Green state, p0 = 1 / (gamma Ma^2)."""
     return 1.0 / (GAMMA * mach * mach)

@@ -85,6 +85,27 @@ def tgv_primitive(xyz, gamma=1.4, mach=0.1):
     return w
 
 
+SUTHERLAND_S = 0.4042   # S / T_o of the supersonic TGV's Sutherland law (Eq. sutherland)
+
+
+def supersonic_tgv_primitive(xyz, gamma=1.4, mach=1.25):
+    """Supersonic Taylor-Green vortex on [-pi,pi]^3 in units rho_o = L = U_o = 1: the
+    subsonic field with p_o = 1/(gamma M^2) and the perturbation rho_o U_o^2 / 16 (...)
+    (the dimensionally consistent reading), uniform temperature T = T_o, so that
+    rho = p / (R T_o) = p / p_o."""
+    w = tgv_primitive(xyz, gamma=gamma, mach=mach)
+    p0 = 1.0 / (gamma * mach * mach)
+    w[:, 0] = w[:, 4] / p0
+    return w
+
+
+def supersonic_tgv_physics(gamma=1.4, mach=1.25, reynolds=1600.0):
+    """Physics keywords of the supersonic TGV in the same units: mu_o = rho_o L U_o / Re at
+    T_o, Sutherland's law with s = S / T_o and the reference p/rho = p_o / rho_o."""
+    return dict(mu=1.0 / reynolds, Pr=0.72, gamma=gamma, sutherland_s=SUTHERLAND_S,
+                sutherland_rt=1.0 / (gamma * mach * mach), indicator_variable=1)
+
+
 def vortex_primitive(xyz, t=0.0, gamma=1.4, eps=5.0, period=10.0):
     """Shu isentropic vortex (2D), advected with v_inf = (1,1) on a periodic square."""
     x = xyz[:, 0] - t
