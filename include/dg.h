@@ -113,6 +113,16 @@ typedef struct {
                                element mean (which it keeps).  The next step's CFL time step
                                uses the wave speeds of the last stage before limiting.  0 for
                                none; must be 0 for mixtures. */
+  double sutherland_s;      /* one gas, Navier-Stokes: > 0 switches on Sutherland's law
+                               (Eq. sutherland), mu(T) = mu (1 + s) th^1.5 / (th + s) with
+                               th = (p / rho) / sutherland_rt, in the viscous fluxes (kappa
+                               scales with mu), the viscous time-step bound and the weights of
+                               the dissipation integrals of dg_diagnostics; s = S / T_ref
+                               (0.4042 in the paper's supersonic TGV); mu is the viscosity at
+                               T_ref.  0 for a constant viscosity. */
+  double sutherland_rt;     /* p / rho at T_ref (R T_ref); > 0 when sutherland_s > 0 */
+  int indicator_variable;   /* shock-indicator quantity: 0 = rho p (Hennemann-Gassner's
+                               default), 1 = p (the paper's supersonic TGV) */
 } dg_physics_desc;
 
 /* LGL nodes and weights used by libdg for degree N (host arrays of N+1).
@@ -152,9 +162,12 @@ dg_status dg_rhs(dg_ctx* ctx, const void* u, void* rhs, double t);
  * time.  Synchronises at the end and returns any latched device error. */
 dg_status dg_step_rk(dg_ctx* ctx, int nsteps, double cfl, double dt_fixed, double* t_inout);
 
-/* FP64 domain integrals of the current state (Eqs. TGV_KE, TGV_SD):
- * out[8] = { KE/|Omega|, enstrophy/|Omega|, int S, int rho, int rho E,
- *            |Omega|, int (div v)^2 / |Omega|, 0 }. Synchronises. */
+/* FP64 domain integrals of the current state (Eqs. TGV_KE, TGV_SD, TGV_DD):
+ * out[8] = { KE/|Omega|, enstrophy/|Omega|, int S, int rho, int rho E, |Omega|,
+ *            int (mu(T)/mu) (div v)^2 / |Omega|, int (mu(T)/mu) |omega|^2 / |Omega| },
+ * KE = int rho|v|^2/2, enstrophy = int rho|omega|^2/2, S = -rho s/(gamma-1) (one gas, else 0);
+ * mu(T)/mu is Sutherland's ratio (1 for a constant viscosity), so that
+ * eps_s = L^2/(Re U^2) out[7] and eps_d = L^2/(3 Re U^2) out[6].  Synchronises. */
 dg_status dg_diagnostics(dg_ctx* ctx, double out[8]);
 
 /* Temperature of the current state of a mixture context (Eqs. total_energy,

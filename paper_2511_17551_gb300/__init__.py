@@ -60,7 +60,9 @@ class PhysicsDesc(C.Structure):
                 ("alpha_max", C.c_double), ("precision", C.c_int), ("thermo", C.c_int),
                 ("n_bc", C.c_int), ("bc_kind", C.c_void_p), ("bc_prim", C.c_void_p),
                 ("stream", C.c_void_p), ("reactions", C.c_void_p), ("n_reactions", C.c_int),
-                ("p_ref", C.c_double), ("positivity_eps", C.c_double)]
+                ("p_ref", C.c_double), ("positivity_eps", C.c_double),
+                ("sutherland_s", C.c_double), ("sutherland_rt", C.c_double),
+                ("indicator_variable", C.c_int)]
 
 
 _lib = None
@@ -316,7 +318,8 @@ class Solver:
                  gamma=1.4, mu=0.0, Pr=0.72, species=None, volume_flux=DG_VF_RANOCHA,
                  surface_flux=DG_SF_LLF, alpha_max=0.0, precision=DG_FP64,
                  thermo=DG_THERMO_NEWTON, bc_kind=None, bc_prim=None, stream=None,
-                 reactions=None, p_ref=0.0, positivity_eps=0.0):
+                 reactions=None, p_ref=0.0, positivity_eps=0.0, sutherland_s=0.0,
+                 sutherland_rt=1.0, indicator_variable=0):
         self.dim, self.N = dim, N
         self.np = (N + 1) ** dim
         self.nsp = max(1, n_species)
@@ -342,7 +345,8 @@ class Solver:
                            bc_kind=_ptr(self._bck), bc_prim=_ptr(self._bcp), stream=stream,
                            reactions=_ptr(self._reac),
                            n_reactions=0 if reactions is None else len(self._reac), p_ref=p_ref,
-                           positivity_eps=positivity_eps)
+                           positivity_eps=positivity_eps, sutherland_s=sutherland_s,
+                           sutherland_rt=sutherland_rt, indicator_variable=indicator_variable)
         self.ctx = dg_init_mesh(mesh, phys)
 
     @property

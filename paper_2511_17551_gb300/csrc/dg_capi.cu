@@ -18,6 +18,8 @@ struct dg_ctx {
   int64_t K;
   int equations, n_species, vf, sf, precision, thermo, n_bc;
   double gamma, mu, Pr, alpha_max, p_ref, pos_eps;
+  double suth_s, suth_rt;
+  int ind_var;
   unsigned long long* pos_count;  // elements changed by the positivity limiter
   cudaStream_t stream;
   bool own_stream;
@@ -206,9 +208,10 @@ __global__ void prim2cons_kernel(const double* w, T* u, float* lo, int64_t K, in
 // FP64 domain integrals, per block partial sums (deterministic: fixed order later)
 template <typename T>
 __global__ void diag_kernel(const T* u, const double* Ja, const double* J, int64_t K, int dim,
-                            int N, int nsp, double gamma, int single_gas, double* partial) {
+                            int N, int nsp, double gamma, int single_gas, double suth_s,
+                            double suth_rt, double* partial) {
   const int np = ipow_d(N + 1, dim), nv = nsp + dim + 1;
-  double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+  double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < K * np;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t k = i / np;
@@ -259,25 +262,32 @@ __global__ void diag_kernel(const T* u, const double* Ja, const double* J, int64
     }
     acc[4] += dV * rho;
     acc[5] += dV * rhoE;
-    acc[6] += dV * div * div;
+    // Sutherland weight mu(T)/mu of the dissipation integrals (Eqs. TGV_SD, TGV_DD)
+    double mr = 1.0;
+    if (single_gas && suth_s > 0.0) {
+      const double th = (gamma - 1.0) * (rhoE - 0.5 * rho * v2) / (rho * suth_rt);
+      mr = (1.0 + suth_s) * th * sqrt(th) / (th + suth_s);
+    }
+    acc[6] += dV * mr * div * div;
+    acc[7] += dV * mr * w2;
   }
-  __shared__ double red[7][256];
-  for (int q = 0; q < 7; ++q) red[q][threadIdx.x] = acc[q];
+  __shared__ double red[8][256];
+  for (int q = 0; q < 8; ++q) red[q][threadIdx.x] = acc[q];
   __syncthreads();
   for (int w = blockDim.x / 2; w > 0; w >>= 1) {
     if ((int)threadIdx.x < w)
-      for (int q = 0; q < 7; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + w];
+      for (int q = 0; q < 8; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + w];
     __syncthreads();
   }
   if (threadIdx.x == 0)
-    for (int q = 0; q < 7; ++q) partial[blockIdx.x * 7 + q] = red[q][0];
+    for (int q = 0; q < 8; ++q) partial[blockIdx.x * 8 + q] = red[q][0];
 }
 
 __global__ void diag_final_kernel(const double* partial, int nb, double* out) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  double s[7] = {0, 0, 0, 0, 0, 0, 0};
+  double s[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   for (int b = 0; b < nb; ++b)
-    for (int q = 0; q < 7; ++q) s[q] += partial[b * 7 + q];
+    for (int q = 0; q < 8; ++q) s[q] += partial[b * 8 + q];
   out[0] = s[1] / s[0];
   out[1] = s[2] / s[0];
   out[2] = s[3];
@@ -285,7 +295,7 @@ __global__ void diag_final_kernel(const double* partial, int nb, double* out) {
   out[4] = s[5];
   out[5] = s[0];
   out[6] = s[6] / s[0];
-  out[7] = 0.0;
+  out[7] = s[7] / s[0];
 }
 
 void rk_ck45(double* A, double* B) {
@@ -326,6 +336,9 @@ DgArgs base_args(dg_ctx* c) {
   a.mu = c->mu;
   a.kappa_fac = a.ns ? c->mu * c->gamma / ((c->gamma - 1.0) * c->Pr) : 0.0;
   a.visc_coef = a.ns ? c->gamma * c->mu / c->Pr : 0.0;
+  a.suth_s = a.ns ? c->suth_s : 0.0;
+  a.suth_rt = c->suth_rt;
+  a.ind_var = c->ind_var;
   const bool f32 = c->precision == DG_MIXED;
   a.Ja = f32 ? (const void*)c->Ja32 : (const void*)c->Ja64;
   a.invJ = f32 ? (const void*)c->invJ32 : (const void*)c->invJ64;
@@ -537,6 +550,9 @@ dg_status dg_init_mesh(const dg_mesh_desc* m, const dg_physics_desc* p, dg_ctx**
   if (p->n_species == 0 && !(p->gamma > 1.0)) return DG_EINVAL;
   if (!(p->p_ref >= 0.0) || (p->n_species > 0 && p->p_ref != 0.0)) return DG_EINVAL;
   if (!(p->positivity_eps >= 0.0) || (p->n_species > 0 && p->positivity_eps != 0.0)) return DG_EINVAL;
+  if (!(p->sutherland_s >= 0.0) || (p->sutherland_s > 0.0 && (!(p->sutherland_rt > 0.0) || p->n_species > 0)))
+    return DG_EINVAL;
+  if (p->indicator_variable != 0 && p->indicator_variable != 1) return DG_EINVAL;
   if (p->precision != DG_FP64 && p->precision != DG_MIXED) return DG_EINVAL;
   if (p->thermo != DG_THERMO_NEWTON && p->thermo != DG_THERMO_MLP) return DG_EINVAL;
   if (p->alpha_max < 0.0 || p->alpha_max > 1.0) return DG_EINVAL;
@@ -588,6 +604,9 @@ dg_status dg_init_mesh(const dg_mesh_desc* m, const dg_physics_desc* p, dg_ctx**
   c->gamma = p->gamma;
   c->p_ref = p->p_ref;
   c->pos_eps = p->positivity_eps;
+  c->suth_s = p->sutherland_s;
+  c->suth_rt = p->sutherland_s > 0.0 ? p->sutherland_rt : 1.0;
+  c->ind_var = p->indicator_variable;
   c->mu = p->mu;
   c->Pr = p->Pr;
   c->alpha_max = p->alpha_max;
@@ -644,7 +663,7 @@ dg_status dg_init_mesh(const dg_mesh_desc* m, const dg_physics_desc* p, dg_ctx**
     TRYM(c->lam, sizeof(unsigned long long) * 4);
     TRYM(c->status, sizeof(unsigned long long));
     c->diag_blocks = 152 * 4;
-    TRYM(c->partial, sizeof(double) * 7 * c->diag_blocks);
+    TRYM(c->partial, sizeof(double) * 8 * c->diag_blocks);
     TRYM(c->stage64, sizeof(double) * nst);
     TRY(cudaMemset(c->status, 0, sizeof(unsigned long long)));
     TRY(cudaMemset(c->scal, 0, sizeof(double) * 4));
@@ -881,15 +900,15 @@ dg_status dg_diagnostics(dg_ctx* c, double out[8]) {
   if (c->precision == DG_MIXED)
     diag_kernel<float><<<nb, 256, 0, c->stream>>>((const float*)c->u[c->cur], c->Ja64, c->J64,
                                                   c->K, c->dim, c->N, c->nsp, c->gamma,
-                                                  c->n_species == 0, c->partial);
+                                                  c->n_species == 0, c->suth_s, c->suth_rt, c->partial);
   else
     diag_kernel<double><<<nb, 256, 0, c->stream>>>((const double*)c->u[c->cur], c->Ja64, c->J64,
                                                    c->K, c->dim, c->N, c->nsp, c->gamma,
-                                                   c->n_species == 0, c->partial);
+                                                   c->n_species == 0, c->suth_s, c->suth_rt, c->partial);
   CK(cudaGetLastError());
-  diag_final_kernel<<<1, 32, 0, c->stream>>>(c->partial, nb, dout + nb * 7);
+  diag_final_kernel<<<1, 32, 0, c->stream>>>(c->partial, nb, dout + nb * 8);
   CK(cudaGetLastError());
-  CK(cudaMemcpyAsync(out, dout + nb * 7, sizeof(double) * 8, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(out, dout + nb * 8, sizeof(double) * 8, cudaMemcpyDeviceToHost, c->stream));
   dg_status w = wait_stream(c);
   if (w != DG_OK) return w;
   return DG_OK;

@@ -26,6 +26,8 @@ struct DgArgs {
   double gamma, mu, kappa_fac;   // kappa_fac = mu gamma / ((gamma-1) Pr)
   double pref;                   // pressure offset of the momentum fluxes (one gas)
   double visc_coef;              // gamma mu / Pr (viscous time-step bound)
+  double suth_s, suth_rt;        // Sutherland's law: s = S / T_ref (0: constant mu), p/rho at T_ref
+  int ind_var;                   // shock indicator on 0: rho p, 1: p
   double cfl, dt_fixed, rkA, rkB;
   const void* u;          // [K][nv][np] input state
   void* out;              // mode 0: rhs; mode 1: new state

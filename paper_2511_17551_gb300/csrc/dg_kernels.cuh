@@ -321,6 +321,14 @@ __device__ __forceinline__ void surface_flux(int sf, const NodeState<real, DIM, 
 // physical viscous flux f^v_x (x = physical direction) for one gas; c = 0..DIM-1
 // momentum, c = DIM energy (the density component is zero).  g[x][a] = d(W_a)/dx_x with
 // W = (v_1..v_DIM, theta = p / rho).
+// mu(T) / mu by Sutherland's law (Eq. sutherland): c1 th^1.5 / (th + s) with
+// th = (p / rho) / rt_ref, c1 = 1 + s, irt = 1 / rt_ref
+template <typename real>
+__device__ __forceinline__ real sutherland_ratio(real p_over_rho, real s, real c1, real irt) {
+  const real th = p_over_rho * irt;
+  return c1 * th * RealOps<real>::sqrt_(th) * RealOps<real>::rcp(th + s);
+}
+
 template <typename real, int DIM>
 __device__ __forceinline__ void viscous_flux(const real (*g)[DIM + 1], const real* v, real mu,
                                              real kap, real (*fv)[DIM + 1]) {

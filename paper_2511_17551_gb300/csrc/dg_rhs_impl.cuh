@@ -4,7 +4,8 @@
 //
 // The right-hand-side kernel comes in two flavours: FL = 1 fixes the production flux
 // pair at compile time (Ranocha volume flux for one gas, Ducros for mixtures; LLF at
-// interfaces and subcells), FL = 0 switches on the runtime choice (every other pair).
+// interfaces and subcells, constant viscosity), FL = 0 switches on the runtime choice
+// (every other pair, and Sutherland's law).
 // A translation unit that defines DG_GENERIC_ONLY emits only the FL = 0 kernels (and
 // its own basis table); the other one emits everything else and forwards non-production
 // pairs to DG_GENERIC_RHS.  The split keeps register pressure of the production kernel
@@ -31,6 +32,7 @@ __constant__ BasisTab<real> c_tab[DG_MAXN + 1];
 struct KConst {
   real gamma, gm1, inv_gm1, mu, kap, visc, rkA, rkB;
   real pref, eref;  // pressure offset of the momentum fluxes and pref / (gamma - 1)
+  real suth_s, suth_c1, suth_irt;  // Sutherland's law: s, 1 + s, 1 / rt_ref (s = 0: off)
 };
 
 inline KConst make_kconst(const DgArgs& a) {
@@ -45,6 +47,9 @@ inline KConst make_kconst(const DgArgs& a) {
   k.rkB = (real)a.rkB;
   k.pref = (real)a.pref;
   k.eref = (real)(a.pref / (a.gamma - 1.0));
+  k.suth_s = (real)a.suth_s;
+  k.suth_c1 = (real)(1.0 + a.suth_s);
+  k.suth_irt = (real)(a.suth_rt > 0.0 ? 1.0 / a.suth_rt : 0.0);
   return k;
 }
 
@@ -229,7 +234,11 @@ __device__ __forceinline__ int outer_state(const DgArgs& a, const KConst& kc, in
 
 // ------------------------------------------------------------------ main RHS / RK kernel
 template <int DIM, int N, int NSP, bool NS, int FL>
-__global__ void __launch_bounds__(Layout<DIM, N, NSP, NS>::THREADS, Layout<DIM, N, NSP, NS>::MINB)
+// the runtime-choice kernel (FL = 0) carries more live branches: at most 5 CTAs per SM
+// (up to 136 registers a thread at 96 threads) instead of 8, so that it does not spill
+__global__ void __launch_bounds__(Layout<DIM, N, NSP, NS>::THREADS,
+                                  FL ? Layout<DIM, N, NSP, NS>::MINB
+                                     : (Layout<DIM, N, NSP, NS>::MINB > 5 ? 5 : Layout<DIM, N, NSP, NS>::MINB))
 rhs_kernel(const DgArgs a, const KConst kc) {
   using S = Shape<DIM, N>;
   using L = Layout<DIM, N, NSP, NS>;
@@ -347,7 +356,13 @@ rhs_kernel(const DgArgs a, const KConst kc) {
         for (int x = 0; x < DIM; ++x)
 #pragma unroll
           for (int c = 0; c <= DIM; ++c) gg[x][c] = gi[(x * (DIM + 1) + c) * NP];
-        viscous_flux<real, DIM>(gg, vv, kc.mu, kc.kap, fv);
+        real mu_n = kc.mu, kap_n = kc.kap;
+        if (!FL && kc.suth_s > real(0)) {
+          const real r = sutherland_ratio(p * RealOps<real>::rcp(rho), kc.suth_s, kc.suth_c1, kc.suth_irt);
+          mu_n *= r;
+          kap_n *= r;
+        }
+        viscous_flux<real, DIM>(gg, vv, mu_n, kap_n, fv);
 #pragma unroll
         for (int d = 0; d < DIM; ++d)
 #pragma unroll
@@ -601,7 +616,13 @@ rhs_kernel(const DgArgs a, const KConst kc) {
       for (int xx = 0; xx < DIM; ++xx)
 #pragma unroll
         for (int c = 0; c <= DIM; ++c) gg[xx][c] = nbg[it][(xx * (DIM + 1) + c) % NG];
-      viscous_flux<real, DIM>(gg, x.v, kc.mu, kc.kap, fvn);
+      real mu_n = kc.mu, kap_n = kc.kap;
+      if (!FL && kc.suth_s > real(0)) {
+        const real r = sutherland_ratio(x.p * RealOps<real>::rcp(x.rho), kc.suth_s, kc.suth_c1, kc.suth_irt);
+        mu_n *= r;
+        kap_n *= r;
+      }
+      viscous_flux<real, DIM>(gg, x.v, mu_n, kap_n, fvn);
 #pragma unroll
       for (int c = 0; c <= DIM; ++c) {
         real nbr_n = 0;
@@ -706,6 +727,7 @@ rhs_kernel(const DgArgs a, const KConst kc) {
         }
         la *= ij;
         lv *= ij * ij * kc.visc * ir;
+        if (!FL && kc.suth_s > real(0)) lv *= sutherland_ratio(p * ir, kc.suth_s, kc.suth_c1, kc.suth_irt);
         if (!(p > real(0)) || !isfinite(la)) {
           latch_status(a.status, DG_ST_NONPHYS, e0 + e);
           la = real(0);
@@ -1049,9 +1071,9 @@ __global__ void lambda_kernel(const DgArgs a, const KConst kc, int slot) {
       v[d] = uu[(NSP + d) * np] * ir;
       ke += uu[(NSP + d) * np] * v[d];
     }
-    real c;
+    real c, p = 0;
     if (NSP == 1) {
-      real p = kc.gm1 * (uu[(NSP + DIM) * np] - real(0.5) * ke);
+      p = kc.gm1 * (uu[(NSP + DIM) * np] - real(0.5) * ke);
       c = RealOps<real>::sqrt_(kc.gamma * p * ir);
     } else {
       c = ((const real*)a.pc)[(e * 2 + 1) * np + node];
@@ -1070,6 +1092,7 @@ __global__ void lambda_kernel(const DgArgs a, const KConst kc, int slot) {
     }
     la *= ij;
     lv *= ij * ij * kc.visc * ir;
+    if (NSP == 1 && kc.suth_s > real(0)) lv *= sutherland_ratio(p * ir, kc.suth_s, kc.suth_c1, kc.suth_irt);
     if (!isfinite(la)) la = real(0);
     la_m = fmax(la_m, la);
     lv_m = fmax(lv_m, lv);
@@ -1084,7 +1107,7 @@ __global__ void lambda_kernel(const DgArgs a, const KConst kc, int slot) {
 }
 
 // ------------------------------------------------------------------ shock indicator
-// Hennemann-Gassner modal energy of rho*p, one thread per element.
+// Hennemann-Gassner modal energy of rho*p (or of p), one thread per element.
 template <int DIM, int N, int NSP>
 __global__ void indicator_kernel(const DgArgs a, const KConst kc, real alpha_max, real* alpha_raw) {
   using S = Shape<DIM, N>;
@@ -1108,7 +1131,7 @@ __global__ void indicator_kernel(const DgArgs a, const KConst kc, real alpha_max
     } else {
       p = ((const real*)a.pc)[(e * 2) * NP + node];
     }
-    f[node] = rho * p;
+    f[node] = a.ind_var ? p : rho * p;
   }
   // modal coefficients: V^{-1} along each direction
 #pragma unroll
@@ -1224,7 +1247,8 @@ cudaError_t launch_ind_t(const DgArgs& a, double amax, void* out, cudaStream_t s
 
 cudaError_t DG_CAT(DG_PREFIX, _rhs)(const DgArgs& a, cudaStream_t st) {
 #ifndef DG_GENERIC_ONLY
-  const bool production = a.sf == DG_SF_LLF && a.vf == (a.nsp == 1 ? DG_VF_RANOCHA : DG_VF_DUCROS);
+  const bool production = a.sf == DG_SF_LLF && a.vf == (a.nsp == 1 ? DG_VF_RANOCHA : DG_VF_DUCROS) &&
+                          !(a.suth_s > 0.0);
   if (!production) return DG_GENERIC_RHS(a, st);
 #endif
   if (a.dim == 3 && a.nsp == 1 && a.ns) { DG_DISPATCH_N(DG_RHS_CALL, 3, 1, true) }
