@@ -27,6 +27,13 @@
  * Sutherland's law, Eq. sutherland, when it is on); interface viscous flux
  * = average of both sides' f^v, dotted with the face normal; it enters as
  * + (1/J)[D Fv + M^{-1} B (Fv* - Fv)].
+ * Viscous boundaries (weakly, through W* and Fv*; reading of the boundary paragraph of the
+ * numerical-results section): supersonic inflow W* = (W + W_ext)/2, Fv* = mean of f^v of
+ * the interior gradient with the interior and with the external state; outflow W* = W,
+ * Fv* = f^v; no-slip walls W* = (0, theta) (adiabatic) or (0, theta_wall) (isothermal),
+ * Fv* = f^v of the interior gradient at wall velocity 0, with the heat flux set to 0 on an
+ * adiabatic wall.  The advective part of a no-slip wall is the slip-wall flux (mirrored
+ * normal velocity through the Riemann solver); Navier-Stokes slip walls are not modelled.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -95,7 +102,9 @@ static int check_mesh(const or_problem* P) {
       } else {
         int64_t bc = -(nb + 1);
         if (bc >= P->n_bc) return 1;
-        if (P->equations == OR_NAVIER_STOKES) return 1; /* viscous BCs are not modelled */
+        int kind = P->bc_kind[bc];
+        if (kind < OR_BC_INFLOW || kind > OR_BC_ISOTHERMAL) return 1;
+        if (P->equations == OR_NAVIER_STOKES && (kind == OR_BC_SLIP_WALL || P->n_species > 0)) return 1;
       }
     }
   return 0;
@@ -117,7 +126,7 @@ static int boundary_state(const or_problem* P, const basis* b, int bc, const dou
     *qg = *qo;
     return 1;
   }
-  /* slip wall: mirror the normal velocity */
+  /* slip and no-slip walls: mirror the normal velocity */
   double nn = 0.0, vn = 0.0;
   for (int d = 0; d < b->dim; ++d) nn += n[d] * n[d];
   nn = sqrt(nn);
@@ -235,6 +244,32 @@ static void node_W(const or_problem* P, const basis* b, const double* u, int64_t
   W[b->dim] = q.p / q.rho;
 }
 
+/* primitive external state of boundary id bc (from its primitive description) */
+static void bc_prim_state(const or_problem* P, const basis* b, int bc, or_prim* q, int* err) {
+  double ug[OR_MAX_NV];
+  or_prim_to_cons(P, P->bc_prim + (size_t)bc * b->nv, ug);
+  if (or_cons_to_prim(P, ug, q)) *err = 1;
+}
+
+/* BR1 boundary value W* at a boundary face node with interior value Wn */
+static void boundary_W(const or_problem* P, const basis* b, int bc, const double* Wn, double* Ws,
+                       int* err) {
+  int dim = b->dim, kind = P->bc_kind[bc];
+  or_prim qe;
+  for (int c = 0; c <= dim; ++c) Ws[c] = Wn[c];
+  if (kind == OR_BC_INFLOW) {
+    bc_prim_state(P, b, bc, &qe, err);
+    for (int d = 0; d < dim; ++d) Ws[d] = 0.5 * (Wn[d] + qe.v[d]);
+    Ws[dim] = 0.5 * (Wn[dim] + qe.p / qe.rho);
+  } else if (kind == OR_BC_NOSLIP_ADIABATIC || kind == OR_BC_ISOTHERMAL) {
+    for (int d = 0; d < dim; ++d) Ws[d] = 0.0;
+    if (kind == OR_BC_ISOTHERMAL) {
+      bc_prim_state(P, b, bc, &qe, err);
+      Ws[dim] = qe.p / qe.rho;
+    }
+  }
+}
+
 static int br1_gradients(const or_problem* P, const basis* b, const double* u, double* G) {
   int dim = b->dim, nW = dim + 1, np = b->np, N = b->N;
   int err = 0;
@@ -256,12 +291,17 @@ static int br1_gradients(const or_problem* P, const basis* b, const double* u, d
           int f = 2 * d + side;
           if (pos != (side ? N : 0)) continue;
           int64_t nb = P->nbr_elem[k * b->nf + f];
-          double Wx[4];
-          node_W(P, b, u, nb, nbr_node(b, f, node), Wx, &err);
+          double Ws[4];
+          if (nb >= 0) {
+            double Wx[4];
+            node_W(P, b, u, nb, nbr_node(b, f, node), Wx, &err);
+            for (int c = 0; c < nW; ++c) Ws[c] = 0.5 * (Wn[c] + Wx[c]);
+          } else {
+            boundary_W(P, b, (int)(-(nb + 1)), Wn, Ws, &err);
+          }
           for (int c = 0; c < nW; ++c) {
-            double Ws = 0.5 * (Wn[c] + Wx[c]);
-            if (side) Q[d][c] += (Ws - Wn[c]) / b->w[N];
-            else Q[d][c] -= (Ws - Wn[c]) / b->w[0];
+            if (side) Q[d][c] += (Ws[c] - Wn[c]) / b->w[N];
+            else Q[d][c] -= (Ws[c] - Wn[c]) / b->w[0];
           }
         }
       }
@@ -476,9 +516,25 @@ int or_rhs(const or_problem* P, const double* u, double* rhs, double* alpha_out,
             node_u(&b, u, k, node, uu);
             or_cons_to_prim(P, uu, &q);
             visc_flux(P, &b, G, k, node, &q, fo);
-            node_u(&b, u, nb, mn, uu);
-            or_cons_to_prim(P, uu, &q);
-            visc_flux(P, &b, G, nb, mn, &q, fx);
+            int kind = nb >= 0 ? 0 : P->bc_kind[-(nb + 1)];
+            if (nb >= 0) {
+              node_u(&b, u, nb, mn, uu);
+              or_cons_to_prim(P, uu, &q);
+              visc_flux(P, &b, G, nb, mn, &q, fx);
+            } else if (kind == OR_BC_INFLOW) {
+              or_prim qe;
+              bc_prim_state(P, &b, (int)(-(nb + 1)), &qe, &err);
+              visc_flux(P, &b, G, k, node, &qe, fx);    /* interior gradient, external state */
+            } else if (kind == OR_BC_OUTFLOW) {
+              memcpy(fx, fo, sizeof(fx));
+            } else {                                     /* no-slip walls: wall velocity 0 */
+              or_prim qw = q;
+              for (int c = 0; c < dim; ++c) qw.v[c] = 0.0;
+              visc_flux(P, &b, G, k, node, &qw, fx);
+              if (kind == OR_BC_NOSLIP_ADIABATIC)
+                for (int x = 0; x < dim; ++x) fx[x][1 + dim] = 0.0;
+              memcpy(fo, fx, sizeof(fx));               /* Fv* = the wall flux itself */
+            }
             node_metric(P, &b, k, d, node, n);
             for (int v = 0; v < nv; ++v) {
               double Fs = 0.0;

@@ -32,7 +32,10 @@ enum { OR_EULER = 0, OR_NAVIER_STOKES = 1 };
 enum { OR_VF_RANOCHA = 0, OR_VF_DUCROS = 1, OR_VF_CENTRAL = 2, OR_VF_KG = 3, OR_VF_PIROZZOLI = 4,
        OR_VF_MORINISHI = 5 };
 enum { OR_SF_LLF = 0, OR_SF_HLLC = 1, OR_SF_EC = 2, OR_SF_HLL = 3 };
-enum { OR_BC_INFLOW = 1, OR_BC_OUTFLOW = 2, OR_BC_SLIP_WALL = 3 };
+/* no-slip walls: the advective part is the slip-wall flux, the no-slip condition enters
+ * through the viscous terms; isothermal walls take T_wall from the bc state's p / rho */
+enum { OR_BC_INFLOW = 1, OR_BC_OUTFLOW = 2, OR_BC_SLIP_WALL = 3, OR_BC_NOSLIP_ADIABATIC = 4,
+       OR_BC_ISOTHERMAL = 5 };
 
 typedef struct {
   int dim, N;
