@@ -67,7 +67,16 @@ enum { DG_SF_LLF = 0, DG_SF_HLLC = 1, DG_SF_EC = 2,
        DG_SF_HLL = 3 };
 enum { DG_FP64 = 0, DG_MIXED = 1 };
 enum { DG_THERMO_NEWTON = 0, DG_THERMO_MLP = 1 };
-enum { DG_BC_INFLOW = 1, DG_BC_OUTFLOW = 2, DG_BC_SLIP_WALL = 3 };
+/* boundary kinds (weak, through the numerical fluxes).  Inflow: advective flux f(u_ext).n;
+ * outflow: f(u).n; walls: the mirror state (normal velocity reversed) through the Riemann
+ * solver.  Navier-Stokes adds the BR1 boundary value W* of W = (v, p/rho) and the viscous
+ * boundary flux Fv*: inflow W* = (W + W_ext)/2, Fv* = mean of f^v of the interior gradient
+ * with the interior and with the external state; outflow W* = W, Fv* = f^v; no-slip walls
+ * W* = (0, p/rho) (adiabatic) or (0, T_wall) (isothermal, T_wall = p/rho of the id's
+ * bc_prim state), Fv* = f^v of the interior gradient at zero velocity, heat flux 0 on an
+ * adiabatic wall.  DG_BC_SLIP_WALL is Euler-only. */
+enum { DG_BC_INFLOW = 1, DG_BC_OUTFLOW = 2, DG_BC_SLIP_WALL = 3, DG_BC_NOSLIP_ADIABATIC = 4,
+       DG_BC_ISOTHERMAL = 5 };
 
 typedef struct {
   int dim;                  /* 2 or 3 */
@@ -81,7 +90,7 @@ typedef struct {
 } dg_mesh_desc;
 
 typedef struct {
-  int equations;            /* DG_EULER | DG_NAVIER_STOKES (one gas, periodic only) */
+  int equations;            /* DG_EULER | DG_NAVIER_STOKES (one gas; no slip walls) */
   int n_species;            /* 0: one calorically perfect gas; 1..8: mixture */
   double gamma;             /* ratio of specific heats (one gas) */
   double mu, Pr;            /* Navier-Stokes: dynamic viscosity, Prandtl number */

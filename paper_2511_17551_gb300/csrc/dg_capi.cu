@@ -17,6 +17,7 @@ struct dg_ctx {
   int dim, N, np, nv, nsp, nf;
   int64_t K;
   int equations, n_species, vf, sf, precision, thermo, n_bc;
+  int has_bnd;  // the mesh has boundary faces
   double gamma, mu, Pr, alpha_max, p_ref, pos_eps;
   double suth_s, suth_rt;
   int ind_var;
@@ -328,6 +329,7 @@ DgArgs base_args(dg_ctx* c) {
   a.nv = c->nv;
   a.np = c->np;
   a.n_bc = c->n_bc;
+  a.has_bnd = c->has_bnd;
   a.vf = c->vf;
   a.sf = c->sf;
   a.ns = c->equations == DG_NAVIER_STOKES;
@@ -560,9 +562,12 @@ dg_status dg_init_mesh(const dg_mesh_desc* m, const dg_physics_desc* p, dg_ctx**
   const int dim = m->dim, nf = 2 * dim, N = m->N;
   const int64_t K = m->K;
   for (int b = 0; b < p->n_bc; ++b)
-    if (p->bc_kind[b] < DG_BC_INFLOW || p->bc_kind[b] > DG_BC_SLIP_WALL) return DG_EINVAL;
+    if (p->bc_kind[b] < DG_BC_INFLOW || p->bc_kind[b] > DG_BC_ISOTHERMAL ||
+        (p->equations == DG_NAVIER_STOKES && p->bc_kind[b] == DG_BC_SLIP_WALL))
+      return DG_EINVAL;
   int* nbr_h = (int*)malloc(sizeof(int) * K * nf);
   if (!nbr_h) return DG_ENOMEM;
+  bool any_bnd = false;
   for (int64_t k = 0; k < K; ++k)
     for (int f = 0; f < nf; ++f) {
       const int64_t nb = m->nbr_elem[k * nf + f];
@@ -571,13 +576,14 @@ dg_status dg_init_mesh(const dg_mesh_desc* m, const dg_physics_desc* p, dg_ctx**
         ok = nb < K && m->nbr_face[k * nf + f] == (f ^ 1) &&
              (!m->nbr_orient || m->nbr_orient[k * nf + f] == 0);
       } else {
-        ok = -(nb + 1) < p->n_bc && p->equations != DG_NAVIER_STOKES;
+        ok = -(nb + 1) < p->n_bc;
       }
       if (!ok) {
         free(nbr_h);
         return DG_EINVAL;
       }
       nbr_h[k * nf + f] = (int)nb;
+      any_bnd |= nb < 0;
     }
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {
@@ -601,6 +607,7 @@ dg_status dg_init_mesh(const dg_mesh_desc* m, const dg_physics_desc* p, dg_ctx**
   c->precision = p->precision;
   c->thermo = p->thermo;
   c->n_bc = p->n_bc;
+  c->has_bnd = any_bnd ? 1 : 0;
   c->gamma = p->gamma;
   c->p_ref = p->p_ref;
   c->pos_eps = p->positivity_eps;

@@ -17,6 +17,7 @@ struct DgArgs {
   int64_t K;
   int dim, N, nsp, nv, np;
   int n_bc;
+  int has_bnd;            // the mesh has boundary faces
   int vf, sf;             // DG_VF_*, DG_SF_*
   int mode;               // 0: write rhs, 1: RK stage
   int stage;              // RK stage 0..4

@@ -216,7 +216,7 @@ __device__ __forceinline__ int outer_state(const DgArgs& a, const KConst& kc, in
   }
   x = own;
   if (kind == DG_BC_OUTFLOW) return 1;
-  // slip wall: mirror the normal velocity
+  // slip and no-slip walls: mirror the normal velocity (no-slip enters through the viscous terms)
   real nn = 0, vn = 0;
 #pragma unroll
   for (int d = 0; d < DIM; ++d) {
@@ -567,6 +567,12 @@ rhs_kernel(const DgArgs a, const KConst kc) {
 #pragma unroll
           for (int c = 0; c < NG; ++c) nbg[it][c] = gn[c * NP];
         }
+      } else if (NS) {
+        // boundary face: the interior gradient at the own face node
+        const int onode = S::line_base(d, m) + (side ? N : 0) * S::stride(d);
+        const real* gn = (const real*)a.gradW + (e0 + e) * L::NFV * NP + onode;
+#pragma unroll
+        for (int c = 0; c < NG; ++c) nbg[it][c] = gn[c * NP];
       }
     }
   }
@@ -608,8 +614,17 @@ rhs_kernel(const DgArgs a, const KConst kc) {
     else surface_flux<real, DIM, NSP>(sf, x, o, nface, kc.inv_gm1, kc.pref, Fs);
 #pragma unroll
     for (int k = 0; k < NV; ++k) sa[k * NP] += iw * Fs[k];
-    if (NS) {
-      // viscous interface flux: mean of both sides' f^v . n, lifted as (Fv* - Fv)
+    const int bkind = nb >= 0 ? 0 : a.bc_kind[-(nb + 1)];
+    if (NS && bkind != DG_BC_OUTFLOW) {
+      // viscous interface flux: mean of both sides' f^v . n (inflow: the interior gradient
+      // with the external state), lifted as (Fv* - Fv); no-slip walls: Fv* is the wall flux
+      // of the interior gradient at zero velocity (no heat flux on an adiabatic wall)
+      const bool wall = bkind == DG_BC_NOSLIP_ADIABATIC || bkind == DG_BC_ISOTHERMAL;
+      if (wall) {
+        x = o;
+#pragma unroll
+        for (int c = 0; c < DIM; ++c) x.v[c] = real(0);
+      }
       const real* fvd = sfv + e * L::SFV + d * (DIM + 1) * NP + node;
       real gg[DIM][DIM + 1], fvn[DIM][DIM + 1];
 #pragma unroll
@@ -623,12 +638,16 @@ rhs_kernel(const DgArgs a, const KConst kc) {
         kap_n *= r;
       }
       viscous_flux<real, DIM>(gg, x.v, mu_n, kap_n, fvn);
+      if (wall && bkind == DG_BC_NOSLIP_ADIABATIC) {
+#pragma unroll
+        for (int xx = 0; xx < DIM; ++xx) fvn[xx][DIM] = real(0);
+      }
 #pragma unroll
       for (int c = 0; c <= DIM; ++c) {
         real nbr_n = 0;
 #pragma unroll
         for (int xx = 0; xx < DIM; ++xx) nbr_n += fvn[xx][c] * nface[xx];
-        sa[(NSP + c) * NP] -= iw * (real(0.5) * (nbr_n - fvd[c * NP]));
+        sa[(NSP + c) * NP] -= iw * (wall ? nbr_n - fvd[c * NP] : real(0.5) * (nbr_n - fvd[c * NP]));
       }
     }
   }
@@ -1006,7 +1025,11 @@ gradient_kernel(const DgArgs a, const KConst kc) {
       const int f = 2 * d + side;
       const int nnode = base + (side ? 0 : N) * s;
       const int nb = a.nbr[eg * 2 * DIM + f];
-      const real* un = gu + (int64_t)nb * NV * NP + nnode;
+      const int i = side ? N : 0;
+      // boundary faces get their lifting from boundary_lift_kernel: here a valid address
+      // (the own element) and a zero weight, without a branch
+      const real* un = gu + (int64_t)(nb >= 0 ? nb : eg) * NV * NP + nnode;
+      const real keep = nb >= 0 ? real(1) : real(0);
       real rn = 0;
 #pragma unroll
       for (int k = 0; k < NSP; ++k) rn += un[k * NP];
@@ -1017,12 +1040,11 @@ gradient_kernel(const DgArgs a, const KConst kc) {
         ke += un[(NSP + c) * NP] * Wn[c];
       }
       Wn[DIM] = kc.gm1 * (un[(NSP + DIM) * NP] - real(0.5) * ke) * irn;
-      const int i = side ? N : 0;
 #pragma unroll
       for (int c = 0; c < NW; ++c) {
         real ws = real(0.5) * (Wl[i][c] + Wn[c]);
-        if (side) G[N][c] += B.iw[N] * (ws - Wl[N][c]);
-        else G[0][c] -= B.iw[0] * (ws - Wl[0][c]);
+        if (side) G[N][c] += keep * B.iw[N] * (ws - Wl[N][c]);
+        else G[0][c] -= keep * B.iw[0] * (ws - Wl[0][c]);
       }
     }
     real* g = sg + e * L::SG + d * NW * NP;
@@ -1047,6 +1069,81 @@ gradient_kernel(const DgArgs a, const KConst kc) {
         out[((e0 + e) * DIM + x) * NW * NP + c * NP + node] = acc * ij;
       }
   }
+}
+
+// BR1 lifting at boundary faces (Eq. auxstrongf with the boundary value W* in place of
+// the interface mean): adds (1/J) sum_d Ja^d (+-1/w) (W* - W) to the gradient of every
+// boundary face node; one thread per node, so that a node on several boundary faces (an
+// edge or corner) sums its faces in one place.  Launched after gradient_kernel only for
+// meshes with boundary faces.  W*: inflow (W + W_ext)/2, outflow W, no-slip walls
+// (0, theta) or (0, theta_wall).
+template <int DIM, int N, int NSP>
+__global__ void boundary_lift_kernel(const DgArgs a, const KConst kc) {
+  using S = Shape<DIM, N>;
+  constexpr int NV = NSP + DIM + 1, NP = S::NP, N1 = S::N1, NW = DIM + 1;
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= a.K * NP) return;
+  const int64_t e = i / NP;
+  const int node = (int)(i % NP);
+  const int* nbr = a.nbr + e * 2 * DIM;
+  bool any = false;
+#pragma unroll
+  for (int f = 0; f < 2 * DIM; ++f) {
+    const int pos = (node / S::stride(f >> 1)) % N1;
+    any |= nbr[f] < 0 && pos == ((f & 1) ? N : 0);
+  }
+  if (!any) return;
+  const BasisTab<real>& B = c_tab[N];
+  auto W_of = [&](const real* u, int64_t st, real* W) {
+    real rho = 0;
+#pragma unroll
+    for (int k = 0; k < NSP; ++k) rho += u[k * st];
+    const real ir = RealOps<real>::rcp(rho);
+    real ke = 0;
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) {
+      W[c] = u[(NSP + c) * st] * ir;
+      ke += u[(NSP + c) * st] * W[c];
+    }
+    W[DIM] = kc.gm1 * (u[(NSP + DIM) * st] - real(0.5) * ke) * ir;
+  };
+  real W[NW];
+  W_of((const real*)a.u + e * NV * NP + node, NP, W);
+  real dQ[DIM][NW];
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) {
+#pragma unroll
+    for (int c = 0; c < NW; ++c) dQ[d][c] = real(0);
+    const int pos = (node / S::stride(d)) % N1;
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+      const int nb = nbr[2 * d + side];
+      if (nb >= 0 || pos != (side ? N : 0)) continue;
+      const int bc = -(nb + 1), kind = a.bc_kind[bc];
+      real We[NW], Ws[NW];
+      W_of((const real*)a.bc_u + (int64_t)bc * NV, 1, We);
+#pragma unroll
+      for (int c = 0; c < NW; ++c) {
+        if (kind == DG_BC_INFLOW) Ws[c] = real(0.5) * (W[c] + We[c]);
+        else if (kind == DG_BC_NOSLIP_ADIABATIC) Ws[c] = c < DIM ? real(0) : W[c];
+        else if (kind == DG_BC_ISOTHERMAL) Ws[c] = c < DIM ? real(0) : We[c];
+        else Ws[c] = W[c];
+        dQ[d][c] += side ? B.iw[N] * (Ws[c] - W[c]) : -B.iw[0] * (Ws[c] - W[c]);
+      }
+    }
+  }
+  const real ij = ((const real*)a.invJ)[e * NP + node];
+  const real* ja = (const real*)a.Ja + e * DIM * DIM * NP + node;
+  real* g = (real*)a.gradW + e * DIM * NW * NP + node;
+#pragma unroll
+  for (int x = 0; x < DIM; ++x)
+#pragma unroll
+    for (int c = 0; c < NW; ++c) {
+      real acc = 0;
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) acc += ja[(d * DIM + x) * NP] * dQ[d][c];
+      g[(x * NW + c) * NP] += acc * ij;
+    }
 }
 
 // ------------------------------------------------------------------ wave speeds (dt)
@@ -1199,6 +1296,10 @@ cudaError_t launch_grad_t(const DgArgs& a, cudaStream_t st) {
   if (err != cudaSuccess) return err;
   const int64_t grid = (a.K + L::EPB - 1) / L::EPB;
   k<<<(unsigned)grid, L::THREADS, smem, st>>>(a, make_kconst(a));
+  err = cudaGetLastError();
+  if (err != cudaSuccess || !a.has_bnd) return err;
+  const int64_t nn = a.K * Shape<DIM, N>::NP;
+  boundary_lift_kernel<DIM, N, NSP><<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(a, make_kconst(a));
   return cudaGetLastError();
 }
 
