@@ -474,6 +474,28 @@ def run_other_shapes(args, stream_ptr, world):
         blk[name] = {"value": world * dof * 5 * n / wall, "ms_per_step": wall * 1e3 / n, "steps": n,
                      "device_ms_per_step_by_kernel": per}
     out["tgv_ns_16^3_N7"] = blk
+    # supersonic TGV 32^3, N = 7: Sutherland's law, pressure-indicator blending, positivity
+    n_el, N = 32, 7
+    xi, _ = dg.dg_lgl_nodes(N)
+    xyz, nbr, face = W.box_mesh((n_el,) * 3, xi, (-np.pi,) * 3, (np.pi,) * 3, periodic=True)
+    w0 = W.supersonic_tgv_primitive(xyz)
+    dof = xyz.shape[0] * (N + 1) ** 3 * 5
+    phys = W.supersonic_tgv_physics()
+    blk = {"workload": "supersonic_tgv_32^3_N7", "dof": dof, "mach": 1.25, "Re": 1600,
+           "alpha_max": 0.5, "positivity_eps": 1e-8, "cfl": 0.4}
+    for name, prec, n in (("mixed", dg.DG_MIXED, 20), ("fp64", dg.DG_FP64, 3)):
+        s = dg.Solver(3, N, xyz, nbr, face, equations=dg.DG_NAVIER_STOKES, alpha_max=0.5,
+                      precision=prec, stream=stream_ptr, positivity_eps=1e-8, **phys)
+        s.set_primitive(w0)
+        try:
+            wall, per = timed(s, n, 0.4)
+            blk[name] = {"value": world * dof * 5 * n / wall, "ms_per_step": wall * 1e3 / n, "steps": n,
+                         "blended_elements": int((dg.dg_get_alpha(s.ctx, s.K) > 0).sum()),
+                         "device_ms_per_step_by_kernel": per}
+        except dg.DgError as e:
+            blk[name] = {"error": str(e)}
+        s.close()
+    out["supersonic_tgv_32^3_N7"] = blk
     # 2D Mach-3 square cylinder
     xi, _ = dg.dg_lgl_nodes(3)
     xyz, nbr, face = W.square_cylinder_mesh(xi)

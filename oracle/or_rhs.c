@@ -189,7 +189,9 @@ static int element_alpha_raw(const or_problem* P, const basis* b, const double* 
     }
     memcpy(m, t, sizeof(double) * np);
   }
-  double Etot = 0.0, E1 = 0.0, E2 = 0.0;
+  /* energy of all modes, of the modes up to degree N-1, and of the highest (degree N) and
+   * second-highest (degree N-1) modes, summed directly (no cancellation) */
+  double Etot = 0.0, E1 = 0.0, Eh1 = 0.0, Eh2 = 0.0;
   for (int node = 0; node < np; ++node) {
     int mx = 0;
     for (int d = 0; d < b->dim; ++d) {
@@ -199,10 +201,11 @@ static int element_alpha_raw(const or_problem* P, const basis* b, const double* 
     double e = m[node] * m[node];
     Etot += e;
     if (mx <= N - 1) E1 += e;
-    if (mx <= N - 2) E2 += e;
+    if (mx == N) Eh1 += e;
+    if (mx == N - 1) Eh2 += e;
   }
-  double frac1 = Etot > 0.0 ? (Etot - E1) / Etot : 0.0;
-  double frac2 = E1 > 0.0 ? (E1 - E2) / E1 : 0.0;
+  double frac1 = Etot > 0.0 ? Eh1 / Etot : 0.0;
+  double frac2 = E1 > 0.0 ? Eh2 / E1 : 0.0;
   double E = frac1 > frac2 ? frac1 : frac2;
   double thr = 0.5 * pow(10.0, -1.8 * pow(N + 1.0, 0.25));
   double s = log((1.0 - 1e-4) / 1e-4);
