@@ -794,14 +794,12 @@ __global__ void step_dt_kernel(const DgArgs a, int slot, int advance_time) {
 // pressure step u <- ubar + th2 (u - ubar), th2 = min over nodes of the root t in (0, 1)
 // of (E(t) - eps/(gamma-1)) rho(t) - |m(t)|^2/2 = 0.  Elements whose nodes are admissible
 // are only read.  An inadmissible mean latches a non-physical status.
+// FP64 passes for one element that may violate the bounds (whole warp)
 template <int DIM, int N>
-__global__ void __launch_bounds__(128) positivity_kernel(const DgArgs a, real* u, real* ulo, double eps,
-                                                         unsigned long long* nlim) {
+__device__ __forceinline__ void limit_element(const DgArgs& a, real* u, real* ulo, double eps,
+                                              unsigned long long* nlim, int64_t k, int lane) {
   using S = Shape<DIM, N>;
   constexpr int NP = S::NP, N1 = S::N1, NV = DIM + 2;
-  const int lane = threadIdx.x & 31;
-  const int64_t k = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  if (k >= a.K) return;
   const BasisTab<real>& B = c_tab[N];
   const double g1 = a.gamma - 1.0;
   real* ue = u + k * NV * NP;
@@ -819,23 +817,6 @@ __global__ void __launch_bounds__(128) positivity_kernel(const DgArgs a, real* u
     for (int d = 0; d < DIM; ++d) m2 += s[1 + d] * s[1 + d];
     return g1 * (s[1 + DIM] - 0.5 * m2 / s[0]);
   };
-  // pass 0, in the form's precision: can any node of the element be outside the bounds?
-  // (margins cover the rounding of the check itself and the low part of the state)
-  {
-    const real tol = sizeof(real) == 4 ? real(1e-6) : real(1e-14);
-    const real epsr = (real)eps;
-    bool viol = false;
-    for (int n = lane; n < NP; n += 32) {
-      const real r = ue[n], E = ue[(1 + DIM) * NP + n];
-      real m2 = 0;
-#pragma unroll
-      for (int d = 0; d < DIM; ++d) m2 += ue[(1 + d) * NP + n] * ue[(1 + d) * NP + n];
-      // with r > 0: p >= eps + margin  <=>  r (E - (eps + margin)/(gamma-1)) >= |m|^2 / 2
-      const real pbound = (epsr + tol * fabs(E)) * (real)(1.0 / g1);
-      viol = viol || !(r >= epsr * (real(1) + tol) && r * (E - pbound) >= real(0.5) * m2);
-    }
-    if (!__any_sync(0xffffffffu, viol)) return;
-  }
   // pass 1: mean, minima
   double acc[NV + 1], rmin = 1e300, pmin = 1e300;
 #pragma unroll
@@ -919,6 +900,44 @@ __global__ void __launch_bounds__(128) positivity_kernel(const DgArgs a, real* u
       for (int v = 0; v < NV; ++v) put(v, n, ub[v] + th2 * (val(v, n) - ub[v]));
   }
   if (lane == 0 && nlim) atomicAdd(nlim, 1ull);
+}
+
+// The limiter kernel: a warp screens EPW consecutive elements (about 128 nodes) in the
+// form's precision with all loads in flight (margins cover the rounding of the check and
+// the low part of the state), then runs the FP64 passes only for the flagged elements.
+template <int DIM, int N>
+__global__ void __launch_bounds__(128) positivity_kernel(const DgArgs a, real* u, real* ulo, double eps,
+                                                         unsigned long long* nlim) {
+  using S = Shape<DIM, N>;
+  constexpr int NP = S::NP, NV = DIM + 2;
+  constexpr int EPW = NP >= 128 ? 1 : 128 / NP;
+  static_assert(EPW <= 32, "flag mask");
+  const int lane = threadIdx.x & 31;
+  const int64_t k0 = ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5) * EPW;
+  if (k0 >= a.K) return;  // uniform per warp
+  const int ch = (int)((a.K - k0) < EPW ? (a.K - k0) : EPW) * NP;
+  const real tol = sizeof(real) == 4 ? real(1e-6) : real(1e-14);
+  const real epsr = (real)eps, igm1 = (real)(1.0 / (a.gamma - 1.0));
+  const real* ub = u + k0 * NV * NP;
+  unsigned flag = 0;
+#pragma unroll 4
+  for (int n = lane; n < ch; n += 32) {
+    const int el = n / NP, node = n - el * NP;
+    const real* ue = ub + el * NV * NP + node;
+    const real r = ue[0], E = ue[(1 + DIM) * NP];
+    real m2 = 0;
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) m2 += ue[(1 + d) * NP] * ue[(1 + d) * NP];
+    // with r > 0: p >= eps + margin  <=>  r (E - (eps + margin)/(gamma-1)) >= |m|^2 / 2
+    const real pbound = (epsr + tol * fabs(E)) * igm1;
+    if (!(r >= epsr * (real(1) + tol) && r * (E - pbound) >= real(0.5) * m2)) flag |= 1u << el;
+  }
+  flag = __reduce_or_sync(0xffffffffu, flag);
+  while (flag) {
+    const int el = __ffs(flag) - 1;
+    flag &= flag - 1;
+    limit_element<DIM, N>(a, u, ulo, eps, nlim, k0 + el, lane);
+  }
 }
 
 // ------------------------------------------------------------------ BR1 gradients
@@ -1204,18 +1223,25 @@ __global__ void lambda_kernel(const DgArgs a, const KConst kc, int slot) {
 }
 
 // ------------------------------------------------------------------ shock indicator
-// Hennemann-Gassner modal energy of rho*p (or of p), one thread per element.
+// Hennemann-Gassner modal energy of rho*p (or of p): one warp per element.  Node-parallel
+// coalesced loads, the tensor-product transform to orthonormal Legendre modes line by line
+// in the warp's shared-memory block, energies of all modes, of the modes up to degree N-1
+// and of the two highest degrees summed directly (no cancellation) and warp-reduced.
+constexpr int IND_WPB = 4;  // warps (elements) per CTA
 template <int DIM, int N, int NSP>
-__global__ void indicator_kernel(const DgArgs a, const KConst kc, real alpha_max, real* alpha_raw) {
+__global__ void __launch_bounds__(IND_WPB * 32) indicator_kernel(const DgArgs a, const KConst kc,
+                                                                  real alpha_max, real* alpha_raw) {
   using S = Shape<DIM, N>;
   constexpr int NP = S::NP, N1 = S::N1, NV = NSP + DIM + 1;
-  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (e >= a.K) return;
+  __shared__ real sf[IND_WPB][NP];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t e = (int64_t)blockIdx.x * IND_WPB + w;
+  if (e >= a.K) return;  // uniform per warp
   const BasisTab<real>& B = c_tab[N];
   const real* uu = (const real*)a.u + e * NV * NP;
-  real f[NP];
-#pragma unroll
-  for (int node = 0; node < NP; ++node) {
+  real* f = sf[w];
+#pragma unroll 4
+  for (int node = lane; node < NP; node += 32) {
     real rho = 0;
 #pragma unroll
     for (int k = 0; k < NSP; ++k) rho += uu[k * NP + node];
@@ -1230,36 +1256,50 @@ __global__ void indicator_kernel(const DgArgs a, const KConst kc, real alpha_max
     }
     f[node] = a.ind_var ? p : rho * p;
   }
-  // modal coefficients: V^{-1} along each direction
+  __syncwarp();
+  // modal coefficients: V^{-1} along each direction, one line per lane at a time
 #pragma unroll
   for (int d = 0; d < DIM; ++d) {
-    const int s = d == 0 ? 1 : (d == 1 ? N1 : N1 * N1);
-    real g[NP];
+    const int s = S::stride(d);
+#pragma unroll 1
+    for (int m = lane; m < S::LPD; m += 32) {
+      const int base = S::line_base(d, m);
+      real x[N1];
 #pragma unroll
-    for (int node = 0; node < NP; ++node) {
-      const int pos = (node / s) % N1, base = node - pos * s;
-      real acc = 0;
+      for (int l = 0; l < N1; ++l) x[l] = f[base + l * s];
 #pragma unroll
-      for (int l = 0; l < N1; ++l) acc += B.Vinv[pos * N1 + l] * f[base + l * s];
-      g[node] = acc;
+      for (int i = 0; i < N1; ++i) {
+        real acc = 0;
+#pragma unroll
+        for (int l = 0; l < N1; ++l) acc += B.Vinv[i * N1 + l] * x[l];
+        f[base + i * s] = acc;
+      }
     }
-#pragma unroll
-    for (int node = 0; node < NP; ++node) f[node] = g[node];
+    __syncwarp();
   }
-  real Et = 0, E1 = 0, E2 = 0;
-#pragma unroll
-  for (int node = 0; node < NP; ++node) {
+  real Et = 0, E1 = 0, Eh1 = 0, Eh2 = 0;
+#pragma unroll 4
+  for (int node = lane; node < NP; node += 32) {
     int mx = node % N1;
     if (DIM >= 2) mx = max(mx, (node / N1) % N1);
     if (DIM == 3) mx = max(mx, node / (N1 * N1));
-    real e2 = f[node] * f[node];
+    const real e2 = f[node] * f[node];
     Et += e2;
     if (mx <= N - 1) E1 += e2;
-    if (mx <= N - 2) E2 += e2;
+    if (mx == N) Eh1 += e2;
+    if (mx == N - 1) Eh2 += e2;
   }
-  real fr1 = Et > real(0) ? (Et - E1) / Et : real(0);
-  real fr2 = E1 > real(0) ? (E1 - E2) / E1 : real(0);
-  real E = fmax(fr1, fr2);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    Et += __shfl_xor_sync(0xffffffffu, Et, o);
+    E1 += __shfl_xor_sync(0xffffffffu, E1, o);
+    Eh1 += __shfl_xor_sync(0xffffffffu, Eh1, o);
+    Eh2 += __shfl_xor_sync(0xffffffffu, Eh2, o);
+  }
+  if (lane != 0) return;
+  const real fr1 = Et > real(0) ? Eh1 / Et : real(0);
+  const real fr2 = E1 > real(0) ? Eh2 / E1 : real(0);
+  const real E = fmax(fr1, fr2);
   const real thr = B.thr;
   const real sp = real(9.21024036697585);  // ln((1 - 1e-4) / 1e-4)
   real al = real(1) / (real(1) + exp(-(sp / thr) * (E - thr)));
@@ -1306,16 +1346,17 @@ cudaError_t launch_grad_t(const DgArgs& a, cudaStream_t st) {
 template <int DIM, int N>
 cudaError_t launch_pos_t(const DgArgs& a, void* u, void* ulo, double eps, unsigned long long* nlim,
                          cudaStream_t st) {
-  const int64_t grid = (a.K * 32 + 127) / 128;
+  constexpr int NP = Shape<DIM, N>::NP, EPW = NP >= 128 ? 1 : 128 / NP;
+  const int64_t warps = (a.K + EPW - 1) / EPW;
+  const int64_t grid = (warps * 32 + 127) / 128;
   positivity_kernel<DIM, N><<<(unsigned)grid, 128, 0, st>>>(a, (real*)u, (real*)ulo, eps, nlim);
   return cudaGetLastError();
 }
 
 template <int DIM, int N, int NSP>
 cudaError_t launch_ind_t(const DgArgs& a, double amax, void* out, cudaStream_t st) {
-  const int bs = 128;
-  const int64_t grid = (a.K + bs - 1) / bs;
-  indicator_kernel<DIM, N, NSP><<<(unsigned)grid, bs, 0, st>>>(a, make_kconst(a), (real)amax, (real*)out);
+  const int64_t grid = (a.K + IND_WPB - 1) / IND_WPB;
+  indicator_kernel<DIM, N, NSP><<<(unsigned)grid, IND_WPB * 32, 0, st>>>(a, make_kconst(a), (real)amax, (real*)out);
   return cudaGetLastError();
 }
 #endif  // DG_GENERIC_ONLY
