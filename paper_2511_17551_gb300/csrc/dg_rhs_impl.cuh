@@ -1223,46 +1223,77 @@ __global__ void lambda_kernel(const DgArgs a, const KConst kc, int slot) {
 }
 
 // ------------------------------------------------------------------ shock indicator
-// Hennemann-Gassner modal energy of rho*p (or of p): one warp per element.  Node-parallel
-// coalesced loads, the tensor-product transform to orthonormal Legendre modes line by line
-// in the warp's shared-memory block, energies of all modes, of the modes up to degree N-1
-// and of the two highest degrees summed directly (no cancellation) and warp-reduced.
-constexpr int IND_WPB = 4;  // warps (elements) per CTA
-template <int DIM, int N, int NSP>
-__global__ void __launch_bounds__(IND_WPB * 32) indicator_kernel(const DgArgs a, const KConst kc,
-                                                                  real alpha_max, real* alpha_raw) {
-  using S = Shape<DIM, N>;
-  constexpr int NP = S::NP, N1 = S::N1, NV = NSP + DIM + 1;
-  __shared__ real sf[IND_WPB][NP];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int64_t e = (int64_t)blockIdx.x * IND_WPB + w;
-  if (e >= a.K) return;  // uniform per warp
+// Hennemann-Gassner modal energy of rho*p (or of p).  The indicator quantity of every node
+// is formed during coalesced loads into shared memory; the tensor-product transform to
+// orthonormal Legendre modes runs line by line in place, and the energies of all modes, of
+// the modes up to degree N-1 and of the two highest degrees are summed directly (no
+// cancellation).  Small elements (NP <= 64): one thread per element on a padded row of the
+// CTA's block; larger ones: one warp per element (lines across lanes, warp reduction).
+template <int DIM, int N>
+struct IndShape {
+  static constexpr int NP = Shape<DIM, N>::NP;
+  static constexpr bool WARP = NP > 64;
+  static constexpr int EPC = WARP ? 4 : (sizeof(real) == 8 ? 64 : 128);  // elements per CTA
+  static constexpr int THREADS = WARP ? EPC * 32 : EPC;
+  static constexpr int ROW = WARP ? NP : NP + 1;  // padded rows: conflict-free per-thread access
+};
+
+template <int DIM, int N>
+__device__ __forceinline__ real indicator_alpha(real Et, real E1, real Eh1, real Eh2, real alpha_max) {
   const BasisTab<real>& B = c_tab[N];
-  const real* uu = (const real*)a.u + e * NV * NP;
-  real* f = sf[w];
-#pragma unroll 4
-  for (int node = lane; node < NP; node += 32) {
+  const real fr1 = Et > real(0) ? Eh1 / Et : real(0);
+  const real fr2 = E1 > real(0) ? Eh2 / E1 : real(0);
+  const real E = fmax(fr1, fr2);
+  const real thr = B.thr;
+  const real sp = real(9.21024036697585);  // ln((1 - 1e-4) / 1e-4)
+  real al = real(1) / (real(1) + exp(-(sp / thr) * (E - thr)));
+  if (al < real(1e-3)) al = real(0);
+  if (al > alpha_max) al = alpha_max;
+  return al;
+}
+
+template <int DIM, int N, int NSP>
+__global__ void __launch_bounds__(IndShape<DIM, N>::THREADS) indicator_kernel(const DgArgs a, const KConst kc,
+                                                                              real alpha_max, real* alpha_raw) {
+  using S = Shape<DIM, N>;
+  using I = IndShape<DIM, N>;
+  constexpr int NP = S::NP, N1 = S::N1, NV = NSP + DIM + 1, ROW = I::ROW;
+  __shared__ real sf[I::EPC * ROW];
+  const BasisTab<real>& B = c_tab[N];
+  const int tid = threadIdx.x;
+  const int64_t e0 = (int64_t)blockIdx.x * I::EPC;
+  const int ne = (int)((a.K - e0) < I::EPC ? (a.K - e0) : I::EPC);
+  const real* ub = (const real*)a.u + e0 * NV * NP;
+  // indicator quantity of every node of the CTA's elements (coalesced: nodes of a variable
+  // block are contiguous)
+  for (int i = tid; i < ne * NP; i += I::THREADS) {
+    const int el = i / NP, node = i - el * NP;
+    const real* uu = ub + el * NV * NP + node;
     real rho = 0;
 #pragma unroll
-    for (int k = 0; k < NSP; ++k) rho += uu[k * NP + node];
+    for (int k = 0; k < NSP; ++k) rho += uu[k * NP];
     real p;
     if (NSP == 1) {
       real ke = 0;
 #pragma unroll
-      for (int d = 0; d < DIM; ++d) ke += uu[(NSP + d) * NP + node] * uu[(NSP + d) * NP + node];
-      p = kc.gm1 * (uu[(NSP + DIM) * NP + node] - real(0.5) * ke * RealOps<real>::rcp(rho));
+      for (int d = 0; d < DIM; ++d) ke += uu[(NSP + d) * NP] * uu[(NSP + d) * NP];
+      p = kc.gm1 * (uu[(NSP + DIM) * NP] - real(0.5) * ke * RealOps<real>::rcp(rho));
     } else {
-      p = ((const real*)a.pc)[(e * 2) * NP + node];
+      p = ((const real*)a.pc)[((e0 + el) * 2) * NP + node];
     }
-    f[node] = a.ind_var ? p : rho * p;
+    sf[el * ROW + node] = a.ind_var ? p : rho * p;
   }
-  __syncwarp();
-  // modal coefficients: V^{-1} along each direction, one line per lane at a time
+  __syncthreads();
+  // worker: a thread (small elements) or a warp (large ones) per element
+  const int lane = I::WARP ? (tid & 31) : 0, step = I::WARP ? 32 : 1;
+  const int el = I::WARP ? (tid >> 5) : tid;
+  if (el >= ne) return;
+  real* f = sf + el * ROW;
 #pragma unroll
   for (int d = 0; d < DIM; ++d) {
     const int s = S::stride(d);
 #pragma unroll 1
-    for (int m = lane; m < S::LPD; m += 32) {
+    for (int m = lane; m < S::LPD; m += step) {
       const int base = S::line_base(d, m);
       real x[N1];
 #pragma unroll
@@ -1275,11 +1306,11 @@ __global__ void __launch_bounds__(IND_WPB * 32) indicator_kernel(const DgArgs a,
         f[base + i * s] = acc;
       }
     }
-    __syncwarp();
+    if (I::WARP) __syncwarp();
   }
   real Et = 0, E1 = 0, Eh1 = 0, Eh2 = 0;
 #pragma unroll 4
-  for (int node = lane; node < NP; node += 32) {
+  for (int node = lane; node < NP; node += step) {
     int mx = node % N1;
     if (DIM >= 2) mx = max(mx, (node / N1) % N1);
     if (DIM == 3) mx = max(mx, node / (N1 * N1));
@@ -1289,23 +1320,17 @@ __global__ void __launch_bounds__(IND_WPB * 32) indicator_kernel(const DgArgs a,
     if (mx == N) Eh1 += e2;
     if (mx == N - 1) Eh2 += e2;
   }
+  if (I::WARP) {
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    Et += __shfl_xor_sync(0xffffffffu, Et, o);
-    E1 += __shfl_xor_sync(0xffffffffu, E1, o);
-    Eh1 += __shfl_xor_sync(0xffffffffu, Eh1, o);
-    Eh2 += __shfl_xor_sync(0xffffffffu, Eh2, o);
+    for (int o = 16; o > 0; o >>= 1) {
+      Et += __shfl_xor_sync(0xffffffffu, Et, o);
+      E1 += __shfl_xor_sync(0xffffffffu, E1, o);
+      Eh1 += __shfl_xor_sync(0xffffffffu, Eh1, o);
+      Eh2 += __shfl_xor_sync(0xffffffffu, Eh2, o);
+    }
+    if (lane != 0) return;
   }
-  if (lane != 0) return;
-  const real fr1 = Et > real(0) ? Eh1 / Et : real(0);
-  const real fr2 = E1 > real(0) ? Eh2 / E1 : real(0);
-  const real E = fmax(fr1, fr2);
-  const real thr = B.thr;
-  const real sp = real(9.21024036697585);  // ln((1 - 1e-4) / 1e-4)
-  real al = real(1) / (real(1) + exp(-(sp / thr) * (E - thr)));
-  if (al < real(1e-3)) al = real(0);
-  if (al > alpha_max) al = alpha_max;
-  alpha_raw[e] = al;
+  alpha_raw[e0 + el] = indicator_alpha<DIM, N>(Et, E1, Eh1, Eh2, alpha_max);
 }
 
 // opt in to more than the default 48 KB (dynamic + static) of shared memory
@@ -1355,8 +1380,9 @@ cudaError_t launch_pos_t(const DgArgs& a, void* u, void* ulo, double eps, unsign
 
 template <int DIM, int N, int NSP>
 cudaError_t launch_ind_t(const DgArgs& a, double amax, void* out, cudaStream_t st) {
-  const int64_t grid = (a.K + IND_WPB - 1) / IND_WPB;
-  indicator_kernel<DIM, N, NSP><<<(unsigned)grid, IND_WPB * 32, 0, st>>>(a, make_kconst(a), (real)amax, (real*)out);
+  using I = IndShape<DIM, N>;
+  const int64_t grid = (a.K + I::EPC - 1) / I::EPC;
+  indicator_kernel<DIM, N, NSP><<<(unsigned)grid, I::THREADS, 0, st>>>(a, make_kconst(a), (real)amax, (real*)out);
   return cudaGetLastError();
 }
 #endif  // DG_GENERIC_ONLY
