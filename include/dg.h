@@ -269,8 +269,9 @@ dg_status dg_mlp_forward(const float* params, int n_out, const float* X, float* 
 /* Blending factors alpha [K] used by the last right-hand side (FP64, host). */
 dg_status dg_get_alpha(dg_ctx* ctx, double* alpha);
 
-/* BR1 gradients of (v, p/rho) from the last Navier-Stokes right-hand side,
- * [K][dim][dim+1][np] FP64 host. */
+/* BR1 gradients of (v, p/rho) (Eq. auxstrongf), [K][dim][dim+1][np] FP64 host: of the input
+ * of the last dg_rhs call, or, once dg_step_rk has run since, of the current state.
+ * DG_ESTATE before any Navier-Stokes right-hand side. Synchronises. */
 dg_status dg_get_gradients(dg_ctx* ctx, double* grad);
 
 /* Per-kernel device timing (tracing).  While enabled, every kernel launch of the

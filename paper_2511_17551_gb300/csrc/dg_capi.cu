@@ -45,6 +45,7 @@ struct dg_ctx {
   int diag_blocks;
   double* stage64;  // FP64 staging buffer for host <-> device state transfers
   bool have_state, have_grad, have_alpha;
+  bool grad_is_gradient;  // gradW holds the gradients of the last dg_rhs input (not fluxes)
   DgThermo th;  // mixtures
   // tracing: CUDA events around each launch while profiling is on
   int prof;
@@ -835,6 +836,14 @@ dg_status dg_rhs(dg_ctx* c, const void* u, void* rhs, double t) {
   a.mode = 0;
   CK(pre_rhs(c, a));
   CK(run_rhs(c, a));
+  if (c->equations == DG_NAVIER_STOKES) {
+    // keep the BR1 gradients of this input for dg_get_gradients (the stepping path
+    // leaves the viscous fluxes in the buffer instead)
+    DgArgs g = a;
+    g.grad_mode = 1;
+    CK(run_grad(c, g));
+    c->grad_is_gradient = true;
+  }
   return DG_OK;
 }
 
@@ -856,6 +865,7 @@ dg_status dg_step_rk(dg_ctx* c, int nsteps, double cfl, double dt_fixed, double*
     CK(run_lambda(c, a, c->lam_slot));
   }
   CK(run_step_dt(c, a, c->lam_slot, 0));
+  if (nsteps > 0) c->grad_is_gradient = false;
   for (int step = 0; step < nsteps; ++step) {
     for (int s = 0; s < 5; ++s) {
       DgArgs b = base_args(c);
@@ -1010,6 +1020,16 @@ dg_status dg_get_alpha(dg_ctx* c, double* alpha) {
 dg_status dg_get_gradients(dg_ctx* c, double* g) {
   if (!c || !g) return DG_EINVAL;
   if (!c->have_grad) return DG_ESTATE;
+  cudaSetDevice(c->dev);
+  if (!c->grad_is_gradient) {
+    // after dg_step_rk: the gradients of the current state
+    DgArgs a = base_args(c);
+    a.u = c->u[c->cur];
+    a.grad_mode = 1;
+    if (c->n_species > 0) CK(run_thermo(c, a.u));
+    CK(run_grad(c, a));
+    c->grad_is_gradient = true;
+  }
   const int64_t n = c->K * c->dim * (c->dim + 1) * c->np;
   if (c->precision == DG_MIXED) {
     double* tmp = NULL;

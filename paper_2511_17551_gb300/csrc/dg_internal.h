@@ -36,7 +36,9 @@ struct DgArgs {
   void* ulo;              // mode 1, FP32 form: low part of the compensated state (or null)
   const void* Ja;         // [K][dim][dim][np]
   const void* invJ;       // [K][np]
-  void* gradW;            // [K][dim][dim+1][np] (Navier-Stokes)
+  void* gradW;            // [K][dim][dim+1][np] (Navier-Stokes): grad_mode 0 the contravariant
+                          // viscous fluxes [d][c] = sum_x Ja^d_x f^v_{x,c}; 1 the gradients [x][c]
+  int grad_mode;
   const void* alpha_raw;  // [K] unsmoothed blending factors, or null
   double* alpha_used;     // [K] smoothed factors actually applied (FP64), or null
   const int* nbr;         // [K][2 dim]

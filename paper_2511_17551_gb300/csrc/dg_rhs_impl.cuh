@@ -347,31 +347,12 @@ rhs_kernel(const DgArgs a, const KConst kc) {
         for (int c = 0; c < DIM * DIM; ++c) jv[c] = jn[c * NP];
       }
       if (NS) {
-        // viscous fluxes from the staged BR1 gradients of (v, theta), stored contravariant:
-        // slot (d, c) holds sum_x Ja^d_x f^v_{x,c}, the flux along reference direction d
-        // (and, at a face of direction d, the own f^v . n)
+        // the contravariant viscous fluxes of the gradient kernel: slot (d, c) holds
+        // sum_x Ja^d_x f^v_{x,c}, the flux along reference direction d (and, at a face of
+        // direction d, the own f^v . n); rewritten at the swizzled position
         const real* gi = sfv + e * L::SFV + n;
-        real gg[DIM][DIM + 1], fv[DIM][DIM + 1];
 #pragma unroll
-        for (int x = 0; x < DIM; ++x)
-#pragma unroll
-          for (int c = 0; c <= DIM; ++c) gg[x][c] = gi[(x * (DIM + 1) + c) * NP];
-        real mu_n = kc.mu, kap_n = kc.kap;
-        if (!FL && kc.suth_s > real(0)) {
-          const real r = sutherland_ratio(p * RealOps<real>::rcp(rho), kc.suth_s, kc.suth_c1, kc.suth_irt);
-          mu_n *= r;
-          kap_n *= r;
-        }
-        viscous_flux<real, DIM>(gg, vv, mu_n, kap_n, fv);
-#pragma unroll
-        for (int d = 0; d < DIM; ++d)
-#pragma unroll
-          for (int c = 0; c <= DIM; ++c) {
-            real acc_c = 0;
-#pragma unroll
-            for (int x = 0; x < DIM; ++x) acc_c += jn[(d * DIM + x) * NP] * fv[x][c];
-            fl[d * (DIM + 1) + c] = acc_c;
-          }
+        for (int c = 0; c < (NS ? L::NFV : 1); ++c) fl[c] = gi[c * NP];
       }
     }
     if (L::SWZ) __syncthreads();
@@ -529,7 +510,7 @@ rhs_kernel(const DgArgs a, const KConst kc) {
 
   // ---- phase B2: one thread per face node: interface fluxes and lifting.  The
   // neighbour traces of all of a thread's face nodes are loaded before any is used.
-  constexpr int FN = L::FACE_NODES, FIT = L::FIT, NG = NS ? L::NFV : 1;
+  constexpr int FN = L::FACE_NODES, FIT = L::FIT, NG = NS ? DIM + 1 : 1;
   // face-node threads: face-uniform warps where the layout is swizzled
   auto face_of = [](int t, int& e, int& f, int& m) {
     if (L::UNI) {
@@ -563,16 +544,12 @@ rhs_kernel(const DgArgs a, const KConst kc) {
           nbpc[it][1] = pc[NP];
         }
         if (NS) {
-          const real* gn = (const real*)a.gradW + (int64_t)nb * L::NFV * NP + nnode;
+          // the neighbour's f^v . n: its contravariant viscous flux of direction d (the
+          // partner face node sees the same face metric)
+          const real* gn = (const real*)a.gradW + (int64_t)nb * L::NFV * NP + d * (DIM + 1) * NP + nnode;
 #pragma unroll
           for (int c = 0; c < NG; ++c) nbg[it][c] = gn[c * NP];
         }
-      } else if (NS) {
-        // boundary face: the interior gradient at the own face node
-        const int onode = S::line_base(d, m) + (side ? N : 0) * S::stride(d);
-        const real* gn = (const real*)a.gradW + (e0 + e) * L::NFV * NP + onode;
-#pragma unroll
-        for (int c = 0; c < NG; ++c) nbg[it][c] = gn[c * NP];
       }
     }
   }
@@ -616,39 +593,44 @@ rhs_kernel(const DgArgs a, const KConst kc) {
     for (int k = 0; k < NV; ++k) sa[k * NP] += iw * Fs[k];
     const int bkind = nb >= 0 ? 0 : a.bc_kind[-(nb + 1)];
     if (NS && bkind != DG_BC_OUTFLOW) {
-      // viscous interface flux: mean of both sides' f^v . n (inflow: the interior gradient
-      // with the external state), lifted as (Fv* - Fv); no-slip walls: Fv* is the wall flux
-      // of the interior gradient at zero velocity (no heat flux on an adiabatic wall)
+      // viscous interface flux: mean of both sides' f^v . n, lifted as (Fv* - Fv).  At a
+      // boundary the other side follows from the own flux (the flux is linear in the
+      // interior gradient): m = sigma . n, h = q . n = Fv_E - m . v; inflow: the external
+      // state's velocity and mu(T) (mean as at an interface); no-slip walls: Fv* = (m, h)
+      // at zero velocity, h = 0 on an adiabatic wall (Fv* itself, not a mean)
       const bool wall = bkind == DG_BC_NOSLIP_ADIABATIC || bkind == DG_BC_ISOTHERMAL;
-      if (wall) {
-        x = o;
-#pragma unroll
-        for (int c = 0; c < DIM; ++c) x.v[c] = real(0);
-      }
       const real* fvd = sfv + e * L::SFV + d * (DIM + 1) * NP + node;
-      real gg[DIM][DIM + 1], fvn[DIM][DIM + 1];
+      real fx[DIM + 1];
+      if (nb >= 0) {
 #pragma unroll
-      for (int xx = 0; xx < DIM; ++xx)
+        for (int c = 0; c <= DIM; ++c) fx[c] = nbg[it][c];
+      } else {
+        real h = fvd[DIM * NP];
 #pragma unroll
-        for (int c = 0; c <= DIM; ++c) gg[xx][c] = nbg[it][(xx * (DIM + 1) + c) % NG];
-      real mu_n = kc.mu, kap_n = kc.kap;
-      if (!FL && kc.suth_s > real(0)) {
-        const real r = sutherland_ratio(x.p * RealOps<real>::rcp(x.rho), kc.suth_s, kc.suth_c1, kc.suth_irt);
-        mu_n *= r;
-        kap_n *= r;
+        for (int c = 0; c < DIM; ++c) {
+          fx[c] = fvd[c * NP];
+          h -= fx[c] * o.v[c];
+        }
+        if (wall) {
+          fx[DIM] = bkind == DG_BC_ISOTHERMAL ? h : real(0);
+        } else {  // inflow
+          real r = 1;
+          if (!FL && kc.suth_s > real(0))
+            r = sutherland_ratio(x.p * RealOps<real>::rcp(x.rho), kc.suth_s, kc.suth_c1, kc.suth_irt) *
+                RealOps<real>::rcp(sutherland_ratio(o.p * RealOps<real>::rcp(o.rho), kc.suth_s, kc.suth_c1,
+                                                    kc.suth_irt));
+          real w = 0;
+#pragma unroll
+          for (int c = 0; c < DIM; ++c) {
+            fx[c] *= r;
+            w += fx[c] * x.v[c];
+          }
+          fx[DIM] = w + r * h;
+        }
       }
-      viscous_flux<real, DIM>(gg, x.v, mu_n, kap_n, fvn);
-      if (wall && bkind == DG_BC_NOSLIP_ADIABATIC) {
 #pragma unroll
-        for (int xx = 0; xx < DIM; ++xx) fvn[xx][DIM] = real(0);
-      }
-#pragma unroll
-      for (int c = 0; c <= DIM; ++c) {
-        real nbr_n = 0;
-#pragma unroll
-        for (int xx = 0; xx < DIM; ++xx) nbr_n += fvn[xx][c] * nface[xx];
-        sa[(NSP + c) * NP] -= iw * (wall ? nbr_n - fvd[c * NP] : real(0.5) * (nbr_n - fvd[c * NP]));
-      }
+      for (int c = 0; c <= DIM; ++c)
+        sa[(NSP + c) * NP] -= iw * (wall ? fx[c] - fvd[c * NP] : real(0.5) * (fx[c] - fvd[c * NP]));
     }
   }
   __syncthreads();
@@ -1073,26 +1055,59 @@ gradient_kernel(const DgArgs a, const KConst kc) {
       for (int c = 0; c < NW; ++c) g[c * NP + SWZ(base + i * s)] = G[i][c];
   }
   __syncthreads();
+  // physical gradients G_x = (1/J) sum_d Ja^d_x Q_d; written as they are (grad_mode 1) or
+  // turned into the contravariant viscous fluxes sum_x Ja^d_x f^v_x(G; v, mu(T)) that the
+  // right-hand-side kernel consumes (grad_mode 0)
   real* out = (real*)a.gradW;
   for (int i = tid; i < ne * NP; i += nth) {
-    const int e = i / NP, node = i % NP;
+    const int e = i / NP, node = i % NP, pn = SWZ(node);
     const real ij = sij[e * NP + node];
+    const real* jn = sja + e * DIM * DIM * NP + node;
+    real G[DIM][NW];
 #pragma unroll
     for (int x = 0; x < DIM; ++x)
 #pragma unroll
       for (int c = 0; c < NW; ++c) {
         real acc = 0;
 #pragma unroll
-        for (int d = 0; d < DIM; ++d)
-          acc += sja[((e * DIM + d) * DIM + x) * NP + node] * sg[e * L::SG + (d * NW + c) * NP + SWZ(node)];
-        out[((e0 + e) * DIM + x) * NW * NP + c * NP + node] = acc * ij;
+        for (int d = 0; d < DIM; ++d) acc += jn[(d * DIM + x) * NP] * sg[e * L::SG + (d * NW + c) * NP + pn];
+        G[x][c] = acc * ij;
+      }
+    real* o = out + (e0 + e) * DIM * NW * NP + node;
+    if (a.grad_mode) {
+#pragma unroll
+      for (int x = 0; x < DIM; ++x)
+#pragma unroll
+        for (int c = 0; c < NW; ++c) o[(x * NW + c) * NP] = G[x][c];
+      continue;
+    }
+    real vv[DIM];
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) vv[c] = sw[e * L::SW + c * NP + pn];
+    real mu_n = kc.mu, kap_n = kc.kap;
+    if (kc.suth_s > real(0)) {
+      const real r = sutherland_ratio(sw[e * L::SW + DIM * NP + pn], kc.suth_s, kc.suth_c1, kc.suth_irt);
+      mu_n *= r;
+      kap_n *= r;
+    }
+    real fv[DIM][DIM + 1];
+    viscous_flux<real, DIM>(G, vv, mu_n, kap_n, fv);
+#pragma unroll
+    for (int d = 0; d < DIM; ++d)
+#pragma unroll
+      for (int c = 0; c < NW; ++c) {
+        real acc = 0;
+#pragma unroll
+        for (int x = 0; x < DIM; ++x) acc += jn[(d * DIM + x) * NP] * fv[x][c];
+        o[(d * NW + c) * NP] = acc;
       }
   }
 }
 
 // BR1 lifting at boundary faces (Eq. auxstrongf with the boundary value W* in place of
-// the interface mean): adds (1/J) sum_d Ja^d (+-1/w) (W* - W) to the gradient of every
-// boundary face node; one thread per node, so that a node on several boundary faces (an
+// the interface mean): adds dG = (1/J) sum_d Ja^d (+-1/w) (W* - W) to the gradient of every
+// boundary face node (grad_mode 1), or f^v(dG) in contravariant form to its viscous fluxes
+// (grad_mode 0: the flux is linear in the gradient); one thread per node, so that a node on several boundary faces (an
 // edge or corner) sums its faces in one place.  Launched after gradient_kernel only for
 // meshes with boundary faces.  W*: inflow (W + W_ext)/2, outflow W, no-slip walls
 // (0, theta) or (0, theta_wall).
@@ -1154,6 +1169,7 @@ __global__ void boundary_lift_kernel(const DgArgs a, const KConst kc) {
   const real ij = ((const real*)a.invJ)[e * NP + node];
   const real* ja = (const real*)a.Ja + e * DIM * DIM * NP + node;
   real* g = (real*)a.gradW + e * DIM * NW * NP + node;
+  real dG[DIM][NW];
 #pragma unroll
   for (int x = 0; x < DIM; ++x)
 #pragma unroll
@@ -1161,7 +1177,32 @@ __global__ void boundary_lift_kernel(const DgArgs a, const KConst kc) {
       real acc = 0;
 #pragma unroll
       for (int d = 0; d < DIM; ++d) acc += ja[(d * DIM + x) * NP] * dQ[d][c];
-      g[(x * NW + c) * NP] += acc * ij;
+      dG[x][c] = acc * ij;
+    }
+  if (a.grad_mode) {
+#pragma unroll
+    for (int x = 0; x < DIM; ++x)
+#pragma unroll
+      for (int c = 0; c < NW; ++c) g[(x * NW + c) * NP] += dG[x][c];
+    return;
+  }
+  // the viscous flux is linear in the gradient: add f^v(dG; v, mu(T)) in contravariant form
+  real mu_n = kc.mu, kap_n = kc.kap;
+  if (kc.suth_s > real(0)) {
+    const real r = sutherland_ratio(W[DIM], kc.suth_s, kc.suth_c1, kc.suth_irt);
+    mu_n *= r;
+    kap_n *= r;
+  }
+  real fv[DIM][DIM + 1];
+  viscous_flux<real, DIM>(dG, W, mu_n, kap_n, fv);
+#pragma unroll
+  for (int d = 0; d < DIM; ++d)
+#pragma unroll
+    for (int c = 0; c < NW; ++c) {
+      real acc = 0;
+#pragma unroll
+      for (int x = 0; x < DIM; ++x) acc += ja[(d * DIM + x) * NP] * fv[x][c];
+      g[(d * NW + c) * NP] += acc;
     }
 }
 
