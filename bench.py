@@ -35,17 +35,18 @@ CONFIGS = {
     "tgv_ns_24^3_N3": dict(n_el=24, N=3, warp=0.1, mu=1.0 / 1600.0),
 }
 # algorithmic HBM words per node of one RK-stage launch (unique bytes, neighbour traces
-# excluded): main kernel reads u, Ja, 1/J, gradW, du and the compensation part u_lo of the
-# FP32 state, writes du, u_new, u_lo; gradient kernel reads u, Ja, 1/J and writes gradW.
+# excluded): main kernel reads u, Ja, 1/J, the contravariant viscous fluxes (12 words), du
+# and the compensation part u_lo of the FP32 state, writes du, u_new, u_lo; gradient kernel
+# reads u, Ja, 1/J and writes the viscous fluxes.
 WORDS_MAIN_NS = 5 + 9 + 1 + 12 + 5 + 5 + 5 + 10
 WORDS_MAIN_EULER = 5 + 9 + 1 + 5 + 5 + 5 + 10
 WORDS_GRAD = 5 + 9 + 1 + 12
 # dram__bytes_read.sum + dram__bytes_write.sum of the current mixed-form NS N=3 rhs_kernel
 # per node, from one ncu capture of the 24^3 case (traffic scales with the node count)
-RHS_DRAM_B_PER_NODE = 160.9
+RHS_DRAM_B_PER_NODE = 156.8
 # FP64 flops per node of the FP64-form NS N=3 rhs_kernel (2 DFMA + DMUL + DADD thread
 # instructions, one ncu capture of the 16^3 case): its roofline is the FP64 pipe
-RHS_FP64_FLOPS_PER_NODE = 1246.3
+RHS_FP64_FLOPS_PER_NODE = 1007.5
 
 
 def job_rate(ms_local, units_local, world, device="cpu"):
