@@ -476,7 +476,7 @@ dg_status take_status(dg_ctx* c, int64_t* elem) {
   if (elem) *elem = st ? (int64_t)(st & 0x00ffffffffffffffull) : -1;
   if (!st) return DG_OK;
   unsigned long long code = st >> 56;
-  return code == DG_ST_NEWTON ? DG_ENEWTON : DG_ENONPHYS;
+  return code == DG_ST_NEWTON ? DG_ENEWTON : (code == DG_ST_TIMEOUT ? DG_ETIMEOUT : DG_ENONPHYS);
 }
 
 void free_ctx(dg_ctx* c) {

@@ -11,6 +11,7 @@
 // device status word: (code << 56) | element
 #define DG_ST_NONPHYS 4ull
 #define DG_ST_NEWTON 5ull
+#define DG_ST_TIMEOUT 6ull  // a bounded wait inside a kernel ran out
 
 // Everything a right-hand-side / RK-stage launch needs, passed by value.
 struct DgArgs {

@@ -134,6 +134,42 @@ __device__ __forceinline__ void cp_async_small(void* dst, const void* src) {
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
+// Bulk copies by the TMA engine (cp.async.bulk, global -> shared), completed through one
+// mbarrier that counts the bytes.  Both addresses must be 16-byte aligned and the size a
+// multiple of 16; the callers check that at compile time (sizes, padded strides) and at run
+// time (pointers), and use the per-thread cp.async path otherwise.
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n"
+               ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(bar)) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+// waits for phase 0 of the barrier; bounded (at most 2^16 polls, each suspending for a
+// short system-defined time), returns false when the limit ran out
+__device__ __forceinline__ bool mbar_wait0(unsigned long long* bar) {
+  for (int it = 0; it < (1 << 16); ++it) {
+    unsigned done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_u32(bar))
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+__device__ __forceinline__ void mbar_inval(unsigned long long* bar) {
+  asm volatile("mbarrier.inval.shared::cta.b64 [%0];\n" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool aligned16(const void* p) { return ((uintptr_t)p & 15) == 0; }
+
 __device__ __forceinline__ void stage_async(real* dst, const real* src, int n, int tid, int nth) {
   constexpr int V = 16 / sizeof(real);
   if ((((uintptr_t)dst | (uintptr_t)src) & 15) == 0 && (n % V) == 0) {
@@ -266,20 +302,59 @@ rhs_kernel(const DgArgs a, const KConst kc) {
   const int sf = FL ? DG_SF_LLF : a.sf;
   auto SW = [](int n) { return Swizzle<DIM, N>::at(n); };
 
-  // ---- phase A: stage state, metric terms, 1/J, BR1 gradients (and du) asynchronously,
-  // unswizzled (16-byte copies)
-  stage_strided<NV, L::SU, NP>(su, (const real*)a.u + e0 * NV * NP, ne, tid, nth);
-  stage_strided<DIM * DIM, L::SJA, NP>(sja, (const real*)a.Ja + e0 * DIM * DIM * NP, ne, tid, nth);
-  stage_strided<1, L::SIJ, NP>(sij, (const real*)a.invJ + e0 * NP, ne, tid, nth);
-  if (NSP > 1) stage_strided<2, (NSP > 1 ? L::SPC : 2 * NP), NP>(spc, (const real*)a.pc + e0 * 2 * NP, ne, tid, nth);
-  if (NS)
-    stage_strided<(NS ? L::NFV : 1), (NS ? L::SFV : NP), NP>(sfv, (const real*)a.gradW + e0 * L::NFV * NP, ne,
-                                                             tid, nth);
-  if (L::PREFETCH_DU && read_du) stage_strided<NV, L::SDU, NP>(sdu, (const real*)a.du + e0 * NV * NP, ne, tid, nth);
-  // low part of the compensated energy (FP32 state), in the accumulator region that the
+  // ---- phase A: stage state, metric terms, 1/J, viscous fluxes (and du) asynchronously,
+  // unswizzled: bulk copies by the TMA engine where sizes and addresses allow (one per
+  // element and array, issued by the first warp), 16-byte cp.async otherwise.  The low
+  // part of the compensated energy (FP32 state) goes to the accumulator region that the
   // line phase fills later: [e][node], unswizzled
   const bool have_elo = sizeof(real) == 4 && NSP == 1 && a.ulo != nullptr;
-  if (have_elo) stage_rows<NP>(sacc, (const real*)a.ulo + e0 * NV * NP + (NSP + DIM) * NP, NV * NP, ne, tid, nth);
+  constexpr int RS = sizeof(real);
+  constexpr bool BULK_SHAPES = (NP * RS) % 16 == 0 && (L::SU * RS) % 16 == 0 && (L::SJA * RS) % 16 == 0 &&
+                               (L::SIJ * RS) % 16 == 0 && (L::SFV * RS) % 16 == 0 && (L::SPC * RS) % 16 == 0 &&
+                               (L::SDU * RS) % 16 == 0 && (L::ACC * RS) % 16 == 0 && (L::DU * RS) % 16 == 0 &&
+                               (L::FV * RS) % 16 == 0 && (L::PC * RS) % 16 == 0 && (L::JA * RS) % 16 == 0 &&
+                               (L::IJ * RS) % 16 == 0;
+  const bool pre_du = L::PREFETCH_DU && read_du;
+  const bool bulk = BULK_SHAPES && aligned16(a.u) && aligned16(a.Ja) && aligned16(a.invJ) &&
+                    (!NS || aligned16(a.gradW)) && (!pre_du || aligned16(a.du)) &&
+                    (!have_elo || aligned16(a.ulo)) && (NSP == 1 || aligned16(a.pc));
+  __shared__ __align__(8) unsigned long long s_bar;
+  if (bulk) {
+    if (tid == 0) mbar_init(&s_bar);
+    __syncthreads();
+    if (tid < 32) {
+      // total bytes first (one arrive with the expected count), then the copies
+      const unsigned per_e = (unsigned)(RS * NP * (NV + DIM * DIM + 1 + (NSP > 1 ? 2 : 0) + (NS ? L::NFV : 0) +
+                                                   (pre_du ? NV : 0) + (have_elo ? 1 : 0)));
+      if (tid == 0) mbar_expect(&s_bar, per_e * (unsigned)ne);
+      __syncwarp();
+      for (int j = tid; j < 8 * ne; j += 32) {
+        const int e = j >> 3, kind = j & 7;
+        const int64_t g = e0 + e;
+        if (kind == 0) bulk_g2s(su + e * L::SU, (const real*)a.u + g * NV * NP, RS * NV * NP, &s_bar);
+        if (kind == 1) bulk_g2s(sja + e * L::SJA, (const real*)a.Ja + g * DIM * DIM * NP, RS * DIM * DIM * NP, &s_bar);
+        if (kind == 2) bulk_g2s(sij + e * L::SIJ, (const real*)a.invJ + g * NP, RS * NP, &s_bar);
+        if (kind == 3 && NSP > 1) bulk_g2s(spc + e * L::SPC, (const real*)a.pc + g * 2 * NP, RS * 2 * NP, &s_bar);
+        if (kind == 4 && NS)
+          bulk_g2s(sfv + e * L::SFV, (const real*)a.gradW + g * L::NFV * NP, RS * L::NFV * NP, &s_bar);
+        if (kind == 5 && pre_du) bulk_g2s(sdu + e * L::SDU, (const real*)a.du + g * NV * NP, RS * NV * NP, &s_bar);
+        if (kind == 6 && have_elo)
+          bulk_g2s(sacc + e * NP, (const real*)a.ulo + g * NV * NP + (NSP + DIM) * NP, RS * NP, &s_bar);
+      }
+    }
+  } else {
+    stage_strided<NV, L::SU, NP>(su, (const real*)a.u + e0 * NV * NP, ne, tid, nth);
+    stage_strided<DIM * DIM, L::SJA, NP>(sja, (const real*)a.Ja + e0 * DIM * DIM * NP, ne, tid, nth);
+    stage_strided<1, L::SIJ, NP>(sij, (const real*)a.invJ + e0 * NP, ne, tid, nth);
+    if (NSP > 1)
+      stage_strided<2, (NSP > 1 ? L::SPC : 2 * NP), NP>(spc, (const real*)a.pc + e0 * 2 * NP, ne, tid, nth);
+    if (NS)
+      stage_strided<(NS ? L::NFV : 1), (NS ? L::SFV : NP), NP>(sfv, (const real*)a.gradW + e0 * L::NFV * NP, ne,
+                                                               tid, nth);
+    if (pre_du) stage_strided<NV, L::SDU, NP>(sdu, (const real*)a.du + e0 * NV * NP, ne, tid, nth);
+    if (have_elo)
+      stage_rows<NP>(sacc, (const real*)a.ulo + e0 * NV * NP + (NSP + DIM) * NP, NV * NP, ne, tid, nth);
+  }
   if (tid < EPB) {
     real al = 0;
     if (a.alpha_raw && tid < ne) {
@@ -299,8 +374,13 @@ rhs_kernel(const DgArgs a, const KConst kc) {
     if (a.mode == 1) s_dt = (real)a.scal[1];
     s_lam[0] = s_lam[1] = 0ull;
   }
-  cp_async_wait_all();
+  if (bulk) {
+    if (!mbar_wait0(&s_bar)) latch_status(a.status, DG_ST_TIMEOUT, e0);
+  } else {
+    cp_async_wait_all();
+  }
   __syncthreads();
+  if (bulk && tid == 0) mbar_inval(&s_bar);
   // One thread per node: primitives (written swizzled), viscous fluxes, and the swizzled
   // rewrite of the metric terms, gradients -> contravariant viscous fluxes and p, c.  The
   // rewrite stays inside k-slabs of N1^2 nodes and nth is a multiple of N1^2, so one
@@ -966,11 +1046,31 @@ gradient_kernel(const DgArgs a, const KConst kc) {
   const real* gu = (const real*)a.u;
   // the conserved state is staged in the gradient region, which is free until the line phase
   static_assert(L::TOTAL - L::G >= L::EPB * NV * NP, "gradient region too small for the state");
-  stage_async(sja, (const real*)a.Ja + e0 * DIM * DIM * NP, ne * DIM * DIM * NP, tid, nth);
-  stage_async(sij, (const real*)a.invJ + e0 * NP, ne * NP, tid, nth);
-  stage_async(sg, gu + e0 * NV * NP, ne * NV * NP, tid, nth);
-  cp_async_wait_all();
+  // contiguous blocks of the CTA's elements: three TMA bulk copies where sizes and
+  // addresses allow, 16-byte cp.async otherwise
+  constexpr int RS = sizeof(real);
+  constexpr bool BULK_SHAPES = (NP * RS) % 16 == 0 && (L::JA * RS) % 16 == 0 && (L::IJ * RS) % 16 == 0 &&
+                               (L::G * RS) % 16 == 0;
+  const bool bulk = BULK_SHAPES && aligned16(a.Ja) && aligned16(a.invJ) && aligned16(gu);
+  __shared__ __align__(8) unsigned long long s_bar;
+  if (bulk) {
+    if (tid == 0) {
+      mbar_init(&s_bar);
+      mbar_expect(&s_bar, (unsigned)(RS * NP * ne * (DIM * DIM + 1 + NV)));
+      bulk_g2s(sja, (const real*)a.Ja + e0 * DIM * DIM * NP, RS * ne * DIM * DIM * NP, &s_bar);
+      bulk_g2s(sij, (const real*)a.invJ + e0 * NP, RS * ne * NP, &s_bar);
+      bulk_g2s(sg, gu + e0 * NV * NP, RS * ne * NV * NP, &s_bar);
+    }
+    __syncthreads();  // the barrier is initialised before anyone polls it
+    if (!mbar_wait0(&s_bar)) latch_status(a.status, DG_ST_TIMEOUT, e0);
+  } else {
+    stage_async(sja, (const real*)a.Ja + e0 * DIM * DIM * NP, ne * DIM * DIM * NP, tid, nth);
+    stage_async(sij, (const real*)a.invJ + e0 * NP, ne * NP, tid, nth);
+    stage_async(sg, gu + e0 * NV * NP, ne * NV * NP, tid, nth);
+    cp_async_wait_all();
+  }
   __syncthreads();
+  if (bulk && tid == 0) mbar_inval(&s_bar);
   auto SWZ = [](int n) { return Swizzle<DIM, N>::at(n); };
   for (int i = tid; i < ne * NP; i += nth) {
     const int e = i / NP, node = i % NP, pn = SWZ(node);
