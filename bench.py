@@ -187,6 +187,19 @@ def run_ours(args, rank, world, local_rank):
     barrier()
     e2e_s = time.perf_counter() - t_start
     e2e_value = world * dof * 5 * e2e_steps / e2e_s
+    # where the end-to-end time goes (each call synchronises): host wall ms per call
+    parts = {"set_state": 0.0, "step": 0.0, "get_state": 0.0}
+    for _ in range(e2e_steps):
+        t0 = time.perf_counter()
+        dg.dg_set_state(s.ctx, u_host)
+        t1 = time.perf_counter()
+        dg.dg_step_rk(s.ctx, 1, cfg_cfl)
+        t2 = time.perf_counter()
+        dg.dg_get_state(s.ctx, u_host)
+        t3 = time.perf_counter()
+        parts["set_state"] += (t1 - t0) * 1e3 / e2e_steps
+        parts["step"] += (t2 - t1) * 1e3 / e2e_steps
+        parts["get_state"] += (t3 - t2) * 1e3 / e2e_steps
     s.close()
     # --- FP64 form on the same GPU
     s64 = make(dg.DG_FP64)
@@ -223,7 +236,8 @@ def run_ours(args, rank, world, local_rank):
                                    "flops_per_node": RHS_FP64_FLOPS_PER_NODE,
                                    "peak_source": "FP64 FMA chains measured here (dg_peak_flops)"}},
         "e2e": {"value": e2e_value, "unit": "DOF*RHS/s", "h2d_bytes_per_step": dof * 8,
-                "d2h_bytes_per_step": dof * 8},
+                "d2h_bytes_per_step": dof * 8,
+                "host_ms_per_call": {k: round(v, 4) for k, v in parts.items()}},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak,
                      "traffic": (RHS_DRAM_B_PER_NODE * K * npn

@@ -456,7 +456,9 @@ cudaError_t pre_rhs(dg_ctx* c, DgArgs& a) {
 }
 
 dg_status wait_stream(dg_ctx* c) {
-  // bounded wait: poll for up to 600 s of wall time
+  // bounded wait: poll for up to 600 s of wall time; the first 2 ms without sleeping (a
+  // sleep overshoots by the timer slack, tens of microseconds, on every short wait), then
+  // with 20 us sleeps
   struct timespec t0, t1;
   clock_gettime(CLOCK_MONOTONIC, &t0);
   for (;;) {
@@ -464,9 +466,12 @@ dg_status wait_stream(dg_ctx* c) {
     if (q == cudaSuccess) return DG_OK;
     if (q != cudaErrorNotReady) return DG_ECUDA;
     clock_gettime(CLOCK_MONOTONIC, &t1);
-    if ((t1.tv_sec - t0.tv_sec) > 600) return DG_ETIMEOUT;
-    struct timespec ts = {0, 20000};
-    nanosleep(&ts, NULL);
+    const double el = (double)(t1.tv_sec - t0.tv_sec) + 1e-9 * (double)(t1.tv_nsec - t0.tv_nsec);
+    if (el > 600.0) return DG_ETIMEOUT;
+    if (el > 2e-3) {
+      struct timespec ts = {0, 20000};
+      nanosleep(&ts, NULL);
+    }
   }
 }
 
