@@ -144,8 +144,11 @@ dg_status dg_lgl_nodes(int N, double* nodes, double* weights);
 dg_status dg_init_mesh(const dg_mesh_desc* mesh, const dg_physics_desc* phys, dg_ctx** out);
 
 /* Set the state from FP64 conserved variables [K][nv][np] (host or device
- * pointer, copied; converted to FP32 in DG_MIXED).  t is the solution time.
- * Mixtures: the per-node temperature cache restarts cold (Newton from 1000 K). */
+ * pointer, copied; converted to the compensated FP32 pair in DG_MIXED).  t is the
+ * solution time.  In DG_MIXED a page-locked host buffer (cudaHostAlloc /
+ * cudaHostRegister) is read by the conversion kernel directly, without a staging copy.
+ * Synchronises.  Mixtures: the per-node temperature cache restarts cold (Newton from
+ * 1000 K). */
 dg_status dg_set_state(dg_ctx* ctx, const double* u, int on_device, double t);
 
 /* Set the state from FP64 primitive variables (Eq. total_energy / eos applied
@@ -153,7 +156,8 @@ dg_status dg_set_state(dg_ctx* ctx, const double* u, int on_device, double t);
 dg_status dg_set_state_primitive(dg_ctx* ctx, const double* w, int on_device, double t);
 
 /* Copy the current state to u (FP64 [K][nv][np], host or device) and its time
- * to *t (may be NULL).  Synchronises the context stream. */
+ * to *t (may be NULL).  In DG_MIXED a page-locked host buffer is written by the
+ * conversion kernel directly.  Synchronises the context stream. */
 dg_status dg_get_state(dg_ctx* ctx, double* u, int on_device, double* t);
 
 /* rhs = du/dt evaluated at u (Eq. strong_form with the split volume term of

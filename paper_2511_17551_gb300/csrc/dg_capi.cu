@@ -759,12 +759,27 @@ fail:
 
 void dg_destroy(dg_ctx* c) { free_ctx(c); }
 
+// device address of page-locked host memory (cudaHostAlloc / cudaHostRegister), or null:
+// kernels then read or write the host buffer directly over the CPU-GPU link, which folds
+// the copy into the split / merge pass of the mixed form
+const void* pinned_device_ptr(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+}
+
 dg_status dg_set_state(dg_ctx* c, const double* u, int on_device, double t) {
   if (!c || !u) return DG_EINVAL;
   const int64_t n = c->K * c->nv * c->np;
   cudaSetDevice(c->dev);
   const double* src = u;
-  if (!on_device) {
+  const void* hp = (!on_device && c->precision == DG_MIXED) ? pinned_device_ptr(u) : nullptr;
+  if (hp) {
+    src = (const double*)hp;
+  } else if (!on_device) {
     CK(cudaMemcpyAsync(c->stage64, u, sizeof(double) * n, cudaMemcpyHostToDevice, c->stream));
     src = c->stage64;
   }
@@ -814,10 +829,11 @@ dg_status dg_get_state(dg_ctx* c, double* u, int on_device, double* t) {
   cudaSetDevice(c->dev);
   const int64_t n = c->K * c->nv * c->np;
   if (c->precision == DG_MIXED) {
-    double* dst = on_device ? u : c->stage64;
+    double* hp = on_device ? nullptr : (double*)pinned_device_ptr(u);
+    double* dst = on_device ? u : (hp ? hp : c->stage64);
     merge_kernel<<<grid_for(n, 256), 256, 0, c->stream>>>((const float*)c->u[c->cur], c->ulo, dst, n);
     CK(cudaGetLastError());
-    if (!on_device)
+    if (!on_device && !hp)
       CK(cudaMemcpyAsync(u, c->stage64, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream));
   } else {
     CK(cudaMemcpyAsync(u, c->u[c->cur], sizeof(double) * n,

@@ -277,3 +277,28 @@ def test_invalid_arguments(dg):
         with pytest.raises(dg.DgError) as ei:
             dg.Solver(3, 3, xyz, nbr, face, n_species=5, species=np.zeros((5, 8)), volume_flux=vf)
         assert ei.value.code == dg.DG_EINVAL
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_pinned_host_buffers_match_pageable(dg, precision):
+    """dg_set_state / dg_get_state with page-locked host buffers (read and written by the
+    conversion kernels directly in the mixed form) give the same bits as pageable ones."""
+    import torch
+    p = cases.Pair(_tgv_builder(shape=(3, 3, 5)), 3, 3, precision=precision)
+    try:
+        u = p.orc.prim_to_cons(cases.perturbed_state(p.mesh_o[3], 11, amp=0.05))
+        pin = torch.from_numpy(u.copy()).pin_memory()
+        p.gpu.set_state(u)
+        a, _ = p.gpu.get_state()
+        dg.dg_set_state(p.gpu.ctx, pin)
+        out = torch.zeros_like(pin).pin_memory()
+        dg.dg_get_state(p.gpu.ctx, out)
+        assert np.array_equal(out.numpy(), a)
+        p.gpu.step(2, dt_fixed=1e-3)
+        b, _ = p.gpu.get_state()
+        dg.dg_set_state(p.gpu.ctx, pin)
+        p.gpu.step(2, dt_fixed=1e-3)
+        dg.dg_get_state(p.gpu.ctx, out)
+        assert np.array_equal(out.numpy(), b)
+    finally:
+        p.close()
