@@ -47,3 +47,31 @@ def test_no_device_fails_loudly():
     with pytest.raises(dg.DgError) as ei:
         dg.Solver(3, 3, xyz, nbr, face)
     assert ei.value.code == dg.DG_ECUDA
+
+
+def test_invalid_descriptors_rejected_before_any_device_use():
+    """Argument validation precedes every device call: an empty mesh, an unsupported degree,
+    a neighbour out of range and out-of-range options return DG_EINVAL here too."""
+    import paper_2511_17551_gb300 as dg
+    import workloads as W
+    x, _ = dg.dg_lgl_nodes(3)
+    xyz, nbr, face = W.box_mesh((2, 2, 2), x, (0, 0, 0), (1, 1, 1))
+    bad_nbr = nbr.copy()
+    bad_nbr[0, 0] = 8
+    cases_ = [
+        dict(xyz=xyz[:0], nbr=nbr[:0], face=face[:0], N=3, kw={}),            # K = 0
+        dict(xyz=xyz, nbr=nbr, face=face, N=6, kw={}),                         # degree not built
+        dict(xyz=xyz, nbr=bad_nbr, face=face, N=3, kw={}),                     # neighbour >= K
+        dict(xyz=xyz, nbr=nbr, face=face, N=3, kw=dict(volume_flux=6)),
+        dict(xyz=xyz, nbr=nbr, face=face, N=3, kw=dict(surface_flux=-1)),
+        dict(xyz=xyz, nbr=nbr, face=face, N=3, kw=dict(sutherland_s=-0.1)),
+        dict(xyz=xyz, nbr=nbr, face=face, N=3, kw=dict(sutherland_s=0.4, sutherland_rt=0.0)),
+        dict(xyz=xyz, nbr=nbr, face=face, N=3, kw=dict(indicator_variable=2)),
+        dict(xyz=xyz, nbr=nbr, face=face, N=3, kw=dict(positivity_eps=-1.0)),
+        dict(xyz=xyz, nbr=nbr, face=face, N=3, kw=dict(alpha_max=1.5)),
+        dict(xyz=xyz, nbr=nbr, face=face, N=3, kw=dict(equations=1, mu=0.0)),
+    ]
+    for c in cases_:
+        with pytest.raises(dg.DgError) as ei:
+            dg.Solver(3, c["N"], c["xyz"], c["nbr"], c["face"], **c["kw"])
+        assert ei.value.code == dg.DG_EINVAL, c["kw"]
