@@ -265,8 +265,10 @@ dg_status dg_mlp_grad(const float* params, int n_out, const float* X, const floa
 dg_status dg_mlp_train_step(float* params, int n_out, float* m, float* v, const float* X,
                             const float* t, int batch, int step, float lr, double* loss,
                             float* workspace, size_t ws_bytes, void* stream);
-/* y[n][n_out] = network(X[n][7]) for standardised X; tensor_cores = 1 uses the BF16 MMA
- * path of the inference kernels (n_out 1 or 10; synchronises), 0 the FP32 path. */
+/* y[n][n_out] = network(X[n][7]) for standardised X; tensor_cores = 1 uses the warp-level
+ * BF16 MMA path of the inference kernels, 2 the tcgen05 path (128-row tiles, tensor-memory
+ * accumulators; DG_ETIMEOUT if a bounded wait inside ran out), both for n_out 1 or 10 and
+ * synchronising; 0 the FP32 path. */
 dg_status dg_mlp_forward(const float* params, int n_out, const float* X, float* y, int64_t n,
                          int tensor_cores, void* stream);
 

@@ -17,6 +17,7 @@
 #include "../../include/dg.h"
 #include "dg_internal.h"
 #include "dg_mlp.cuh"
+#include "dg_mlp_tc5.cuh"
 #include "dg_thermo.h"
 
 #define NI DG_MLP_NI
@@ -498,6 +499,29 @@ cudaError_t dg_mlp_sample(DgThermo* th, const void* u, int f32, int64_t n, uint6
   return cudaGetLastError();
 }
 
+// tcgen05 forward: persistent CTAs of 128 threads over 128-row tiles; the dynamic
+// shared memory is padded to 60 KB so that at most 3 CTAs (3 x 128 tensor-memory columns)
+// share an SM
+__device__ unsigned g_tc5_err;
+template <int NO>
+static dg_status forward_tc5(const float* P, const float* X, float* y, int64_t n, cudaStream_t st) {
+  const size_t smem = sizeof(dgtc5::Smem<NO>) > 60 * 1024 ? sizeof(dgtc5::Smem<NO>) : 60 * 1024;
+  auto k = dgtc5::mlp_forward_tc5_kernel<NO>;
+  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return DG_ECUDA;
+  unsigned* err = NULL;
+  if (cudaGetSymbolAddress((void**)&err, g_tc5_err) != cudaSuccess) return DG_ECUDA;
+  if (cudaMemsetAsync(err, 0, sizeof(unsigned), st) != cudaSuccess) return DG_ECUDA;
+  const int64_t tiles = (n + dgtc5::ROWS - 1) / dgtc5::ROWS;
+  const unsigned grid = (unsigned)(tiles < 152 * 3 ? tiles : 152 * 3);
+  k<<<grid, dgtc5::THREADS, smem, st>>>(P, X, y, n, err);
+  if (cudaGetLastError() != cudaSuccess) return DG_ECUDA;
+  unsigned h = 0;
+  if (cudaMemcpyAsync(&h, err, sizeof(unsigned), cudaMemcpyDeviceToHost, st) != cudaSuccess) return DG_ECUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return DG_ECUDA;
+  return h ? DG_ETIMEOUT : DG_OK;
+}
+
 template <int NO>
 static dg_status forward_tc(const float* hp, const float* X, float* y, int64_t n, cudaStream_t st) {
   DgMlpW<NO> h;
@@ -579,6 +603,8 @@ dg_status dg_mlp_forward(const float* params, int n_out, const float* X, float* 
     return cudaGetLastError() == cudaSuccess ? DG_OK : DG_ECUDA;
   }
   if (n_out != 1 && n_out != 10) return DG_EINVAL;  // the surrogates' output counts
+  if (tensor_cores == 2) return n_out == 1 ? forward_tc5<1>(params, X, y, n, st) : forward_tc5<10>(params, X, y, n, st);
+  if (tensor_cores != 1) return DG_EINVAL;
   const int npar = dg_mlp_np(n_out);
   float* hp = (float*)malloc(sizeof(float) * npar);
   if (!hp) return DG_ENOMEM;

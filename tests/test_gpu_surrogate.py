@@ -60,6 +60,33 @@ def test_forward_fp32_and_tensor_cores(env):
     assert np.linalg.norm(ytc - y_o) / np.linalg.norm(y_o) < 3e-2
 
 
+@pytest.mark.parametrize("n_out", [1, 10])
+def test_forward_tcgen05_matches_oracle_and_warp_mma(env, n_out):
+    """The tcgen05 forward (128-row tiles, tensor-memory accumulators) against the oracle's
+    FP64 network and the warp-level BF16 path, on a ragged row count that spans many tiles
+    and several tiles per CTA."""
+    dg, oracle, torch = env
+    rng = np.random.default_rng(40 + n_out)
+    n = 1_000_003
+    p = (0.3 * rng.normal(size=oracle.mlp_nparams(n_out))).astype(np.float32)
+    X = rng.normal(size=(n, 7)).astype(np.float32)
+    P, Xd = torch.from_numpy(p).cuda(), torch.from_numpy(X).cuda()
+    shape = (n,) if n_out == 1 else (n, n_out)
+    y5 = torch.full(shape, float("nan"), dtype=torch.float32, device="cuda")
+    y1 = torch.empty_like(y5)
+    dg.dg_mlp_forward(P, Xd, y5, tensor_cores=2)
+    dg.dg_mlp_forward(P, Xd, y1, tensor_cores=1)
+    torch.cuda.synchronize()
+    y5, y1 = y5.cpu().numpy().reshape(n, n_out), y1.cpu().numpy().reshape(n, n_out)
+    assert np.all(np.isfinite(y5))
+    sample = np.r_[0:2000, n - 2000:n]             # the oracle on a sample, the ragged tail included
+    y_o = oracle.mlp_forward(p.astype(np.float64), X[sample].astype(np.float64), n_out).reshape(-1, n_out)
+    assert np.linalg.norm(y5[sample] - y_o) / np.linalg.norm(y_o) < 3e-2
+    # same BF16 roundings of inputs, weights and hidden units; only the summation order of
+    # the FP32 accumulation differs
+    assert np.linalg.norm(y5 - y1) / np.linalg.norm(y1) < 5e-3
+
+
 def test_adam_step_matches_oracle(env):
     dg, oracle, torch = env
     p, X, t = _rand(oracle, 3)
