@@ -251,6 +251,7 @@ def run_ours(args, rank, world, local_rank):
     }
     out["arith_peaks_tflops"] = {"fp64_fma": fp64_peak, "fp32_fma": fp32_peak,
                                  "source": "measured here, FMA chains, 152x8 CTAs"}
+    out["mlp_forward"] = run_mlp_forward()
     if not args.no_mixture:
         out["mixture"] = run_mixture(args, stream.cuda_stream, world)
     if not args.no_reacting:
@@ -284,6 +285,34 @@ def run_ours(args, rank, world, local_rank):
         print(json.dumps(out))
     if world > 1:
         dist.destroy_process_group()
+
+
+def run_mlp_forward(n=4_608_000, reps=5):
+    """The perceptron forward alone (ten outputs, one row per node of the reacting
+    workload): the warp-level BF16 MMA path against the tcgen05 path, host wall time per
+    call (each synchronises), best of reps; tensor FLOPs = the two BF16 layers as executed
+    (K padded to 16 in layer 1) over the measured dense BF16 peak."""
+    import torch
+    import paper_2511_17551_gb300 as dg
+    rng = np.random.default_rng(5)
+    P = torch.from_numpy((0.3 * rng.normal(size=dg.dg_mlp_nparams(10))).astype(np.float32)).cuda()
+    X = torch.from_numpy(rng.normal(size=(n, 7)).astype(np.float32)).cuda()
+    y = torch.empty((n, 10), dtype=torch.float32, device="cuda")
+    flops_row = 2 * (16 * 64 + 64 * 64)
+    peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("bf16_tflops") \
+        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 1900.0
+    out = {"rows": n, "n_out": 10, "tensor_flops_per_row": flops_row, "bf16_peak_tflops": peak}
+    for name, tc in (("warp_mma_sync", 1), ("tcgen05", 2)):
+        dg.dg_mlp_forward(P, X, y, tensor_cores=tc)
+        best = 1e9
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            dg.dg_mlp_forward(P, X, y, tensor_cores=tc)
+            best = min(best, time.perf_counter() - t0)
+        out[name] = {"ms": best * 1e3, "tensor_tflops": flops_row * n / best / 1e12,
+                     "frac_of_bf16_peak": flops_row * n / best / 1e12 / peak}
+    return out
 
 
 def run_mixture(args, stream_ptr, world):
