@@ -17,6 +17,7 @@
 #include "../../include/dg.h"
 #include "dg_internal.h"
 #include "dg_mlp.cuh"
+#include "dg_mlp_tc5.cuh"
 #include "dg_thermo.h"
 
 #define NSPEC 5
@@ -149,8 +150,6 @@ struct __align__(16) DgChemMlp {
   double tol_check, floor;
 };
 
-#define CM_WARPS 4
-
 __device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
   x += 0x9E3779B97F4A7C15ull;
   x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
@@ -174,62 +173,63 @@ __device__ __forceinline__ void chem_features(const T* uu, int np, double Tk, fl
   x[6] = (float)Tk;
 }
 
+// The learned source on the fifth-generation tensor cores: CTAs of 128 threads take
+// 128-node tiles through the tcgen05 tile engine (dg_mlp_tc5.cuh); each thread forms its
+// node's features (and the trust-box test) before the two tensor-core layers and decodes
+// its node's ten outputs after them (species sources, mass-balance test).  Flags per
+// 32-node (warp) tile: 0 accepted, 1 rejected; a tile whose tensor-core waits ran out is
+// rejected too, so the plain fallback recomputes it.
 template <typename T>
-__global__ void __launch_bounds__(32 * CM_WARPS)
-chem_mlp_kernel(const T* u, const double* Tc, int64_t K, int np, int dim, const DgChemMlp* mlp,
-                const double* dtp, T* src, unsigned char* flags) {
+__global__ void __launch_bounds__(dgtc5::THREADS, 1)
+chem_mlp_tc5_kernel(const T* u, const double* Tc, int64_t K, int np, int dim, const DgChemMlp* mlp,
+                    const double* dtp, T* src, unsigned char* flags) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  dgtc5::Smem<10>& s = *reinterpret_cast<dgtc5::Smem<10>*>(smem_raw);
   __shared__ DgChemMlp m;
-  __shared__ float feat[CM_WARPS][32][17];
-  __shared__ float yv[CM_WARPS][2][10][16];
   dgmlp::copy_to_smem(m, mlp);
   __syncthreads();
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  dgtc5::load_weights<10>(s, m.w);
   const int nv = NSPEC + dim + 1;
   const int64_t total = K * np;
   const float dt = dtp ? (float)*dtp : 0.f;
-  for (int64_t base = ((int64_t)blockIdx.x * CM_WARPS + w) * 32; base < total;
-       base += (int64_t)gridDim.x * CM_WARPS * 32) {
-    const int64_t i = base + lane;
-    const bool mine = i < total;
-    const int64_t k = mine ? i / np : 0;
-    const int node = mine ? (int)(i % np) : 0;
-    float x[7];
+  auto prod = [&](int64_t i, float* x) {
+    float raw[7];
     bool ok = true;
-    if (mine) {
-      chem_features<T>(u + k * nv * np + node, np, Tc[i], x);
+    if (i < total) {
+      chem_features<T>(u + (i / np) * nv * np + (i % np), np, Tc[i], raw);
 #pragma unroll
-      for (int q = 0; q < 7; ++q) ok = ok && x[q] >= m.lo[q] && x[q] <= m.hi[q];
+      for (int q = 0; q < 7; ++q) ok = ok && raw[q] >= m.lo[q] && raw[q] <= m.hi[q];
     } else {
 #pragma unroll
-      for (int q = 0; q < 7; ++q) x[q] = m.mean[q];
+      for (int q = 0; q < 7; ++q) raw[q] = m.mean[q];
     }
 #pragma unroll
-    for (int q = 0; q < 7; ++q) feat[w][lane][q] = (x[q] - m.mean[q]) * m.inv_std[q];
-#pragma unroll
-    for (int q = 7; q < 17; ++q) feat[w][lane][q] = 0.f;
-    __syncwarp();
-    dgmlp::mlp16<10>(m.w, feat[w], yv[w][0]);
-    dgmlp::mlp16<10>(m.w, feat[w] + 16, yv[w][1]);
-    __syncwarp();
-    if (mine) {
+    for (int q = 0; q < 7; ++q) x[q] = (raw[q] - m.mean[q]) * m.inv_std[q];
+    x[7] = 0.f;
+    return ok;
+  };
+  auto cons = [&](int64_t i, const float* y, bool ok, bool valid) {
+    ok = ok && valid;
+    if (i < total && valid) {
       float om[NSPEC], jp[NSPEC], msum = 0.f, asum = 0.f;
 #pragma unroll
-      for (int s = 0; s < NSPEC; ++s) {
-        om[s] = m.w_ref * sinhf(m.muY[s] + m.sdY[s] * yv[w][lane >> 4][s][lane & 15]);
-        jp[s] = fmaxf(0.f, m.j_ref * sinhf(m.muY[5 + s] + m.sdY[5 + s] * yv[w][lane >> 4][5 + s][lane & 15]));
-        msum += om[s];
-        asum += fabsf(om[s]);
+      for (int q = 0; q < NSPEC; ++q) {
+        om[q] = m.w_ref * sinhf(m.muY[q] + m.sdY[q] * y[q]);
+        jp[q] = fmaxf(0.f, m.j_ref * sinhf(m.muY[5 + q] + m.sdY[5 + q] * y[5 + q]));
+        msum += om[q];
+        asum += fabsf(om[q]);
       }
       ok = ok && isfinite(asum) && fabsf(msum) <= m.tol_mass * asum + m.floor32;
       const float f = asum > 0.f ? msum / asum : 0.f;
-      T* so = src + k * NSPEC * np + node;
+      T* so = src + (i / np) * NSPEC * np + (i % np);
 #pragma unroll
-      for (int s = 0; s < NSPEC; ++s) so[s * np] = (T)((om[s] - fabsf(om[s]) * f) / (1.f + dt * jp[s]));
+      for (int q = 0; q < NSPEC; ++q) so[q * np] = (T)((om[q] - fabsf(om[q]) * f) / (1.f + dt * jp[q]));
     }
     const bool tile_ok = __all_sync(0xffffffffu, ok);
-    if (lane == 0) flags[base >> 5] = tile_ok ? 0 : 1;
-    __syncwarp();
-  }
+    const int64_t base = i - (threadIdx.x & 31);  // first node of this warp's 32-node tile
+    if ((threadIdx.x & 31) == 0 && base < total) flags[base >> 5] = tile_ok ? 0 : 1;
+  };
+  dgtc5::run_tiles<10>(s, total, prod, cons);
 }
 
 // one thread per tile still accepted: compare the learned source at the tile's sampled
@@ -382,10 +382,15 @@ template <typename T>
 static cudaError_t chem_learned(DgThermo* th, const T* u, const double* dt_dev, cudaStream_t s) {
   const int64_t total = th->K * th->np, ntiles = (total + 31) / 32;
   const DgChemMlp* m = (const DgChemMlp*)th->chem_mlp;
-  int64_t g1 = (ntiles + CM_WARPS - 1) / CM_WARPS;
-  if (g1 > 152 * 16) g1 = 152 * 16;
-  chem_mlp_kernel<T><<<(unsigned)g1, 32 * CM_WARPS, 0, s>>>(u, th->T, th->K, th->np, th->dim, m, dt_dev,
-                                                             (T*)th->src, th->chem_flags);
+  // tensor-core tiles of 128 nodes; the dynamic shared memory is padded to 60 KB so that at
+  // most 3 CTAs (3 x 128 tensor-memory columns) share an SM
+  const size_t smem = sizeof(dgtc5::Smem<10>) > 60 * 1024 ? sizeof(dgtc5::Smem<10>) : 60 * 1024;
+  auto k1 = chem_mlp_tc5_kernel<T>;
+  cudaError_t e = cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int64_t t128 = (total + dgtc5::ROWS - 1) / dgtc5::ROWS;
+  k1<<<(unsigned)(t128 < 152 * 3 ? t128 : 152 * 3), dgtc5::THREADS, smem, s>>>(u, th->T, th->K, th->np, th->dim, m,
+                                                                              dt_dev, (T*)th->src, th->chem_flags);
   chem_check_kernel<T><<<grid_of(ntiles), 128, 0, s>>>(u, th->T, th->K, th->np, th->dim, th->species_raw,
                                                        th->reac, th->nr, m, dt_dev, (const T*)th->src,
                                                        th->chem_flags, th->chem_calls++);

@@ -100,17 +100,12 @@ __device__ __forceinline__ void ld16(uint32_t taddr, float* v) {
 }
 __device__ __forceinline__ void ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory"); }
 
-// y[n][NO] = network(X[n][7]) for standardised X.  *err is set to 1 when a bounded wait ran
-// out (the outputs of that launch are then not valid).  Launch with THREADS threads and
-// dynamic shared memory of at least sizeof(Smem<NO>) (more to limit resident CTAs).
+// weights from the FP32 parameter vector (layout of dg_mlp_np) into the canonical
+// BF16 operands, biases and the FP32 output layer
 template <int NO>
-__global__ void __launch_bounds__(THREADS, 1) mlp_forward_tc5_kernel(const float* P, const float* X, float* y,
-                                                                     int64_t n, unsigned* err) {
+__device__ __forceinline__ void load_weights(Smem<NO>& s, const float* P) {
   constexpr int NI = DG_MLP_NI, NH = DG_MLP_NH;
-  extern __shared__ __align__(1024) unsigned char smem_raw[];
-  Smem<NO>& s = *reinterpret_cast<Smem<NO>*>(smem_raw);
-  const int tid = threadIdx.x, warp = tid >> 5;
-  // weights in the canonical layout (BF16), biases and W3 (FP32)
+  const int tid = threadIdx.x;
   for (int i = tid; i < NH * 16; i += THREADS) {
     const int j = i / 16, k = i % 16;
     *reinterpret_cast<__nv_bfloat16*>(reinterpret_cast<unsigned char*>(s.W1) + canon(j, k, 16)) =
@@ -127,6 +122,36 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_forward_tc5_kernel(const float
   }
   for (int i = tid; i < NO * NH; i += THREADS) s.W3[i / NH][i % NH] = P[dg_mlp_off_w3() + i];
   if (tid < NO) s.b3[tid] = P[dg_mlp_off_b3(NO) + tid];
+}
+
+// the same from a packed BF16 weight image (dg_mlp_pack)
+template <int NO>
+__device__ __forceinline__ void load_weights(Smem<NO>& s, const DgMlpW<NO>& w) {
+  constexpr int NH = DG_MLP_NH;
+  const int tid = threadIdx.x;
+  for (int i = tid; i < NH * 16; i += THREADS)
+    *reinterpret_cast<__nv_bfloat16*>(reinterpret_cast<unsigned char*>(s.W1) + canon(i / 16, i % 16, 16)) = w.W1[i];
+  for (int i = tid; i < NH * NH; i += THREADS)
+    *reinterpret_cast<__nv_bfloat16*>(reinterpret_cast<unsigned char*>(s.W2) + canon(i / NH, i % NH, NH)) = w.W2[i];
+  for (int j = tid; j < NH; j += THREADS) {
+    s.b1[j] = w.b1[j];
+    s.b2[j] = w.b2[j];
+  }
+  for (int i = tid; i < NO * NH; i += THREADS) s.W3[i / NH][i % NH] = w.W3[i / NH][i % NH];
+  if (tid < NO) s.b3[tid] = w.b3[tid];
+}
+
+// The tile engine (after load_weights): for each 128-row tile of the CTA, thread t takes
+// row = 128 tile + t.  prod(row, x) writes the row's 7 standardised features and returns a
+// flag of its own; cons(row, out, flag, valid) gets the NO outputs, that flag and whether
+// the launch's tensor-core waits all completed (when not, out is not valid).  Both are
+// called by every thread of the CTA for every tile (rows >= n included), so consumers may
+// use warp votes.  The engine allocates and frees the tensor memory and returns false
+// after a timeout (the remaining tiles still reach cons with valid = false).
+template <int NO, class Prod, class Cons>
+__device__ __forceinline__ bool run_tiles(Smem<NO>& s, int64_t n, Prod prod, Cons cons) {
+  constexpr int NH = DG_MLP_NH;
+  const int tid = threadIdx.x, warp = tid >> 5;
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(su32(&s.tmem)),
                  "r"(TMEM_COLS)
@@ -147,37 +172,35 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_forward_tc5_kernel(const float
   uint32_t parity = 0;
   bool ok = true;
   const int64_t tiles = (n + ROWS - 1) / ROWS;
-  for (int64_t tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x) {
+  for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
     const int64_t row = tile * ROWS + tid;
-    // features of this thread's row -> A of layer 1 (two core-matrix rows of 8)
-    {
-      float f[8];
-#pragma unroll
-      for (int k = 0; k < 8; ++k) f[k] = (row < n && k < NI) ? X[row * NI + k] : 0.0f;
+    float x[8];
+    const bool flag = prod(row, x);
+    if (ok) {
+      // features -> A of layer 1 (this thread's row: K 0-7 and the zero padding 8-15)
       uint4 lo, hi = make_uint4(0u, 0u, 0u, 0u);
-      lo.x = dgmlp::pack_bf16(f[0], f[1]);
-      lo.y = dgmlp::pack_bf16(f[2], f[3]);
-      lo.z = dgmlp::pack_bf16(f[4], f[5]);
-      lo.w = dgmlp::pack_bf16(f[6], f[7]);
+      lo.x = dgmlp::pack_bf16(x[0], x[1]);
+      lo.y = dgmlp::pack_bf16(x[2], x[3]);
+      lo.z = dgmlp::pack_bf16(x[4], x[5]);
+      lo.w = dgmlp::pack_bf16(x[6], x[7]);
       unsigned char* xb = reinterpret_cast<unsigned char*>(s.X);
       *reinterpret_cast<uint4*>(xb + canon(tid, 0, 16)) = lo;
       *reinterpret_cast<uint4*>(xb + canon(tid, 8, 16)) = hi;
+      fence_smem_async();
+      fence_before();
+      __syncthreads();
+      fence_after();
+      if (tid == 0) {
+        mma(tmem, sdesc(s.X, 128, 256), sdesc(s.W1, 128, 256), ID_L, 0);
+        commit(&s.bar);
+      }
+      // the wait's outcome made uniform across the CTA; the phase flips only on completion
+      ok = __syncthreads_and(wait_parity(&s.bar, parity)) != 0;
+      if (ok) parity ^= 1u;
+      fence_after();
     }
-    fence_smem_async();
-    fence_before();
-    __syncthreads();
-    fence_after();
-    if (tid == 0) {
-      mma(tmem, sdesc(s.X, 128, 256), sdesc(s.W1, 128, 256), ID_L, 0);
-      commit(&s.bar);
-    }
-    // the wait's outcome made uniform across the CTA (every later barrier is then reached
-    // by all threads); the phase flips only when it completed
-    ok = __syncthreads_and(wait_parity(&s.bar, parity)) != 0;
-    if (ok) parity ^= 1u;
-    fence_after();
-    // layer-1 epilogue: bias, GELU, BF16 -> A of layer 2 (this thread's row)
-    {
+    if (ok) {
+      // layer-1 epilogue: bias, GELU, BF16 -> A of layer 2 (this thread's row)
       unsigned char* hb = reinterpret_cast<unsigned char*>(s.H);
       float v[NH / 16][16];
 #pragma unroll
@@ -198,57 +221,75 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_forward_tc5_kernel(const float
           *reinterpret_cast<uint4*>(hb + canon(tid, 16 * c + 8 * h, NH)) = pk;
         }
       }
-    }
-    fence_smem_async();
-    fence_before();
-    __syncthreads();
-    fence_after();
-    if (tid == 0 && ok) {
+      fence_smem_async();
+      fence_before();
+      __syncthreads();
+      fence_after();
+      if (tid == 0) {
 #pragma unroll
-      for (int kb = 0; kb < NH / 16; ++kb)
-        mma(tmem + NH, sdesc(reinterpret_cast<unsigned char*>(s.H) + 256 * kb, 128, 1024),
-            sdesc(reinterpret_cast<unsigned char*>(s.W2) + 256 * kb, 128, 1024), ID_L, kb > 0);
-      commit(&s.bar);
-    }
-    if (ok) {
+        for (int kb = 0; kb < NH / 16; ++kb)
+          mma(tmem + NH, sdesc(reinterpret_cast<unsigned char*>(s.H) + 256 * kb, 128, 1024),
+              sdesc(reinterpret_cast<unsigned char*>(s.W2) + 256 * kb, 128, 1024), ID_L, kb > 0);
+        commit(&s.bar);
+      }
       ok = __syncthreads_and(wait_parity(&s.bar, parity)) != 0;
       if (ok) parity ^= 1u;
+      fence_after();
     }
-    fence_after();
     // layer-2 epilogue: bias, GELU, then the NO outputs as FP32 dot products with W3
     float out[NO];
 #pragma unroll
     for (int o = 0; o < NO; ++o) out[o] = s.b3[o];
-    float v2[NH / 16][16];
+    if (ok) {
+      float v2[NH / 16][16];
 #pragma unroll
-    for (int c = 0; c < NH / 16; ++c) ld16(tmem + lane_base + NH + 16 * c, v2[c]);
-    ld_wait();
+      for (int c = 0; c < NH / 16; ++c) ld16(tmem + lane_base + NH + 16 * c, v2[c]);
+      ld_wait();
 #pragma unroll
-    for (int c = 0; c < NH / 16; ++c) {
+      for (int c = 0; c < NH / 16; ++c) {
 #pragma unroll
-      for (int q = 0; q < 16; ++q) {
-        const float g = dgmlp::gelu_fast(v2[c][q] + s.b2[16 * c + q]);
+        for (int q = 0; q < 16; ++q) {
+          const float g = dgmlp::gelu_fast(v2[c][q] + s.b2[16 * c + q]);
 #pragma unroll
-        for (int o = 0; o < NO; ++o) out[o] += s.W3[o][16 * c + q] * g;
+          for (int o = 0; o < NO; ++o) out[o] += s.W3[o][16 * c + q] * g;
+        }
       }
     }
-    if (row < n && ok)
-#pragma unroll
-      for (int o = 0; o < NO; ++o) y[row * NO + o] = out[o];
+    cons(row, out, flag, ok);
     fence_before();
     __syncthreads();  // the next tile rewrites X, H and the accumulators
     fence_after();
   }
-  if (!ok) {  // uniform
-    if (tid == 0) atomicExch(err, 1u);
-    // the MMAs of the phase that timed out may still be in flight: one more bounded wait
+  if (!ok)  // uniform: the MMAs of the phase that timed out may still run; one more bounded wait
     wait_parity(&s.bar, parity);
-    fence_after();
-  }
   fence_before();
   __syncthreads();
+  fence_after();
   if (warp == 0)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+  return ok;
+}
+
+// y[n][NO] = network(X[n][7]) for standardised X.  *err is set to 1 when a bounded wait ran
+// out (the outputs of that launch are then not valid).  Launch with THREADS threads and
+// dynamic shared memory of at least sizeof(Smem<NO>) (more to limit resident CTAs).
+template <int NO>
+__global__ void __launch_bounds__(THREADS, 1) mlp_forward_tc5_kernel(const float* P, const float* X, float* y,
+                                                                     int64_t n, unsigned* err) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  Smem<NO>& s = *reinterpret_cast<Smem<NO>*>(smem_raw);
+  load_weights<NO>(s, P);
+  auto prod = [&](int64_t row, float* x) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) x[k] = (row < n && k < DG_MLP_NI) ? X[row * DG_MLP_NI + k] : 0.0f;
+    return true;
+  };
+  auto cons = [&](int64_t row, const float* out, bool, bool valid) {
+    if (row < n && valid)
+#pragma unroll
+      for (int o = 0; o < NO; ++o) y[row * NO + o] = out[o];
+  };
+  if (!run_tiles<NO>(s, n, prod, cons) && threadIdx.x == 0) atomicExch(err, 1u);
 }
 
 }  // namespace dgtc5
