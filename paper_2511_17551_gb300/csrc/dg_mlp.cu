@@ -3,10 +3,10 @@
 // Newton polish and the Newton fallback.
 //
 // Temperature surrogate: x in R^7 -> 64 -> 64 -> 1, x = standardised (Y_1..Y_5, ln rho,
-// e), output = standardised T.  Inference (dg_thermo_update in surrogate mode): one warp
-// evaluates 32 nodes as two 16-row tensor-core tiles (dg_mlp.cuh), then per node in
-// FP64: one Newton step from the prediction, accept when the next correction would be
-// <= 1e-6 T, otherwise run the plain Newton iteration (fallback, counted).
+// e), output = standardised T.  Inference (dg_thermo_update in surrogate mode): 128-node
+// tiles on the tcgen05 tensor cores (dg_mlp_tc5.cuh), then per node: one Newton step from
+// the prediction, accept when the next correction would be <= 1e-6 T, otherwise run the
+// plain Newton iteration (fallback, counted).
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <math.h>
@@ -64,36 +64,33 @@ __device__ __forceinline__ double clampT(double T) { return T < 200.0 ? 200.0 : 
 
 #define MLP_WARPS 4
 
+// Temperature surrogate on the fifth-generation tensor cores: CTAs of 128 threads take
+// 128-node tiles through the tcgen05 tile engine (dg_mlp_tc5.cuh).  Each thread forms its
+// node's features before the two tensor-core layers and, after them, polishes the
+// predicted temperature by one Newton step with the residual check, or runs the plain
+// Newton iteration (fallback, counted; also when the engine's waits ran out).
 template <typename T>
-__global__ void __launch_bounds__(32 * MLP_WARPS)
+__global__ void __launch_bounds__(dgtc5::THREADS, 1)
 thermo_mlp_kernel(const T* u, int64_t K, int np, int dim, const double* sp, const float* sp32, double* Tc,
                   T* pc, unsigned long long* status, const DgMlpDev* mlp, unsigned long long* stats) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  dgtc5::Smem<1>& sm = *reinterpret_cast<dgtc5::Smem<1>*>(smem_raw);
   __shared__ DgMlpDev m;
-  __shared__ float feat[MLP_WARPS][32][17];
-  __shared__ float yv[MLP_WARPS][2][1][16];
   copy_to_smem(m, mlp);
   __syncthreads();
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  dgtc5::load_weights<1>(sm, m.w);
   const int nv = NSPEC + dim + 1;
   const int64_t total = K * np;
   unsigned long long n_ok = 0, n_fb = 0;
-  // 32 nodes per warp and pass: two 16-row MMA tiles, then one node per lane in FP64
-  for (int64_t base = ((int64_t)blockIdx.x * MLP_WARPS + w) * 32; base < total;
-       base += (int64_t)gridDim.x * MLP_WARPS * 32) {
-    const int64_t i = base + lane;
-    const bool mine = i < total;
-    double Y[NSPEC], rho = 1.0, e = 0.0;
-    int64_t k = 0;
-    int node = 0;
-    if (mine) {
-      k = i / np;
-      node = (int)(i % np);
-      const T* uu = u + k * nv * np + node;
+  double Y[NSPEC], rho = 1.0, e = 0.0;  // this thread's node, carried from features to polish
+  auto prod = [&](int64_t i, float* x) {
+    if (i < total) {
+      const T* uu = u + (i / np) * nv * np + (i % np);
       rho = 0.0;
 #pragma unroll
-      for (int s = 0; s < NSPEC; ++s) {
-        Y[s] = (double)uu[s * np];
-        rho += Y[s];
+      for (int q = 0; q < NSPEC; ++q) {
+        Y[q] = (double)uu[q * np];
+        rho += Y[q];
       }
       double ke = 0.0;
       for (int d = 0; d < dim; ++d) {
@@ -103,42 +100,52 @@ thermo_mlp_kernel(const T* u, int64_t K, int np, int dim, const double* sp, cons
       const double ir = 1.0 / rho;
       e = (double)uu[(NSPEC + dim) * np] * ir - 0.5 * ke * ir * ir;
 #pragma unroll
-      for (int s = 0; s < NSPEC; ++s) Y[s] *= ir;
+      for (int q = 0; q < NSPEC; ++q) Y[q] *= ir;
     } else {
+      rho = 1.0;
+      e = 0.0;
 #pragma unroll
-      for (int s = 0; s < NSPEC; ++s) Y[s] = 0.2;
+      for (int q = 0; q < NSPEC; ++q) Y[q] = 0.2;
     }
-    {
-      float f[NI];
+    float f[NI];
 #pragma unroll
-      for (int s = 0; s < NSPEC; ++s) f[s] = (float)Y[s];
-      f[5] = logf((float)rho);
-      f[6] = (float)e;
+    for (int q = 0; q < NSPEC; ++q) f[q] = (float)Y[q];
+    f[5] = logf((float)rho);
+    f[6] = (float)e;
 #pragma unroll
-      for (int q = 0; q < NI; ++q) feat[w][lane][q] = (f[q] - m.mean[q]) * m.inv_std[q];
-#pragma unroll
-      for (int q = NI; q < 17; ++q) feat[w][lane][q] = 0.f;
+    for (int q = 0; q < NI; ++q) x[q] = (f[q] - m.mean[q]) * m.inv_std[q];
+    x[7] = 0.f;
+    return true;
+  };
+  // the plain FP64 Newton iteration from T1 (fallback); false when it did not converge
+  auto newton = [&](const PolyD& P, double& T1) {
+    for (int it = 0; it < 50; ++it) {
+      const double Tn = clampT(T1 - (P.e(T1) - e) / P.cv(T1));
+      const double step = fabs(Tn - T1);
+      T1 = Tn;
+      if (step <= 1e-12 * T1) return true;
     }
-    __syncwarp();
-    mlp16<1>(m.w, feat[w], yv[w][0]);
-    mlp16<1>(m.w, feat[w] + 16, yv[w][1]);
-    __syncwarp();
-    if (mine && sizeof(T) == 4) {
+    return false;
+  };
+  auto cons = [&](int64_t i, const float* y, bool, bool valid) {
+    if (i >= total) return;
+    const int64_t k = i / np;
+    const int node = (int)(i % np);
+    if (sizeof(T) == 4) {
       // mixed form: the same equation as its plain solve -- FP64 formation-energy constant
       // b0, FP32-rounded temperature coefficients, FP64 residual -- so accepted nodes and
       // the plain path agree to the acceptance tolerance
-      const double T0 = clampT((double)(m.muT + m.sigT * yv[w][lane >> 4][0][lane & 15]));
       float c32[6], R32 = 0.f;
       double b0 = 0.0;
 #pragma unroll
       for (int q = 0; q < 6; ++q) c32[q] = 0.f;
 #pragma unroll
-      for (int s = 0; s < NSPEC; ++s) {
-        b0 += Y[s] * sp[8 * s];
-        const float yf = (float)Y[s];
+      for (int q = 0; q < NSPEC; ++q) {
+        b0 += Y[q] * sp[8 * q];
+        const float yf = (float)Y[q];
 #pragma unroll
-        for (int q = 1; q < 6; ++q) c32[q] += yf * sp32[8 * s + q];
-        R32 += yf * sp32[8 * s + 6];
+        for (int r = 1; r < 6; ++r) c32[r] += yf * sp32[8 * q + r];
+        R32 += yf * sp32[8 * q + 6];
       }
       auto e64 = [&](double t) {
         return b0 + t * ((double)c32[1] + t * ((double)c32[2] + t * ((double)c32[3] +
@@ -147,72 +154,59 @@ thermo_mlp_kernel(const T* u, int64_t K, int np, int dim, const double* sp, cons
       auto cv32 = [&](float t) {
         return c32[1] + t * (2.f * c32[2] + t * (3.f * c32[3] + t * (4.f * c32[4] + t * 5.f * c32[5])));
       };
-      const float cv0 = cv32((float)T0);
-      double T1 = clampT(T0 - (e64(T0) - e) * (double)(1.0f / cv0));
-      const double r1 = e64(T1) - e;
-      if (fabs(r1) <= 1e-6 * (double)cv0 * T1) {
+      double T1 = 1000.0;
+      bool acc = false;
+      if (valid) {
+        const double T0 = clampT((double)(m.muT + m.sigT * y[0]));
+        const float cv0 = cv32((float)T0);
+        T1 = clampT(T0 - (e64(T0) - e) * (double)(1.0f / cv0));
+        acc = fabs(e64(T1) - e) <= 1e-6 * (double)cv0 * T1;
+      }
+      if (acc) {
         ++n_ok;
       } else {
-        // fallback: the plain FP64 Newton iteration from the polished value
         ++n_fb;
         PolyD P;
         poly_d(sp, Y, P);
-        bool conv = false;
-        for (int it = 0; it < 50; ++it) {
-          const double Tn = clampT(T1 - (P.e(T1) - e) / P.cv(T1));
-          const double step = fabs(Tn - T1);
-          T1 = Tn;
-          if (step <= 1e-12 * T1) {
-            conv = true;
-            break;
-          }
-        }
-        if (!conv) atomicCAS(status, 0ull, (DG_ST_NEWTON << 56) | (unsigned long long)k);
+        if (!newton(P, T1)) atomicCAS(status, 0ull, (DG_ST_NEWTON << 56) | (unsigned long long)k);
       }
       Tc[k * np + node] = T1;
       const float Tq = (float)T1, rhof = (float)rho;
       const float pf = rhof * R32 * Tq, cvf = cv32(Tq);
       pc[(k * 2 + 0) * np + node] = (T)pf;
       pc[(k * 2 + 1) * np + node] = (T)sqrtf((cvf + R32) / cvf * pf / rhof);
-    } else if (mine) {
+    } else {
       PolyD P;
       poly_d(sp, Y, P);
-      double T0 = clampT((double)(m.muT + m.sigT * yv[w][lane >> 4][0][lane & 15]));
-      // FP64 residuals; cv only scales the correction, FP32 is enough for it
-      const float cv0 = (float)P.b[1] + (float)T0 * (2.f * (float)P.b[2] + (float)T0 *
-                        (3.f * (float)P.b[3] + (float)T0 * (4.f * (float)P.b[4] + (float)T0 * 5.f * (float)P.b[5])));
-      double T1 = clampT(T0 - (P.e(T0) - e) / (double)cv0);
-      const double r1 = P.e(T1) - e;
-      if (fabs(r1) <= 1e-6 * (double)cv0 * T1) {
+      double T1 = 1000.0;
+      bool acc = false;
+      if (valid) {
+        const double T0 = clampT((double)(m.muT + m.sigT * y[0]));
+        // FP64 residuals; cv only scales the correction, FP32 is enough for it
+        const float cv0 = (float)P.b[1] + (float)T0 * (2.f * (float)P.b[2] + (float)T0 *
+                          (3.f * (float)P.b[3] + (float)T0 * (4.f * (float)P.b[4] + (float)T0 * 5.f * (float)P.b[5])));
+        T1 = clampT(T0 - (P.e(T0) - e) / (double)cv0);
+        acc = fabs(P.e(T1) - e) <= 1e-6 * (double)cv0 * T1;
+      }
+      if (acc) {
         ++n_ok;
       } else {
-        // fallback: the plain Newton iteration from the polished value
         ++n_fb;
-        bool conv = false;
-        for (int it = 0; it < 50; ++it) {
-          const double Tn = clampT(T1 - (P.e(T1) - e) / P.cv(T1));
-          const double step = fabs(Tn - T1);
-          T1 = Tn;
-          if (step <= 1e-12 * T1) {
-            conv = true;
-            break;
-          }
-        }
-        if (!conv) atomicCAS(status, 0ull, (DG_ST_NEWTON << 56) | (unsigned long long)k);
+        if (!newton(P, T1)) atomicCAS(status, 0ull, (DG_ST_NEWTON << 56) | (unsigned long long)k);
       }
       Tc[k * np + node] = T1;
       const double p = rho * P.Rmix * T1, cv = P.cv(T1);
       pc[(k * 2 + 0) * np + node] = (T)p;
       pc[(k * 2 + 1) * np + node] = (T)sqrt((cv + P.Rmix) / cv * p / rho);
     }
-    __syncwarp();
-  }
+  };
+  dgtc5::run_tiles<1>(sm, total, prod, cons);
   if (stats) {
     for (int o = 16; o > 0; o >>= 1) {
       n_ok += __shfl_xor_sync(0xffffffffu, n_ok, o);
       n_fb += __shfl_xor_sync(0xffffffffu, n_fb, o);
     }
-    if (lane == 0) {
+    if ((threadIdx.x & 31) == 0) {
       atomicAdd(&stats[0], n_ok);
       atomicAdd(&stats[1], n_fb);
     }
@@ -478,13 +472,26 @@ cudaError_t dg_mlp_set(DgThermo* th, const float* params_host, const double* sta
 
 cudaError_t dg_mlp_thermo_update(DgThermo* th, const void* u, int f32, cudaStream_t s) {
   const int64_t n = th->K * th->np;
-  const unsigned grid = grid_of((n + 31) / 32, MLP_WARPS);
-  if (f32)
-    thermo_mlp_kernel<float><<<grid, 32 * MLP_WARPS, 0, s>>>((const float*)u, th->K, th->np, th->dim,
-        th->species, th->coef32, th->T, (float*)th->pc, th->status, (const DgMlpDev*)th->mlp, th->mlp_stats);
-  else
-    thermo_mlp_kernel<double><<<grid, 32 * MLP_WARPS, 0, s>>>((const double*)u, th->K, th->np, th->dim,
-        th->species, th->coef32, th->T, (double*)th->pc, th->status, (const DgMlpDev*)th->mlp, th->mlp_stats);
+  // tensor-core tiles of 128 nodes; the dynamic shared memory is padded to 60 KB so that at
+  // most 3 CTAs (3 x 128 tensor-memory columns) share an SM
+  const size_t smem = sizeof(dgtc5::Smem<1>) > 60 * 1024 ? sizeof(dgtc5::Smem<1>) : 60 * 1024;
+  const int64_t t128 = (n + dgtc5::ROWS - 1) / dgtc5::ROWS;
+  const unsigned grid = (unsigned)(t128 < 152 * 3 ? t128 : 152 * 3);
+  cudaError_t e;
+  if (f32) {
+    auto k = thermo_mlp_kernel<float>;
+    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k<<<grid, dgtc5::THREADS, smem, s>>>((const float*)u, th->K, th->np, th->dim, th->species, th->coef32, th->T,
+                                         (float*)th->pc, th->status, (const DgMlpDev*)th->mlp, th->mlp_stats);
+  } else {
+    auto k = thermo_mlp_kernel<double>;
+    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k<<<grid, dgtc5::THREADS, smem, s>>>((const double*)u, th->K, th->np, th->dim, th->species, th->coef32,
+                                         th->T, (double*)th->pc, th->status, (const DgMlpDev*)th->mlp,
+                                         th->mlp_stats);
+  }
   return cudaGetLastError();
 }
 
