@@ -641,9 +641,20 @@ def run_reference(args, rank, world):
 def run_profile_case(name):
     """Small cases for ncu section captures (2 RK steps, then exit): 'fp64rhs' (NS TGV 16^3,
     N = 3, FP64 form), 'mixture' (5-species O-grid 16^3, N = 4, mixed), 'reacting'
-    (reacting O-grid 24 x 24 x 8, N = 4, mixed)."""
+    (reacting O-grid 24 x 24 x 8, N = 4, mixed); 'mlp' (the tcgen05 perceptron forward,
+    1 M rows, three calls)."""
     import torch
     import paper_2511_17551_gb300 as dg
+    if name == "mlp":
+        # the perceptron forward on the tcgen05 path, ten outputs, 1 M rows (3 calls)
+        rng = np.random.default_rng(5)
+        P = torch.from_numpy((0.3 * rng.normal(size=dg.dg_mlp_nparams(10))).astype(np.float32)).cuda()
+        X = torch.from_numpy(rng.normal(size=(1_000_000, 7)).astype(np.float32)).cuda()
+        y = torch.empty((1_000_000, 10), dtype=torch.float32, device="cuda")
+        for _ in range(3):
+            dg.dg_mlp_forward(P, X, y, tensor_cores=2)
+        torch.cuda.synchronize()
+        return
     if name == "fp64rhs":
         N = 3
         xi, _ = dg.dg_lgl_nodes(N)
@@ -691,7 +702,7 @@ def main():
                     help="skip the 16^3 N=7 Taylor-Green and the square-cylinder blocks")
     ap.add_argument("--react-elements", type=int, default=48, help="O-grid radial/angular elements")
     ap.add_argument("--react-steps", type=int, default=4)
-    ap.add_argument("--profile-case", choices=["fp64rhs", "mixture", "reacting"],
+    ap.add_argument("--profile-case", choices=["fp64rhs", "mixture", "reacting", "mlp"],
                     help="run one small case for an ncu capture and exit")
     args = ap.parse_args()
     rank, world, local_rank = _env_rank()
