@@ -328,18 +328,25 @@ rhs_kernel(const DgArgs a, const KConst kc) {
                                                    (pre_du ? NV : 0) + (have_elo ? 1 : 0)));
       if (tid == 0) mbar_expect(&s_bar, per_e * (unsigned)ne);
       __syncwarp();
+      // one copy per array when the shared-memory element stride equals the global block
+      // (the CTA's elements are contiguous), one per element and array otherwise
+      auto copy = [&](real* dst, int sstride, const real* src, int block, int e) {
+        if (sstride == block) {
+          if (e == 0) bulk_g2s(dst, src + e0 * block, (unsigned)(RS * block * ne), &s_bar);
+        } else {
+          bulk_g2s(dst + e * sstride, src + (e0 + e) * block, (unsigned)(RS * block), &s_bar);
+        }
+      };
       for (int j = tid; j < 8 * ne; j += 32) {
         const int e = j >> 3, kind = j & 7;
-        const int64_t g = e0 + e;
-        if (kind == 0) bulk_g2s(su + e * L::SU, (const real*)a.u + g * NV * NP, RS * NV * NP, &s_bar);
-        if (kind == 1) bulk_g2s(sja + e * L::SJA, (const real*)a.Ja + g * DIM * DIM * NP, RS * DIM * DIM * NP, &s_bar);
-        if (kind == 2) bulk_g2s(sij + e * L::SIJ, (const real*)a.invJ + g * NP, RS * NP, &s_bar);
-        if (kind == 3 && NSP > 1) bulk_g2s(spc + e * L::SPC, (const real*)a.pc + g * 2 * NP, RS * 2 * NP, &s_bar);
-        if (kind == 4 && NS)
-          bulk_g2s(sfv + e * L::SFV, (const real*)a.gradW + g * L::NFV * NP, RS * L::NFV * NP, &s_bar);
-        if (kind == 5 && pre_du) bulk_g2s(sdu + e * L::SDU, (const real*)a.du + g * NV * NP, RS * NV * NP, &s_bar);
-        if (kind == 6 && have_elo)
-          bulk_g2s(sacc + e * NP, (const real*)a.ulo + g * NV * NP + (NSP + DIM) * NP, RS * NP, &s_bar);
+        if (kind == 0) copy(su, L::SU, (const real*)a.u, NV * NP, e);
+        if (kind == 1) copy(sja, L::SJA, (const real*)a.Ja, DIM * DIM * NP, e);
+        if (kind == 2) copy(sij, L::SIJ, (const real*)a.invJ, NP, e);
+        if (kind == 3 && NSP > 1) copy(spc, L::SPC, (const real*)a.pc, 2 * NP, e);
+        if (kind == 4 && NS) copy(sfv, L::SFV, (const real*)a.gradW, L::NFV * NP, e);
+        if (kind == 5 && pre_du) copy(sdu, L::SDU, (const real*)a.du, NV * NP, e);
+        if (kind == 6 && have_elo)  // rows at a source stride of NV NP: one per element
+          bulk_g2s(sacc + e * NP, (const real*)a.ulo + (e0 + e) * NV * NP + (NSP + DIM) * NP, RS * NP, &s_bar);
       }
     }
   } else {
