@@ -1055,37 +1055,6 @@ gradient_kernel(const DgArgs a, const KConst kc) {
   const real* gu = (const real*)a.u;
   // the conserved state is staged in the gradient region, which is free until the line phase
   static_assert(L::TOTAL - L::G >= L::EPB * NV * NP, "gradient region too small for the state");
-  // this thread's grid line (at most one: THREADS >= EPB x LINES) and the states of the
-  // neighbours across its two end faces, loaded before the staging below so that their
-  // latency overlaps it
-  auto line_of = [](int t, int& e, int& d, int& m) {
-    if (L::UNI) {  // warp-uniform direction
-      d = t / (L::EPB * S::LPD);
-      e = (t / S::LPD) % L::EPB;
-      m = t % S::LPD;
-    } else {
-      e = t / S::LINES;
-      d = (t % S::LINES) / S::LPD;
-      m = t % S::LPD;
-    }
-  };
-  real nbs[2][NV], keep[2];
-  {
-    int e = 0, d = 0, m = 0;
-    if (tid < L::EPB * S::LINES) line_of(tid, e, d, m);
-    const bool mine = tid < L::EPB * S::LINES && e < ne;
-    const int s = S::stride(d), base = S::line_base(d, m);
-#pragma unroll
-    for (int side = 0; side < 2; ++side) {
-      const int nb = mine ? a.nbr[(e0 + e) * 2 * DIM + 2 * d + side] : -1;
-      // boundary faces get their lifting from boundary_lift_kernel: here a valid address
-      // (the own element, or element 0 for idle threads) and a zero weight
-      const real* un = gu + (int64_t)(nb >= 0 ? nb : (mine ? e0 + e : 0)) * NV * NP + base + (side ? 0 : N) * s;
-      keep[side] = nb >= 0 ? real(1) : real(0);
-#pragma unroll
-      for (int k = 0; k < NV; ++k) nbs[side][k] = un[k * NP];
-    }
-  }
   // contiguous blocks of the CTA's elements: three TMA bulk copies where sizes and
   // addresses allow, 16-byte cp.async otherwise
   constexpr int RS = sizeof(real);
@@ -1131,12 +1100,20 @@ gradient_kernel(const DgArgs a, const KConst kc) {
     sw[e * L::SW + DIM * NP + pn] = p * ir;
   }
   __syncthreads();
-  if (tid < L::EPB * S::LINES) {
-    const int t = tid;
+  for (int t = tid; t < L::EPB * S::LINES; t += nth) {
     int e, d, m;
-    line_of(t, e, d, m);
-    if (e < ne) {
+    if (L::UNI) {  // warp-uniform direction
+      d = t / (L::EPB * S::LPD);
+      e = (t / S::LPD) % L::EPB;
+      m = t % S::LPD;
+    } else {
+      e = t / S::LINES;
+      d = (t % S::LINES) / S::LPD;
+      m = t % S::LPD;
+    }
+    if (e >= ne) continue;
     const int s = S::stride(d), base = S::line_base(d, m);
+    const int64_t eg = e0 + e;
     const real* w = sw + e * L::SW;
     real Wl[N1][NW];
 #pragma unroll
@@ -1155,23 +1132,29 @@ gradient_kernel(const DgArgs a, const KConst kc) {
       }
 #pragma unroll
     for (int side = 0; side < 2; ++side) {
+      const int f = 2 * d + side;
+      const int nnode = base + (side ? 0 : N) * s;
+      const int nb = a.nbr[eg * 2 * DIM + f];
       const int i = side ? N : 0;
-      const real* un = nbs[side];
+      // boundary faces get their lifting from boundary_lift_kernel: here a valid address
+      // (the own element) and a zero weight, without a branch
+      const real* un = gu + (int64_t)(nb >= 0 ? nb : eg) * NV * NP + nnode;
+      const real keep = nb >= 0 ? real(1) : real(0);
       real rn = 0;
 #pragma unroll
-      for (int k = 0; k < NSP; ++k) rn += un[k];
+      for (int k = 0; k < NSP; ++k) rn += un[k * NP];
       real irn = RealOps<real>::rcp(rn), ke = 0, Wn[NW];
 #pragma unroll
       for (int c = 0; c < DIM; ++c) {
-        Wn[c] = un[NSP + c] * irn;
-        ke += un[NSP + c] * Wn[c];
+        Wn[c] = un[(NSP + c) * NP] * irn;
+        ke += un[(NSP + c) * NP] * Wn[c];
       }
-      Wn[DIM] = kc.gm1 * (un[NSP + DIM] - real(0.5) * ke) * irn;
+      Wn[DIM] = kc.gm1 * (un[(NSP + DIM) * NP] - real(0.5) * ke) * irn;
 #pragma unroll
       for (int c = 0; c < NW; ++c) {
         real ws = real(0.5) * (Wl[i][c] + Wn[c]);
-        if (side) G[N][c] += keep[side] * B.iw[N] * (ws - Wl[N][c]);
-        else G[0][c] -= keep[side] * B.iw[0] * (ws - Wl[0][c]);
+        if (side) G[N][c] += keep * B.iw[N] * (ws - Wl[N][c]);
+        else G[0][c] -= keep * B.iw[0] * (ws - Wl[0][c]);
       }
     }
     real* g = sg + e * L::SG + d * NW * NP;
@@ -1179,7 +1162,6 @@ gradient_kernel(const DgArgs a, const KConst kc) {
     for (int i = 0; i < N1; ++i)
 #pragma unroll
       for (int c = 0; c < NW; ++c) g[c * NP + SWZ(base + i * s)] = G[i][c];
-    }
   }
   __syncthreads();
   // physical gradients G_x = (1/J) sum_d Ja^d_x Q_d; written as they are (grad_mode 1) or
