@@ -464,8 +464,10 @@ rhs_kernel(const DgArgs a, const KConst kc) {
   }
   __syncthreads();
 
-  // ---- phase B1: one thread per line: volume terms
-  for (int t = tid; t < EPB * S::LINES; t += nth) {
+  // ---- phase B1: one thread per line (THREADS >= EPB x LINES: at most one each): volume terms
+  static_assert(L::THREADS >= EPB * S::LINES, "one line per thread");
+  if (tid < EPB * S::LINES) {
+    const int t = tid;
     int e, d, m;
     if (L::UNI) {  // warp-uniform direction
       d = t / (EPB * S::LPD);
@@ -476,7 +478,7 @@ rhs_kernel(const DgArgs a, const KConst kc) {
       d = (t % S::LINES) / S::LPD;
       m = t % S::LPD;
     }
-    if (e >= ne) continue;
+    if (e < ne) {
     const int s = S::stride(d), base = S::line_base(d, m);
     const real* q = sq + e * L::SQ;
     const real* ja = sja + e * L::SJA + d * DIM * NP;  // Ja^d components at [c][node]
@@ -594,6 +596,7 @@ rhs_kernel(const DgArgs a, const KConst kc) {
     for (int i = 0; i < N1; ++i)
 #pragma unroll
       for (int k = 0; k < NV; ++k) sa[k * NP + SW(base + i * s)] = acc[i][k];
+    }
   }
   __syncthreads();
 
