@@ -249,6 +249,31 @@ __device__ __forceinline__ void volume_flux(int vf, real rL, const real* vL, rea
   (void)NV;
 }
 
+// LLF flux between the own state o and the other side's state x for either orientation
+// with one code instance: F(L, R) with (L, R) = (o, x) when own_left, (x, o) otherwise;
+// bit for bit the same as surface_flux(DG_SF_LLF, L, R, ...) (the mean and the maximum
+// are symmetric, the jump only changes sign)
+template <typename real, int DIM, int NSP>
+__device__ __forceinline__ void llf_oriented(const NodeState<real, DIM, NSP>& o, const NodeState<real, DIM, NSP>& x,
+                                             bool own_left, const real* n, real* f) {
+  constexpr int NV = NSP + DIM + 1;
+  real nn = 0, vno = 0, vnx = 0;
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) {
+    nn += n[d] * n[d];
+    vno += o.v[d] * n[d];
+    vnx += x.v[d] * n[d];
+  }
+  nn = RealOps<real>::sqrt_(nn);
+  real fo[NV], fx[NV];
+  phys_flux<real, DIM, NSP>(o, n, fo);
+  phys_flux<real, DIM, NSP>(x, n, fx);
+  const real lam = fmax(fabs(vno) + o.c * nn, fabs(vnx) + x.c * nn);
+  const real hl = own_left ? real(0.5) * lam : real(-0.5) * lam;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) f[k] = real(0.5) * (fo[k] + fx[k]) - hl * (x.u[k] - o.u[k]);
+}
+
 template <typename real, int DIM, int NSP>
 __device__ __forceinline__ void surface_flux(int sf, const NodeState<real, DIM, NSP>& L,
                                              const NodeState<real, DIM, NSP>& R, const real* n,

@@ -679,6 +679,7 @@ rhs_kernel(const DgArgs a, const KConst kc) {
     int phys = outer_state<DIM, NSP>(a, kc, nb, nbu[it], nbpc[it], nbe[it], o, nface, x, ok);
     if (!ok) latch_status(a.status, DG_ST_NONPHYS, nb >= 0 ? nb : eg);
     if (phys) phys_flux<real, DIM, NSP>(x, nface, Fs);
+    else if (FL) llf_oriented<real, DIM, NSP>(o, x, side != 0, nface, Fs);  // the production pair: LLF
     else if (side) surface_flux<real, DIM, NSP>(sf, o, x, nface, kc.inv_gm1, kc.pref, Fs);
     else surface_flux<real, DIM, NSP>(sf, x, o, nface, kc.inv_gm1, kc.pref, Fs);
 #pragma unroll
