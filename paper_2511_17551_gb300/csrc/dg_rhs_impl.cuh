@@ -728,27 +728,21 @@ rhs_kernel(const DgArgs a, const KConst kc) {
   }
   __syncthreads();
 
-  // ---- phase C: one thread per node.  The compensation parts of all of a thread's
-  // nodes are loaded first (one memory round trip).
+  // ---- phase C: one thread per node and pass.
   real lam_a = 0, lam_v = 0;
   constexpr int CIT = (EPB * NP + L::THREADS - 1) / L::THREADS;
   const bool comp = sizeof(real) == 4 && a.mode == 1 && a.ulo != nullptr;
-  real lo_r[CIT][NV];
-  if (comp) {
-#pragma unroll
-    for (int it = 0; it < CIT; ++it) {
-      const int i = tid + it * L::THREADS;
-      if (i < ne * NP) {
-        const real* lp = (const real*)a.ulo + (e0 + i / NP) * NV * NP + i % NP;
-#pragma unroll
-        for (int k = 0; k < NV; ++k) lo_r[it][k] = lp[k * NP];
-      }
-    }
-  }
-#pragma unroll
+  // one node per pass (a loop, not unrolled: one code instance of the update)
+#pragma unroll 1
   for (int it = 0; it < CIT; ++it) {
     const int i = tid + it * L::THREADS;
     if (i >= ne * NP) break;
+    real lo_r[1][NV];
+    if (comp) {
+      const real* lp = (const real*)a.ulo + (e0 + i / NP) * NV * NP + i % NP;
+#pragma unroll
+      for (int k = 0; k < NV; ++k) lo_r[0][k] = lp[k * NP];
+    }
     const int e = i / NP, node = i % NP, pn = SW(node);
     const real ij = sij[e * L::SIJ + node];
     const real* sa = sacc + e * L::SACC + pn;
@@ -784,7 +778,7 @@ rhs_kernel(const DgArgs a, const KConst kc) {
         if (comp) {
           // compensated FP32 state: (hi, lo) += B dn by an exact TwoSum (Knuth), so the
           // rounding of every stage update is carried instead of lost
-          const real inc = lo_r[it][k] + kc.rkB * dn;
+          const real inc = lo_r[0][k] + kc.rkB * dn;
           const real s2 = hi + inc;
           const real bb = s2 - hi;
           ((real*)a.ulo)[gbase + k * NP] = (hi - (s2 - bb)) + (inc - bb);
