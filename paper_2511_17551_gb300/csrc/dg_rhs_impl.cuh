@@ -1098,9 +1098,7 @@ gradient_kernel(const DgArgs a, const KConst kc) {
     sw[e * L::SW + DIM * NP + pn] = p * ir;
   }
   __syncthreads();
-  static_assert(L::THREADS >= L::EPB * S::LINES, "one line per thread");
-  if (tid < L::EPB * S::LINES) {  // one line per thread
-    const int t = tid;
+  for (int t = tid; t < L::EPB * S::LINES; t += nth) {
     int e, d, m;
     if (L::UNI) {  // warp-uniform direction
       d = t / (L::EPB * S::LPD);
@@ -1111,7 +1109,7 @@ gradient_kernel(const DgArgs a, const KConst kc) {
       d = (t % S::LINES) / S::LPD;
       m = t % S::LPD;
     }
-    if (e < ne) {
+    if (e >= ne) continue;
     const int s = S::stride(d), base = S::line_base(d, m);
     const int64_t eg = e0 + e;
     const real* w = sw + e * L::SW;
@@ -1162,7 +1160,6 @@ gradient_kernel(const DgArgs a, const KConst kc) {
     for (int i = 0; i < N1; ++i)
 #pragma unroll
       for (int c = 0; c < NW; ++c) g[c * NP + SWZ(base + i * s)] = G[i][c];
-    }
   }
   __syncthreads();
   // physical gradients G_x = (1/J) sum_d Ja^d_x Q_d; written as they are (grad_mode 1) or
