@@ -598,10 +598,9 @@ rhs_kernel(const DgArgs a, const KConst kc) {
       for (int k = 0; k < NV; ++k) sa[k * NP + SW(base + i * s)] = acc[i][k];
     }
   }
-  __syncthreads();
-
   // ---- phase B2: one thread per face node and pass: the neighbour trace, then the
-  // interface flux and lifting.
+  // interface flux and lifting.  The first pass's neighbour trace is loaded before the
+  // line phase's closing barrier, so that its latency overlaps the wait.
   constexpr int FN = L::FACE_NODES, FIT = L::FIT, NG = NS ? DIM + 1 : 1;
   // face-node threads: face-uniform warps where the layout is swizzled
   auto face_of = [](int t, int& e, int& f, int& m) {
@@ -615,38 +614,39 @@ rhs_kernel(const DgArgs a, const KConst kc) {
       m = t % S::LPD;
     }
   };
+  real nbu[1][NV], nbpc[1][2], nbg[1][NG], nbe[1];
+  auto gather = [&](int it) {
+    int e, f, m;
+    face_of(tid + it * L::THREADS, e, f, m);
+    if (e >= ne) return;
+    const int d = f >> 1, side = f & 1;
+    const int nnode = S::line_base(d, m) + (side ? 0 : N) * S::stride(d);
+    const int nb = a.nbr[(e0 + e) * 2 * DIM + f];
+    nbe[0] = real(0);
+    if (nb < 0) return;
+    const real* gu = (const real*)a.u + (int64_t)nb * NV * NP + nnode;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) nbu[0][k] = gu[k * NP];
+    if (have_elo) nbe[0] = ((const real*)a.ulo)[(int64_t)nb * NV * NP + (NSP + DIM) * NP + nnode];
+    if (NSP > 1) {
+      const real* pc = (const real*)a.pc + (int64_t)nb * 2 * NP + nnode;
+      nbpc[0][0] = pc[0];
+      nbpc[0][1] = pc[NP];
+    }
+    if (NS) {
+      // the neighbour's f^v . n: its contravariant viscous flux of direction d (the
+      // partner face node sees the same face metric)
+      const real* gn = (const real*)a.gradW + (int64_t)nb * L::NFV * NP + d * (DIM + 1) * NP + nnode;
+#pragma unroll
+      for (int c = 0; c < NG; ++c) nbg[0][c] = gn[c * NP];
+    }
+  };
+  gather(0);
+  __syncthreads();
   // one face node per pass (a loop, not unrolled: one code instance of the face work)
 #pragma unroll 1
   for (int it = 0; it < FIT; ++it) {
-    real nbu[1][NV], nbpc[1][2], nbg[1][NG], nbe[1];
-    {
-    int e, f, m;
-    face_of(tid + it * L::THREADS, e, f, m);
-    if (e < ne) {
-      const int d = f >> 1, side = f & 1;
-      const int nnode = S::line_base(d, m) + (side ? 0 : N) * S::stride(d);
-      const int nb = a.nbr[(e0 + e) * 2 * DIM + f];
-      nbe[0] = real(0);
-      if (nb >= 0) {
-        const real* gu = (const real*)a.u + (int64_t)nb * NV * NP + nnode;
-#pragma unroll
-        for (int k = 0; k < NV; ++k) nbu[0][k] = gu[k * NP];
-        if (have_elo) nbe[0] = ((const real*)a.ulo)[(int64_t)nb * NV * NP + (NSP + DIM) * NP + nnode];
-        if (NSP > 1) {
-          const real* pc = (const real*)a.pc + (int64_t)nb * 2 * NP + nnode;
-          nbpc[0][0] = pc[0];
-          nbpc[0][1] = pc[NP];
-        }
-        if (NS) {
-          // the neighbour's f^v . n: its contravariant viscous flux of direction d (the
-          // partner face node sees the same face metric)
-          const real* gn = (const real*)a.gradW + (int64_t)nb * L::NFV * NP + d * (DIM + 1) * NP + nnode;
-#pragma unroll
-          for (int c = 0; c < NG; ++c) nbg[0][c] = gn[c * NP];
-        }
-      }
-    }
-  }
+    if (it > 0) gather(it);
     int e, f, m;
     face_of(tid + it * L::THREADS, e, f, m);
     if (e >= ne) continue;
