@@ -726,26 +726,23 @@ rhs_kernel(const DgArgs a, const KConst kc) {
         sa[(NSP + c) * NP] -= iw * (wall ? fx[c] - fvd[c * NP] : real(0.5) * (fx[c] - fvd[c * NP]));
     }
   }
-  // ---- phase C: one thread per node and pass.  The first pass's compensation parts are
-  // loaded before the interface phase's closing barrier, so that their latency overlaps it.
+  __syncthreads();
+
+  // ---- phase C: one thread per node and pass.
   real lam_a = 0, lam_v = 0;
   constexpr int CIT = (EPB * NP + L::THREADS - 1) / L::THREADS;
   const bool comp = sizeof(real) == 4 && a.mode == 1 && a.ulo != nullptr;
-  real lo_r[1][NV];
-  auto load_lo = [&](int i) {
-    if (!comp || i >= ne * NP) return;
-    const real* lp = (const real*)a.ulo + (e0 + i / NP) * NV * NP + i % NP;
-#pragma unroll
-    for (int k = 0; k < NV; ++k) lo_r[0][k] = lp[k * NP];
-  };
-  load_lo(tid);
-  __syncthreads();
   // one node per pass (a loop, not unrolled: one code instance of the update)
 #pragma unroll 1
   for (int it = 0; it < CIT; ++it) {
     const int i = tid + it * L::THREADS;
     if (i >= ne * NP) break;
-    if (it > 0) load_lo(i);
+    real lo_r[1][NV];
+    if (comp) {
+      const real* lp = (const real*)a.ulo + (e0 + i / NP) * NV * NP + i % NP;
+#pragma unroll
+      for (int k = 0; k < NV; ++k) lo_r[0][k] = lp[k * NP];
+    }
     const int e = i / NP, node = i % NP, pn = SW(node);
     const real ij = sij[e * L::SIJ + node];
     const real* sa = sacc + e * L::SACC + pn;
