@@ -1097,38 +1097,21 @@ gradient_kernel(const DgArgs a, const KConst kc) {
     for (int d = 0; d < DIM; ++d) sw[e * L::SW + d * NP + pn] = vv[d];
     sw[e * L::SW + DIM * NP + pn] = p * ir;
   }
-  // this thread's grid line (at most one: THREADS >= EPB x LINES) and the states of the
-  // neighbours across its two end faces, loaded before the barrier so that their latency
-  // overlaps it; boundary faces get their lifting from boundary_lift_kernel (here a valid
-  // address, the own element, and a zero weight)
-  static_assert(L::THREADS >= L::EPB * S::LINES, "one line per thread");
-  int le = 0, ld = 0, lm = 0;
-  if (L::UNI) {  // warp-uniform direction
-    ld = tid / (L::EPB * S::LPD);
-    le = (tid / S::LPD) % L::EPB;
-    lm = tid % S::LPD;
-  } else {
-    le = tid / S::LINES;
-    ld = (tid % S::LINES) / S::LPD;
-    lm = tid % S::LPD;
-  }
-  const bool line_mine = tid < L::EPB * S::LINES && le < ne;
-  real nbs[2][NV], keep[2];
-  if (line_mine) {
-#pragma unroll
-    for (int side = 0; side < 2; ++side) {
-      const int nb = a.nbr[(e0 + le) * 2 * DIM + 2 * ld + side];
-      const real* un = gu + (int64_t)(nb >= 0 ? nb : e0 + le) * NV * NP + S::line_base(ld, lm) +
-                       (side ? 0 : N) * S::stride(ld);
-      keep[side] = nb >= 0 ? real(1) : real(0);
-#pragma unroll
-      for (int k = 0; k < NV; ++k) nbs[side][k] = un[k * NP];
-    }
-  }
   __syncthreads();
-  if (line_mine) {
-    const int e = le, d = ld, m = lm;
+  for (int t = tid; t < L::EPB * S::LINES; t += nth) {
+    int e, d, m;
+    if (L::UNI) {  // warp-uniform direction
+      d = t / (L::EPB * S::LPD);
+      e = (t / S::LPD) % L::EPB;
+      m = t % S::LPD;
+    } else {
+      e = t / S::LINES;
+      d = (t % S::LINES) / S::LPD;
+      m = t % S::LPD;
+    }
+    if (e >= ne) continue;
     const int s = S::stride(d), base = S::line_base(d, m);
+    const int64_t eg = e0 + e;
     const real* w = sw + e * L::SW;
     real Wl[N1][NW];
 #pragma unroll
@@ -1147,23 +1130,29 @@ gradient_kernel(const DgArgs a, const KConst kc) {
       }
 #pragma unroll
     for (int side = 0; side < 2; ++side) {
+      const int f = 2 * d + side;
+      const int nnode = base + (side ? 0 : N) * s;
+      const int nb = a.nbr[eg * 2 * DIM + f];
       const int i = side ? N : 0;
-      const real* un = nbs[side];
+      // boundary faces get their lifting from boundary_lift_kernel: here a valid address
+      // (the own element) and a zero weight, without a branch
+      const real* un = gu + (int64_t)(nb >= 0 ? nb : eg) * NV * NP + nnode;
+      const real keep = nb >= 0 ? real(1) : real(0);
       real rn = 0;
 #pragma unroll
-      for (int k = 0; k < NSP; ++k) rn += un[k];
+      for (int k = 0; k < NSP; ++k) rn += un[k * NP];
       real irn = RealOps<real>::rcp(rn), ke = 0, Wn[NW];
 #pragma unroll
       for (int c = 0; c < DIM; ++c) {
-        Wn[c] = un[NSP + c] * irn;
-        ke += un[NSP + c] * Wn[c];
+        Wn[c] = un[(NSP + c) * NP] * irn;
+        ke += un[(NSP + c) * NP] * Wn[c];
       }
-      Wn[DIM] = kc.gm1 * (un[NSP + DIM] - real(0.5) * ke) * irn;
+      Wn[DIM] = kc.gm1 * (un[(NSP + DIM) * NP] - real(0.5) * ke) * irn;
 #pragma unroll
       for (int c = 0; c < NW; ++c) {
         real ws = real(0.5) * (Wl[i][c] + Wn[c]);
-        if (side) G[N][c] += keep[side] * B.iw[N] * (ws - Wl[N][c]);
-        else G[0][c] -= keep[side] * B.iw[0] * (ws - Wl[0][c]);
+        if (side) G[N][c] += keep * B.iw[N] * (ws - Wl[N][c]);
+        else G[0][c] -= keep * B.iw[0] * (ws - Wl[0][c]);
       }
     }
     real* g = sg + e * L::SG + d * NW * NP;
