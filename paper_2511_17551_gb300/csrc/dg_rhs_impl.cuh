@@ -614,7 +614,7 @@ rhs_kernel(const DgArgs a, const KConst kc) {
       m = t % S::LPD;
     }
   };
-  real nbu[1][NV], nbpc[1][2], nbg[1][NG], nbe[1];
+  real nbu[NV], nbpc[2], nbg[NG], nbe;  // the neighbour's trace at this pass's face node
   auto gather = [&](int it) {
     int e, f, m;
     face_of(tid + it * L::THREADS, e, f, m);
@@ -622,23 +622,23 @@ rhs_kernel(const DgArgs a, const KConst kc) {
     const int d = f >> 1, side = f & 1;
     const int nnode = S::line_base(d, m) + (side ? 0 : N) * S::stride(d);
     const int nb = a.nbr[(e0 + e) * 2 * DIM + f];
-    nbe[0] = real(0);
+    nbe = real(0);
     if (nb < 0) return;
     const real* gu = (const real*)a.u + (int64_t)nb * NV * NP + nnode;
 #pragma unroll
-    for (int k = 0; k < NV; ++k) nbu[0][k] = gu[k * NP];
-    if (have_elo) nbe[0] = ((const real*)a.ulo)[(int64_t)nb * NV * NP + (NSP + DIM) * NP + nnode];
+    for (int k = 0; k < NV; ++k) nbu[k] = gu[k * NP];
+    if (have_elo) nbe = ((const real*)a.ulo)[(int64_t)nb * NV * NP + (NSP + DIM) * NP + nnode];
     if (NSP > 1) {
       const real* pc = (const real*)a.pc + (int64_t)nb * 2 * NP + nnode;
-      nbpc[0][0] = pc[0];
-      nbpc[0][1] = pc[NP];
+      nbpc[0] = pc[0];
+      nbpc[1] = pc[NP];
     }
     if (NS) {
       // the neighbour's f^v . n: its contravariant viscous flux of direction d (the
       // partner face node sees the same face metric)
       const real* gn = (const real*)a.gradW + (int64_t)nb * L::NFV * NP + d * (DIM + 1) * NP + nnode;
 #pragma unroll
-      for (int c = 0; c < NG; ++c) nbg[0][c] = gn[c * NP];
+      for (int c = 0; c < NG; ++c) nbg[c] = gn[c * NP];
     }
   };
   gather(0);
@@ -676,7 +676,7 @@ rhs_kernel(const DgArgs a, const KConst kc) {
     NodeState<real, DIM, NSP> x;
     bool ok = true;
     real Fs[NV];
-    int phys = outer_state<DIM, NSP>(a, kc, nb, nbu[0], nbpc[0], nbe[0], o, nface, x, ok);
+    int phys = outer_state<DIM, NSP>(a, kc, nb, nbu, nbpc, nbe, o, nface, x, ok);
     if (!ok) latch_status(a.status, DG_ST_NONPHYS, nb >= 0 ? nb : eg);
     if (phys) phys_flux<real, DIM, NSP>(x, nface, Fs);
     else if (FL) llf_oriented<real, DIM, NSP>(o, x, side != 0, nface, Fs);  // the production pair: LLF
@@ -696,7 +696,7 @@ rhs_kernel(const DgArgs a, const KConst kc) {
       real fx[DIM + 1];
       if (nb >= 0) {
 #pragma unroll
-        for (int c = 0; c <= DIM; ++c) fx[c] = nbg[0][c];
+        for (int c = 0; c <= DIM; ++c) fx[c] = nbg[c];
       } else {
         real h = fvd[DIM * NP];
 #pragma unroll
