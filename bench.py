@@ -43,7 +43,7 @@ WORDS_MAIN_EULER = 5 + 9 + 1 + 5 + 5 + 5 + 10
 WORDS_GRAD = 5 + 9 + 1 + 12
 # dram__bytes_read.sum + dram__bytes_write.sum of the current mixed-form NS N=3 rhs_kernel
 # per node, from one ncu capture of the 24^3 case (traffic scales with the node count)
-RHS_DRAM_B_PER_NODE = 157.2
+RHS_DRAM_B_PER_NODE = 157.4
 # FP64 flops per node of the FP64-form NS N=3 rhs_kernel (2 DFMA + DMUL + DADD thread
 # instructions, one ncu capture of the 16^3 case): its roofline is the FP64 pipe
 RHS_FP64_FLOPS_PER_NODE = 1005.3
