@@ -665,11 +665,105 @@ int or_step_rk(const or_problem* P, double* u, int nsteps, double cfl, double dt
  * Both steps keep the element mean.  Returns 1 when an element mean itself is not
  * admissible (rhobar <= eps or p(ubar) <= eps).  n_limited (may be NULL) counts the
  * elements changed. */
+/* Zhang-Shu limiter for a mixture (reading of the positivity-preservation remark for the
+ * reacting cases): per element, with J-weighted means, (1) the partial densities move
+ * toward their means by one common factor th1 until every rho_s >= min(eps, mean rho_s);
+ * (2) every variable moves toward its mean by th2 until T >= OR_T_FLOOR at every node,
+ * i.e. g(u) = (E - sum_s rho_s e_s(T_floor)) rho - |m|^2 / 2 >= 0 (e(T) increases with T),
+ * th2 the smallest root in [0, 1] of the quadratic g(ubar + t (u - ubar)) = 0. */
+static int positivity_mixture(const or_problem* P, const basis* b, double* u, double eps, int* n_limited) {
+  const int dim = b->dim, np = b->np, nv = b->nv, ns = P->n_species;
+  double ef[OR_MAX_SPECIES];
+  for (int s = 0; s < ns; ++s) ef[s] = or_species_energy(P->species + 8 * s, OR_T_FLOOR);
+  int err = 0, nlim = 0;
+  double* W = (double*)malloc(sizeof(double) * np);
+  for (int64_t k = 0; k < P->K; ++k) {
+    double* ue = u + (size_t)k * nv * np;
+    double Wsum = 0.0, ubar[OR_MAX_NV] = {0};
+    for (int node = 0; node < np; ++node) {
+      double wq = 1.0;
+      for (int d = 0; d < dim; ++d) wq *= b->w[line_pos(b, d, node)];
+      W[node] = wq * P->J[(size_t)k * np + node];
+      Wsum += W[node];
+      for (int v = 0; v < nv; ++v) ubar[v] += W[node] * ue[v * np + node];
+    }
+    for (int v = 0; v < nv; ++v) ubar[v] /= Wsum;
+    /* g at the mean and the mean's admissibility */
+    double rbar = 0.0, Ebar = ubar[ns + dim], mb2 = 0.0;
+    int bad = 0;
+    for (int s = 0; s < ns; ++s) {
+      rbar += ubar[s];
+      Ebar -= ubar[s] * ef[s];
+      bad |= !(ubar[s] >= 0.0);
+    }
+    for (int d = 0; d < dim; ++d) mb2 += ubar[ns + d] * ubar[ns + d];
+    if (bad || !(rbar > 0.0) || !(Ebar * rbar - 0.5 * mb2 > 0.0)) {
+      err = 1;
+      continue;
+    }
+    int changed = 0;
+    /* 1. partial densities, one common factor */
+    double th1 = 1.0;
+    for (int s = 0; s < ns; ++s) {
+      const double es = fmin(eps, ubar[s]);
+      double mn = ue[s * np];
+      for (int node = 1; node < np; ++node) mn = fmin(mn, ue[s * np + node]);
+      if (mn < es) th1 = fmin(th1, (ubar[s] - es) / (ubar[s] - mn));
+    }
+    if (th1 < 1.0) {
+      for (int s = 0; s < ns; ++s)
+        for (int node = 0; node < np; ++node) ue[s * np + node] = ubar[s] + th1 * (ue[s * np + node] - ubar[s]);
+      changed = 1;
+    }
+    /* 2. temperature floor */
+    double th2 = 1.0;
+    for (int node = 0; node < np; ++node) {
+      double r = 0.0, Ep = ue[(ns + dim) * np + node], m2 = 0.0, dr = 0.0, dE = 0.0, mdm = 0.0, dm2 = 0.0;
+      for (int s = 0; s < ns; ++s) {
+        r += ue[s * np + node];
+        Ep -= ue[s * np + node] * ef[s];
+        dr += ue[s * np + node] - ubar[s];
+        dE -= (ue[s * np + node] - ubar[s]) * ef[s];
+      }
+      dE += ue[(ns + dim) * np + node] - ubar[ns + dim];
+      for (int d = 0; d < dim; ++d) {
+        const double m = ue[(ns + d) * np + node], dm = m - ubar[ns + d];
+        m2 += m * m;
+        mdm += ubar[ns + d] * dm;
+        dm2 += dm * dm;
+      }
+      if (Ep * r - 0.5 * m2 >= 0.0 && r > 0.0) continue;
+      const double a = dE * dr - 0.5 * dm2;
+      const double bq = dE * rbar + Ebar * dr - mdm;
+      const double c = Ebar * rbar - 0.5 * mb2; /* > 0 */
+      double t;
+      if (fabs(a) < 1e-14 * (fabs(bq) + fabs(c))) {
+        t = -c / bq;
+      } else {
+        const double disc = fmax(0.0, bq * bq - 4.0 * a * c);
+        const double q = -0.5 * (bq + copysign(sqrt(disc), bq));
+        const double t1 = q / a, t2 = c / q;
+        t = (t1 >= 0.0 && t1 <= 1.0) ? t1 : t2;
+      }
+      th2 = fmin(th2, fmin(1.0, fmax(0.0, t)));
+    }
+    if (th2 < 1.0) {
+      for (int v = 0; v < nv; ++v)
+        for (int node = 0; node < np; ++node) ue[v * np + node] = ubar[v] + th2 * (ue[v * np + node] - ubar[v]);
+      changed = 1;
+    }
+    nlim += changed;
+  }
+  free(W);
+  if (n_limited) *n_limited = nlim;
+  return err;
+}
+
 int or_positivity(const or_problem* P, double* u, double eps, int* n_limited) {
   basis b;
   make_basis(P, &b);
   const int dim = b.dim, np = b.np, nv = b.nv;
-  if (P->n_species > 0) return 1;
+  if (P->n_species > 0) return positivity_mixture(P, &b, u, eps, n_limited);
   const double g1 = P->gamma - 1.0;
   int err = 0, nlim = 0;
   double* W = (double*)malloc(sizeof(double) * np);

@@ -59,7 +59,9 @@ typedef struct {
   int n_reactions;          /* finite-rate chemistry (5 species), 0 = frozen */
   const double* reactions;  /* [n_reactions][19] */
   double chem_dt;           /* point-implicit time scale of the source; 0 = explicit */
-  double positivity_eps;    /* > 0: Zhang-Shu positivity limiter after every RK stage (one gas) */
+  double positivity_eps;    /* > 0: Zhang-Shu positivity limiter after every RK stage: one gas,
+                               density and pressure >= eps; mixtures, partial densities >= eps
+                               (or their element mean, if smaller) and T >= OR_T_FLOOR */
   /* NS, one gas: s > 0 switches on Sutherland's law (Eq. sutherland),
    * mu(T) = mu (1 + s) th^1.5 / (th + s), th = (p / rho) / rt; mu is the viscosity at th = 1 */
   double sutherland_s, sutherland_rt;
@@ -123,6 +125,7 @@ double or_max_dt(const or_problem* P, const double* u, double cfl);
 int or_step_rk(const or_problem* P, double* u, int nsteps, double cfl, double dt_fixed,
                double* t);
 int or_diagnostics(const or_problem* P, const double* u, double* out);
+#define OR_T_FLOOR 200.0  /* temperature floor of the mixture limiter (the Newton clamp) */
 int or_positivity(const or_problem* P, double* u, double eps, int* n_limited);
 void or_ck45(double* A, double* B, double* c);
 int or_temperature_field(const or_problem* P, const double* u, double* T);

@@ -103,3 +103,117 @@ def test_both_steps_leave_an_admissible_element_with_the_same_mean():
     assert _pressure(v).min() >= eps * (1 - 1e-9)
     # the pressure bound is the active one: some node sits on it
     assert abs(_pressure(v)[3].min() - eps) < 1e-9
+
+
+# ---------------------------------------------------------------- mixtures
+T_FLOOR = 200.0
+
+
+def _mix_problem(orc_mod, seed=7):
+    import workloads as W
+    x, _ = orc_mod.lgl(3)
+    xyz, nbr, face = W.box_mesh((3, 2, 2), x, (-np.pi,) * 3, (np.pi,) * 3, periodic=True, warp=0.1)
+    sp = W.species_table()
+    w = W.mixture_primitive(xyz, rho=0.1, vel=(300.0, -50.0, 20.0), T=1500.0, seed=seed)
+    o = orc_mod.Oracle(3, 3, xyz, nbr, face, n_species=5, volume_flux=orc_mod.VF_DUCROS, species=sp)
+    return o, sp, w
+
+
+def _energy_at(sp, rs, T):
+    """rho e(T) of a node with partial densities rs (the e_s(T) of the species table)."""
+    RU = 8.314462618
+    e = 0.0
+    for s in range(len(rs)):
+        a = sp[s, 1:]
+        h = a[0] * T + a[1] * T ** 2 / 2 + a[2] * T ** 3 / 3 + a[3] * T ** 4 / 4 + a[4] * T ** 5 / 5 + a[5]
+        e += rs[s] * RU / sp[s, 0] * (h - T)
+    return e
+
+
+def _mix_means(o, u):
+    import oracle
+    _, w = oracle.lgl(3)
+    Wt = _weights(o, w)
+    return np.einsum("kn,kvn->kv", Wt, u) / Wt.sum(1)[:, None]
+
+
+def test_mixture_admissible_state_is_untouched():
+    import oracle
+    o, sp, w = _mix_problem(oracle)
+    u = o.prim_to_cons(w)
+    v, n = o.positivity(u, 1e-8)
+    assert n == 0 and np.array_equal(v, u)
+
+
+def test_mixture_negative_partial_density_is_lifted_keeping_the_means():
+    """A negative partial density at one node: all species of the element move toward their
+    means by one factor, the critical species lands on the floor, the means are kept."""
+    import oracle
+    o, sp, w = _mix_problem(oracle)
+    u = o.prim_to_cons(w)
+    k, node, s = 2, 17, 3
+    u[k, s, node] = -0.2 * u[k, s].mean()
+    eps = 1e-6
+    v, n = o.positivity(u, eps)
+    assert n == 1
+    assert v[:, :5].min() >= eps * (1 - 1e-12) - 1e-18
+    assert abs(v[k, s, node] - eps) < 1e-12 * abs(u[k, s].mean())
+    assert np.allclose(_mix_means(o, v), _mix_means(o, u), rtol=1e-13, atol=1e-14)
+    others = [kk for kk in range(u.shape[0]) if kk != k]
+    assert np.array_equal(v[others], u[others])
+    # one common factor for the species; momentum and energy untouched by this step
+    th = (v[k, :5] - _mix_means(o, u)[k, :5, None]) / (u[k, :5] - _mix_means(o, u)[k, :5, None])
+    assert np.allclose(th, th[0, 0], rtol=1e-9) and np.array_equal(v[k, 5:], u[k, 5:])
+
+
+def _excess(sp, uu):
+    """rho (e - e(T_floor)) at every node of uu [..., 9, np] (rho e from the conserved state;
+    e(T) written out from the species table here): >= 0 exactly when T >= T_floor."""
+    rs = uu[..., :5, :]
+    rho = rs.sum(-2)
+    m2 = (uu[..., 5:8, :] ** 2).sum(-2)
+    rho_e = uu[..., 8, :] - 0.5 * m2 / rho
+    ef = np.array([_energy_at(sp, np.eye(5)[s], T_FLOOR) for s in range(5)])
+    return rho_e - np.tensordot(ef, rs, axes=([0], [-2]))
+
+
+def test_mixture_temperature_floor_matches_bisection():
+    """A node below the temperature floor (150 K): the element moves toward its mean by the
+    factor at which that node's internal energy reaches e(T_floor), found here by bisection;
+    afterwards no node lies below the floor."""
+    import oracle
+    o, sp, w = _mix_problem(oracle)
+    u = o.prim_to_cons(w)
+    k, node = 5, 30
+    rs, m = u[k, :5, node], u[k, 5:8, node]
+    u[k, 8, node] = _energy_at(sp, rs, 150.0) + 0.5 * (m @ m) / rs.sum()
+    assert _excess(sp, u[k])[node] < 0
+    v, n = o.positivity(u, 1e-8)
+    assert n == 1
+    scale = np.abs(u[k, 8]).max()
+    assert _excess(sp, v).min() > -1e-12 * scale
+    assert abs(_excess(sp, v[k])[node]) < 1e-10 * scale     # the critical node on the floor
+    ubar = _mix_means(o, u)[k]
+    lo, hi = 0.0, 1.0   # excess(0) > 0, excess(1) < 0
+    for _ in range(60):
+        mid = 0.5 * (lo + hi)
+        uu = ubar[:, None] + mid * (u[k] - ubar[:, None])
+        if _excess(sp, uu)[node] >= 0:
+            lo = mid
+        else:
+            hi = mid
+    th = (v[k, 8, node] - ubar[8]) / (u[k, 8, node] - ubar[8])
+    assert abs(th - lo) < 1e-9
+    assert np.allclose(_mix_means(o, v), _mix_means(o, u), rtol=1e-13, atol=1e-14)
+
+
+def test_mixture_inadmissible_mean_is_refused():
+    import oracle
+    o, sp, w = _mix_problem(oracle)
+    u = o.prim_to_cons(w)
+    k = 1
+    for node in range(u.shape[2]):   # the whole element below the floor
+        rs, m = u[k, :5, node], u[k, 5:8, node]
+        u[k, 8, node] = _energy_at(sp, rs, 150.0) + 0.5 * (m @ m) / rs.sum()
+    with pytest.raises(ValueError):
+        o.positivity(u, 1e-8)
