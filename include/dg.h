@@ -66,6 +66,8 @@ enum { DG_SF_LLF = 0, DG_SF_HLLC = 1, DG_SF_EC = 2,
        /* HLL with the Davis wave speeds (the third solver the paper names) */
        DG_SF_HLL = 3 };
 enum { DG_FP64 = 0, DG_MIXED = 1 };
+/* temperature floor of the mixture positivity limiter: the clamp of the temperature solve (K) */
+#define DG_T_FLOOR 200.0
 enum { DG_THERMO_NEWTON = 0, DG_THERMO_MLP = 1 };
 /* boundary kinds (weak, through the numerical fluxes).  Inflow: advective flux f(u_ext).n;
  * outflow: f(u).n; walls: the mirror state (normal velocity reversed) through the Riemann
@@ -115,13 +117,15 @@ typedef struct {
                                recovered from the compensated energy relative to
                                p_ref / (gamma - 1): low-Mach fluctuations keep their FP32
                                digits.  0 for none; must be 0 for mixtures. */
-  double positivity_eps;    /* one gas: > 0 applies the Zhang-Shu positivity limiter (the
-                               limiter the paper uses for its shock problems) to the state
-                               after every RK stage of dg_step_rk: per element, density then
-                               pressure >= positivity_eps at every node by scaling toward the
-                               element mean (which it keeps).  The next step's CFL time step
-                               uses the wave speeds of the last stage before limiting.  0 for
-                               none; must be 0 for mixtures. */
+  double positivity_eps;    /* > 0 applies the Zhang-Shu positivity limiter (the limiter the
+                               paper uses for its shock problems) to the state after every RK
+                               stage of dg_step_rk, per element by scaling toward the element
+                               mean (which it keeps).  One gas: density, then pressure >=
+                               positivity_eps at every node.  Mixtures: partial densities >=
+                               min(positivity_eps, their element mean), by one common factor,
+                               then T >= DG_T_FLOOR (internal energy >= e(DG_T_FLOOR)).  The
+                               next step's CFL time step uses the wave speeds of the last stage
+                               before limiting.  0 for none. */
   double sutherland_s;      /* one gas, Navier-Stokes: > 0 switches on Sutherland's law
                                (Eq. sutherland), mu(T) = mu (1 + s) th^1.5 / (th + s) with
                                th = (p / rho) / sutherland_rt, in the viscous fluxes (kappa

@@ -21,6 +21,7 @@ struct dg_ctx {
   double gamma, mu, Pr, alpha_max, p_ref, pos_eps;
   double suth_s, suth_rt;
   int ind_var;
+  double pos_ef[8];  // mixture limiter: e_s(T_floor) per unit mass
   unsigned long long* pos_count;  // elements changed by the positivity limiter
   cudaStream_t stream;
   bool own_stream;
@@ -342,6 +343,7 @@ DgArgs base_args(dg_ctx* c) {
   a.suth_s = a.ns ? c->suth_s : 0.0;
   a.suth_rt = c->suth_rt;
   a.ind_var = c->ind_var;
+  for (int q = 0; q < 8; ++q) a.pos_ef[q] = c->pos_ef[q];
   const bool f32 = c->precision == DG_MIXED;
   a.Ja = f32 ? (const void*)c->Ja32 : (const void*)c->Ja64;
   a.invJ = f32 ? (const void*)c->invJ32 : (const void*)c->invJ64;
@@ -557,7 +559,7 @@ dg_status dg_init_mesh(const dg_mesh_desc* m, const dg_physics_desc* p, dg_ctx**
     return DG_EINVAL;
   if (p->n_species == 0 && !(p->gamma > 1.0)) return DG_EINVAL;
   if (!(p->p_ref >= 0.0) || (p->n_species > 0 && p->p_ref != 0.0)) return DG_EINVAL;
-  if (!(p->positivity_eps >= 0.0) || (p->n_species > 0 && p->positivity_eps != 0.0)) return DG_EINVAL;
+  if (!(p->positivity_eps >= 0.0)) return DG_EINVAL;
   if (!(p->sutherland_s >= 0.0) || (p->sutherland_s > 0.0 && (!(p->sutherland_rt > 0.0) || p->n_species > 0)))
     return DG_EINVAL;
   if (p->indicator_variable != 0 && p->indicator_variable != 1) return DG_EINVAL;
@@ -620,6 +622,13 @@ dg_status dg_init_mesh(const dg_mesh_desc* m, const dg_physics_desc* p, dg_ctx**
   c->suth_s = p->sutherland_s;
   c->suth_rt = p->sutherland_s > 0.0 ? p->sutherland_rt : 1.0;
   c->ind_var = p->indicator_variable;
+  // the mixture limiter's energy floor: e_s(T_floor) = R_s (a1 T + a2 T^2/2 + ... + a6 - T)
+  for (int q = 0; q < p->n_species; ++q) {
+    const double* sp = p->species + 8 * q;
+    const double T = DG_T_FLOOR, Rs = 8.314462618 / sp[0];
+    c->pos_ef[q] = Rs * (sp[1] * T + sp[2] * T * T / 2.0 + sp[3] * T * T * T / 3.0 + sp[4] * T * T * T * T / 4.0 +
+                         sp[5] * T * T * T * T * T / 5.0 + sp[6] - T);
+  }
   c->mu = p->mu;
   c->Pr = p->Pr;
   c->alpha_max = p->alpha_max;

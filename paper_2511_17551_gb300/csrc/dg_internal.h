@@ -30,6 +30,7 @@ struct DgArgs {
   double visc_coef;              // gamma mu / Pr (viscous time-step bound)
   double suth_s, suth_rt;        // Sutherland's law: s = S / T_ref (0: constant mu), p/rho at T_ref
   int ind_var;                   // shock indicator on 0: rho p, 1: p
+  double pos_ef[8];              // mixture limiter: e_s(T_floor) per unit mass of each species
   double cfl, dt_fixed, rkA, rkB;
   const void* u;          // [K][nv][np] input state
   void* out;              // mode 0: rhs; mode 1: new state

@@ -971,14 +971,152 @@ __device__ __forceinline__ void limit_element(const DgArgs& a, real* u, real* ul
   if (lane == 0 && nlim) atomicAdd(nlim, 1ull);
 }
 
+// FP64 passes for one element of a mixture (whole warp): partial densities toward their
+// means by one common factor th1 until rho_s >= min(eps, mean rho_s); then every variable
+// toward its mean by th2 until the internal energy reaches e(T_floor) at every node, i.e.
+// g = (E - sum_s rho_s e_s(T_floor)) rho - |m|^2 / 2 >= 0, th2 the smallest root in [0, 1]
+// of the quadratic g(ubar + t (u - ubar)); e_s(T_floor) per unit mass in a.pos_ef.
+template <int DIM, int N, int NSP>
+__device__ __forceinline__ void limit_element_mix(const DgArgs& a, real* u, real* ulo, double eps,
+                                                  unsigned long long* nlim, int64_t k, int lane) {
+  using S = Shape<DIM, N>;
+  constexpr int NP = S::NP, N1 = S::N1, NV = NSP + DIM + 1;
+  const BasisTab<real>& B = c_tab[N];
+  real* ue = u + k * NV * NP;
+  real* le = ulo ? ulo + k * NV * NP : nullptr;
+  const real* ij = (const real*)a.invJ + k * NP;
+  auto val = [&](int v, int n) { return (double)ue[v * NP + n] + (le ? (double)le[v * NP + n] : 0.0); };
+  auto weight = [&](int n) {
+    double wq = (double)B.w[n % N1] * (double)B.w[(n / N1) % N1];
+    if (DIM == 3) wq *= (double)B.w[n / (N1 * N1)];
+    return wq / (double)ij[n];
+  };
+  // g of a state and its two parts: E' = E - sum_s rho_s e_s(T_floor), rho
+  auto gparts = [&](const double* x, double& Ep, double& r) {
+    Ep = x[NSP + DIM];
+    r = 0.0;
+#pragma unroll
+    for (int q = 0; q < NSP; ++q) {
+      Ep -= x[q] * a.pos_ef[q];
+      r += x[q];
+    }
+  };
+  // pass 1: means and minima
+  double acc[NV + 1], smin[NSP], gmin = 1e300;
+#pragma unroll
+  for (int v = 0; v <= NV; ++v) acc[v] = 0.0;
+#pragma unroll
+  for (int q = 0; q < NSP; ++q) smin[q] = 1e300;
+  for (int n = lane; n < NP; n += 32) {
+    const double W = weight(n);
+    double x[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      x[v] = val(v, n);
+      acc[v] += W * x[v];
+    }
+    acc[NV] += W;
+#pragma unroll
+    for (int q = 0; q < NSP; ++q) smin[q] = fmin(smin[q], x[q]);
+    double Ep, r, m2 = 0.0;
+    gparts(x, Ep, r);
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) m2 += x[NSP + d] * x[NSP + d];
+    gmin = fmin(gmin, r > 0.0 ? Ep * r - 0.5 * m2 : -1.0);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+    for (int v = 0; v <= NV; ++v) acc[v] += __shfl_xor_sync(0xffffffffu, acc[v], o);
+#pragma unroll
+    for (int q = 0; q < NSP; ++q) smin[q] = fmin(smin[q], __shfl_xor_sync(0xffffffffu, smin[q], o));
+    gmin = fmin(gmin, __shfl_xor_sync(0xffffffffu, gmin, o));
+  }
+  double ub[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) ub[v] = acc[v] / acc[NV];
+  double th1 = 1.0;
+  bool bad = false;
+#pragma unroll
+  for (int q = 0; q < NSP; ++q) {
+    bad = bad || !(ub[q] >= 0.0);
+    const double es = fmin(eps, ub[q]);
+    if (smin[q] < es) th1 = fmin(th1, (ub[q] - es) / (ub[q] - smin[q]));
+  }
+  if (th1 >= 1.0 && gmin >= 0.0) return;
+  double Ebar, rbar, mb2 = 0.0;
+  gparts(ub, Ebar, rbar);
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) mb2 += ub[NSP + d] * ub[NSP + d];
+  const double c = Ebar * rbar - 0.5 * mb2;
+  if (bad || !(rbar > 0.0) || !(c > 0.0)) {
+    if (lane == 0) latch_status(a.status, DG_ST_NONPHYS, k);
+    return;
+  }
+  auto put = [&](int v, int n, double x) {
+    const real h = (real)x;
+    ue[v * NP + n] = h;
+    if (le) le[v * NP + n] = (real)(x - (double)h);
+  };
+  // pass 2: partial densities, one common factor
+  if (th1 < 1.0) {
+    for (int n = lane; n < NP; n += 32)
+#pragma unroll
+      for (int q = 0; q < NSP; ++q) put(q, n, ub[q] + th1 * (val(q, n) - ub[q]));
+    __syncwarp();
+  }
+  // pass 3: temperature floor
+  double th2 = 1.0;
+  for (int n = lane; n < NP; n += 32) {
+    double x[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) x[v] = val(v, n);
+    double Ep, r, m2 = 0.0, dr = 0.0, dE = x[NSP + DIM] - ub[NSP + DIM], mdm = 0.0, dm2 = 0.0;
+    gparts(x, Ep, r);
+#pragma unroll
+    for (int q = 0; q < NSP; ++q) {
+      dr += x[q] - ub[q];
+      dE -= (x[q] - ub[q]) * a.pos_ef[q];
+    }
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+      const double dm = x[NSP + d] - ub[NSP + d];
+      m2 += x[NSP + d] * x[NSP + d];
+      mdm += ub[NSP + d] * dm;
+      dm2 += dm * dm;
+    }
+    if (r > 0.0 && Ep * r - 0.5 * m2 >= 0.0) continue;
+    const double qa = dE * dr - 0.5 * dm2;
+    const double qb = dE * rbar + Ebar * dr - mdm;
+    double t;
+    if (fabs(qa) < 1e-14 * (fabs(qb) + fabs(c))) {
+      t = -c / qb;
+    } else {
+      const double disc = fmax(0.0, qb * qb - 4.0 * qa * c);
+      const double q = -0.5 * (qb + copysign(sqrt(disc), qb));
+      const double t1 = q / qa, t2 = c / q;
+      t = (t1 >= 0.0 && t1 <= 1.0) ? t1 : t2;
+    }
+    th2 = fmin(th2, fmin(1.0, fmax(0.0, t)));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) th2 = fmin(th2, __shfl_xor_sync(0xffffffffu, th2, o));
+  if (th2 < 1.0) {
+    for (int n = lane; n < NP; n += 32)
+#pragma unroll
+      for (int v = 0; v < NV; ++v) put(v, n, ub[v] + th2 * (val(v, n) - ub[v]));
+  }
+  if (lane == 0 && nlim && (th1 < 1.0 || th2 < 1.0)) atomicAdd(nlim, 1ull);
+}
+
 // The limiter kernel: a warp screens EPW consecutive elements (about 128 nodes) in the
 // form's precision with all loads in flight (margins cover the rounding of the check and
 // the low part of the state), then runs the FP64 passes only for the flagged elements.
-template <int DIM, int N>
+template <int DIM, int N, int NSP>
 __global__ void __launch_bounds__(128) positivity_kernel(const DgArgs a, real* u, real* ulo, double eps,
                                                          unsigned long long* nlim) {
   using S = Shape<DIM, N>;
-  constexpr int NP = S::NP, NV = DIM + 2;
+  constexpr int NP = S::NP, NV = NSP + DIM + 1;
   constexpr int EPW = NP >= 128 ? 1 : 128 / NP;
   static_assert(EPW <= 32, "flag mask");
   const int lane = threadIdx.x & 31;
@@ -993,19 +1131,40 @@ __global__ void __launch_bounds__(128) positivity_kernel(const DgArgs a, real* u
   for (int n = lane; n < ch; n += 32) {
     const int el = n / NP, node = n - el * NP;
     const real* ue = ub + el * NV * NP + node;
-    const real r = ue[0], E = ue[(1 + DIM) * NP];
+    const real E = ue[(NSP + DIM) * NP];
     real m2 = 0;
 #pragma unroll
-    for (int d = 0; d < DIM; ++d) m2 += ue[(1 + d) * NP] * ue[(1 + d) * NP];
-    // with r > 0: p >= eps + margin  <=>  r (E - (eps + margin)/(gamma-1)) >= |m|^2 / 2
-    const real pbound = (epsr + tol * fabs(E)) * igm1;
-    if (!(r >= epsr * (real(1) + tol) && r * (E - pbound) >= real(0.5) * m2)) flag |= 1u << el;
+    for (int d = 0; d < DIM; ++d) m2 += ue[(NSP + d) * NP] * ue[(NSP + d) * NP];
+    bool ok;
+    if (NSP == 1) {
+      // with r > 0: p >= eps + margin  <=>  r (E - (eps + margin)/(gamma-1)) >= |m|^2 / 2
+      const real r = ue[0];
+      const real pbound = (epsr + tol * fabs(E)) * igm1;
+      ok = r >= epsr * (real(1) + tol) && r * (E - pbound) >= real(0.5) * m2;
+    } else {
+      // every partial density above the floor; E - sum rho_s e_s(T_floor), less a margin,
+      // times rho above |m|^2 / 2
+      real r = 0, Ep = E, mag = fabs(E);
+      ok = true;
+#pragma unroll
+      for (int q = 0; q < NSP; ++q) {
+        const real rq = ue[q * NP];
+        ok = ok && rq >= epsr * (real(1) + tol);
+        r += rq;
+        const real t = rq * (real)a.pos_ef[q];
+        Ep -= t;
+        mag += fabs(t);
+      }
+      ok = ok && r * (Ep - tol * mag) >= real(0.5) * m2;
+    }
+    if (!ok) flag |= 1u << el;
   }
   flag = __reduce_or_sync(0xffffffffu, flag);
   while (flag) {
     const int el = __ffs(flag) - 1;
     flag &= flag - 1;
-    limit_element<DIM, N>(a, u, ulo, eps, nlim, k0 + el, lane);
+    if (NSP == 1) limit_element<DIM, N>(a, u, ulo, eps, nlim, k0 + el, lane);
+    else limit_element_mix<DIM, N, NSP>(a, u, ulo, eps, nlim, k0 + el, lane);
   }
 }
 
@@ -1516,13 +1675,13 @@ cudaError_t launch_grad_t(const DgArgs& a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-template <int DIM, int N>
+template <int DIM, int N, int NSP>
 cudaError_t launch_pos_t(const DgArgs& a, void* u, void* ulo, double eps, unsigned long long* nlim,
                          cudaStream_t st) {
   constexpr int NP = Shape<DIM, N>::NP, EPW = NP >= 128 ? 1 : 128 / NP;
   const int64_t warps = (a.K + EPW - 1) / EPW;
   const int64_t grid = (warps * 32 + 127) / 128;
-  positivity_kernel<DIM, N><<<(unsigned)grid, 128, 0, st>>>(a, (real*)u, (real*)ulo, eps, nlim);
+  positivity_kernel<DIM, N, NSP><<<(unsigned)grid, 128, 0, st>>>(a, (real*)u, (real*)ulo, eps, nlim);
   return cudaGetLastError();
 }
 
@@ -1559,7 +1718,7 @@ cudaError_t launch_ind_t(const DgArgs& a, double amax, void* out, cudaStream_t s
 #define DG_RHS_CALL(DIM, N, NSP, NS) DG_PREFIX::launch_rhs_t<DIM, N, NSP, NS>(a, st)
 #define DG_GRAD_CALL(DIM, N, NSP, X) DG_PREFIX::launch_grad_t<DIM, N, NSP>(a, st)
 #define DG_IND_CALL(DIM, N, NSP, X) DG_PREFIX::launch_ind_t<DIM, N, NSP>(a, amax, out, st)
-#define DG_POS_CALL(DIM, N, NSP, X) DG_PREFIX::launch_pos_t<DIM, N>(a, u, ulo, eps, nlim, st)
+#define DG_POS_CALL(DIM, N, NSP, X) DG_PREFIX::launch_pos_t<DIM, N, NSP>(a, u, ulo, eps, nlim, st)
 
 cudaError_t DG_CAT(DG_PREFIX, _rhs)(const DgArgs& a, cudaStream_t st) {
 #ifndef DG_GENERIC_ONLY
@@ -1591,6 +1750,7 @@ cudaError_t DG_CAT(DG_PREFIX, _positivity)(const DgArgs& a, void* u, void* ulo, 
                                           unsigned long long* nlim, cudaStream_t st) {
   if (a.dim == 3 && a.nsp == 1) { DG_DISPATCH_N(DG_POS_CALL, 3, 1, 0) }
   if (a.dim == 2 && a.nsp == 1) { DG_DISPATCH_N(DG_POS_CALL, 2, 1, 0) }
+  if (a.dim == 3 && a.nsp == 5) { DG_DISPATCH_N_MIX(DG_POS_CALL, 3, 5, 0) }
   return cudaErrorInvalidValue;
 }
 
