@@ -336,10 +336,10 @@ def run_mixture(args, stream_ptr, world):
     steps = max(2, args.mix_steps)
     sp = W.species_table()
 
-    def make(precision):
+    def make(precision, positivity_eps=0.0):
         s = dg.Solver(3, N, xyz, nbr, face, n_species=5, species=sp, volume_flux=dg.DG_VF_DUCROS,
                       surface_flux=dg.DG_SF_LLF, bc_kind=[1, 2, 3], bc_prim=np.stack([fs] * 3),
-                      alpha_max=0.5, precision=precision, stream=stream_ptr)
+                      alpha_max=0.5, precision=precision, stream=stream_ptr, positivity_eps=positivity_eps)
         s.set_primitive(w0)
         return s
 
@@ -367,6 +367,14 @@ def run_mixture(args, stream_ptr, world):
                            "thermo_ms_per_launch": prof["thermo"][0] / max(1, prof["thermo"][1]),
                            "rhs_ms_per_launch": prof["rhs"][0] / max(1, prof["rhs"][1]),
                            "device_ms_per_step_by_kernel": per_kind(prof, steps)}
+    # the same with the mixture positivity limiter after every stage (partial densities
+    # >= 1e-9 kg/m^3, T >= 200 K): its screening pass and any limiting it does
+    sl = make(dg.DG_MIXED, positivity_eps=1e-9)
+    wl, pl, _ = timed(sl, steps)
+    out["mixed_newton_limiter"] = {"value": world * dof * 5 * steps / wl, "ms_per_step": wl * 1e3 / steps,
+                                   "limited_element_stages": dg.dg_limiter_stats(sl.ctx),
+                                   "device_ms_per_step_by_kernel": per_kind(pl, steps)}
+    sl.close()
     # training data from the plain solver's own run, then the surrogate
     t0 = time.perf_counter()
     X, T = S.collect(s.ctx, args.train_samples, 10, 2, cfl=0.3)
