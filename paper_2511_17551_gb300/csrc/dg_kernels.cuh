@@ -346,6 +346,25 @@ __device__ __forceinline__ void surface_flux(int sf, const NodeState<real, DIM, 
 // physical viscous flux f^v_x (x = physical direction) for one gas; c = 0..DIM-1
 // momentum, c = DIM energy (the density component is zero).  g[x][a] = d(W_a)/dx_x with
 // W = (v_1..v_DIM, theta = p / rho).
+// a[k] += c x[k] for k < M: two at a time with the packed FP32 FMA of sm_100 (__ffma2_rn,
+// per component the same rounding as fmaf) in single precision, one at a time otherwise
+template <int M, typename real>
+__device__ __forceinline__ void axpy(real* a, real c, const real* x) {
+  if constexpr (sizeof(real) == 4) {
+    const float2 cc = make_float2(c, c);
+#pragma unroll
+    for (int k = 0; k + 1 < M; k += 2) {
+      const float2 r = __ffma2_rn(cc, make_float2(x[k], x[k + 1]), make_float2(a[k], a[k + 1]));
+      a[k] = r.x;
+      a[k + 1] = r.y;
+    }
+    if (M % 2) a[M - 1] = fmaf(c, x[M - 1], a[M - 1]);
+  } else {
+#pragma unroll
+    for (int k = 0; k < M; ++k) a[k] = fma(c, x[k], a[k]);
+  }
+}
+
 // mu(T) / mu by Sutherland's law (Eq. sutherland): c1 th^1.5 / (th + s) with
 // th = (p / rho) / rt_ref, c1 = 1 + s, irt = 1 / rt_ref
 template <typename real>

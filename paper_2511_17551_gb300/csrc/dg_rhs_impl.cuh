@@ -519,11 +519,8 @@ rhs_kernel(const DgArgs a, const KConst kc) {
                                     q[nl], vl, q[(1 + DIM) * NP + nl], q[(2 + DIM) * NP + nl], ul,
                                     nrm, kc.inv_gm1, kc.pref, F);
         const real cil = wdg * B.D2[i * N1 + l], cli = wdg * B.D2[l * N1 + i];
-#pragma unroll
-        for (int k = 0; k < NV; ++k) {
-          acc[i][k] += cil * F[k];
-          acc[l][k] += cli * F[k];
-        }
+        axpy<NV>(acc[i], cil, F);
+        axpy<NV>(acc[l], cli, F);
       }
     }
 
@@ -580,15 +577,21 @@ rhs_kernel(const DgArgs a, const KConst kc) {
       // viscous volume term along the line: D Fv (enters the RHS with + sign), with the
       // contravariant flux of this direction read from shared memory
       const real* fvd = sfv + e * L::SFV + d * (DIM + 1) * NP;
+      real fl[N1][DIM + 1];
 #pragma unroll
-      for (int i = 0; i < N1; ++i)
+      for (int l = 0; l < N1; ++l)
 #pragma unroll
-        for (int c = 0; c <= DIM; ++c) {
-          real dsum = 0;
+        for (int c = 0; c <= DIM; ++c) fl[l][c] = fvd[c * NP + SW(base + l * s)];
 #pragma unroll
-          for (int l = 0; l < N1; ++l) dsum += B.D[i * N1 + l] * fvd[c * NP + SW(base + l * s)];
-          acc[i][NSP + c] -= dsum;
-        }
+      for (int i = 0; i < N1; ++i) {
+        real dsum[DIM + 1];
+#pragma unroll
+        for (int c = 0; c <= DIM; ++c) dsum[c] = 0;
+#pragma unroll
+        for (int l = 0; l < N1; ++l) axpy<DIM + 1>(dsum, B.D[i * N1 + l], fl[l]);
+#pragma unroll
+        for (int c = 0; c <= DIM; ++c) acc[i][NSP + c] -= dsum[c];
+      }
     }
 
     real* sa = sacc + e * L::SACC + d * NV * NP;
