@@ -92,6 +92,28 @@ __device__ __forceinline__ real inv_ln_mean(real x, real y) {
   return RealOps<real>::div(RealOps<real>::log_(RealOps<real>::div(y, x)), d);
 }
 
+// Single precision: L(xr, yr) and 1 / L(xb, yb) together, the two near-equal series in
+// the lanes of the packed FP32 operations of sm_100 (same roundings as ln_mean and
+// inv_ln_mean); the closed forms one at a time when either pair is not near-equal.
+__device__ __forceinline__ void ln_mean_pair(float xr, float yr, float xb, float yb, float& Lr, float& iLb) {
+  const float2 x = make_float2(xr, xb), y = make_float2(yr, yb);
+  const float2 s = __fadd2_rn(x, y);
+  const float2 d = __ffma2_rn(x, make_float2(-1.f, -1.f), y);  // y - x
+  const float2 rs = make_float2(RealOps<float>::rcp(s.x), RealOps<float>::rcp(s.y));
+  const float2 f = __fmul2_rn(d, rs);
+  const float2 f2 = __fmul2_rn(f, f);
+  if (f2.x < RealOps<float>::ln_eps && f2.y < RealOps<float>::ln_eps) {
+    float2 poly = __ffma2_rn(f2, make_float2(2.f / 7.f, 2.f / 7.f), make_float2(2.f / 5.f, 2.f / 5.f));
+    poly = __ffma2_rn(f2, poly, make_float2(2.f / 3.f, 2.f / 3.f));
+    poly = __ffma2_rn(f2, poly, make_float2(2.f, 2.f));
+    Lr = s.x * RealOps<float>::rcp(poly.x);
+    iLb = poly.y * rs.y;
+    return;
+  }
+  Lr = ln_mean(xr, yr);
+  iLb = inv_ln_mean(xb, yb);
+}
+
 __device__ __forceinline__ void latch_status(unsigned long long* st, unsigned long long code,
                                              int64_t elem) {
   unsigned long long v = (code << 56) | (unsigned long long)(elem & 0x00ffffffffffffffll);
@@ -187,14 +209,27 @@ __device__ __forceinline__ void volume_flux(int vf, real rL, const real* vL, rea
                                             real inv_gm1, real pref, real* f) {
   constexpr int NV = NSP + DIM + 1;
   real vnL = 0, vnR = 0;
+  if constexpr (sizeof(real) == 4) {
+    float2 vn = make_float2(0.f, 0.f);
 #pragma unroll
-  for (int d = 0; d < DIM; ++d) {
-    vnL += vL[d] * n[d];
-    vnR += vR[d] * n[d];
+    for (int d = 0; d < DIM; ++d) vn = __ffma2_rn(make_float2(vL[d], vR[d]), make_float2(n[d], n[d]), vn);
+    vnL = vn.x;
+    vnR = vn.y;
+  } else {
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+      vnL += vL[d] * n[d];
+      vnR += vR[d] * n[d];
+    }
   }
   if (NSP == 1 && vf == DG_VF_RANOCHA) {
-    real rho_m = ln_mean(rL, rR);
-    real ib = inv_ln_mean(bL, bR);  // 1 / L(rho/p)
+    real rho_m, ib;  // L(rho), 1 / L(rho/p)
+    if constexpr (sizeof(real) == 4) {
+      ln_mean_pair(rL, rR, bL, bR, rho_m, ib);
+    } else {
+      rho_m = ln_mean(rL, rR);
+      ib = inv_ln_mean(bL, bR);
+    }
     real vv = 0;
 #pragma unroll
     for (int d = 0; d < DIM; ++d) vv += vL[d] * vR[d];
