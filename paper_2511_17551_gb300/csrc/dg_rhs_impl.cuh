@@ -490,6 +490,10 @@ rhs_kernel(const DgArgs a, const KConst kc) {
       for (int k = 0; k < NV; ++k) acc[i][k] = 0;
     const real al = s_alpha[e];
     const real wdg = real(1) - al;
+    // every two-point flux is linear in the normal: F(n_i + n_l) = 2 F((n_i + n_l) / 2)
+    // exactly (a power-of-two scale), so the pair's mean normal is left unhalved and the
+    // half goes into the coefficient
+    const real hwdg = real(0.5) * wdg;
 
     // flux differencing: every symmetric pair once (split form, zero diagonal)
 #pragma unroll
@@ -509,7 +513,7 @@ rhs_kernel(const DgArgs a, const KConst kc) {
 #pragma unroll
         for (int c = 0; c < DIM; ++c) {
           vl[c] = q[(1 + c) * NP + nl];
-          nrm[c] = real(0.5) * (ja[c * NP + ni] + ja[c * NP + nl]);
+          nrm[c] = ja[c * NP + ni] + ja[c * NP + nl];
         }
         if (NSP > 1 || vf != DG_VF_RANOCHA) {
 #pragma unroll
@@ -518,7 +522,7 @@ rhs_kernel(const DgArgs a, const KConst kc) {
         volume_flux<real, DIM, NSP>(vf, q[ni], vi, q[(1 + DIM) * NP + ni], q[(2 + DIM) * NP + ni], ui,
                                     q[nl], vl, q[(1 + DIM) * NP + nl], q[(2 + DIM) * NP + nl], ul,
                                     nrm, kc.inv_gm1, kc.pref, F);
-        const real cil = wdg * B.D2[i * N1 + l], cli = wdg * B.D2[l * N1 + i];
+        const real cil = hwdg * B.D2[i * N1 + l], cli = hwdg * B.D2[l * N1 + i];
         axpy<NV>(acc[i], cil, F);
         axpy<NV>(acc[l], cli, F);
       }
