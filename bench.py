@@ -43,7 +43,7 @@ WORDS_MAIN_EULER = 5 + 9 + 1 + 5 + 5 + 5 + 10
 WORDS_GRAD = 5 + 9 + 1 + 12
 # dram__bytes_read.sum + dram__bytes_write.sum of the current mixed-form NS N=3 rhs_kernel
 # per node, from one ncu capture of the 24^3 case (traffic scales with the node count)
-RHS_DRAM_B_PER_NODE = 157.4
+RHS_DRAM_B_PER_NODE = 157.6
 # FP64 flops per node of the FP64-form NS N=3 rhs_kernel (2 DFMA + DMUL + DADD thread
 # instructions, one ncu capture of the 16^3 case): its roofline is the FP64 pipe
 RHS_FP64_FLOPS_PER_NODE = 1005.3
@@ -526,6 +526,51 @@ def run_other_shapes(args, stream_ptr, world):
         blk[name] = {"value": world * dof * 5 * n / wall, "ms_per_step": wall * 1e3 / n, "steps": n,
                      "device_ms_per_step_by_kernel": per}
     out["tgv_ns_16^3_N7"] = blk
+    # the runtime-choice two-point volume fluxes and interface fluxes on the bench workload
+    # (TGV Navier-Stokes 32^3, N = 3, mixed form); ranocha_llf is the compile-time production
+    # pair of the headline number, the others run the runtime-choice kernel
+    cfg = CONFIGS["tgv_ns_32^3_N3"]
+    xi, _ = dg.dg_lgl_nodes(cfg["N"])
+    xyz, nbr, face, w0 = build_workload(cfg, xi)
+    dof = xyz.shape[0] * (cfg["N"] + 1) ** 3 * 5
+    blk = {"workload": "tgv_ns_32^3_N3", "dof": dof, "form": "mixed", "steps": 20}
+    for name, vf, sf in (("ranocha_llf", dg.DG_VF_RANOCHA, dg.DG_SF_LLF),
+                         ("kennedy_gruber_hll", dg.DG_VF_KG, dg.DG_SF_HLL),
+                         ("pirozzoli_hllc", dg.DG_VF_PIROZZOLI, dg.DG_SF_HLLC),
+                         ("morinishi_llf", dg.DG_VF_MORINISHI, dg.DG_SF_LLF),
+                         ("ducros_ec", dg.DG_VF_DUCROS, dg.DG_SF_EC),
+                         ("standard_dg_hll", dg.DG_VF_CENTRAL, dg.DG_SF_HLL)):
+        s = dg.Solver(3, cfg["N"], xyz, nbr, face, equations=dg.DG_NAVIER_STOKES, mu=cfg["mu"],
+                      Pr=0.72, precision=dg.DG_MIXED, stream=stream_ptr, p_ref=1.0 / (1.4 * 0.01),
+                      volume_flux=vf, surface_flux=sf)
+        s.set_primitive(w0)
+        wall, per = timed(s, 20, 0.5)
+        s.close()
+        blk[name] = {"value": world * dof * 5 * 20 / wall, "ms_per_step": wall * 1e3 / 20,
+                     "device_ms_per_step_by_kernel": per}
+    out["split_forms_tgv_ns_32^3_N3"] = blk
+    # wall-bounded channel, 64 x 16 x 32 elements, N = 3: periodic in x and z, a no-slip
+    # adiabatic wall at y = 0 and an isothermal wall at y = 1 (BR1 boundary values, boundary
+    # viscous fluxes and the boundary lifting kernel), Mach-0.1 shear flow, Re 1600
+    xi, _ = dg.dg_lgl_nodes(3)
+    xyz, nbr, face = W.box_mesh((64, 16, 32), xi, (0.0, 0.0, 0.0), (4.0, 1.0, 2.0),
+                                periodic=(True, False, True), bc_ids=[9, 9, 0, 1, 9, 9])
+    p0 = 1.0 / (1.4 * 0.01)
+    w0 = W.channel_primitive(xyz, p0)
+    dof = xyz.shape[0] * 64 * 5
+    blk = {"workload": "channel_walls_64x16x32_N3", "dof": dof, "walls": "no-slip adiabatic / isothermal",
+           "Re": 1600}
+    for name, prec, n in (("mixed", dg.DG_MIXED, 20), ("fp64", dg.DG_FP64, 3)):
+        s = dg.Solver(3, 3, xyz, nbr, face, equations=dg.DG_NAVIER_STOKES, mu=1.0 / 1600.0,
+                      Pr=0.72, precision=prec, stream=stream_ptr, p_ref=p0,
+                      bc_kind=[dg.DG_BC_NOSLIP_ADIABATIC, dg.DG_BC_ISOTHERMAL],
+                      bc_prim=np.array([[1.0, 0.0, 0.0, 0.0, p0]] * 2))
+        s.set_primitive(w0)
+        wall, per = timed(s, n, 0.5)
+        s.close()
+        blk[name] = {"value": world * dof * 5 * n / wall, "ms_per_step": wall * 1e3 / n, "steps": n,
+                     "device_ms_per_step_by_kernel": per}
+    out["channel_walls_64x16x32_N3"] = blk
     # supersonic TGV 32^3, N = 7: Sutherland's law, pressure-indicator blending, positivity
     n_el, N = 32, 7
     xi, _ = dg.dg_lgl_nodes(N)

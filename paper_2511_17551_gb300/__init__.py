@@ -26,7 +26,7 @@ DG_VF_RANOCHA, DG_VF_DUCROS, DG_VF_CENTRAL, DG_VF_KG, DG_VF_PIROZZOLI, DG_VF_MOR
 DG_SF_LLF, DG_SF_HLLC, DG_SF_EC, DG_SF_HLL = 0, 1, 2, 3
 DG_FP64, DG_MIXED = 0, 1
 DG_THERMO_NEWTON, DG_THERMO_MLP = 0, 1
-DG_BC_INFLOW, DG_BC_OUTFLOW, DG_BC_SLIP_WALL = 1, 2, 3
+DG_BC_INFLOW, DG_BC_OUTFLOW, DG_BC_SLIP_WALL, DG_BC_NOSLIP_ADIABATIC, DG_BC_ISOTHERMAL = 1, 2, 3, 4, 5
 
 # every symbol declared in include/dg.h
 EXPORTED = [

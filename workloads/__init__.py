@@ -99,6 +99,20 @@ def supersonic_tgv_primitive(xyz, gamma=1.4, mach=1.25):
     return w
 
 
+def channel_primitive(xyz, p0):
+    """Wall-bounded channel 0 <= y <= 1 (walls at y = 0 and 1): a parabolic streamwise
+    profile 4y(1-y) with peak 1, zero at both walls, a small wall-normal and spanwise
+    perturbation, rho = 1, uniform pressure p0."""
+    x, y, z = xyz[:, 0], xyz[:, 1], xyz[:, 2]
+    w = np.empty((xyz.shape[0], 5, xyz.shape[2]))
+    w[:, 0] = 1.0 + 0.01 * np.sin(0.5 * np.pi * x)
+    w[:, 1] = 4.0 * y * (1.0 - y)
+    w[:, 2] = 0.01 * np.sin(0.5 * np.pi * x) * np.sin(np.pi * y)
+    w[:, 3] = 0.01 * np.cos(np.pi * z) * np.sin(np.pi * y)
+    w[:, 4] = p0
+    return w
+
+
 def supersonic_tgv_physics(gamma=1.4, mach=1.25, reynolds=1600.0):
     """Physics keywords of the supersonic TGV in the same units: mu_o = rho_o L U_o / Re at
     T_o, Sutherland's law with s = S / T_o and the reference p/rho = p_o / rho_o."""
