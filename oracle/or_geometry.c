@@ -12,6 +12,11 @@
  *     with every derivative taken by the LGL derivative matrix,
  *   - 2D: Ja^1 = ( y_eta, -x_eta ),  Ja^2 = ( -y_xi, x_xi ),
  *   - J = det(dx/dxi) from the same derivatives.
+ *   - the undifferentiated factor x_l is taken relative to the element's first
+ *     node: a constant shift c changes the curl form by c curl_xi grad_xi x_m,
+ *     which vanishes (the tensor-product derivative matrices of different
+ *     directions commute), and without it the products x_l grad x_m of size
+ *     |x| h cancel to Ja of size h^2, which amplifies rounding by |x| / h.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -63,10 +68,12 @@ int or_geometry(int dim, int N, int64_t K, const double* xyz, double* Ja, double
     if (dim == 3) {
       for (int n = 0; n < 3; ++n) {
         int m = (n + 1) % 3, l = (n + 2) % 3;
-        /* V_j = x_l * d x_m / d xi_j  (nodal interpolant of the product) */
+        /* V_j = (x_l - x_l(first node)) * d x_m / d xi_j  (nodal interpolant of
+           the product) */
+        const double c = X[l * np];
         for (int node = 0; node < np; ++node)
           for (int j = 0; j < 3; ++j)
-            V[j * np + node] = X[l * np + node] * dref(3, N, D, X + m * np, j, node);
+            V[j * np + node] = (X[l * np + node] - c) * dref(3, N, D, X + m * np, j, node);
         for (int node = 0; node < np; ++node) {
           double c0 = dref(3, N, D, V + 2 * np, 1, node) - dref(3, N, D, V + 1 * np, 2, node);
           double c1 = dref(3, N, D, V + 0 * np, 2, node) - dref(3, N, D, V + 2 * np, 0, node);

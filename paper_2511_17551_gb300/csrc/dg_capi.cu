@@ -137,11 +137,16 @@ __global__ void metrics_kernel(int dim, int N, int64_t K, const double* xyz, dou
     if (!(det > 0.0)) atomicCAS(status, 0ull, (4ull << 56) | (unsigned long long)k);
   }
   if (dim == 3) {
+    // curl form Ja^i_n = -[curl_xi(x_l grad_xi x_m)]_i with x_l taken relative to the
+    // element's first node: the shift adds c curl grad x_m = 0 (the derivative matrices of
+    // different directions commute) and keeps the products of size h^2 instead of |x| h,
+    // so that rounding is not amplified by |x| / h in the cancellation
     for (int n = 0; n < 3; ++n) {
       const int m = (n + 1) % 3, l = (n + 2) % 3;
       __syncthreads();
+      const double c = X[l * np];
       for (int node = threadIdx.x; node < np; node += blockDim.x)
-        for (int j = 0; j < 3; ++j) V[j * np + node] = X[l * np + node] * dref(X + m * np, N, j, node);
+        for (int j = 0; j < 3; ++j) V[j * np + node] = (X[l * np + node] - c) * dref(X + m * np, N, j, node);
       __syncthreads();
       for (int node = threadIdx.x; node < np; node += blockDim.x) {
         double c0 = dref(V + 2 * np, N, 1, node) - dref(V + 1 * np, N, 2, node);
