@@ -187,6 +187,77 @@ __global__ void merge_kernel(const float* hi, const float* lo, double* b, int64_
        i += (int64_t)gridDim.x * blockDim.x)
     b[i] = (double)hi[i] + (double)lo[i];
 }
+// The same two conversions for 16-byte aligned buffers, built for the host link (a
+// page-locked host buffer read or written in place): pairs of values as 16-byte accesses,
+// four independent ones in flight per thread, so that the link's latency is covered by
+// bytes in flight rather than by resident threads.  n2 = n / 2 pairs; an odd last value
+// goes through the scalar kernels.
+__global__ void split_kernel_x4(const double2* a, float2* hi, float2* lo, int64_t n2) {
+  const int64_t st = (int64_t)gridDim.x * blockDim.x;
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  for (; i + 3 * st < n2; i += 4 * st) {
+    double2 v[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) v[j] = a[i + j * st];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const float hx = (float)v[j].x, hy = (float)v[j].y;
+      hi[i + j * st] = make_float2(hx, hy);
+      lo[i + j * st] = make_float2((float)(v[j].x - (double)hx), (float)(v[j].y - (double)hy));
+    }
+  }
+  for (; i < n2; i += st) {
+    const double2 v = a[i];
+    const float hx = (float)v.x, hy = (float)v.y;
+    hi[i] = make_float2(hx, hy);
+    lo[i] = make_float2((float)(v.x - (double)hx), (float)(v.y - (double)hy));
+  }
+}
+__global__ void merge_kernel_x4(const float2* hi, const float2* lo, double2* b, int64_t n2) {
+  const int64_t st = (int64_t)gridDim.x * blockDim.x;
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  for (; i + 3 * st < n2; i += 4 * st) {
+    float2 h[4], l[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      h[j] = hi[i + j * st];
+      l[j] = lo[i + j * st];
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      b[i + j * st] = make_double2((double)h[j].x + (double)l[j].x, (double)h[j].y + (double)l[j].y);
+  }
+  for (; i < n2; i += st) {
+    const float2 hh = hi[i], ll = lo[i];
+    b[i] = make_double2((double)hh.x + (double)ll.x, (double)hh.y + (double)ll.y);
+  }
+}
+// split / merge of n values: the 16-byte kernels where every pointer allows, the odd last
+// value (and unaligned buffers) by the scalar ones
+unsigned grid_for(int64_t n, int bs);
+bool host_aligned16(const void* p) { return ((uintptr_t)p & 15) == 0; }
+void launch_split(const double* src, float* hi, float* lo, int64_t n, cudaStream_t st) {
+  if (host_aligned16(src) && host_aligned16(hi) && host_aligned16(lo)) {
+    const int64_t n2 = n / 2;
+    if (n2 > 0)
+      split_kernel_x4<<<grid_for((n2 + 3) / 4, 256), 256, 0, st>>>((const double2*)src, (float2*)hi,
+                                                                    (float2*)lo, n2);
+    if (n & 1) split_kernel<<<1, 32, 0, st>>>(src + 2 * n2, hi + 2 * n2, lo + 2 * n2, 1);
+  } else {
+    split_kernel<<<grid_for(n, 256), 256, 0, st>>>(src, hi, lo, n);
+  }
+}
+void launch_merge(const float* hi, const float* lo, double* dst, int64_t n, cudaStream_t st) {
+  if (host_aligned16(dst) && host_aligned16(hi) && host_aligned16(lo)) {
+    const int64_t n2 = n / 2;
+    if (n2 > 0)
+      merge_kernel_x4<<<grid_for((n2 + 3) / 4, 256), 256, 0, st>>>((const float2*)hi, (const float2*)lo,
+                                                                    (double2*)dst, n2);
+    if (n & 1) merge_kernel<<<1, 32, 0, st>>>(hi + 2 * n2, lo + 2 * n2, dst + 2 * n2, 1);
+  } else {
+    merge_kernel<<<grid_for(n, 256), 256, 0, st>>>(hi, lo, dst, n);
+  }
+}
 
 // one-gas primitive (rho, v, p) -> conserved, written in the form precision
 // (lo: the FP32 form's compensation part, or null)
@@ -798,7 +869,7 @@ dg_status dg_set_state(dg_ctx* c, const double* u, int on_device, double t) {
     src = c->stage64;
   }
   if (c->precision == DG_MIXED) {
-    split_kernel<<<grid_for(n, 256), 256, 0, c->stream>>>(src, (float*)c->u[c->cur], c->ulo, n);
+    launch_split(src, (float*)c->u[c->cur], c->ulo, n, c->stream);
   } else {
     CK(cudaMemcpyAsync(c->u[c->cur], src, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream));
   }
@@ -845,7 +916,7 @@ dg_status dg_get_state(dg_ctx* c, double* u, int on_device, double* t) {
   if (c->precision == DG_MIXED) {
     double* hp = on_device ? nullptr : (double*)pinned_device_ptr(u);
     double* dst = on_device ? u : (hp ? hp : c->stage64);
-    merge_kernel<<<grid_for(n, 256), 256, 0, c->stream>>>((const float*)c->u[c->cur], c->ulo, dst, n);
+    launch_merge((const float*)c->u[c->cur], c->ulo, dst, n, c->stream);
     CK(cudaGetLastError());
     if (!on_device && !hp)
       CK(cudaMemcpyAsync(u, c->stage64, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream));

@@ -143,3 +143,42 @@ def test_unaligned_input_takes_the_per_thread_staging(dg, precision):
         assert torch.equal(r_a, r_b)
     finally:
         s.close()
+
+
+@pytest.mark.parametrize("where", ["pinned", "device"])
+def test_state_conversion_odd_length_and_unaligned(dg, where):
+    """The mixed form's state conversions (FP64 <-> FP32 pair) use 16-byte accesses for
+    aligned buffers and the scalar path for the odd last value and for unaligned buffers:
+    an odd-length state (3^3 elements at N = 2, 3645 values) gives the same bits through a
+    16-byte aligned buffer and one 8 bytes off, and set / get returns the input to the
+    pair's precision (|u - (hi + lo)| <= 2^-48 |u|)."""
+    import torch
+    p = cases.Pair(lambda x: cases.tgv(x, None, warp=0.1, shape=(3, 3, 3)), 3, 2,
+                   precision=dg.DG_MIXED)
+    try:
+        u = p.orc.prim_to_cons(cases.perturbed_state(p.mesh_o[3], 5, amp=0.05))
+        n = u.size
+        assert n % 2 == 1
+        dev = "cuda" if where == "device" else "cpu"
+
+        def buf(off):
+            b = torch.zeros(n + 2, dtype=torch.float64, device=dev)
+            if where == "pinned":
+                b = b.pin_memory()
+            v = b[off:off + n].view(u.shape)
+            assert v.data_ptr() % 16 == 8 * off
+            return v
+
+        outs = []
+        for off in (0, 1):
+            src = buf(off)
+            src.copy_(torch.from_numpy(u))
+            dg.dg_set_state(p.gpu.ctx, src)
+            dst = buf(off)
+            dg.dg_get_state(p.gpu.ctx, dst)
+            torch.cuda.synchronize()
+            outs.append(dst.cpu().numpy().copy())
+        assert np.array_equal(outs[0], outs[1])
+        assert np.abs(outs[0] - u).max() <= 2.0 ** -47 * np.abs(u).max()
+    finally:
+        p.close()
