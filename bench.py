@@ -529,20 +529,24 @@ def run_other_shapes(args, stream_ptr, world):
         blk[name] = {"value": world * dof * 5 * n / wall, "ms_per_step": wall * 1e3 / n, "steps": n,
                      "device_ms_per_step_by_kernel": per}
     out["tgv_ns_16^3_N7"] = blk
-    # the runtime-choice two-point volume fluxes and interface fluxes on the bench workload
-    # (TGV Navier-Stokes 32^3, N = 3, mixed form); ranocha_llf is the compile-time production
-    # pair of the headline number, the others run the runtime-choice kernel
+    # the split-form volume fluxes and the interface fluxes on the bench workload (TGV
+    # Navier-Stokes 32^3, N = 3, mixed form): ranocha_llf is the production pair of the
+    # headline number, the other *_llf pairs run their compile-time kernels, the rest the
+    # runtime-choice kernel
     cfg = CONFIGS["tgv_ns_32^3_N3"]
     xi, _ = dg.dg_lgl_nodes(cfg["N"])
     xyz, nbr, face, w0 = build_workload(cfg, xi)
     dof = xyz.shape[0] * (cfg["N"] + 1) ** 3 * 5
     blk = {"workload": "tgv_ns_32^3_N3", "dof": dof, "form": "mixed", "steps": 20}
     for name, vf, sf in (("ranocha_llf", dg.DG_VF_RANOCHA, dg.DG_SF_LLF),
+                         ("kennedy_gruber_llf", dg.DG_VF_KG, dg.DG_SF_LLF),
+                         ("pirozzoli_llf", dg.DG_VF_PIROZZOLI, dg.DG_SF_LLF),
+                         ("morinishi_llf", dg.DG_VF_MORINISHI, dg.DG_SF_LLF),
+                         ("ducros_llf", dg.DG_VF_DUCROS, dg.DG_SF_LLF),
+                         ("standard_dg_llf", dg.DG_VF_CENTRAL, dg.DG_SF_LLF),
                          ("kennedy_gruber_hll", dg.DG_VF_KG, dg.DG_SF_HLL),
                          ("pirozzoli_hllc", dg.DG_VF_PIROZZOLI, dg.DG_SF_HLLC),
-                         ("morinishi_llf", dg.DG_VF_MORINISHI, dg.DG_SF_LLF),
-                         ("ducros_ec", dg.DG_VF_DUCROS, dg.DG_SF_EC),
-                         ("standard_dg_hll", dg.DG_VF_CENTRAL, dg.DG_SF_HLL)):
+                         ("ducros_ec", dg.DG_VF_DUCROS, dg.DG_SF_EC)):
         s = dg.Solver(3, cfg["N"], xyz, nbr, face, equations=dg.DG_NAVIER_STOKES, mu=cfg["mu"],
                       Pr=0.72, precision=dg.DG_MIXED, stream=stream_ptr, p_ref=1.0 / (1.4 * 0.01),
                       volume_flux=vf, surface_flux=sf)

@@ -69,6 +69,8 @@ int dg_host_basis(int N, DgHostBasis* b);
 // for non-production flux pairs; their basis tables are uploaded with the production ones)
 cudaError_t dg_f64g_upload_basis();
 cudaError_t dg_f32g_upload_basis();
+cudaError_t dg_f32s_upload_basis();
+cudaError_t dg_f32s_rhs(const DgArgs& a, cudaStream_t s);
 cudaError_t dg_f64g_rhs(const DgArgs& a, cudaStream_t s);
 cudaError_t dg_f32g_rhs(const DgArgs& a, cudaStream_t s);
 // Zhang-Shu positivity limiter on a state of the context's precision (one gas)

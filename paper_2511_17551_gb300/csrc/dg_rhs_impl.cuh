@@ -2,14 +2,16 @@
 // defines DG_REAL (double or float) and DG_PREFIX (namespace and function-name
 // prefix, e.g. dg_f32), so profiles name kernels dg_f32::rhs_kernel<...>.
 //
-// The right-hand-side kernel comes in two flavours: FL = 1 fixes the production flux
+// The right-hand-side kernel comes in three flavours: FL = 1 fixes the production flux
 // pair at compile time (Ranocha volume flux for one gas, Ducros for mixtures; LLF at
-// interfaces and subcells, constant viscosity), FL = 0 switches on the runtime choice
-// (every other pair, and Sutherland's law).
+// interfaces and subcells, constant viscosity), FL = 2 + vf fixes another one-gas volume
+// flux vf with LLF and constant viscosity (the split forms, emitted for 3D at N = 3), and
+// FL = 0 switches on the runtime choice (every other pair, and Sutherland's law).
 // A translation unit that defines DG_GENERIC_ONLY emits only the FL = 0 kernels (and
-// its own basis table); the other one emits everything else and forwards non-production
-// pairs to DG_GENERIC_RHS.  The split keeps register pressure of the production kernel
-// free of the unused branches and lets the two halves compile in parallel.
+// its own basis table); one that also defines DG_SPLIT_ONLY emits only the FL = 2 + vf
+// kernels; the main one emits everything else and forwards the other pairs to
+// DG_SPLIT_RHS (where defined) or DG_GENERIC_RHS.  The split keeps register pressure of the
+// compile-time kernels free of the unused branches and lets the parts compile in parallel.
 #pragma once
 #include <stdint.h>
 #include "dg_kernels.cuh"
@@ -271,10 +273,13 @@ __device__ __forceinline__ int outer_state(const DgArgs& a, const KConst& kc, in
 // ------------------------------------------------------------------ main RHS / RK kernel
 template <int DIM, int N, int NSP, bool NS, int FL>
 // the runtime-choice kernel (FL = 0) carries more live branches: at most 5 CTAs per SM
-// (up to 136 registers a thread at 96 threads) instead of 8, so that it does not spill
+// (up to 136 registers a thread at 96 threads) instead of 8, so that it does not spill;
+// the split forms (FL >= 2) hold both nodes' conserved states per flux pair: at most 6
+// (96 registers; at 7 the allocator is held to 80 and spills)
 __global__ void __launch_bounds__(Layout<DIM, N, NSP, NS>::THREADS,
-                                  FL ? Layout<DIM, N, NSP, NS>::MINB
-                                     : (Layout<DIM, N, NSP, NS>::MINB > 5 ? 5 : Layout<DIM, N, NSP, NS>::MINB))
+                                  (Layout<DIM, N, NSP, NS>::MINB > (FL == 1 ? 8 : FL ? 6 : 5))
+                                      ? (FL == 1 ? 8 : FL ? 6 : 5)
+                                      : Layout<DIM, N, NSP, NS>::MINB)
 rhs_kernel(const DgArgs a, const KConst kc) {
   using S = Shape<DIM, N>;
   using L = Layout<DIM, N, NSP, NS>;
@@ -298,7 +303,7 @@ rhs_kernel(const DgArgs a, const KConst kc) {
   const int ne = (int)((a.K - e0) < EPB ? (a.K - e0) : EPB);
   const BasisTab<real>& B = c_tab[N];
   const bool read_du = a.mode == 1 && a.stage != 0;
-  const int vf = FL ? (NSP == 1 ? DG_VF_RANOCHA : DG_VF_DUCROS) : a.vf;
+  const int vf = FL == 0 ? a.vf : FL == 1 ? (NSP == 1 ? DG_VF_RANOCHA : DG_VF_DUCROS) : FL - 2;
   const int sf = FL ? DG_SF_LLF : a.sf;
   auto SW = [](int n) { return Swizzle<DIM, N>::at(n); };
 
@@ -1654,10 +1659,10 @@ cudaError_t set_smem(KernelT k, size_t bytes) {
   return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
-template <int DIM, int N, int NSP, bool NS>
+template <int DIM, int N, int NSP, bool NS, int FL = DG_FL>
 cudaError_t launch_rhs_t(const DgArgs& a, cudaStream_t st) {
   using L = Layout<DIM, N, NSP, NS>;
-  auto k = rhs_kernel<DIM, N, NSP, NS, DG_FL>;
+  auto k = rhs_kernel<DIM, N, NSP, NS, FL>;
   cudaError_t err = set_smem(k, L::SMEM);
   if (err != cudaSuccess) return err;
   const int64_t grid = (a.K + L::EPB - 1) / L::EPB;
@@ -1727,10 +1732,33 @@ cudaError_t launch_ind_t(const DgArgs& a, double amax, void* out, cudaStream_t s
 #define DG_IND_CALL(DIM, N, NSP, X) DG_PREFIX::launch_ind_t<DIM, N, NSP>(a, amax, out, st)
 #define DG_POS_CALL(DIM, N, NSP, X) DG_PREFIX::launch_pos_t<DIM, N, NSP>(a, u, ulo, eps, nlim, st)
 
+#ifdef DG_SPLIT_ONLY
+// the compile-time split forms: one-gas 3D at N = 3, LLF, constant viscosity
+#define DG_SPLIT_CALL(VF)                                                                        \
+  return a.ns ? DG_PREFIX::launch_rhs_t<3, 3, 1, true, 2 + (VF)>(a, st)                          \
+              : DG_PREFIX::launch_rhs_t<3, 3, 1, false, 2 + (VF)>(a, st)
+cudaError_t DG_CAT(DG_PREFIX, _rhs)(const DgArgs& a, cudaStream_t st) {
+  if (!(a.dim == 3 && a.nsp == 1 && a.N == 3 && a.sf == DG_SF_LLF && !(a.suth_s > 0.0)))
+    return cudaErrorInvalidValue;
+  switch (a.vf) {
+    case DG_VF_DUCROS: DG_SPLIT_CALL(DG_VF_DUCROS);
+    case DG_VF_CENTRAL: DG_SPLIT_CALL(DG_VF_CENTRAL);
+    case DG_VF_KG: DG_SPLIT_CALL(DG_VF_KG);
+    case DG_VF_PIROZZOLI: DG_SPLIT_CALL(DG_VF_PIROZZOLI);
+    case DG_VF_MORINISHI: DG_SPLIT_CALL(DG_VF_MORINISHI);
+    default: return cudaErrorInvalidValue;
+  }
+}
+#else
 cudaError_t DG_CAT(DG_PREFIX, _rhs)(const DgArgs& a, cudaStream_t st) {
 #ifndef DG_GENERIC_ONLY
   const bool production = a.sf == DG_SF_LLF && a.vf == (a.nsp == 1 ? DG_VF_RANOCHA : DG_VF_DUCROS) &&
                           !(a.suth_s > 0.0);
+#ifdef DG_SPLIT_RHS
+  const bool split = a.dim == 3 && a.nsp == 1 && a.N == 3 && a.sf == DG_SF_LLF && !(a.suth_s > 0.0) &&
+                     a.vf != DG_VF_RANOCHA;
+  if (split) return DG_SPLIT_RHS(a, st);
+#endif
   if (!production) return DG_GENERIC_RHS(a, st);
 #endif
   if (a.dim == 3 && a.nsp == 1 && a.ns) { DG_DISPATCH_N(DG_RHS_CALL, 3, 1, true) }
@@ -1739,6 +1767,7 @@ cudaError_t DG_CAT(DG_PREFIX, _rhs)(const DgArgs& a, cudaStream_t st) {
   if (a.dim == 3 && a.nsp == 5) { DG_DISPATCH_N_MIX(DG_RHS_CALL, 3, 5, false) }
   return cudaErrorInvalidValue;
 }
+#endif  // DG_SPLIT_ONLY
 
 #ifndef DG_GENERIC_ONLY
 cudaError_t DG_CAT(DG_PREFIX, _gradients)(const DgArgs& a, cudaStream_t st) {
@@ -1803,6 +1832,9 @@ cudaError_t DG_CAT(DG_PREFIX, _upload_basis)() {
   cudaError_t err = cudaMemcpyToSymbol(DG_PREFIX::c_tab, tab, sizeof(tab));
 #ifndef DG_GENERIC_ONLY
   if (err == cudaSuccess) err = DG_GENERIC_UPLOAD();
+#ifdef DG_SPLIT_UPLOAD
+  if (err == cudaSuccess) err = DG_SPLIT_UPLOAD();
+#endif
 #endif
   return err;
 }

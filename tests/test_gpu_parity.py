@@ -81,6 +81,21 @@ RHS_CASES = {
     "tgv_ns_warped_N7": dict(builder=_tgv_builder(shape=(2, 2, 3)), dim=3, N=7,
                              kw=dict(equations=1, mu=0.01, Pr=0.72)),
     "vortex_2d_N3": dict(builder=lambda x: cases.vortex(x, 5), dim=2, N=3, kw={}),
+    # the split forms with LLF at N = 3 in 3D: compile-time kernels in the mixed form
+    "tgv_ns_warped_N3_kg_pref": dict(builder=_tgv_builder(shape=(3, 3, 5)), dim=3, N=3,
+                                     kw=dict(equations=1, mu=0.01, Pr=0.72, volume_flux=3,
+                                             p_ref=cases.tgv_p0())),
+    "tgv_ns_warped_N3_pirozzoli_llf": dict(builder=_tgv_builder(shape=(3, 3, 5)), dim=3, N=3,
+                                           kw=dict(equations=1, mu=0.01, Pr=0.72, volume_flux=4)),
+    "tgv_ns_warped_N3_morinishi_llf_pref": dict(builder=_tgv_builder(shape=(3, 3, 5)), dim=3, N=3,
+                                                kw=dict(equations=1, mu=0.01, Pr=0.72, volume_flux=5,
+                                                        p_ref=cases.tgv_p0())),
+    "tgv_ns_warped_N3_ducros_llf": dict(builder=_tgv_builder(shape=(3, 3, 5)), dim=3, N=3,
+                                        kw=dict(equations=1, mu=0.01, Pr=0.72, volume_flux=1)),
+    "tgv_ns_warped_N3_central_llf": dict(builder=_tgv_builder(shape=(3, 3, 5)), dim=3, N=3,
+                                         kw=dict(equations=1, mu=0.01, Pr=0.72, volume_flux=2)),
+    "tgv_warped_ragged_N3_kg_llf": dict(builder=_tgv_builder(shape=(3, 3, 5)), dim=3, N=3,
+                                        kw=dict(volume_flux=3)),
 }
 
 
@@ -194,9 +209,11 @@ def test_rk_c1_ten_steps(dg, precision, tol):
         p.close()
 
 
+@pytest.mark.parametrize("case", ["tgv_ns_warped_N3", "tgv_ns_warped_N3_kg_pref",
+                                  "tgv_ns_warped_N3_morinishi_llf_pref"])
 @pytest.mark.parametrize("precision,tol", [(0, FP64_TOL), (1, 1e-5)])
-def test_rk_ns_warped(dg, precision, tol):
-    c = RHS_CASES["tgv_ns_warped_N3"]
+def test_rk_ns_warped(dg, precision, tol, case):
+    c = RHS_CASES[case]
     p = cases.Pair(c["builder"], 3, 3, precision=precision, **c["kw"])
     try:
         u_o = p.orc.prim_to_cons(p.mesh_o[3])
