@@ -8,8 +8,8 @@ CFL 0.5 with the time step reduced on the device.  ``value`` is the mixed form
 
 Arms: ``--impl ours`` (default) runs libdg; ``--impl reference`` times the FP64 CPU
 oracle on the host cores on a bounded sample of the same workload.
-Multi-GPU: the method shards by elements, but every gpurun box has one GPU, so N > 1
-runs independent replicas (one per rank, weak scaling, no collective on the data path).
+Multi-GPU: N > 1 runs independent replicas of the workload, one per rank (weak scaling,
+no collective on the data path).
 """
 import argparse
 import json
