@@ -34,16 +34,21 @@ CONFIGS = {
     # profiling case for ncu section captures: same kernels, 245 MB working set (> L2)
     "tgv_ns_24^3_N3": dict(n_el=24, N=3, warp=0.1, mu=1.0 / 1600.0),
 }
-# algorithmic HBM words per node of one RK-stage launch (unique bytes, neighbour traces
-# excluded): main kernel reads u, Ja, 1/J, the contravariant viscous fluxes (12 words), du
-# and the compensation part u_lo of the FP32 state, writes du, u_new, u_lo; gradient kernel
+# algorithmic HBM words per node of one RK-stage launch of the method (unique bytes,
+# neighbour traces excluded): the main kernel reads u, du, the metric terms Ja and 1/J
+# and the 12 viscous words, and writes du and the new u (5 + 5 + 9 + 1 + 12 + 5 + 5 = 42
+# words = 168 B in FP32 with NS; 30 words = 120 B for Euler).  The compensated FP32 state
+# adds its low part u_lo, read and written (10 words = 40 B): an implementation choice of
+# the mixed form, reported beside the method's bytes, not in them.  The gradient kernel
 # reads u, Ja, 1/J and writes the viscous fluxes.
-WORDS_MAIN_NS = 5 + 9 + 1 + 12 + 5 + 5 + 5 + 10
-WORDS_MAIN_EULER = 5 + 9 + 1 + 5 + 5 + 5 + 10
+WORDS_MAIN_NS = 5 + 5 + 9 + 1 + 12 + 5 + 5
+WORDS_MAIN_EULER = 5 + 5 + 9 + 1 + 5 + 5
+WORDS_COMPENSATION = 10
 WORDS_GRAD = 5 + 9 + 1 + 12
-# dram__bytes_read.sum + dram__bytes_write.sum of the current mixed-form NS N=3 rhs_kernel
-# per node, from one ncu capture of the 24^3 case (traffic scales with the node count)
-RHS_DRAM_B_PER_NODE = 157.6
+# dram__bytes_read.sum + dram__bytes_write.sum per node of one launch of the current
+# mixed-form NS N=3 rhs_kernel on the full 32^3 workload (one ncu capture, one pass), or
+# None while no capture of the current kernel exists
+RHS_DRAM_B_PER_NODE = None
 # FP64 flops per node of the FP64-form NS N=3 rhs_kernel (2 DFMA + DMUL + DADD thread
 # instructions, one ncu capture of the 16^3 case): its roofline is the FP64 pipe
 RHS_FP64_FLOPS_PER_NODE = 1005.3
@@ -218,6 +223,7 @@ def run_ours(args, rank, world, local_rank):
     words = WORDS_MAIN_NS if eq == dg.DG_NAVIER_STOKES else WORDS_MAIN_EULER
     bytes_launch = words * 4 * K * npn
     achieved = bytes_launch / (rhs_ms / rhs_n * 1e-3) / 1e9
+    moved = (words + WORDS_COMPENSATION) * 4 * K * npn / (rhs_ms / rhs_n * 1e-3) / 1e9
     launches = sum(n for _, n in prof.values())
     out = {
         "metric": "DOF*RHS-evals/s (FP32+FP64-reductions form; FP64 form beside it)",
@@ -227,7 +233,7 @@ def run_ours(args, rank, world, local_rank):
         "config": {"workload": args.config, "elements": K, "N": N, "dof": dof,
                    "rk": "CK45 5-stage, CFL 0.5, device dt", "parallelism": "replicas",
                    "l2_flush": "working set %.0f MB > L2 (129 MB)" % (
-                       (words + WORDS_GRAD) * 4 * K * npn / 1e6)},
+                       (words + WORDS_COMPENSATION + WORDS_GRAD) * 4 * K * npn / 1e6)},
         "fp64_form": {"value": value64, "ms_per_step": ms64 / k64, "steps": k64,
                       "rhs_kernel_ms": rhs64_ms,
                       "roofline": None if not (eq == dg.DG_NAVIER_STOKES and N == 3) else
@@ -241,9 +247,14 @@ def run_ours(args, rank, world, local_rank):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak,
                      "traffic": (RHS_DRAM_B_PER_NODE * K * npn
-                                 if eq == dg.DG_NAVIER_STOKES and N == 3 else None),
+                                 if RHS_DRAM_B_PER_NODE and eq == dg.DG_NAVIER_STOKES and N == 3
+                                 else None),
                      "kernel": "rhs_kernel<3,%d,1,NS> f32" % N,
-                     "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)"},
+                     "algorithmic_bytes_per_node": words * 4,
+                     "ms_per_launch": rhs_ms / rhs_n,
+                     "with_compensation": {"bytes_per_node": (words + WORDS_COMPENSATION) * 4,
+                                           "achieved": moved, "frac": moved / peak},
+                     "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs, burst copy)"},
         "kernels": {k: {"ms_per_launch": v[0] / v[1], "launches": v[1]}
                     for k, v in prof.items() if v[1]},
         "gpu_launches": launches,
@@ -440,7 +451,7 @@ def run_reacting(args, stream_ptr, world):
                              hot=(1.2, 3000.0))
     fs = W.mixture_primitive(xyz[:1], rho=0.1, vel=u_inf, T=300.0, seed=7)[0, :, 0]
     K, npn = xyz.shape[0], (N + 1) ** 3
-    dof = K * npn * 10
+    dof = K * npn * 9  # 5 species densities, 3 momenta, energy
     cfl = 0.05
     out = {"workload": "reacting_5sp_17r_ogrid_%dx%dx%d_N4" % (nr, nth, nz), "elements": K,
            "dof": dof, "cfl": cfl}

@@ -279,6 +279,13 @@ dg_status dg_mlp_forward(const float* params, int n_out, const float* X, float* 
 /* Blending factors alpha [K] used by the last right-hand side (FP64, host). */
 dg_status dg_get_alpha(dg_ctx* ctx, double* alpha);
 
+/* Metric terms of the context (Methodology, curvilinear mapping: Eqs. mapp, jacobian;
+ * contravariant terms in the conservative curl form), FP64: Ja [K][dim][dim][np] with
+ * Ja[k][i][n][node] = Ja^i_n, invJ [K][np] = 1/J.  Host buffers (on_device = 0) or
+ * device buffers (1) of the caller; the copies are queued on the context stream and
+ * waited for (bounded).  These are the arrays dg_rhs_ns_noalloc takes. */
+dg_status dg_get_metrics(dg_ctx* ctx, double* Ja, double* invJ, int on_device);
+
 /* BR1 gradients of (v, p/rho) (Eq. auxstrongf), [K][dim][dim+1][np] FP64 host: of the input
  * of the last dg_rhs call, or, once dg_step_rk has run since, of the current state.
  * DG_ESTATE before any Navier-Stokes right-hand side. Synchronises. */
@@ -340,14 +347,29 @@ void dg_destroy(dg_ctx* ctx);
  * device address (cudaGetSymbolAddress) and uploads the basis tables, so make
  * that first call before any stream capture.  All calls share the one array:
  * calls whose work overlaps on the GPU (other streams, other host threads)
- * race on it; serialise them.  The status word is cleared at every call;
- * device-side errors are latched there and not returned.  Queued on `stream`
- * (cudaStream_t, NULL = legacy default); returns before the work finishes. */
+ * race on it; serialise them.  The problem must be fully periodic: every nbr
+ * entry must lie in [0, K).  The call copies nbr into the scratch first and
+ * replaces an entry outside that range by the element's own index (so that no
+ * kernel reads outside u), latching DG_EINVAL with that element; the output is
+ * then not valid.  The status word is cleared at every call; device-side errors
+ * (DG_EINVAL for a bad nbr entry, DG_ENONPHYS for rho <= 0, p <= 0 or NaN) are
+ * latched there and read by dg_noalloc_status.  Queued on `stream`
+ * (cudaStream_t, NULL = legacy default); returns before the work finishes.
+ * Concurrent first calls from several host threads are safe (the set-up is
+ * serialised). */
 #define DG_NOALLOC_SCRATCH_BYTES (16u << 20)
 dg_status dg_rhs_ns_noalloc(int N, int64_t K, const int32_t* nbr, const double* Ja,
                             const double* invJ, double gamma, double mu, double Pr,
                             int volume_flux, int surface_flux, const double* u, double* rhs,
                             void* stream);
+
+/* Status word latched by the last dg_rhs_ns_noalloc call on the current device
+ * (no counterpart in the paper).  Copies the 8-byte word into *status_out (a
+ * host variable; (code << 56) | element, 0 when clean) after the work queued on
+ * `stream` before it, waiting for the stream (bounded: DG_ETIMEOUT after 600 s),
+ * and returns DG_OK, DG_EINVAL (a neighbour index outside [0, K)) or
+ * DG_ENONPHYS.  Allocates no device memory.  Does not clear the word. */
+dg_status dg_noalloc_status(void* stream, uint64_t* status_out);
 
 #ifdef __cplusplus
 }

@@ -36,6 +36,7 @@ EXPORTED = [
     "dg_rhs_ns_noalloc", "dg_get_temperature", "dg_set_surrogate", "dg_surrogate_stats",
     "dg_thermo_sample", "dg_mlp_nparams", "dg_mlp_workspace_bytes", "dg_mlp_grad",
     "dg_mlp_train_step", "dg_mlp_forward", "dg_peak_flops", "dg_chem_sample", "dg_limiter_stats", "dg_limit_state",
+    "dg_noalloc_status", "dg_get_metrics",
 ]
 PROF_KINDS = ["rhs", "gradients", "indicator", "lambda", "thermo", "mlp", "chem", "other", "limiter"]
 
@@ -86,6 +87,8 @@ def lib():
             "dg_diagnostics": (i, [vp, vp]),
             "dg_get_alpha": (i, [vp, vp]),
             "dg_get_gradients": (i, [vp, vp]),
+            "dg_get_metrics": (i, [vp, vp, vp, i]),
+            "dg_noalloc_status": (i, [vp, vp]),
             "dg_sync": (i, [vp]),
             "dg_error_element": (i64, [vp]),
             "dg_status_string": (C.c_char_p, [i]),
@@ -275,6 +278,12 @@ def dg_get_gradients(ctx, shape):
     return g
 
 
+def dg_get_metrics(ctx, Ja, invJ):
+    """FP64 metric terms of the context into caller buffers Ja [K][dim][dim][np] and
+    invJ [K][np] (numpy arrays or CUDA tensors, both on the same side)."""
+    _check(lib().dg_get_metrics(ctx, _ptr(Ja), _ptr(invJ), _on_device(Ja)), "dg_get_metrics")
+
+
 def dg_sync(ctx):
     _check(lib().dg_sync(ctx), "dg_sync")
 
@@ -303,6 +312,16 @@ def dg_rhs_ns_noalloc(N, K, nbr, Ja, invJ, gamma, mu, Pr, volume_flux, surface_f
     _check(lib().dg_rhs_ns_noalloc(N, K, _ptr(nbr), _ptr(Ja), _ptr(invJ), gamma, mu, Pr,
                                    volume_flux, surface_flux, _ptr(u), _ptr(rhs), stream),
            "dg_rhs_ns_noalloc")
+
+
+def dg_noalloc_status(stream=None):
+    """(code, raw status word) latched by the last dg_rhs_ns_noalloc call on the current
+    device, after the stream's queued work: code DG_OK, DG_EINVAL or DG_ENONPHYS."""
+    w = C.c_uint64(0)
+    code = lib().dg_noalloc_status(stream, C.byref(w))
+    if code not in (DG_OK, DG_EINVAL, DG_ENONPHYS):
+        raise DgError(code, "dg_noalloc_status")
+    return code, int(w.value)
 
 
 def dg_destroy(ctx):

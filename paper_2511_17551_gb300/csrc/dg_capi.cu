@@ -1123,6 +1123,15 @@ dg_status dg_get_alpha(dg_ctx* c, double* alpha) {
   return wait_stream(c);
 }
 
+dg_status dg_get_metrics(dg_ctx* c, double* Ja, double* invJ, int on_device) {
+  if (!c || !Ja || !invJ) return DG_EINVAL;
+  cudaSetDevice(c->dev);
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  CK(cudaMemcpyAsync(Ja, c->Ja64, sizeof(double) * c->K * c->dim * c->dim * c->np, kind, c->stream));
+  CK(cudaMemcpyAsync(invJ, c->invJ64, sizeof(double) * c->K * c->np, kind, c->stream));
+  return wait_stream(c);
+}
+
 dg_status dg_get_gradients(dg_ctx* c, double* g) {
   if (!c || !g) return DG_EINVAL;
   if (!c->have_grad) return DG_ESTATE;
