@@ -212,7 +212,8 @@ dg_status dg_get_temperature(dg_ctx* ctx, double* T);
  *   S_s = omega_s / (1 + dt jpi_s) for any RK step dt.  Stats (FP64, DG_SRC_NSTATS)
  *   indexed by the DG_SRC_* offsets below.  Acceptance per tile of 32 consecutive nodes:
  *   every node's raw features inside the training box, every node's raw rates
- *   mass-balanced (|sum omega| <= tol_mass sum |omega| + floor), and, at one node per tile drawn
+ *   mass-balanced (|sum omega| <= tol_mass sum |omega| + floor), every node's learned
+ *   update positive (rho_s + dt S_s >= 0, dt the running step), and, at one node per tile drawn
  *   anew each evaluation, |S_learned - S_plain| <= tol_check sum_s |S_plain| + floor for
  *   every species; rejected tiles are recomputed with the plain FP64 source.  Accepted
  *   rates are projected onto exact mass balance, omega_s -= |omega_s| sum omega / sum|omega|. */
@@ -242,6 +243,17 @@ dg_status dg_set_surrogate(dg_ctx* ctx, int which, const float* params, const do
 /* Nodes accepted and nodes recomputed plainly by the surrogate `which` since the last
  * call (host int64[2]); resets the counters. */
 dg_status dg_surrogate_stats(dg_ctx* ctx, int which, int64_t* accepted_fallback);
+
+/* The species source of the last evaluation (the appendix's finite-rate source with its
+ * point-implicit factor, Eqs. nrp .. calc_prod; learned where the surrogate's tile was
+ * accepted): S [K][5][np] FP64 host (converted from the form precision).  flags (host,
+ * (K np + 31) / 32 bytes, or NULL) receives the per-tile decision of that evaluation:
+ * 0 learned, 1 rejected by the trust box or the mass balance, 2 rejected by the sampled
+ * check (255 everywhere when the learned source is off); *call (or NULL) the evaluation
+ * counter that drew the tiles' sampled nodes (-1 before the first learned evaluation).
+ * DG_EINVAL for a context without chemistry, DG_ESTATE before any evaluation.  Waits for
+ * the context stream (bounded). */
+dg_status dg_get_source(dg_ctx* ctx, double* S, unsigned char* flags, int64_t* call);
 
 /* Training data from the plain solver: runs the temperature solve on the current state,
  * then writes n samples drawn with splitmix64(seed + j) over all nodes:

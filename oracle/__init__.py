@@ -83,6 +83,7 @@ def lib():
             "or_mlp_nparams": (i, []),
             "or_mlp_nparams_n": (i, [i]),
             "or_mlp_forward_n": (i, [vp, i, i, vp, vp]),
+            "or_mlp_forward_sd_n": (i, [vp, i, i, vp, d, d, d, d, vp, vp, vp]),
             "or_mlp_loss_grad_n": (d, [vp, i, i, vp, vp, vp]),
             "or_chem_eval": (i, [vp, i, vp, i, vp, vp, d, vp, vp, vp]),
             "or_gelu": (d, [d]),
@@ -92,6 +93,7 @@ def lib():
             "or_adam_step": (None, [vp, vp, vp, vp, i, i, d, d, d, d]),
             "or_mixture_temperature": (i, [i, vp, i, vp, vp, vp, vp, vp]),
             "or_positivity": (i, [vp, vp, d, vp]),
+            "or_set_threads": (i, [i]),
         }
         for name, (res, args) in sig.items():
             f = getattr(_lib, name)
@@ -102,6 +104,11 @@ def lib():
 
 def _p(a):
     return a.ctypes.data if a is not None else None
+
+
+def set_threads(n):
+    """OpenMP threads of the oracle's element loops (n <= 0: query); returns the count."""
+    return lib().or_set_threads(int(n))
 
 
 def lgl(N):
@@ -328,34 +335,241 @@ def mlp_loss_grad(params, X, t, n_out=1):
     return loss, g
 
 
-def chem_surrogate_source(params, stats, rhos, T, dt=0.0):
-    """FP64 evaluation of the learned chemistry source at nodes (rhos [n][5] species
-    densities, T [n]) with the ten-output perceptron and the statistics vector of the
-    C interface (offsets: feature mean 0, std 7; target mean 14, std 24; omega_ref 34,
-    jpi_ref 35; box lo 36, hi 43; tolerances 50 (check), 51 (mass), floor 52).
+# unit roundoff of BF16 (8-bit significand, round to nearest)
+BF16_U = 2.0 ** -8
+# bound on the absolute error of the GPU's hardware tanh approximation (tanh.approx.f32):
+# measured on a GB300 over 2^24 arguments in [-12, 12], 8.0e-6 = 2^-16.9; taken as 2^-16
+TANH_APPROX_EPS = 2.0 ** -16
 
-    Steps: raw features x = (Y_1..Y_5, ln rho, T); network on (x - mean)/std; decode
-    omega_s = omega_ref sinh(mu_s + sd_s y_s), jpi_s = max(0, jpi_ref sinh(mu_{5+s} +
-    sd_{5+s} y_{5+s})); node accepted when x lies in the box and |sum omega| <=
-    tol_mass sum|omega| + floor; projection omega_s -= |omega_s| sum(omega)/sum|omega|;
-    S_s = omega_s / (1 + dt jpi_s).  Returns (S [n][5], accepted [n] bool, omega raw
-    [n][5], jpi [n][5])."""
+
+def mlp_forward_sd(params, X, n_out=1, u=BF16_U, eps_t=TANH_APPROX_EPS, x_rel=0.0, u_flip=0.0,
+                   want_flip=False):
+    """Exact FP64 outputs [n][n_out] and the standard deviation of the GPU's difference from
+    a reference under the first-order rounding model of or_mlp_forward_sd_n (u = BF16_U:
+    the reference is the exact network; u = 0, u_flip = BF16_U: the reference is the BF16
+    emulation mlp_forward_bf16, and want_flip adds the largest effect of one hidden unit
+    rounding to its neighbouring BF16 value)."""
+    params = np.ascontiguousarray(params, dtype=np.float64)
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    y = np.zeros((X.shape[0], n_out))
+    sd = np.zeros((X.shape[0], n_out))
+    fl = np.zeros((X.shape[0], n_out)) if want_flip else None
+    if lib().or_mlp_forward_sd_n(_p(params), n_out, X.shape[0], _p(X), u, u_flip, eps_t, x_rel, _p(y),
+                                 _p(sd), _p(fl)):
+        raise ValueError("n_out out of range")
+    return (y, sd, fl) if want_flip else (y, sd)
+
+
+def bf16(x):
+    """Round to BF16 (round to nearest, ties to even) via the FP32 bit pattern; returns
+    float32 values."""
+    b = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    b = (b + 0x7FFF + ((b >> 16) & 1)) & 0xFFFF0000
+    return b.astype(np.uint32).view(np.float32)
+
+
+def _gelu32(z):
+    k = np.float32(np.sqrt(2.0 / np.pi))
+    arg = (k * (z + np.float32(0.044715) * z * z * z)).astype(np.float32)
+    t = np.tanh(arg.astype(np.float64)).astype(np.float32)
+    return (np.float32(0.5) * z * (np.float32(1.0) + t)).astype(np.float32)
+
+
+def mlp_forward_bf16(params, Xn32, n_out, want_flip=False, eps_t=TANH_APPROX_EPS):
+    """The network evaluated with the GPU's roundings, for decisions in the kernel's
+    precision: FP32 standardised inputs Xn32 [n][7], inputs, W1, W2 and the first hidden
+    layer's activations rounded to BF16, each sum rounded once to FP32 (exact products of
+    BF16 values summed in FP64), GELU in FP32 with the tanh of FP64 rounded to FP32, the
+    output layer in FP32 with FP32 weights.  Returns float64 [n][n_out].
+
+    want_flip: also returns, per output, the effect of the first hidden units that may
+    round to the other BF16 neighbour on the GPU: a unit whose FP32 activation lies within
+    d of a rounding boundary, d bounding the GPU's difference before rounding (its FP32 sum
+    of 8 terms, the tanh approximation's eps_t, the GELU's FP32 operations), contributes
+    the first-order effect of one BF16 spacing on each output,
+    sum_j |W3_oj| |gelu'(z2_j)| |W2_ji| spacing_i."""
+    NI_, NH_ = 7, 64
+    p32 = np.asarray(params, dtype=np.float32)
+    W1 = bf16(p32[:NH_ * NI_].reshape(NH_, NI_)).astype(np.float64)
+    b1 = p32[NH_ * NI_:NH_ * NI_ + NH_]
+    o = NH_ * NI_ + NH_
+    W2 = bf16(p32[o:o + NH_ * NH_].reshape(NH_, NH_)).astype(np.float64)
+    b2 = p32[o + NH_ * NH_:o + NH_ * NH_ + NH_]
+    o3 = o + NH_ * NH_ + NH_
+    W3 = p32[o3:o3 + n_out * NH_].reshape(n_out, NH_).astype(np.float64)
+    b3 = p32[o3 + n_out * NH_:o3 + n_out * NH_ + n_out]
+    xb = bf16(np.asarray(Xn32, dtype=np.float32)).astype(np.float64)
+    z1 = ((xb @ W1.T).astype(np.float32) + b1).astype(np.float32)
+    a1f = _gelu32(z1)
+    a1 = bf16(a1f).astype(np.float64)
+    z2 = ((a1 @ W2.T).astype(np.float32) + b2).astype(np.float32)
+    a2 = _gelu32(z2).astype(np.float64)
+    y = ((a2 @ W3.T).astype(np.float32) + b3).astype(np.float64)
+    if not want_flip:
+        return y
+    u32 = 2.0 ** -24
+    z1d = z1.astype(np.float64)
+    mag1 = np.abs(xb) @ np.abs(W1.T) + np.abs(b1.astype(np.float64))
+    gd1 = np.abs(_gelu_d_np(z1d))
+    d = gd1 * 10 * u32 * mag1 + 0.5 * np.abs(z1d) * eps_t + 6 * u32 * np.abs(a1f.astype(np.float64))
+    # distance of the FP32 activation to the nearest BF16 rounding boundary (the midpoints
+    # between neighbouring BF16 values), and the BF16 spacing there
+    lo = bf16(a1f).astype(np.float64)
+    b = np.ascontiguousarray(bf16(a1f)).view(np.uint32).astype(np.int64)
+    # neighbouring BF16 values: the next and previous 16-bit patterns (BF16 is the top half
+    # of the FP32 pattern)
+    up = (b + (1 << 16)).astype(np.uint32).view(np.float32).astype(np.float64)
+    dn = (b - (1 << 16)).astype(np.uint32).view(np.float32).astype(np.float64)
+    dist = np.minimum(np.abs(a1f - 0.5 * (lo + up)), np.abs(a1f - 0.5 * (lo + dn)))
+    spacing = np.maximum(np.abs(up - lo), np.abs(lo - dn))
+    near = dist <= d
+    gd2 = np.abs(_gelu_d_np(z2.astype(np.float64)))
+    flip = np.zeros((xb.shape[0], n_out))
+    for r in np.nonzero(near.any(axis=1))[0]:
+        units = np.nonzero(near[r])[0]
+        # effect of unit i on output o: sum_j |W3_oj| |gelu'(z2_j)| |W2_ji| spacing_i
+        eff = (np.abs(W3) * gd2[r][None, :]) @ np.abs(W2[:, units]) * spacing[r, units][None, :]
+        flip[r] = eff.sum(axis=1)
+    return y, flip
+
+
+def _gelu_d_np(x):
+    """Derivative of the tanh form of GELU (vectorised; the same formula as or_gelu_d)."""
+    k = np.sqrt(2.0 / np.pi)
+    t = np.tanh(k * (x + 0.044715 * x ** 3))
+    return 0.5 * (1.0 + t) + 0.5 * x * (1.0 - t * t) * k * (1.0 + 3.0 * 0.044715 * x * x)
+
+
+_M64 = (1 << 64) - 1
+
+
+def splitmix64(x):
+    """Steele, Lea & Flood's SplitMix64 output function of the state increment x (one step
+    from state x): z = x + 0x9E3779B97F4A7C15, then two xor-shift-multiply rounds (30, 27)
+    and a final xor-shift (31).  Python integers, vectorised over a sequence."""
+    out = []
+    for v in np.atleast_1d(x):
+        z = (int(v) + 0x9E3779B97F4A7C15) & _M64
+        z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & _M64
+        z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & _M64
+        out.append(z ^ (z >> 31))
+    return out
+
+
+def chem_surrogate_source(params, stats, rhos, T, dt=0.0, *, species=None, reactions=None, call=None,
+                          lam=8.0, x_rel=0.0, network="fp64"):
+    """The learned chemistry source by the acceptance rule of reading R18s, in FP64.
+
+    params: ten-output perceptron (FP32 values); stats: the statistics vector of the C
+    interface (feature mean 0:7, std 7:14; target mean 14:24, std 24:34; omega_ref 34,
+    jpi_ref 35; trust box lo 36:43, hi 43:50; tau_c 50, tau_m 51, floor 52); rhos [n][5]
+    species densities, T [n] temperatures of the nodes in element-major order; dt the
+    point-implicit step.
+
+    Steps (R18s): features x = (Y_1..Y_5, ln rho, T); network on (x - mean)/std; decode
+    omega = omega_ref sinh(z), jpi = max(0, jpi_ref sinh(z')) with z = mean + std y; trust
+    box in FP32; mass balance |sum omega| <= tau_m sum|omega| + floor (finite); projection
+    omega_s -= |omega_s| sum(omega) / sum|omega|; S = omega / (1 + dt jpi); positivity
+    rho_s + dt S_s >= 0 in FP32 (reported in mass_ok and, alone, in positive).  With species,
+    reactions and the call counter given: the sampled check of every 32-node tile against
+    the plain source (chem_eval) at node 32 t + splitmix64(call 1099511628211 + t) mod n_t,
+    and the per-tile decision.
+
+    network = "fp64" evaluates the network exactly (the definition) and bounds the GPU's
+    difference by its BF16 roundings; network = "bf16" evaluates it with the GPU's own
+    roundings (mlp_forward_bf16: decisions in the kernel's precision) and bounds only what
+    remains (FP32 sum order, the tanh approximation, the rare BF16 rounding of a hidden
+    unit to the neighbouring value).  The bound is lam standard deviations of the
+    first-order model, carried through decode, projection and the point-implicit factor;
+    per tile, the result says whether any decision lies within that bound of its
+    threshold (ambiguous: the GPU may decide either way).  x_rel: relative error of the
+    raw features of the GPU's input state (0 for an FP64 state)."""
     st = np.asarray(stats, dtype=np.float64)
     rhos = np.asarray(rhos, dtype=np.float64)
     T = np.asarray(T, dtype=np.float64)
+    n = len(T)
+    u32 = 2.0 ** -24
     rho = rhos.sum(axis=1)
     x = np.column_stack([rhos / rho[:, None], np.log(rho), T])
-    y = mlp_forward(params, (x - st[0:7]) / st[7:14], 10)
+    # 1. trust box, decided in FP32
+    x32 = x.astype(np.float32)
+    lo32, hi32 = st[36:43].astype(np.float32), st[43:50].astype(np.float32)
+    inside = np.all((x32 >= lo32) & (x32 <= hi32), axis=1)
+    ulp = np.spacing(np.abs(x32)).astype(np.float64)
+    box_amb = np.any((np.abs(x32.astype(np.float64) - lo32) <= ulp) |
+                     (np.abs(x32.astype(np.float64) - hi32) <= ulp), axis=1)
+    # 2. network and decode, with the rounding bound
+    if network == "bf16":
+        # standardisation as the kernel does it: FP32 features, FP32 mean and 1/std
+        xn32 = ((x32 - st[0:7].astype(np.float32)) * (1.0 / st[7:14]).astype(np.float32)).astype(np.float32)
+        _, sd = mlp_forward_sd(params, xn32.astype(np.float64), 10, u=0.0, x_rel=x_rel)
+        y, fl = mlp_forward_bf16(params, xn32, 10, want_flip=True)
+        # the hidden units that may round to the other BF16 neighbour, as worst-case jumps
+        sd = sd + fl / lam
+    else:
+        y, sd = mlp_forward_sd(params, (x - st[0:7]) / st[7:14], 10, x_rel=x_rel)
     z = st[14:24] + st[24:34] * y
+    Bz = lam * np.abs(st[24:34]) * sd + 4 * u32 * (np.abs(st[14:24]) + np.abs(st[24:34] * y))
     om = st[34] * np.sinh(z[:, :5])
-    jpi = np.maximum(0.0, st[35] * np.sinh(z[:, 5:]))
+    jp_raw = st[35] * np.sinh(z[:, 5:])
+    jpi = np.maximum(0.0, jp_raw)
+    Bom = st[34] * np.cosh(np.abs(z[:, :5]) + Bz[:, :5]) * Bz[:, :5] + 8 * u32 * np.abs(om)
+    Bjp = st[35] * np.cosh(np.abs(z[:, 5:]) + Bz[:, 5:]) * Bz[:, 5:] + 8 * u32 * np.abs(jp_raw)
+    # 3. mass balance
+    tau_c, tau_m, floor = st[50], st[51], st[52]
     msum = om.sum(axis=1)
     asum = np.abs(om).sum(axis=1)
-    inside = np.all((x >= st[36:43]) & (x <= st[43:50]), axis=1)
-    accepted = inside & (np.abs(msum) <= st[51] * asum + st[52])
-    frac = np.divide(msum, asum, out=np.zeros_like(msum), where=asum > 0)
-    S = (om - np.abs(om) * frac[:, None]) / (1.0 + dt * jpi)
-    return S, accepted, om, jpi
+    finite = np.isfinite(asum)
+    margin = tau_m * asum + floor - np.abs(msum)
+    unc = (1.0 + tau_m) * (Bom.sum(axis=1) + 6 * u32 * asum) + u32 * floor
+    mass_ok = finite & (margin >= 0.0)
+    mass_amb = np.abs(margin) <= unc
+    # 4. projection and the point-implicit factor
+    f = np.divide(msum, asum, out=np.zeros_like(msum), where=asum > 0)
+    om_t = om - np.abs(om) * f[:, None]
+    den = 1.0 + dt * jpi
+    S_l = om_t / den
+    dA = Bom.sum(axis=1)
+    Bomt = (1.0 + np.abs(f))[:, None] * (Bom + np.abs(om) * np.divide(
+        dA, asum, out=np.zeros_like(dA), where=asum > 0)[:, None]) + 4 * u32 * np.abs(om) * (1 + np.abs(f))[:, None]
+    bound = Bomt / den + np.abs(S_l) * dt * Bjp / den + 4 * u32 * np.abs(S_l)
+    # 5b. positivity of the learned update, decided in FP32: rho_s + dt S_s >= 0
+    dt32 = np.float32(dt)
+    pos_val = (rhos.astype(np.float32) + dt32 * S_l.astype(np.float32)).astype(np.float64)
+    pos_ok = np.all(pos_val >= 0.0, axis=1)
+    pos_amb = np.any(np.abs(pos_val) <= dt * bound + 4 * u32 * np.abs(rhos), axis=1)
+    mass_ok = mass_ok & pos_ok
+    mass_amb = mass_amb | pos_amb
+    out = {"S_learned": S_l, "bound": bound, "inside": inside, "mass_ok": mass_ok, "positive": pos_ok,
+           "omega": om, "jpi": jpi, "x": x}
+    if call is None:
+        return out
+    # 5. sampled check per 32-node tile and the decisions
+    _, _, S_p = chem_eval(species, reactions, rhos, T, dt)
+    ntiles = (n + 31) // 32
+    flag = np.zeros(ntiles, dtype=np.int8)
+    amb = np.zeros(ntiles, dtype=bool)
+    sampled = np.zeros(ntiles, dtype=np.int64)
+    node_ok = inside & mass_ok
+    node_amb = box_amb | mass_amb
+    hashes = splitmix64([(int(call) * 1099511628211 + t) & _M64 for t in range(ntiles)])
+    for t in range(ntiles):
+        a, b = 32 * t, min(n, 32 * t + 32)
+        i = a + int(hashes[t] % (b - a))
+        sampled[t] = i
+        amb[t] = bool(node_amb[a:b].any())
+        if not node_ok[a:b].all():
+            flag[t] = 1
+            continue
+        thr = tau_c * np.abs(S_p[i]).sum() + floor
+        m = thr - np.abs(S_l[i] - S_p[i])
+        if (m < 0.0).any():
+            flag[t] = 2
+        amb[t] |= bool((np.abs(m) <= bound[i] + 1e-10 * np.abs(S_p[i]).sum() + u32 * thr).any())
+    acc_node = np.repeat(flag == 0, 32)[:n]
+    out.update({"S_plain": S_p, "S": np.where(acc_node[:, None], S_l, S_p), "tile_flag": flag,
+                "tile_ambiguous": amb, "sampled_node": sampled})
+    return out
 
 
 def adam_step(params, m, v, g, step, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):

@@ -113,3 +113,17 @@ int or_invert(int n, const double* A, double* Ainv) {
   free(M);
   return 0;
 }
+
+/* number of OpenMP threads of the oracle's element loops (timing only; <= 0 leaves it) */
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+int or_set_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+  return omp_get_max_threads();
+#else
+  (void)n;
+  return 1;
+#endif
+}

@@ -73,6 +73,98 @@ int or_mlp_forward_n(const double* p, int no, int n, const double* X, double* Y)
 
 void or_mlp_forward(const double* p, int n, const double* X, double* y) { or_mlp_forward_n(p, 1, n, X, y); }
 
+/* First-order statistical model of the error of the network's evaluation on the GPU with
+ * BF16 operands (reading R18s of the learned chemistry source).  The GPU rounds the
+ * standardised inputs, W1, W2 and the first hidden layer's activations to BF16, accumulates
+ * in FP32, evaluates GELU with a tanh approximation of absolute error at most eps_t and the
+ * output layer in FP32.  Each rounding is modelled as an independent zero-mean error,
+ * uniform within its bound (variance (u |v|)^2 / 3 for a value v rounded with unit
+ * roundoff u, eps_t^2 / 3 for the tanh error), and propagated to first order (GELU through
+ * its derivative).
+ *   u_round: unit roundoff of the BF16 roundings (2^-8 against the exact network; 0 against
+ *            a network that rounds exactly where the GPU does);
+ *   u_flip:  against such an emulation, a first hidden activation of the GPU (off from the
+ *            emulation's by its FP32 sums and tanh) can round to the neighbouring BF16 value,
+ *            a rare jump of 2 u_flip |a| that no variance describes: FLIP [n][n_out] (when
+ *            not NULL) receives, per output, the largest first-order effect of one such jump
+ *            over the 64 hidden units, sum_j |W3_oj| |gelu'(z2_j)| |W2_ji| 2 u_flip |a_i|;
+ *   x_rel:   a relative error of the raw inputs (an input state in FP32), in units of |x| + 1.
+ * Returns the exact FP64 outputs Y [n][n_out] and the standard deviations SD [n][n_out] of
+ * the GPU's difference from the reference under the model. */
+int or_mlp_forward_sd_n(const double* p, int no, int n, const double* X, double u, double u_flip,
+                        double eps_t, double x_rel, double* Y, double* SD, double* FLIP) {
+  if (no < 1 || no > NO_MAX) return 1;
+  const double u32 = ldexp(1.0, -23);  /* FP32 accumulation, one rounding per addition */
+  const double third = 1.0 / 3.0;
+  double a1[NH], h1[NH], a2[NH], h2[NH];
+  double vx[NI], va1[NH], va2[NH];
+  for (int s = 0; s < n; ++s) {
+    const double* x = X + (size_t)s * NI;
+    double* y = Y + (size_t)s * no;
+    double* sd = SD + (size_t)s * no;
+    forward1(p, no, x, a1, h1, a2, h2, y);
+    for (int i = 0; i < NI; ++i) {
+      const double r = u * fabs(x[i]), q = x_rel * (fabs(x[i]) + 1.0);
+      vx[i] = third * (r * r + q * q);
+    }
+    /* layer 1: rounded inputs and weights, FP32 sum of 7 products and the bias */
+    for (int j = 0; j < NH; ++j) {
+      double v = 0.0, mag = fabs(p[OFF_B1 + j]);
+      for (int i = 0; i < NI; ++i) {
+        const double w = p[OFF_W1 + j * NI + i];
+        v += w * w * vx[i] + third * (u * w * x[i]) * (u * w * x[i]);
+        mag += fabs(w * x[i]);
+      }
+      v += third * (NI + 1) * (u32 * mag) * (u32 * mag);
+      const double g = or_gelu_d(a1[j]), t = 0.5 * a1[j] * eps_t;
+      /* GELU (derivative, tanh approximation, a few FP32 operations), then BF16 rounding */
+      const double vg = g * g * v + third * t * t + third * 4.0 * (u32 * h1[j]) * (u32 * h1[j]);
+      va1[j] = vg + third * (u * h1[j]) * (u * h1[j]);
+    }
+    /* layer 2: rounded activations and weights, FP32 sum of 64 products and the bias */
+    for (int j = 0; j < NH; ++j) {
+      double v = 0.0, mag = fabs(p[OFF_B2 + j]);
+      for (int i = 0; i < NH; ++i) {
+        const double w = p[OFF_W2 + j * NH + i];
+        v += w * w * va1[i] + third * (u * w * h1[i]) * (u * w * h1[i]);
+        mag += fabs(w * h1[i]);
+      }
+      v += third * (NH + 1) * (u32 * mag) * (u32 * mag);
+      const double g = or_gelu_d(a2[j]), t = 0.5 * a2[j] * eps_t;
+      va2[j] = g * g * v + third * t * t + third * 4.0 * (u32 * h2[j]) * (u32 * h2[j]);
+    }
+    /* output layer in FP32 with FP32 weights */
+    for (int o = 0; o < no; ++o) {
+      double v = 0.0, mag = fabs(p[OFF_B3(no) + o]);
+      for (int i = 0; i < NH; ++i) {
+        const double w = p[OFF_W3 + o * NH + i];
+        v += w * w * va2[i];
+        mag += fabs(w * h2[i]);
+      }
+      v += third * (NH + 1) * (u32 * mag) * (u32 * mag);
+      sd[o] = sqrt(v);
+    }
+    if (FLIP && u_flip > 0.0) {
+      double gd2[NH];
+      for (int j = 0; j < NH; ++j) gd2[j] = fabs(or_gelu_d(a2[j]));
+      for (int o = 0; o < no; ++o) {
+        double worst = 0.0;
+        for (int i = 0; i < NH; ++i) {
+          double e = 0.0;
+          for (int j = 0; j < NH; ++j)
+            e += fabs(p[OFF_W3 + o * NH + j]) * gd2[j] * fabs(p[OFF_W2 + j * NH + i]);
+          e *= 2.0 * u_flip * fabs(h1[i]);
+          if (e > worst) worst = e;
+        }
+        FLIP[(size_t)s * no + o] = worst;
+      }
+    } else if (FLIP) {
+      for (int o = 0; o < no; ++o) FLIP[(size_t)s * no + o] = 0.0;
+    }
+  }
+  return 0;
+}
+
 /* loss = (1/(n n_out)) sum_s sum_o (y_so - t_so)^2 and its gradient with respect to every
  * parameter; returns the loss (negative on invalid n_out) */
 double or_mlp_loss_grad_n(const double* p, int no, int n, const double* X, const double* t, double* g) {

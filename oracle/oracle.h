@@ -142,6 +142,8 @@ int or_chem_eval(const double* species, int nr, const double* reac, int n, const
 int or_mlp_nparams(void);
 int or_mlp_nparams_n(int n_out);
 int or_mlp_forward_n(const double* p, int n_out, int n, const double* X, double* Y);
+int or_mlp_forward_sd_n(const double* p, int n_out, int n, const double* X, double u, double u_flip,
+                        double eps_t, double x_rel, double* Y, double* SD, double* FLIP);
 double or_mlp_loss_grad_n(const double* p, int n_out, int n, const double* X, const double* t,
                           double* g);
 double or_gelu(double x);
@@ -151,4 +153,5 @@ double or_mlp_loss_grad(const double* p, int n, const double* X, const double* t
 void or_adam_step(double* p, double* m, double* v, const double* g, int np_, int step, double lr,
                   double b1, double b2, double eps);
 
+int or_set_threads(int n);
 #endif

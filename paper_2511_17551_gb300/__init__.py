@@ -36,7 +36,7 @@ EXPORTED = [
     "dg_rhs_ns_noalloc", "dg_get_temperature", "dg_set_surrogate", "dg_surrogate_stats",
     "dg_thermo_sample", "dg_mlp_nparams", "dg_mlp_workspace_bytes", "dg_mlp_grad",
     "dg_mlp_train_step", "dg_mlp_forward", "dg_peak_flops", "dg_chem_sample", "dg_limiter_stats", "dg_limit_state",
-    "dg_noalloc_status", "dg_get_metrics",
+    "dg_noalloc_status", "dg_get_metrics", "dg_get_source",
 ]
 PROF_KINDS = ["rhs", "gradients", "indicator", "lambda", "thermo", "mlp", "chem", "other", "limiter"]
 
@@ -88,6 +88,7 @@ def lib():
             "dg_get_alpha": (i, [vp, vp]),
             "dg_get_gradients": (i, [vp, vp]),
             "dg_get_metrics": (i, [vp, vp, vp, i]),
+            "dg_get_source": (i, [vp, vp, vp, vp]),
             "dg_noalloc_status": (i, [vp, vp]),
             "dg_sync": (i, [vp]),
             "dg_error_element": (i64, [vp]),
@@ -282,6 +283,16 @@ def dg_get_metrics(ctx, Ja, invJ):
     """FP64 metric terms of the context into caller buffers Ja [K][dim][dim][np] and
     invJ [K][np] (numpy arrays or CUDA tensors, both on the same side)."""
     _check(lib().dg_get_metrics(ctx, _ptr(Ja), _ptr(invJ), _on_device(Ja)), "dg_get_metrics")
+
+
+def dg_get_source(ctx, shape):
+    """(S [K][5][np] FP64, tile flags uint8, call index) of the last source evaluation."""
+    K, _, npn = shape
+    S = np.zeros((K, 5, npn))
+    flags = np.zeros((K * npn + 31) // 32, dtype=np.uint8)
+    call = C.c_int64(-1)
+    _check(lib().dg_get_source(ctx, _ptr(S), _ptr(flags), C.byref(call)), "dg_get_source")
+    return S, flags, call.value
 
 
 def dg_sync(ctx):

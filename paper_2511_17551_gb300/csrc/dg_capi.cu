@@ -515,6 +515,7 @@ cudaError_t pre_rhs(dg_ctx* c, DgArgs& a) {
                               c->stream);
       });
       if (e != cudaSuccess) return e;
+      c->th.src_valid = 1;
       a.src = c->th.src;
     }
   }
@@ -1121,6 +1122,31 @@ dg_status dg_get_alpha(dg_ctx* c, double* alpha) {
   if (!c->have_alpha) return DG_ESTATE;
   CK(cudaMemcpyAsync(alpha, c->alpha_used, sizeof(double) * c->K, cudaMemcpyDeviceToHost, c->stream));
   return wait_stream(c);
+}
+
+dg_status dg_get_source(dg_ctx* c, double* S, unsigned char* flags, int64_t* call) {
+  if (!c || !S || c->n_species == 0 || c->th.nr == 0) return DG_EINVAL;
+  if (!c->th.src_valid) return DG_ESTATE;
+  cudaSetDevice(c->dev);
+  dg_status w = wait_stream(c);
+  if (w != DG_OK) return w;
+  const int64_t n = c->K * 5 * c->np, ntiles = (c->K * c->np + 31) / 32;
+  if (c->precision == DG_MIXED) {
+    float* tmp = (float*)malloc(sizeof(float) * n);
+    if (!tmp) return DG_ENOMEM;
+    const cudaError_t e = cudaMemcpy(tmp, c->th.src, sizeof(float) * n, cudaMemcpyDeviceToHost);
+    for (int64_t i = 0; e == cudaSuccess && i < n; ++i) S[i] = (double)tmp[i];
+    free(tmp);
+    CK(e);
+  } else {
+    CK(cudaMemcpy(S, c->th.src, sizeof(double) * n, cudaMemcpyDeviceToHost));
+  }
+  if (flags) {
+    if (c->th.chem_mlp && c->th.chem_flags) CK(cudaMemcpy(flags, c->th.chem_flags, (size_t)ntiles, cudaMemcpyDeviceToHost));
+    else memset(flags, 255, (size_t)ntiles);
+  }
+  if (call) *call = c->th.chem_calls > 0 ? (int64_t)c->th.chem_calls - 1 : -1;
+  return DG_OK;
 }
 
 dg_status dg_get_metrics(dg_ctx* c, double* Ja, double* invJ, int on_device) {

@@ -138,10 +138,10 @@ __global__ void chem_kernel(const T* u, const double* Tc, int64_t K, int np, int
 // (Y_1..Y_5, ln rho, T); outputs are the standardised asinh images
 // z_s = asinh(omega_s / omega_ref), z_{5+s} = asinh(jpi_s / jpi_ref).
 // Acceptance, per tile of 32 nodes (one warp): every node inside the training box, every
-// node's raw rates mass-balanced (|sum omega| <= tol_mass sum|omega| + floor), and one
-// sampled node per tile (moved
-// each call) within tol_check of the plain FP64 source; otherwise the tile's source is
-// recomputed plainly.  Accepted rates are projected onto exact mass balance:
+// node's raw rates mass-balanced (|sum omega| <= tol_mass sum|omega| + floor), every
+// node's learned update positive (rho_s + dt S_s >= 0), and one sampled node per tile
+// (moved each call) within tol_check of the plain FP64 source; otherwise the tile's source
+// is recomputed plainly.  Accepted rates are projected onto exact mass balance:
 // omega_s -= |omega_s| sum(omega) / sum|omega|.
 struct __align__(16) DgChemMlp {
   DgMlpW<10> w;
@@ -222,8 +222,15 @@ chem_mlp_tc5_kernel(const T* u, const double* Tc, int64_t K, int np, int dim, co
       ok = ok && isfinite(asum) && fabsf(msum) <= m.tol_mass * asum + m.floor32;
       const float f = asum > 0.f ? msum / asum : 0.f;
       T* so = src + (i / np) * NSPEC * np + (i % np);
+      // positivity of the learned update: rho_s + dt S_s >= 0 (the plain point-implicit
+      // source never consumes a species faster than the step allows; a learned one can)
+      const T* uu = u + (i / np) * nv * np + (i % np);
 #pragma unroll
-      for (int q = 0; q < NSPEC; ++q) so[q * np] = (T)((om[q] - fabsf(om[q]) * f) / (1.f + dt * jp[q]));
+      for (int q = 0; q < NSPEC; ++q) {
+        const float Sq = (om[q] - fabsf(om[q]) * f) / (1.f + dt * jp[q]);
+        ok = ok && ((float)uu[q * np] + dt * Sq >= 0.f);
+        so[q * np] = (T)Sq;
+      }
     }
     const bool tile_ok = __all_sync(0xffffffffu, ok);
     const int64_t base = i - (threadIdx.x & 31);  // first node of this warp's 32-node tile

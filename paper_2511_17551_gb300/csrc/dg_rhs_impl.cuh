@@ -369,6 +369,53 @@ rhs_kernel(const DgArgs a, const KConst kc) {
     if (have_elo)
       stage_rows<NP>(sacc, (const real*)a.ulo + e0 * NV * NP + (NSP + DIM) * NP, NV * NP, ne, tid, nth);
   }
+  // The line of this thread (phase B) and its neighbour traces at both end nodes (the
+  // element's face nodes of faces 2d and 2d + 1): requested now, so that they arrive while
+  // the element blocks are staged and the node phase runs, and consumed first thing in
+  // the line phase (the registers are free again before its flux pairs).
+  constexpr int NG = NS ? DIM + 1 : 1;
+  int ln_e, ln_d, ln_m;
+  if (L::UNI) {  // warp-uniform direction
+    ln_d = tid / (EPB * S::LPD);
+    ln_e = (tid / S::LPD) % EPB;
+    ln_m = tid % S::LPD;
+  } else {
+    ln_e = tid / S::LINES;
+    ln_d = (tid % S::LINES) / S::LPD;
+    ln_m = tid % S::LPD;
+  }
+  const bool line_thread = tid < EPB * S::LINES && ln_e < ne;
+  real pf_u[2][NV], pf_pc[2][2], pf_g[2][NG], pf_e[2];
+  int pf_nb[2];
+#pragma unroll
+  for (int side = 0; side < 2; ++side) {
+    pf_nb[side] = -1;
+    pf_e[side] = real(0);
+    if (line_thread) {
+      const int nb = a.nbr[(e0 + ln_e) * 2 * DIM + 2 * ln_d + side];
+      pf_nb[side] = nb;
+      if (nb >= 0) {
+        // the neighbour's node of this face: the other end of the same line there
+        const int nnode = S::line_base(ln_d, ln_m) + (side ? 0 : N) * S::stride(ln_d);
+        const real* gu = (const real*)a.u + (int64_t)nb * NV * NP + nnode;
+#pragma unroll
+        for (int k = 0; k < NV; ++k) pf_u[side][k] = gu[k * NP];
+        if (have_elo) pf_e[side] = ((const real*)a.ulo)[(int64_t)nb * NV * NP + (NSP + DIM) * NP + nnode];
+        if (NSP > 1) {
+          const real* pc = (const real*)a.pc + (int64_t)nb * 2 * NP + nnode;
+          pf_pc[side][0] = pc[0];
+          pf_pc[side][1] = pc[NP];
+        }
+        if (NS) {
+          // the neighbour's f^v . n: its contravariant viscous flux of direction d (the
+          // partner face node sees the same face metric)
+          const real* gn = (const real*)a.gradW + (int64_t)nb * L::NFV * NP + ln_d * (DIM + 1) * NP + nnode;
+#pragma unroll
+          for (int c = 0; c < NG; ++c) pf_g[side][c] = gn[c * NP];
+        }
+      }
+    }
+  }
   if (tid < EPB) {
     real al = 0;
     if (a.alpha_raw && tid < ne) {
@@ -469,21 +516,15 @@ rhs_kernel(const DgArgs a, const KConst kc) {
   }
   __syncthreads();
 
-  // ---- phase B1: one thread per line (THREADS >= EPB x LINES: at most one each): volume terms
+  // ---- phase B: one thread per line (THREADS >= EPB x LINES: at most one each): the volume
+  // terms along the line, then the interface fluxes at its two end nodes.  The end nodes of
+  // the lines of direction d are the element's face nodes of faces 2d and 2d + 1, so the
+  // line thread lifts those fluxes onto its own sums in registers: no face pass, no second
+  // barrier and no read-modify-write of the sums in shared memory.
   static_assert(L::THREADS >= EPB * S::LINES, "one line per thread");
-  if (tid < EPB * S::LINES) {
-    const int t = tid;
-    int e, d, m;
-    if (L::UNI) {  // warp-uniform direction
-      d = t / (EPB * S::LPD);
-      e = (t / S::LPD) % EPB;
-      m = t % S::LPD;
-    } else {
-      e = t / S::LINES;
-      d = (t % S::LINES) / S::LPD;
-      m = t % S::LPD;
-    }
-    if (e < ne) {
+  if (line_thread) {
+    const int e = ln_e, d = ln_d, m = ln_m;
+    {
     const int s = S::stride(d), base = S::line_base(d, m);
     const real* q = sq + e * L::SQ;
     const real* ja = sja + e * L::SJA + d * DIM * NP;  // Ja^d components at [c][node]
@@ -493,6 +534,113 @@ rhs_kernel(const DgArgs a, const KConst kc) {
     for (int i = 0; i < N1; ++i)
 #pragma unroll
       for (int k = 0; k < NV; ++k) acc[i][k] = 0;
+    // interface and boundary fluxes at the line's end nodes first (R5, R6: LLF / HLLC / EC,
+    // the boundary states), lifted with -w_0^-1 (face 2d) and +w_N^-1 (face 2d + 1), and
+    // the averaged viscous interface flux (R11) lifted as (Fv* - Fv).  One code instance
+    // for both sides (a loop, not unrolled); the sums of the two end nodes take the lifted
+    // terms by selects.
+    const int64_t eg = e0 + e;
+#pragma unroll 1
+    for (int side = 0; side < 2; ++side) {
+      const int f = 2 * d + side;
+      const int rnode = base + (side ? N : 0) * s, node = SW(rnode);
+      // the prefetched neighbour trace of this side (selects: one code instance, no
+      // dynamically indexed registers)
+      const int nb = side ? pf_nb[1] : pf_nb[0];
+      real nbu[NV], nbpc[2], nbg[NG];
+#pragma unroll
+      for (int k = 0; k < NV; ++k) nbu[k] = side ? pf_u[1][k] : pf_u[0][k];
+      const real nbe = side ? pf_e[1] : pf_e[0];
+      if (NSP > 1) {
+        nbpc[0] = side ? pf_pc[1][0] : pf_pc[0][0];
+        nbpc[1] = side ? pf_pc[1][1] : pf_pc[0][1];
+      }
+      if (NS) {
+#pragma unroll
+        for (int c = 0; c < NG; ++c) nbg[c] = side ? pf_g[1][c] : pf_g[0][c];
+      }
+      const real iw = side ? B.iw[N] : -B.iw[0];
+      NodeState<real, DIM, NSP> o;
+#pragma unroll
+      for (int k = 0; k < NV; ++k) o.u[k] = ue[k * NP + rnode];
+      o.rho = q[node];
+#pragma unroll
+      for (int c = 0; c < DIM; ++c) o.v[c] = q[(1 + c) * NP + node];
+      o.pp = q[(1 + DIM) * NP + node];
+      o.p = o.pp + kc.pref;
+      o.c = NSP == 1 ? RealOps<real>::sqrt_(kc.gamma * o.p * RealOps<real>::rcp(o.rho))
+                     : spc[e * L::SPC + NP + node];
+      real nface[DIM];
+#pragma unroll
+      for (int c = 0; c < DIM; ++c) nface[c] = ja[c * NP + node];
+      NodeState<real, DIM, NSP> x;
+      bool ok = true;
+      real Fs[NV];
+      int phys = outer_state<DIM, NSP>(a, kc, nb, nbu, nbpc, nbe, o, nface, x, ok);
+      if (!ok) latch_status(a.status, DG_ST_NONPHYS, nb >= 0 ? nb : eg);
+      if (phys) phys_flux<real, DIM, NSP>(x, nface, Fs);
+      else if (FL) llf_oriented<real, DIM, NSP>(o, x, side != 0, nface, Fs);  // the production pair: LLF
+      else if (side) surface_flux<real, DIM, NSP>(sf, o, x, nface, kc.inv_gm1, kc.pref, Fs);
+      else surface_flux<real, DIM, NSP>(sf, x, o, nface, kc.inv_gm1, kc.pref, Fs);
+      const int bkind = nb >= 0 ? 0 : a.bc_kind[-(nb + 1)];
+      real vl[DIM + 1];
+#pragma unroll
+      for (int c = 0; c <= DIM; ++c) vl[c] = 0;
+      const bool visc = NS && bkind != DG_BC_OUTFLOW;
+      if (visc) {
+        // viscous interface flux: mean of both sides' f^v . n, lifted as (Fv* - Fv).  At a
+        // boundary the other side follows from the own flux (the flux is linear in the
+        // interior gradient): m = sigma . n, h = q . n = Fv_E - m . v; inflow: the external
+        // state's velocity and mu(T) (mean as at an interface); no-slip walls: Fv* = (m, h)
+        // at zero velocity, h = 0 on an adiabatic wall (Fv* itself, not a mean)
+        const bool wall = bkind == DG_BC_NOSLIP_ADIABATIC || bkind == DG_BC_ISOTHERMAL;
+        const real* fvd = sfv + e * L::SFV + d * (DIM + 1) * NP + node;
+        real fx[DIM + 1];
+        if (nb >= 0) {
+#pragma unroll
+          for (int c = 0; c <= DIM; ++c) fx[c] = nbg[c];
+        } else {
+          real h = fvd[DIM * NP];
+#pragma unroll
+          for (int c = 0; c < DIM; ++c) {
+            fx[c] = fvd[c * NP];
+            h -= fx[c] * o.v[c];
+          }
+          if (wall) {
+            fx[DIM] = bkind == DG_BC_ISOTHERMAL ? h : real(0);
+          } else {  // inflow
+            real r = 1;
+            if (!FL && kc.suth_s > real(0))
+              r = sutherland_ratio(x.p * RealOps<real>::rcp(x.rho), kc.suth_s, kc.suth_c1, kc.suth_irt) *
+                  RealOps<real>::rcp(sutherland_ratio(o.p * RealOps<real>::rcp(o.rho), kc.suth_s, kc.suth_c1,
+                                                      kc.suth_irt));
+            real w = 0;
+#pragma unroll
+            for (int c = 0; c < DIM; ++c) {
+              fx[c] *= r;
+              w += fx[c] * x.v[c];
+            }
+            fx[DIM] = w + r * h;
+          }
+        }
+#pragma unroll
+        for (int c = 0; c <= DIM; ++c) vl[c] = wall ? fx[c] - fvd[c * NP] : real(0.5) * (fx[c] - fvd[c * NP]);
+      }
+      // the end node's sums take the lifted terms: + iw F*, then - iw (Fv* - Fv)
+#pragma unroll
+      for (int k = 0; k < NV; ++k) {
+        if (side) acc[N][k] += iw * Fs[k];
+        else acc[0][k] += iw * Fs[k];
+      }
+      if (visc) {
+#pragma unroll
+        for (int c = 0; c <= DIM; ++c) {
+          if (side) acc[N][NSP + c] -= iw * vl[c];
+          else acc[0][NSP + c] -= iw * vl[c];
+        }
+      }
+    }
+
     const real al = s_alpha[e];
     const real wdg = real(1) - al;
     // every two-point flux is linear in the normal: F(n_i + n_l) = 2 F((n_i + n_l) / 2)
@@ -608,134 +756,6 @@ rhs_kernel(const DgArgs a, const KConst kc) {
     for (int i = 0; i < N1; ++i)
 #pragma unroll
       for (int k = 0; k < NV; ++k) sa[k * NP + SW(base + i * s)] = acc[i][k];
-    }
-  }
-  // ---- phase B2: one thread per face node and pass: the neighbour trace, then the
-  // interface flux and lifting.  The first pass's neighbour trace is loaded before the
-  // line phase's closing barrier, so that its latency overlaps the wait.
-  constexpr int FN = L::FACE_NODES, FIT = L::FIT, NG = NS ? DIM + 1 : 1;
-  // face-node threads: face-uniform warps where the layout is swizzled
-  auto face_of = [](int t, int& e, int& f, int& m) {
-    if (L::UNI) {
-      f = t / (EPB * S::LPD);
-      e = f < 2 * DIM ? (t / S::LPD) % EPB : EPB;
-      m = t % S::LPD;
-    } else {
-      e = t / FN;
-      f = (t % FN) / S::LPD;
-      m = t % S::LPD;
-    }
-  };
-  real nbu[NV], nbpc[2], nbg[NG], nbe;  // the neighbour's trace at this pass's face node
-  auto gather = [&](int it) {
-    int e, f, m;
-    face_of(tid + it * L::THREADS, e, f, m);
-    if (e >= ne) return;
-    const int d = f >> 1, side = f & 1;
-    const int nnode = S::line_base(d, m) + (side ? 0 : N) * S::stride(d);
-    const int nb = a.nbr[(e0 + e) * 2 * DIM + f];
-    nbe = real(0);
-    if (nb < 0) return;
-    const real* gu = (const real*)a.u + (int64_t)nb * NV * NP + nnode;
-#pragma unroll
-    for (int k = 0; k < NV; ++k) nbu[k] = gu[k * NP];
-    if (have_elo) nbe = ((const real*)a.ulo)[(int64_t)nb * NV * NP + (NSP + DIM) * NP + nnode];
-    if (NSP > 1) {
-      const real* pc = (const real*)a.pc + (int64_t)nb * 2 * NP + nnode;
-      nbpc[0] = pc[0];
-      nbpc[1] = pc[NP];
-    }
-    if (NS) {
-      // the neighbour's f^v . n: its contravariant viscous flux of direction d (the
-      // partner face node sees the same face metric)
-      const real* gn = (const real*)a.gradW + (int64_t)nb * L::NFV * NP + d * (DIM + 1) * NP + nnode;
-#pragma unroll
-      for (int c = 0; c < NG; ++c) nbg[c] = gn[c * NP];
-    }
-  };
-  gather(0);
-  __syncthreads();
-  // one face node per pass (a loop, not unrolled: one code instance of the face work)
-#pragma unroll 1
-  for (int it = 0; it < FIT; ++it) {
-    if (it > 0) gather(it);
-    int e, f, m;
-    face_of(tid + it * L::THREADS, e, f, m);
-    if (e >= ne) continue;
-    const int d = f >> 1, side = f & 1;
-    const int s = S::stride(d), base = S::line_base(d, m);
-    const int rnode = base + (side ? N : 0) * s, node = SW(rnode);
-    const int64_t eg = e0 + e;
-    const real* q = sq + e * L::SQ;
-    const real* ja = sja + e * L::SJA + d * DIM * NP;
-    const real* ue = su + e * L::SU;
-    real* sa = sacc + e * L::SACC + d * NV * NP + node;
-    const real iw = side ? B.iw[N] : -B.iw[0];
-    NodeState<real, DIM, NSP> o;
-#pragma unroll
-    for (int k = 0; k < NV; ++k) o.u[k] = ue[k * NP + rnode];
-    o.rho = q[node];
-#pragma unroll
-    for (int c = 0; c < DIM; ++c) o.v[c] = q[(1 + c) * NP + node];
-    o.pp = q[(1 + DIM) * NP + node];
-    o.p = o.pp + kc.pref;
-    o.c = NSP == 1 ? RealOps<real>::sqrt_(kc.gamma * o.p * RealOps<real>::rcp(o.rho))
-                   : spc[e * L::SPC + NP + node];
-    real nface[DIM];
-#pragma unroll
-    for (int c = 0; c < DIM; ++c) nface[c] = ja[c * NP + node];
-    const int nb = a.nbr[eg * 2 * DIM + f];
-    NodeState<real, DIM, NSP> x;
-    bool ok = true;
-    real Fs[NV];
-    int phys = outer_state<DIM, NSP>(a, kc, nb, nbu, nbpc, nbe, o, nface, x, ok);
-    if (!ok) latch_status(a.status, DG_ST_NONPHYS, nb >= 0 ? nb : eg);
-    if (phys) phys_flux<real, DIM, NSP>(x, nface, Fs);
-    else if (FL) llf_oriented<real, DIM, NSP>(o, x, side != 0, nface, Fs);  // the production pair: LLF
-    else if (side) surface_flux<real, DIM, NSP>(sf, o, x, nface, kc.inv_gm1, kc.pref, Fs);
-    else surface_flux<real, DIM, NSP>(sf, x, o, nface, kc.inv_gm1, kc.pref, Fs);
-#pragma unroll
-    for (int k = 0; k < NV; ++k) sa[k * NP] += iw * Fs[k];
-    const int bkind = nb >= 0 ? 0 : a.bc_kind[-(nb + 1)];
-    if (NS && bkind != DG_BC_OUTFLOW) {
-      // viscous interface flux: mean of both sides' f^v . n, lifted as (Fv* - Fv).  At a
-      // boundary the other side follows from the own flux (the flux is linear in the
-      // interior gradient): m = sigma . n, h = q . n = Fv_E - m . v; inflow: the external
-      // state's velocity and mu(T) (mean as at an interface); no-slip walls: Fv* = (m, h)
-      // at zero velocity, h = 0 on an adiabatic wall (Fv* itself, not a mean)
-      const bool wall = bkind == DG_BC_NOSLIP_ADIABATIC || bkind == DG_BC_ISOTHERMAL;
-      const real* fvd = sfv + e * L::SFV + d * (DIM + 1) * NP + node;
-      real fx[DIM + 1];
-      if (nb >= 0) {
-#pragma unroll
-        for (int c = 0; c <= DIM; ++c) fx[c] = nbg[c];
-      } else {
-        real h = fvd[DIM * NP];
-#pragma unroll
-        for (int c = 0; c < DIM; ++c) {
-          fx[c] = fvd[c * NP];
-          h -= fx[c] * o.v[c];
-        }
-        if (wall) {
-          fx[DIM] = bkind == DG_BC_ISOTHERMAL ? h : real(0);
-        } else {  // inflow
-          real r = 1;
-          if (!FL && kc.suth_s > real(0))
-            r = sutherland_ratio(x.p * RealOps<real>::rcp(x.rho), kc.suth_s, kc.suth_c1, kc.suth_irt) *
-                RealOps<real>::rcp(sutherland_ratio(o.p * RealOps<real>::rcp(o.rho), kc.suth_s, kc.suth_c1,
-                                                    kc.suth_irt));
-          real w = 0;
-#pragma unroll
-          for (int c = 0; c < DIM; ++c) {
-            fx[c] *= r;
-            w += fx[c] * x.v[c];
-          }
-          fx[DIM] = w + r * h;
-        }
-      }
-#pragma unroll
-      for (int c = 0; c <= DIM; ++c)
-        sa[(NSP + c) * NP] -= iw * (wall ? fx[c] - fvd[c * NP] : real(0.5) * (fx[c] - fvd[c * NP]));
     }
   }
   __syncthreads();

@@ -22,7 +22,8 @@ struct DgThermo {
   void* chem_mlp;                 // chemistry-source surrogate (device) or null
   unsigned long long* chem_stats; // [accepted, fallback] node counts of the source surrogate
   unsigned char* chem_flags;      // per 32-node tile: 0 accepted, otherwise recomputed plainly
-  unsigned long long chem_calls;  // source evaluations so far (moves each tile's sampled node)
+  unsigned long long chem_calls;  // learned-source evaluations so far (moves each tile's sampled node)
+  int src_valid;                  // src holds an evaluation
 };
 
 cudaError_t dg_thermo_upload_basis();

@@ -1,7 +1,9 @@
-"""The learned chemistry source on the GPU: ten-output training / forward kernels against
-the FP64 oracle; the learned source against the oracle's evaluation of the same network
-(decode, projection, point-implicit terms); rejected tiles reproduce the plain FP64
-source bit for bit; and a network trained on data of the plain reacting run."""
+"""The learned chemistry source on the GPU against the oracle's reading of its acceptance
+rule (R18s): the ten-output training and forward kernels; the decoded, projected learned
+source element by element within the rounding bound of the BF16 network; the per-tile
+decisions (trust box, mass balance, sampled check) wherever they are not within that
+bound of their thresholds; rejected tiles bit for bit the plain source; and a network
+trained on the plain run, stepped against the oracle's plain FP64 run."""
 import numpy as np
 import pytest
 
@@ -34,42 +36,71 @@ def test_ten_output_gradient_and_forward_match_oracle(env):
     ws = torch.empty(dg.dg_mlp_workspace_bytes(300, 10) // 4 + 1, dtype=torch.float32, device="cuda")
     dg.dg_mlp_grad(P, Xd, td, grad, loss, ws)
     y32 = torch.empty((300, 10), dtype=torch.float32, device="cuda")
-    ytc = torch.empty_like(y32)
     dg.dg_mlp_forward(P, Xd, y32, tensor_cores=0)
-    dg.dg_mlp_forward(P, Xd, ytc, tensor_cores=1)
     torch.cuda.synchronize()
     g = grad.cpu().numpy().astype(np.float64)
     assert np.linalg.norm(g - g_o) / np.linalg.norm(g_o) < 1e-5
     assert abs(loss.item() / loss_o - 1) < 1e-5
-    y_o = oracle.mlp_forward(p.astype(np.float64), X.astype(np.float64), 10)
+    y_o, sd = oracle.mlp_forward_sd(p.astype(np.float64), X.astype(np.float64), 10)
     assert np.linalg.norm(y32.cpu().numpy() - y_o) / np.linalg.norm(y_o) < 1e-5
-    # BF16 operands, FP32 accumulation
-    assert np.linalg.norm(ytc.cpu().numpy() - y_o) / np.linalg.norm(y_o) < 3e-2
+    # BF16 operands, FP32 accumulation: both tensor-core paths within 8 standard deviations
+    # of the rounding model, element by element
+    for tc in (1, 2):
+        ytc = torch.empty_like(y32)
+        dg.dg_mlp_forward(P, Xd, ytc, tensor_cores=tc)
+        torch.cuda.synchronize()
+        r = np.abs(ytc.cpu().numpy() - y_o) / sd
+        assert r.max() <= 8.0, (tc, r.max())
 
 
-def _reacting(dg, precision=0, N=3):
+# the reacting O-grid as a long run needs it: the positivity limiter (partial densities
+# >= 1e-9, T >= 200 K) and subcell blending (alpha <= 0.5) on both sides
+LIMITED = dict(positivity_eps=1e-9, alpha_max=0.5)
+
+
+def _reacting(dg, precision=0, N=3, limited=False):
     import workloads as W
     x, _ = dg.dg_lgl_nodes(N)
     xyz, nbr, face, w = cases.mixture_ogrid(x, hot=(1.2, 2500.0))
     kinds, bcp = cases.mixture_bc(w)
     s = dg.Solver(3, N, xyz, nbr, face, n_species=5, species=W.species_table(), volume_flux=1,
                   surface_flux=0, bc_kind=kinds, bc_prim=bcp, precision=precision,
-                  reactions=W.reaction_table())
+                  reactions=W.reaction_table(), **(LIMITED if limited else {}))
     s.set_primitive(w)
     s.w0 = w
     return s
 
 
-def _rhs(dg, torch, s):
-    """Right-hand side of the initial state.  Setting the state again re-seeds the
-    temperature cache, so repeated evaluations start the Newton solve identically."""
+def _reacting_oracle(oracle, N=3, limited=False):
+    import workloads as W
+    xo, _ = oracle.lgl(N)
+    xyz, nbr, face, w = cases.mixture_ogrid(xo, hot=(1.2, 2500.0))
+    kinds, bcp = cases.mixture_bc(w)
+    o = oracle.Oracle(3, N, xyz, nbr, face, n_species=5, species=W.species_table(), volume_flux=1,
+                      bc_kind=kinds, bc_prim=bcp, reactions=W.reaction_table(),
+                      **(LIMITED if limited else {}))
+    u = o.prim_to_cons(w)
+    return o, u
+
+
+def _nodes(o, u):
+    """Species densities [K np][5] and the oracle's temperatures [K np] (element-major)."""
+    rhos = u[:, :5, :].transpose(0, 2, 1).reshape(-1, 5)
+    return rhos, o.temperature(u).reshape(-1)
+
+
+def _eval_source(dg, s):
+    """Evaluate the source at the initial state through dg_rhs; returns (S [n][5], flags,
+    call)."""
+    import torch
     s.set_primitive(s.w0)
     u = torch.empty(s.shape, dtype=torch.float64, device="cuda")
     dg.dg_get_state(s.ctx, u)
     r = torch.empty_like(u)
     dg.dg_rhs(s.ctx, u, r)
     dg.dg_sync(s.ctx)
-    return u.cpu().numpy(), r.cpu().numpy()
+    S, flags, call = dg.dg_get_source(s.ctx, s.shape)
+    return S.transpose(0, 2, 1).reshape(-1, 5), flags, call
 
 
 def _stats(w_ref=1e2, j_ref=1e3, lo=-1e30, hi=1e30, tol_check=1e30, tol_mass=1e30, floor=0.0):
@@ -84,62 +115,63 @@ def _stats(w_ref=1e2, j_ref=1e3, lo=-1e30, hi=1e30, tol_check=1e30, tol_mass=1e3
     return st
 
 
-def _plain_source(oracle, u, T, dt=0.0):
-    import workloads as W
-    rhos = u[:, :5, :].transpose(0, 2, 1).reshape(-1, 5)
-    _, _, S = oracle.chem_eval(W.species_table(), W.reaction_table(), rhos, T.reshape(-1), dt)
-    return rhos, S
-
-
 def test_rejected_tiles_reproduce_the_plain_source_bitwise(env):
     dg, oracle, torch = env
     s = _reacting(dg)
     try:
-        _, r_plain = _rhs(dg, torch, s)
+        S_plain, flags, _ = _eval_source(dg, s)
+        assert (flags == 255).all()
         n = s.K * s.np
         p = (0.3 * np.random.default_rng(3).normal(size=dg.dg_mlp_nparams(10))).astype(np.float32)
         # an empty trust box rejects every tile
         dg.dg_set_surrogate(s.ctx, p, _stats(lo=1e30, hi=-1e30), which=dg.DG_SURROGATE_SOURCE)
-        _, r_box = _rhs(dg, torch, s)
+        S_box, flags, _ = _eval_source(dg, s)
         acc, fb = dg.dg_surrogate_stats(s.ctx, dg.DG_SURROGATE_SOURCE)
         assert (acc, fb) == (0, n)
-        assert np.array_equal(r_box, r_plain)
+        assert (flags == 1).all()
+        assert np.array_equal(S_box, S_plain)
         # a zero tolerance at the sampled node rejects every tile whose sample is off
         dg.dg_set_surrogate(s.ctx, p, _stats(tol_check=0.0), which=dg.DG_SURROGATE_SOURCE)
-        _, r_chk = _rhs(dg, torch, s)
+        S_chk, flags, _ = _eval_source(dg, s)
         acc, fb = dg.dg_surrogate_stats(s.ctx, dg.DG_SURROGATE_SOURCE)
         assert (acc, fb) == (0, n)
-        assert np.array_equal(r_chk, r_plain)
+        assert (flags == 2).all()
+        assert np.array_equal(S_chk, S_plain)
         # switched off again: plain
         dg.dg_set_surrogate(s.ctx, None, which=dg.DG_SURROGATE_SOURCE)
-        _, r_off = _rhs(dg, torch, s)
-        assert np.array_equal(r_off, r_plain)
+        S_off, _, _ = _eval_source(dg, s)
+        assert np.array_equal(S_off, S_plain)
     finally:
         s.close()
 
 
-def test_accepted_source_matches_the_oracle_surrogate(env):
-    """Everything accepted: the species rows of the right-hand side move by exactly
-    S_learned - S_plain; S_learned against the oracle's FP64 evaluation of the same
-    network (BF16 hidden layers on the GPU), compared in the asinh image."""
+def test_accepted_source_matches_the_oracle_elementwise(env):
+    """Everything accepted (tolerances open): the GPU's learned source against the
+    oracle's FP64 evaluation of the same network, decode, projection, element by element
+    within the BF16 rounding bound; the plain source against the oracle's plain source."""
     dg, oracle, torch = env
     s = _reacting(dg)
+    o, u_o = _reacting_oracle(oracle)
     try:
-        u, r_plain = _rhs(dg, torch, s)
-        T = dg.dg_get_temperature(s.ctx, (s.K, s.np))
+        import workloads as W
+        rhos, T = _nodes(o, u_o)
+        S_plain_gpu, _, _ = _eval_source(dg, s)
+        _, _, S_plain_o = oracle.chem_eval(W.species_table(), W.reaction_table(), rhos, T, 0.0)
+        scale = np.abs(S_plain_o).sum(axis=1, keepdims=True) + 1e-300
+        assert (np.abs(S_plain_gpu - S_plain_o) / scale).max() < 1e-11
         p = (0.1 * np.random.default_rng(4).normal(size=dg.dg_mlp_nparams(10))).astype(np.float32)
         st = _stats()
         dg.dg_set_surrogate(s.ctx, p, st, which=dg.DG_SURROGATE_SOURCE)
-        _, r_mlp = _rhs(dg, torch, s)
+        S_gpu, flags, _ = _eval_source(dg, s)
         acc, fb = dg.dg_surrogate_stats(s.ctx, dg.DG_SURROGATE_SOURCE)
-        assert (acc, fb) == (s.K * s.np, 0)
-        rhos, S_plain = _plain_source(oracle, u, T)
-        dS = (r_mlp - r_plain)[:, :5, :].transpose(0, 2, 1).reshape(-1, 5)
-        S_gpu = S_plain + dS
-        S_o, ok_o, _, _ = oracle.chem_surrogate_source(p.astype(np.float64), st, rhos, T.reshape(-1))
-        assert ok_o.all()
-        err = np.abs(np.arcsinh(S_gpu / st[34]) - np.arcsinh(S_o / st[34]))
-        assert err.max() < 0.05, err.max()
+        assert (acc, fb) == (s.K * s.np, 0) and (flags == 0).all()
+        r = oracle.chem_surrogate_source(p.astype(np.float64), st, rhos, T)
+        assert (r["inside"] & r["mass_ok"]).all()
+        ratio = np.abs(S_gpu - r["S_learned"]) / r["bound"]
+        assert ratio.max() <= 1.0, ratio.max()
+        # the bound is a rounding bound, not a loose tolerance: the learned values differ
+        # from the plain ones by far more than it
+        assert np.median(r["bound"] / (np.abs(r["S_learned"] - S_plain_o) + 1e-300)) < 0.1
         # projected rates conserve mass
         assert np.abs(S_gpu.sum(1)).max() <= 1e-5 * np.abs(S_gpu).sum(1).max()
     finally:
@@ -148,69 +180,113 @@ def test_accepted_source_matches_the_oracle_surrogate(env):
 
 @pytest.fixture(scope="module")
 def trained_source(env):
-    """Plain reacting run on the O-grid (FP64), 24 states x 2000 samples, short training."""
+    """The limited plain reacting run on the O-grid (FP64): 50 states 10 steps apart x 1000
+    samples, training by libdg's kernels."""
     dg, oracle, torch = env
     from paper_2511_17551_gb300 import surrogate as S
-    s = _reacting(dg)
+    s = _reacting(dg, limited=True)
     try:
-        import workloads as W
-        xo, _ = oracle.lgl(3)
-        xyz_o, nbr, face, w_o = cases.mixture_ogrid(xo, hot=(1.2, 2500.0))
-        kinds, bcp = cases.mixture_bc(w_o)
-        o = oracle.Oracle(3, 3, xyz_o, nbr, face, n_species=5, species=W.species_table(), volume_flux=1,
-                          bc_kind=kinds, bc_prim=bcp, reactions=W.reaction_table())
-        dt = 0.1 * o.max_dt(o.prim_to_cons(w_o), 0.5)
-        X, Y = S.collect_source(s.ctx, 48000, 24, 1, dt_fixed=dt)
+        o, u_o = _reacting_oracle(oracle)
+        dt = 0.1 * o.max_dt(u_o, 0.5)
+        X, Y = S.collect_source(s.ctx, 50000, 50, 10, dt_fixed=dt)
         params, stats, hist = S.train_source(X, Y, epochs=150, batch=2048, lr=3e-3)
         return params, stats, hist, dt
     finally:
         s.close()
 
 
-def test_trained_source_surrogate(env, trained_source):
-    """A network trained on the plain run: training converges, most tiles are accepted on
-    the initial state, and the accepted source is within the acceptance tolerance of the
-    oracle's plain source at 95 % of the nodes."""
+def test_tile_decisions_and_values_match_oracle(env, trained_source):
+    """Real tolerances (trained network), decisions in the kernel's precision (the oracle
+    evaluates the network with the GPU's BF16 roundings): on every tile that no decision
+    puts within the remaining difference bound of a threshold, the GPU's decision equals
+    the oracle's; accepted tiles carry the oracle's learned values within that bound and
+    within the BF16 rounding bound of the exact network; rejected tiles the plain values."""
     dg, oracle, torch = env
+    import workloads as W
     params, stats, hist, dt = trained_source
     assert hist[-1][2] < 0.2 * hist[0][2]
     s = _reacting(dg)
+    o, u_o = _reacting_oracle(oracle)
     try:
-        u, _ = _rhs(dg, torch, s)
-        T = dg.dg_get_temperature(s.ctx, (s.K, s.np))
+        rhos, T = _nodes(o, u_o)
         dg.dg_set_surrogate(s.ctx, params, stats, which=dg.DG_SURROGATE_SOURCE)
-        _, r_mlp = _rhs(dg, torch, s)
-        acc, fb = dg.dg_surrogate_stats(s.ctx, dg.DG_SURROGATE_SOURCE)
-        assert acc + fb == s.K * s.np
-        assert acc > 0
-        dg.dg_set_surrogate(s.ctx, None, which=dg.DG_SURROGATE_SOURCE)
-        _, r_plain = _rhs(dg, torch, s)
-        rhos, S_plain = _plain_source(oracle, u, T)
-        dS = (r_mlp - r_plain)[:, :5, :].transpose(0, 2, 1).reshape(-1, 5)
-        bound = stats[50] * np.abs(S_plain).sum(1) + stats[52]
-        frac_within = np.mean(np.all(np.abs(dS) <= 2.0 * bound[:, None], axis=1))
-        assert frac_within > 0.95, (frac_within, acc, fb)
-        # RK steps with the learned source stay close to the plain FP64 run
+        n = len(T)
+        seen = np.zeros(3, dtype=np.int64)
+        for _ in range(3):  # three evaluations: three draws of the sampled nodes
+            S_gpu, flags, call = _eval_source(dg, s)
+            kw = dict(species=W.species_table(), reactions=W.reaction_table(), call=call)
+            r = oracle.chem_surrogate_source(params.astype(np.float64), stats, rhos, T, network="bf16", **kw)
+            clear = ~r["tile_ambiguous"]
+            assert np.array_equal(flags[clear], r["tile_flag"][clear].astype(np.uint8)), \
+                (flags[clear], r["tile_flag"][clear])
+            # near a threshold either decision is correct; the GPU and the oracle still agree
+            # on nearly every tile (a stated empirical bar)
+            agree = np.mean(flags == r["tile_flag"].astype(np.uint8))
+            assert agree >= 0.9, agree
+            seen += np.bincount(flags.astype(np.int64), minlength=3)[:3]
+            acc_node = np.repeat(flags == 0, 32)[:n]
+            ratio = np.abs(S_gpu[acc_node] - r["S_learned"][acc_node]) / r["bound"][acc_node]
+            assert ratio.size == 0 or ratio.max() <= 1.0, ratio.max()
+            r64 = oracle.chem_surrogate_source(params.astype(np.float64), stats, rhos, T)
+            ratio = np.abs(S_gpu[acc_node] - r64["S_learned"][acc_node]) / r64["bound"][acc_node]
+            assert ratio.size == 0 or ratio.max() <= 1.0, ratio.max()
+            scale = np.abs(r["S_plain"]).sum(axis=1, keepdims=True) + 1e-300
+            rel = np.abs(S_gpu[~acc_node] - r["S_plain"][~acc_node]) / scale[~acc_node]
+            assert rel.size == 0 or rel.max() < 1e-11, rel.max()
+        print("tile decisions over three evaluations (accepted, box/mass, sampled):", seen)
+        assert seen[0] > 0
+    finally:
+        s.close()
+
+
+# state error of the learned-source run against the oracle's plain FP64 run (stated bar,
+# per conserved field, relative L2 of R19) after LEARNED_STEPS CK45 steps at the fixed step,
+# with the acceptance tolerances tau_c = tau_m = LEARNED_TOL (the network trained on this
+# small case is coarse: at 0.05 the learned run leaves the admissible states within 60
+# steps, at 0.02 it ends 500 steps within 3e-3)
+LEARNED_STEPS = 500
+LEARNED_TOL = 0.005
+LEARNED_L2_BAR = 1e-3
+
+
+def test_learned_source_run_against_oracle(env, trained_source):
+    """The FP64 form with the learned source, LEARNED_STEPS CK45 steps, positivity limiter
+    and blending on, the oracle's plain FP64 run beside it: every conserved field within
+    LEARNED_L2_BAR.  The plain FP64 GPU run stays within 1e-6 of the oracle: over 500 steps
+    the limiter's per-element decisions and the 200 K floor of the temperature solve,
+    which both sides take in FP64 at rounding-level different states, amplify rounding
+    (5e-8 measured; single right-hand sides and short runs agree to 1e-11)."""
+    dg, oracle, torch = env
+    params, stats, hist, dt = trained_source
+    s = _reacting(dg, limited=True)
+    o, u_o = _reacting_oracle(oracle, limited=True)
+    try:
+        u_ref, _ = o.step_rk(u_o, LEARNED_STEPS, dt_fixed=dt)
         s.set_primitive(s.w0)
-        dg.dg_set_surrogate(s.ctx, params, stats, which=dg.DG_SURROGATE_SOURCE)
-        s.step(3, dt_fixed=dt)
+        s.step(LEARNED_STEPS, dt_fixed=dt)
+        u_plain, _ = s.get_state()
+        st = stats.copy()
+        st[50] = st[51] = LEARNED_TOL
+        dg.dg_set_surrogate(s.ctx, params, st, which=dg.DG_SURROGATE_SOURCE)
+        dg.dg_surrogate_stats(s.ctx, dg.DG_SURROGATE_SOURCE)
+        s.set_primitive(s.w0)
+        s.step(LEARNED_STEPS, dt_fixed=dt)
         u_l, _ = s.get_state()
-        dg.dg_set_surrogate(s.ctx, None, which=dg.DG_SURROGATE_SOURCE)
-        s.set_primitive(s.w0)
-        s.step(3, dt_fixed=dt)
-        u_p, _ = s.get_state()
-        # the species increments of the learned run against those of the plain run: the
-        # accepted sources carry up to tol_check of the local rates (plus the floor), so
-        # the increments differ by a fraction of that order
-        u0 = np.zeros_like(u_p)
-        s.set_primitive(s.w0)
-        u0, _ = s.get_state()
-        inc = np.linalg.norm((u_p - u0)[:, :5, :].transpose(1, 0, 2).reshape(5, -1), axis=1)
-        dif = np.linalg.norm((u_l - u_p)[:, :5, :].transpose(1, 0, 2).reshape(5, -1), axis=1)
-        ratio = dif / inc
-        assert ratio.max() < 0.25, (ratio, acc, fb)
-        # momentum and energy are not touched by the source beyond the coupling
-        err = cases.field_errors(u_l, u_p, 5, 3)
-        assert err[5:].max() < 1e-3, err
+        acc, fb = dg.dg_surrogate_stats(s.ctx, dg.DG_SURROGATE_SOURCE)
+        e_plain = cases.field_errors(u_plain, u_ref, 5, 3)
+        e_l = cases.field_errors(u_l, u_ref, 5, 3)
+        moved = cases.field_errors(u_o, u_ref, 5, 3)  # how far the run moved each field
+        rec = {"steps": LEARNED_STEPS, "accepted_fraction": acc / max(1, acc + fb),
+               "l2_learned_vs_oracle": e_l.tolist(), "l2_plain_gpu_vs_oracle": e_plain.tolist(),
+               "l2_change_over_run": moved.tolist()}
+        print("learned-source run:", rec)
+        import json
+        import os
+        if os.environ.get("DG_GAIN_LOG"):
+            with open(os.environ["DG_GAIN_LOG"], "a") as f:
+                f.write(json.dumps({"learned_run": rec}) + "\n")
+        assert e_plain.max() < 1e-6, e_plain
+        assert acc > 0
+        assert e_l.max() < LEARNED_L2_BAR, e_l
     finally:
         s.close()
