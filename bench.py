@@ -46,9 +46,9 @@ WORDS_MAIN_EULER = 5 + 5 + 9 + 1 + 5 + 5
 WORDS_COMPENSATION = 10
 WORDS_GRAD = 5 + 9 + 1 + 12
 # dram__bytes_read.sum + dram__bytes_write.sum per node of one launch of the current
-# mixed-form NS N=3 rhs_kernel on the full 32^3 workload (one ncu capture, one pass), or
-# None while no capture of the current kernel exists
-RHS_DRAM_B_PER_NODE = None
+# mixed-form NS N=3 rhs_kernel on the full 32^3 workload (one ncu capture, one pass:
+# 271,964,672 B read + 95,295,488 B written over 2,097,152 nodes)
+RHS_DRAM_B_PER_NODE = 175.12
 # FP64 flops per node of the FP64-form NS N=3 rhs_kernel (2 DFMA + DMUL + DADD thread
 # instructions, one ncu capture of the 16^3 case): its roofline is the FP64 pipe
 RHS_FP64_FLOPS_PER_NODE = 1005.3
@@ -273,7 +273,8 @@ def run_ours(args, rank, world, local_rank):
         out.update(run_other_shapes(args, stream.cuda_stream, world))
     if rank == 0:
         if not args.no_cpu_baseline:
-            out["cpu_baseline"], r_oracle, u_oracle, n_or, dt_or, floor = cpu_baseline(cfg, args.cpu_seconds)
+            out["cpu_baseline"], r_oracle, u_oracle, n_or, dt_or, floors = cpu_baseline(cfg, args.cpu_seconds)
+            floor, floor32, u_init_or = floors
             # both GPU forms against what the baseline leg computed: the state after the
             # same CK45 steps, and the right-hand side of the initial state
             par = {"norm": "relative L2 per conserved field (rho, rho v x3, rho E); momentum "
@@ -284,7 +285,10 @@ def run_ours(args, rank, world, local_rank):
                            "discretisation-error-sized norm; at Mach 0.1 the pressure p0 = 71 "
                            "cancels to gradients of order 0.1, so every right-hand-side "
                            "comparison sits on the rounding floor in rhs_oracle_ulp_floor",
-                   "rhs_oracle_ulp_floor": floor}
+                   "rhs_oracle_ulp_floor": floor, "rhs_oracle_fp32_ulp_floor": floor32,
+                   "increment_note": "relative L2 per field of the increment u_n - u_0 over the steps "
+                                     "against the oracle's increment (the state error divides by the "
+                                     "state's norm, the increment error by the change's)"}
             for name, prec in (("fp64", dg.DG_FP64), ("mixed", dg.DG_MIXED)):
                 sp = make(prec)
                 ud = torch.empty(sp.shape, dtype=torch.float64, device="cuda")
@@ -294,8 +298,11 @@ def run_ours(args, rank, world, local_rank):
                 dg.dg_rhs(sp.ctx, ud, rd)
                 dg.dg_sync(sp.ctx)
                 par["rhs_" + name] = field_errors(rd.double().cpu().numpy(), r_oracle)
+                u0_g = sp.get_state()[0]
                 sp.step(n_or, dt_fixed=dt_or)
-                par["state_after_steps_" + name] = field_errors(sp.get_state()[0], u_oracle)
+                un_g = sp.get_state()[0]
+                par["state_after_steps_" + name] = field_errors(un_g, u_oracle)
+                par["increment_after_steps_" + name] = field_errors(un_g - u0_g, u_oracle - u_init_or)
                 sp.close()
             out["parity_vs_oracle"] = par
             if not args.no_mixture:
@@ -715,6 +722,10 @@ def cpu_baseline(cfg, budget_s):
     # value moves by one unit in the last place (seeded signs), before the timed steps
     sgn = np.random.default_rng(5).choice([-1.0, 1.0], size=u.shape)
     floor = field_errors(o.rhs(u * (1.0 + np.finfo(np.float64).eps * sgn)), r0)
+    # and to one FP32 unit of every state value: the floor of any right-hand side that is
+    # computed from an FP32 state
+    floor32 = field_errors(o.rhs(u * (1.0 + 2.0 ** -24 * sgn)), r0)
+    u_init = u.copy()
     dt_step = o.max_dt(u, 0.5)
     dof = u.size
     n, t0 = 0, time.perf_counter()
@@ -741,7 +752,7 @@ def cpu_baseline(cfg, budget_s):
     oracle.set_threads(cores)
     info["single_thread"] = {"value": dof * n1 / w1, "unit": "DOF*RHS/s", "cores": 1,
                              "sample": "%d right-hand sides of the full workload in %.1f s" % (n1, w1)}
-    return info, r0, u, n, dt_step, floor
+    return info, r0, u, n, dt_step, (floor, floor32, u_init)
 
 
 def _cpu_model():

@@ -288,6 +288,32 @@ dg_status dg_mlp_train_step(float* params, int n_out, float* m, float* v, const 
 dg_status dg_mlp_forward(const float* params, int n_out, const float* X, float* y, int64_t n,
                          int tensor_cores, void* stream);
 
+/* Data preparation of the learned surrogates (no counterpart in the paper; the steps
+ * that turn the plain solver's samples into training arrays), on the device, with
+ * fixed-order reductions (deterministic).  Sample arrays are row-major [n][d] device arrays
+ * of FP32 (is_f64 = 0) or FP64 values; `ref` (host, [d] positive, or NULL) maps each value
+ * v of column c to asinh(v / ref[c]) first.  Each call synchronises `stream`.
+ *
+ * dg_column_stats: out (host, [4][d]) = per column mean, standard deviation (divisor
+ *   n - 1), min and max of the (mapped) values; n >= 2, d <= 64. */
+dg_status dg_column_stats(const void* X, int is_f64, int64_t n, int d, const double* ref, double* out,
+                          void* stream);
+/* dg_standardize: out[i][c] = (mapped X[i][c] - mean[c]) / std[c] as FP32 (device [n][d]);
+ *   mean, std host [d], std > 0. */
+dg_status dg_standardize(const void* X, int is_f64, int64_t n, int d, const double* ref, const double* mean,
+                         const double* std_dev, float* out, void* stream);
+/* dg_abs_quantile: the q-quantile (0 <= q <= 1) of |Y[i][c]| over all rows and the columns
+ *   c0 .. c0 + nc - 1 of an FP64 device array Y [n][d]: the order statistics around
+ *   position q (m - 1), m = n nc, found exactly by bisection on their bit patterns, and
+ *   linear interpolation between them; *out on the host. */
+dg_status dg_abs_quantile(const double* Y, int64_t n, int d, int c0, int nc, double q, double* out, void* stream);
+/* dg_gather_rows: out[r][:] = X[idx[r]][:] for r < m (device arrays; idx int64 in range). */
+dg_status dg_gather_rows(const float* X, int d, const int64_t* idx, int64_t m, float* out, void* stream);
+/* dg_mlp_loss: *loss (host) = mean over the n samples and n_out outputs of
+ *   (network(X) - t)^2 with the FP32 forward (params, X [n][7], t [n][n_out] device). */
+dg_status dg_mlp_loss(const float* params, int n_out, const float* X, const float* t, int64_t n, double* loss,
+                      void* stream);
+
 /* Blending factors alpha [K] used by the last right-hand side (FP64, host). */
 dg_status dg_get_alpha(dg_ctx* ctx, double* alpha);
 

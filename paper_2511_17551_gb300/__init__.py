@@ -36,7 +36,8 @@ EXPORTED = [
     "dg_rhs_ns_noalloc", "dg_get_temperature", "dg_set_surrogate", "dg_surrogate_stats",
     "dg_thermo_sample", "dg_mlp_nparams", "dg_mlp_workspace_bytes", "dg_mlp_grad",
     "dg_mlp_train_step", "dg_mlp_forward", "dg_peak_flops", "dg_chem_sample", "dg_limiter_stats", "dg_limit_state",
-    "dg_noalloc_status", "dg_get_metrics", "dg_get_source",
+    "dg_noalloc_status", "dg_get_metrics", "dg_get_source", "dg_column_stats", "dg_standardize",
+    "dg_abs_quantile", "dg_gather_rows", "dg_mlp_loss",
 ]
 PROF_KINDS = ["rhs", "gradients", "indicator", "lambda", "thermo", "mlp", "chem", "other", "limiter"]
 
@@ -89,6 +90,11 @@ def lib():
             "dg_get_gradients": (i, [vp, vp]),
             "dg_get_metrics": (i, [vp, vp, vp, i]),
             "dg_get_source": (i, [vp, vp, vp, vp]),
+            "dg_column_stats": (i, [vp, i, i64, i, vp, vp, vp]),
+            "dg_standardize": (i, [vp, i, i64, i, vp, vp, vp, vp, vp]),
+            "dg_abs_quantile": (i, [vp, i64, i, i, i, d, vp, vp]),
+            "dg_gather_rows": (i, [vp, i, vp, i64, vp, vp]),
+            "dg_mlp_loss": (i, [vp, i, vp, vp, i64, vp, vp]),
             "dg_noalloc_status": (i, [vp, vp]),
             "dg_sync": (i, [vp]),
             "dg_error_element": (i64, [vp]),
@@ -293,6 +299,51 @@ def dg_get_source(ctx, shape):
     call = C.c_int64(-1)
     _check(lib().dg_get_source(ctx, _ptr(S), _ptr(flags), C.byref(call)), "dg_get_source")
     return S, flags, call.value
+
+
+def _dev_f64(a):
+    return None if a is None else np.ascontiguousarray(a, dtype=np.float64)
+
+
+def dg_column_stats(X, ref=None, stream=None):
+    """Per-column (mean, std, min, max) of a device array X [n][d] (FP32 or FP64), of
+    asinh(X / ref) when ref [d] is given; four float64 arrays."""
+    n, d = X.shape
+    out = np.zeros(4 * d)
+    r = _dev_f64(ref)
+    _check(lib().dg_column_stats(_ptr(X), int(X.element_size() == 8), n, d, _ptr(r), _ptr(out), stream),
+           "dg_column_stats")
+    return out[:d], out[d:2 * d], out[2 * d:3 * d], out[3 * d:]
+
+
+def dg_standardize(X, mean, std, out, ref=None, stream=None):
+    """out [n][d] FP32 = ((asinh(X / ref) or X) - mean) / std, on the device."""
+    n, d = X.shape
+    m, s, r = _dev_f64(mean), _dev_f64(std), _dev_f64(ref)
+    _check(lib().dg_standardize(_ptr(X), int(X.element_size() == 8), n, d, _ptr(r), _ptr(m), _ptr(s), _ptr(out),
+                                stream), "dg_standardize")
+
+
+def dg_abs_quantile(Y, c0, nc, q, stream=None):
+    """q-quantile of |Y[:, c0:c0+nc]| (FP64 device array), linear interpolation."""
+    n, d = Y.shape
+    out = C.c_double(0.0)
+    _check(lib().dg_abs_quantile(_ptr(Y), n, d, c0, nc, float(q), C.byref(out), stream), "dg_abs_quantile")
+    return out.value
+
+
+def dg_gather_rows(X, idx, out, stream=None):
+    """out[r] = X[idx[r]] (FP32 rows, int64 indices; device arrays)."""
+    _check(lib().dg_gather_rows(_ptr(X), X.shape[1], _ptr(idx), idx.shape[0], _ptr(out), stream), "dg_gather_rows")
+
+
+def dg_mlp_loss(params, X, t, stream=None):
+    """Mean squared error of the FP32 network on (X, t) (device arrays)."""
+    loss = C.c_double(0.0)
+    n_out = 1 if t.dim() == 1 else t.shape[1]
+    _check(lib().dg_mlp_loss(_ptr(params), n_out, _ptr(X), _ptr(t), X.shape[0], C.byref(loss), stream),
+           "dg_mlp_loss")
+    return loss.value
 
 
 def dg_sync(ctx):

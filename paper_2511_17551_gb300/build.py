@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libdg.so")
-SOURCES = ["dg_capi.cu", "dg_rhs_f64.cu", "dg_rhs_f32.cu", "dg_rhs_f64g.cu", "dg_rhs_f32g.cu", "dg_rhs_f32s.cu", "dg_thermo.cu", "dg_mlp.cu", "dg_noalloc.cu", "dg_chem.cu", "dg_peak.cu",
+SOURCES = ["dg_capi.cu", "dg_rhs_f64.cu", "dg_rhs_f32.cu", "dg_rhs_f64g.cu", "dg_rhs_f32g.cu", "dg_rhs_f32s.cu", "dg_thermo.cu", "dg_mlp.cu", "dg_noalloc.cu", "dg_chem.cu", "dg_peak.cu", "dg_data.cu",
            "dg_basis.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]

@@ -546,6 +546,12 @@ static dg_status forward_tc(const float* hp, const float* X, float* y, int64_t n
   return e == cudaSuccess ? DG_OK : DG_ECUDA;
 }
 
+// FP32 forward launch for the data-preparation module (dg_data.cu)
+cudaError_t dg_mlp_forward_f32_launch(const float* P, int no, const float* X, float* y, int64_t n, cudaStream_t s) {
+  mlp_forward_f32_kernel<<<grid_of(n, 128), 128, 0, s>>>(P, no, X, y, n);
+  return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------- C ABI (training)
 extern "C" {
 

@@ -3,17 +3,20 @@
 Data come from the plain solver itself: a mixture context is stepped with the plain
 computations and ``dg_thermo_sample`` / ``dg_chem_sample`` draw node states after every
 ``steps_between`` RK steps (raw features and the plain FP64 results).  The drivers
-standardise the data, initialise the network (Xavier-uniform from a seed) and run Adam
-epochs with ``dg_mlp_train_step``; forward, back-propagation, the gradient reduction and
-the update all run in libdg's kernels.  PyTorch only holds the device buffers and draws
-the epoch permutations.
+standardise the data (``dg_column_stats``, ``dg_standardize``, ``dg_abs_quantile``),
+initialise the network (Xavier-uniform from a seed) and run Adam epochs with
+``dg_mlp_train_step`` on minibatches gathered by ``dg_gather_rows``; statistics, the asinh
+target map, the trust box, forward, back-propagation, the gradient reduction, the update
+and the validation loss all run in libdg's kernels.  PyTorch only holds the device
+buffers; numpy draws the seeded permutations.
 """
 import math
 
 import numpy as np
 
-from . import (DG_SRC_NSTATS, dg_chem_sample, dg_mlp_nparams, dg_mlp_train_step,
-               dg_mlp_workspace_bytes, dg_step_rk, dg_thermo_sample)
+from . import (DG_SRC_NSTATS, dg_abs_quantile, dg_chem_sample, dg_column_stats, dg_gather_rows,
+               dg_mlp_loss, dg_mlp_nparams, dg_mlp_train_step, dg_mlp_workspace_bytes,
+               dg_standardize, dg_step_rk, dg_thermo_sample)
 
 NI, NH = 7, 64
 
@@ -57,16 +60,25 @@ def xavier_params(seed=0, n_out=1):
     return p
 
 
+def _std(sd, floor):
+    return np.maximum(sd, floor)
+
+
 def standardise(X, T):
-    """Temperature surrogate statistics: mean/std of each feature and of T (float64 [16])."""
-    mx = X.double().mean(0)
-    sx = X.double().std(0).clamp_min(1e-12)
-    mt = T.double().mean()
-    st = T.double().std().clamp_min(1e-12)
-    stats = np.concatenate([mx.cpu().numpy(), sx.cpu().numpy(), [mt.item(), st.item()]])
-    Xn = ((X.double() - mx) / sx).float().contiguous()
-    Tn = ((T.double() - mt) / st).float().contiguous()
-    return Xn, Tn, stats
+    """Temperature surrogate statistics: mean/std of each feature and of T (float64 [16]),
+    and the standardised arrays (device FP32)."""
+    import torch
+    mx, sx, _, _ = dg_column_stats(X)
+    sx = _std(sx, 1e-12)
+    T2 = T.reshape(-1, 1)
+    mt, st_, _, _ = dg_column_stats(T2)
+    st_ = _std(st_, 1e-12)
+    stats = np.concatenate([mx, sx, mt, st_])
+    Xn = torch.empty(X.shape, dtype=torch.float32, device=X.device)
+    Tn = torch.empty(T2.shape, dtype=torch.float32, device=X.device)
+    dg_standardize(X, mx, sx, Xn)
+    dg_standardize(T2, mt, st_, Tn)
+    return Xn, Tn.reshape(-1), stats
 
 
 def fit(Xn, Yn, epochs=20, batch=4096, lr=1e-3, seed=0, val_frac=0.1, log=None):
@@ -74,31 +86,43 @@ def fit(Xn, Yn, epochs=20, batch=4096, lr=1e-3, seed=0, val_frac=0.1, log=None):
     Returns (params float32 [P] device, history of (epoch, train, val))."""
     import torch
     n_out = 1 if Yn.dim() == 1 else Yn.shape[1]
+    Y2 = Yn.reshape(-1, n_out)
     n = Xn.shape[0]
-    g = torch.Generator(device="cpu").manual_seed(seed)
-    perm = torch.randperm(n, generator=g).cuda()
+    rng = np.random.default_rng(seed)
+    dev = Xn.device
+    perm = torch.from_numpy(rng.permutation(n).astype(np.int64)).to(dev)
     nval = max(1, int(val_frac * n))
-    Xv, Yv = Xn[perm[:nval]], Yn[perm[:nval]]
-    Xt, Yt = Xn[perm[nval:]], Yn[perm[nval:]]
-    batch = min(batch, Xt.shape[0])
-    params = torch.from_numpy(xavier_params(seed, n_out)).cuda()
+    ntr = n - nval
+
+    def gather(A, idx):
+        out = torch.empty((idx.shape[0], A.shape[1]), dtype=torch.float32, device=dev)
+        dg_gather_rows(A, idx, out)
+        return out
+
+    Xv, Yv = gather(Xn, perm[:nval]), gather(Y2, perm[:nval])
+    Xt, Yt = gather(Xn, perm[nval:]), gather(Y2, perm[nval:])
+    batch = min(batch, ntr)
+    params = torch.from_numpy(xavier_params(seed, n_out)).to(dev)
     m = torch.zeros_like(params)
     v = torch.zeros_like(params)
-    ws = torch.empty(dg_mlp_workspace_bytes(batch, n_out) // 4 + 1, dtype=torch.float32, device="cuda")
-    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    ws = torch.empty(dg_mlp_workspace_bytes(batch, n_out) // 4 + 1, dtype=torch.float32, device=dev)
+    loss = torch.zeros(1, dtype=torch.float64, device=dev)
+    xb = torch.empty((batch, NI), dtype=torch.float32, device=dev)
+    tb = torch.empty((batch, n_out), dtype=torch.float32, device=dev)
     hist = []
     step = 0
     for ep in range(epochs):
-        order = torch.randperm(Xt.shape[0], generator=g).cuda()
+        order = torch.from_numpy(rng.permutation(ntr).astype(np.int64)).to(dev)
         tot, nb = 0.0, 0
-        for b0 in range(0, Xt.shape[0] - batch + 1, batch):
+        for b0 in range(0, ntr - batch + 1, batch):
             idx = order[b0:b0 + batch]
-            xb, tb = Xt[idx].contiguous(), Yt[idx].contiguous()
+            dg_gather_rows(Xt, idx, xb)
+            dg_gather_rows(Yt, idx, tb)
             step += 1
-            dg_mlp_train_step(params, m, v, xb, tb, step, lr, loss, ws)
+            dg_mlp_train_step(params, m, v, xb, tb if n_out > 1 else tb.reshape(-1), step, lr, loss, ws)
             tot += loss.item() if (nb % 50 == 0) else 0.0
             nb += 1
-        vloss = validation_loss(params, Xv, Yv)
+        vloss = validation_loss(params, Xv, Yv if n_out > 1 else Yv.reshape(-1))
         hist.append((ep, tot, vloss))
         if log:
             log("epoch %d  val mse %.3e" % (ep, vloss))
@@ -123,26 +147,24 @@ def source_stats(X, Y, ref_quantile=0.99, ref_fraction=1e-3, tol_check=0.05, tol
     floor_fraction omega_ref (the sampled-node check accepts |S_learned - S_plain| <=
     tol_check sum|S_plain| + floor)."""
     import torch
-    Xd, Yd = X.double(), Y.double()
-    w_ref = float(torch.quantile(Yd[:, :5].abs().flatten(), ref_quantile).item()) * ref_fraction
-    j_ref = float(torch.quantile(Yd[:, 5:].abs().flatten(), ref_quantile).item()) * ref_fraction
-    w_ref = max(w_ref, 1e-30)
-    j_ref = max(j_ref, 1e-30)
-    Z = torch.cat([torch.asinh(Yd[:, :5] / w_ref), torch.asinh(Yd[:, 5:] / j_ref)], dim=1)
-    mx, sx = Xd.mean(0), Xd.std(0).clamp_min(1e-12)
-    mz, sz = Z.mean(0), Z.std(0).clamp_min(1e-6)
+    w_ref = max(dg_abs_quantile(Y, 0, 5, ref_quantile) * ref_fraction, 1e-30)
+    j_ref = max(dg_abs_quantile(Y, 5, 5, ref_quantile) * ref_fraction, 1e-30)
+    ref = np.array([w_ref] * 5 + [j_ref] * 5)
+    mz, sz, _, _ = dg_column_stats(Y, ref=ref)
+    sz = _std(sz, 1e-6)
+    mx, sx, lo, hi = dg_column_stats(X)
+    sx = _std(sx, 1e-12)
     st = np.zeros(DG_SRC_NSTATS)
-    st[0:7] = mx.cpu().numpy()
-    st[7:14] = sx.cpu().numpy()
-    st[14:24] = mz.cpu().numpy()
-    st[24:34] = sz.cpu().numpy()
+    st[0:7], st[7:14] = mx, sx
+    st[14:24], st[24:34] = mz, sz
     st[34], st[35] = w_ref, j_ref
-    lo, hi = Xd.min(0).values, Xd.max(0).values
-    st[36:43] = (lo - box_margin * (hi - lo)).cpu().numpy()
-    st[43:50] = (hi + box_margin * (hi - lo)).cpu().numpy()
+    st[36:43] = lo - box_margin * (hi - lo)
+    st[43:50] = hi + box_margin * (hi - lo)
     st[50], st[51], st[52] = tol_check, tol_mass, floor_fraction * w_ref
-    Xn = ((Xd - mx) / sx).float().contiguous()
-    Zn = ((Z - mz) / sz).float().contiguous()
+    Xn = torch.empty(X.shape, dtype=torch.float32, device=X.device)
+    Zn = torch.empty(Y.shape, dtype=torch.float32, device=X.device)
+    dg_standardize(X, mx, sx, Xn)
+    dg_standardize(Y, mz, sz, Zn, ref=ref)
     return Xn, Zn, st
 
 
@@ -155,8 +177,4 @@ def train_source(X, Y, epochs=30, batch=4096, lr=2e-3, seed=0, val_frac=0.1, log
 
 
 def validation_loss(params, Xv, Yv):
-    import torch
-    from . import dg_mlp_forward
-    y = torch.empty_like(Yv)
-    dg_mlp_forward(params, Xv, y, tensor_cores=0)
-    return float(((y - Yv) ** 2).mean().item())
+    return dg_mlp_loss(params, Xv, Yv)

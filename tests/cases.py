@@ -126,3 +126,30 @@ def mixture_perturbed(w, seed):
     w[:, 5:8] += 100.0 * rng.normal(size=w[:, 5:8].shape)
     w[:, 8] *= 1 + 0.3 * rng.uniform(-1, 1, size=w[:, 8].shape)
     return w
+
+
+def rounding_floor(orc, u, eps=2.0 ** -24, seed=5):
+    """The oracle's own sensitivity of its right-hand side to a rounding of the state:
+    relative L2 per field (R19) of rhs(u (1 + eps s)) - rhs(u) with seeded signs s = +-1.
+    eps = 2^-24 is one FP32 unit in the last place, the rounding floor of any right-hand
+    side computed from an FP32 state; eps = 2^-53 the FP64 one."""
+    sgn = np.random.default_rng(seed).choice([-1.0, 1.0], size=u.shape)
+    r0 = orc.rhs(u)
+    return field_errors(orc.rhs(u * (1.0 + eps * sgn)), r0, orc.nv - orc.dim - 1, orc.dim)
+
+
+def step_floor(orc, u0, nsteps, dt, eps=2.0 ** -53, seed=5, nsp=None):
+    """The oracle's own sensitivity of nsteps CK45 steps (and whatever limiter or blending
+    the problem carries) to a rounding of the initial state: relative L2 per field of the
+    end states from u0 and from u0 (1 + eps s), s = +-1 seeded."""
+    sgn = np.random.default_rng(seed).choice([-1.0, 1.0], size=u0.shape)
+    a, _ = orc.step_rk(u0, nsteps, dt_fixed=dt)
+    b, _ = orc.step_rk(u0 * (1.0 + eps * sgn), nsteps, dt_fixed=dt)
+    nsp = orc.nv - orc.dim - 1 if nsp is None else nsp
+    return field_errors(b, a, nsp, orc.dim)
+
+
+def fp64_bar(floor):
+    """The FP64 parity bar of a case: 1e-12 relative L2, or 16 times the oracle's own one-ulp
+    floor of that case where rounding amplification puts the floor above 1e-12 / 16."""
+    return np.maximum(1e-12, 16.0 * np.asarray(floor))

@@ -99,6 +99,11 @@ RHS_CASES = {
 }
 
 
+# the mixed form's right-hand side against the oracle, per field, in units of the oracle's
+# FP32 rounding floor (cases.rounding_floor)
+MIXED_FLOOR_FACTOR = 16.0
+
+
 def _perturbed(case, mesh, seed):
     w = mesh[3]
     return cases.perturbed_state(w, seed=seed, amp=0.05)
@@ -125,10 +130,14 @@ def test_rhs_mixed(dg, name):
     try:
         w_o = _perturbed(c, p.mesh_o, 7)
         w_g = _perturbed(c, p.mesh_g, 7)
-        r_g, r_o, _ = _rhs_pair(dg, p, w_o, w_g)
+        r_g, r_o, u_o = _rhs_pair(dg, p, w_o, w_g)
         err = cases.field_errors(r_g, r_o, 1, c["dim"])
-        # FP32 rounding of the state (6e-8) amplified by the flux-difference cancellation
-        assert err.max() < 2e-4, err
+        # per field within MIXED_FLOOR_FACTOR times the oracle's own FP32 rounding floor
+        # (its right-hand side moved by one FP32 unit of every state value): the FP32 state
+        # alone puts the right-hand side that far off; the kernel's FP32 arithmetic adds
+        # roundings of the same size
+        floor = cases.rounding_floor(p.orc, u_o)
+        assert np.all(err <= MIXED_FLOOR_FACTOR * floor), (err, floor)
     finally:
         p.close()
 

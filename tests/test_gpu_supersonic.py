@@ -101,7 +101,7 @@ def test_viscous_time_step_and_integrals(dg):
         p.close()
 
 
-@pytest.mark.parametrize("precision,tol", [(0, 1e-11), (1, 1e-5)])
+@pytest.mark.parametrize("precision,tol", [(0, None), (1, 1e-5)])
 def test_rk_supersonic_tgv_with_limiter(dg, precision, tol):
     """Ten CK45 steps of the supersonic TGV on the warped box: Sutherland's law, pressure
     indicator blending and the positivity limiter (a bound above the initial minimum
@@ -117,6 +117,9 @@ def test_rk_supersonic_tgv_with_limiter(dg, precision, tol):
         assert dg.dg_limiter_stats(p.gpu.ctx) > 0
         u_r, _ = p.orc.step_rk(u_o, 10, dt_fixed=dt)
         err = cases.field_errors(u_g, u_r, 1, 3)
-        assert err.max() < tol, err
+        if tol is None:  # FP64: 1e-12 or the oracle's own one-ulp floor of these 10 steps
+            tol = cases.fp64_bar(cases.step_floor(p.orc, u_o, 10, dt))
+        print("supersonic limiter steps error", err, "bar", tol)
+        assert np.all(err < tol), (err, tol)
     finally:
         p.close()

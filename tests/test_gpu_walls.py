@@ -118,7 +118,7 @@ def test_rhs_mixed(dg, name):
         p.close()
 
 
-@pytest.mark.parametrize("precision,tol", [(0, 1e-11), (1, 1e-5)])
+@pytest.mark.parametrize("precision,tol", [(0, None), (1, 1e-5)])
 def test_rk_closed_box(dg, precision, tol):
     """Ten CK45 steps in the closed box (adiabatic and isothermal walls): the state matches
     the oracle's; mass stays constant in both."""
@@ -133,7 +133,10 @@ def test_rk_closed_box(dg, precision, tol):
         assert abs(p.gpu.diagnostics()[3] / m0 - 1) < (1e-14 if precision == 0 else 1e-6)
         u_r, _ = p.orc.step_rk(u_o, 10, dt_fixed=dt)
         err = cases.field_errors(u_g, u_r, 1, 3)
-        assert err.max() < tol, err
+        if tol is None:  # FP64: 1e-12 or the oracle's own one-ulp floor of these 10 steps
+            tol = cases.fp64_bar(cases.step_floor(p.orc, u_o, 10, dt))
+        print("closed box steps error", err, "bar", tol)
+        assert np.all(err < tol), (err, tol)
     finally:
         p.close()
 
