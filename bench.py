@@ -546,10 +546,11 @@ def run_reacting(args, stream_ptr, world, fp64_peak):
         out["roofline"] = _fp64_roofline("chem_kernel<float> (mixed form, the block's dominant kernel)",
                                          CHEM_FP64_FLOPS_PER_NODE, K * npn, out["mixed"]["chem_ms_per_launch"],
                                          fp64_peak)
-    # learned source: data from the plain run's own states, training, the same steps again
+    # learned source: data from the plain run's own states (8 snapshots spread over the
+    # run's length), training, the same steps again
     t0 = time.perf_counter()
     s.set_primitive(w0)
-    X, Y = S.collect_source(s.ctx, args.train_samples, 8, 1, cfl=cfl)
+    X, Y = S.collect_source(s.ctx, args.train_samples, 8, max(1, n // 8), cfl=cfl)
     params, stats, hist = S.train_source(X, Y, epochs=args.train_epochs, batch=4096, lr=2e-3)
     train_s = time.perf_counter() - t0
     out["training"] = {"samples": int(X.shape[0]), "epochs": args.train_epochs,
