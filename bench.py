@@ -449,7 +449,7 @@ def run_mixture(args, stream_ptr, world, fp64_peak):
     t0 = time.perf_counter()
     s.set_primitive(w0)
     X, T = S.collect(s.ctx, args.train_samples, 10, 2, cfl=cfl)
-    params, stats, hist = S.train(X, T, epochs=args.train_epochs, batch=4096, lr=2e-3)
+    params, stats, hist = S.train(X, T, epochs=args.train_epochs, batch=4096, lr=2e-3, lr_final=1e-4)
     out["training"] = {"samples": int(X.shape[0]), "epochs": args.train_epochs,
                        "val_mse_first_last": [hist[0][2], hist[-1][2]],
                        "seconds": time.perf_counter() - t0}
@@ -551,7 +551,7 @@ def run_reacting(args, stream_ptr, world, fp64_peak):
     t0 = time.perf_counter()
     s.set_primitive(w0)
     X, Y = S.collect_source(s.ctx, args.train_samples, 8, max(1, n // 8), cfl=cfl)
-    params, stats, hist = S.train_source(X, Y, epochs=args.train_epochs, batch=4096, lr=2e-3)
+    params, stats, hist = S.train_source(X, Y, epochs=args.train_epochs, batch=4096, lr=3e-3, lr_final=1e-4)
     train_s = time.perf_counter() - t0
     out["training"] = {"samples": int(X.shape[0]), "epochs": args.train_epochs,
                        "val_mse_first_last": [hist[0][2], hist[-1][2]], "seconds": train_s}
@@ -907,7 +907,8 @@ def main():
     ap.add_argument("--mix-elements", type=int, default=24, help="O-grid elements per direction")
     ap.add_argument("--mix-steps", type=int, default=100)
     ap.add_argument("--train-samples", type=int, default=1000000)
-    ap.add_argument("--train-epochs", type=int, default=20)
+    ap.add_argument("--train-epochs", type=int, default=60, help="epochs of each surrogate's training "
+                    "(Adam, step size decaying by a cosine to 1e-4)")
     ap.add_argument("--no-reacting", action="store_true")
     ap.add_argument("--no-other-shapes", action="store_true",
                     help="skip the 16^3 N=7 Taylor-Green and the square-cylinder blocks")

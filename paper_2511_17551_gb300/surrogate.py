@@ -81,8 +81,9 @@ def standardise(X, T):
     return Xn, Tn.reshape(-1), stats
 
 
-def fit(Xn, Yn, epochs=20, batch=4096, lr=1e-3, seed=0, val_frac=0.1, log=None):
-    """Adam on the mean-squared error of standardised targets Yn ([n] or [n][n_out]).
+def fit(Xn, Yn, epochs=20, batch=4096, lr=1e-3, seed=0, val_frac=0.1, log=None, lr_final=None):
+    """Adam on the mean-squared error of standardised targets Yn ([n] or [n][n_out]); with
+    lr_final the step size decays from lr to lr_final over the epochs (cosine).
     Returns (params float32 [P] device, history of (epoch, train, val))."""
     import torch
     n_out = 1 if Yn.dim() == 1 else Yn.shape[1]
@@ -112,6 +113,8 @@ def fit(Xn, Yn, epochs=20, batch=4096, lr=1e-3, seed=0, val_frac=0.1, log=None):
     hist = []
     step = 0
     for ep in range(epochs):
+        lr_ep = lr if lr_final is None else \
+            lr_final + 0.5 * (lr - lr_final) * (1.0 + math.cos(math.pi * ep / max(1, epochs - 1)))
         order = torch.from_numpy(rng.permutation(ntr).astype(np.int64)).to(dev)
         tot, nb = 0.0, 0
         for b0 in range(0, ntr - batch + 1, batch):
@@ -119,7 +122,7 @@ def fit(Xn, Yn, epochs=20, batch=4096, lr=1e-3, seed=0, val_frac=0.1, log=None):
             dg_gather_rows(Xt, idx, xb)
             dg_gather_rows(Yt, idx, tb)
             step += 1
-            dg_mlp_train_step(params, m, v, xb, tb if n_out > 1 else tb.reshape(-1), step, lr, loss, ws)
+            dg_mlp_train_step(params, m, v, xb, tb if n_out > 1 else tb.reshape(-1), step, lr_ep, loss, ws)
             tot += loss.item() if (nb % 50 == 0) else 0.0
             nb += 1
         vloss = validation_loss(params, Xv, Yv if n_out > 1 else Yv.reshape(-1))
@@ -129,11 +132,11 @@ def fit(Xn, Yn, epochs=20, batch=4096, lr=1e-3, seed=0, val_frac=0.1, log=None):
     return params, hist
 
 
-def train(X, T, epochs=20, batch=4096, lr=1e-3, seed=0, val_frac=0.1, log=None):
+def train(X, T, epochs=20, batch=4096, lr=1e-3, seed=0, val_frac=0.1, log=None, lr_final=None):
     """Temperature surrogate.  Returns (params float32 [P] host, stats float64 [16],
     history of (epoch, train, val))."""
     Xn, Tn, stats = standardise(X, T)
-    params, hist = fit(Xn, Tn, epochs, batch, lr, seed, val_frac, log)
+    params, hist = fit(Xn, Tn, epochs, batch, lr, seed, val_frac, log, lr_final)
     return params.cpu().numpy(), stats, hist
 
 
@@ -168,11 +171,12 @@ def source_stats(X, Y, ref_quantile=0.99, ref_fraction=1e-3, tol_check=0.05, tol
     return Xn, Zn, st
 
 
-def train_source(X, Y, epochs=30, batch=4096, lr=2e-3, seed=0, val_frac=0.1, log=None, **stat_kw):
+def train_source(X, Y, epochs=30, batch=4096, lr=2e-3, seed=0, val_frac=0.1, log=None, lr_final=None,
+                 **stat_kw):
     """Source surrogate (ten outputs).  Returns (params float32 [P] host, stats float64
     [DG_SRC_NSTATS], history)."""
     Xn, Zn, st = source_stats(X, Y, **stat_kw)
-    params, hist = fit(Xn, Zn, epochs, batch, lr, seed, val_frac, log)
+    params, hist = fit(Xn, Zn, epochs, batch, lr, seed, val_frac, log, lr_final)
     return params.cpu().numpy(), st, hist
 
 
