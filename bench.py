@@ -492,7 +492,8 @@ def run_reacting(args, stream_ptr, world, fp64_peak):
     scaling) on a 48 x 48 x 16-element cylinder O-grid, N = 4, with a 3000 K layer round the
     body: args.react_steps CK45 steps from the same state in the FP64 plain form, the mixed
     form with the plain source, and the mixed form with the learned source (trained here on
-    states of the plain run) at the default acceptance tolerance 0.05 and at 0.01;
+    states of the plain run) at the default acceptance tolerance 0.05 and at 0.01, and with
+    the plain correction (refresh every 1 or 2 steps);
     throughput, per-kernel device time, and per-field relative L2 of each mixed run's end
     state against the FP64 form's."""
     import torch
@@ -555,17 +556,26 @@ def run_reacting(args, stream_ptr, world, fp64_peak):
     train_s = time.perf_counter() - t0
     out["training"] = {"samples": int(X.shape[0]), "epochs": args.train_epochs,
                        "val_mse_first_last": [hist[0][2], hist[-1][2]], "seconds": train_s}
-    for tol in (0.05, 0.01):
+    # the learned source alone at two tolerances, and with the plain correction (a refresh
+    # at the first stage of every k-th step, the refresh's full check at the same tolerance)
+    for key, tol, k in (("mixed_learned_source", 0.05, 0), ("mixed_learned_source_tol0.01", 0.01, 0),
+                        ("mixed_corrected_source_tol0.01_k1", 0.01, 1),
+                        ("mixed_corrected_source_tol0.01_k2", 0.01, 2),
+                        ("mixed_corrected_source_tol0.05_k2", 0.05, 2)):
         st = stats.copy()
         st[50] = st[51] = tol
         dg.dg_set_surrogate(s.ctx, params, st, which=dg.DG_SURROGATE_SOURCE)
+        dg.dg_set_source_refresh(s.ctx, k)
         dg.dg_surrogate_stats(s.ctx, dg.DG_SURROGATE_SOURCE)
         ul, wall, prof = _timed_run(dg, torch, s, w0, n, cfl)
         acc, fb = dg.dg_surrogate_stats(s.ctx, dg.DG_SURROGATE_SOURCE)
         d = form(ul, wall, prof, u64)
         d["tolerance"] = tol
+        d["refresh_period_steps"] = k
         d["accepted_node_fraction"] = acc / max(1, acc + fb)
-        out["mixed_learned_source" if tol == 0.05 else "mixed_learned_source_tol0.01"] = d
+        if k:
+            d["refresh_evaluations_per_step"] = 1.0 / k
+        out[key] = d
         if ul is None:
             s.close()
             s = make(dg.DG_MIXED)

@@ -240,16 +240,34 @@ enum {
  * context, a frozen mixture with DG_SURROGATE_SOURCE, or non-positive deviations. */
 dg_status dg_set_surrogate(dg_ctx* ctx, int which, const float* params, const double* stats);
 
+/* Plain correction of the learned source (reacting contexts).  period 0 (the default)
+ * switches it off.  period k >= 1: a refresh evaluation takes the plain FP64 source at
+ * every node and stores per node the plain rates minus the network's decoded rates
+ * (omega_s - omega^_s and jpi_s - jpi'_s, jpi' the decoded jpi before its clamp at 0;
+ * FP32, 40 bytes per node, allocated here); the learned evaluations that follow add these
+ * differences to the decoded rates (omega^_s + c_s, max(0, jpi'_s + c_{5+s})) before the
+ * acceptance tests above.  At a refresh every node is also checked: its uncorrected learned
+ * source against the plain one with the sampled check's test; a tile with a failing node
+ * takes the plain source at every evaluation until the next refresh (flag 4 in
+ * dg_get_source).  Refreshes happen at the first source evaluation of each
+ * dg_step_rk call, at the first RK stage of every k-th step after it, and at the first
+ * dg_rhs after the state, the network or the period was set.  Reading R18s step 9: the
+ * corrected network is exact at the refresh state; the checks still decide acceptance.
+ * DG_EINVAL for a context without chemistry or a negative period. */
+dg_status dg_set_source_refresh(dg_ctx* ctx, int period);
+
 /* Nodes accepted and nodes recomputed plainly by the surrogate `which` since the last
- * call (host int64[2]); resets the counters. */
+ * call (host int64[2]); resets the counters.  Refresh evaluations of the source are
+ * counted in neither. */
 dg_status dg_surrogate_stats(dg_ctx* ctx, int which, int64_t* accepted_fallback);
 
 /* The species source of the last evaluation (the appendix's finite-rate source with its
  * point-implicit factor, Eqs. nrp .. calc_prod; learned where the surrogate's tile was
  * accepted): S [K][5][np] FP64 host (converted from the form precision).  flags (host,
  * (K np + 31) / 32 bytes, or NULL) receives the per-tile decision of that evaluation:
- * 0 learned, 1 rejected by the trust box or the mass balance, 2 rejected by the sampled
- * check (255 everywhere when the learned source is off); *call (or NULL) the evaluation
+ * 0 learned, 1 rejected by the trust box, the mass balance or the positivity test, 2
+ * rejected by the sampled check, 3 a refresh evaluation (plain everywhere), 4 not trusted
+ * since the last refresh (255 everywhere when the learned source is off); *call (or NULL) the evaluation
  * counter that drew the tiles' sampled nodes (-1 before the first learned evaluation).
  * DG_EINVAL for a context without chemistry, DG_ESTATE before any evaluation.  Waits for
  * the context stream (bounded). */

@@ -456,8 +456,43 @@ def splitmix64(x):
     return out
 
 
+def chem_surrogate_correction(params, stats, rhos, T, dt=0.0, *, species, reactions, lam=8.0, x_rel=0.0,
+                              network="fp64"):
+    """Step 9 of reading R18s (plain correction) at a refresh state rhos [n][5], T [n] with
+    the running step dt: the plain rates minus the network's decoded rates, c_omega =
+    omega - omega^ and c_jpi = jpi - jpi' (jpi = max(0, -d omega_s / d rho_s) of the plain
+    source, jpi' the decoded value before its clamp at 0), with the bounds of the GPU's
+    difference from them (the network's rounding bound at this state, and the FP32 storage
+    of the corrections); and the full check of every node: the uncorrected learned source
+    (steps 2 and 5) against the plain source with the sampled check's test (step 6), a
+    32-node tile trusted when all of its nodes pass (trust_ambiguous where a margin lies
+    within the bound).  Returns the dict that chem_surrogate_source takes as
+    `correction`."""
+    st = np.asarray(stats, dtype=np.float64)
+    d = chem_surrogate_source(params, stats, rhos, T, dt, lam=lam, x_rel=x_rel, network=network)
+    om_p, jd, S_p = chem_eval(species, reactions, rhos, T, dt)
+    jpi_p = np.maximum(0.0, -jd)
+    c_om = om_p - d["omega_net"]
+    c_j = jpi_p - d["jpi_raw"]
+    u32 = 2.0 ** -24
+    n = len(T)
+    scale = np.abs(S_p).sum(axis=1)
+    thr = st[50] * scale + st[52]
+    m = thr[:, None] - np.abs(d["S_learned"] - S_p)
+    node_ok = np.all(m >= 0.0, axis=1) & np.isfinite(d["S_learned"]).all(axis=1)
+    node_amb = np.any(np.abs(m) <= d["bound"] + 1e-10 * scale[:, None] + u32 * thr[:, None], axis=1)
+    ntiles = (n + 31) // 32
+    pad = ntiles * 32 - n
+    trust = np.concatenate([node_ok, np.ones(pad, dtype=bool)]).reshape(ntiles, 32).all(axis=1)
+    trust_amb = np.concatenate([node_amb, np.zeros(pad, dtype=bool)]).reshape(ntiles, 32).any(axis=1)
+    return {"c_omega": c_om, "c_jpi": c_j,
+            "B_omega": d["B_omega"] + u32 * (np.abs(c_om) + 1e-10 * np.abs(om_p)),
+            "B_jpi": d["B_jpi"] + u32 * (np.abs(c_j) + 1e-10 * jpi_p),
+            "trust": trust, "trust_ambiguous": trust_amb}
+
+
 def chem_surrogate_source(params, stats, rhos, T, dt=0.0, *, species=None, reactions=None, call=None,
-                          lam=8.0, x_rel=0.0, network="fp64"):
+                          lam=8.0, x_rel=0.0, network="fp64", correction=None):
     """The learned chemistry source by the acceptance rule of reading R18s, in FP64.
 
     params: ten-output perceptron (FP32 values); stats: the statistics vector of the C
@@ -483,7 +518,10 @@ def chem_surrogate_source(params, stats, rhos, T, dt=0.0, *, species=None, react
     first-order model, carried through decode, projection and the point-implicit factor;
     per tile, the result says whether any decision lies within that bound of its
     threshold (ambiguous: the GPU may decide either way).  x_rel: relative error of the
-    raw features of the GPU's input state (0 for an FP64 state)."""
+    raw features of the GPU's input state (0 for an FP64 state).  correction (the dict of
+    chem_surrogate_correction at a refresh state, step 9): the decoded rates become
+    omega^ + c_omega and max(0, jpi' + c_jpi) before the tests, and the bound adds the
+    correction's own."""
     st = np.asarray(stats, dtype=np.float64)
     rhos = np.asarray(rhos, dtype=np.float64)
     T = np.asarray(T, dtype=np.float64)
@@ -512,9 +550,17 @@ def chem_surrogate_source(params, stats, rhos, T, dt=0.0, *, species=None, react
     Bz = lam * np.abs(st[24:34]) * sd + 4 * u32 * (np.abs(st[14:24]) + np.abs(st[24:34] * y))
     om = st[34] * np.sinh(z[:, :5])
     jp_raw = st[35] * np.sinh(z[:, 5:])
-    jpi = np.maximum(0.0, jp_raw)
     Bom = st[34] * np.cosh(np.abs(z[:, :5]) + Bz[:, :5]) * Bz[:, :5] + 8 * u32 * np.abs(om)
     Bjp = st[35] * np.cosh(np.abs(z[:, 5:]) + Bz[:, 5:]) * Bz[:, 5:] + 8 * u32 * np.abs(jp_raw)
+    net = {"omega_net": om, "jpi_raw": jp_raw, "B_omega": Bom, "B_jpi": Bjp}
+    if correction is not None:
+        # step 9: the stored plain-minus-network differences, added in FP32 on the GPU
+        c_om, c_j = correction["c_omega"], correction["c_jpi"]
+        Bom = Bom + correction["B_omega"] + 2 * u32 * (np.abs(om) + np.abs(c_om))
+        Bjp = Bjp + correction["B_jpi"] + 2 * u32 * (np.abs(jp_raw) + np.abs(c_j))
+        om = om + c_om
+        jp_raw = jp_raw + c_j
+    jpi = np.maximum(0.0, jp_raw)
     # 3. mass balance
     tau_c, tau_m, floor = st[50], st[51], st[52]
     msum = om.sum(axis=1)
@@ -542,6 +588,7 @@ def chem_surrogate_source(params, stats, rhos, T, dt=0.0, *, species=None, react
     mass_amb = mass_amb | pos_amb
     out = {"S_learned": S_l, "bound": bound, "inside": inside, "mass_ok": mass_ok, "positive": pos_ok,
            "omega": om, "jpi": jpi, "x": x}
+    out.update(net)
     if call is None:
         return out
     # 5. sampled check per 32-node tile and the decisions
@@ -552,12 +599,17 @@ def chem_surrogate_source(params, stats, rhos, T, dt=0.0, *, species=None, react
     sampled = np.zeros(ntiles, dtype=np.int64)
     node_ok = inside & mass_ok
     node_amb = box_amb | mass_amb
+    trust = np.ones(ntiles, dtype=bool) if correction is None else correction["trust"]
+    trust_amb = np.zeros(ntiles, dtype=bool) if correction is None else correction["trust_ambiguous"]
     hashes = splitmix64([(int(call) * 1099511628211 + t) & _M64 for t in range(ntiles)])
     for t in range(ntiles):
         a, b = 32 * t, min(n, 32 * t + 32)
         i = a + int(hashes[t] % (b - a))
         sampled[t] = i
-        amb[t] = bool(node_amb[a:b].any())
+        amb[t] = bool(node_amb[a:b].any()) or bool(trust_amb[t])
+        if not trust[t]:
+            flag[t] = 4  # step 9: the network missed the plain source at the last refresh
+            continue
         if not node_ok[a:b].all():
             flag[t] = 1
             continue

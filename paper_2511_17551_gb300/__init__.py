@@ -37,7 +37,7 @@ EXPORTED = [
     "dg_thermo_sample", "dg_mlp_nparams", "dg_mlp_workspace_bytes", "dg_mlp_grad",
     "dg_mlp_train_step", "dg_mlp_forward", "dg_peak_flops", "dg_chem_sample", "dg_limiter_stats", "dg_limit_state",
     "dg_noalloc_status", "dg_get_metrics", "dg_get_source", "dg_column_stats", "dg_standardize",
-    "dg_abs_quantile", "dg_gather_rows", "dg_mlp_loss",
+    "dg_abs_quantile", "dg_gather_rows", "dg_mlp_loss", "dg_set_source_refresh",
 ]
 PROF_KINDS = ["rhs", "gradients", "indicator", "lambda", "thermo", "mlp", "chem", "other", "limiter"]
 
@@ -106,6 +106,7 @@ def lib():
             "dg_get_temperature": (i, [vp, vp]),
             "dg_set_surrogate": (i, [vp, i, vp, vp]),
             "dg_surrogate_stats": (i, [vp, i, vp]),
+            "dg_set_source_refresh": (i, [vp, i]),
             "dg_chem_sample": (i, [vp, i64, C.c_uint64, vp, vp]),
             "dg_limiter_stats": (i, [vp, vp]),
             "dg_limit_state": (i, [vp]),
@@ -204,6 +205,11 @@ def dg_set_surrogate(ctx, params=None, stats=None, which=DG_SURROGATE_TEMPERATUR
     p = None if params is None else np.ascontiguousarray(params, dtype=np.float32)
     s = None if stats is None else np.ascontiguousarray(stats, dtype=np.float64)
     _check(lib().dg_set_surrogate(ctx, which, _ptr(p), _ptr(s)), "dg_set_surrogate")
+
+
+def dg_set_source_refresh(ctx, period):
+    """Plain correction of the learned source: refresh every `period` RK steps (0: off)."""
+    _check(lib().dg_set_source_refresh(ctx, int(period)), "dg_set_source_refresh")
 
 
 def dg_surrogate_stats(ctx, which=DG_SURROGATE_TEMPERATURE):

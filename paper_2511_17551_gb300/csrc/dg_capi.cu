@@ -41,6 +41,7 @@ struct dg_ctx {
   double* scal;
   unsigned long long* lam;
   int lam_slot;
+  int64_t rk_step;  // step index within the running dg_step_rk call
   unsigned long long* status;
   double* partial;
   int diag_blocks;
@@ -510,9 +511,15 @@ cudaError_t pre_rhs(dg_ctx* c, DgArgs& a) {
     if (e != cudaSuccess) return e;
     if (c->th.nr > 0) {
       // species sources; point-implicit with the running step in RK stages
+      // plain correction of the learned source: refresh at the first evaluation after the
+      // corrections were invalidated (new state, new network, new dg_step_rk call) and at
+      // the first stage of every k-th step
+      const int kref = c->th.refresh_period;
+      const int refresh = c->th.chem_mlp && kref > 0 &&
+                          (!c->th.corr_valid || (a.mode == 1 && a.stage == 0 && c->rk_step % kref == 0));
       e = timed(c, DG_PROF_CHEM, [&] {
         return dg_chem_source(&c->th, a.u, c->precision == DG_MIXED, a.mode == 1 ? c->scal + 1 : NULL,
-                              c->stream);
+                              refresh, c->stream);
       });
       if (e != cudaSuccess) return e;
       c->th.src_valid = 1;
@@ -876,6 +883,7 @@ dg_status dg_set_state(dg_ctx* c, const double* u, int on_device, double t) {
   }
   CK(cudaGetLastError());
   if (c->n_species > 0) CK(dg_thermo_reset(&c->th, c->stream));
+  c->th.corr_valid = 0;
   CK(cudaMemcpyAsync(c->scal, &t, sizeof(double), cudaMemcpyHostToDevice, c->stream));
   c->have_state = true;
   return wait_stream(c);
@@ -904,6 +912,7 @@ dg_status dg_set_state_primitive(dg_ctx* c, const double* w, int on_device, doub
     CK(dg_thermo_prim2cons(&c->th, src, c->u[c->cur], c->stream));
     if (c->ulo) CK(cudaMemsetAsync(c->ulo, 0, sizeof(float) * n, c->stream));
   }
+  c->th.corr_valid = 0;
   CK(cudaMemcpyAsync(c->scal, &t, sizeof(double), cudaMemcpyHostToDevice, c->stream));
   c->have_state = true;
   return wait_stream(c);
@@ -973,7 +982,9 @@ dg_status dg_step_rk(dg_ctx* c, int nsteps, double cfl, double dt_fixed, double*
   }
   CK(run_step_dt(c, a, c->lam_slot, 0));
   if (nsteps > 0) c->grad_is_gradient = false;
+  c->th.corr_valid = 0;  // the call's first source evaluation refreshes the corrections
   for (int step = 0; step < nsteps; ++step) {
+    c->rk_step = step;
     for (int s = 0; s < 5; ++s) {
       DgArgs b = base_args(c);
       b.u = c->u[c->cur];
@@ -1073,6 +1084,18 @@ dg_status dg_set_surrogate(dg_ctx* c, int which, const float* params, const doub
   }
   CK(dg_mlp_set(&c->th, params, stats));
   c->th.mode = params ? DG_THERMO_MLP : DG_THERMO_NEWTON;
+  return DG_OK;
+}
+
+dg_status dg_set_source_refresh(dg_ctx* c, int period) {
+  if (!c || period < 0 || c->n_species == 0 || c->th.nr == 0) return DG_EINVAL;
+  cudaSetDevice(c->dev);
+  CK(cudaStreamSynchronize(c->stream));
+  if (period > 0 && !c->th.chem_corr)
+    CK(cudaMalloc((void**)&c->th.chem_corr, sizeof(float) * 10 * c->K * c->np));
+  if (period > 0 && !c->th.chem_trust) CK(cudaMalloc((void**)&c->th.chem_trust, (size_t)(c->K * c->np + 31) / 32));
+  c->th.refresh_period = period;
+  c->th.corr_valid = 0;
   return DG_OK;
 }
 

@@ -143,6 +143,10 @@ __global__ void chem_kernel(const T* u, const double* Tc, int64_t K, int np, int
 // (moved each call) within tol_check of the plain FP64 source; otherwise the tile's source
 // is recomputed plainly.  Accepted rates are projected onto exact mass balance:
 // omega_s -= |omega_s| sum(omega) / sum|omega|.
+// With a refresh period (plain correction): a refresh evaluation takes the plain source at
+// every node and stores, per node, the plain rates minus the network's decoded ones; the
+// evaluations until the next refresh add those differences to the decoded rates before the
+// tests, so the corrected network is exact at the refresh state.
 struct __align__(16) DgChemMlp {
   DgMlpW<10> w;
   float mean[7], inv_std[7], muY[10], sdY[10], lo[7], hi[7];
@@ -179,10 +183,15 @@ __device__ __forceinline__ void chem_features(const T* uu, int np, double Tk, fl
 // its node's ten outputs after them (species sources, mass-balance test).  Flags per
 // 32-node (warp) tile: 0 accepted, 1 rejected; a tile whose tensor-core waits ran out is
 // rejected too, so the plain fallback recomputes it.
+// corr ([10][K np], FP32) with cmode 1: the decoded rates are corrected by the stored
+// plain-minus-network differences before the tests (omega_s + c_s, max(0, jpi'_s + c_5+s));
+// cmode 2 (refresh): only the decoded rates (jpi' before its clamp) are written to corr,
+// for chem_refresh_kernel to turn into corrections.
 template <typename T>
 __global__ void __launch_bounds__(dgtc5::THREADS, 1)
 chem_mlp_tc5_kernel(const T* u, const double* Tc, int64_t K, int np, int dim, const DgChemMlp* mlp,
-                    const double* dtp, T* src, unsigned char* flags) {
+                    const double* dtp, T* src, unsigned char* flags, float* corr, const unsigned char* trust,
+                    int cmode) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   dgtc5::Smem<10>& s = *reinterpret_cast<dgtc5::Smem<10>*>(smem_raw);
   __shared__ DgChemMlp m;
@@ -209,13 +218,28 @@ chem_mlp_tc5_kernel(const T* u, const double* Tc, int64_t K, int np, int dim, co
     return ok;
   };
   auto cons = [&](int64_t i, const float* y, bool ok, bool valid) {
+    if (cmode == 2) {  // uniform over the grid: no lane reaches the vote below
+      if (i < total && valid) {
+#pragma unroll
+        for (int q = 0; q < NSPEC; ++q) {
+          corr[q * total + i] = m.w_ref * sinhf(m.muY[q] + m.sdY[q] * y[q]);
+          corr[(5 + q) * total + i] = m.j_ref * sinhf(m.muY[5 + q] + m.sdY[5 + q] * y[5 + q]);
+        }
+      }
+      return;
+    }
     ok = ok && valid;
     if (i < total && valid) {
       float om[NSPEC], jp[NSPEC], msum = 0.f, asum = 0.f;
 #pragma unroll
       for (int q = 0; q < NSPEC; ++q) {
         om[q] = m.w_ref * sinhf(m.muY[q] + m.sdY[q] * y[q]);
-        jp[q] = fmaxf(0.f, m.j_ref * sinhf(m.muY[5 + q] + m.sdY[5 + q] * y[5 + q]));
+        float jr = m.j_ref * sinhf(m.muY[5 + q] + m.sdY[5 + q] * y[5 + q]);
+        if (cmode == 1) {
+          om[q] += corr[q * total + i];
+          jr += corr[(5 + q) * total + i];
+        }
+        jp[q] = fmaxf(0.f, jr);
         msum += om[q];
         asum += fabsf(om[q]);
       }
@@ -234,7 +258,12 @@ chem_mlp_tc5_kernel(const T* u, const double* Tc, int64_t K, int np, int dim, co
     }
     const bool tile_ok = __all_sync(0xffffffffu, ok);
     const int64_t base = i - (threadIdx.x & 31);  // first node of this warp's 32-node tile
-    if ((threadIdx.x & 31) == 0 && base < total) flags[base >> 5] = tile_ok ? 0 : 1;
+    if ((threadIdx.x & 31) == 0 && base < total) {
+      // with corrections, a tile whose network missed the plain source at the last refresh
+      // is not trusted until the next one
+      const bool trusted = cmode != 1 || trust[base >> 5];
+      flags[base >> 5] = !trusted ? 4 : (tile_ok ? 0 : 1);
+    }
   };
   dgtc5::run_tiles<10>(s, total, prod, cons);
 }
@@ -308,6 +337,59 @@ chem_fallback_kernel(const T* u, const double* Tc, int64_t K, int np, int dim, c
   if (lane == 0 && (n_ok | n_fb)) {
     atomicAdd(&stats[0], n_ok);
     atomicAdd(&stats[1], n_fb);
+  }
+}
+
+// refresh of the corrections: every node takes the plain FP64 source, and corr (holding
+// the network's decoded rates of this state, written by chem_mlp_tc5_kernel in cmode 2)
+// becomes the plain-minus-network differences; every tile is flagged 3 (plain).  The full
+// check: each node's uncorrected learned source (projection, point-implicit factor) against
+// the plain one with the sampled check's test; a tile is trusted until the next refresh when
+// all of its nodes pass.  Threads are grouped in warps over whole 32-node tiles.
+template <typename T>
+__global__ void __launch_bounds__(128)
+chem_refresh_kernel(const T* u, const double* Tc, int64_t K, int np, int dim, const double* sp_raw,
+                    const double* reac, int nr, const DgChemMlp* mlp, const double* dtp, T* src, float* corr,
+                    unsigned char* flags, unsigned char* trust) {
+  const int nv = NSPEC + dim + 1;
+  const int64_t total = K * np;
+  const double dt = dtp ? *dtp : 0.0;
+  const double tol = mlp->tol_check, floor_ = mlp->floor;
+  const int lane = threadIdx.x & 31;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;  // a multiple of 32
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i - lane < total; i += stride) {
+    bool ok = true;
+    if (i < total) {
+      const int64_t k = i / np;
+      const int node = (int)(i % np);
+      double om[NSPEC], jpi[NSPEC], Sp[NSPEC], oh[NSPEC], jh[NSPEC], scale = 0.0, msum = 0.0, asum = 0.0;
+      chem_node<T>(u + k * nv * np + node, np, Tc[i], sp_raw, reac, nr, om, jpi);
+      T* so = src + k * NSPEC * np + node;
+#pragma unroll
+      for (int s = 0; s < NSPEC; ++s) {
+        Sp[s] = om[s] / (1.0 + dt * jpi[s]);
+        so[s * np] = (T)Sp[s];
+        scale += fabs(Sp[s]);
+        oh[s] = (double)corr[s * total + i];
+        jh[s] = (double)corr[(5 + s) * total + i];
+        msum += oh[s];
+        asum += fabs(oh[s]);
+      }
+      const double f = asum > 0.0 ? msum / asum : 0.0;
+      ok = isfinite(asum);
+#pragma unroll
+      for (int s = 0; s < NSPEC; ++s) {
+        const double Sl = (oh[s] - fabs(oh[s]) * f) / (1.0 + dt * fmax(0.0, jh[s]));
+        ok = ok && fabs(Sl - Sp[s]) <= tol * scale + floor_;
+        corr[s * total + i] = (float)(om[s] - oh[s]);
+        corr[(5 + s) * total + i] = (float)(jpi[s] - jh[s]);
+      }
+    }
+    const bool tile_ok = __all_sync(0xffffffffu, ok);
+    if (lane == 0) {
+      flags[i >> 5] = 3;
+      trust[i >> 5] = tile_ok ? 1 : 0;
+    }
   }
 }
 
@@ -386,7 +468,7 @@ cudaError_t dg_chem_init(DgThermo* th, const double* species_host, const double*
 }
 
 template <typename T>
-static cudaError_t chem_learned(DgThermo* th, const T* u, const double* dt_dev, cudaStream_t s) {
+static cudaError_t chem_learned(DgThermo* th, const T* u, const double* dt_dev, int refresh, cudaStream_t s) {
   const int64_t total = th->K * th->np, ntiles = (total + 31) / 32;
   const DgChemMlp* m = (const DgChemMlp*)th->chem_mlp;
   // tensor-core tiles of 128 nodes; the dynamic shared memory is padded to 60 KB so that at
@@ -396,8 +478,22 @@ static cudaError_t chem_learned(DgThermo* th, const T* u, const double* dt_dev, 
   cudaError_t e = cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int64_t t128 = (total + dgtc5::ROWS - 1) / dgtc5::ROWS;
-  k1<<<(unsigned)(t128 < 152 * 3 ? t128 : 152 * 3), dgtc5::THREADS, smem, s>>>(u, th->T, th->K, th->np, th->dim, m,
-                                                                              dt_dev, (T*)th->src, th->chem_flags);
+  const unsigned g1 = (unsigned)(t128 < 152 * 3 ? t128 : 152 * 3);
+  if (refresh) {
+    if (!th->chem_corr || !th->chem_trust) return cudaErrorInvalidValue;
+    k1<<<g1, dgtc5::THREADS, smem, s>>>(u, th->T, th->K, th->np, th->dim, m, dt_dev, (T*)th->src,
+                                        th->chem_flags, th->chem_corr, th->chem_trust, 2);
+    chem_refresh_kernel<T><<<grid_of(ntiles * 32), 128, 0, s>>>(u, th->T, th->K, th->np, th->dim,
+                                                                th->species_raw, th->reac, th->nr, m, dt_dev,
+                                                                (T*)th->src, th->chem_corr, th->chem_flags,
+                                                                th->chem_trust);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) th->corr_valid = 1;
+    return e;
+  }
+  const int cmode = th->chem_corr && th->chem_trust && th->corr_valid ? 1 : 0;
+  k1<<<g1, dgtc5::THREADS, smem, s>>>(u, th->T, th->K, th->np, th->dim, m, dt_dev, (T*)th->src, th->chem_flags,
+                                      th->chem_corr, th->chem_trust, cmode);
   chem_check_kernel<T><<<grid_of(ntiles), 128, 0, s>>>(u, th->T, th->K, th->np, th->dim, th->species_raw,
                                                        th->reac, th->nr, m, dt_dev, (const T*)th->src,
                                                        th->chem_flags, th->chem_calls++);
@@ -409,10 +505,11 @@ static cudaError_t chem_learned(DgThermo* th, const T* u, const double* dt_dev, 
   return cudaGetLastError();
 }
 
-cudaError_t dg_chem_source(DgThermo* th, const void* u, int f32, const double* dt_dev, cudaStream_t s) {
+cudaError_t dg_chem_source(DgThermo* th, const void* u, int f32, const double* dt_dev, int refresh,
+                           cudaStream_t s) {
   if (th->chem_mlp)
-    return f32 ? chem_learned<float>(th, (const float*)u, dt_dev, s)
-               : chem_learned<double>(th, (const double*)u, dt_dev, s);
+    return f32 ? chem_learned<float>(th, (const float*)u, dt_dev, refresh, s)
+               : chem_learned<double>(th, (const double*)u, dt_dev, refresh, s);
   if (f32)
     chem_kernel<float><<<grid_of(th->K * th->np), 128, 0, s>>>(
         (const float*)u, th->T, th->K, th->np, th->dim, th->species_raw, th->reac, th->nr, dt_dev,
@@ -425,6 +522,7 @@ cudaError_t dg_chem_source(DgThermo* th, const void* u, int f32, const double* d
 }
 
 cudaError_t dg_chem_mlp_set(DgThermo* th, const float* params_host, const double* st) {
+  th->corr_valid = 0;
   if (!params_host) {
     if (th->chem_mlp) cudaFree(th->chem_mlp);
     th->chem_mlp = NULL;

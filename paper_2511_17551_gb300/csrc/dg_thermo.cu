@@ -260,6 +260,8 @@ void dg_thermo_free(DgThermo* th) {
   if (th->chem_mlp) cudaFree(th->chem_mlp);
   if (th->chem_stats) cudaFree(th->chem_stats);
   if (th->chem_flags) cudaFree(th->chem_flags);
+  if (th->chem_corr) cudaFree(th->chem_corr);
+  if (th->chem_trust) cudaFree(th->chem_trust);
   if (th->species) cudaFree(th->species);
   if (th->coef32) cudaFree(th->coef32);
   if (th->species_raw) cudaFree(th->species_raw);

@@ -24,6 +24,10 @@ struct DgThermo {
   unsigned char* chem_flags;      // per 32-node tile: 0 accepted, otherwise recomputed plainly
   unsigned long long chem_calls;  // learned-source evaluations so far (moves each tile's sampled node)
   int src_valid;                  // src holds an evaluation
+  float* chem_corr;               // [10][K np] plain-minus-network corrections of the learned source
+  int refresh_period;             // 0: no correction; k: refresh at stage 0 of every k-th RK step
+  int corr_valid;                 // chem_corr holds the corrections of a refresh
+  unsigned char* chem_trust;      // per 32-node tile: 1 when the network passed the last refresh's full check
 };
 
 cudaError_t dg_thermo_upload_basis();
@@ -36,7 +40,10 @@ cudaError_t dg_thermo_boundary(DgThermo* th, const double* bw, int n_bc, void* b
 cudaError_t dg_thermo_prim2cons(DgThermo* th, const double* w, void* u, cudaStream_t s);
 // chemistry (dg_chem.cu)
 cudaError_t dg_chem_init(DgThermo* th, const double* species_host, const double* reac_host, int nr);
-cudaError_t dg_chem_source(DgThermo* th, const void* u, int f32, const double* dt_dev, cudaStream_t s);
+// refresh != 0 (learned source with corrections only): plain source everywhere, and the
+// corrections of this state stored for the evaluations that follow
+cudaError_t dg_chem_source(DgThermo* th, const void* u, int f32, const double* dt_dev, int refresh,
+                           cudaStream_t s);
 // learned source (dg_chem.cu): set / clear (params null) and plain-source training samples
 cudaError_t dg_chem_mlp_set(DgThermo* th, const float* params_host, const double* stats_host);
 cudaError_t dg_chem_sample_dev(DgThermo* th, const void* u, int f32, int64_t n, uint64_t seed, float* X,

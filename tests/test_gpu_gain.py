@@ -1,6 +1,7 @@
 """What the trained networks gain over the method without them, on the same GB300 and the
 same state: the learned chemistry source against the plain FP64 source (device time per
-evaluation, and the learned values' error against the plain ones), and the learned
+evaluation, and the learned values' error against the plain ones), the corrected learned
+source over a run (time per step, and the end state's error against the FP64 form), and the learned
 temperature solve against the plain Newton iteration (device time per launch, and T
 against the oracle's Newton solve).  Both networks are trained here by libdg's kernels
 on states of the plain solver's own run (a 24 x 24 x 8 O-grid, N = 4: 576,000 nodes)."""
@@ -29,7 +30,7 @@ def env():
     return dg, torch
 
 
-def _mesh(dg, react):
+def _mesh(dg, react, precision=None):
     import workloads as W
     N = 4
     xi, _ = dg.dg_lgl_nodes(N)
@@ -40,7 +41,8 @@ def _mesh(dg, react):
     fs = W.mixture_primitive(xyz[:1], rho=0.1, vel=vel, T=300.0, seed=7)[0, :, 0]
     s = dg.Solver(3, N, xyz, nbr, face, n_species=5, species=W.species_table(),
                   volume_flux=dg.DG_VF_DUCROS, surface_flux=dg.DG_SF_LLF, bc_kind=[1, 2, 3],
-                  bc_prim=np.stack([fs] * 3), alpha_max=0.5, precision=dg.DG_MIXED,
+                  bc_prim=np.stack([fs] * 3), alpha_max=0.5,
+                  precision=dg.DG_MIXED if precision is None else precision,
                   reactions=W.reaction_table() if react else None)
     s.set_primitive(w0)
     return s, w0, xyz, nbr, face
@@ -92,6 +94,65 @@ def test_learned_source_gain(env):
         _record("source", rec)
         assert learned_ms < plain_ms, rec
         assert l2.max() < SOURCE_L2_BAR, rec
+    finally:
+        s.close()
+
+
+# the corrected learned source over a run: per-field relative L2 of the end state against
+# the FP64 form's plain run (the stated bar of the mixed form with learned parts)
+RUN_STEPS = 50
+RUN_L2_BAR = 1e-5
+
+
+def _l2(a, ref):
+    mom = np.linalg.norm(ref[:, 5:8])
+    return np.array([np.linalg.norm(a[:, v] - ref[:, v]) / (mom if 5 <= v < 8 else np.linalg.norm(ref[:, v]))
+                     for v in range(a.shape[1])])
+
+
+def test_corrected_source_run_gain(env):
+    """RUN_STEPS CK45 steps of the reacting O-grid (CFL 0.05): the mixed form with the plain
+    source against the mixed form with the corrected learned source (tolerance 0.01, a
+    refresh every step), both against the FP64 form's plain run.  The corrected run is
+    faster than the plain mixed run and within RUN_L2_BAR on every conserved field."""
+    dg, torch = env
+    import time
+    from paper_2511_17551_gb300 import surrogate as S
+    s64, w0, *_ = _mesh(dg, True, dg.DG_FP64)
+    try:
+        s64.step(RUN_STEPS, 0.05)
+        u64, _ = s64.get_state()
+    finally:
+        s64.close()
+    s, w0, *_ = _mesh(dg, True)
+    try:
+        def run():
+            s.set_primitive(w0)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            s.step(RUN_STEPS, 0.05)
+            torch.cuda.synchronize()
+            return (time.perf_counter() - t0) * 1e3 / RUN_STEPS, s.get_state()[0]
+        run()  # warm
+        plain_ms, u_plain = run()
+        s.set_primitive(w0)
+        X, Y = S.collect_source(s.ctx, 500_000, 8, max(1, RUN_STEPS // 8), cfl=0.05)
+        params, stats, hist = S.train_source(X, Y, epochs=60, batch=4096, lr=3e-3, lr_final=1e-4)
+        st = stats.copy()
+        st[50] = st[51] = 0.01
+        dg.dg_set_surrogate(s.ctx, params, st, which=dg.DG_SURROGATE_SOURCE)
+        dg.dg_set_source_refresh(s.ctx, 1)
+        dg.dg_surrogate_stats(s.ctx, dg.DG_SURROGATE_SOURCE)
+        corr_ms, u_c = run()
+        acc, fb = dg.dg_surrogate_stats(s.ctx, dg.DG_SURROGATE_SOURCE)
+        rec = {"steps": RUN_STEPS, "plain_mixed_ms_per_step": plain_ms, "corrected_ms_per_step": corr_ms,
+               "gain": plain_ms / corr_ms, "accepted_fraction": acc / max(1, acc + fb),
+               "l2_plain_mixed_vs_fp64": _l2(u_plain, u64).tolist(),
+               "l2_corrected_vs_fp64": _l2(u_c, u64).tolist()}
+        print("corrected source run:", rec)
+        _record("corrected_run", rec)
+        assert corr_ms < plain_ms, rec
+        assert _l2(u_c, u64).max() < RUN_L2_BAR, rec
     finally:
         s.close()
 

@@ -450,3 +450,97 @@ def test_positivity_rule_both_sides(orc):
     for dt, ok in ((0.9e-4, True), (1.1e-4, False), (0.0, True)):  # rho_1 / 100 = 1e-4
         r = orc.chem_surrogate_source(net, st, rhos, T, dt)
         assert bool(r["positive"][0]) is ok and bool(r["mass_ok"][0]) is ok, (dt, r["positive"])
+
+
+def _refresh_case(orc, n=96, seed=21):
+    import workloads as W
+    rng = np.random.default_rng(seed)
+    sp, R = W.species_table(), W.reaction_table()
+    rhos = np.array([[0.012, 0.021, 0.030, 0.006, 0.0019]]) * rng.uniform(0.5, 1.5, size=(n, 5))
+    T = rng.uniform(2000.0, 4000.0, size=n)
+    p = 0.4 * rng.normal(size=orc.mlp_nparams(10))
+    om, jd, _ = orc.chem_eval(sp, R, rhos, T, 0.0)
+    st = _stats(np.zeros(10), np.ones(10), w_ref=np.abs(om).mean(), j_ref=np.abs(jd).mean(), tol_mass=1e9)
+    return sp, R, rhos, T, p, st
+
+
+def test_plain_correction_is_exact_at_the_refresh_state(orc):
+    """Step 9 of R18s: with the corrections taken at a state, the corrected network gives
+    the plain rates there (omega, and jpi = max(0, -d omega / d rho) through the decoded
+    value before its clamp), hence the plain point-implicit source and mass balance; nodes
+    whose decoded jpi is negative while the plain one is positive are present, so a
+    correction taken after the clamp would fail."""
+    sp, R, rhos, T, p, st = _refresh_case(orc)
+    dt = 3e-7
+    om_p, jd, S_p = orc.chem_eval(sp, R, rhos, T, dt)
+    c = orc.chem_surrogate_correction(p, st, rhos, T, species=sp, reactions=R)
+    r = orc.chem_surrogate_source(p, st, rhos, T, dt, correction=c)
+    raw = orc.chem_surrogate_source(p, st, rhos, T, dt)
+    assert ((raw["jpi_raw"] < 0) & (-jd > 0)).sum() >= 10
+    scale = np.abs(om_p).sum(axis=1, keepdims=True)
+    # up to the rounding of (omega - omega^) + omega^ (FP64, relative to the larger part)
+    eps = 2.0 ** -52
+    tol_om = 4 * eps * (np.abs(om_p) + np.abs(raw["omega_net"]))
+    assert np.all(np.abs(r["omega"] - om_p) <= tol_om)
+    tol_j = 4 * eps * (np.abs(jd) + np.abs(raw["jpi_raw"]))
+    assert np.all(np.abs(r["jpi"] - np.maximum(0.0, -jd)) <= tol_j)
+    assert np.all(np.abs(r["S_learned"] - S_p) <= 1e-13 * scale + 2 * tol_om.sum(axis=1, keepdims=True))
+    # the uncorrected network is far from the plain source on the same nodes
+    assert np.median(np.abs(raw["S_learned"] - S_p).sum(axis=1) / scale[:, 0]) > 0.1
+
+
+def test_plain_correction_error_is_first_order_in_the_state_change(orc):
+    """A state u0 + h d away from the refresh state u0: the corrected error
+    [net(u) - net(u0)] - [plain(u) - plain(u0)] halves with h (first order), while the
+    uncorrected network's error stays of its own size."""
+    sp, R, rhos, T, p, st = _refresh_case(orc, n=64, seed=22)
+    rng = np.random.default_rng(23)
+    d_rho = rhos * rng.uniform(-1.0, 1.0, size=rhos.shape)
+    d_T = T * rng.uniform(-1.0, 1.0, size=T.shape)
+    c = orc.chem_surrogate_correction(p, st, rhos, T, species=sp, reactions=R)
+    errs, raw_errs = [], []
+    for h in (2e-3, 1e-3, 5e-4):
+        r1, T1 = rhos + h * d_rho, T + h * d_T
+        _, _, S_p = orc.chem_eval(sp, R, r1, T1, 0.0)
+        errs.append(np.linalg.norm(orc.chem_surrogate_source(p, st, r1, T1, correction=c)["S_learned"] - S_p))
+        raw_errs.append(np.linalg.norm(orc.chem_surrogate_source(p, st, r1, T1)["S_learned"] - S_p))
+    for a, b in zip(errs, errs[1:]):
+        assert 1.8 < a / b < 2.2, errs
+    assert 0.9 < raw_errs[0] / raw_errs[-1] < 1.1, raw_errs
+    assert errs[0] < 0.05 * raw_errs[0], (errs, raw_errs)
+
+
+def test_refresh_full_check_both_sides_and_tiles(orc):
+    """Step 9's full check at a refresh: learned rates = the plain source + d (e_1 - e_2)
+    at every node trust both 32-node tiles of 40 nodes at d = 0.9 (tau_c sum|S| + floor)
+    and neither at 1.1; a node of the second tile whose plain source moved (T 2500 K
+    instead of 3500 K) leaves only that tile untrusted: flag 4 and the plain source there,
+    the corrected (exact) source in the first tile."""
+    import workloads as W
+    sp, R = W.species_table(), W.reaction_table()
+    n = 40
+    rhos, T = _hot_state(n)
+    _, _, S_p = orc.chem_eval(sp, R, rhos, T, 0.0)
+    thr = 0.05 * np.abs(S_p[0]).sum()
+    w_ref = np.abs(S_p[0]).max()
+    st = _stats(np.zeros(10), np.ones(10), w_ref=w_ref, tol_mass=0.05)
+    for kappa, trust in ((0.9, [True, True]), (1.1, [False, False])):
+        om = S_p[0].copy()
+        om[0] += kappa * thr
+        om[1] -= kappa * thr
+        c = orc.chem_surrogate_correction(_net_for_rates(orc, om, w_ref), st, rhos, T, species=sp, reactions=R)
+        assert list(c["trust"]) == trust and not c["trust_ambiguous"].any()
+    T2 = T.copy()
+    T2[35] = 2500.0
+    _, _, S_p2 = orc.chem_eval(sp, R, rhos, T2, 0.0)
+    assert np.abs(S_p2[35] - S_p[0]).max() > 2 * thr
+    om = S_p[0].copy()
+    om[0] += 0.5 * thr
+    om[1] -= 0.5 * thr
+    net = _net_for_rates(orc, om, w_ref)
+    c = orc.chem_surrogate_correction(net, st, rhos, T2, species=sp, reactions=R)
+    assert list(c["trust"]) == [True, False]
+    r = orc.chem_surrogate_source(net, st, rhos, T2, species=sp, reactions=R, call=0, correction=c)
+    assert list(r["tile_flag"]) == [0, 4]
+    assert np.array_equal(r["S"][32:], S_p2[32:])
+    assert np.allclose(r["S"][:32], S_p2[:32], rtol=1e-12, atol=1e-12 * w_ref)
