@@ -108,7 +108,8 @@ typedef struct {
   void* stream;             /* cudaStream_t to queue work on, or NULL for a private stream */
   const double* reactions;  /* host [n_reactions][19] finite-rate mechanism (mixtures):
                                nu'(5), nu''(5), third-body flag, efficiencies(5), A, beta,
-                               theta = E/R_u (appendix, Eqs. chemreact..calc_prod), or NULL */
+                               theta = E/R_u (appendix, Eqs. chemreact..calc_prod), or NULL;
+                               stoichiometric coefficients in {0, 1, 2, 3}, else DG_EINVAL */
   int n_reactions;          /* 0: frozen mixture; 1..64 */
   double p_ref;             /* one gas: pressure offset p_ref; the momentum components of
                                every numerical flux use p - p_ref (a constant pressure adds

@@ -812,10 +812,12 @@ dg_status dg_init_mesh(const dg_mesh_desc* m, const dg_physics_desc* p, dg_ctx**
         st = DG_ENOMEM;
         goto fail;
       }
-      if (p->n_reactions > 0 &&
-          dg_chem_init(&c->th, p->species, p->reactions, p->n_reactions) != cudaSuccess) {
-        st = DG_ENOMEM;
-        goto fail;
+      if (p->n_reactions > 0) {
+        const cudaError_t ce = dg_chem_init(&c->th, p->species, p->reactions, p->n_reactions);
+        if (ce != cudaSuccess) {
+          st = ce == cudaErrorInvalidValue ? DG_EINVAL : DG_ENOMEM;
+          goto fail;
+        }
       }
     }
     // boundary states (primitive -> conserved on the device)

@@ -26,20 +26,22 @@
 
 namespace {
 
-// c^nu for the small non-negative integer stoichiometric coefficients (0..3 here)
-__device__ __forceinline__ double ipow012(double c, double nu) {
-  double r = 1.0;
-  for (int q = 0; q < (int)nu; ++q) r *= c;
-  return r;
-}
-
 // Device tables (built by dg_chem_init from the species and reaction arrays):
 // species rows [16]: 1e-6/W, 1e6 W, h/(RT) coefficients (a1, a2/2, a3/3, a4/4, a5/5, a6),
 //   s/R coefficients (a1 [times ln T], a2, a3/2, a4/3, a5/4, a7), ln(1e-6 p0 / R_u), 0;
 // reaction rows [32]: nu'(5), nu''(5), third_body, eff(5), ln A, beta, theta,
-//   dn = sum dnu, dnu(5), 0...
+//   dn = sum dnu, dnu(5), then (slot 25, as raw bits) the integer form of the row: 2 bits
+//   per species of nu' in {0..3} (bits 0-9) and nu'' (bits 10-19), the third-body flag (bit 20) and
+//   one bit per species with dnu != 0 (bits 21-25).  The integer form drives the uniform
+//   branches of the reaction loop, so that no FP64 compare or conversion is spent on them.
 #define SP_W 16
 #define RX_W 32
+#define RX_META 25
+
+// c^nu for the stoichiometric coefficients nu in {1, 2, 3} (c2 = c c)
+__device__ __forceinline__ double pow123(int nu, double c, double c2) {
+  return nu == 1 ? c : (nu == 2 ? c2 : c2 * c);
+}
 
 // Plain FP64 source at one node: omega_s (kg/m^3/s) and the point-implicit terms
 // jpi_s = max(0, -d omega_s / d rho_s) of the analytic diagonal Jacobian at fixed T.
@@ -50,34 +52,41 @@ __device__ __forceinline__ void chem_node(const T* uu, int np, double Tk, const 
   const double lnT = log(Tk), iT = 1.0 / Tk;
   // ln(1e-6 p0 / (R_u T)) = ln(1e-6 p0 / R_u) - ln T (the constant sits in species row 0)
   const double lnP = sp[14] - lnT;
-  double c[NSPEC], ic[NSPEC], g[NSPEC], jd[NSPEC];
+  double c[NSPEC], c2[NSPEC], ic[NSPEC], g[NSPEC], jd[NSPEC];
+  bool pos[NSPEC];
 #pragma unroll
   for (int s = 0; s < NSPEC; ++s) {
     const double* q = sp + SP_W * s;
     c[s] = q[0] * (double)uu[s * np];
-    ic[s] = c[s] > 0.0 ? 1.0 / c[s] : 0.0;
+    c2[s] = c[s] * c[s];
+    pos[s] = c[s] > 0.0;
+    ic[s] = pos[s] ? 1.0 / c[s] : 0.0;
     const double h = q[2] + Tk * (q[3] + Tk * (q[4] + Tk * (q[5] + Tk * q[6]))) + q[7] * iT;
     const double sr = q[8] * lnT + Tk * (q[9] + Tk * (q[10] + Tk * (q[11] + Tk * q[12]))) + q[13];
     g[s] = h - sr;
     om[s] = 0.0;
     jd[s] = 0.0;
   }
+#pragma unroll 1
   for (int r = 0; r < nr; ++r) {
     const double* row = reac + RX_W * r;
+    const int meta = (int)__double_as_longlong(row[RX_META]);
     double dg = 0.0;
 #pragma unroll
-    for (int s = 0; s < NSPEC; ++s) dg += row[20 + s] * g[s];
+    for (int s = 0; s < NSPEC; ++s)
+      if (meta & (1 << (21 + s))) dg += row[20 + s] * g[s];
     const double lnkf = row[16] + row[17] * lnT - row[18] * iT;
     const double kf = exp(lnkf);
     const double kb = exp(lnkf + dg - row[19] * lnP);
     double pf = kf, pb = kb;
 #pragma unroll
     for (int s = 0; s < NSPEC; ++s) {
-      pf *= ipow012(c[s], row[s]);
-      pb *= ipow012(c[s], row[5 + s]);
+      const int a = (meta >> (2 * s)) & 3, b = (meta >> (10 + 2 * s)) & 3;
+      if (a) pf *= pow123(a, c[s], c2[s]);
+      if (b) pb *= pow123(b, c[s], c2[s]);
     }
     double M = 1.0;
-    const bool tb = row[10] != 0.0;
+    const bool tb = meta & (1 << 20);
     if (tb) {
       M = 0.0;
 #pragma unroll
@@ -86,22 +95,33 @@ __device__ __forceinline__ void chem_node(const T* uu, int np, double Tk, const 
     const double Rr = (pf - pb) * M;
 #pragma unroll
     for (int s = 0; s < NSPEC; ++s) {
+      if (!(meta & (1 << (21 + s)))) continue;  // the same for every node: no divergence
       const double d = row[20 + s];
-      if (d == 0.0) continue;  // the same for every node: no divergence
       om[s] += d * Rr;
       // d R_r / d c_s (explicit products when c_s = 0)
+      const int a = (meta >> (2 * s)) & 3, b = (meta >> (10 + 2 * s)) & 3;
       double dpf = 0.0, dpb = 0.0;
-      if (c[s] > 0.0) {
-        dpf = pf * row[s] * ic[s];
-        dpb = pb * row[5 + s] * ic[s];
+      if (pos[s]) {
+        if (a) dpf = pf * (a == 1 ? ic[s] : (double)a * ic[s]);
+        if (b) dpb = pb * (b == 1 ? ic[s] : (double)b * ic[s]);
       } else {
-        if (row[s] == 1.0) {
+        if (a == 1) {
           dpf = kf;
-          for (int q = 0; q < NSPEC; ++q) if (q != s) dpf *= ipow012(c[q], row[q]);
+#pragma unroll
+          for (int q = 0; q < NSPEC; ++q)
+            if (q != s) {
+              const int aq = (meta >> (2 * q)) & 3;
+              if (aq) dpf *= pow123(aq, c[q], c2[q]);
+            }
         }
-        if (row[5 + s] == 1.0) {
+        if (b == 1) {
           dpb = kb;
-          for (int q = 0; q < NSPEC; ++q) if (q != s) dpb *= ipow012(c[q], row[5 + q]);
+#pragma unroll
+          for (int q = 0; q < NSPEC; ++q)
+            if (q != s) {
+              const int bq = (meta >> (10 + 2 * q)) & 3;
+              if (bq) dpb *= pow123(bq, c[q], c2[q]);
+            }
         }
       }
       jd[s] += d * ((dpf - dpb) * M + (tb ? (pf - pb) * row[11 + s] : 0.0));
@@ -430,11 +450,22 @@ cudaError_t dg_chem_init(DgThermo* th, const double* species_host, const double*
     o[17] = in[17];
     o[18] = in[18];
     double dn = 0.0;
+    long long meta = 0;
     for (int s = 0; s < NSPEC; ++s) {
       o[20 + s] = in[5 + s] - in[s];
       dn += o[20 + s];
+      const double a = in[s], b = in[5 + s];
+      if (!(a == 0.0 || a == 1.0 || a == 2.0 || a == 3.0) || !(b == 0.0 || b == 1.0 || b == 2.0 || b == 3.0)) {
+        free(rows);  // the integer form holds nu in {0, 1, 2, 3}
+        return cudaErrorInvalidValue;
+      }
+      meta |= (long long)a << (2 * s);
+      meta |= (long long)b << (10 + 2 * s);
+      if (o[20 + s] != 0.0) meta |= 1ll << (21 + s);
     }
+    if (in[10] != 0.0) meta |= 1ll << 20;
     o[19] = dn;
+    memcpy(&o[RX_META], &meta, sizeof(meta));
   }
   double* sp = rows + (size_t)RX_W * nr;
   for (int s = 0; s < NSPEC; ++s) {
