@@ -42,6 +42,10 @@ struct dg_ctx {
   unsigned long long* lam;
   int lam_slot;
   int64_t rk_step;  // step index within the running dg_step_rk call
+  // mixtures: the temperature cache and (p, c) hold the solve of the state thermo_u while
+  // thermo_ok (cleared by every write to a state buffer)
+  const void* thermo_u;
+  bool thermo_ok;
   unsigned long long* status;
   double* partial;
   int diag_blocks;
@@ -491,9 +495,12 @@ cudaError_t run_step_dt(dg_ctx* c, DgArgs& a, int slot, int advance) {
   });
 }
 cudaError_t run_thermo(dg_ctx* c, const void* u) {
-  return timed(c, DG_PROF_THERMO, [&] {
+  const cudaError_t e = timed(c, DG_PROF_THERMO, [&] {
     return dg_thermo_update(&c->th, u, c->precision == DG_MIXED, c->stream);
   });
+  c->thermo_u = u;
+  c->thermo_ok = e == cudaSuccess;
+  return e;
 }
 
 cudaError_t run_positivity(dg_ctx* c, const DgArgs& b) {
@@ -507,7 +514,9 @@ cudaError_t run_positivity(dg_ctx* c, const DgArgs& b) {
 cudaError_t pre_rhs(dg_ctx* c, DgArgs& a) {
   cudaError_t e = cudaSuccess;
   if (c->n_species > 0) {
-    e = run_thermo(c, a.u);
+    // an RK stage whose state was just solved (the first stage after the previous step's
+    // wave-speed solve) reuses that solve
+    if (!(a.mode == 1 && c->thermo_ok && c->thermo_u == a.u)) e = run_thermo(c, a.u);
     if (e != cudaSuccess) return e;
     if (c->th.nr > 0) {
       // species sources; point-implicit with the running step in RK stages
@@ -886,6 +895,7 @@ dg_status dg_set_state(dg_ctx* c, const double* u, int on_device, double t) {
   CK(cudaGetLastError());
   if (c->n_species > 0) CK(dg_thermo_reset(&c->th, c->stream));
   c->th.corr_valid = 0;
+  c->thermo_ok = false;
   CK(cudaMemcpyAsync(c->scal, &t, sizeof(double), cudaMemcpyHostToDevice, c->stream));
   c->have_state = true;
   return wait_stream(c);
@@ -915,6 +925,7 @@ dg_status dg_set_state_primitive(dg_ctx* c, const double* w, int on_device, doub
     if (c->ulo) CK(cudaMemsetAsync(c->ulo, 0, sizeof(float) * n, c->stream));
   }
   c->th.corr_valid = 0;
+  c->thermo_ok = false;
   CK(cudaMemcpyAsync(c->scal, &t, sizeof(double), cudaMemcpyHostToDevice, c->stream));
   c->have_state = true;
   return wait_stream(c);
@@ -1002,6 +1013,7 @@ dg_status dg_step_rk(dg_ctx* c, int nsteps, double cfl, double dt_fixed, double*
       b.lam_cur = c->lam_slot;
       b.want_lambda = (s == 4 && cfl_mode && c->n_species == 0) ? 1 : 0;
       CK(pre_rhs(c, b));
+      c->thermo_ok = false;  // the stage writes the other state buffer
       CK(run_rhs(c, b));
       if (c->pos_eps > 0.0) CK(run_positivity(c, b));
       c->cur ^= 1;
@@ -1080,6 +1092,7 @@ dg_status dg_set_surrogate(dg_ctx* c, int which, const float* params, const doub
     }
   }
   CK(cudaStreamSynchronize(c->stream));
+  c->thermo_ok = false;
   if (which == DG_SURROGATE_SOURCE) {
     CK(dg_chem_mlp_set(&c->th, params, stats));
     return DG_OK;
@@ -1281,6 +1294,7 @@ extern "C" dg_status dg_limit_state(dg_ctx* c) {
   cudaSetDevice(c->dev);
   DgArgs b = base_args(c);
   b.out = c->u[c->cur];
+  c->thermo_ok = false;
   CK(run_positivity(c, b));
   dg_status w = wait_stream(c);
   if (w != DG_OK) return w;
