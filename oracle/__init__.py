@@ -457,7 +457,7 @@ def splitmix64(x):
 
 
 def chem_surrogate_correction(params, stats, rhos, T, dt=0.0, *, species, reactions, lam=8.0, x_rel=0.0,
-                              network="fp64"):
+                              network="fp64", plain_rel=1e-10):
     """Step 9 of reading R18s (plain correction) at a refresh state rhos [n][5], T [n] with
     the running step dt: the plain rates minus the network's decoded rates, c_omega =
     omega - omega^ and c_jpi = jpi - jpi' (jpi = max(0, -d omega_s / d rho_s) of the plain
@@ -466,8 +466,10 @@ def chem_surrogate_correction(params, stats, rhos, T, dt=0.0, *, species, reacti
     of the corrections); and the full check of every node: the uncorrected learned source
     (steps 2 and 5) against the plain source with the sampled check's test (step 6), a
     32-node tile trusted when all of its nodes pass (trust_ambiguous where a margin lies
-    within the bound).  Returns the dict that chem_surrogate_source takes as
-    `correction`."""
+    within the bound).  plain_rel: the relative difference allowed between the GPU's plain
+    rates at this state and the oracle's (1e-10 for an FP64 state; larger where the GPU's
+    temperature differs, as in the mixed form).  Returns the dict that
+    chem_surrogate_source takes as `correction`."""
     st = np.asarray(stats, dtype=np.float64)
     d = chem_surrogate_source(params, stats, rhos, T, dt, lam=lam, x_rel=x_rel, network=network)
     om_p, jd, S_p = chem_eval(species, reactions, rhos, T, dt)
@@ -480,14 +482,19 @@ def chem_surrogate_correction(params, stats, rhos, T, dt=0.0, *, species, reacti
     thr = st[50] * scale + st[52]
     m = thr[:, None] - np.abs(d["S_learned"] - S_p)
     node_ok = np.all(m >= 0.0, axis=1) & np.isfinite(d["S_learned"]).all(axis=1)
-    node_amb = np.any(np.abs(m) <= d["bound"] + 1e-10 * scale[:, None] + u32 * thr[:, None], axis=1)
+    node_amb = np.any(np.abs(m) <= d["bound"] + max(plain_rel, 1e-10) * scale[:, None] + u32 * thr[:, None],
+                      axis=1)
     ntiles = (n + 31) // 32
     pad = ntiles * 32 - n
     trust = np.concatenate([node_ok, np.ones(pad, dtype=bool)]).reshape(ntiles, 32).all(axis=1)
     trust_amb = np.concatenate([node_amb, np.zeros(pad, dtype=bool)]).reshape(ntiles, 32).any(axis=1)
+    # the plain rates' own difference: relative to the node's largest rate (the rates are
+    # sums of forward and backward terms that cancel near equilibrium)
+    om_scale = np.abs(om_p).max(axis=1, keepdims=True)
+    j_scale = jpi_p.max(axis=1, keepdims=True)
     return {"c_omega": c_om, "c_jpi": c_j,
-            "B_omega": d["B_omega"] + u32 * (np.abs(c_om) + 1e-10 * np.abs(om_p)),
-            "B_jpi": d["B_jpi"] + u32 * (np.abs(c_j) + 1e-10 * jpi_p),
+            "B_omega": d["B_omega"] + u32 * np.abs(c_om) + plain_rel * (np.abs(om_p) + om_scale),
+            "B_jpi": d["B_jpi"] + u32 * np.abs(c_j) + plain_rel * (jpi_p + j_scale),
             "trust": trust, "trust_ambiguous": trust_amb}
 
 

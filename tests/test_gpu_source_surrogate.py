@@ -379,6 +379,67 @@ def test_corrected_source_matches_oracle_after_refresh(env, trained_source):
         s.close()
 
 
+def test_mixed_form_learned_and_corrected_source_match_oracle(env, trained_source):
+    """The mixed form's instances (FP32 state, source and corrections): with the tolerances
+    opened, the learned source at an FP32 state, the refresh there (the plain source, every
+    tile flagged 3) and the corrected source at a state whose species densities moved by up
+    to 1e-3 match the oracle on the same FP32-valued states within the BF16 bounds, the
+    features' FP32 rounding (x_rel) and the difference between the GPU's mixed temperature
+    solve and the oracle's Newton (relative 1e-5 on the plain rates)."""
+    dg, oracle, torch = env
+    import workloads as W
+    params, stats, hist, dt = trained_source
+    sp, R = W.species_table(), W.reaction_table()
+    s = _reacting(dg, precision=dg.DG_MIXED)
+    o, _ = _reacting_oracle(oracle)
+    try:
+        u0 = s.get_state()[0].astype(np.float32)
+        u1 = _perturbed(u0.astype(np.float64), 1e-3, 6).astype(np.float32)
+        rhos0, T0 = _nodes(o, u0.astype(np.float64))
+        rhos1, T1 = _nodes(o, u1.astype(np.float64))
+        n = len(T0)
+        p64 = params.astype(np.float64)
+        kw = dict(species=sp, reactions=R)
+        opened = stats.copy()
+        opened[50] = opened[51] = 1e30
+        X_REL, PLAIN_REL = 1e-6, 1e-5
+
+        def rhs_source(u32):
+            u = torch.from_numpy(np.ascontiguousarray(u32)).cuda()
+            r = torch.empty_like(u)
+            dg.dg_rhs(s.ctx, u, r)
+            dg.dg_sync(s.ctx)
+            S, flags, call = dg.dg_get_source(s.ctx, s.shape)
+            return S.transpose(0, 2, 1).reshape(-1, 5), flags
+
+        dg.dg_set_surrogate(s.ctx, params, opened, which=dg.DG_SURROGATE_SOURCE)
+        # the learned source alone
+        S0, flags = rhs_source(u0)
+        r = oracle.chem_surrogate_source(p64, opened, rhos0, T0, x_rel=X_REL)
+        acc = np.repeat(flags == 0, 32)[:n]
+        assert acc.mean() > 0.5, acc.mean()
+        bound = r["bound"] + PLAIN_REL * np.abs(r["S_learned"]) + 2.0 ** -24 * np.abs(r["S_learned"])
+        ratio = np.abs(S0[acc] - r["S_learned"][acc]) / bound[acc]
+        assert ratio.max() <= 1.0, ratio.max()
+        # the refresh at u0 and the corrected source at u1
+        dg.dg_set_source_refresh(s.ctx, 1)
+        Sr, flags = rhs_source(u0)
+        assert (flags == 3).all()
+        _, _, S_p0 = oracle.chem_eval(sp, R, rhos0, T0, 0.0)
+        scale0 = np.abs(S_p0).sum(axis=1, keepdims=True) + 1e-300
+        assert (np.abs(Sr - S_p0) / scale0).max() < PLAIN_REL
+        S1, flags = rhs_source(u1)
+        c = oracle.chem_surrogate_correction(p64, opened, rhos0, T0, x_rel=X_REL, plain_rel=PLAIN_REL, **kw)
+        r1 = oracle.chem_surrogate_source(p64, opened, rhos1, T1, x_rel=X_REL, correction=c)
+        acc = np.repeat(flags == 0, 32)[:n]
+        assert acc.mean() > 0.5, acc.mean()
+        bound = r1["bound"] + PLAIN_REL * np.abs(r1["S_learned"]) + 2.0 ** -24 * np.abs(r1["S_learned"])
+        ratio = np.abs(S1[acc] - r1["S_learned"][acc]) / bound[acc]
+        assert ratio.max() <= 1.0, ratio.max()
+    finally:
+        s.close()
+
+
 def test_refresh_schedule(env, trained_source):
     """Refreshes at the first evaluation of each dg_step_rk call and at the first stage of
     every k-th step: 3 steps at k = 2 take 2 refreshes and 13 learned evaluations, 2 steps at
