@@ -27,10 +27,12 @@
 namespace {
 
 // Device tables (built by dg_chem_init from the species and reaction arrays):
-// species rows [16]: 1e-6/W, 1e6 W, h/(RT) coefficients (a1, a2/2, a3/3, a4/4, a5/5, a6),
-//   s/R coefficients (a1 [times ln T], a2, a3/2, a4/3, a5/4, a7), ln(1e-6 p0 / R_u), 0;
+// species rows [16]: 1e-6/W, 1e6 W, g/(RT) = h/(RT) - s/R as the coefficients of 1, T, T^2,
+//   T^3, T^4 (from a1..a5 and a7), the 1/T coefficient a6 and the ln T coefficient a1,
+//   slots 9-13 unused, ln(1e-6 p0 / R_u), 0;
 // reaction rows [32]: nu'(5), nu''(5), third_body, eff(5), ln A, beta, theta,
-//   dn = sum dnu, dnu(5), then (slot 25, as raw bits) the integer form of the row: 2 bits
+//   dn = sum dnu, dnu(5), then (slot 25, as raw bits) the integer form of the row, and
+//   dnu_s eff_s (5, slots 26-30); the integer form holds 2 bits
 //   per species of nu' in {0..3} (bits 0-9) and nu'' (bits 10-19), the third-body flag (bit 20) and
 //   one bit per species with dnu != 0 (bits 21-25).  The integer form drives the uniform
 //   branches of the reaction loop, so that no FP64 compare or conversion is spent on them.
@@ -46,13 +48,16 @@ __device__ __forceinline__ double pow123(int nu, double c, double c2) {
 // Plain FP64 source at one node: omega_s (kg/m^3/s) and the point-implicit terms
 // jpi_s = max(0, -d omega_s / d rho_s) of the analytic diagonal Jacobian at fixed T.
 // uu points at the node's first species density, stride np between variables.
+// The Jacobian of reaction r with respect to c_s is M (nu'_s pf - nu''_s pb) / c_s plus, for
+// third-body reactions, eff_s (pf - pb); the first part is summed over the reactions and
+// divided by c_s once after the loop (c_s > 0), the explicit products are kept for c_s = 0.
 template <typename T>
 __device__ __forceinline__ void chem_node(const T* uu, int np, double Tk, const double* sp,
                                           const double* reac, int nr, double* om, double* jpi) {
   const double lnT = log(Tk), iT = 1.0 / Tk;
   // ln(1e-6 p0 / (R_u T)) = ln(1e-6 p0 / R_u) - ln T (the constant sits in species row 0)
   const double lnP = sp[14] - lnT;
-  double c[NSPEC], c2[NSPEC], ic[NSPEC], g[NSPEC], jd[NSPEC];
+  double c[NSPEC], c2[NSPEC], g[NSPEC], jd[NSPEC], j1[NSPEC];
   bool pos[NSPEC];
 #pragma unroll
   for (int s = 0; s < NSPEC; ++s) {
@@ -60,12 +65,11 @@ __device__ __forceinline__ void chem_node(const T* uu, int np, double Tk, const 
     c[s] = q[0] * (double)uu[s * np];
     c2[s] = c[s] * c[s];
     pos[s] = c[s] > 0.0;
-    ic[s] = pos[s] ? 1.0 / c[s] : 0.0;
-    const double h = q[2] + Tk * (q[3] + Tk * (q[4] + Tk * (q[5] + Tk * q[6]))) + q[7] * iT;
-    const double sr = q[8] * lnT + Tk * (q[9] + Tk * (q[10] + Tk * (q[11] + Tk * q[12]))) + q[13];
-    g[s] = h - sr;
+    // g/(RT) = h/(RT) - s/R as one polynomial in T plus the 1/T and ln T terms
+    g[s] = q[2] + Tk * (q[3] + Tk * (q[4] + Tk * (q[5] + Tk * q[6]))) + q[7] * iT - q[8] * lnT;
     om[s] = 0.0;
     jd[s] = 0.0;
+    j1[s] = 0.0;
   }
 #pragma unroll 1
   for (int r = 0; r < nr; ++r) {
@@ -92,19 +96,22 @@ __device__ __forceinline__ void chem_node(const T* uu, int np, double Tk, const 
 #pragma unroll
       for (int s = 0; s < NSPEC; ++s) M += row[11 + s] * c[s];
     }
-    const double Rr = (pf - pb) * M;
+    const double dp = pf - pb, Rr = dp * M;
 #pragma unroll
     for (int s = 0; s < NSPEC; ++s) {
       if (!(meta & (1 << (21 + s)))) continue;  // the same for every node: no divergence
       const double d = row[20 + s];
       om[s] += d * Rr;
-      // d R_r / d c_s (explicit products when c_s = 0)
+      if (tb) jd[s] += row[26 + s] * dp;  // dnu_s eff_s (pf - pb)
       const int a = (meta >> (2 * s)) & 3, b = (meta >> (10 + 2 * s)) & 3;
-      double dpf = 0.0, dpb = 0.0;
+      if (!(a | b)) continue;
       if (pos[s]) {
-        if (a) dpf = pf * (a == 1 ? ic[s] : (double)a * ic[s]);
-        if (b) dpb = pb * (b == 1 ? ic[s] : (double)b * ic[s]);
+        // nu'_s pf - nu''_s pb (the stoichiometric coefficients are exact small integers)
+        const double t = row[s] * pf - row[5 + s] * pb;
+        j1[s] += (tb ? d * M : d) * t;
       } else {
+        // c_s = 0: the explicit products for nu = 1 (higher powers have zero derivative)
+        double dpf = 0.0, dpb = 0.0;
         if (a == 1) {
           dpf = kf;
 #pragma unroll
@@ -123,13 +130,14 @@ __device__ __forceinline__ void chem_node(const T* uu, int np, double Tk, const 
               if (bq) dpb *= pow123(bq, c[q], c2[q]);
             }
         }
+        jd[s] += d * (dpf - dpb) * M;
       }
-      jd[s] += d * ((dpf - dpb) * M + (tb ? (pf - pb) * row[11 + s] : 0.0));
     }
   }
   // omega in kg/(m^3 s); d omega_s / d rho_s = 1e6 W_s (1e-6 / W_s) d(...)/dc_s = jd_s
 #pragma unroll
   for (int s = 0; s < NSPEC; ++s) {
+    if (pos[s]) jd[s] += j1[s] / c[s];
     om[s] *= sp[SP_W * s + 1];
     jpi[s] = -jd[s] > 0.0 ? -jd[s] : 0.0;
   }
@@ -466,25 +474,23 @@ cudaError_t dg_chem_init(DgThermo* th, const double* species_host, const double*
     if (in[10] != 0.0) meta |= 1ll << 20;
     o[19] = dn;
     memcpy(&o[RX_META], &meta, sizeof(meta));
+    for (int s = 0; s < NSPEC; ++s) o[26 + s] = o[20 + s] * in[11 + s];  // dnu_s eff_s
   }
   double* sp = rows + (size_t)RX_W * nr;
   for (int s = 0; s < NSPEC; ++s) {
     const double* in = species_host + 8 * s;  // [W, a1..a7]
     double* o = sp + SP_W * s;
+    // g/(RT) = h/(RT) - s/R = (a1 - a7) + T (a2/2 - a2) + T^2 (a3/3 - a3/2) + T^3 (a4/4 - a4/3)
+    //         + T^4 (a5/5 - a5/4) + a6 / T - a1 ln T
     o[0] = 1e-6 / in[0];
     o[1] = 1e6 * in[0];
-    o[2] = in[1];
-    o[3] = in[2] / 2.0;
-    o[4] = in[3] / 3.0;
-    o[5] = in[4] / 4.0;
-    o[6] = in[5] / 5.0;
+    o[2] = in[1] - in[7];
+    o[3] = in[2] / 2.0 - in[2];
+    o[4] = in[3] / 3.0 - in[3] / 2.0;
+    o[5] = in[4] / 4.0 - in[4] / 3.0;
+    o[6] = in[5] / 5.0 - in[5] / 4.0;
     o[7] = in[6];
     o[8] = in[1];
-    o[9] = in[2];
-    o[10] = in[3] / 2.0;
-    o[11] = in[4] / 3.0;
-    o[12] = in[5] / 4.0;
-    o[13] = in[7];
     o[14] = log(1e-6 * DG_P0 / DG_RU);
   }
   const size_t rs = th->f32 ? sizeof(float) : sizeof(double);
