@@ -29,12 +29,14 @@ namespace {
 // Device tables (built by dg_chem_init from the species and reaction arrays):
 // species rows [16]: 1e-6/W, 1e6 W, g/(RT) = h/(RT) - s/R as the coefficients of 1, T, T^2,
 //   T^3, T^4 (from a1..a5 and a7), the 1/T coefficient a6 and the ln T coefficient a1,
-//   slots 9-13 unused, ln(1e-6 p0 / R_u), 0;
+//   1e-6 p0 / R_u and its reciprocal, slots 11-13 unused, ln(1e-6 p0 / R_u), 0;
 // reaction rows [32]: nu'(5), nu''(5), third_body, eff(5), ln A, beta, theta,
 //   dn = sum dnu, dnu(5), then (slot 25, as raw bits) the integer form of the row, and
 //   dnu_s eff_s (5, slots 26-30); the integer form holds 2 bits
 //   per species of nu' in {0..3} (bits 0-9) and nu'' (bits 10-19), the third-body flag (bit 20) and
-//   one bit per species with dnu != 0 (bits 21-25).  The integer form drives the uniform
+//   one bit per species with dnu != 0 (bits 21-25), and, where k_b may be formed as a product
+//   (sum |dnu_s| <= 15 and |dn| <= 3), sum |dnu_s| (bits 26-29) with bit 30 set.  The
+//   integer form drives the uniform
 //   branches of the reaction loop, so that no FP64 compare or conversion is spent on them.
 #define SP_W 16
 #define RX_W 32
@@ -43,6 +45,13 @@ namespace {
 // c^nu for the stoichiometric coefficients nu in {1, 2, 3} (c2 = c c)
 __device__ __forceinline__ double pow123(int nu, double c, double c2) {
   return nu == 1 ? c : (nu == 2 ? c2 : c2 * c);
+}
+
+// x^n for n in {-3..3} \ {0} from x and 1/x
+__device__ __forceinline__ double ipow_pm3(int n, double x, double xi) {
+  const double b = n > 0 ? x : xi;
+  const int m = n > 0 ? n : -n;
+  return m == 1 ? b : (m == 2 ? b * b : b * b * b);
 }
 
 // Plain FP64 source at one node: omega_s (kg/m^3/s) and the point-implicit terms
@@ -59,6 +68,7 @@ __device__ __forceinline__ void chem_node(const T* uu, int np, double Tk, const 
   const double lnP = sp[14] - lnT;
   double c[NSPEC], c2[NSPEC], g[NSPEC], jd[NSPEC], j1[NSPEC];
   bool pos[NSPEC];
+  double gmax = 0.0;
 #pragma unroll
   for (int s = 0; s < NSPEC; ++s) {
     const double* q = sp + SP_W * s;
@@ -67,21 +77,51 @@ __device__ __forceinline__ void chem_node(const T* uu, int np, double Tk, const 
     pos[s] = c[s] > 0.0;
     // g/(RT) = h/(RT) - s/R as one polynomial in T plus the 1/T and ln T terms
     g[s] = q[2] + Tk * (q[3] + Tk * (q[4] + Tk * (q[5] + Tk * q[6]))) + q[7] * iT - q[8] * lnT;
+    gmax = fmax(gmax, fabs(g[s]));
     om[s] = 0.0;
     jd[s] = 0.0;
     j1[s] = 0.0;
+  }
+  // k_b = k_f X with X = exp(sum dnu_s g_s) P^-dn, P = 1e-6 p0 / (R_u T): from E_s = exp(g_s)
+  // taken once per node, X is a product of powers of E_s, 1/E_s and P.  A reaction takes it
+  // when X stays inside the double range, sum |dnu_s| max|g_s| < 700 (the integer gcap
+  // bounds sum |dnu_s|), and k_f is a normal number; otherwise one exp of the whole exponent.
+  double E[NSPEC], Ei[NSPEC];
+  const double P = sp[9] * iT, Pi = Tk * sp[10];
+  const int gcap = gmax < 700.0 ? (gmax > 0.0 ? (int)fmin(700.0 / gmax, 64.0) : 64) : 0;
+  if (gcap) {
+#pragma unroll
+    for (int s = 0; s < NSPEC; ++s) {
+      E[s] = exp(g[s]);
+      Ei[s] = 1.0 / E[s];
+    }
   }
 #pragma unroll 1
   for (int r = 0; r < nr; ++r) {
     const double* row = reac + RX_W * r;
     const int meta = (int)__double_as_longlong(row[RX_META]);
-    double dg = 0.0;
-#pragma unroll
-    for (int s = 0; s < NSPEC; ++s)
-      if (meta & (1 << (21 + s))) dg += row[20 + s] * g[s];
     const double lnkf = row[16] + row[17] * lnT - row[18] * iT;
     const double kf = exp(lnkf);
-    const double kb = exp(lnkf + dg - row[19] * lnP);
+    double kb;
+    // bits 26-29: sum |dnu_s|; bit 30: |dn| <= 3 (set at init)
+    if ((meta >> 30) & 1 && ((meta >> 26) & 15) <= gcap && lnkf > -700.0) {
+      double X = 1.0;
+      int dn = 0;
+#pragma unroll
+      for (int s = 0; s < NSPEC; ++s) {
+        const int ds = ((meta >> (10 + 2 * s)) & 3) - ((meta >> (2 * s)) & 3);
+        dn += ds;
+        if (ds) X *= ipow_pm3(ds, E[s], Ei[s]);
+      }
+      if (dn) X *= ipow_pm3(-dn, P, Pi);
+      kb = kf * X;
+    } else {
+      double dg = 0.0;
+#pragma unroll
+      for (int s = 0; s < NSPEC; ++s)
+        if (meta & (1 << (21 + s))) dg += row[20 + s] * g[s];
+      kb = exp(lnkf + dg - row[19] * lnP);
+    }
     double pf = kf, pb = kb;
 #pragma unroll
     for (int s = 0; s < NSPEC; ++s) {
@@ -472,6 +512,13 @@ cudaError_t dg_chem_init(DgThermo* th, const double* species_host, const double*
       if (o[20 + s] != 0.0) meta |= 1ll << (21 + s);
     }
     if (in[10] != 0.0) meta |= 1ll << 20;
+    int sabs = 0, dnt = 0;
+    for (int s = 0; s < NSPEC; ++s) {
+      const int ds = (int)in[5 + s] - (int)in[s];
+      sabs += ds < 0 ? -ds : ds;
+      dnt += ds;
+    }
+    if (sabs <= 15 && dnt >= -3 && dnt <= 3) meta |= ((long long)sabs << 26) | (1ll << 30);
     o[19] = dn;
     memcpy(&o[RX_META], &meta, sizeof(meta));
     for (int s = 0; s < NSPEC; ++s) o[26 + s] = o[20 + s] * in[11 + s];  // dnu_s eff_s
@@ -491,6 +538,8 @@ cudaError_t dg_chem_init(DgThermo* th, const double* species_host, const double*
     o[6] = in[5] / 5.0 - in[5] / 4.0;
     o[7] = in[6];
     o[8] = in[1];
+    o[9] = 1e-6 * DG_P0 / DG_RU;  // P = o[9] / T
+    o[10] = DG_RU / (1e-6 * DG_P0);  // 1/P = o[10] T
     o[14] = log(1e-6 * DG_P0 / DG_RU);
   }
   const size_t rs = th->f32 ? sizeof(float) : sizeof(double);
