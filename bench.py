@@ -345,7 +345,7 @@ def run_mlp_forward(n=4_608_000, reps=5):
 # reacting 24 x 24 x 8, N = 4, mixed form).  The temperature solve's count depends on the
 # Newton iterations its states need (1 to 2 from the cached temperature there).
 THERMO_FP64_FLOPS_PER_NODE = 119.0
-CHEM_FP64_FLOPS_PER_NODE = 2005.0
+CHEM_FP64_FLOPS_PER_NODE = 1714.0
 
 
 def _fp64_roofline(kernel, flops_per_node, nodes, ms_per_launch, fp64_peak):
