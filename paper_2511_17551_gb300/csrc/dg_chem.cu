@@ -84,11 +84,12 @@ __device__ __forceinline__ void chem_node(const T* uu, int np, double Tk, const 
   }
   // k_b = k_f X with X = exp(sum dnu_s g_s) P^-dn, P = 1e-6 p0 / (R_u T): from E_s = exp(g_s)
   // taken once per node, X is a product of powers of E_s, 1/E_s and P.  A reaction takes it
-  // when X stays inside the double range, sum |dnu_s| max|g_s| < 700 (the integer gcap
-  // bounds sum |dnu_s|), and k_f is a normal number; otherwise one exp of the whole exponent.
+  // when every partial product stays inside the double range: sum |dnu_s| max|g_s| < 650
+  // (the integer gcap bounds sum |dnu_s|; |P^-dn| adds at most e^42 for |dn| <= 3 and
+  // 200 K <= T <= 10^4 K) and k_f is a normal number; otherwise one exp of the whole exponent.
   double E[NSPEC], Ei[NSPEC];
   const double P = sp[9] * iT, Pi = Tk * sp[10];
-  const int gcap = gmax < 700.0 ? (gmax > 0.0 ? (int)fmin(700.0 / gmax, 64.0) : 64) : 0;
+  const int gcap = gmax < 650.0 ? (gmax > 0.0 ? (int)fmin(650.0 / gmax, 64.0) : 64) : 0;
   if (gcap) {
 #pragma unroll
     for (int s = 0; s < NSPEC; ++s) {

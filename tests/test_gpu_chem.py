@@ -79,7 +79,7 @@ def test_reacting_rk_steps(dg, precision, tol):
 
 def test_chem_source_both_backward_rate_forms(dg):
     """The backward rate constants come either from products of per-species exp(g_s) or,
-    where a product could leave the double range (sum |dnu_s| max|g_s| >= 700), from one exp
+    where a product could leave the double range (sum |dnu_s| max|g_s| >= 650), from one exp
     of the whole exponent.  A species table whose first species has twice its formation
     constant puts the cold nodes (g up to about 240) on the second form and the hot layer
     on the first; the FP64 source at every node matches the oracle's finite-rate source
@@ -107,15 +107,15 @@ def test_chem_source_both_backward_rate_forms(dg):
         T = dg.dg_get_temperature(s.ctx, (s.K, s.np)).reshape(-1)
         rhos = u[:, :5, :].transpose(0, 2, 1).reshape(-1, 5)
         _, _, S_o = oracle.chem_eval(sp, R, rhos, T, 0.0)
-        # both forms occur: max_s |g_s| / RT on either side of 700 / 4 (the mechanism's
-        # largest sum |dnu_s| is 4)
+        # both forms occur: max_s |g_s| on either side of 650 / 4 (the mechanism's largest
+        # sum |dnu_s| is 4)
         gmax = np.zeros(len(T))
         for q in range(5):
             a = sp[q, 1:8]
             h = a[0] + a[1] / 2 * T + a[2] / 3 * T ** 2 + a[3] / 4 * T ** 3 + a[4] / 5 * T ** 4 + a[5] / T
             sr = a[0] * np.log(T) + a[1] * T + a[2] / 2 * T ** 2 + a[3] / 3 * T ** 3 + a[4] / 4 * T ** 4 + a[6]
             gmax = np.maximum(gmax, np.abs(h - sr))
-        assert (gmax > 176.0).sum() > 100 and (gmax < 174.0).sum() > 100, (gmax.min(), gmax.max())
+        assert (gmax > 163.5).sum() > 100 and (gmax < 161.5).sum() > 100, (gmax.min(), gmax.max())
         scale = np.abs(S_o).sum(axis=1, keepdims=True) + 1e-300
         rel = np.abs(S - S_o) / scale
         print("source relative to the node scale: max", rel.max())
