@@ -560,6 +560,7 @@ def run_reacting(args, stream_ptr, world, fp64_peak):
     # at the first stage of every k-th step, the refresh's full check at the same tolerance)
     for key, tol, k in (("mixed_learned_source", 0.05, 0), ("mixed_learned_source_tol0.01", 0.01, 0),
                         ("mixed_corrected_source_tol0.002_k1", 0.002, 1),
+                        ("mixed_corrected_source_tol0.002_k2", 0.002, 2),
                         ("mixed_corrected_source_tol0.01_k1", 0.01, 1),
                         ("mixed_corrected_source_tol0.01_k2", 0.01, 2)):
         st = stats.copy()
