@@ -75,6 +75,12 @@ struct Swizzle {
   }
 };
 
+// resident-CTA target of the one-gas kernels: 8 (measured with the aliased layout below:
+// 9 and 10 CTAs of 96 threads cap the registers at 72 and 64, and the spills cost more than
+// the extra warps give back)
+#ifndef DG_RHS_CAP1
+#define DG_RHS_CAP1 8
+#endif
 template <int DIM, int N, int NSP, bool NS>
 struct Layout {
   using S = Shape<DIM, N>;
@@ -94,7 +100,14 @@ struct Layout {
   static constexpr int padded(int w) { return (SWZ && sizeof(real) == 4) ? w + (48 - w % 32) % 32 : w; }
   // per-element strides (reals) and region offsets of one CTA
   static constexpr int SU = padded(NV * NP), SQ = padded(NQ * NP), SJA = padded(DIM * DIM * NP);
-  static constexpr int SIJ = NP, SACC = padded(DIM * NV * NP), SFV = NS ? padded(NFV * NP) : 0;
+  // The staged viscous fluxes of direction d sit in the first DIM + 1 planes of direction d's
+  // block of the sums region (DIM blocks of NV planes), which the line phase overwrites with
+  // the sums: each line reads the fluxes of its own nodes in its own direction before it
+  // writes their sums, so the two never need separate space.  The staged low part of the
+  // compensated energy sits in direction 0's plane DIM + 1 (free until the line phase).
+  static constexpr int SIJ = NP, SACC = padded(DIM * NV * NP), SFV = 0;
+  static constexpr int ELO = DIM + 1;  // plane of the compensated energy's low part
+  static __device__ __forceinline__ int fvp(int c) { return (c / (DIM + 1)) * NV + c % (DIM + 1); }
   static constexpr int SPC = NSP > 1 ? padded(2 * NP) : 0, SDU = NV * NP;
   static constexpr int U = 0;
   static constexpr int Q = U + EPB * SU;
@@ -104,10 +117,10 @@ struct Layout {
   static constexpr int FV = ACC + EPB * SACC;
   static constexpr int PC = FV + EPB * SFV;          // mixtures: p, c per node
   static constexpr int DU = PC + EPB * SPC;           // prefetched RK register du
-  // resident-CTA target (measured: 8 of the 96-thread CTAs for one gas; 3 for mixtures,
-  // whose 9-variable line accumulators spill below ~110 registers a thread), lowered where
-  // shared memory binds
-  static constexpr int CAP = NSP > 1 ? 3 : 8;
+  // resident-CTA target (8 of the 96-thread CTAs for one gas; 3 for mixtures, whose
+  // 9-variable line accumulators spill below ~110 registers a thread), lowered where shared
+  // memory binds
+  static constexpr int CAP = NSP > 1 ? 3 : DG_RHS_CAP1;
   static constexpr int ctas_of(size_t bytes) {
     return (int)((227 * 1024) / (bytes + 1024)) >= CAP ? CAP : (int)((227 * 1024) / (bytes + 1024));
   }
@@ -206,6 +219,25 @@ __device__ __forceinline__ void stage_strided(real* dst, const real* src, int ne
 
 // stage one NP-block per element (source stride sstride reals between elements) into
 // dst[e][NP], 16-byte copies when aligned
+// W reals per element from a source element stride sstride to a destination stride dstride
+template <int W>
+__device__ __forceinline__ void stage_block(real* dst, int dstride, const real* src, int sstride, int ne, int tid,
+                                            int nth) {
+  constexpr int V = 16 / sizeof(real);
+  if (W % V == 0 && (sstride % V) == 0 && (dstride % V) == 0 && (((uintptr_t)dst | (uintptr_t)src) & 15) == 0) {
+    constexpr int PER = W / V;
+    for (int i = tid; i < ne * PER; i += nth) {
+      const int e = i / PER, r = i % PER;
+      cp_async16(dst + e * dstride + r * V, src + (int64_t)e * sstride + r * V);
+    }
+  } else {
+    for (int i = tid; i < ne * W; i += nth) {
+      const int e = i / W, r = i % W;
+      cp_async_small<sizeof(real)>(dst + e * dstride + r, src + (int64_t)e * sstride + r);
+    }
+  }
+}
+
 template <int NP>
 __device__ __forceinline__ void stage_rows(real* dst, const real* src, int sstride, int ne, int tid, int nth) {
   constexpr int V = 16 / sizeof(real);
@@ -279,8 +311,8 @@ template <int DIM, int N, int NSP, bool NS, int FL, bool BND = true>
 // the split forms (FL >= 2) hold both nodes' conserved states per flux pair: at most 6
 // (96 registers; at 7 the allocator is held to 80 and spills)
 __global__ void __launch_bounds__(Layout<DIM, N, NSP, NS>::THREADS,
-                                  (Layout<DIM, N, NSP, NS>::MINB > (FL == 1 ? 8 : FL ? 6 : 5))
-                                      ? (FL == 1 ? 8 : FL ? 6 : 5)
+                                  (Layout<DIM, N, NSP, NS>::MINB > (FL == 1 ? DG_RHS_CAP1 : FL ? 6 : 5))
+                                      ? (FL == 1 ? DG_RHS_CAP1 : FL ? 6 : 5)
                                       : Layout<DIM, N, NSP, NS>::MINB)
 rhs_kernel(const DgArgs a, const KConst kc) {
   using S = Shape<DIM, N>;
@@ -293,7 +325,7 @@ rhs_kernel(const DgArgs a, const KConst kc) {
   real* sja = sm + L::JA;
   real* sij = sm + L::IJ;
   real* sacc = sm + L::ACC;
-  real* sfv = sm + L::FV;
+  real* sfv = sacc;  // aliased: see Layout
   real* spc = sm + L::PC;
   real* sdu = sm + L::DU;
   __shared__ real s_alpha[EPB];
@@ -352,10 +384,16 @@ rhs_kernel(const DgArgs a, const KConst kc) {
         if (kind == 1) copy(sja, L::SJA, (const real*)a.Ja, DIM * DIM * NP, e);
         if (kind == 2) copy(sij, L::SIJ, (const real*)a.invJ, NP, e);
         if (kind == 3 && NSP > 1) copy(spc, L::SPC, (const real*)a.pc, 2 * NP, e);
-        if (kind == 4 && NS) copy(sfv, L::SFV, (const real*)a.gradW, L::NFV * NP, e);
+        if (kind == 4 && NS) {
+#pragma unroll
+          for (int d = 0; d < DIM; ++d)
+            bulk_g2s(sfv + e * L::SACC + d * NV * NP,
+                     (const real*)a.gradW + ((e0 + e) * L::NFV + d * (DIM + 1)) * NP, RS * (DIM + 1) * NP, &s_bar);
+        }
         if (kind == 5 && pre_du) copy(sdu, L::SDU, (const real*)a.du, NV * NP, e);
         if (kind == 6 && have_elo)  // rows at a source stride of NV NP: one per element
-          bulk_g2s(sacc + e * NP, (const real*)a.ulo + (e0 + e) * NV * NP + (NSP + DIM) * NP, RS * NP, &s_bar);
+          bulk_g2s(sacc + e * L::SACC + L::ELO * NP, (const real*)a.ulo + (e0 + e) * NV * NP + (NSP + DIM) * NP,
+                   RS * NP, &s_bar);
       }
     }
   } else {
@@ -365,11 +403,14 @@ rhs_kernel(const DgArgs a, const KConst kc) {
     if (NSP > 1)
       stage_strided<2, (NSP > 1 ? L::SPC : 2 * NP), NP>(spc, (const real*)a.pc + e0 * 2 * NP, ne, tid, nth);
     if (NS)
-      stage_strided<(NS ? L::NFV : 1), (NS ? L::SFV : NP), NP>(sfv, (const real*)a.gradW + e0 * L::NFV * NP, ne,
-                                                               tid, nth);
+#pragma unroll
+      for (int d = 0; d < DIM; ++d)
+        stage_block<(DIM + 1) * NP>(sfv + d * NV * NP, L::SACC, (const real*)a.gradW + (e0 * L::NFV + d * (DIM + 1)) * NP,
+                                    L::NFV * NP, ne, tid, nth);
     if (pre_du) stage_strided<NV, L::SDU, NP>(sdu, (const real*)a.du + e0 * NV * NP, ne, tid, nth);
     if (have_elo)
-      stage_rows<NP>(sacc, (const real*)a.ulo + e0 * NV * NP + (NSP + DIM) * NP, NV * NP, ne, tid, nth);
+      stage_block<NP>(sacc + L::ELO * NP, L::SACC, (const real*)a.ulo + e0 * NV * NP + (NSP + DIM) * NP, NV * NP, ne,
+                      tid, nth);
   }
   // The line of this thread (phase B) and its neighbour traces at both end nodes (the
   // element's face nodes of faces 2d and 2d + 1): requested now, so that they arrive while
@@ -471,7 +512,7 @@ rhs_kernel(const DgArgs a, const KConst kc) {
       }
       real p, pp;
       if (NSP == 1) {
-        const real elo = have_elo ? sacc[e * NP + n] : real(0);
+        const real elo = have_elo ? sacc[e * L::SACC + L::ELO * NP + n] : real(0);
         pp = kc.gm1 * (((uu[(NSP + DIM) * NP] - kc.eref) + elo) - real(0.5) * ke);
         p = pp + kc.pref;
       } else {
@@ -493,9 +534,9 @@ rhs_kernel(const DgArgs a, const KConst kc) {
         // the contravariant viscous fluxes of the gradient kernel: slot (d, c) holds
         // sum_x Ja^d_x f^v_{x,c}, the flux along reference direction d (and, at a face of
         // direction d, the own f^v . n); rewritten at the swizzled position
-        const real* gi = sfv + e * L::SFV + n;
+        const real* gi = sfv + e * L::SACC + n;
 #pragma unroll
-        for (int c = 0; c < (NS ? L::NFV : 1); ++c) fl[c] = gi[c * NP];
+        for (int c = 0; c < (NS ? L::NFV : 1); ++c) fl[c] = gi[L::fvp(c) * NP];
       }
     }
     if (L::SWZ) __syncthreads();
@@ -510,9 +551,9 @@ rhs_kernel(const DgArgs a, const KConst kc) {
         }
       }
       if (NS) {
-        real* so = sfv + e * L::SFV + pn;
+        real* so = sfv + e * L::SACC + pn;
 #pragma unroll
-        for (int c = 0; c < (NS ? L::NFV : 1); ++c) so[c * NP] = fl[c];
+        for (int c = 0; c < (NS ? L::NFV : 1); ++c) so[L::fvp(c) * NP] = fl[c];
       }
     }
   }
@@ -596,7 +637,7 @@ rhs_kernel(const DgArgs a, const KConst kc) {
         // state's velocity and mu(T) (mean as at an interface); no-slip walls: Fv* = (m, h)
         // at zero velocity, h = 0 on an adiabatic wall (Fv* itself, not a mean)
         const bool wall = bkind == DG_BC_NOSLIP_ADIABATIC || bkind == DG_BC_ISOTHERMAL;
-        const real* fvd = sfv + e * L::SFV + d * (DIM + 1) * NP + node;
+        const real* fvd = sfv + e * L::SACC + d * NV * NP + node;
         real fx[DIM + 1];
         if (!BND || nb >= 0) {
 #pragma unroll
@@ -735,7 +776,7 @@ rhs_kernel(const DgArgs a, const KConst kc) {
     if (NS) {
       // viscous volume term along the line: D Fv (enters the RHS with + sign), with the
       // contravariant flux of this direction read from shared memory
-      const real* fvd = sfv + e * L::SFV + d * (DIM + 1) * NP;
+      const real* fvd = sfv + e * L::SACC + d * NV * NP;
       real fl[N1][DIM + 1];
 #pragma unroll
       for (int l = 0; l < N1; ++l)
