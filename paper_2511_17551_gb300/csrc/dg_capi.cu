@@ -8,6 +8,8 @@
 #include <string.h>
 #include <time.h>
 
+#include <utility>
+
 #include "../../include/dg.h"
 #include "dg_internal.h"
 #include "dg_thermo.h"
@@ -30,7 +32,8 @@ struct dg_ctx {
   double *Ja64, *J64, *invJ64;
   float *Ja32, *invJ32;
   void* u[2];
-  float* ulo;  // mixed form: low part of the compensated state (in place)
+  float* ulo;      // mixed form: low part of the compensated current state
+  float* ulo_alt;  // the other buffer: an RK stage writes the new state's low part there
   int cur;
   void* du;
   void* gradW;
@@ -505,7 +508,8 @@ cudaError_t run_thermo(dg_ctx* c, const void* u) {
 
 cudaError_t run_positivity(dg_ctx* c, const DgArgs& b) {
   return timed(c, DG_PROF_LIMITER, [&] {
-    return c->precision == DG_MIXED ? dg_f32_positivity(b, b.out, c->ulo, c->pos_eps, c->pos_count, c->stream)
+    return c->precision == DG_MIXED ? dg_f32_positivity(b, b.out, b.ulo_out ? b.ulo_out : c->ulo, c->pos_eps,
+                                                        c->pos_count, c->stream)
                                     : dg_f64_positivity(b, b.out, nullptr, c->pos_eps, c->pos_count, c->stream);
   });
 }
@@ -583,7 +587,7 @@ void free_ctx(dg_ctx* c) {
   if (!c) return;
   cudaSetDevice(c->dev);
   void* ptrs[] = {c->nbr, c->Ja64, c->J64, c->invJ64, c->Ja32, c->invJ32, c->u[0], c->u[1],
-                  c->du, c->ulo, c->pos_count, c->gradW, c->alpha_raw, c->alpha_used, c->bc_kind, c->bc_u, c->scal,
+                  c->du, c->ulo, c->ulo_alt, c->pos_count, c->gradW, c->alpha_raw, c->alpha_used, c->bc_kind, c->bc_u, c->scal,
                   c->lam, c->status, c->partial, c->stage64};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -762,7 +766,10 @@ dg_status dg_init_mesh(const dg_mesh_desc* m, const dg_physics_desc* p, dg_ctx**
     TRYM(c->u[0], c->rs * nst);
     TRYM(c->u[1], c->rs * nst);
     TRYM(c->du, c->rs * nst);
-    if (c->precision == DG_MIXED) TRYM(c->ulo, sizeof(float) * nst);
+    if (c->precision == DG_MIXED) {
+      TRYM(c->ulo, sizeof(float) * nst);
+      TRYM(c->ulo_alt, sizeof(float) * nst);
+    }
     if (c->pos_eps > 0.0) {
       TRYM(c->pos_count, sizeof(unsigned long long));
       TRY(cudaMemset(c->pos_count, 0, sizeof(unsigned long long)));
@@ -1004,6 +1011,7 @@ dg_status dg_step_rk(dg_ctx* c, int nsteps, double cfl, double dt_fixed, double*
       b.out = c->u[c->cur ^ 1];
       b.du = c->du;
       b.ulo = c->ulo;
+      b.ulo_out = c->ulo_alt;
       b.mode = 1;
       b.stage = s;
       b.rkA = A[s];
@@ -1017,6 +1025,7 @@ dg_status dg_step_rk(dg_ctx* c, int nsteps, double cfl, double dt_fixed, double*
       CK(run_rhs(c, b));
       if (c->pos_eps > 0.0) CK(run_positivity(c, b));
       c->cur ^= 1;
+      std::swap(c->ulo, c->ulo_alt);
     }
     if (cfl_mode) {
       if (c->n_species > 0) {

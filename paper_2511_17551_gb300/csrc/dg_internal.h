@@ -35,7 +35,9 @@ struct DgArgs {
   const void* u;          // [K][nv][np] input state
   void* out;              // mode 0: rhs; mode 1: new state
   void* du;               // mode 1: 2N-storage register
-  void* ulo;              // mode 1, FP32 form: low part of the compensated state (or null)
+  void* ulo;              // mode 1, FP32 form: low part of the compensated input state (or null)
+  void* ulo_out;          // mode 1, FP32 form: low part of the new state (a second buffer: other
+                          // CTAs still read their neighbours' input low parts)
   const void* Ja;         // [K][dim][dim][np]
   const void* invJ;       // [K][np]
   void* gradW;            // [K][dim][dim+1][np] (Navier-Stokes): grad_mode 0 the contravariant

@@ -806,7 +806,7 @@ rhs_kernel(const DgArgs a, const KConst kc) {
   // ---- phase C: one thread per node and pass.
   real lam_a = 0, lam_v = 0;
   constexpr int CIT = (EPB * NP + L::THREADS - 1) / L::THREADS;
-  const bool comp = sizeof(real) == 4 && a.mode == 1 && a.ulo != nullptr;
+  const bool comp = sizeof(real) == 4 && a.mode == 1 && a.ulo != nullptr && a.ulo_out != nullptr;
   // one node per pass (a loop, not unrolled: one code instance of the update)
 #pragma unroll 1
   for (int it = 0; it < CIT; ++it) {
@@ -856,7 +856,7 @@ rhs_kernel(const DgArgs a, const KConst kc) {
           const real inc = lo_r[0][k] + kc.rkB * dn;
           const real s2 = hi + inc;
           const real bb = s2 - hi;
-          ((real*)a.ulo)[gbase + k * NP] = (hi - (s2 - bb)) + (inc - bb);
+          ((real*)a.ulo_out)[gbase + k * NP] = (hi - (s2 - bb)) + (inc - bb);
           un[k] = s2;
         } else {
           un[k] = hi + kc.rkB * dn;
