@@ -81,7 +81,7 @@ struct Swizzle {
 #ifndef DG_RHS_CAP1
 #define DG_RHS_CAP1 8
 #endif
-template <int DIM, int N, int NSP, bool NS>
+template <int DIM, int N, int NSP, bool NS, bool AL = true>
 struct Layout {
   using S = Shape<DIM, N>;
   static constexpr int NV = NSP + DIM + 1;
@@ -100,14 +100,20 @@ struct Layout {
   static constexpr int padded(int w) { return (SWZ && sizeof(real) == 4) ? w + (48 - w % 32) % 32 : w; }
   // per-element strides (reals) and region offsets of one CTA
   static constexpr int SU = padded(NV * NP), SQ = padded(NQ * NP), SJA = padded(DIM * DIM * NP);
-  // The staged viscous fluxes of direction d sit in the first DIM + 1 planes of direction d's
-  // block of the sums region (DIM blocks of NV planes), which the line phase overwrites with
-  // the sums: each line reads the fluxes of its own nodes in its own direction before it
-  // writes their sums, so the two never need separate space.  The staged low part of the
-  // compensated energy sits in direction 0's plane DIM + 1 (free until the line phase).
-  static constexpr int SIJ = NP, SACC = padded(DIM * NV * NP), SFV = 0;
-  static constexpr int ELO = DIM + 1;  // plane of the compensated energy's low part
-  static __device__ __forceinline__ int fvp(int c) { return (c / (DIM + 1)) * NV + c % (DIM + 1); }
+  // AL (the production flux pair's instances): the staged viscous fluxes of direction d sit in
+  // the first DIM + 1 planes of direction d's block of the sums region (DIM blocks of NV
+  // planes), which the line phase overwrites with the sums: each line reads the fluxes of
+  // its own nodes in its own direction before it writes their sums, so the two need no
+  // separate space, and the staged low part of the compensated energy sits in direction 0's
+  // plane DIM + 1 (free until the line phase).  Otherwise (measured slower for the
+  // compile-time split forms) the fluxes have a region of their own, planes [d][c], and the
+  // low energy part sits at the start of the sums region, [e][node].
+  static constexpr int SIJ = NP, SACC = padded(DIM * NV * NP);
+  static constexpr int SFV = (AL || !NS) ? 0 : padded(NFV * NP);
+  static constexpr int FVE = AL ? SACC : SFV;          // element stride of the fluxes
+  static constexpr int FVD = AL ? NV : DIM + 1;        // planes per direction of the fluxes
+  static __device__ __forceinline__ int fvp(int c) { return (c / (DIM + 1)) * FVD + c % (DIM + 1); }
+  static __device__ __forceinline__ int elo(int e) { return AL ? e * SACC + (DIM + 1) * NP : e * NP; }
   static constexpr int SPC = NSP > 1 ? padded(2 * NP) : 0, SDU = NV * NP;
   static constexpr int U = 0;
   static constexpr int Q = U + EPB * SU;
@@ -124,14 +130,19 @@ struct Layout {
   static constexpr int ctas_of(size_t bytes) {
     return (int)((227 * 1024) / (bytes + 1024)) >= CAP ? CAP : (int)((227 * 1024) / (bytes + 1024));
   }
+  // The residency and register targets below are taken on the footprint with the viscous
+  // fluxes in a region of their own (RSV more reals): with the aliasing alone they would
+  // rise for the larger instances (N = 7, FP64) and cut their registers into spills; the
+  // smaller allocation leaves the SM more L1 cache instead.
+  static constexpr int RSV = AL ? EPB * (NS ? padded(NFV * NP) : 0) : 0;
   // du is staged with the rest when that does not cost a resident CTA
   static constexpr bool PREFETCH_DU =
-      ctas_of(sizeof(real) * (DU + EPB * SDU)) == ctas_of(sizeof(real) * DU);
+      ctas_of(sizeof(real) * (DU + RSV + EPB * SDU)) == ctas_of(sizeof(real) * (DU + RSV));
   static constexpr int TOTAL = DU + (PREFETCH_DU ? EPB * SDU : 0);
   static constexpr int THREADS = ((EPB * S::LINES + 31) / 32) * 32;
   static constexpr size_t SMEM = sizeof(real) * TOTAL;
   // CTAs per SM we ask the register allocator for (bounded by shared memory)
-  static constexpr int MINB = ctas_of(SMEM) < 1 ? 1 : ctas_of(SMEM);
+  static constexpr int MINB = ctas_of(SMEM + sizeof(real) * RSV) < 1 ? 1 : ctas_of(SMEM + sizeof(real) * RSV);
   // face nodes each thread takes in the interface phase
   static constexpr int FIT = (EPB * FACE_NODES + THREADS - 1) / THREADS;
 };
@@ -310,13 +321,13 @@ template <int DIM, int N, int NSP, bool NS, int FL, bool BND = true>
 // (up to 136 registers a thread at 96 threads) instead of 8, so that it does not spill;
 // the split forms (FL >= 2) hold both nodes' conserved states per flux pair: at most 6
 // (96 registers; at 7 the allocator is held to 80 and spills)
-__global__ void __launch_bounds__(Layout<DIM, N, NSP, NS>::THREADS,
-                                  (Layout<DIM, N, NSP, NS>::MINB > (FL == 1 ? DG_RHS_CAP1 : FL ? 6 : 5))
+__global__ void __launch_bounds__(Layout<DIM, N, NSP, NS, FL == 1>::THREADS,
+                                  (Layout<DIM, N, NSP, NS, FL == 1>::MINB > (FL == 1 ? DG_RHS_CAP1 : FL ? 6 : 5))
                                       ? (FL == 1 ? DG_RHS_CAP1 : FL ? 6 : 5)
-                                      : Layout<DIM, N, NSP, NS>::MINB)
+                                      : Layout<DIM, N, NSP, NS, FL == 1>::MINB)
 rhs_kernel(const DgArgs a, const KConst kc) {
   using S = Shape<DIM, N>;
-  using L = Layout<DIM, N, NSP, NS>;
+  using L = Layout<DIM, N, NSP, NS, FL == 1>;
   constexpr int NV = L::NV, NP = L::NP, N1 = S::N1, EPB = L::EPB, NQ = L::NQ;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   real* sm = reinterpret_cast<real*>(smem_raw);
@@ -325,7 +336,7 @@ rhs_kernel(const DgArgs a, const KConst kc) {
   real* sja = sm + L::JA;
   real* sij = sm + L::IJ;
   real* sacc = sm + L::ACC;
-  real* sfv = sacc;  // aliased: see Layout
+  real* sfv = sm + (L::SFV ? L::FV : L::ACC);  // the sums region itself when aliased (AL)
   real* spc = sm + L::PC;
   real* sdu = sm + L::DU;
   __shared__ real s_alpha[EPB];
@@ -385,15 +396,18 @@ rhs_kernel(const DgArgs a, const KConst kc) {
         if (kind == 2) copy(sij, L::SIJ, (const real*)a.invJ, NP, e);
         if (kind == 3 && NSP > 1) copy(spc, L::SPC, (const real*)a.pc, 2 * NP, e);
         if (kind == 4 && NS) {
+          if (L::FVD == DIM + 1) {
+            copy(sfv, L::FVE, (const real*)a.gradW, L::NFV * NP, e);
+          } else {
 #pragma unroll
-          for (int d = 0; d < DIM; ++d)
-            bulk_g2s(sfv + e * L::SACC + d * NV * NP,
-                     (const real*)a.gradW + ((e0 + e) * L::NFV + d * (DIM + 1)) * NP, RS * (DIM + 1) * NP, &s_bar);
+            for (int d = 0; d < DIM; ++d)
+              bulk_g2s(sfv + e * L::FVE + d * L::FVD * NP,
+                       (const real*)a.gradW + ((e0 + e) * L::NFV + d * (DIM + 1)) * NP, RS * (DIM + 1) * NP, &s_bar);
+          }
         }
         if (kind == 5 && pre_du) copy(sdu, L::SDU, (const real*)a.du, NV * NP, e);
         if (kind == 6 && have_elo)  // rows at a source stride of NV NP: one per element
-          bulk_g2s(sacc + e * L::SACC + L::ELO * NP, (const real*)a.ulo + (e0 + e) * NV * NP + (NSP + DIM) * NP,
-                   RS * NP, &s_bar);
+          bulk_g2s(sacc + L::elo(e), (const real*)a.ulo + (e0 + e) * NV * NP + (NSP + DIM) * NP, RS * NP, &s_bar);
       }
     }
   } else {
@@ -405,12 +419,13 @@ rhs_kernel(const DgArgs a, const KConst kc) {
     if (NS)
 #pragma unroll
       for (int d = 0; d < DIM; ++d)
-        stage_block<(DIM + 1) * NP>(sfv + d * NV * NP, L::SACC, (const real*)a.gradW + (e0 * L::NFV + d * (DIM + 1)) * NP,
-                                    L::NFV * NP, ne, tid, nth);
+        stage_block<(DIM + 1) * NP>(sfv + d * L::FVD * NP, L::FVE,
+                                    (const real*)a.gradW + (e0 * L::NFV + d * (DIM + 1)) * NP, L::NFV * NP, ne, tid,
+                                    nth);
     if (pre_du) stage_strided<NV, L::SDU, NP>(sdu, (const real*)a.du + e0 * NV * NP, ne, tid, nth);
     if (have_elo)
-      stage_block<NP>(sacc + L::ELO * NP, L::SACC, (const real*)a.ulo + e0 * NV * NP + (NSP + DIM) * NP, NV * NP, ne,
-                      tid, nth);
+      stage_block<NP>(sacc + L::elo(0), L::elo(1) - L::elo(0), (const real*)a.ulo + e0 * NV * NP + (NSP + DIM) * NP,
+                      NV * NP, ne, tid, nth);
   }
   // The line of this thread (phase B) and its neighbour traces at both end nodes (the
   // element's face nodes of faces 2d and 2d + 1): requested now, so that they arrive while
@@ -512,7 +527,7 @@ rhs_kernel(const DgArgs a, const KConst kc) {
       }
       real p, pp;
       if (NSP == 1) {
-        const real elo = have_elo ? sacc[e * L::SACC + L::ELO * NP + n] : real(0);
+        const real elo = have_elo ? sacc[L::elo(e) + n] : real(0);
         pp = kc.gm1 * (((uu[(NSP + DIM) * NP] - kc.eref) + elo) - real(0.5) * ke);
         p = pp + kc.pref;
       } else {
@@ -534,7 +549,7 @@ rhs_kernel(const DgArgs a, const KConst kc) {
         // the contravariant viscous fluxes of the gradient kernel: slot (d, c) holds
         // sum_x Ja^d_x f^v_{x,c}, the flux along reference direction d (and, at a face of
         // direction d, the own f^v . n); rewritten at the swizzled position
-        const real* gi = sfv + e * L::SACC + n;
+        const real* gi = sfv + e * L::FVE + n;
 #pragma unroll
         for (int c = 0; c < (NS ? L::NFV : 1); ++c) fl[c] = gi[L::fvp(c) * NP];
       }
@@ -551,7 +566,7 @@ rhs_kernel(const DgArgs a, const KConst kc) {
         }
       }
       if (NS) {
-        real* so = sfv + e * L::SACC + pn;
+        real* so = sfv + e * L::FVE + pn;
 #pragma unroll
         for (int c = 0; c < (NS ? L::NFV : 1); ++c) so[L::fvp(c) * NP] = fl[c];
       }
@@ -637,7 +652,7 @@ rhs_kernel(const DgArgs a, const KConst kc) {
         // state's velocity and mu(T) (mean as at an interface); no-slip walls: Fv* = (m, h)
         // at zero velocity, h = 0 on an adiabatic wall (Fv* itself, not a mean)
         const bool wall = bkind == DG_BC_NOSLIP_ADIABATIC || bkind == DG_BC_ISOTHERMAL;
-        const real* fvd = sfv + e * L::SACC + d * NV * NP + node;
+        const real* fvd = sfv + e * L::FVE + d * L::FVD * NP + node;
         real fx[DIM + 1];
         if (!BND || nb >= 0) {
 #pragma unroll
@@ -776,7 +791,7 @@ rhs_kernel(const DgArgs a, const KConst kc) {
     if (NS) {
       // viscous volume term along the line: D Fv (enters the RHS with + sign), with the
       // contravariant flux of this direction read from shared memory
-      const real* fvd = sfv + e * L::SACC + d * NV * NP;
+      const real* fvd = sfv + e * L::FVE + d * L::FVD * NP;
       real fl[N1][DIM + 1];
 #pragma unroll
       for (int l = 0; l < N1; ++l)
@@ -1724,7 +1739,7 @@ cudaError_t set_smem(KernelT k, size_t bytes) {
 
 template <int DIM, int N, int NSP, bool NS, int FL, bool BND>
 cudaError_t launch_rhs_b(const DgArgs& a, cudaStream_t st) {
-  using L = Layout<DIM, N, NSP, NS>;
+  using L = Layout<DIM, N, NSP, NS, FL == 1>;
   auto k = rhs_kernel<DIM, N, NSP, NS, FL, BND>;
   cudaError_t err = set_smem(k, L::SMEM);
   if (err != cudaSuccess) return err;
