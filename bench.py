@@ -48,7 +48,7 @@ WORDS_GRAD = 5 + 9 + 1 + 12
 # dram__bytes_read.sum + dram__bytes_write.sum per node of one launch of the current
 # mixed-form NS N=3 rhs_kernel on the full 32^3 workload (one ncu capture, one pass:
 # 271,931,392 B read + 95,960,832 B written over 2,097,152 nodes)
-RHS_DRAM_B_PER_NODE = 175.42
+RHS_DRAM_B_PER_NODE = 176.64
 # FP64 flops per node of the FP64-form NS N=3 rhs_kernel (2 DFMA + DMUL + DADD thread
 # instructions, one ncu capture of the 16^3 case): its roofline is the FP64 pipe
 RHS_FP64_FLOPS_PER_NODE = 1005.3
