@@ -996,7 +996,8 @@ dg_status dg_step_rk(dg_ctx* c, int nsteps, double cfl, double dt_fixed, double*
   a.dt_fixed = dt_fixed;
   if (cfl_mode) {
     a.u = c->u[c->cur];
-    if (c->n_species > 0) CK(run_thermo(c, a.u));
+    // (a solve of this very state, e.g. the previous call's last wave-speed solve, stands)
+    if (c->n_species > 0 && !(c->thermo_ok && c->thermo_u == a.u)) CK(run_thermo(c, a.u));
     CK(cudaMemsetAsync(c->lam + 2 * c->lam_slot, 0, 2 * sizeof(unsigned long long), c->stream));
     CK(run_lambda(c, a, c->lam_slot));
   }
