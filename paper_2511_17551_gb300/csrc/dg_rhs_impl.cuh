@@ -132,8 +132,8 @@ struct Layout {
   }
   // The residency and register targets below are taken on the footprint with the viscous
   // fluxes in a region of their own (RSV more reals): with the aliasing alone they would
-  // rise for the larger instances (N = 7, FP64) and cut their registers into spills; the
-  // smaller allocation leaves the SM more L1 cache instead.
+  // rise for the larger instances (N = 7, FP64) and cut their registers into spills; only the
+  // allocation shrinks.
   static constexpr int RSV = AL ? EPB * (NS ? padded(NFV * NP) : 0) : 0;
   // du is staged with the rest when that does not cost a resident CTA
   static constexpr bool PREFETCH_DU =
