@@ -461,6 +461,22 @@ def test_refresh_schedule(env, trained_source):
             dg.dg_set_source_refresh(s.ctx, -1)
     finally:
         s.close()
+    # contexts without chemistry: a frozen mixture and a single gas
+    import workloads as W
+    x, _ = dg.dg_lgl_nodes(3)
+    xyz, nbr, face, w = cases.mixture_ogrid(x)
+    kinds, bcp = cases.mixture_bc(w)
+    frozen = dg.Solver(3, 3, xyz, nbr, face, n_species=5, species=W.species_table(), volume_flux=1,
+                       surface_flux=0, bc_kind=kinds, bc_prim=bcp)
+    xyz1, nbr1, face1 = W.box_mesh((2, 2, 2), x, (0.0,) * 3, (1.0,) * 3, periodic=True)
+    gas = dg.Solver(3, 3, xyz1, nbr1, face1)
+    try:
+        for ctx in (frozen.ctx, gas.ctx):
+            with pytest.raises(dg.DgError):
+                dg.dg_set_source_refresh(ctx, 1)
+    finally:
+        frozen.close()
+        gas.close()
 
 
 # the corrected learned source over the same run: refresh every CORR_PERIOD steps, the
