@@ -489,13 +489,15 @@ CORR_TOL = 0.1
 CORR_L2_BAR = 1e-5
 
 
-def test_corrected_source_run_against_oracle(env, trained_source):
-    """The FP64 form with the corrected learned source (refresh every CORR_PERIOD steps,
-    tolerances CORR_TOL), LEARNED_STEPS CK45 steps with the limiter and blending, against
-    the oracle's plain FP64 run: every conserved field within CORR_L2_BAR."""
+@pytest.mark.parametrize("precision", [0, 1])
+def test_corrected_source_run_against_oracle(env, trained_source, precision):
+    """The FP64 and the mixed form with the corrected learned source (refresh every
+    CORR_PERIOD steps, tolerances CORR_TOL), LEARNED_STEPS CK45 steps with the limiter and
+    blending, against the oracle's plain FP64 run: every conserved field within
+    CORR_L2_BAR."""
     dg, oracle, torch = env
     params, stats, hist, dt = trained_source
-    s = _reacting(dg, limited=True)
+    s = _reacting(dg, precision=precision, limited=True)
     o, u_o = _reacting_oracle(oracle, limited=True)
     try:
         u_ref, _ = o.step_rk(u_o, LEARNED_STEPS, dt_fixed=dt)
@@ -509,7 +511,7 @@ def test_corrected_source_run_against_oracle(env, trained_source):
         u_c, _ = s.get_state()
         acc, fb = dg.dg_surrogate_stats(s.ctx, dg.DG_SURROGATE_SOURCE)
         e_c = cases.field_errors(u_c, u_ref, 5, 3)
-        rec = {"steps": LEARNED_STEPS, "refresh_period": CORR_PERIOD,
+        rec = {"steps": LEARNED_STEPS, "refresh_period": CORR_PERIOD, "form": ("FP64", "mixed")[precision],
                "accepted_fraction": acc / max(1, acc + fb), "l2_corrected_vs_oracle": e_c.tolist()}
         print("corrected learned-source run:", rec)
         import json
